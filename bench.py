@@ -1,0 +1,323 @@
+"""Benchmark: free-space stokeslet Spectral Ewald sum, N = 1e6 uniform points.
+
+One step = one full evaluation (se_eval: binning, spreading, R2C FFT, scaling,
+C2R FFT, gather + self term, real-space sum) of the FP32 path (relative error
+2e-6, FFT grid capped at 256^3) on inputs already resident in HBM.  The FP64
+path (relative error 1e-10) is timed on the same points and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank evaluates its own copy of the workload
+(replicas; weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_POINTS = 1_000_000
+BOX = (0.0, 0.0, 0.0, 1.0)
+METRIC = "Mpoints/s, free-space stokeslet SE N=1e6: FP32 @2e-6 vs FP64 @1e-10; % HBM"
+WORKLOAD = "stokeslet sum, N=1e6 uniform iid in [0,1)^3, f iid N(0,1)^3; FP32 path rel. err 2e-6 (P=12, FFT <= 256^3) beside FP64 path rel. err 1e-10"
+OUR_KERNELS_PER_EVAL = 9  # bin count, 2 scans, bin scatter, zero octant, spread, scale, gather, real space
+# FP32 flops of one screened stokeslet pair (see the design notes): difference 3,
+# |r|^2 5, rsqrt 1, r 1, xi r 1, -xi^2 r^2 1, exp 2, erfc 20, c e 1, A 2, B 3,
+# r.f 5, B (r.f) 1, u += A f + B (r.f) r 12.
+FLOP_PER_PAIR = 58
+
+
+def pair_fraction_unit_cube(r: float) -> float:
+    """P(|X - Y| <= r) for X, Y uniform in the unit cube (r <= 1): the integral of the
+    distance density 4 pi r^2 - 6 pi r^3 + 8 r^4 - r^5."""
+    return 4 * math.pi / 3 * r**3 - 1.5 * math.pi * r**4 + 1.6 * r**5 - r**6 / 6
+
+
+def read_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        try:
+            rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+            sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+            mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = set()
+            for r in rows:
+                for k, nm in enumerate(names):
+                    if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            return {"sm_mhz": float(np.median(sm)) if sm else None,
+                    "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                    "samples": len(rows)}
+        except Exception:
+            return None
+
+
+def cpu_baseline(x, f, budget_s=12.0):
+    """The oracle's FP64 direct sum (all N sources) at a bounded random sample of
+    targets, on the host cores; Mpoints/s = sampled targets / time."""
+    from oracle import direct
+    rng = np.random.default_rng(123)
+    t0 = time.perf_counter()
+    direct.direct("stokeslet", x, f, targets=rng.choice(len(x), 16, replace=False))
+    rate = 16 / max(time.perf_counter() - t0, 1e-6)
+    nt = int(max(16, min(len(x), rate * budget_s)))
+    idx = rng.choice(len(x), nt, replace=False)
+    t0 = time.perf_counter()
+    direct.direct("stokeslet", x, f, targets=idx)
+    dt = time.perf_counter() - t0
+    return {"value": nt / dt / 1e6, "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 direct sum over all {len(x)} sources at {nt} random targets "
+                      f"({dt:.1f} s), scaled to targets per second"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import workloads as W
+    x, f = W.stokeslet_uniform(N_POINTS, 1)
+    from oracle import direct
+    rng = np.random.default_rng(7)
+    t0 = time.perf_counter()
+    direct.direct("stokeslet", x, f, targets=rng.choice(N_POINTS, 8, replace=False))
+    rate = 8 / max(time.perf_counter() - t0, 1e-6)
+    per_step = int(max(8, min(N_POINTS, rate * 8.0)))  # about 8 s of CPU work per step
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = rng.choice(N_POINTS, per_step, replace=False)
+        t0 = time.perf_counter()
+        direct.direct("stokeslet", x, f, targets=idx)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    val = per_step / (ms * 1e-3) / 1e6
+    sample = (f"FP64 direct sum over all {N_POINTS} sources at {per_step} random targets per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpoints/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_POINTS, "reference": "CPU oracle (no reference code exists)"},
+        "cpu_baseline": {"value": val, "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    import paper_1607_04808_gb300 as se
+    import workloads as W
+    from paper_1607_04808_gb300 import _build
+
+    _build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    x64, f64 = W.stokeslet_uniform(N_POINTS, 1)
+    x32 = torch.tensor(x64, dtype=torch.float32, device=dev)
+    f32 = torch.tensor(f64, dtype=torch.float32, device=dev)
+    plan = se.Plan("stokeslet", N_POINTS, BOX, prec="fp32", tol=2e-6, max_fft=256)
+    prm = plan.params
+    plan.set_timing(True)
+    u = torch.empty_like(x32)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.eval(x32, f32, out=u)
+    plan.check()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    stage_acc = {}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            plan.eval(x32, f32, out=u)
+            evs[k][1].record(stream)
+            torch.cuda.synchronize()
+            for name, v in plan.stage_times().items():
+                stage_acc.setdefault(name, []).append(v)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    plan.check()
+    stages = {k: float(np.mean(v)) for k, v in stage_acc.items()}
+
+    # end to end through se_eval_host (pinned host buffers; copies inside the timed region)
+    xh = torch.tensor(x64, dtype=torch.float32).pin_memory()
+    fh = torch.tensor(f64, dtype=torch.float32).pin_memory()
+    uh = torch.empty((N_POINTS, 3), dtype=torch.float32).pin_memory()
+    plan.set_timing(False)
+    plan.eval_host(xh, fh, out=uh)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 10))):
+        t0 = time.perf_counter()
+        plan.eval_host(xh, fh, out=uh)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * float(np.mean(e2e_t))
+
+    # FP64 path on the same points
+    fp64 = None
+    if not args.no_fp64:
+        x64d = torch.tensor(x64, device=dev)
+        f64d = torch.tensor(f64, device=dev)
+        plan64 = se.Plan("stokeslet", N_POINTS, BOX, prec="fp64", tol=1e-10)
+        p64 = plan64.params
+        plan64.set_timing(True)
+        u64 = torch.empty_like(x64d)
+        plan64.eval(x64d, f64d, out=u64)
+        torch.cuda.synchronize()
+        t64 = []
+        st64 = {}
+        for _ in range(2):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan64.eval(x64d, f64d, out=u64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t64.append(a.elapsed_time(b))
+            for name, v in plan64.stage_times().items():
+                st64.setdefault(name, []).append(v)
+        plan64.check()
+        ms64 = float(np.mean(t64))
+        fp64 = {"value": N_POINTS / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
+                "tol": 1e-10, "params": {k: p64[k] for k in ("M", "P", "xi", "rc", "Mtilde")},
+                "stages_ms": {k: float(np.mean(v)) for k, v in st64.items()},
+                "fp32_speedup": ms64 / ms}
+        plan64.close()
+
+    if rank != 0:
+        return
+    value = world * N_POINTS / (ms * 1e-3) / 1e6
+    peaks = read_peaks()
+    clocks = clk.summary()
+    sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s FP32 (152 SMs x 128 lanes x FMA)
+    pairs = N_POINTS * (N_POINTS - 1) * pair_fraction_unit_cube(prm["rc"] / BOX[3])
+    real_ms = stages.get("real", float("nan"))
+    achieved = pairs * FLOP_PER_PAIR / (real_ms * 1e-3) / 1e12
+    hbm = (peaks or {}).get("hbm_gbs", 6800.0)
+    Mt, Mf = prm["Mtilde"], 2 * prm["Mtilde"]
+    nk = Mf * Mf * (Mf // 2 + 1)
+    stage_bytes = {
+        "spread": N_POINTS * 32 + 2 * 3 * Mt**3 * 4,
+        "scale": nk * 48 + (Mt + 1) ** 3 * 4,
+        "gather": 3 * Mt**3 * 4 + N_POINTS * (16 + 12 + 12),
+        "real": N_POINTS * (32 + 24),
+    }
+    stage_gbs = {k: stage_bytes[k] / (stages[k] * 1e-3) / 1e9 for k in stage_bytes if stages.get(k)}
+    cpu = None if args.no_cpu else cpu_baseline(x64, f64)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_POINTS, "tol": 2e-6, "max_fft": 256,
+                   "params": {k: prm[k] for k in ("M", "P", "xi", "rc", "Mtilde", "eta")},
+                   "l2": "512 MB buffer zeroed between timed steps, outside the per-step events",
+                   "parallelism": f"replicas x{world}", "wall_s_timed_region": t_wall},
+        "stages_ms": stages,
+        "stage_algorithmic_gbs": stage_gbs,
+        "roofline": {"bound": "alu", "kernel": "k_real (real-space pair sum)", "achieved": achieved,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                     "pairs_per_launch": pairs, "flop_per_pair": FLOP_PER_PAIR},
+        "hbm_peak_gbs": hbm,
+        "fp64": fp64,
+        "cpu_baseline": cpu,
+        "e2e": {"value": N_POINTS / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 2 * N_POINTS * 3 * 4, "d2h_bytes_per_step": N_POINTS * 3 * 4},
+        "gpu_launches": OUR_KERNELS_PER_EVAL * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, rank, world, dist)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+/*
+ * se.h -- C ABI of the GB300 free-space Spectral Ewald library (libse.so).
+ *
+ * Computes, for N points x_n in a cube and their sources,
+ *
+ *     u(x_m) = sum_{n != m} K(x_m - x_n) . f_n            (Section 1, eq. usumfree;
+ *                                                           Section 2, eq. usum)
+ *
+ * for the stokeslet  u_j = S_jl f_l,       S_jl = delta_jl/r + r_j r_l/r^3   (eq. def_stokeslet)
+ *     stresslet      u_j = T_jlm f_l q_m,  T_jlm = -6 r_j r_l r_m / r^5     (eq. def_stresslet)
+ *     rotlet         u_j = Omega_jl f_l,   Omega_jl = eps_jlm r_m / r^3      (eq. def_rotlet)
+ *
+ * with the free-space Ewald split of Section 3.2 (Hasimoto screening for S and
+ * T, Ewald screening for Omega): u = u^R + u^F + u^self (Section 8).  u^F uses
+ * the Spectral Ewald steps of Section 5.2 (spreading, zero-padded FFT, scaling
+ * by the precomputed truncated Green's function of Section 4.3, inverse FFT,
+ * quadrature) and u^R the screened real-space sum over |r| <= rc (Section 6).
+ * No 1/(8 pi mu) prefactor is applied.  The rotlet is the definition above;
+ * the operator form of eq. rotlet_op is twice as large.
+ *
+ * Conventions for every call below:
+ *  - Arrays are row-major, contiguous, in the plan's precision (float for
+ *    SE_FP32, double for SE_FP64): x, f, q, u, grad_* are N x 3.
+ *  - Device pointers are owned by the caller; the library never frees them.
+ *    Host pointers are accepted only where a name ends in _host.
+ *  - Points must lie in the half-open cube [x0, x0+L)^3 of the plan.
+ *  - Calls taking a stream are asynchronous on that stream (0 = legacy
+ *    default stream).  A plan is used by one stream at a time and is not
+ *    thread-safe.
+ *  - Every call returns an se_status_t.  Errors found on the device (a point
+ *    outside the box, coincident points) are recorded in the plan and
+ *    reported by se_plan_check, which synchronises the plan's last stream.
+ *  - se_last_error() returns a message for the last failing call on the
+ *    calling thread.
+ */
+#ifndef SE_H
+#define SE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { SE_STOKESLET = 0, SE_STRESSLET = 1, SE_ROTLET = 2 } se_kernel_t;
+typedef enum { SE_FP32 = 0, SE_FP64 = 1 } se_prec_t;
+
+typedef enum {
+    SE_OK = 0,
+    SE_ERR_INVALID_ARG = 1,   /* bad size, pointer, parameter or kernel/precision combination */
+    SE_ERR_OUT_OF_BOX = 2,    /* a point lies outside [x0, x0+L)^3 (results undefined)        */
+    SE_ERR_COINCIDENT = 3,    /* two distinct points coincide; the pair was skipped (warning)  */
+    SE_ERR_OOM = 4,           /* device or host allocation failed                             */
+    SE_ERR_CUDA = 5,          /* a CUDA runtime call failed                                   */
+    SE_ERR_CUFFT = 6,         /* a cuFFT call failed                                          */
+    SE_ERR_TIMEOUT = 7,       /* a bounded device wait ran out                                */
+    SE_ERR_NOT_SUPPORTED = 8  /* valid request this build does not implement                  */
+} se_status_t;
+
+typedef struct se_plan_s *se_plan_t;
+
+/* Method parameters (Section 8.2).  A zero/negative field is chosen by the
+ * library's parameter selection (Tables 2 and 3, Section 8.2); set fields are
+ * taken as given.  After se_plan_create, se_plan_get_params fills every field. */
+typedef struct {
+    double xi;          /* Ewald parameter xi                                          */
+    double rc;          /* real-space cutoff radius r_c                                */
+    int M;              /* grid points across the box side L (h = L/M)                 */
+    int P;              /* Gaussian support: P^3 grid points per source (Section 5.2)  */
+    int deltaL_policy;  /* 0: delta_L = d = hP;  1: eq. deltaL_cond (Section 5.3)      */
+    int max_fft;        /* upper bound on the FFT size 2*Mtilde per dimension (0: none) */
+    /* derived, filled by se_plan_get_params (ignored on input) */
+    int Mtilde;         /* extended grid points per dimension, M + delta_L/h           */
+    int Mg;             /* precompute grid size: smallest even > (1+sqrt 3) Mtilde      */
+    double eta;         /* Gaussian shape parameter eta = (xi d / m)^2, m = 0.976 sqrt(pi P) */
+    double h;           /* grid spacing L/M                                            */
+} se_params_t;
+
+/* Create a plan for N points in the cube box = {x0, y0, z0, L}.
+ *   kernel  SE_STOKESLET, SE_STRESSLET or SE_ROTLET
+ *   N       number of points (sources = targets), N >= 1
+ *   xi      Ewald parameter; <= 0 lets the library choose (overridden by params->xi > 0)
+ *   tol     target relative RMS error used when parameters are chosen (e.g. 2e-6)
+ *   prec    SE_FP32 or SE_FP64 arithmetic for spreading, FFTs, gather and real space;
+ *           the truncated Green's function is always precomputed in FP64
+ *   params  optional overrides (NULL: choose everything)
+ * Allocates all device workspaces, builds the cuFFT plans and runs the FP64
+ * precomputation of Section 4.3 on the current device (synchronously).
+ * The plan owns its memory until se_plan_destroy. */
+se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const double box[4], double tol,
+                           se_prec_t prec, const se_params_t *params, se_plan_t *plan_out);
+
+/* u = sum_{n != m} K(x_m - x_n) . f_n at every point (Section 8).
+ *   x  N x 3 device positions; f N x 3 device strengths (forces, dipoles or torques)
+ *   q  N x 3 device second source vector for the stresslet (u_j = T_jlm f_l q_m), else NULL
+ *   u  N x 3 device output (overwritten)
+ * Asynchronous on `stream`. */
+se_status_t se_eval(se_plan_t plan, const void *x, const void *f, const void *q, void *u, void *stream);
+
+/* Same as se_eval with HOST arrays: copies x, f (, q) to the device, evaluates,
+ * copies u back and synchronises `stream` before returning. */
+se_status_t se_eval_host(se_plan_t plan, const void *x_host, const void *f_host, const void *q_host,
+                         void *u_host, void *stream);
+
+/* Gradients of L = sum_m grad_u_m . u_m for the stokeslet and the rotlet:
+ *   grad_f_n = sum_m K(x_m - x_n)^T grad_u_m      (the transposed sum; equal to the
+ *              same kernel applied to grad_u, since both operators are symmetric)
+ *   grad_x_p = d L / d x_p                          (Gaussian-derivative quadrature on the
+ *              forward and adjoint grids plus the real-space kernel derivative)
+ * Either output may be NULL.  The forward grid is recomputed, not stored.
+ * Returns SE_ERR_NOT_SUPPORTED for the stresslet. */
+se_status_t se_eval_backward(se_plan_t plan, const void *x, const void *f, const void *q,
+                             const void *grad_u, void *grad_f, void *grad_x, void *stream);
+
+/* Parameter selection without a device (host only; the same rules as
+ * se_plan_create, Section 8.2 with Tables 2 and 3): fills M, P, xi and rc of
+ * *out from the overrides in *in (may be NULL), the box side L, N, tol and
+ * the precision.  Derived fields are not filled. */
+se_status_t se_choose_params(se_kernel_t kernel, se_prec_t prec, int64_t N, double L, double tol, double xi,
+                             const se_params_t *in, se_params_t *out);
+
+/* Fill *out with the plan's parameters (chosen or given, plus derived values). */
+se_status_t se_plan_get_params(se_plan_t plan, se_params_t *out);
+
+/* Synchronise the stream of the plan's last call and return (and clear) the
+ * device-side status: SE_OK, SE_ERR_OUT_OF_BOX or SE_ERR_COINCIDENT. */
+se_status_t se_plan_check(se_plan_t plan);
+
+/* Per-stage device times of the plan's last se_eval, in milliseconds, when
+ * stage timing was enabled with se_plan_set_timing(plan, 1).  Order:
+ * bin, spread, fft, scale, ifft, gather, real.  Returns the number written. */
+int se_plan_stage_times(se_plan_t plan, float *ms, int max_n);
+se_status_t se_plan_set_timing(se_plan_t plan, int on);
+
+/* Destroy the plan and free its device memory (synchronises the device). */
+se_status_t se_plan_destroy(se_plan_t plan);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *se_last_error(void);
+
+/* Library version string. */
+const char *se_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SE_H */

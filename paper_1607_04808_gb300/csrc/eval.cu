@@ -1,0 +1,175 @@
+// Evaluation: u = u^R + u^F + u^self (Section 8), and the gradients of
+// L = sum g . u for the backward pass.
+//   bin -> spread (step 1) -> R2C FFT (step 2) -> scale (step 3) -> C2R FFT
+//   (step 4) -> gather + self (step 5, eq. Slimit) -> real-space sum (Section 6)
+#include <string>
+
+#include "se_internal.cuh"
+
+using namespace se;
+
+namespace {
+
+template <typename T>
+cufftResult exec_fwd(cufftHandle h, void *in, void *out);
+template <>
+cufftResult exec_fwd<float>(cufftHandle h, void *in, void *out) {
+    return cufftExecR2C(h, (cufftReal *)in, (cufftComplex *)out);
+}
+template <>
+cufftResult exec_fwd<double>(cufftHandle h, void *in, void *out) {
+    return cufftExecD2Z(h, (cufftDoubleReal *)in, (cufftDoubleComplex *)out);
+}
+template <typename T>
+cufftResult exec_inv(cufftHandle h, void *in, void *out);
+template <>
+cufftResult exec_inv<float>(cufftHandle h, void *in, void *out) {
+    return cufftExecC2R(h, (cufftComplex *)in, (cufftReal *)out);
+}
+template <>
+cufftResult exec_inv<double>(cufftHandle h, void *in, void *out) {
+    return cufftExecZ2D(h, (cufftDoubleComplex *)in, (cufftDoubleReal *)out);
+}
+
+struct StageTimer {
+    se_plan_s *p;
+    cudaStream_t st;
+    int k = 0;
+    void mark() {
+        if (p->timing && k < 9) cudaEventRecord(p->ev[k++], st);
+    }
+    void finish() {
+        if (!p->timing) return;
+        cudaEventSynchronize(p->ev[k - 1]);
+        p->n_stage = k - 1;
+        for (int i = 0; i + 1 < k; i++) cudaEventElapsedTime(&p->stage_ms[i], p->ev[i], p->ev[i + 1]);
+    }
+};
+
+#define CK(expr)                                                                        \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess)                                                          \
+            return fail(SE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+#define CF(expr)                                                                              \
+    do {                                                                                      \
+        cufftResult _r = (expr);                                                              \
+        if (_r != CUFFT_SUCCESS)                                                              \
+            return fail(SE_ERR_CUFFT, std::string(#expr) + " failed, code " + std::to_string((int)_r)); \
+    } while (0)
+
+// Fourier grid w = IFFT(scale(FFT(spread(sources)))) from the tile-sorted sources
+// currently held in the plan (fs_t, qs_t).
+template <typename T>
+se_status_t fourier_grid(se_plan_s *p, cudaStream_t st, void *wout, int nc, StageTimer *tm) {
+    CK(launch_spread<T>(p, st, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->grid, nc));
+    if (tm) tm->mark();
+    cufftHandle fwd = (nc == p->nc) ? p->fwd : p->fwd3;
+    CF(cufftSetStream(fwd, st));
+    CF(exec_fwd<T>(fwd, p->grid, p->spec));
+    if (tm) tm->mark();
+    CK(launch_scale<T>(p, st, p->spec, 0));
+    if (tm) tm->mark();
+    CF(cufftSetStream(p->inv, st));
+    CF(exec_inv<T>(p->inv, p->spec, wout));
+    if (tm) tm->mark();
+    return SE_OK;
+}
+
+template <typename T>
+se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaStream_t st) {
+    p->last_stream = st;
+    StageTimer tm{p, st};
+    tm.mark();
+    CK(launch_bin<T>(p, x, f, q, st));
+    tm.mark();
+    se_status_t s = fourier_grid<T>(p, st, p->wgrid, p->nc, &tm);
+    if (s != SE_OK) return s;
+    CK(launch_gather<T>(p, st, p->wgrid, f, u));
+    tm.mark();
+    CK(launch_real<T>(p, st, u));
+    tm.mark();
+    tm.finish();
+    return SE_OK;
+}
+
+template <typename T>
+se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *gu, T *gf, T *gx, cudaStream_t st) {
+    p->last_stream = st;
+    const size_t Mf3 = (size_t)p->Mf * p->Mf * p->Mf;
+    if (!p->wgrid2) {
+        cudaError_t e = cudaMalloc(&p->wgrid2, 3 * Mf3 * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SE_ERR_OOM, "backward: adjoint grid allocation failed");
+        }
+    }
+    // adjoint grid w' = A^T spread(g); the stokeslet and rotlet multipliers are
+    // their own transposes (A_jl(-k) = A_lj(k))
+    CK(launch_bin<T>(p, x, gu, nullptr, st));
+    se_status_t s = fourier_grid<T>(p, st, p->wgrid2, 3, nullptr);
+    if (s != SE_OK) return s;
+    if (gf) {
+        // transposed operator applied to g: same kernel (S and Omega are symmetric operators)
+        CK(launch_gather<T>(p, st, p->wgrid2, gu, gf));
+        CK(launch_real<T>(p, st, gf));
+    }
+    if (gx) {
+        CK(launch_bin<T>(p, x, f, nullptr, st));
+        s = fourier_grid<T>(p, st, p->wgrid, 3, nullptr);
+        if (s != SE_OK) return s;
+        CK(launch_gather_grad<T>(p, st, p->wgrid, p->wgrid2, f, gu, gx));
+        CK(launch_real_grad<T>(p, st, gu, gx));
+    }
+    return SE_OK;
+}
+
+}  // namespace
+
+extern "C" se_status_t se_eval(se_plan_t p, const void *x, const void *f, const void *q, void *u, void *stream) {
+    if (!p || !x || !f || !u) return fail(SE_ERR_INVALID_ARG, "se_eval: NULL pointer");
+    if (p->kernel == SE_STRESSLET && !q) return fail(SE_ERR_INVALID_ARG, "se_eval: the stresslet needs q");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prec == SE_FP32)
+        return eval_t<float>(p, (const float *)x, (const float *)f, (const float *)q, (float *)u, st);
+    return eval_t<double>(p, (const double *)x, (const double *)f, (const double *)q, (double *)u, st);
+}
+
+extern "C" se_status_t se_eval_host(se_plan_t p, const void *x, const void *f, const void *q, void *u,
+                                    void *stream) {
+    if (!p || !x || !f || !u) return fail(SE_ERR_INVALID_ARG, "se_eval_host: NULL pointer");
+    if (p->kernel == SE_STRESSLET && !q) return fail(SE_ERR_INVALID_ARG, "se_eval_host: the stresslet needs q");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = (size_t)p->N * 3 * (p->prec == SE_FP32 ? 4 : 8);
+    if (!p->dx) {
+        if (cudaMalloc(&p->dx, bytes) || cudaMalloc(&p->df, bytes) || cudaMalloc(&p->du, bytes) ||
+            (p->kernel == SE_STRESSLET && cudaMalloc(&p->dq, bytes))) {
+            cudaGetLastError();
+            return fail(SE_ERR_OOM, "se_eval_host: staging allocation failed");
+        }
+    }
+    CK(cudaMemcpyAsync(p->dx, x, bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(p->df, f, bytes, cudaMemcpyHostToDevice, st));
+    if (q) CK(cudaMemcpyAsync(p->dq, q, bytes, cudaMemcpyHostToDevice, st));
+    se_status_t s = se_eval(p, p->dx, p->df, q ? p->dq : nullptr, p->du, stream);
+    if (s != SE_OK) return s;
+    CK(cudaMemcpyAsync(u, p->du, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SE_OK;
+}
+
+extern "C" se_status_t se_eval_backward(se_plan_t p, const void *x, const void *f, const void *q, const void *grad_u,
+                                        void *grad_f, void *grad_x, void *stream) {
+    (void)q;
+    if (!p || !x || !f || !grad_u) return fail(SE_ERR_INVALID_ARG, "se_eval_backward: NULL pointer");
+    if (p->kernel == SE_STRESSLET)
+        return fail(SE_ERR_NOT_SUPPORTED, "se_eval_backward: the stresslet gradient is not implemented");
+    if (!grad_f && !grad_x) return SE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prec == SE_FP32)
+        return backward_t<float>(p, (const float *)x, (const float *)f, (const float *)grad_u, (float *)grad_f,
+                                 (float *)grad_x, st);
+    return backward_t<double>(p, (const double *)x, (const double *)f, (const double *)grad_u, (double *)grad_f,
+                              (double *)grad_x, st);
+}

@@ -1,0 +1,366 @@
+// Plan creation: parameter selection (Section 8.2 with the truncation-error
+// estimates of Tables 2 and 3), grid sizing (Sections 4.2, 5.2, 5.3, 9),
+// workspace allocation, cuFFT plans and the FP64 precomputation (Section 4.3).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "se_internal.cuh"
+
+namespace se {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+se_status_t fail(se_status_t st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+// ---------------------------------------------------------------- parameter selection
+namespace {
+
+// Fourier truncation error, Table 2 (absolute RMS), Q = sum |f|^2.
+double est_fourier(int kernel, double Q, double xi, double L, int M, int P) {
+    double kinf = M_PI * M / L;
+    double Lt = L * (M + P) / (double)M;  // Ltilde with delta_L = d
+    double R = sqrt(3.0) * Lt;
+    double ex = exp(-kinf * kinf / (4.0 * xi * xi));
+    if (kernel == SE_STOKESLET) return sqrt(Q) * R * kinf * kinf * kinf / (xi * xi * M_PI * L) * ex;
+    if (kernel == SE_STRESSLET)
+        return sqrt(7.0 * Q / 6.0) * R * kinf * kinf * kinf * kinf / (xi * xi * M_PI * L) * ex;
+    return sqrt(8.0 * xi * xi * Q / (3.0 * M_PI * L * L * L * kinf)) * ex;
+}
+
+// Real-space truncation error, Table 3 (absolute RMS).
+double est_real(int kernel, double Q, double xi, double L, double rc) {
+    double ex = exp(-xi * xi * rc * rc);
+    double L3 = L * L * L;
+    if (kernel == SE_STOKESLET) return sqrt(4.0 * Q * rc / L3) * ex;
+    if (kernel == SE_STRESSLET) return sqrt(112.0 * Q * xi * xi * xi * xi * rc * rc * rc / (9.0 * L3)) * ex;
+    return sqrt(8.0 * Q / (3.0 * L3 * rc)) * ex;
+}
+
+// Smallest M meeting the Fourier budget (the estimate decreases with M).
+int min_M(int kernel, double Q, double xi, double L, int P, double budget) {
+    for (int M = 2; M < 4096; M++)
+        if (est_fourier(kernel, Q, xi, L, M, P) <= budget) return M;
+    return 4096;
+}
+
+double min_rc(int kernel, double Q, double xi, double L, double budget) {
+    double lo = 1e-6 * L, hi = 2.0 * L;
+    if (est_real(kernel, Q, xi, L, hi) > budget) return hi;
+    for (int it = 0; it < 100; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (est_real(kernel, Q, xi, L, mid) <= budget) hi = mid; else lo = mid;
+    }
+    return hi;
+}
+
+}  // namespace
+
+// Parameter selection.  Relative tolerances are turned into absolute RMS
+// budgets with the RMS of u for uniformly distributed points and unit-variance
+// sources, |u|_rms^2 ~ 6 <1/r^2> N ~ 33.6 N / L^2 (stokeslet; the same scale is
+// used, conservatively, for the stresslet and rotlet whose RMS is larger).  P is
+// the smallest even support whose approximation error 10^{-(P+1)/2} stays below
+// tol/3 (Section 8.2: P = 16 ~ 8 digits, 24 ~ 12 digits).  With a bound on the
+// FFT size, xi is the largest value whose Fourier estimate at the largest
+// admissible M meets the budget; otherwise xi minimises a work model.
+se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
+                          double xi_arg, se_params_t *out) {
+    se_params_t p;
+    memset(&p, 0, sizeof(p));
+    if (in) p = *in;
+    if (tol <= 0) tol = (prec == SE_FP32) ? 2e-6 : 1e-10;
+    double Q = 3.0 * (double)N;
+    double deg = (kernel == SE_STOKESLET) ? 1.0 : 2.0;
+    double uabs = sqrt(33.6 * (double)N) / pow(L, deg);
+    double budget = tol * uabs / sqrt(3.0);
+    if (p.P <= 0) {
+        int P = 4;
+        while (P < 32 && pow(10.0, -0.5 * P - 0.5) > tol / 3.0) P += 2;
+        p.P = P;
+    }
+    double xi = (p.xi > 0) ? p.xi : xi_arg;
+    if (!(xi > 0)) {
+        if (p.max_fft > 0 && p.M <= 0) {
+            int Mmax = p.max_fft / 2 - p.P;
+            if (Mmax < 2) return fail(SE_ERR_INVALID_ARG, "max_fft too small for the support P");
+            double lo = 0.1 / L, hi = 10.0 * Mmax / L;
+            for (int it = 0; it < 100; it++) {
+                double mid = 0.5 * (lo + hi);
+                if (est_fourier(kernel, Q, mid, L, Mmax, p.P) <= budget) lo = mid; else hi = mid;
+            }
+            xi = lo;
+        } else if (p.M > 0) {
+            double lo = 0.1 / L, hi = 10.0 * p.M / L;
+            for (int it = 0; it < 100; it++) {
+                double mid = 0.5 * (lo + hi);
+                if (est_fourier(kernel, Q, mid, L, p.M, p.P) <= budget) lo = mid; else hi = mid;
+            }
+            xi = lo;
+        } else {
+            // work model (relative units per GB300 stage): real-space pairs,
+            // spreading+gather grid updates, FFT points * log
+            double best = 1e300, bxi = 1.0 / L;
+            double cpair = (prec == SE_FP32) ? 1.0 : 1.0, cgrid = 0.12, cfft = 0.6;
+            for (double x = 0.5 / L; x < 4000.0 / L; x *= 1.03) {
+                int M = min_M(kernel, Q, x, L, p.P, budget);
+                double rc = min_rc(kernel, Q, x, L, budget);
+                if (rc > L) continue;
+                double Mf = 2.0 * (M + p.P);
+                double pairs = (double)N * (double)N * 4.18879 * rc * rc * rc / (L * L * L);
+                double cost = cpair * pairs + cgrid * (double)N * p.P * p.P * p.P * 2.0 +
+                              cfft * Mf * Mf * Mf * log2(Mf) * 6.0;
+                if (cost < best) { best = cost; bxi = x; }
+            }
+            xi = bxi;
+        }
+    }
+    p.xi = xi;
+    if (p.M <= 0) p.M = min_M(kernel, Q, xi, L, p.P, budget);
+    if (p.max_fft > 0 && 2 * (p.M + p.P) > p.max_fft) p.M = p.max_fft / 2 - p.P;
+    if (p.rc <= 0) p.rc = min_rc(kernel, Q, xi, L, budget);
+    *out = p;
+    return SE_OK;
+}
+
+}  // namespace se
+
+using namespace se;
+
+static void free_plan(se_plan_s *p) {
+    if (!p) return;
+    if (p->have_fwd) cufftDestroy(p->fwd);
+    if (p->have_inv) cufftDestroy(p->inv);
+    if (p->have_fwd3) cufftDestroy(p->fwd3);
+    void *ptrs[] = {p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
+                    p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
+                    p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
+                    p->b.key_r, p->b.status, p->dx, p->df, p->dq, p->du};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (int i = 0; i < 9; i++)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    delete p;
+}
+
+template <typename P_>
+static cudaError_t dmalloc(P_ **ptr, size_t bytes) {
+    return cudaMalloc((void **)ptr, bytes ? bytes : 16);
+}
+
+extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const double box[4], double tol,
+                                      se_prec_t prec, const se_params_t *params, se_plan_t *plan_out) {
+    if (!plan_out) return fail(SE_ERR_INVALID_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    if (kernel < SE_STOKESLET || kernel > SE_ROTLET) return fail(SE_ERR_INVALID_ARG, "unknown kernel");
+    if (prec != SE_FP32 && prec != SE_FP64) return fail(SE_ERR_INVALID_ARG, "unknown precision");
+    if (N < 1 || N > (int64_t)INT32_MAX / 4) return fail(SE_ERR_INVALID_ARG, "N out of range");
+    if (!box || !(box[3] > 0)) return fail(SE_ERR_INVALID_ARG, "box side L must be positive");
+    se_params_t pr;
+    se_status_t s = choose_params(kernel, prec, N, box[3], tol, params, xi, &pr);
+    if (s != SE_OK) return s;
+    if (pr.P < 1 || pr.P > 32) return fail(SE_ERR_INVALID_ARG, "P must be in [1, 32]");
+    if (pr.M < 1 || !(pr.xi > 0) || !(pr.rc > 0)) return fail(SE_ERR_INVALID_ARG, "invalid M, xi or rc");
+
+    se_plan_s *p = new se_plan_s();
+    p->kernel = kernel;
+    p->prec = prec;
+    p->N = N;
+    for (int d = 0; d < 3; d++) p->x0[d] = box[d];
+    p->L = box[3];
+    p->xi = pr.xi;
+    p->rc = pr.rc;
+    p->M = pr.M;
+    p->P = pr.P;
+    p->deltaL_policy = pr.deltaL_policy;
+    p->max_fft = pr.max_fft;
+    // Sections 5.2-5.3: h = L/M, d = hP, m = C sqrt(pi P), eta = (xi d / m)^2
+    p->h = p->L / p->M;
+    double d = p->h * p->P;
+    p->m = 0.976 * sqrt(M_PI * p->P);
+    p->eta = (p->xi * d / p->m) * (p->xi * d / p->m);
+    double need = d;
+    if (p->deltaL_policy == 1 && p->eta < 1.0)
+        need = std::max(d, sqrt(2.0 * (1.0 - p->eta) * p->m * p->m / (p->xi * p->xi)));
+    p->n_ext = (int)ceil(need / p->h - 1e-9);
+    p->deltaL = p->n_ext * p->h;
+    p->Mt = p->M + p->n_ext;
+    p->Mf = 2 * p->Mt;
+    p->R = sqrt(3.0) * p->Mt * p->h;
+    p->Mg = 2 * (int)floor((1.0 + sqrt(3.0)) * p->Mt / 2.0) + 2;
+    p->nc = (kernel == SE_STRESSLET) ? 6 : 3;
+    if (p->max_fft > 0 && p->Mf > p->max_fft) {
+        free_plan(p);
+        return fail(SE_ERR_INVALID_ARG, "FFT size 2*Mtilde exceeds max_fft");
+    }
+    // geometry
+    Geom &g = p->geom;
+    for (int dd = 0; dd < 3; dd++) g.x0[dd] = p->x0[dd];
+    g.L = p->L;
+    g.h = p->h;
+    g.inv_h = 1.0 / p->h;
+    g.half_ext = 0.5 * p->n_ext;
+    g.P = p->P;
+    g.Mt = p->Mt;
+    g.Mf = p->Mf;
+    g.a = 2.0 * p->xi * p->xi / p->eta;
+    g.xi = p->xi;
+    g.rc = p->rc;
+    size_t esz = (prec == SE_FP32) ? 4 : 8;
+    // spreading tiles: the largest edge whose padded tile (all components) fits
+    // in 110 KB of shared memory; otherwise the atomic spreading path is used and
+    // tiles of 8 only order the points
+    int T = 0;
+    for (int cand : {8, 6, 4, 2}) {
+        size_t PT = cand + p->P - 1;
+        if ((size_t)p->nc * PT * PT * PT * esz <= 110 * 1024) { T = cand; break; }
+    }
+    p->tiled = (T > 0);
+    g.T = (T > 0) ? T : 8;
+    g.ntd = (p->Mt - p->P + 1 + g.T - 1) / g.T;
+    p->ntiles = g.ntd * g.ntd * g.ntd;
+    // real-space cells of width >= rc/2 (at most 160 per dimension)
+    int ncd = (int)floor(2.0 * p->L / p->rc);
+    ncd = std::max(1, std::min(ncd, 160));
+    g.ncd = ncd;
+    g.cw = p->L / ncd;
+    g.inv_cw = ncd / p->L;
+    p->ncells = ncd * ncd * ncd;
+
+    // allocations
+    cudaError_t e = cudaSuccess;
+    const size_t Nn = (size_t)N;
+    const size_t Mf3 = (size_t)p->Mf * p->Mf * p->Mf;
+    const size_t nk = (size_t)p->Mf * p->Mf * (p->Mf / 2 + 1);
+    const size_t O3 = (size_t)(p->Mt + 1) * (p->Mt + 1) * (p->Mt + 1);
+    const size_t v4 = 4 * esz;
+    int tile_keys = p->ntiles;
+    do {
+        if ((e = dmalloc(&p->ghat64, O3 * sizeof(double)))) break;
+        if (prec == SE_FP32 && (e = dmalloc(&p->ghat, O3 * sizeof(float)))) break;
+        if ((e = dmalloc(&p->grid, (size_t)p->nc * Mf3 * esz))) break;
+        if ((e = dmalloc(&p->spec, (size_t)p->nc * nk * 2 * esz))) break;
+        if ((e = dmalloc(&p->wgrid, 3 * Mf3 * esz))) break;
+        if ((e = dmalloc(&p->b.xs_t, Nn * v4))) break;
+        if ((e = dmalloc(&p->b.fs_t, Nn * v4))) break;
+        if ((e = dmalloc(&p->b.qs_t, (kernel == SE_STRESSLET ? Nn : 1) * v4))) break;
+        if ((e = dmalloc(&p->b.perm_t, Nn * 4))) break;
+        if ((e = dmalloc(&p->b.slot_t, Nn * 4))) break;
+        if ((e = dmalloc(&p->b.key_t, Nn * 4))) break;
+        if ((e = dmalloc(&p->b.cnt_t, (tile_keys + 1) * 4))) break;
+        if ((e = dmalloc(&p->b.xs_r, Nn * v4))) break;
+        if ((e = dmalloc(&p->b.fs_r, Nn * v4))) break;
+        if ((e = dmalloc(&p->b.qs_r, (kernel == SE_STRESSLET ? Nn : 1) * v4))) break;
+        if ((e = dmalloc(&p->b.perm_r, Nn * 4))) break;
+        if ((e = dmalloc(&p->b.slot_r, Nn * 4))) break;
+        if ((e = dmalloc(&p->b.key_r, Nn * 4))) break;
+        if ((e = dmalloc(&p->b.cnt_r, ((size_t)p->ncells + 1) * 4))) break;
+        if ((e = dmalloc(&p->b.status, 16))) break;
+        if ((e = cudaMemset(p->grid, 0, (size_t)p->nc * Mf3 * esz))) break;
+        if ((e = cudaMemset(p->b.status, 0, 16))) break;
+    } while (0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return fail(e == cudaErrorMemoryAllocation ? SE_ERR_OOM : SE_ERR_CUDA,
+                    std::string("plan allocation: ") + cudaGetErrorString(e));
+    }
+    // cuFFT plans: forward R2C batched over nc components, inverse C2R over 3
+    {
+        int n[3] = {p->Mf, p->Mf, p->Mf};
+        cufftType tf = (prec == SE_FP32) ? CUFFT_R2C : CUFFT_D2Z;
+        cufftType ti = (prec == SE_FP32) ? CUFFT_C2R : CUFFT_Z2D;
+        int idist = (int)Mf3, odist = (int)nk;
+        if (cufftPlanMany(&p->fwd, 3, n, nullptr, 1, idist, nullptr, 1, odist, tf, p->nc) != CUFFT_SUCCESS) {
+            free_plan(p);
+            return fail(SE_ERR_CUFFT, "cufftPlanMany (forward) failed");
+        }
+        p->have_fwd = true;
+        if (cufftPlanMany(&p->inv, 3, n, nullptr, 1, odist, nullptr, 1, idist, ti, 3) != CUFFT_SUCCESS) {
+            free_plan(p);
+            return fail(SE_ERR_CUFFT, "cufftPlanMany (inverse) failed");
+        }
+        p->have_inv = true;
+        if (p->nc != 3) {
+            if (cufftPlanMany(&p->fwd3, 3, n, nullptr, 1, idist, nullptr, 1, odist, tf, 3) != CUFFT_SUCCESS) {
+                free_plan(p);
+                return fail(SE_ERR_CUFFT, "cufftPlanMany (forward, 3) failed");
+            }
+            p->have_fwd3 = true;
+        }
+    }
+    for (int i = 0; i < 9; i++) cudaEventCreate(&p->ev[i]);
+    s = precompute(p);
+    if (s != SE_OK) {
+        free_plan(p);
+        return s;
+    }
+    *plan_out = p;
+    return SE_OK;
+}
+
+extern "C" se_status_t se_choose_params(se_kernel_t kernel, se_prec_t prec, int64_t N, double L, double tol,
+                                        double xi, const se_params_t *in, se_params_t *out) {
+    if (!out) return fail(SE_ERR_INVALID_ARG, "out is NULL");
+    if (kernel < SE_STOKESLET || kernel > SE_ROTLET) return fail(SE_ERR_INVALID_ARG, "unknown kernel");
+    if (N < 1 || !(L > 0)) return fail(SE_ERR_INVALID_ARG, "N and L must be positive");
+    return choose_params(kernel, prec, N, L, tol, in, xi, out);
+}
+
+extern "C" se_status_t se_plan_destroy(se_plan_t plan) {
+    if (!plan) return SE_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return SE_OK;
+}
+
+extern "C" se_status_t se_plan_get_params(se_plan_t p, se_params_t *out) {
+    if (!p || !out) return fail(SE_ERR_INVALID_ARG, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->xi = p->xi;
+    out->rc = p->rc;
+    out->M = p->M;
+    out->P = p->P;
+    out->deltaL_policy = p->deltaL_policy;
+    out->max_fft = p->max_fft;
+    out->Mtilde = p->Mt;
+    out->Mg = p->Mg;
+    out->eta = p->eta;
+    out->h = p->h;
+    return SE_OK;
+}
+
+extern "C" se_status_t se_plan_check(se_plan_t p) {
+    if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
+    cudaError_t e = p->last_stream ? cudaStreamSynchronize(p->last_stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(SE_ERR_CUDA, std::string("se_plan_check: ") + cudaGetErrorString(e));
+    int flags = 0;
+    if ((e = cudaMemcpy(&flags, p->b.status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(SE_ERR_CUDA, std::string("se_plan_check: ") + cudaGetErrorString(e));
+    cudaMemset(p->b.status, 0, sizeof(int));
+    if (flags & FLAG_OOB) return fail(SE_ERR_OUT_OF_BOX, "a point lies outside the plan's box");
+    if (flags & FLAG_COINCIDENT) return fail(SE_ERR_COINCIDENT, "coincident points were skipped");
+    return SE_OK;
+}
+
+extern "C" se_status_t se_plan_set_timing(se_plan_t p, int on) {
+    if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
+    p->timing = on != 0;
+    return SE_OK;
+}
+
+extern "C" int se_plan_stage_times(se_plan_t p, float *ms, int max_n) {
+    if (!p || !ms) return 0;
+    int n = std::min(max_n, p->n_stage);
+    for (int i = 0; i < n; i++) ms[i] = p->stage_ms[i];
+    return n;
+}
+
+extern "C" const char *se_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *se_version(void) { return "se-gb300 0.1 (sm_103a)"; }

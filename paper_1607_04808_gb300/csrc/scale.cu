@@ -1,0 +1,140 @@
+// Step 3 of Section 5.2 (scaling, eq. gridfcnsc): in Fourier space
+//   w^_j(k) = e^{-(1-eta) k^2 / 4 xi^2} A_j..(k) g^_..(k)
+// with the multipliers of eqs. AS, AT, AR where the truncated harmonic /
+// biharmonic transform is replaced by the precomputed mollified kernel G~^(k)
+// (Section 4.3, stored as the (Mt+1)^3 octant of a real, even array).
+//   stokeslet  A_jl  = -(k^2 d_jl - k_j k_l)(1 + k^2/4xi^2) G~^
+//   stresslet  A_jlm = -i[(k_m d_jl + k_j d_lm + k_l d_mj) k^2 - 2 k_j k_l k_m](1 + k^2/4xi^2) G~^
+//   rotlet     A_jl  = -i eps_jlm k_m G~^
+// The odd symbols are the transform of the kernel under f^(k) = int f e^{-ik.x}
+// (d/dx_m -> +i k_m), and the rotlet is the definition eps_jlm r_m / r^3.
+// The constant `norm` folds in the inverse-FFT normalisation 1/Mf^3, the
+// quadrature weight h^3 (Section 5.2 step 5) and the two Gaussian prefactors
+// (2 xi^2/(pi eta))^{3/2} of eqs. Hx and u_integr.
+// Memory-bound: reads nc complex values and writes 3 per k-point, in place.
+#include "se_internal.cuh"
+
+namespace se {
+
+namespace {
+
+struct ScaleConst {
+    double dk;       // 2 pi / (Mf h)
+    double inv4xi2;  // 1 / (4 xi^2)
+    double ecoef;    // -(1 - eta) / (4 xi^2)
+    double norm;     // h^3 / Mf^3 * pre^2
+    int Mt, Mf, nxh; // nxh = Mf/2 + 1
+};
+
+__device__ __forceinline__ float sexp(float v) { return expf(v); }
+__device__ __forceinline__ double sexp(double v) { return exp(v); }
+
+template <typename T, int KERNEL>
+__global__ void k_scale(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__restrict__ spec) {
+    using C = cplx<T>;
+    const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nk) return;
+    int kx = idx % sc.nxh;
+    int ky = (idx / sc.nxh) % sc.Mf;
+    int kz = idx / ((size_t)sc.nxh * sc.Mf);
+    int bx = (kx == sc.Mt) ? -sc.Mt : kx;
+    int by = (ky < sc.Mt) ? ky : ky - sc.Mf;
+    int bz = (kz < sc.Mt) ? kz : kz - sc.Mf;
+    int ax = abs(bx), ay = abs(by), az = abs(bz);
+    const int O = sc.Mt + 1;
+    T G = ghat[((size_t)az * O + ay) * O + ax];
+    T k1 = (T)sc.dk;
+    T kv[3] = {k1 * bx, k1 * by, k1 * bz};
+    T k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+    T F = (T)sc.norm * G * sexp((T)sc.ecoef * k2);
+    if (KERNEL != SE_ROTLET) F *= (T(1) + k2 * (T)sc.inv4xi2);
+    C *w0 = spec + idx;
+    if (KERNEL == SE_STOKESLET) {
+        C g[3];
+        for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
+        C kg;
+        kg.x = kv[0] * g[0].x + kv[1] * g[1].x + kv[2] * g[2].x;
+        kg.y = kv[0] * g[0].y + kv[1] * g[1].y + kv[2] * g[2].y;
+        for (int j = 0; j < 3; j++) {
+            C o;
+            o.x = -F * (k2 * g[j].x - kv[j] * kg.x);
+            o.y = -F * (k2 * g[j].y - kv[j] * kg.y);
+            w0[j * nk] = o;
+        }
+    } else if (KERNEL == SE_ROTLET) {
+        C g[3];
+        for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
+        // (g x k)_j = eps_jlm g_l k_m ; multiply by -i F: (a + ib)(-i) = b - ia
+        C cr[3];
+        cr[0].x = g[1].x * kv[2] - g[2].x * kv[1];
+        cr[0].y = g[1].y * kv[2] - g[2].y * kv[1];
+        cr[1].x = g[2].x * kv[0] - g[0].x * kv[2];
+        cr[1].y = g[2].y * kv[0] - g[0].y * kv[2];
+        cr[2].x = g[0].x * kv[1] - g[1].x * kv[0];
+        cr[2].y = g[0].y * kv[1] - g[1].y * kv[0];
+        for (int j = 0; j < 3; j++) {
+            C o;
+            o.x = F * cr[j].y;
+            o.y = -F * cr[j].x;
+            w0[j * nk] = o;
+        }
+    } else {
+        // symmetric source s: xx, yy, zz, xy, xz, yz
+        C s[6];
+        for (int c = 0; c < 6; c++) s[c] = w0[c * nk];
+        C sk[3], tr, ksk;
+        sk[0].x = s[0].x * kv[0] + s[3].x * kv[1] + s[4].x * kv[2];
+        sk[0].y = s[0].y * kv[0] + s[3].y * kv[1] + s[4].y * kv[2];
+        sk[1].x = s[3].x * kv[0] + s[1].x * kv[1] + s[5].x * kv[2];
+        sk[1].y = s[3].y * kv[0] + s[1].y * kv[1] + s[5].y * kv[2];
+        sk[2].x = s[4].x * kv[0] + s[5].x * kv[1] + s[2].x * kv[2];
+        sk[2].y = s[4].y * kv[0] + s[5].y * kv[1] + s[2].y * kv[2];
+        tr.x = s[0].x + s[1].x + s[2].x;
+        tr.y = s[0].y + s[1].y + s[2].y;
+        ksk.x = kv[0] * sk[0].x + kv[1] * sk[1].x + kv[2] * sk[2].x;
+        ksk.y = kv[0] * sk[0].y + kv[1] * sk[1].y + kv[2] * sk[2].y;
+        for (int j = 0; j < 3; j++) {
+            // b = k^2 (2 (s k)_j + k_j tr s) - 2 k_j (k.s.k); out = -i F b
+            T bx_ = k2 * (T(2) * sk[j].x + kv[j] * tr.x) - T(2) * kv[j] * ksk.x;
+            T by_ = k2 * (T(2) * sk[j].y + kv[j] * tr.y) - T(2) * kv[j] * ksk.y;
+            C o;
+            o.x = F * by_;
+            o.y = -F * bx_;
+            w0[j * nk] = o;
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpose) {
+    (void)transpose;  // the stokeslet and rotlet multipliers equal their transposes
+    ScaleConst sc;
+    sc.Mt = p->Mt;
+    sc.Mf = p->Mf;
+    sc.nxh = p->Mf / 2 + 1;
+    sc.dk = 2.0 * M_PI / (p->Mf * p->h);
+    sc.inv4xi2 = 1.0 / (4.0 * p->xi * p->xi);
+    sc.ecoef = -(1.0 - p->eta) / (4.0 * p->xi * p->xi);
+    double pre = pow(2.0 * p->xi * p->xi / (M_PI * p->eta), 1.5);
+    sc.norm = p->h * p->h * p->h / ((double)p->Mf * p->Mf * p->Mf) * pre * pre;
+    size_t nk = (size_t)p->Mf * p->Mf * sc.nxh;
+    int bs = 256;
+    unsigned gs = (unsigned)((nk + bs - 1) / bs);
+    const T *gh = (const T *)p->ghat;
+    cplx<T> *sp = (cplx<T> *)spec;
+    if (p->kernel == SE_STOKESLET)
+        k_scale<T, SE_STOKESLET><<<gs, bs, 0, st>>>(sc, gh, sp);
+    else if (p->kernel == SE_STRESSLET)
+        k_scale<T, SE_STRESSLET><<<gs, bs, 0, st>>>(sc, gh, sp);
+    else
+        k_scale<T, SE_ROTLET><<<gs, bs, 0, st>>>(sc, gh, sp);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_scale<float>(se_plan_s *, cudaStream_t, void *, int);
+template cudaError_t launch_scale<double>(se_plan_s *, cudaStream_t, void *, int);
+
+}  // namespace se

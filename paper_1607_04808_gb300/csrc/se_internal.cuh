@@ -1,0 +1,172 @@
+// Internal declarations of the GB300 free-space Spectral Ewald library.
+// Plan layout, precision traits and the launchers of each stage.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/se.h"
+
+namespace se {
+
+// ---------------------------------------------------------------- status
+enum : int { FLAG_OOB = 1, FLAG_COINCIDENT = 2 };
+
+void set_error(const std::string &msg);
+se_status_t fail(se_status_t st, const std::string &msg);
+
+#define SE_CUDA_TRY(expr)                                                                  \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess)                                                             \
+            return ::se::fail(SE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+#define SE_CUFFT_TRY(expr)                                                               \
+    do {                                                                                 \
+        cufftResult _r = (expr);                                                         \
+        if (_r != CUFFT_SUCCESS)                                                         \
+            return ::se::fail(SE_ERR_CUFFT, std::string(#expr) + " failed, code " +      \
+                                                std::to_string((int)_r));               \
+    } while (0)
+
+// ---------------------------------------------------------------- precision traits
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4_32a; };
+template <typename T> using vec4 = typename V4<T>::type;
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename T> using cplx = typename Cplx<T>::type;
+
+// ---------------------------------------------------------------- geometry shared by kernels
+// Everything a kernel needs to place a point on the grids and in the cells.
+struct Geom {
+    double x0[3];      // box corner
+    double L;          // box side
+    double h, inv_h;   // grid spacing and its inverse
+    double half_ext;   // n_ext / 2 (grid units): t = (x - x0)/h + n_ext/2 is (x - y0)/h
+    int P;             // Gaussian support (grid points per dimension)
+    int Mt;            // extended grid points per dimension
+    int Mf;            // FFT size per dimension (2 Mt)
+    int T;             // spreading tile edge (window starts per tile per dimension)
+    int ntd;           // tiles per dimension
+    double a;          // Gaussian exponent 2 xi^2 / eta (per unit length^2)
+    // real-space cells
+    int ncd;           // cells per dimension
+    double cw, inv_cw; // cell width and inverse
+    double rc;         // cutoff
+    double xi;
+};
+
+// Coordinate relative to the box corner, clamped into [0, L) for points outside
+// the box (they are flagged by the binning kernel; clamping keeps every kernel's
+// indexing in bounds and consistent with the binning).
+__host__ __device__ inline double clamp_rel(double rel, double L) {
+    if (!(rel >= 0.0 && rel < L)) rel = (rel >= L) ? L * (1.0 - 1e-12) : 0.0;
+    return rel;
+}
+
+// Window start of a point in one dimension (Section 5.2 with the P^3 block):
+//   P even: floor(t) - P/2 + 1, P odd: floor(t + 1/2) - (P-1)/2, t = (x - y0)/h,
+// computed in FP64 so that both precisions place a point identically.
+__host__ __device__ inline int window_start(double rel, const Geom &g, double &t) {
+    t = rel * g.inv_h + g.half_ext;
+    int i0;
+    if ((g.P & 1) == 0)
+        i0 = (int)floor(t) - g.P / 2 + 1;
+    else
+        i0 = (int)floor(t + 0.5) - (g.P - 1) / 2;
+    return i0;
+}
+
+// ---------------------------------------------------------------- the plan
+struct Buffers {
+    // points sorted by spreading tile
+    void *xs_t = nullptr;   // N vec4<T>: x, y, z, (unused)
+    void *fs_t = nullptr;   // N vec4<T>: f
+    void *qs_t = nullptr;   // N vec4<T>: q (stresslet)
+    int *perm_t = nullptr;  // sorted -> original
+    int *cnt_t = nullptr;   // ntiles (+1) histogram, then exclusive scan (starts)
+    int *slot_t = nullptr;  // N rank within tile
+    int *key_t = nullptr;   // N tile id
+    // points sorted by real-space cell
+    void *xs_r = nullptr;
+    void *fs_r = nullptr;
+    void *qs_r = nullptr;
+    int *perm_r = nullptr;
+    int *cnt_r = nullptr;
+    int *slot_r = nullptr;
+    int *key_r = nullptr;
+    int *status = nullptr;  // device flags
+};
+
+}  // namespace se
+
+struct se_plan_s {
+    int kernel = 0;
+    int prec = 0;
+    int64_t N = 0;
+    double x0[3] = {0, 0, 0};
+    double L = 1;
+    // method parameters
+    double xi = 0, rc = 0, h = 0, eta = 0, m = 0, deltaL = 0, R = 0;
+    int M = 0, P = 0, n_ext = 0, Mt = 0, Mf = 0, Mg = 0, deltaL_policy = 0, max_fft = 0;
+    int nc = 3;  // spread components (3; stresslet 6)
+    se::Geom geom{};
+    int ntiles = 0, ncells = 0;
+    bool tiled = true;  // tiled shared-memory spreading (else global atomics)
+    // device memory
+    double *ghat64 = nullptr;  // (Mt+1)^3 octant of the precomputed kernel, FP64
+    void *ghat = nullptr;      // same in the plan precision
+    void *grid = nullptr;      // nc x Mf^3 real, zero padded (R2C input)
+    void *spec = nullptr;      // nc x Mf x Mf x (Mf/2+1) complex
+    void *wgrid = nullptr;     // 3 x Mf^3 real (C2R output)
+    void *wgrid2 = nullptr;    // 3 x Mf^3 real (backward: adjoint grid)
+    void *spec2 = nullptr;     // backward spectrum
+    void *tmp3 = nullptr;      // N x 3 scratch in plan precision (backward)
+    se::Buffers b;
+    cufftHandle fwd = 0, inv = 0, fwd3 = 0;
+    bool have_fwd = false, have_inv = false, have_fwd3 = false;
+    cudaStream_t last_stream = nullptr;
+    bool timing = false;
+    cudaEvent_t ev[9] = {};
+    float stage_ms[8] = {};
+    int n_stage = 0;
+    double precompute_ms = 0;
+    // host staging for se_eval_host
+    void *dx = nullptr, *df = nullptr, *dq = nullptr, *du = nullptr;
+};
+
+namespace se {
+
+// launchers (defined in the .cu files); all asynchronous on `st`
+template <typename T>
+cudaError_t launch_bin(se_plan_s *p, const T *x, const T *f, const T *q, cudaStream_t st);
+template <typename T>
+cudaError_t launch_spread(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
+                          void *grid, int nc_mode);
+template <typename T>
+cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpose);
+template <typename T>
+cudaError_t launch_gather(se_plan_s *p, cudaStream_t st, const void *wgrid, const T *f_orig, T *u);
+template <typename T>
+cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u);
+template <typename T>
+cudaError_t launch_zero_octant(se_plan_s *p, cudaStream_t st, void *grid, int nc);
+template <typename T>
+cudaError_t launch_gather_grad(se_plan_s *p, cudaStream_t st, const void *w_fwd, const void *w_adj,
+                               const T *f_orig, const T *g_orig, T *gx);
+template <typename T>
+cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *gx);
+
+se_status_t precompute(se_plan_s *p);
+se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
+                          double xi_arg, se_params_t *out);
+
+}  // namespace se

@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libse.so (include/se.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch supplies device memory and the current stream.  There is no CPU
+fallback: if the library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libse.so")
+
+KERNELS = {"stokeslet": 0, "stresslet": 1, "rotlet": 2}
+PRECS = {"fp32": 0, "fp64": 1}
+STATUS = {
+    0: "SE_OK", 1: "SE_ERR_INVALID_ARG", 2: "SE_ERR_OUT_OF_BOX", 3: "SE_ERR_COINCIDENT",
+    4: "SE_ERR_OOM", 5: "SE_ERR_CUDA", 6: "SE_ERR_CUFFT", 7: "SE_ERR_TIMEOUT",
+    8: "SE_ERR_NOT_SUPPORTED",
+}
+STAGES = ["bin", "spread", "fft", "scale", "ifft", "gather", "real"]
+
+
+class SEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SEParams(ctypes.Structure):
+    _fields_ = [
+        ("xi", ctypes.c_double), ("rc", ctypes.c_double), ("M", ctypes.c_int), ("P", ctypes.c_int),
+        ("deltaL_policy", ctypes.c_int), ("max_fft", ctypes.c_int), ("Mtilde", ctypes.c_int),
+        ("Mg", ctypes.c_int), ("eta", ctypes.c_double), ("h", ctypes.c_double),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libse.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_SO):
+                raise RuntimeError(
+                    f"{_SO} is missing: build it with paper_1607_04808_gb300._build.build() "
+                    "(or __graft_entry__.build())")
+            L = ctypes.CDLL(_SO)
+            vp, i64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+            L.se_plan_create.restype = i32
+            L.se_plan_create.argtypes = [i32, i64, dbl, ctypes.POINTER(ctypes.c_double), dbl, i32,
+                                         ctypes.POINTER(SEParams), ctypes.POINTER(vp)]
+            L.se_eval.restype = i32
+            L.se_eval.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.se_eval_host.restype = i32
+            L.se_eval_host.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.se_eval_backward.restype = i32
+            L.se_eval_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+            L.se_choose_params.restype = i32
+            L.se_choose_params.argtypes = [i32, i32, i64, dbl, dbl, dbl, ctypes.POINTER(SEParams),
+                                           ctypes.POINTER(SEParams)]
+            L.se_plan_get_params.restype = i32
+            L.se_plan_get_params.argtypes = [vp, ctypes.POINTER(SEParams)]
+            L.se_plan_check.restype = i32
+            L.se_plan_check.argtypes = [vp]
+            L.se_plan_set_timing.restype = i32
+            L.se_plan_set_timing.argtypes = [vp, i32]
+            L.se_plan_stage_times.restype = i32
+            L.se_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
+            L.se_plan_destroy.restype = i32
+            L.se_plan_destroy.argtypes = [vp]
+            L.se_last_error.restype = ctypes.c_char_p
+            L.se_last_error.argtypes = []
+            L.se_version.restype = ctypes.c_char_p
+            L.se_version.argtypes = []
+            _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise SEError(code, lib().se_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A Spectral Ewald plan for N points in the cube [x0, x0+L)^3 (se_plan_create)."""
+
+    def __init__(self, kernel: str, N: int, box=(0.0, 0.0, 0.0, 1.0), *, xi: float = 0.0,
+                 tol: float = 0.0, prec: str = "fp32", M: int = 0, P: int = 0, rc: float = 0.0,
+                 deltaL_policy: int = 0, max_fft: int = 0):
+        self.kernel = kernel
+        self.kid = KERNELS[kernel]
+        self.N = int(N)
+        self.prec = prec
+        self.dtype = torch.float32 if prec == "fp32" else torch.float64
+        self.box = tuple(float(b) for b in box)
+        prm = SEParams(xi=float(xi), rc=float(rc), M=int(M), P=int(P),
+                       deltaL_policy=int(deltaL_policy), max_fft=int(max_fft))
+        boxa = (ctypes.c_double * 4)(*self.box)
+        h = ctypes.c_void_p()
+        _check(lib().se_plan_create(self.kid, self.N, float(xi), boxa, float(tol), PRECS[prec],
+                                    ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def params(self) -> dict:
+        p = SEParams()
+        _check(lib().se_plan_get_params(self._h, ctypes.byref(p)))
+        return {k: getattr(p, k) for k, _ in SEParams._fields_}
+
+    def _arg(self, t, name):
+        if t is None:
+            return None
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.shape == (self.N, 3)):
+            raise ValueError(f"{name}: expected a contiguous CUDA tensor ({self.N}, 3) of {self.dtype}")
+        return t
+
+    def eval(self, x, f, q=None, out=None, stream=None, check=False):
+        """u = sum_{n != m} K(x_m - x_n) . f_n (se_eval) on device tensors."""
+        x, f, q = self._arg(x, "x"), self._arg(f, "f"), self._arg(q, "q")
+        if out is None:
+            out = torch.empty_like(x)
+        self._arg(out, "out")
+        _check(lib().se_eval(self._h, _ptr(x), _ptr(f), _ptr(q), _ptr(out), _stream(stream)))
+        if check:
+            self.check()
+        return out
+
+    def eval_host(self, x: np.ndarray, f: np.ndarray, q: np.ndarray | None = None,
+                  out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """se_eval_host: host arrays in, host array out (copies inside the call)."""
+        dt = np.float32 if self.prec == "fp32" else np.float64
+
+        def host(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                assert a.device.type == "cpu" and a.dtype == self.dtype and a.is_contiguous()
+                return a
+            a = np.ascontiguousarray(a, dtype=dt)
+            assert a.shape == (self.N, 3)
+            return a
+
+        def p(a):
+            if a is None:
+                return None
+            return ctypes.c_void_p(a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data)
+
+        x, f, q = host(x), host(f), host(q)
+        if out is None:
+            out = np.empty((self.N, 3), dtype=dt)
+        _check(lib().se_eval_host(self._h, p(x), p(f), p(q), p(out), _stream(stream)))
+        return out
+
+    def backward(self, x, f, grad_u, want_f=True, want_x=True, stream=None):
+        """Gradients of L = sum grad_u . u: (grad_f, grad_x) (se_eval_backward)."""
+        x, f, grad_u = self._arg(x, "x"), self._arg(f, "f"), self._arg(grad_u, "grad_u")
+        gf = torch.empty_like(x) if want_f else None
+        gx = torch.empty_like(x) if want_x else None
+        _check(lib().se_eval_backward(self._h, _ptr(x), _ptr(f), None, _ptr(grad_u), _ptr(gf),
+                                      _ptr(gx), _stream(stream)))
+        return gf, gx
+
+    def check(self):
+        """se_plan_check: synchronise and raise on a device-side error."""
+        _check(lib().se_plan_check(self._h))
+
+    def set_timing(self, on: bool = True):
+        _check(lib().se_plan_set_timing(self._h, 1 if on else 0))
+
+    def stage_times(self) -> dict:
+        buf = (ctypes.c_float * 8)()
+        n = lib().se_plan_stage_times(self._h, buf, 8)
+        return {STAGES[i]: buf[i] for i in range(n)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().se_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SEFunction(torch.autograd.Function):
+    """u = SE(x, f) with gradients for x and f (stokeslet, rotlet) through se_eval_backward."""
+
+    @staticmethod
+    def forward(ctx, x, f, plan: Plan):
+        ctx.plan = plan
+        ctx.save_for_backward(x, f)
+        return plan.eval(x.contiguous(), f.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        x, f = ctx.saved_tensors
+        gf, gx = ctx.plan.backward(x, f, grad_u.contiguous(), want_f=ctx.needs_input_grad[1],
+                                   want_x=ctx.needs_input_grad[0])
+        return gx, gf, None
+
+
+def se_sum(x, f, plan: Plan):
+    """Differentiable u = sum K(x_m - x_n) f_n."""
+    return SEFunction.apply(x, f, plan)
+
+
+def choose_params(kernel: str, N: int, L: float = 1.0, tol: float = 0.0, prec: str = "fp32",
+                  xi: float = 0.0, **overrides) -> dict:
+    """Parameters the library would choose (se_choose_params; host only, no GPU needed)."""
+    pin = SEParams(**{k: v for k, v in overrides.items()})
+    pout = SEParams()
+    _check(lib().se_choose_params(KERNELS[kernel], PRECS[prec], int(N), float(L), float(tol), float(xi),
+                                  ctypes.byref(pin), ctypes.byref(pout)))
+    return {k: getattr(pout, k) for k in ("xi", "rc", "M", "P", "deltaL_policy", "max_fft")}
+
+
+def version() -> str:
+    return lib().se_version().decode()

@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: relative L2 and relative max error (c10 reading: max|du| / max|u|)
+against the direct sum O1 of 1e-10 for the FP64 path and 2e-6 for the FP32
+path.  FP32 runs are compared with the oracle evaluated on the FP32-rounded
+inputs (exactly representable in FP64).  Against O2 (the plain CPU Spectral
+Ewald with the same parameters) the FP64 path agrees far more tightly: both
+compute the same discrete approximation, so only rounding separates them.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import direct, se as ose
+
+pytestmark = pytest.mark.gpu
+
+BOX = (0.0, 0.0, 0.0, 1.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_04808_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+
+
+def P():
+    import paper_1607_04808_gb300 as pkg
+    return pkg
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rel_max(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def gpu_eval(kernel, x, f, q=None, prec="fp64", box=BOX, **kw):
+    pkg = P()
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    plan = pkg.Plan(kernel, len(x), box, prec=prec, **kw)
+    tx = torch.tensor(x, dtype=dt, device="cuda")
+    tf = torch.tensor(f, dtype=dt, device="cuda")
+    tq = None if q is None else torch.tensor(q, dtype=dt, device="cuda")
+    u = plan.eval(tx, tf, tq)
+    plan.check()
+    out = u.double().cpu().numpy()
+    prm = plan.params
+    plan.close()
+    return out, prm
+
+
+def as32(a):
+    return None if a is None else np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+KN = ["stokeslet", "stresslet", "rotlet"]
+
+
+# ------------------------------------------------------------------ small cases
+
+@pytest.mark.parametrize("kernel", KN)
+def test_fp64_small_vs_direct_and_o2(kernel):
+    """1000 uniform points (the first workload's size), FP64 path at 1e-10."""
+    x, f = W.stokeslet_uniform(1000, 0)
+    q = W.unit_vectors(1000, 0) if kernel == "stresslet" else None
+    u, prm = gpu_eval(kernel, x, f, q, "fp64", tol=1e-10)
+    ref = direct.direct(kernel, x, f, q)
+    assert rel_l2(u, ref) <= 1e-10
+    assert rel_max(u, ref) <= 1e-10
+    o2 = ose.se_eval(kernel, x, f, q, M=prm["M"], P=prm["P"], xi=prm["xi"], rc=prm["rc"])
+    assert rel_l2(u, o2) <= 1e-12
+
+
+@pytest.mark.parametrize("kernel", KN)
+def test_fp32_small_vs_direct_and_o2(kernel):
+    x, f = W.stokeslet_uniform(3000, 1)
+    q = W.unit_vectors(3000, 1) if kernel == "stresslet" else None
+    x32, f32, q32 = as32(x), as32(f), as32(q)
+    u, prm = gpu_eval(kernel, x32, f32, q32, "fp32", tol=2e-6)
+    ref = direct.direct(kernel, x32, f32, q32)
+    assert rel_l2(u, ref) <= 2e-6
+    assert rel_max(u, ref) <= 2e-6
+    o2 = ose.se_eval(kernel, x32, f32, q32, M=prm["M"], P=prm["P"], xi=prm["xi"], rc=prm["rc"])
+    assert rel_l2(u, o2) <= 1e-6
+
+
+@pytest.mark.parametrize("N", [1, 2, 33, 517])
+def test_ragged_and_tiny(N):
+    """Sizes that leave tiles, cells and warps partly empty; N = 1 has no pairs."""
+    x, f = W.stokeslet_uniform(N, 5)
+    u, prm = gpu_eval("stokeslet", x, f, None, "fp64", tol=1e-10)
+    if N == 1:
+        # the self term cancels the point's own image in the Fourier part
+        assert np.abs(u).max() <= 1e-9 * 4 * prm["xi"] * np.abs(f).max()
+    else:
+        ref = direct.direct("stokeslet", x, f)
+        assert rel_l2(u, ref) <= 1e-10
+
+
+def test_box_offset_and_side():
+    """A box not at the origin and not of unit side (x0 = (-2, 1, 0.5), L = 3)."""
+    box = (-2.0, 1.0, 0.5, 3.0)
+    x = W.uniform_points(800, 6, L=3.0, x0=box[:3])
+    f = W.normal_vectors(800, 6)
+    u, _ = gpu_eval("rotlet", x, f, None, "fp64", box=box, tol=1e-10)
+    assert rel_l2(u, direct.direct("rotlet", x, f)) <= 1e-10
+
+
+def test_clustered_stresslet_fp32():
+    """Blobs (the stresslet workload's distribution) at reduced N."""
+    x, f, q = W.stresslet_blobs(4000, 2)
+    x32, f32, q32 = as32(x), as32(f), as32(q)
+    u, _ = gpu_eval("stresslet", x32, f32, q32, "fp32", tol=2e-6)
+    ref = direct.direct("stresslet", x32, f32, q32)
+    assert rel_l2(u, ref) <= 2e-6
+
+
+def test_explicit_parameters_and_strict_deltaL():
+    x, f = W.stokeslet_uniform(600, 7)
+    kw = dict(M=24, P=24, xi=5.0, rc=0.9, deltaL_policy=1)
+    u, prm = gpu_eval("stokeslet", x, f, None, "fp64", **kw)
+    assert prm["Mtilde"] > 24 + 24
+    o2 = ose.se_eval("stokeslet", x, f, M=24, P=24, xi=5.0, rc=0.9, deltaL_policy="strict")
+    assert rel_l2(u, o2) <= 1e-12
+
+
+def test_eval_host_matches_device():
+    pkg = P()
+    x, f = W.stokeslet_uniform(2000, 8)
+    plan = pkg.Plan("stokeslet", 2000, BOX, prec="fp32", tol=2e-6)
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+    ud = plan.eval(xd, fd).cpu().numpy()
+    uh = plan.eval_host(x.astype(np.float32), f.astype(np.float32))
+    assert rel_l2(uh.astype(np.float64), ud.astype(np.float64)) <= 1e-6
+    plan.close()
+
+
+def test_status_out_of_box_and_coincident():
+    pkg = P()
+    x, f = W.stokeslet_uniform(100, 9)
+    plan = pkg.Plan("stokeslet", 100, BOX, prec="fp64", tol=1e-8)
+    xd = torch.tensor(x, device="cuda")
+    fd = torch.tensor(f, device="cuda")
+    plan.eval(xd, fd)
+    plan.check()
+    xb = x.copy()
+    xb[3] = [0.5, 1.0, 0.5]  # on the open upper face
+    with pytest.raises(pkg.SEError) as ei:
+        plan.eval(torch.tensor(xb, device="cuda"), fd, check=True)
+    assert ei.value.code == 2
+    xc = x.copy()
+    xc[5] = xc[6]
+    u = plan.eval(torch.tensor(xc, device="cuda"), fd)
+    with pytest.raises(pkg.SEError) as ei:
+        plan.check()
+    assert ei.value.code == 3
+    # the other points are still evaluated (the coincident pair is skipped on both sides)
+    ref = direct.direct("stokeslet", xc, fd.cpu().numpy())
+    keep = np.ones(100, bool)
+    keep[[5, 6]] = False
+    assert rel_l2(u.cpu().numpy()[keep], ref[keep]) <= 1e-7
+    plan.close()
+
+
+def test_invalid_arguments():
+    pkg = P()
+    with pytest.raises(pkg.SEError) as ei:
+        pkg.Plan("stokeslet", 0, BOX)
+    assert ei.value.code == 1
+    with pytest.raises(pkg.SEError):
+        pkg.Plan("stokeslet", 10, (0, 0, 0, -1.0))
+    plan = pkg.Plan("stresslet", 10, BOX, prec="fp64", tol=1e-6)
+    x = torch.rand(10, 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.SEError) as ei:
+        plan.eval(x, x)  # the stresslet needs q
+    assert ei.value.code == 1
+    plan.close()
+
+
+def test_stage_timing_reported():
+    pkg = P()
+    x, f = W.stokeslet_uniform(5000, 10)
+    plan = pkg.Plan("stokeslet", 5000, BOX, prec="fp32", tol=2e-6)
+    plan.set_timing(True)
+    plan.eval(torch.tensor(x, dtype=torch.float32, device="cuda"),
+              torch.tensor(f, dtype=torch.float32, device="cuda"))
+    t = plan.stage_times()
+    assert set(t) == {"bin", "spread", "fft", "scale", "ifft", "gather", "real"}
+    assert all(v >= 0 for v in t.values())
+    plan.close()
+
+
+# ------------------------------------------------------------------ backward
+
+@pytest.mark.parametrize("kernel", ["stokeslet", "rotlet"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_backward_vs_direct_gradients(kernel, prec):
+    x, f, g = W.rotlet_uniform(2000, 11)
+    if prec == "fp32":
+        x, f, g = as32(x), as32(f), as32(g)
+    pkg = P()
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    plan = pkg.Plan(kernel, 2000, BOX, prec=prec, tol=1e-10 if prec == "fp64" else 2e-6)
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")  # noqa: E731
+    gf, gx = plan.backward(t(x), t(f), t(g))
+    torch.cuda.synchronize()
+    ref_gf = direct.grad_f(kernel, x, g)
+    ref_gx = direct.grad_x(kernel, x, f, g)
+    tol_f, tol_x = (1e-9, 1e-8) if prec == "fp64" else (2e-6, 2e-5)
+    assert rel_l2(gf.double().cpu().numpy(), ref_gf) <= tol_f
+    assert rel_l2(gx.double().cpu().numpy(), ref_gx) <= tol_x
+    plan.close()
+
+
+def test_autograd_function_matches_fd():
+    """torch.autograd through SEFunction; central differences of the FP64 forward."""
+    pkg = P()
+    x, f, g = W.rotlet_uniform(300, 12)
+    plan = pkg.Plan("rotlet", 300, BOX, prec="fp64", tol=1e-11)
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    ft = torch.tensor(f, device="cuda", requires_grad=True)
+    gt = torch.tensor(g, device="cuda")
+    u = pkg.se_sum(xt, ft, plan)
+    (u * gt).sum().backward()
+    h = 1e-4
+    for p_, a in ((0, 0), (123, 2), (299, 1)):
+        xp, xm = x.copy(), x.copy()
+        xp[p_, a] += h
+        xm[p_, a] -= h
+        lp = float((plan.eval(torch.tensor(xp, device="cuda"), ft.detach()) * gt).sum())
+        lm = float((plan.eval(torch.tensor(xm, device="cuda"), ft.detach()) * gt).sum())
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - float(xt.grad[p_, a])) <= 1e-5 * max(1.0, abs(fd))
+    np.testing.assert_allclose(ft.grad.cpu().numpy(), direct.grad_f("rotlet", x, g), rtol=0,
+                               atol=1e-9 * np.abs(direct.grad_f("rotlet", x, g)).max())
+    plan.close()
+
+
+# ------------------------------------------------------------------ full size
+
+def test_full_size_fp32_stokeslet_sampled():
+    """N = 1e6 stokeslet, FP32 path with the FFT capped at 256^3 (the benchmarked
+    launch configuration); 256 sampled targets against the exact direct sum."""
+    N = 1_000_000
+    x, f = W.stokeslet_uniform(N, 1)
+    x32, f32 = as32(x), as32(f)
+    u, prm = gpu_eval("stokeslet", x32, f32, None, "fp32", tol=2e-6, max_fft=256)
+    assert 2 * prm["Mtilde"] <= 256
+    idx = np.random.default_rng(0).choice(N, 256, replace=False)
+    ref = direct.direct("stokeslet", x32, f32, targets=idx)
+    assert rel_l2(u[idx], ref) <= 2e-6
+
+
+def test_full_size_fp64_stokeslet_sampled():
+    N = 1_000_000
+    x, f = W.stokeslet_uniform(N, 1)
+    u, prm = gpu_eval("stokeslet", x, f, None, "fp64", tol=1e-10)
+    idx = np.random.default_rng(1).choice(N, 96, replace=False)
+    ref = direct.direct("stokeslet", x, f, targets=idx)
+    assert rel_l2(u[idx], ref) <= 1e-10
