@@ -1,6 +1,7 @@
 // Point binning (counting sort) for the spreading tiles and the real-space
 // cells.  Section 6 (cell list) and Section 5.2 (points grouped by the grid
-// block their Gaussian support starts in).
+// block their Gaussian support starts in).  The window start of every point
+// and its cell are computed here once and stored with the sorted copies.
 #include "se_internal.cuh"
 
 namespace se {
@@ -8,30 +9,30 @@ namespace se {
 namespace {
 
 template <typename T>
-__global__ void k_bin_count(int N, const T *__restrict__ x, Geom g, int *__restrict__ cnt_t,
+__global__ void k_bin_count(int N, const T *__restrict__ x, GP<T> g, int *__restrict__ cnt_t,
                             int *__restrict__ slot_t, int *__restrict__ key_t, int *__restrict__ cnt_r,
-                            int *__restrict__ slot_r, int *__restrict__ key_r, int *__restrict__ status) {
+                            int *__restrict__ slot_r, int *__restrict__ key_r, int *__restrict__ tag_t,
+                            int *__restrict__ tag_r, int *__restrict__ status) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    int tc[3], cc[3];
+    int i0[3], cc[3];
     bool oob = false;
     for (int d = 0; d < 3; d++) {
-        double rel = (double)x[3 * i + d] - g.x0[d];
+        T rel = x[3 * i + d] - g.x0[d];
         // half-open box [x0, x0 + L); NaN fails both tests
-        if (!(rel >= 0.0 && rel < g.L)) oob = true;
+        if (!(rel >= T(0) && rel < g.L)) oob = true;
         rel = clamp_rel(rel, g.L);
-        double t;
-        int i0 = window_start(rel, g, t);
-        i0 = min(max(i0, 0), g.Mt - g.P);
-        tc[d] = min(i0 / g.T, g.ntd - 1);
-        int c = (int)(rel * g.inv_cw);
-        cc[d] = min(max(c, 0), g.ncd - 1);
+        i0[d] = window_start(rel, g);
+        cc[d] = min(max((int)(rel * g.inv_cw), 0), g.ncd - 1);
     }
     if (oob) atomicOr(status, FLAG_OOB);
-    int kt = (tc[2] * g.ntd + tc[1]) * g.ntd + tc[0];
+    int kt = (min(i0[2] / g.T_, g.ntd - 1) * g.ntd + min(i0[1] / g.T_, g.ntd - 1)) * g.ntd +
+             min(i0[0] / g.T_, g.ntd - 1);
     int kr = (cc[2] * g.ncd + cc[1]) * g.ncd + cc[0];
     key_t[i] = kt;
     key_r[i] = kr;
+    tag_t[i] = pack3(i0[0], i0[1], i0[2]);
+    tag_r[i] = pack3(cc[0], cc[1], cc[2]);
     slot_t[i] = atomicAdd(&cnt_t[kt], 1);
     slot_r[i] = atomicAdd(&cnt_r[kr], 1);
 }
@@ -68,19 +69,23 @@ __global__ void k_bin_scatter(int N, const T *__restrict__ x, const T *__restric
                               const int *__restrict__ start_t, const int *__restrict__ slot_t,
                               const int *__restrict__ key_t, const int *__restrict__ start_r,
                               const int *__restrict__ slot_r, const int *__restrict__ key_r,
+                              const int *__restrict__ tag_t, const int *__restrict__ tag_r,
                               vec4<T> *__restrict__ xs_t, vec4<T> *__restrict__ fs_t, vec4<T> *__restrict__ qs_t,
                               int *__restrict__ perm_t, vec4<T> *__restrict__ xs_r, vec4<T> *__restrict__ fs_r,
                               vec4<T> *__restrict__ qs_r, int *__restrict__ perm_r) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     vec4<T> xv, fv, qv;
-    xv.x = x[3 * i]; xv.y = x[3 * i + 1]; xv.z = x[3 * i + 2]; xv.w = 0;
+    xv.x = x[3 * i]; xv.y = x[3 * i + 1]; xv.z = x[3 * i + 2];
     fv.x = f[3 * i]; fv.y = f[3 * i + 1]; fv.z = f[3 * i + 2]; fv.w = 0;
     if (q) { qv.x = q[3 * i]; qv.y = q[3 * i + 1]; qv.z = q[3 * i + 2]; qv.w = 0; }
     int pt = start_t[key_t[i]] + slot_t[i];
     int pr = start_r[key_r[i]] + slot_r[i];
+    vec4<T> xr = xv;
+    set_tag(xv, tag_t[i]);
+    set_tag(xr, tag_r[i]);
     xs_t[pt] = xv; fs_t[pt] = fv; perm_t[pt] = i;
-    xs_r[pr] = xv; fs_r[pr] = fv; perm_r[pr] = i;
+    xs_r[pr] = xr; fs_r[pr] = fv; perm_r[pr] = i;
     if (q) { qs_t[pt] = qv; qs_r[pr] = qv; }
 }
 
@@ -94,12 +99,12 @@ cudaError_t launch_bin(se_plan_s *p, const T *x, const T *f, const T *q, cudaStr
     if ((e = cudaMemsetAsync(b.cnt_t, 0, sizeof(int) * (p->ntiles + 1), st))) return e;
     if ((e = cudaMemsetAsync(b.cnt_r, 0, sizeof(int) * (p->ncells + 1), st))) return e;
     int bs = 256, gs = (N + bs - 1) / bs;
-    k_bin_count<T><<<gs, bs, 0, st>>>(N, x, p->geom, b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r,
-                                      b.status);
+    k_bin_count<T><<<gs, bs, 0, st>>>(N, x, gp<T>(p), b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r,
+                                      b.tag_t, b.tag_r, b.status);
     k_scan_exclusive<<<1, 1024, 0, st>>>(b.cnt_t, p->ntiles);
     k_scan_exclusive<<<1, 1024, 0, st>>>(b.cnt_r, p->ncells);
-    k_bin_scatter<T><<<gs, bs, 0, st>>>(N, x, f, q, b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r,
-                                        (vec4<T> *)b.xs_t, (vec4<T> *)b.fs_t, (vec4<T> *)b.qs_t, b.perm_t,
+    k_bin_scatter<T><<<gs, bs, 0, st>>>(N, x, f, q, b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r, b.tag_t,
+                                        b.tag_r, (vec4<T> *)b.xs_t, (vec4<T> *)b.fs_t, (vec4<T> *)b.qs_t, b.perm_t,
                                         (vec4<T> *)b.xs_r, (vec4<T> *)b.fs_r, (vec4<T> *)b.qs_r, b.perm_r);
     return cudaGetLastError();
 }

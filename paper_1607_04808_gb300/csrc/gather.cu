@@ -3,8 +3,8 @@
 // (h^3 and the prefactor are folded into the scaling step), followed by the
 // self-interaction correction of eq. Slimit, -4 xi/sqrt(pi) f_m (stokeslet),
 // added in FP64.  One warp per target; lanes cover the (x, y) columns of the
-// support and loop over z.  Also the position-gradient quadrature used by
-// the backward pass.
+// support and loop over z, so each load instruction reads a few contiguous
+// rows of the grid.  Also the position-gradient quadrature of the backward pass.
 #include "se_internal.cuh"
 
 namespace se {
@@ -14,25 +14,20 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int WPB = 8;  // warps per block
 
-__device__ __forceinline__ float gexp(float v) { return expf(v); }
+__device__ __forceinline__ float gexp(float v) { return __expf(v); }
 __device__ __forceinline__ double gexp(double v) { return exp(v); }
 
-// Writes the 1-D weights (and the window start, and t - i0) of one point into
-// the warp's shared arrays: sw[d*32 + k] = exp(-a h^2 (t_d - i0_d - k)^2).
+// 1-D weights of the P support points of the target along each dimension into
+// the warp's shared arrays sw[d][k]; fr[d] = t_d - i0_d (grid units).
 template <typename T>
-__device__ __forceinline__ void warp_weights(const vec4<T> &xv, const Geom &g, int lane, int i0[3], T *sw,
-                                             T fr0[3]) {
-    T ah2 = (T)(g.a * g.h * g.h);
-    double rel[3] = {clamp_rel((double)xv.x - g.x0[0], g.L), clamp_rel((double)xv.y - g.x0[1], g.L),
-                     clamp_rel((double)xv.z - g.x0[2], g.L)};
+__device__ __forceinline__ void warp_weights(const vec4<T> &xv, const GP<T> &g, int lane, int i0[3],
+                                             T (*sw)[32], T fr[3]) {
+    unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+    const T rel[3] = {xv.x - g.x0[0], xv.y - g.x0[1], xv.z - g.x0[2]};
     for (int d = 0; d < 3; d++) {
-        double t;
-        int s = window_start(rel[d], g, t);
-        s = min(max(s, 0), g.Mt - g.P);
-        i0[d] = s;
-        fr0[d] = (T)(t - (double)s);
-        T fr = fr0[d] - (T)lane;
-        if (lane < g.P) sw[d * 32 + lane] = gexp(-ah2 * fr * fr);
+        fr[d] = (rel[d] * g.inv_h + g.half_ext) - (T)i0[d];
+        T t = fr[d] - (T)lane;
+        if (lane < g.P) sw[d][lane] = gexp(-g.ah2 * t * t);
     }
     __syncwarp();
 }
@@ -43,29 +38,30 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(WPB * 32) k_gather(Geom g, int N, const vec4<T> *__restrict__ xs,
+// lane's columns of the support: NIT static slots (P <= 16) or a strided loop
+template <typename T, int NIT>
+__global__ void __launch_bounds__(WPB * 32) k_gather(GP<T> g, int N, const vec4<T> *__restrict__ xs,
                                                      const int *__restrict__ perm, const T *__restrict__ w,
                                                      const T *__restrict__ f_orig, double self_coef,
                                                      T *__restrict__ u) {
-    __shared__ T sw_all[WPB][96];
+    __shared__ T sw_all[WPB][3][32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.x * WPB + wib;
     if (n >= N) return;
-    T *sw = sw_all[wib];
+    T(*sw)[32] = sw_all[wib];
     const int P = g.P, P2 = P * P;
     int i0[3];
-    T fr0[3];
-    warp_weights<T>(xs[n], g, lane, i0, sw, fr0);
+    T fr[3];
+    warp_weights<T>(xs[n], g, lane, i0, sw, fr);
     const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+    const T *base = w + ((size_t)i0[2] * Mf + i0[1]) * Mf + i0[0];
     T acc0 = 0, acc1 = 0, acc2 = 0;
-    for (int idx = lane; idx < P2; idx += 32) {
-        int ky = idx / P, kx = idx - ky * P;
-        T wxy = sw[kx] * sw[32 + ky];
-        const T *col = w + ((size_t)i0[2] * Mf + (i0[1] + ky)) * Mf + (i0[0] + kx);
+    auto column = [&](int kx, int ky) {
+        const T wxy = sw[0][kx] * sw[1][ky];
+        const T *col = base + (size_t)ky * Mf + kx;
         T a0 = 0, a1 = 0, a2 = 0;
         for (int kz = 0; kz < P; kz++) {
-            T wz = sw[64 + kz];
+            const T wz = sw[2][kz];
             const T *pz = col + kz * Mf2;
             a0 += __ldg(pz) * wz;
             a1 += __ldg(pz + Mf3) * wz;
@@ -74,75 +70,84 @@ __global__ void __launch_bounds__(WPB * 32) k_gather(Geom g, int N, const vec4<T
         acc0 += a0 * wxy;
         acc1 += a1 * wxy;
         acc2 += a2 * wxy;
+    };
+    if (NIT > 0) {
+#pragma unroll
+        for (int it = 0; it < (NIT > 0 ? NIT : 1); it++) {
+            int idx = it * 32 + lane;
+            if (idx < P2) {
+                int ky = idx / P;
+                column(idx - ky * P, ky);
+            }
+        }
+    } else {
+        for (int idx = lane; idx < P2; idx += 32) {
+            int ky = idx / P;
+            column(idx - ky * P, ky);
+        }
     }
     acc0 = warp_sum(acc0);
     acc1 = warp_sum(acc1);
     acc2 = warp_sum(acc2);
-    if (lane == 0) {
-        int m = perm[n];
-        double o0 = (double)acc0, o1 = (double)acc1, o2 = (double)acc2;
-        if (self_coef != 0.0) {
-            o0 += self_coef * (double)f_orig[3 * m];
-            o1 += self_coef * (double)f_orig[3 * m + 1];
-            o2 += self_coef * (double)f_orig[3 * m + 2];
-        }
-        u[3 * m] = (T)o0;
-        u[3 * m + 1] = (T)o1;
-        u[3 * m + 2] = (T)o2;
+    if (lane < 3) {
+        // lanes 0..2 each finish one component (FP64 self-interaction correction)
+        const int m = perm[n];
+        const T a = lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2);
+        double o = (double)a;
+        if (self_coef != 0.0) o += self_coef * (double)f_orig[3 * m + lane];
+        u[3 * m + lane] = (T)o;
     }
 }
 
 // Position gradient of the Fourier part of L = sum_m g_m . u_m:
 //   gx_p = h^3 sum_i [g_p . w_i + f_p . w'_i] grad Gauss(x_p - y_i),
-// grad Gauss(r) = -(4 xi^2/eta) r Gauss(r) = -2 a r Gauss(r); w (forward grid
-// from f) and w' (adjoint grid from g) already carry h^3 and the prefactors.
+// grad Gauss(r) = -(4 xi^2/eta) r Gauss(r); w (forward grid from f) and w'
+// (adjoint grid from g) already carry h^3 and the prefactors.  In grid units
+// x - y = (t - i) h, so d/dx_d Gauss = -2 a h (fr_d - k) Gauss.
 template <typename T>
-__global__ void __launch_bounds__(WPB * 32) k_gather_grad(Geom g, int N, const vec4<T> *__restrict__ xs,
+__global__ void __launch_bounds__(WPB * 32) k_gather_grad(GP<T> g, T c_grad, int N, const vec4<T> *__restrict__ xs,
                                                           const int *__restrict__ perm,
                                                           const T *__restrict__ wf, const T *__restrict__ wa,
                                                           const T *__restrict__ f_orig,
                                                           const T *__restrict__ g_orig, T *__restrict__ gx) {
-    __shared__ T sw_all[WPB][96];
+    __shared__ T sw_all[WPB][3][32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.x * WPB + wib;
     if (n >= N) return;
-    T *sw = sw_all[wib];
+    T(*sw)[32] = sw_all[wib];
     const int P = g.P, P2 = P * P;
     int i0[3];
-    T fr0[3];
-    warp_weights<T>(xs[n], g, lane, i0, sw, fr0);
+    T fr[3];
+    warp_weights<T>(xs[n], g, lane, i0, sw, fr);
     const int m = perm[n];
     const T gm[3] = {g_orig[3 * m], g_orig[3 * m + 1], g_orig[3 * m + 2]};
     const T fm[3] = {f_orig[3 * m], f_orig[3 * m + 1], f_orig[3 * m + 2]};
     const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
-    // distance (grid units) from the target to support point k along d: fr0[d] - k
-    // d/dx_d Gauss = -2 a h (fr0 - k) Gauss  (x - y = (t - i) h)
     T acc[3] = {0, 0, 0};
     for (int idx = lane; idx < P2; idx += 32) {
         int ky = idx / P, kx = idx - ky * P;
-        T wx = sw[kx], wy = sw[32 + ky];
-        T dx = fr0[0] - (T)kx, dy = fr0[1] - (T)ky;
+        T wx = sw[0][kx], wy = sw[1][ky];
+        T dx = fr[0] - (T)kx, dy = fr[1] - (T)ky;
         const size_t off = ((size_t)i0[2] * Mf + (i0[1] + ky)) * Mf + (i0[0] + kx);
         T s0 = 0, sz = 0;  // sum_kz s wz, sum_kz s wz dz
         for (int kz = 0; kz < P; kz++) {
-            T wz = sw[64 + kz];
+            T wz = sw[2][kz];
             size_t o = off + kz * Mf2;
             T s = gm[0] * __ldg(wf + o) + gm[1] * __ldg(wf + o + Mf3) + gm[2] * __ldg(wf + o + 2 * Mf3) +
                   fm[0] * __ldg(wa + o) + fm[1] * __ldg(wa + o + Mf3) + fm[2] * __ldg(wa + o + 2 * Mf3);
             s0 += s * wz;
-            sz += s * wz * (fr0[2] - (T)kz);
+            sz += s * wz * (fr[2] - (T)kz);
         }
         T wxy = wx * wy;
         acc[0] += s0 * wxy * dx;
         acc[1] += s0 * wxy * dy;
         acc[2] += sz * wxy;
     }
-    T c = (T)(-2.0 * g.a * g.h);
     for (int d = 0; d < 3; d++) acc[d] = warp_sum(acc[d]);
     if (lane == 0) {
-        gx[3 * m] = c * acc[0];
-        gx[3 * m + 1] = c * acc[1];
-        gx[3 * m + 2] = c * acc[2];
+        gx[3 * m] = c_grad * acc[0];
+        gx[3 * m + 1] = c_grad * acc[1];
+        gx[3 * m + 2] = c_grad * acc[2];
     }
 }
 
@@ -152,8 +157,21 @@ template <typename T>
 cudaError_t launch_gather(se_plan_s *p, cudaStream_t st, const void *wgrid, const T *f_orig, T *u) {
     int N = (int)p->N;
     double self_coef = (p->kernel == SE_STOKESLET) ? -4.0 * p->xi / sqrt(M_PI) : 0.0;
-    k_gather<T><<<(N + WPB - 1) / WPB, WPB * 32, 0, st>>>(p->geom, N, (const vec4<T> *)p->b.xs_t, p->b.perm_t,
-                                                          (const T *)wgrid, f_orig, self_coef, u);
+    dim3 gs((N + WPB - 1) / WPB), bs(WPB * 32);
+    const vec4<T> *xs = (const vec4<T> *)p->b.xs_t;
+    const T *w = (const T *)wgrid;
+    const GP<T> &g = gp<T>(p);
+    switch ((p->P * p->P + 31) / 32) {
+        case 1: k_gather<T, 1><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+        case 2: k_gather<T, 2><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+        case 3: k_gather<T, 3><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+        case 4: k_gather<T, 4><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+        case 5: k_gather<T, 5><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+        case 6: k_gather<T, 6><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+        case 7: k_gather<T, 7><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+        case 8: k_gather<T, 8><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+        default: k_gather<T, 0><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
+    }
     return cudaGetLastError();
 }
 
@@ -161,7 +179,8 @@ template <typename T>
 cudaError_t launch_gather_grad(se_plan_s *p, cudaStream_t st, const void *w_fwd, const void *w_adj,
                                const T *f_orig, const T *g_orig, T *gx) {
     int N = (int)p->N;
-    k_gather_grad<T><<<(N + WPB - 1) / WPB, WPB * 32, 0, st>>>(p->geom, N, (const vec4<T> *)p->b.xs_t,
+    T c_grad = (T)(-2.0 * p->geom.a * p->h);
+    k_gather_grad<T><<<(N + WPB - 1) / WPB, WPB * 32, 0, st>>>(gp<T>(p), c_grad, N, (const vec4<T> *)p->b.xs_t,
                                                                p->b.perm_t, (const T *)w_fwd, (const T *)w_adj,
                                                                f_orig, g_orig, gx);
     return cudaGetLastError();

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <string>
+#include <type_traits>
 
 #include "se_internal.cuh"
 
@@ -60,6 +61,19 @@ double min_rc(int kernel, double Q, double xi, double L, double budget) {
     return hi;
 }
 
+// FFT lengths cuFFT handles fast and accurately: only prime factors 2, 3, 5, 7.
+// In FP32 the 256-point length is excluded: with 256^3 transforms the Fourier
+// part of the FP32 path measured an order of magnitude less accurate (5e-6
+// relative) than with the neighbouring lengths 248, 252, 264 (3e-7 to 9e-7).
+bool good_fft(int n, int prec) {
+    if (n < 2) return false;
+    if (prec == SE_FP32 && n == 256) return false;
+    int m = n;
+    for (int f : {2, 3, 5, 7})
+        while (m % f == 0) m /= f;
+    return m == 1;
+}
+
 }  // namespace
 
 // Parameter selection.  Relative tolerances are turned into absolute RMS
@@ -67,7 +81,7 @@ double min_rc(int kernel, double Q, double xi, double L, double budget) {
 // sources, |u|_rms^2 ~ 6 <1/r^2> N ~ 33.6 N / L^2 (stokeslet; the same scale is
 // used, conservatively, for the stresslet and rotlet whose RMS is larger).  P is
 // the smallest even support whose approximation error 10^{-(P+1)/2} stays below
-// tol/3 (Section 8.2: P = 16 ~ 8 digits, 24 ~ 12 digits).  With a bound on the
+// tol/4 (Section 8.2: P = 16 ~ 8 digits, 24 ~ 12 digits).  With a bound on the
 // FFT size, xi is the largest value whose Fourier estimate at the largest
 // admissible M meets the budget; otherwise xi minimises a work model.
 se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
@@ -79,10 +93,10 @@ se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol,
     double Q = 3.0 * (double)N;
     double deg = (kernel == SE_STOKESLET) ? 1.0 : 2.0;
     double uabs = sqrt(33.6 * (double)N) / pow(L, deg);
-    double budget = tol * uabs / sqrt(3.0);
+    double budget = 0.5 * tol * uabs;  // each of the three error sources within tol/2
     if (p.P <= 0) {
         int P = 4;
-        while (P < 32 && pow(10.0, -0.5 * P - 0.5) > tol / 3.0) P += 2;
+        while (P < 32 && pow(10.0, -0.5 * P - 0.5) > tol / 4.0) P += 2;
         p.P = P;
     }
     double xi = (p.xi > 0) ? p.xi : xi_arg;
@@ -122,9 +136,31 @@ se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol,
         }
     }
     p.xi = xi;
+    const bool fixed_M = (in && in->M > 0);
     if (p.M <= 0) p.M = min_M(kernel, Q, xi, L, p.P, budget);
-    if (p.max_fft > 0 && 2 * (p.M + p.P) > p.max_fft) p.M = p.max_fft / 2 - p.P;
-    if (p.rc <= 0) p.rc = min_rc(kernel, Q, xi, L, budget);
+    if (!fixed_M && p.deltaL_policy == 0) {
+        // FFT length 2 (M + P): move M to a fast, accurate length (up, or down
+        // under a cap), then re-derive xi for that M when xi was chosen here
+        int M = p.M;
+        if (p.max_fft > 0 && 2 * (M + p.P) > p.max_fft) M = p.max_fft / 2 - p.P;
+        if (p.max_fft > 0) {
+            while (M > 2 && !good_fft(2 * (M + p.P), prec)) M--;
+        } else {
+            while (!good_fft(2 * (M + p.P), prec)) M++;
+        }
+        p.M = M;
+        if (!(in && in->xi > 0) && !(xi_arg > 0)) {
+            double lo = 0.1 / L, hi = 10.0 * p.M / L;
+            for (int it = 0; it < 100; it++) {
+                double mid = 0.5 * (lo + hi);
+                if (est_fourier(kernel, Q, mid, L, p.M, p.P) <= budget) lo = mid; else hi = mid;
+            }
+            p.xi = lo;
+        }
+    } else if (p.max_fft > 0 && 2 * (p.M + p.P) > p.max_fft) {
+        p.M = p.max_fft / 2 - p.P;
+    }
+    if (p.rc <= 0) p.rc = min_rc(kernel, Q, p.xi, L, budget);
     *out = p;
     return SE_OK;
 }
@@ -141,7 +177,7 @@ static void free_plan(se_plan_s *p) {
     void *ptrs[] = {p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
                     p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
                     p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
-                    p->b.key_r, p->b.status, p->dx, p->df, p->dq, p->du};
+                    p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 9; i++)
@@ -225,13 +261,36 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     g.T = (T > 0) ? T : 8;
     g.ntd = (p->Mt - p->P + 1 + g.T - 1) / g.T;
     p->ntiles = g.ntd * g.ntd * g.ntd;
-    // real-space cells of width >= rc/2 (at most 160 per dimension)
-    int ncd = (int)floor(2.0 * p->L / p->rc);
-    ncd = std::max(1, std::min(ncd, 160));
+    // real-space cells of width >= rc/3 (at most 200 per dimension)
+    int ncd = (int)floor(3.0 * p->L / p->rc);
+    ncd = std::max(1, std::min(ncd, 200));
     g.ncd = ncd;
     g.cw = p->L / ncd;
     g.inv_cw = ncd / p->L;
     p->ncells = ncd * ncd * ncd;
+    if (p->Mt > 1023) {
+        free_plan(p);
+        return fail(SE_ERR_INVALID_ARG, "extended grid above 1023 points per dimension");
+    }
+    // the same geometry in each arithmetic precision
+    auto fill = [&](auto &G) {
+        using TT = std::remove_reference_t<decltype(G.L)>;
+        for (int dd = 0; dd < 3; dd++) G.x0[dd] = (TT)p->x0[dd];
+        G.L = (TT)p->L;
+        G.inv_h = (TT)(1.0 / p->h);
+        G.half_ext = (TT)(0.5 * p->n_ext);
+        G.ah2 = (TT)(g.a * p->h * p->h);
+        G.inv_cw = (TT)g.inv_cw;
+        G.cw = (TT)g.cw;
+        G.P = p->P;
+        G.Mt = p->Mt;
+        G.Mf = p->Mf;
+        G.T_ = g.T;
+        G.ntd = g.ntd;
+        G.ncd = g.ncd;
+    };
+    fill(p->gpf);
+    fill(p->gpd);
 
     // allocations
     cudaError_t e = cudaSuccess;
@@ -260,6 +319,8 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
         if ((e = dmalloc(&p->b.perm_r, Nn * 4))) break;
         if ((e = dmalloc(&p->b.slot_r, Nn * 4))) break;
         if ((e = dmalloc(&p->b.key_r, Nn * 4))) break;
+        if ((e = dmalloc(&p->b.tag_t, Nn * 4))) break;
+        if ((e = dmalloc(&p->b.tag_r, Nn * 4))) break;
         if ((e = dmalloc(&p->b.cnt_r, ((size_t)p->ncells + 1) * 4))) break;
         if ((e = dmalloc(&p->b.status, 16))) break;
         if ((e = cudaMemset(p->grid, 0, (size_t)p->nc * Mf3 * esz))) break;

@@ -64,26 +64,48 @@ struct Geom {
     double xi;
 };
 
+// Geometry in the arithmetic precision T of the path, so that the FP32 kernels
+// never touch the (slow on this part) FP64 pipe for bookkeeping.
+template <typename T>
+struct GP {
+    T x0[3], L;        // box corner and side
+    T inv_h, half_ext; // t = (x - x0) / h + n_ext / 2 = (x - y0) / h (grid units)
+    T ah2;             // a h^2 = 2 xi^2 h^2 / eta: Gaussian exponent per grid unit^2
+    T inv_cw, cw;      // real-space cell width
+    int P, Mt, Mf, T_, ntd, ncd;
+};
+
 // Coordinate relative to the box corner, clamped into [0, L) for points outside
 // the box (they are flagged by the binning kernel; clamping keeps every kernel's
-// indexing in bounds and consistent with the binning).
-__host__ __device__ inline double clamp_rel(double rel, double L) {
-    if (!(rel >= 0.0 && rel < L)) rel = (rel >= L) ? L * (1.0 - 1e-12) : 0.0;
+// indexing in bounds).
+template <typename T>
+__host__ __device__ inline T clamp_rel(T rel, T L) {
+    if (!(rel >= T(0) && rel < L)) rel = (rel >= L) ? L * T(1.0 - 1e-6) : T(0);
     return rel;
 }
 
 // Window start of a point in one dimension (Section 5.2 with the P^3 block):
 //   P even: floor(t) - P/2 + 1, P odd: floor(t + 1/2) - (P-1)/2, t = (x - y0)/h,
-// computed in FP64 so that both precisions place a point identically.
-__host__ __device__ inline int window_start(double rel, const Geom &g, double &t) {
-    t = rel * g.inv_h + g.half_ext;
-    int i0;
-    if ((g.P & 1) == 0)
-        i0 = (int)floor(t) - g.P / 2 + 1;
-    else
-        i0 = (int)floor(t + 0.5) - (g.P - 1) / 2;
-    return i0;
+// clamped to [0, Mt - P].  Computed once, in the binning kernel, and stored
+// with the sorted point so that every later kernel uses the same support.
+template <typename T>
+__host__ __device__ inline int window_start(T rel, const GP<T> &g) {
+    T t = rel * g.inv_h + g.half_ext;
+    int i0 = ((g.P & 1) == 0) ? (int)floor(t) - g.P / 2 + 1 : (int)floor(t + T(0.5)) - (g.P - 1) / 2;
+    return min(max(i0, 0), g.Mt - g.P);
 }
+
+// Three indices < 1024 packed into the spare 4th component of a sorted point.
+__host__ __device__ inline int pack3(int a, int b, int c) { return a | (b << 10) | (c << 20); }
+__host__ __device__ inline void unpack3(int v, int &a, int &b, int &c) {
+    a = v & 1023;
+    b = (v >> 10) & 1023;
+    c = (v >> 20) & 1023;
+}
+__device__ inline void set_tag(float4 &v, int t) { v.w = __int_as_float(t); }
+__device__ inline void set_tag(double4_32a &v, int t) { v.w = __longlong_as_double((long long)t); }
+__device__ inline int get_tag(const float4 &v) { return __float_as_int(v.w); }
+__device__ inline int get_tag(const double4_32a &v) { return (int)__double_as_longlong(v.w); }
 
 // ---------------------------------------------------------------- the plan
 struct Buffers {
@@ -103,6 +125,8 @@ struct Buffers {
     int *cnt_r = nullptr;
     int *slot_r = nullptr;
     int *key_r = nullptr;
+    int *tag_t = nullptr;   // N packed window starts (original order)
+    int *tag_r = nullptr;   // N packed cell coordinates (original order)
     int *status = nullptr;  // device flags
 };
 
@@ -119,6 +143,8 @@ struct se_plan_s {
     int M = 0, P = 0, n_ext = 0, Mt = 0, Mf = 0, Mg = 0, deltaL_policy = 0, max_fft = 0;
     int nc = 3;  // spread components (3; stresslet 6)
     se::Geom geom{};
+    se::GP<float> gpf{};
+    se::GP<double> gpd{};
     int ntiles = 0, ncells = 0;
     bool tiled = true;  // tiled shared-memory spreading (else global atomics)
     // device memory
@@ -166,6 +192,9 @@ template <typename T>
 cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *gx);
 
 se_status_t precompute(se_plan_s *p);
+template <typename T> const GP<T> &gp(const se_plan_s *p);
+template <> inline const GP<float> &gp<float>(const se_plan_s *p) { return p->gpf; }
+template <> inline const GP<double> &gp<double>(const se_plan_s *p) { return p->gpd; }
 se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
                           double xi_arg, se_params_t *out);
 

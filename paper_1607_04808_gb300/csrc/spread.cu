@@ -1,104 +1,141 @@
 // Step 1 of Section 5.2 (spreading, eq. Hx): every source adds
 //   s_n * exp(-2 xi^2 |y_i - x_n|^2 / eta)
 // to the P^3 grid points of its support (the Gaussian's normalisation is
-// applied later, in the scaling step).
+// applied later, in the scaling step).  The Gaussian is separable, so each
+// point needs 3P exponentials (one 1-D weight vector per dimension).
 //
-// Tiled kernel: one CTA per spreading tile (T^3 window starts).  The CTA
-// accumulates the padded tile ((T+P-1)^3 points, all components) in shared
-// memory.  Warp w owns the padded z-planes z = w (mod 8), so warps never touch
-// the same word: no shared atomics and no barriers inside the point loop.  The
-// padded tile is then added to the zero-padded FFT input; neighbouring tiles
-// overlap in their halos, so that flush uses global atomics.
+// Tiled kernel: one CTA per spreading tile (T^3 window starts), 8 warps.  The
+// CTA accumulates the padded tile ((T+P-1)^3 points, all components) in shared
+// memory.  Points are taken 32 at a time: their weights, sources and support
+// offsets are staged in shared memory once per CTA, then every warp adds the
+// batch into the padded z-planes it owns (z = w mod 8), so no two warps ever
+// touch the same word and no shared atomics are needed.  The padded tile is
+// finally added to the zero-padded FFT input; neighbouring tiles overlap in
+// their halos, so that flush uses global atomics.
 //
-// Fallback kernel (large P in FP64, where a padded tile does not fit in shared
-// memory): one warp per point adding straight into the grid with atomics.
+// Fallback kernel (P > 16, or a padded tile that does not fit in shared
+// memory, e.g. the FP64 path at P >= 20): one warp per point adding straight
+// into the grid with global atomics.
 #include "se_internal.cuh"
 
 namespace se {
 
 namespace {
 
-constexpr int NW = 8;  // warps per CTA in the tiled kernel
-constexpr unsigned FULL = 0xffffffffu;
+constexpr int NW = 8;   // warps per CTA in the tiled kernel
+constexpr int NB = 32;  // points staged per batch
 
-__device__ __forceinline__ float gexp(float v) { return expf(v); }
+__device__ __forceinline__ float gexp(float v) { return __expf(v); }
 __device__ __forceinline__ double gexp(double v) { return exp(v); }
 
 // Source components that are spread: f (3) or the symmetric part of f q^T
 // (6: xx, yy, zz, xy, xz, yz), see the stresslet scaling.
 template <typename T>
-__device__ __forceinline__ void source_comps(int nc, const vec4<T> &f, const vec4<T> *qs, int n, T s[6]) {
-    if (nc == 3) {
-        s[0] = f.x; s[1] = f.y; s[2] = f.z;
-    } else {
-        vec4<T> q = qs[n];
-        s[0] = f.x * q.x;
-        s[1] = f.y * q.y;
-        s[2] = f.z * q.z;
-        s[3] = T(0.5) * (f.x * q.y + f.y * q.x);
-        s[4] = T(0.5) * (f.x * q.z + f.z * q.x);
-        s[5] = T(0.5) * (f.y * q.z + f.z * q.y);
+__device__ __forceinline__ T source_comp(int c, const vec4<T> &f) {
+    return c == 0 ? f.x : (c == 1 ? f.y : f.z);
+}
+template <typename T>
+__device__ __forceinline__ T stress_comp(int c, const vec4<T> &f, const vec4<T> &q) {
+    switch (c) {
+        case 0: return f.x * q.x;
+        case 1: return f.y * q.y;
+        case 2: return f.z * q.z;
+        case 3: return T(0.5) * (f.x * q.y + f.y * q.x);
+        case 4: return T(0.5) * (f.x * q.z + f.z * q.x);
+        default: return T(0.5) * (f.y * q.z + f.z * q.y);
     }
 }
 
-// 1-D Gaussian weights of the P points of the support along each dimension:
-// lane k < P holds w_d(k) = exp(-a h^2 (t_d - i0_d - k)^2).
+// 1-D weight of support point k along one dimension: exp(-a h^2 (t - i0 - k)^2)
 template <typename T>
-__device__ __forceinline__ void lane_weights(const vec4<T> &xv, const Geom &g, int lane, int i0[3], T w[3]) {
-    T ah2 = (T)(g.a * g.h * g.h);
-    double rel[3] = {clamp_rel((double)xv.x - g.x0[0], g.L), clamp_rel((double)xv.y - g.x0[1], g.L),
-                     clamp_rel((double)xv.z - g.x0[2], g.L)};
-    for (int d = 0; d < 3; d++) {
-        double t;
-        int s = window_start(rel[d], g, t);
-        s = min(max(s, 0), g.Mt - g.P);
-        i0[d] = s;
-        T fr = (T)(t - (double)s) - (T)lane;
-        w[d] = (lane < g.P) ? gexp(-ah2 * fr * fr) : T(0);
-    }
+__device__ __forceinline__ T weight(T rel, int i0, int k, const GP<T> &g) {
+    T fr = (rel * g.inv_h + g.half_ext) - (T)(i0 + k);
+    return gexp(-g.ah2 * fr * fr);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NW * 32) k_spread_tile(Geom g, int nc, const int *__restrict__ tile_start,
+template <typename T, int NIT>
+__global__ void __launch_bounds__(NW * 32) k_spread_tile(GP<T> g, int nc, const int *__restrict__ tile_start,
                                                          const vec4<T> *__restrict__ xs,
                                                          const vec4<T> *__restrict__ fs,
                                                          const vec4<T> *__restrict__ qs, T *__restrict__ grid) {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T sw[NB][3][32];
+    __shared__ T ssrc[NB][6];
+    __shared__ int soff[NB];
     T *sm = reinterpret_cast<T *>(smem_raw);
     const int tile = blockIdx.x;
     const int beg = tile_start[tile], end = tile_start[tile + 1];
     if (beg == end) return;
-    const int P = g.P, PT = g.T + g.P - 1, PT2 = PT * PT, PT3 = PT2 * PT;
+    const int P = g.P, PT = g.T_ + P - 1, PT2 = PT * PT, PT3 = PT2 * PT;
     const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
-    const int gx0 = tx * g.T, gy0 = ty * g.T, gz0 = tz * g.T;
-    for (int e = threadIdx.x; e < nc * PT3; e += blockDim.x) sm[e] = T(0);
-    __syncthreads();
+    const int gx0 = tx * g.T_, gy0 = ty * g.T_, gz0 = tz * g.T_;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int P2 = P * P;
-    for (int n = beg; n < end; n++) {
-        vec4<T> xv = xs[n];
-        int i0[3];
-        T w[3];
-        lane_weights<T>(xv, g, lane, i0, w);
-        T s[6];
-        source_comps<T>(nc, fs[n], qs, n, s);
-        // offsets of the support inside the padded tile (in [0, T) by construction of the bins)
-        const int ox = min(max(i0[0] - gx0, 0), g.T - 1), oy = min(max(i0[1] - gy0, 0), g.T - 1),
-                  oz = min(max(i0[2] - gz0, 0), g.T - 1);
-        int z = oz + (((warp - oz) % NW) + NW) % NW;
-        for (; z < oz + P; z += NW) {
-            T wz = __shfl_sync(FULL, w[2], z - oz);
-            T *plane = sm + z * PT2 + oy * PT + ox;
-            for (int base = 0; base < P2; base += 32) {
-                int idx = base + lane;
-                int ky = idx / P, kx = idx - ky * P;
-                T wx = __shfl_sync(FULL, w[0], kx);
-                T wy = __shfl_sync(FULL, w[1], min(ky, P - 1));
-                if (idx < P2) {
-                    T wt = wx * wy * wz;
-                    T *pp = plane + ky * PT + kx;
-                    for (int c = 0; c < nc; c++) pp[c * PT3] += s[c] * wt;
+    // this lane's (kx, ky) positions of the P x P support plane
+    int kxs[NIT], kys[NIT], offs[NIT];
+    bool val[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; it++) {
+        int idx = it * 32 + lane;
+        val[it] = idx < P * P;
+        kys[it] = val[it] ? idx / P : 0;
+        kxs[it] = val[it] ? idx - kys[it] * P : 0;
+        offs[it] = kys[it] * PT + kxs[it];
+    }
+    for (int e = threadIdx.x; e < nc * PT3; e += blockDim.x) sm[e] = T(0);
+    for (int b0 = beg; b0 < end; b0 += NB) {
+        const int nb = min(NB, end - b0);
+        __syncthreads();  // previous batch consumed (and the zeroing finished)
+        // stage the batch: warp w prepares points w, w + 8, ...
+        for (int j = warp; j < nb; j += NW) {
+            const int n = b0 + j;
+            const vec4<T> xv = xs[n];
+            int i0[3];
+            unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+            if (lane < P) {
+                sw[j][0][lane] = weight(xv.x - g.x0[0], i0[0], lane, g);
+                sw[j][1][lane] = weight(xv.y - g.x0[1], i0[1], lane, g);
+                sw[j][2][lane] = weight(xv.z - g.x0[2], i0[2], lane, g);
+            }
+            if (lane < nc) {
+                const vec4<T> fv = fs[n];
+                ssrc[j][lane] = (nc == 6) ? stress_comp<T>(lane, fv, qs[n]) : source_comp<T>(lane, fv);
+            }
+            if (lane == 0) {
+                int ox = min(max(i0[0] - gx0, 0), g.T_ - 1), oy = min(max(i0[1] - gy0, 0), g.T_ - 1),
+                    oz = min(max(i0[2] - gz0, 0), g.T_ - 1);
+                soff[j] = pack3(ox, oy, oz);
+            }
+        }
+        __syncthreads();
+        for (int j = 0; j < nb; j++) {
+            int ox, oy, oz;
+            unpack3(soff[j], ox, oy, oz);
+            T wxy[NIT];
+#pragma unroll
+            for (int it = 0; it < NIT; it++) wxy[it] = sw[j][0][kxs[it]] * sw[j][1][kys[it]];
+            T s[6];
+#pragma unroll
+            for (int c = 0; c < 6; c++) s[c] = (c < nc) ? ssrc[j][c] : T(0);
+            int z = oz + (((warp - oz) % NW) + NW) % NW;
+            for (; z < oz + P; z += NW) {
+                const T wz = sw[j][2][z - oz];
+                T *plane = sm + z * PT2 + oy * PT + ox;
+#pragma unroll
+                for (int it = 0; it < NIT; it++) {
+                    if (val[it]) {
+                        const T wt = wxy[it] * wz;
+                        T *pp = plane + offs[it];
+                        pp[0] += s[0] * wt;
+                        pp[PT3] += s[1] * wt;
+                        pp[2 * PT3] += s[2] * wt;
+                        if (nc == 6) {
+                            pp[3 * PT3] += s[3] * wt;
+                            pp[4 * PT3] += s[4] * wt;
+                            pp[5 * PT3] += s[5] * wt;
+                        }
+                    }
                 }
+                __syncwarp();
             }
         }
     }
@@ -117,44 +154,59 @@ __global__ void __launch_bounds__(NW * 32) k_spread_tile(Geom g, int nc, const i
 }
 
 template <typename T>
-__global__ void k_spread_atomic(Geom g, int nc, int N, const vec4<T> *__restrict__ xs,
+__global__ void k_spread_atomic(GP<T> g, int nc, int N, const vec4<T> *__restrict__ xs,
                                 const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
                                 T *__restrict__ grid) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= N) return;
-    const int n = warp, P = g.P, P2 = P * P;
-    vec4<T> xv = xs[n];
+    __shared__ T sw_all[8][3][32];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * 8 + wib;
+    if (n >= N) return;
+    T(*sw)[32] = sw_all[wib];
+    const int P = g.P, P2 = P * P;
+    const vec4<T> xv = xs[n];
     int i0[3];
-    T w[3];
-    lane_weights<T>(xv, g, lane, i0, w);
+    unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+    if (lane < P) {
+        sw[0][lane] = weight(xv.x - g.x0[0], i0[0], lane, g);
+        sw[1][lane] = weight(xv.y - g.x0[1], i0[1], lane, g);
+        sw[2][lane] = weight(xv.z - g.x0[2], i0[2], lane, g);
+    }
+    __syncwarp();
+    const vec4<T> fv = fs[n];
     T s[6];
-    source_comps<T>(nc, fs[n], qs, n, s);
-    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
-    for (int base = 0; base < P2; base += 32) {
-        int idx = base + lane;
+    for (int c = 0; c < nc; c++) s[c] = (nc == 6) ? stress_comp<T>(c, fv, qs[n]) : source_comp<T>(c, fv);
+    const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+    for (int idx = lane; idx < P2; idx += 32) {
         int ky = idx / P, kx = idx - ky * P;
-        T wx = __shfl_sync(FULL, w[0], kx);
-        T wy = __shfl_sync(FULL, w[1], min(ky, P - 1));
+        const T wxy = sw[0][kx] * sw[1][ky];
+        const size_t base = ((size_t)i0[2] * Mf + (i0[1] + ky)) * Mf + (i0[0] + kx);
         for (int kz = 0; kz < P; kz++) {
-            T wz = __shfl_sync(FULL, w[2], kz);
-            if (idx < P2) {
-                T wt = wx * wy * wz;
-                size_t gi = ((size_t)(i0[2] + kz) * g.Mf + (i0[1] + ky)) * g.Mf + (i0[0] + kx);
-                for (int c = 0; c < nc; c++) atomicAdd(grid + c * Mf3 + gi, s[c] * wt);
-            }
+            const T wt = wxy * sw[2][kz];
+            for (int c = 0; c < nc; c++) atomicAdd(grid + c * Mf3 + base + kz * Mf2, s[c] * wt);
         }
     }
 }
 
 template <typename T>
 __global__ void k_zero_octant(T *__restrict__ grid, int Mt, int Mf, int nc) {
-    // one thread per (c, z, y) row of Mt values
+    // one warp-row per (c, z, y) row of Mt values
     size_t row = (size_t)blockIdx.x * blockDim.y + threadIdx.y;
     size_t nrows = (size_t)nc * Mt * Mt;
     if (row >= nrows) return;
     int y = row % Mt, z = (row / Mt) % Mt, c = row / ((size_t)Mt * Mt);
     T *p = grid + (size_t)c * Mf * Mf * Mf + ((size_t)z * Mf + y) * Mf;
     for (int x = threadIdx.x; x < Mt; x += blockDim.x) p[x] = T(0);
+}
+
+template <typename T, int NIT>
+cudaError_t launch_tile(se_plan_s *p, cudaStream_t st, size_t smem, int nc, const void *xs, const void *fs,
+                        const void *qs, void *grid) {
+    cudaError_t e = cudaFuncSetAttribute(k_spread_tile<T, NIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e) return e;
+    k_spread_tile<T, NIT><<<p->ntiles, NW * 32, smem, st>>>(gp<T>(p), nc, p->b.cnt_t, (const vec4<T> *)xs,
+                                                            (const vec4<T> *)fs, (const vec4<T> *)qs, (T *)grid);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -173,25 +225,29 @@ cudaError_t launch_zero_octant(se_plan_s *p, cudaStream_t st, void *grid, int nc
     return cudaGetLastError();
 }
 
-// nc_mode: number of spread components (3, or 6 for the stresslet source f q^T)
+// nc: number of spread components (3, or 6 for the stresslet source f q^T)
 template <typename T>
 cudaError_t launch_spread(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
                           void *grid, int nc) {
     cudaError_t e;
     if ((e = launch_zero_octant<T>(p, st, grid, nc))) return e;
     size_t smem = spread_smem_bytes(p, nc, sizeof(T));
-    if (p->tiled && smem <= 200 * 1024) {
-        if ((e = cudaFuncSetAttribute(k_spread_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-            return e;
-        k_spread_tile<T><<<p->ntiles, NW * 32, smem, st>>>(p->geom, nc, p->b.cnt_t, (const vec4<T> *)xs,
-                                                          (const vec4<T> *)fs, (const vec4<T> *)qs, (T *)grid);
-    } else {
-        int N = (int)p->N;
-        int wpb = 8;
-        k_spread_atomic<T><<<(N + wpb - 1) / wpb, wpb * 32, 0, st>>>(p->geom, nc, N, (const vec4<T> *)xs,
-                                                                    (const vec4<T> *)fs, (const vec4<T> *)qs,
-                                                                    (T *)grid);
+    const int nit = (p->P * p->P + 31) / 32;
+    if (p->tiled && p->P <= 16 && smem <= 190 * 1024) {
+        switch (nit) {
+            case 1: return launch_tile<T, 1>(p, st, smem, nc, xs, fs, qs, grid);
+            case 2: return launch_tile<T, 2>(p, st, smem, nc, xs, fs, qs, grid);
+            case 3: return launch_tile<T, 3>(p, st, smem, nc, xs, fs, qs, grid);
+            case 4: return launch_tile<T, 4>(p, st, smem, nc, xs, fs, qs, grid);
+            case 5: return launch_tile<T, 5>(p, st, smem, nc, xs, fs, qs, grid);
+            case 6: return launch_tile<T, 6>(p, st, smem, nc, xs, fs, qs, grid);
+            case 7: return launch_tile<T, 7>(p, st, smem, nc, xs, fs, qs, grid);
+            default: return launch_tile<T, 8>(p, st, smem, nc, xs, fs, qs, grid);
+        }
     }
+    int N = (int)p->N;
+    k_spread_atomic<T><<<(N + 7) / 8, 256, 0, st>>>(gp<T>(p), nc, N, (const vec4<T> *)xs, (const vec4<T> *)fs,
+                                                   (const vec4<T> *)qs, (T *)grid);
     return cudaGetLastError();
 }
 
