@@ -23,12 +23,13 @@ __global__ void k_bin_count(int N, const T *__restrict__ x, GP<T> g, int *__rest
         if (!(rel >= T(0) && rel < g.L)) oob = true;
         rel = clamp_rel(rel, g.L);
         i0[d] = window_start(rel, g);
-        cc[d] = min(max((int)(rel * g.inv_cw), 0), g.ncd - 1);
+        cc[d] = (d == 0) ? min(max((int)(rel * g.inv_cwx), 0), g.ncdx - 1)
+                         : min(max((int)(rel * g.inv_cw), 0), g.ncd - 1);
     }
     if (oob) atomicOr(status, FLAG_OOB);
     int kt = (min(i0[2] / g.T_, g.ntd - 1) * g.ntd + min(i0[1] / g.T_, g.ntd - 1)) * g.ntd +
              min(i0[0] / g.T_, g.ntd - 1);
-    int kr = (cc[2] * g.ncd + cc[1]) * g.ncd + cc[0];
+    int kr = (cc[2] * g.ncd + cc[1]) * g.ncdx + cc[0];
     key_t[i] = kt;
     key_r[i] = kr;
     tag_t[i] = pack3(i0[0], i0[1], i0[2]);
@@ -106,6 +107,81 @@ cudaError_t launch_bin(se_plan_s *p, const T *x, const T *f, const T *q, cudaStr
     k_bin_scatter<T><<<gs, bs, 0, st>>>(N, x, f, q, b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r, b.tag_t,
                                         b.tag_r, (vec4<T> *)b.xs_t, (vec4<T> *)b.fs_t, (vec4<T> *)b.qs_t, b.perm_t,
                                         (vec4<T> *)b.xs_r, (vec4<T> *)b.fs_r, (vec4<T> *)b.qs_r, b.perm_r);
+    return cudaGetLastError();
+}
+
+// Three-pass exclusive scan for long arrays: per-block sums of contiguous
+// tiles, a scan of the block sums, then each block scans its tile from its
+// offset (block-wide scan in shared memory, coalesced loads and stores).
+constexpr int SCAN_TILE = 4096;
+
+__global__ void k_scan_tile_sums(const int *__restrict__ cnt, int n, int *__restrict__ sums) {
+    __shared__ int red[32];
+    const int b = blockIdx.x, lo = b * SCAN_TILE, hi = min(n, lo + SCAN_TILE);
+    int s = 0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) s += cnt[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sums[b] = v;
+    }
+}
+
+__global__ void k_scan_tiles(int *cnt, int n, const int *__restrict__ offs) {
+    __shared__ int wsum[32];
+    const int b = blockIdx.x, lo = b * SCAN_TILE;
+    const int per = SCAN_TILE / blockDim.x;  // contiguous elements per thread
+    const int i0 = lo + threadIdx.x * per;
+    int v[SCAN_TILE / 1024 > 0 ? SCAN_TILE / 1024 : 1];
+    int s = 0;
+    for (int k = 0; k < per; k++) {
+        const int i = i0 + k;
+        v[k] = (i < n) ? cnt[i] : 0;
+        s += v[k];
+    }
+    // block-wide exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = (lane < (blockDim.x >> 5)) ? wsum[lane] : 0;
+        int xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        wsum[lane] = xi - x;
+    }
+    __syncthreads();
+    int run = offs[b] + wsum[w] + incl - s;
+    for (int k = 0; k < per; k++) {
+        const int i = i0 + k;
+        if (i < n) cnt[i] = run;
+        run += v[k];
+    }
+    if (i0 <= n - 1 && n - 1 < i0 + per) cnt[n] = run;  // the owner of the last element writes the total
+}
+
+cudaError_t launch_scan(int *cnt, int n, cudaStream_t st) {
+    if (n <= 64 * 1024) {
+        k_scan_exclusive<<<1, 1024, 0, st>>>(cnt, n);
+        return cudaGetLastError();
+    }
+    // the tile sums live past the end of the array's total slot: callers
+    // allocate n + 1 + ceil(n / SCAN_TILE) + 1 ints
+    const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int *sums = cnt + n + 1;
+    k_scan_tile_sums<<<nb, 1024, 0, st>>>(cnt, n, sums);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(sums, nb);
+    k_scan_tiles<<<nb, 1024, 0, st>>>(cnt, n, sums);
     return cudaGetLastError();
 }
 

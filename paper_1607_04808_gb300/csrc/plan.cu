@@ -174,7 +174,7 @@ static void free_plan(se_plan_s *p) {
     if (p->have_fwd) cufftDestroy(p->fwd);
     if (p->have_inv) cufftDestroy(p->inv);
     if (p->have_fwd3) cufftDestroy(p->fwd3);
-    void *ptrs[] = {p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
+    void *ptrs[] = {p->rq_a, p->rq_b, p->b.ncl, p->b.clusters, p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
                     p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
                     p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
                     p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du};
@@ -261,13 +261,29 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     g.T = (T > 0) ? T : 8;
     g.ntd = (p->Mt - p->P + 1 + g.T - 1) / g.T;
     p->ntiles = g.ntd * g.ntd * g.ntd;
-    // real-space cells of width >= rc/3 (at most 200 per dimension)
-    int ncd = (int)floor(3.0 * p->L / p->rc);
+    // real-space cells: width >= rc/5 (FP32) or rc/3 (FP64) across rows (y, z;
+    // at most 200) and >= rc/16 along the rows (x; at most 1000), so that
+    // trimming each row to the cutoff sphere wastes little
+#ifndef SE_RS_YZDIV32
+#define SE_RS_YZDIV32 5.0
+#endif
+#ifndef SE_RS_XDIV
+#define SE_RS_XDIV 16.0
+#endif
+    // FP32 (clustered evaluation): rc/5 across rows; FP64 (per-target rows): rc/3
+    const double yzdiv = (prec == SE_FP32) ? SE_RS_YZDIV32 : 3.0;
+    int ncd = (int)floor(yzdiv * p->L / p->rc);
     ncd = std::max(1, std::min(ncd, 200));
+    int ncdx = (int)floor(SE_RS_XDIV * p->L / p->rc);
+    ncdx = std::max(1, std::min(ncdx, 1000));
+    if ((long)ncd * ncd * ncdx > (1L << 26)) ncdx = std::max(1L, (1L << 26) / ((long)ncd * ncd));
     g.ncd = ncd;
     g.cw = p->L / ncd;
     g.inv_cw = ncd / p->L;
-    p->ncells = ncd * ncd * ncd;
+    g.ncdx = ncdx;
+    g.cwx = p->L / ncdx;
+    g.inv_cwx = ncdx / p->L;
+    p->ncells = ncd * ncd * ncdx;
     if (p->Mt > 1023) {
         free_plan(p);
         return fail(SE_ERR_INVALID_ARG, "extended grid above 1023 points per dimension");
@@ -282,6 +298,9 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
         G.ah2 = (TT)(g.a * p->h * p->h);
         G.inv_cw = (TT)g.inv_cw;
         G.cw = (TT)g.cw;
+        G.inv_cwx = (TT)g.inv_cwx;
+        G.cwx = (TT)g.cwx;
+        G.ncdx = g.ncdx;
         G.P = p->P;
         G.Mt = p->Mt;
         G.Mf = p->Mf;
@@ -312,7 +331,9 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
         if ((e = dmalloc(&p->b.perm_t, Nn * 4))) break;
         if ((e = dmalloc(&p->b.slot_t, Nn * 4))) break;
         if ((e = dmalloc(&p->b.key_t, Nn * 4))) break;
-        if ((e = dmalloc(&p->b.cnt_t, (tile_keys + 1) * 4))) break;
+        // counting-sort arrays carry room for the scan's tile sums (see launch_scan)
+        auto scan_len = [](size_t n) { return n + 2 + (n + 4095) / 4096 + 1; };
+        if ((e = dmalloc(&p->b.cnt_t, scan_len(tile_keys) * 4))) break;
         if ((e = dmalloc(&p->b.xs_r, Nn * v4))) break;
         if ((e = dmalloc(&p->b.fs_r, Nn * v4))) break;
         if ((e = dmalloc(&p->b.qs_r, (kernel == SE_STRESSLET ? Nn : 1) * v4))) break;
@@ -321,7 +342,12 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
         if ((e = dmalloc(&p->b.key_r, Nn * 4))) break;
         if ((e = dmalloc(&p->b.tag_t, Nn * 4))) break;
         if ((e = dmalloc(&p->b.tag_r, Nn * 4))) break;
-        if ((e = dmalloc(&p->b.cnt_r, ((size_t)p->ncells + 1) * 4))) break;
+        {
+            const size_t nrows = (size_t)p->geom.ncd * p->geom.ncd;
+            if ((e = dmalloc(&p->b.ncl, scan_len(nrows) * 4))) break;
+            if ((e = dmalloc(&p->b.clusters, (Nn / 4 + nrows + 1) * sizeof(int2)))) break;
+        }
+        if ((e = dmalloc(&p->b.cnt_r, scan_len(p->ncells) * 4))) break;
         if ((e = dmalloc(&p->b.status, 16))) break;
         if ((e = cudaMemset(p->grid, 0, (size_t)p->nc * Mf3 * esz))) break;
         if ((e = cudaMemset(p->b.status, 0, 16))) break;
@@ -358,6 +384,7 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     }
     for (int i = 0; i < 9; i++) cudaEventCreate(&p->ev[i]);
     s = precompute(p);
+    if (s == SE_OK) s = build_real_table(p);
     if (s != SE_OK) {
         free_plan(p);
         return s;

@@ -1,23 +1,32 @@
 // Real-space part (Section 6): u^R(x_m) = sum_{0 < |x_m - x_n| <= rc} K^R(x_m - x_n) . f_n
-// with the screened kernels of Section 3.2:
-//   S^R     = (erfc(xi r)/r - c e) delta + (erfc(xi r)/r + c e) r^ r^            (eq. SR_Op)
-//   T^R     = A1 r^ r^ r^ + A2 (delta r^ + ...),  A1 = -(2/r)[3 erfc/r + c(3 + 2 xi^2 r^2) e],
-//             A2 = (4 xi^3 r / sqrt(pi)) e                                        (eq. TR_Op; A2 with
-//             the factor r that the third derivative of r - Phi^H gives)
-//   Omega^R = eps_jlm r^_m (erfc/r^2 + c e / r)                                   (eq. RR_Op / 2)
-// c = 2 xi / sqrt(pi), e = exp(-xi^2 r^2).  In FP32, erfc(x) = e Q(2/(2+x)) with
-// the fitted polynomial Q ~ erfcx of erfc_poly.cuh, so one exponential serves
-// both terms; FP64 uses the library erfc.
+// with the screened kernels of Section 3.2 (x = xi r, e = exp(-x^2), c = 2 xi/sqrt(pi)):
+//   S^R     = A delta + B r r^T,  A r = erfc(x) - (2/sqrt(pi)) x e,  B r^3 = erfc(x) + (2/sqrt(pi)) x e
+//             (eq. SR_Op)
+//   T^R     = A1 r^ r^ r^ + A2 (delta r^ + ...),  A1 r^2 = -2 [3 erfc(x) + (2/sqrt(pi)) x (3 + 2 x^2) e],
+//             A2 = xi^2 (4/sqrt(pi)) x e   (eq. TR_Op; A2 with the factor r that the third
+//             derivative of r - Phi^H gives)
+//   Omega^R = eps_jlm r_m B                                                (eq. RR_Op / 2)
+// Each kernel needs two smooth functions of x only (T1 = A r or A1 r^2, T2 = B r^3
+// or A2/xi^2).  FP32 evaluates erfc(x) = e Q(2/(2+x)) with the fitted erfcx
+// polynomial Q of erfc_poly.cuh, sharing the exponential; FP64 uses erfc and exp.
 //
-// Cell list: points are sorted by cell (cells of width >= rc/3, x fastest), so
-// one row of cells along x is a contiguous range.  One warp per target: lanes
-// first compute, for each (y, z) row of cells within reach, the x-range of cells
-// that can hold points within rc of this target (trimmed by the target's own
-// distance to the row), then stream those candidates 32 at a time.  Candidates
-// inside the cutoff are compacted (ballot + popc) into a per-warp queue, and each
-// full queue of 32 pairs is evaluated with every lane busy.  FP32 partial sums are
-// folded into Kahan-compensated totals after each row of cells; the final
-// cross-lane sum and the update of u (which already holds u^F + u^self) are FP64.
+// Cell list: points are sorted by cell (cells of width >= rc/3 across rows and
+// >= rc/8 along x, x fastest), so each (y, z) row of cells is a contiguous
+// range of sorted points.  Forward sum: every row is cut into clusters of 8
+// consecutive targets (a cluster never crosses a row, so it spans a few cells
+// along x and one across); one warp per cluster, lane = (target, candidate
+// stream).  The candidates of every row of cells within reach, trimmed along x
+// to the cutoff sphere around the cluster's cells, are staged 32 at a time in
+// shared memory and each of the 4 streams takes every 4th one: every lane tests
+// and evaluates its own (target, candidate) pairs, with no compaction.  FP32
+// partial sums are folded into Kahan-compensated totals after each row; the
+// streams are combined with a compensated shuffle sum and u (which already holds
+// u^F + u^self) is updated in FP64.  The backward kernel keeps one warp per
+// target with ballot compaction of the candidates.
+#include <math.h>
+
+#include <vector>
+
 #include "erfc_poly.cuh"
 #include "se_internal.cuh"
 
@@ -25,61 +34,152 @@ namespace se {
 
 namespace {
 
+// Build-time layout of the FP32 clustered kernel: radial functions from the
+// quadratic table (1) or the fitted erfcx polynomial (0); persistent blocks
+// sweeping contiguous cluster ranges (1) or one cluster per warp (0).
+#ifndef SE_RS_QTAB
+#define SE_RS_QTAB 0
+#endif
+#ifndef SE_RS_PERSIST
+#define SE_RS_PERSIST 0
+#endif
+
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int WPB = 8;
 constexpr int QCAP = 64;
-constexpr int MAXROWS = 49;  // reach <= 3 cells
+constexpr int MAXROWS = 121;  // reach <= 5 cells across rows
 
 template <typename T>
 struct RC {
     T xi, xi2, c, c3, rc2;  // xi, xi^2, 2 xi/sqrt(pi), 4 xi^3/sqrt(pi), rc^2
-    int reach;
+    T tab_scale;            // xi / (table interval width in x)
+    int reach;              // rows of cells within reach on each side (y, z)
 };
 
-// rsqrt, exp(-xi^2 r^2) and erfc(xi r) of one pair
-__device__ __forceinline__ void radial(const RC<float> &rk, float r2, float &rinv, float &r, float &e, float &ec) {
+// The two radial functions at r: erfc(x) = exp(-x^2) Q(2/(2+x)) with the
+// fitted erfcx polynomial Q
+template <int KERNEL>
+__device__ __forceinline__ void radial2(const RC<float> &rk, float r2, float &rinv, float &t1, float &t2) {
     rinv = rsqrtf(r2);
-    r = r2 * rinv;
-    e = __expf(-rk.xi2 * r2);
-    const float x = rk.xi * r;
+    const float x = rk.xi * r2 * rinv;
+    const float e = __expf(-rk.xi2 * r2);
     const float t = __fdividef(2.0f, 2.0f + x);
     float q = ERFC_Q[SE_ERFC_DEG];
 #pragma unroll
     for (int k = SE_ERFC_DEG - 1; k >= 0; k--) q = fmaf(q, t, ERFC_Q[k]);
-    ec = e * q;
+    const float ec = e * q;
+    const float g = 1.12837917f * x * e;  // (2/sqrt(pi)) x e
+    if (KERNEL == SE_STRESSLET) {
+        t1 = -2.0f * (3.0f * ec + g * (3.0f + 2.0f * x * x));
+        t2 = 2.0f * g;
+    } else {
+        t1 = ec - g;
+        t2 = ec + g;
+    }
 }
-__device__ __forceinline__ void radial(const RC<double> &rk, double r2, double &rinv, double &r, double &e,
-                                       double &ec) {
+
+// FP64: the same two functions from erfc and exp
+template <int KERNEL>
+__device__ __forceinline__ void radial2(const RC<double> &rk, double r2, double &rinv, double &t1, double &t2) {
     rinv = rsqrt(r2);
-    r = r2 * rinv;
-    e = exp(-rk.xi2 * r2);
-    ec = erfc(rk.xi * r);
+    const double x = rk.xi * r2 * rinv;
+    const double e = exp(-x * x);
+    const double ec = erfc(x);
+    const double g = 1.1283791670955126 * x * e;  // (2/sqrt(pi)) x e
+    if (KERNEL == SE_STRESSLET) {
+        t1 = -2.0 * (3.0 * ec + g * (3.0 + 2.0 * x * x));
+        t2 = 2.0 * g;
+    } else {
+        t1 = ec - g;
+        t2 = ec + g;
+    }
 }
 
 // K^R(d) . source, added to acc (d = x_target - x_source, r2 = |d|^2 > 0)
 template <typename T, int KERNEL>
-__device__ __forceinline__ void pair(const RC<T> &rk, T dx, T dy, T dz, T r2, const vec4<T> &f,
-                                     const vec4<T> &q, T acc[3]) {
-    T rinv, r, e, ec;
-    radial(rk, r2, rinv, r, e, ec);
-    const T ce = rk.c * e;
-    const T ecr = ec * rinv;
+__device__ __forceinline__ void pair(const RC<T> &rk, T dx, T dy, T dz, T r2, const vec4<T> &f, const vec4<T> &q,
+                                     T acc[3]) {
+    T rinv, t1, t2;
+    radial2<KERNEL>(rk, r2, rinv, t1, t2);
+    const T rinv2 = rinv * rinv;
     if (KERNEL == SE_STOKESLET) {
-        const T A = ecr - ce;
-        const T B = (ecr + ce) * rinv * rinv;
-        const T Brf = B * (dx * f.x + dy * f.y + dz * f.z);
+        const T A = t1 * rinv;
+        const T Brf = t2 * rinv2 * rinv * (dx * f.x + dy * f.y + dz * f.z);
         acc[0] += A * f.x + Brf * dx;
         acc[1] += A * f.y + Brf * dy;
         acc[2] += A * f.z + Brf * dz;
     } else if (KERNEL == SE_ROTLET) {
-        const T B = (ecr + ce) * rinv * rinv;
+        const T B = t2 * rinv2 * rinv;
         acc[0] += B * (f.y * dz - f.z * dy);
         acc[1] += B * (f.z * dx - f.x * dz);
         acc[2] += B * (f.x * dy - f.y * dx);
     } else {
         const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
-        const T A1 = -T(2) * rinv * (T(3) * ecr + rk.c * (T(3) + T(2) * rk.xi2 * r2) * e);
-        const T A2 = rk.c3 * r * e;
+        const T A1 = t1 * rinv2;
+        const T A2 = rk.xi2 * t2;
+        const T hf = hx * f.x + hy * f.y + hz * f.z;
+        const T hq = hx * q.x + hy * q.y + hz * q.z;
+        const T fq = f.x * q.x + f.y * q.y + f.z * q.z;
+        const T a1 = A1 * hf * hq;
+        acc[0] += a1 * hx + A2 * (hx * fq + f.x * hq + q.x * hf);
+        acc[1] += a1 * hy + A2 * (hy * fq + f.y * hq + q.y * hf);
+        acc[2] += a1 * hz + A2 * (hz * fq + f.z * hq + q.z * hf);
+    }
+}
+
+// FP32 quadratic table of the two radial functions of x = xi r (see the
+// header): interval j of RQ_N on [0, xi rc (1 + 1e-3)] holds c0 + c1 u + c2 u^2,
+// u in [0, 1), for both functions: a = (c0_1, c0_2, c1_1, c1_2), b = (c2_1, c2_2).
+constexpr int RQ_N = 1024;
+struct QTab {
+    const float4 *a;
+    const float2 *b;
+};
+
+template <int KERNEL>
+__device__ __forceinline__ void radial2_tab(const RC<float> &rk, const QTab &qt, float r2, float &rinv, float &t1,
+                                            float &t2) {
+    if (!SE_RS_QTAB) {
+        radial2<KERNEL>(rk, r2, rinv, t1, t2);
+        return;
+    }
+    rinv = rsqrtf(r2);
+    const float sx = r2 * rinv * rk.tab_scale;
+    // floor without a conversion unit: round (s - 1/2) in the mantissa of 1.5 * 2^23
+    const float v = (sx - 0.5f) + 12582912.0f;
+    const int j = min(__float_as_int(v) - 0x4B400000, RQ_N - 1);
+    const float u = sx - (v - 12582912.0f);
+    const float4 a = qt.a[j];
+    const float2 b = qt.b[j];
+    t1 = fmaf(u, fmaf(u, b.x, a.z), a.x);
+    t2 = fmaf(u, fmaf(u, b.y, a.w), a.y);
+}
+template <int KERNEL>
+__device__ __forceinline__ void radial2_tab(const RC<double> &rk, const QTab &, double r2, double &rinv, double &t1,
+                                            double &t2) {
+    radial2<KERNEL>(rk, r2, rinv, t1, t2);
+}
+
+template <typename T, int KERNEL>
+__device__ __forceinline__ void pair_tab(const RC<T> &rk, const QTab &qt, T dx, T dy, T dz, T r2, const vec4<T> &f,
+                                         const vec4<T> &q, T acc[3]) {
+    T rinv, t1, t2;
+    radial2_tab<KERNEL>(rk, qt, r2, rinv, t1, t2);
+    const T rinv2 = rinv * rinv;
+    if (KERNEL == SE_STOKESLET) {
+        const T A = t1 * rinv;
+        const T Brf = t2 * rinv2 * rinv * (dx * f.x + dy * f.y + dz * f.z);
+        acc[0] += A * f.x + Brf * dx;
+        acc[1] += A * f.y + Brf * dy;
+        acc[2] += A * f.z + Brf * dz;
+    } else if (KERNEL == SE_ROTLET) {
+        const T B = t2 * rinv2 * rinv;
+        acc[0] += B * (f.y * dz - f.z * dy);
+        acc[1] += B * (f.z * dx - f.x * dz);
+        acc[2] += B * (f.x * dy - f.y * dx);
+    } else {
+        const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
+        const T A1 = t1 * rinv2;
+        const T A2 = rk.xi2 * t2;
         const T hf = hx * f.x + hy * f.y + hz * f.z;
         const T hq = hx * q.x + hy * q.y + hz * q.z;
         const T fq = f.x * q.x + f.y * q.y + f.z * q.z;
@@ -103,8 +203,8 @@ __device__ __forceinline__ void kahan_add(T &s, T &comp, T x) {
 // half-chord of the cutoff sphere at the row's distance.  A small relative
 // margin keeps rounding from dropping a cell; the exact test comes later.
 template <typename T>
-__device__ __forceinline__ void row_segments(const GP<T> &g, const RC<T> &rk, const vec4<T> &xt,
-                                             const int *__restrict__ cell_start, int lane, int2 *seg) {
+__device__ __forceinline__ int row_segments(const GP<T> &g, const RC<T> &rk, const vec4<T> &xt,
+                                            const int *__restrict__ cell_start, int lane, int2 *seg) {
     int cc[3];
     unpack3(get_tag(xt), cc[0], cc[1], cc[2]);
     const T rel[3] = {xt.x - g.x0[0], xt.y - g.x0[1], xt.z - g.x0[2]};
@@ -119,11 +219,11 @@ __device__ __forceinline__ void row_segments(const GP<T> &g, const RC<T> &rk, co
             const T dz = max(T(0), max(zlo - rel[2], rel[2] - (zlo + g.cw)));
             const T d2 = dy * dy + dz * dz;
             if (d2 <= rc2m) {
-                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cw;
-                const int ixl = max(0, (int)floor((rel[0] - del) * g.inv_cw));
-                const int ixh = min(g.ncd - 1, (int)floor((rel[0] + del) * g.inv_cw));
+                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cwx;
+                const int ixl = max(0, (int)floor((rel[0] - del) * g.inv_cwx));
+                const int ixh = min(g.ncdx - 1, (int)floor((rel[0] + del) * g.inv_cwx));
                 if (ixl <= ixh) {
-                    const int base = (iz * g.ncd + iy) * g.ncd;
+                    const int base = (iz * g.ncd + iy) * g.ncdx;
                     sg = make_int2(cell_start[base + ixl], cell_start[base + ixh + 1]);
                 }
             }
@@ -131,15 +231,192 @@ __device__ __forceinline__ void row_segments(const GP<T> &g, const RC<T> &rk, co
         seg[r] = sg;
     }
     __syncwarp();
+    return nrows;
 }
 
+// Clusters: each (y, z) row of cells is a contiguous range of sorted points;
+// it is cut into clusters of at most TPW consecutive points (never crossing a
+// row), so a cluster is compact (at most a few cells along x, one cell across).
+__global__ void k_cluster_count(int nrows, int ncdx, int tpw, const int *__restrict__ cell_start, int *ncl) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int len = cell_start[(r + 1) * ncdx] - cell_start[r * ncdx];
+    ncl[r] = (len + tpw - 1) / tpw;
+}
+
+__global__ void k_cluster_fill(int nrows, int ncdx, int tpw, const int *__restrict__ cell_start,
+                               const int *__restrict__ ncl_start, int2 *__restrict__ cl) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int a = cell_start[r * ncdx], b = cell_start[(r + 1) * ncdx];
+    int o = ncl_start[r];
+    for (int s = a; s < b; s += tpw) cl[o++] = make_int2(s, min(tpw, b - s));
+}
+
+// One warp per cluster: lane = (target k = lane % TPW, candidate stream
+// s = lane / TPW).  Candidates of every row within reach are loaded 32 at a
+// time into shared memory and stream s takes every NS-th of them, so each lane
+// tests and evaluates (target k, candidate) pairs without any compaction.
+template <typename T, int KERNEL, int TPW>
+__global__ void __launch_bounds__(256) k_real_cl(GP<T> g, RC<T> rk, const vec4<T> *__restrict__ xs,
+                                                 const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
+                                                 const int *__restrict__ cell_start,
+                                                 const int2 *__restrict__ clusters, const int *__restrict__ ncl_total,
+                                                 const int *__restrict__ perm, const float4 *__restrict__ qa_g,
+                                                 const float2 *__restrict__ qb_g, T *__restrict__ u,
+                                                 int *__restrict__ status) {
+    constexpr int WPB = 8, NS = 32 / TPW;
+    __shared__ vec4<T> sx_all[WPB][32];
+    __shared__ vec4<T> sf_all[WPB][32];
+    __shared__ vec4<T> sq_all[KERNEL == SE_STRESSLET ? WPB : 1][32];
+    __shared__ int2 seg_all[WPB][MAXROWS];
+    __shared__ int pre_all[WPB][MAXROWS + 1];
+    __shared__ float4 qa_s[SE_RS_QTAB ? RQ_N : 1];
+    __shared__ float2 qb_s[SE_RS_QTAB ? RQ_N : 1];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (sizeof(T) == 4 && SE_RS_QTAB) {
+        for (int i = threadIdx.x; i < RQ_N; i += blockDim.x) {
+            qa_s[i] = qa_g[i];
+            qb_s[i] = qb_g[i];
+        }
+        __syncthreads();
+    }
+    const QTab qt{qa_s, qb_s};
+    const int ntot = *ncl_total;
+    vec4<T> *sx = sx_all[wib];
+    vec4<T> *sf = sf_all[wib];
+    vec4<T> *sq = sq_all[KERNEL == SE_STRESSLET ? wib : 0];
+    int2 *seg = seg_all[wib];
+    // each block sweeps a contiguous range of clusters (neighbours in space, so
+    // the candidate loads of its warps share the L1 cache)
+    const int per_blk = SE_RS_PERSIST ? (ntot + gridDim.x - 1) / gridDim.x : WPB;
+    const int c_end = min(ntot, (blockIdx.x + 1) * per_blk);
+    for (int c = blockIdx.x * per_blk + wib; c < c_end; c += WPB) {
+    const int2 cl = clusters[c];
+    const int k = lane % TPW, s = lane / TPW;
+    const bool has = k < cl.y;
+    const int t = cl.x + min(k, cl.y - 1);
+    const vec4<T> xt = xs[t];
+    // rows of cells within reach of the cluster's cells
+    int c0[3], c1[3];
+    unpack3(get_tag(xs[cl.x]), c0[0], c0[1], c0[2]);
+    unpack3(get_tag(xs[cl.x + cl.y - 1]), c1[0], c1[1], c1[2]);
+    const int R = rk.reach, W = 2 * R + 1, nrows = W * W;
+    const T rc2m = rk.rc2 * T(1.0001);
+    for (int r = lane; r < nrows; r += 32) {
+        const int dyc = (r % W) - R, dzc = (r / W) - R;
+        const int iy = c0[1] + dyc, iz = c0[2] + dzc;
+        int2 sg = make_int2(0, 0);
+        if (iy >= 0 && iy < g.ncd && iz >= 0 && iz < g.ncd) {
+            const T dy = T(max(abs(dyc) - 1, 0)) * g.cw, dz = T(max(abs(dzc) - 1, 0)) * g.cw;
+            const T d2 = dy * dy + dz * dz;
+            if (d2 <= rc2m) {
+                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cwx;
+                const int ixl = max(0, (int)floor((T(c0[0]) * g.cwx - del) * g.inv_cwx));
+                const int ixh = min(g.ncdx - 1, (int)floor((T(c1[0] + 1) * g.cwx + del) * g.inv_cwx));
+                if (ixl <= ixh) {
+                    const int base = (iz * g.ncd + iy) * g.ncdx;
+                    sg = make_int2(cell_start[base + ixl], cell_start[base + ixh + 1]);
+                }
+            }
+        }
+        seg[r] = sg;
+    }
+    __syncwarp();
+    // flat candidate stream over all row segments: exclusive prefix of the
+    // segment lengths (warp scan), then each lane finds its segment by bisection
+    int *pre = pre_all[wib];
+    int run = 0;
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+        const int r = r0 + lane;
+        int len = (r < nrows) ? seg[r].y - seg[r].x : 0;
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (r < nrows) pre[r] = run + incl - len;
+        run += __shfl_sync(FULL, incl, 31);
+    }
+    if (lane == 0) pre[nrows] = run;
+    __syncwarp();
+    const int total = run;
+    T acc[3] = {0, 0, 0}, ks[3] = {0, 0, 0}, kc[3] = {0, 0, 0};
+    int zeros = 0;  // candidates at distance 0 seen by this lane (its own target included once)
+    vec4<T> zero4;
+    zero4.x = zero4.y = zero4.z = zero4.w = 0;
+    for (int cb = 0; cb < total; cb += 32) {
+        const int v = cb + lane;
+        if (v < total) {
+            int lo = 0, hi = nrows;  // pre[lo] <= v < pre[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pre[mid] <= v) lo = mid; else hi = mid;
+            }
+            const int m = seg[lo].x + (v - pre[lo]);
+            vec4<T> xv = xs[m];
+            xv.w = T(0);
+            sx[lane] = xv;
+            sf[lane] = fs[m];
+            if (KERNEL == SE_STRESSLET) sq[lane] = qs[m];
+        }
+        __syncwarp();
+        const int nch = min(32, total - cb);
+        auto step = [&](int j) {
+            const vec4<T> xv = sx[j];
+            const T dx = xt.x - xv.x, dy = xt.y - xv.y, dz = xt.z - xv.z;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            // the target itself (and any coincident point) has r2 = 0
+            zeros += (r2 == T(0)) ? 1 : 0;
+            if (has && r2 > T(0) && r2 <= rk.rc2) {
+                const vec4<T> qv = (KERNEL == SE_STRESSLET) ? sq[j] : zero4;
+                pair_tab<T, KERNEL>(rk, qt, dx, dy, dz, r2, sf[j], qv, acc);
+            }
+        };
+        if (nch == 32) {
+#pragma unroll
+            for (int i = 0; i < 32 / NS; i++) step(s + i * NS);
+        } else {
+            for (int j = s; j < nch; j += NS) step(j);
+        }
+        __syncwarp();
+        for (int d = 0; d < 3; d++) {
+            kahan_add(ks[d], kc[d], acc[d]);
+            acc[d] = 0;
+        }
+    }
+    // combine the NS streams of each target (lanes k, k + TPW, ...)
+    T tot[3];
+    for (int d = 0; d < 3; d++) {
+        T sm_ = ks[d], cm_ = kc[d];
+        for (int o = TPW; o < 32; o <<= 1) {
+            const T so = __shfl_xor_sync(FULL, sm_, o), co = __shfl_xor_sync(FULL, cm_, o);
+            kahan_add(sm_, cm_, so);  // sm_ - cm_ now holds the own and the partner's sums
+            cm_ += co;                // minus the partner's compensation
+        }
+        tot[d] = sm_ - cm_;
+    }
+    for (int o = TPW; o < 32; o <<= 1) zeros += __shfl_xor_sync(FULL, zeros, o);
+    if (__any_sync(FULL, has && zeros > 1) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
+    if (s == 0 && has) {
+        const int mi = perm[t];
+        for (int d = 0; d < 3; d++) u[3 * mi + d] = (T)((double)u[3 * mi + d] + (double)tot[d]);
+    }
+    __syncwarp();
+    }
+}
+
+// One warp per target with ballot compaction of the candidates (the FP64 path,
+// where evaluating a pair costs far more than testing one): lanes stream the
+// candidates of the target's rows 32 at a time, those inside the cutoff are
+// appended to a per-warp queue, and every full queue of 32 pairs is evaluated
+// with all lanes busy.
 template <typename T, int KERNEL>
-__global__ void __launch_bounds__(WPB * 32) k_real(GP<T> g, RC<T> rk, int N, const vec4<T> *__restrict__ xs,
-                                                   const vec4<T> *__restrict__ fs,
-                                                   const vec4<T> *__restrict__ qs,
-                                                   const int *__restrict__ cell_start,
-                                                   const int *__restrict__ perm, T *__restrict__ u,
-                                                   int *__restrict__ status) {
+__global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, const vec4<T> *__restrict__ xs,
+                                                  const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
+                                                  const int *__restrict__ cell_start, const int *__restrict__ perm,
+                                                  T *__restrict__ u, int *__restrict__ status) {
+    constexpr int WPB = 8;
     __shared__ vec4<T> qd_all[WPB][QCAP];
     __shared__ int qn_all[WPB][QCAP];
     __shared__ int2 seg_all[WPB][MAXROWS];
@@ -150,14 +427,19 @@ __global__ void __launch_bounds__(WPB * 32) k_real(GP<T> g, RC<T> rk, int N, con
     int *qn = qn_all[wib];
     int2 *seg = seg_all[wib];
     const vec4<T> xt = xs[t];
-    row_segments(g, rk, xt, cell_start, lane, seg);
-    const int W = 2 * rk.reach + 1, nrows = W * W;
-    T acc[3] = {0, 0, 0}, ks[3] = {0, 0, 0}, kc[3] = {0, 0, 0};
+    const int nrows = row_segments(g, rk, xt, cell_start, lane, seg);
+    T acc[3] = {0, 0, 0};
     int cnt = 0;
     bool coinc = false;
     const unsigned lt = (1u << lane) - 1u;
     vec4<T> zero4;
     zero4.x = zero4.y = zero4.z = zero4.w = 0;
+    auto eval = [&](int slot) {
+        const vec4<T> v = qd[slot];
+        const int m = qn[slot];
+        const vec4<T> qv = (KERNEL == SE_STRESSLET) ? qs[m] : zero4;
+        pair<T, KERNEL>(rk, v.x, v.y, v.z, v.w, fs[m], qv, acc);
+    };
     for (int r = 0; r < nrows; r++) {
         const int2 sg = seg[r];
         for (int base = sg.x; base < sg.y; base += 32) {
@@ -187,10 +469,7 @@ __global__ void __launch_bounds__(WPB * 32) k_real(GP<T> g, RC<T> rk, int N, con
             cnt += __popc(mask);
             __syncwarp();
             if (cnt >= 32) {
-                const vec4<T> v = qd[lane];
-                const int m = qn[lane];
-                const vec4<T> qv = (KERNEL == SE_STRESSLET) ? qs[m] : zero4;
-                pair<T, KERNEL>(rk, v.x, v.y, v.z, v.w, fs[m], qv, acc);
+                eval(lane);
                 __syncwarp();
                 if (lane < cnt - 32) {
                     qd[lane] = qd[32 + lane];
@@ -200,35 +479,19 @@ __global__ void __launch_bounds__(WPB * 32) k_real(GP<T> g, RC<T> rk, int N, con
                 __syncwarp();
             }
         }
-        for (int d = 0; d < 3; d++) {
-            kahan_add(ks[d], kc[d], acc[d]);
-            acc[d] = 0;
-        }
     }
-    if (lane < cnt) {
-        const vec4<T> v = qd[lane];
-        const int m = qn[lane];
-        const vec4<T> qv = (KERNEL == SE_STRESSLET) ? qs[m] : zero4;
-        pair<T, KERNEL>(rk, v.x, v.y, v.z, v.w, fs[m], qv, acc);
-    }
-    T tot[3];
+    if (lane < cnt) eval(lane);
+    double tot[3];
     for (int d = 0; d < 3; d++) {
-        kahan_add(ks[d], kc[d], acc[d]);
-        // tree sum of the compensated lane totals
-        T s = ks[d], c = kc[d];
-        for (int o = 16; o > 0; o >>= 1) {
-            const T so = __shfl_xor_sync(FULL, s, o), co = __shfl_xor_sync(FULL, c, o);
-            kahan_add(s, c, so);  // s - c now holds s_self + s_partner - c_self
-            c += co;              // minus the partner's compensation
-        }
-        tot[d] = s - c;
+        double v = (double)acc[d];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        tot[d] = v;
     }
     if (__any_sync(FULL, coinc) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
     if (lane < 3) {
-        // lanes 0..2 each finish one component in FP64
         const int m = perm[t];
-        const T v = lane == 0 ? tot[0] : (lane == 1 ? tot[1] : tot[2]);
-        u[3 * m + lane] = (T)((double)u[3 * m + lane] + (double)v);
+        const double v = lane == 0 ? tot[0] : (lane == 1 ? tot[1] : tot[2]);
+        u[3 * m + lane] = (T)((double)u[3 * m + lane] + v);
     }
 }
 
@@ -243,12 +506,20 @@ __global__ void __launch_bounds__(WPB * 32) k_real(GP<T> g, RC<T> rk, int N, con
 // a' = -c1 e/r - erfc/r^2 + 2 c1 xi^2 r e,  b' = -3 c1 e/r^3 - 3 erfc/r^4 - 2 c1 xi^2 e/r.
 // Same cell traversal and compaction as the forward kernel; g of a source is
 // read through the permutation.
+__device__ __forceinline__ float s_erfc(float v) { return erfcf(v); }
+__device__ __forceinline__ double s_erfc(double v) { return erfc(v); }
+__device__ __forceinline__ float s_exp(float v) { return expf(v); }
+__device__ __forceinline__ double s_exp(double v) { return exp(v); }
+__device__ __forceinline__ float s_rsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double s_rsqrt(double v) { return rsqrt(v); }
+
 template <typename T, int KERNEL>
-__global__ void __launch_bounds__(WPB * 32) k_real_grad(GP<T> g, RC<T> rk, int N, const vec4<T> *__restrict__ xs,
-                                                        const vec4<T> *__restrict__ fs,
-                                                        const int *__restrict__ cell_start,
-                                                        const int *__restrict__ perm, const T *__restrict__ g_orig,
-                                                        T *__restrict__ gx) {
+__global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, const vec4<T> *__restrict__ xs,
+                                                   const vec4<T> *__restrict__ fs,
+                                                   const int *__restrict__ cell_start,
+                                                   const int *__restrict__ perm, const T *__restrict__ g_orig,
+                                                   T *__restrict__ gx) {
+    constexpr int WPB = 8;
     __shared__ vec4<T> qd_all[WPB][QCAP];
     __shared__ int qn_all[WPB][QCAP];
     __shared__ int2 seg_all[WPB][MAXROWS];
@@ -262,8 +533,7 @@ __global__ void __launch_bounds__(WPB * 32) k_real_grad(GP<T> g, RC<T> rk, int N
     const vec4<T> fp = fs[t];
     const int mp = perm[t];
     const T gp_[3] = {g_orig[3 * mp], g_orig[3 * mp + 1], g_orig[3 * mp + 2]};
-    row_segments(g, rk, xt, cell_start, lane, seg);
-    const int W = 2 * rk.reach + 1, nrows = W * W;
+    const int nrows = row_segments(g, rk, xt, cell_start, lane, seg);
     T acc[3] = {0, 0, 0};
     int cnt = 0;
     const unsigned lt = (1u << lane) - 1u;
@@ -274,8 +544,10 @@ __global__ void __launch_bounds__(WPB * 32) k_real_grad(GP<T> g, RC<T> rk, int N
         const int mn = perm[n];
         const T gn[3] = {g_orig[3 * mn], g_orig[3 * mn + 1], g_orig[3 * mn + 2]};
         const T d[3] = {v.x, v.y, v.z};
-        T rinv, r, e, ec;
-        radial(rk, v.w, rinv, r, e, ec);
+        const T rinv = s_rsqrt(v.w);
+        const T r = v.w * rinv;
+        const T e = s_exp(-rk.xi2 * v.w);
+        const T ec = s_erfc(rk.xi * r);
         const T c1 = rk.c;
         const T ecr = ec * rinv;
         const T rinv2 = rinv * rinv;
@@ -357,46 +629,107 @@ RC<T> make_rc(const se_plan_s *p) {
     rk.c = (T)(2.0 * p->xi / sqrt(M_PI));
     rk.c3 = (T)(4.0 * p->xi * p->xi * p->xi / sqrt(M_PI));
     rk.rc2 = (T)(p->rc * p->rc);
+    rk.tab_scale = (T)(p->xi * RQ_N / (p->xi * p->rc * (1.0 + 1e-3)));
     rk.reach = (int)ceil(p->rc * p->geom.inv_cw - 1e-9);
     return rk;
 }
 
-}  // namespace
+#ifndef SE_RS_TPW
+#define SE_RS_TPW 16
+#endif
 
-template <typename T>
-cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u) {
-    int N = (int)p->N;
-    RC<T> rk = make_rc<T>(p);
-    if (rk.reach > 3) return cudaErrorInvalidValue;
-    unsigned gs = (N + WPB - 1) / WPB;
+template <typename T, int KERNEL>
+cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) {
+    const int N = (int)p->N;
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r,
                   *qs = (const vec4<T> *)p->b.qs_r;
     const GP<T> &g = gp<T>(p);
-    if (p->kernel == SE_STOKESLET)
-        k_real<T, SE_STOKESLET><<<gs, WPB * 32, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, u,
-                                                       p->b.status);
-    else if (p->kernel == SE_STRESSLET)
-        k_real<T, SE_STRESSLET><<<gs, WPB * 32, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, u,
-                                                       p->b.status);
-    else
-        k_real<T, SE_ROTLET><<<gs, WPB * 32, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, u,
-                                                    p->b.status);
+    if (sizeof(T) == 8) {
+        k_real_cmp<T, KERNEL><<<(N + 7) / 8, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, u,
+                                                           p->b.status);
+        return cudaGetLastError();
+    }
+    constexpr int TPW = SE_RS_TPW;
+    const int nrows = p->geom.ncd * p->geom.ncd;
+    k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, TPW, p->b.cnt_r, p->b.ncl);
+    launch_scan(p->b.ncl, nrows, st);
+    k_cluster_fill<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, TPW, p->b.cnt_r, p->b.ncl,
+                                                         p->b.clusters);
+    const long max_cl = N / TPW + nrows + 1;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long nblk = SE_RS_PERSIST ? std::min<long>((max_cl + 7) / 8, 4L * nsm) : (max_cl + 7) / 8;
+    k_real_cl<T, KERNEL, TPW><<<(unsigned)nblk, 256, 0, st>>>(g, rk, xs, fs, qs, p->b.cnt_r, p->b.clusters,
+                                                              p->b.ncl + nrows, p->b.perm_r, p->rq_a, p->rq_b, u,
+                                                              p->b.status);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+// Host construction of the FP32 quadratic table (FP64 arithmetic): on each
+// interval the quadratic through the values at u = 0, 1/2, 1.
+se_status_t build_real_table(se_plan_s *p) {
+    const double xmax = p->xi * p->rc * (1.0 + 1e-3);
+    const double hx = xmax / RQ_N;
+    auto fns = [&](double x, double &t1, double &t2) {
+        const double e = exp(-x * x), ec = erfc(x), gg = 2.0 / sqrt(M_PI) * x * e;
+        if (p->kernel == SE_STRESSLET) {
+            t1 = -2.0 * (3.0 * ec + gg * (3.0 + 2.0 * x * x));
+            t2 = 2.0 * gg;
+        } else {
+            t1 = ec - gg;
+            t2 = ec + gg;
+        }
+    };
+    std::vector<float4> a(RQ_N);
+    std::vector<float2> b(RQ_N);
+    for (int j = 0; j < RQ_N; j++) {
+        double f0[2], fm[2], f1[2];
+        fns(j * hx, f0[0], f0[1]);
+        fns((j + 0.5) * hx, fm[0], fm[1]);
+        fns((j + 1) * hx, f1[0], f1[1]);
+        double c1[2], c2[2];
+        for (int k = 0; k < 2; k++) {
+            c2[k] = 2.0 * (f1[k] - 2.0 * fm[k] + f0[k]);
+            c1[k] = f1[k] - f0[k] - c2[k];
+        }
+        a[j] = make_float4((float)f0[0], (float)f0[1], (float)c1[0], (float)c1[1]);
+        b[j] = make_float2((float)c2[0], (float)c2[1]);
+    }
+    if (!p->rq_a && (cudaMalloc(&p->rq_a, RQ_N * sizeof(float4)) != cudaSuccess ||
+                     cudaMalloc(&p->rq_b, RQ_N * sizeof(float2)) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(SE_ERR_OOM, "real-space table allocation failed");
+    }
+    if (cudaMemcpy(p->rq_a, a.data(), RQ_N * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->rq_b, b.data(), RQ_N * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(SE_ERR_CUDA, "real-space table upload failed");
+    return SE_OK;
+}
+
+template <typename T>
+cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u) {
+    RC<T> rk = make_rc<T>(p);
+    if (rk.reach > 5) return cudaErrorInvalidValue;
+    if (p->kernel == SE_STOKESLET) return launch_real_k<T, SE_STOKESLET>(p, st, rk, u);
+    if (p->kernel == SE_STRESSLET) return launch_real_k<T, SE_STRESSLET>(p, st, rk, u);
+    return launch_real_k<T, SE_ROTLET>(p, st, rk, u);
 }
 
 template <typename T>
 cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *gx) {
     int N = (int)p->N;
     RC<T> rk = make_rc<T>(p);
-    if (rk.reach > 3) return cudaErrorInvalidValue;
-    unsigned gs = (N + WPB - 1) / WPB;
+    if (rk.reach > 5) return cudaErrorInvalidValue;
+    unsigned gs = (N + 7) / 8;
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r;
     const GP<T> &g = gp<T>(p);
     if (p->kernel == SE_STOKESLET)
-        k_real_grad<T, SE_STOKESLET><<<gs, WPB * 32, 0, st>>>(g, rk, N, xs, fs, p->b.cnt_r, p->b.perm_r, g_orig,
-                                                            gx);
+        k_real_grad<T, SE_STOKESLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
     else if (p->kernel == SE_ROTLET)
-        k_real_grad<T, SE_ROTLET><<<gs, WPB * 32, 0, st>>>(g, rk, N, xs, fs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
+        k_real_grad<T, SE_ROTLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -58,8 +58,10 @@ struct Geom {
     int ntd;           // tiles per dimension
     double a;          // Gaussian exponent 2 xi^2 / eta (per unit length^2)
     // real-space cells
-    int ncd;           // cells per dimension
-    double cw, inv_cw; // cell width and inverse
+    int ncd;           // cells per dimension across rows (y, z)
+    double cw, inv_cw; // cell width and inverse (y, z)
+    int ncdx;          // cells along x (rows are split finer along x)
+    double cwx, inv_cwx;
     double rc;         // cutoff
     double xi;
 };
@@ -71,8 +73,9 @@ struct GP {
     T x0[3], L;        // box corner and side
     T inv_h, half_ext; // t = (x - x0) / h + n_ext / 2 = (x - y0) / h (grid units)
     T ah2;             // a h^2 = 2 xi^2 h^2 / eta: Gaussian exponent per grid unit^2
-    T inv_cw, cw;      // real-space cell width
-    int P, Mt, Mf, T_, ntd, ncd;
+    T inv_cw, cw;      // real-space cell width across rows (y, z)
+    T inv_cwx, cwx;    // real-space cell width along x (the row direction)
+    int P, Mt, Mf, T_, ntd, ncd, ncdx;
 };
 
 // Coordinate relative to the box corner, clamped into [0, L) for points outside
@@ -127,6 +130,8 @@ struct Buffers {
     int *key_r = nullptr;
     int *tag_t = nullptr;   // N packed window starts (original order)
     int *tag_r = nullptr;   // N packed cell coordinates (original order)
+    int *ncl = nullptr;     // clusters per row of cells, then their exclusive scan (+ total)
+    int2 *clusters = nullptr;  // (first sorted index, count) of each real-space cluster
     int *status = nullptr;  // device flags
 };
 
@@ -148,6 +153,8 @@ struct se_plan_s {
     int ntiles = 0, ncells = 0;
     bool tiled = true;  // tiled shared-memory spreading (else global atomics)
     // device memory
+    float4 *rq_a = nullptr;    // FP32 real-space quadratic table (see realspace.cu)
+    float2 *rq_b = nullptr;
     double *ghat64 = nullptr;  // (Mt+1)^3 octant of the precomputed kernel, FP64
     void *ghat = nullptr;      // same in the plan precision
     void *grid = nullptr;      // nc x Mf^3 real, zero padded (R2C input)
@@ -192,6 +199,8 @@ template <typename T>
 cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *gx);
 
 se_status_t precompute(se_plan_s *p);
+cudaError_t launch_scan(int *cnt, int n, cudaStream_t st);
+se_status_t build_real_table(se_plan_s *p);  // exclusive scan, cnt[n] = total
 template <typename T> const GP<T> &gp(const se_plan_s *p);
 template <> inline const GP<float> &gp<float>(const se_plan_s *p) { return p->gpf; }
 template <> inline const GP<double> &gp<double>(const se_plan_s *p) { return p->gpd; }
