@@ -29,11 +29,14 @@ N_POINTS = 1_000_000
 BOX = (0.0, 0.0, 0.0, 1.0)
 METRIC = "Mpoints/s, free-space stokeslet SE N=1e6: FP32 @2e-6 vs FP64 @1e-10; % HBM"
 WORKLOAD = "stokeslet sum, N=1e6 uniform iid in [0,1)^3, f iid N(0,1)^3; FP32 path rel. err 2e-6 (P=12, FFT <= 256^3) beside FP64 path rel. err 1e-10"
-OUR_KERNELS_PER_EVAL = 9  # bin count, 2 scans, bin scatter, zero octant, spread, scale, gather, real space
 # FP32 flops of one screened stokeslet pair (see the design notes): difference 3,
 # |r|^2 5, rsqrt 1, r 1, xi r 1, -xi^2 r^2 1, exp 2, erfc 20, c e 1, A 2, B 3,
 # r.f 5, B (r.f) 1, u += A f + B (r.f) r 12.
 FLOP_PER_PAIR = 58
+# DRAM bytes (read + write) of one launch of the FP32 stokeslet real-space kernel on
+# this workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
+# Set to None whenever that kernel changes, until it is captured again.
+REAL_TRAFFIC_BYTES = 50_572_544 + 1_910_784
 
 
 def pair_fraction_unit_cube(r: float) -> float:
@@ -65,7 +68,7 @@ class ClockSampler:
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -106,9 +109,11 @@ def cpu_baseline(x, f, budget_s=12.0):
     from oracle import direct
     rng = np.random.default_rng(123)
     t0 = time.perf_counter()
-    direct.direct("stokeslet", x, f, targets=rng.choice(len(x), 16, replace=False))
-    rate = 16 / max(time.perf_counter() - t0, 1e-6)
-    nt = int(max(16, min(len(x), rate * budget_s)))
+    # calibrate on enough targets to keep every host core busy
+    ncal = 16 * (os.cpu_count() or 1)
+    direct.direct("stokeslet", x, f, targets=rng.choice(len(x), ncal, replace=False))
+    rate = ncal / max(time.perf_counter() - t0, 1e-6)
+    nt = int(max(ncal, min(len(x), rate * budget_s)))
     idx = rng.choice(len(x), nt, replace=False)
     t0 = time.perf_counter()
     direct.direct("stokeslet", x, f, targets=idx)
@@ -126,9 +131,10 @@ def run_reference(args, rank, world):
     from oracle import direct
     rng = np.random.default_rng(7)
     t0 = time.perf_counter()
-    direct.direct("stokeslet", x, f, targets=rng.choice(N_POINTS, 8, replace=False))
-    rate = 8 / max(time.perf_counter() - t0, 1e-6)
-    per_step = int(max(8, min(N_POINTS, rate * 8.0)))  # about 8 s of CPU work per step
+    ncal = 16 * (os.cpu_count() or 1)
+    direct.direct("stokeslet", x, f, targets=rng.choice(N_POINTS, ncal, replace=False))
+    rate = ncal / max(time.perf_counter() - t0, 1e-6)
+    per_step = int(max(ncal, min(N_POINTS, rate * 8.0)))  # about 8 s of CPU work per step
     times = []
     for s in range(args.warmup + args.steps):
         idx = rng.choice(N_POINTS, per_step, replace=False)
@@ -192,6 +198,7 @@ def run_ours(args, rank, world, dist):
                 stage_acc.setdefault(name, []).append(v)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+    launches_per_eval = plan.launch_count()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = float(np.mean(step_ms))
     if dist:
@@ -276,8 +283,8 @@ def run_ours(args, rank, world, dist):
                    "parallelism": f"replicas x{world}", "wall_s_timed_region": t_wall},
         "stages_ms": stages,
         "stage_algorithmic_gbs": stage_gbs,
-        "roofline": {"bound": "alu", "kernel": "k_real (real-space pair sum)", "achieved": achieved,
-                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": "k_real_cl (real-space pair sum)", "achieved": achieved,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": REAL_TRAFFIC_BYTES,
                      "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                      "pairs_per_launch": pairs, "flop_per_pair": FLOP_PER_PAIR},
         "hbm_peak_gbs": hbm,
@@ -285,7 +292,8 @@ def run_ours(args, rank, world, dist):
         "cpu_baseline": cpu,
         "e2e": {"value": N_POINTS / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 2 * N_POINTS * 3 * 4, "d2h_bytes_per_step": N_POINTS * 3 * 4},
-        "gpu_launches": OUR_KERNELS_PER_EVAL * args.steps,
+        "gpu_launches": launches_per_eval * args.steps,
+        "gpu_launches_note": "kernels of libse.so per step (host-side count); cuFFT adds 2 transforms per step",
         "clocks": clocks,
     }
     print(json.dumps(line))

@@ -112,6 +112,13 @@ se_status_t se_eval_host(se_plan_t plan, const void *x_host, const void *f_host,
 se_status_t se_eval_backward(se_plan_t plan, const void *x, const void *f, const void *q,
                              const void *grad_u, void *grad_f, void *grad_x, void *stream);
 
+/* The screened real-space part alone (Section 6): u^R(x_m) = sum over
+ * 0 < |x_m - x_n| <= rc of K^R(x_m - x_n) . f_n with the split kernels of
+ * Section 3.2 and the plan's xi and rc (no Fourier part, no self term).
+ * Same argument conventions as se_eval; u is overwritten.  Uses the plan's
+ * cell-list workspaces.  Asynchronous on `stream`. */
+se_status_t se_eval_real_space(se_plan_t plan, const void *x, const void *f, const void *q, void *u, void *stream);
+
 /* Parameter selection without a device (host only; the same rules as
  * se_plan_create, Section 8.2 with Tables 2 and 3): fills M, P, xi and rc of
  * *out from the overrides in *in (may be NULL), the box side L, N, tol and
@@ -128,9 +135,17 @@ se_status_t se_plan_check(se_plan_t plan);
 
 /* Per-stage device times of the plan's last se_eval, in milliseconds, when
  * stage timing was enabled with se_plan_set_timing(plan, 1).  Order:
- * bin, spread, fft, scale, ifft, gather, real.  Returns the number written. */
+ * bin, spread, fft, scale, ifft, gather, real_setup (the real-space cluster
+ * list; 0 in FP64), real (the real-space pair-sum kernel alone).  Returns the
+ * number written (8, or 0 before the first timed se_eval). */
 int se_plan_stage_times(se_plan_t plan, float *ms, int max_n);
 se_status_t se_plan_set_timing(se_plan_t plan, int on);
+
+/* Number of this library's kernels launched by the plan's last se_eval,
+ * se_eval_host, se_eval_real_space or se_eval_backward call (cuFFT's kernels
+ * and memsets are not counted; the count is taken on the host at launch).
+ * Returns -1 for a NULL plan. */
+int64_t se_plan_launch_count(se_plan_t plan);
 
 /* Destroy the plan and free its device memory (synchronises the device). */
 se_status_t se_plan_destroy(se_plan_t plan);

@@ -102,8 +102,9 @@ cudaError_t launch_bin(se_plan_s *p, const T *x, const T *f, const T *q, cudaStr
     int bs = 256, gs = (N + bs - 1) / bs;
     k_bin_count<T><<<gs, bs, 0, st>>>(N, x, gp<T>(p), b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r,
                                       b.tag_t, b.tag_r, b.status);
-    k_scan_exclusive<<<1, 1024, 0, st>>>(b.cnt_t, p->ntiles);
-    k_scan_exclusive<<<1, 1024, 0, st>>>(b.cnt_r, p->ncells);
+    if ((e = launch_scan(b.cnt_t, (int)p->ntiles, st))) return e;
+    if ((e = launch_scan(b.cnt_r, (int)p->ncells, st))) return e;
+    p->launches += 2 + scan_launch_count((int)p->ntiles) + scan_launch_count((int)p->ncells);
     k_bin_scatter<T><<<gs, bs, 0, st>>>(N, x, f, q, b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r, b.tag_t,
                                         b.tag_r, (vec4<T> *)b.xs_t, (vec4<T> *)b.fs_t, (vec4<T> *)b.qs_t, b.perm_t,
                                         (vec4<T> *)b.xs_r, (vec4<T> *)b.fs_r, (vec4<T> *)b.qs_r, b.perm_r);

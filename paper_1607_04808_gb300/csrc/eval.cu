@@ -38,11 +38,15 @@ struct StageTimer {
     void mark() {
         if (p->timing && k < 9) cudaEventRecord(p->ev[k++], st);
     }
+    // stages: bin, spread, fft, scale, ifft, gather, then the real-space sum
+    // split at ev_real into its set-up (cluster list) and its main kernel
     void finish() {
-        if (!p->timing) return;
+        if (!p->timing || k != 8) return;
         cudaEventSynchronize(p->ev[k - 1]);
-        p->n_stage = k - 1;
-        for (int i = 0; i + 1 < k; i++) cudaEventElapsedTime(&p->stage_ms[i], p->ev[i], p->ev[i + 1]);
+        for (int i = 0; i < 6; i++) cudaEventElapsedTime(&p->stage_ms[i], p->ev[i], p->ev[i + 1]);
+        cudaEventElapsedTime(&p->stage_ms[6], p->ev[6], p->ev_real);
+        cudaEventElapsedTime(&p->stage_ms[7], p->ev_real, p->ev[7]);
+        p->n_stage = 8;
     }
 };
 
@@ -80,6 +84,7 @@ se_status_t fourier_grid(se_plan_s *p, cudaStream_t st, void *wout, int nc, Stag
 template <typename T>
 se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaStream_t st) {
     p->last_stream = st;
+    p->launches = 0;
     StageTimer tm{p, st};
     tm.mark();
     CK(launch_bin<T>(p, x, f, q, st));
@@ -97,6 +102,7 @@ se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaS
 template <typename T>
 se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *gu, T *gf, T *gx, cudaStream_t st) {
     p->last_stream = st;
+    p->launches = 0;
     const size_t Mf3 = (size_t)p->Mf * p->Mf * p->Mf;
     if (!p->wgrid2) {
         cudaError_t e = cudaMalloc(&p->wgrid2, 3 * Mf3 * sizeof(T));
@@ -134,6 +140,25 @@ extern "C" se_status_t se_eval(se_plan_t p, const void *x, const void *f, const 
     if (p->prec == SE_FP32)
         return eval_t<float>(p, (const float *)x, (const float *)f, (const float *)q, (float *)u, st);
     return eval_t<double>(p, (const double *)x, (const double *)f, (const double *)q, (double *)u, st);
+}
+
+extern "C" se_status_t se_eval_real_space(se_plan_t p, const void *x, const void *f, const void *q, void *u,
+                                          void *stream) {
+    if (!p || !x || !f || !u) return fail(SE_ERR_INVALID_ARG, "se_eval_real_space: NULL pointer");
+    if (p->kernel == SE_STRESSLET && !q) return fail(SE_ERR_INVALID_ARG, "se_eval_real_space: the stresslet needs q");
+    cudaStream_t st = (cudaStream_t)stream;
+    p->last_stream = st;
+    p->launches = 0;
+    const size_t bytes = (size_t)p->N * 3 * (p->prec == SE_FP32 ? 4 : 8);
+    CK(cudaMemsetAsync(u, 0, bytes, st));
+    if (p->prec == SE_FP32) {
+        CK(launch_bin<float>(p, (const float *)x, (const float *)f, (const float *)q, st));
+        CK(launch_real<float>(p, st, (float *)u));
+    } else {
+        CK(launch_bin<double>(p, (const double *)x, (const double *)f, (const double *)q, st));
+        CK(launch_real<double>(p, st, (double *)u));
+    }
+    return SE_OK;
 }
 
 extern "C" se_status_t se_eval_host(se_plan_t p, const void *x, const void *f, const void *q, void *u,

@@ -172,6 +172,7 @@ cudaError_t launch_gather(se_plan_s *p, cudaStream_t st, const void *wgrid, cons
         case 8: k_gather<T, 8><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
         default: k_gather<T, 0><<<gs, bs, 0, st>>>(g, N, xs, p->b.perm_t, w, f_orig, self_coef, u); break;
     }
+    p->launches++;
     return cudaGetLastError();
 }
 
@@ -183,6 +184,7 @@ cudaError_t launch_gather_grad(se_plan_s *p, cudaStream_t st, const void *w_fwd,
     k_gather_grad<T><<<(N + WPB - 1) / WPB, WPB * 32, 0, st>>>(gp<T>(p), c_grad, N, (const vec4<T> *)p->b.xs_t,
                                                                p->b.perm_t, (const T *)w_fwd, (const T *)w_adj,
                                                                f_orig, g_orig, gx);
+    p->launches++;
     return cudaGetLastError();
 }
 

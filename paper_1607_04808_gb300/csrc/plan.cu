@@ -182,6 +182,7 @@ static void free_plan(se_plan_s *p) {
         if (q) cudaFree(q);
     for (int i = 0; i < 9; i++)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    if (p->ev_real) cudaEventDestroy(p->ev_real);
     delete p;
 }
 
@@ -229,7 +230,12 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     p->Mt = p->M + p->n_ext;
     p->Mf = 2 * p->Mt;
     p->R = sqrt(3.0) * p->Mt * p->h;
+    // precompute grid: the smallest even size above (1 + sqrt 3) Mt (Section 9),
+    // rounded up to a length with prime factors 2, 3, 5, 7 (a larger
+    // oversampling factor is still valid, Section 4.2, and avoids cuFFT's slow
+    // path for lengths with large prime factors)
     p->Mg = 2 * (int)floor((1.0 + sqrt(3.0)) * p->Mt / 2.0) + 2;
+    while (!good_fft(p->Mg, SE_FP64) || (p->Mg & 1)) p->Mg++;
     p->nc = (kernel == SE_STRESSLET) ? 6 : 3;
     if (p->max_fft > 0 && p->Mf > p->max_fft) {
         free_plan(p);
@@ -383,6 +389,7 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
         }
     }
     for (int i = 0; i < 9; i++) cudaEventCreate(&p->ev[i]);
+    cudaEventCreate(&p->ev_real);
     s = precompute(p);
     if (s == SE_OK) s = build_real_table(p);
     if (s != SE_OK) {
@@ -449,6 +456,8 @@ extern "C" int se_plan_stage_times(se_plan_t p, float *ms, int max_n) {
     for (int i = 0; i < n; i++) ms[i] = p->stage_ms[i];
     return n;
 }
+
+extern "C" int64_t se_plan_launch_count(se_plan_t p) { return p ? p->launches : -1; }
 
 extern "C" const char *se_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char *se_version(void) { return "se-gb300 0.1 (sm_103a)"; }

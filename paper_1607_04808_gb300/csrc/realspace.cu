@@ -645,8 +645,10 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
                   *qs = (const vec4<T> *)p->b.qs_r;
     const GP<T> &g = gp<T>(p);
     if (sizeof(T) == 8) {
+        if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
         k_real_cmp<T, KERNEL><<<(N + 7) / 8, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, u,
                                                            p->b.status);
+        p->launches++;
         return cudaGetLastError();
     }
     constexpr int TPW = SE_RS_TPW;
@@ -660,9 +662,11 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long nblk = SE_RS_PERSIST ? std::min<long>((max_cl + 7) / 8, 4L * nsm) : (max_cl + 7) / 8;
+    if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
     k_real_cl<T, KERNEL, TPW><<<(unsigned)nblk, 256, 0, st>>>(g, rk, xs, fs, qs, p->b.cnt_r, p->b.clusters,
                                                               p->b.ncl + nrows, p->b.perm_r, p->rq_a, p->rq_b, u,
                                                               p->b.status);
+    p->launches += 3 + scan_launch_count(nrows);
     return cudaGetLastError();
 }
 
@@ -732,6 +736,7 @@ cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *
         k_real_grad<T, SE_ROTLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
     else
         return cudaErrorInvalidValue;
+    p->launches++;
     return cudaGetLastError();
 }
 

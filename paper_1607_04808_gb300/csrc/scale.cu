@@ -131,6 +131,7 @@ cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpos
         k_scale<T, SE_STRESSLET><<<gs, bs, 0, st>>>(sc, gh, sp);
     else
         k_scale<T, SE_ROTLET><<<gs, bs, 0, st>>>(sc, gh, sp);
+    p->launches++;
     return cudaGetLastError();
 }
 

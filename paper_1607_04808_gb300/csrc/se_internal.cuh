@@ -169,8 +169,10 @@ struct se_plan_s {
     cudaStream_t last_stream = nullptr;
     bool timing = false;
     cudaEvent_t ev[9] = {};
+    cudaEvent_t ev_real = nullptr;  // recorded before the main real-space kernel when timing
     float stage_ms[8] = {};
     int n_stage = 0;
+    int64_t launches = 0;  // kernels of this library launched by the last evaluation call
     double precompute_ms = 0;
     // host staging for se_eval_host
     void *dx = nullptr, *df = nullptr, *dq = nullptr, *du = nullptr;
@@ -200,6 +202,8 @@ cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *
 
 se_status_t precompute(se_plan_s *p);
 cudaError_t launch_scan(int *cnt, int n, cudaStream_t st);
+// number of kernels launch_scan issues for an array of n counts
+inline int scan_launch_count(int n) { return n <= 64 * 1024 ? 1 : 3; }
 se_status_t build_real_table(se_plan_s *p);  // exclusive scan, cnt[n] = total
 template <typename T> const GP<T> &gp(const se_plan_s *p);
 template <> inline const GP<float> &gp<float>(const se_plan_s *p) { return p->gpf; }

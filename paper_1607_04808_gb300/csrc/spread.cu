@@ -206,6 +206,7 @@ cudaError_t launch_tile(se_plan_s *p, cudaStream_t st, size_t smem, int nc, cons
     if (e) return e;
     k_spread_tile<T, NIT><<<p->ntiles, NW * 32, smem, st>>>(gp<T>(p), nc, p->b.cnt_t, (const vec4<T> *)xs,
                                                             (const vec4<T> *)fs, (const vec4<T> *)qs, (T *)grid);
+    p->launches++;
     return cudaGetLastError();
 }
 
@@ -222,6 +223,7 @@ cudaError_t launch_zero_octant(se_plan_s *p, cudaStream_t st, void *grid, int nc
     size_t nrows = (size_t)nc * p->Mt * p->Mt;
     dim3 gs((unsigned)((nrows + bs.y - 1) / bs.y));
     k_zero_octant<T><<<gs, bs, 0, st>>>((T *)grid, p->Mt, p->Mf, nc);
+    p->launches++;
     return cudaGetLastError();
 }
 
@@ -248,6 +250,7 @@ cudaError_t launch_spread(se_plan_s *p, cudaStream_t st, const void *xs, const v
     int N = (int)p->N;
     k_spread_atomic<T><<<(N + 7) / 8, 256, 0, st>>>(gp<T>(p), nc, N, (const vec4<T> *)xs, (const vec4<T> *)fs,
                                                    (const vec4<T> *)qs, (T *)grid);
+    p->launches++;
     return cudaGetLastError();
 }
 

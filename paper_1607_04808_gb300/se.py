@@ -23,7 +23,7 @@ STATUS = {
     4: "SE_ERR_OOM", 5: "SE_ERR_CUDA", 6: "SE_ERR_CUFFT", 7: "SE_ERR_TIMEOUT",
     8: "SE_ERR_NOT_SUPPORTED",
 }
-STAGES = ["bin", "spread", "fft", "scale", "ifft", "gather", "real"]
+STAGES = ["bin", "spread", "fft", "scale", "ifft", "gather", "real_setup", "real"]
 
 
 class SEError(RuntimeError):
@@ -60,6 +60,8 @@ def lib():
                                          ctypes.POINTER(SEParams), ctypes.POINTER(vp)]
             L.se_eval.restype = i32
             L.se_eval.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.se_eval_real_space.restype = i32
+            L.se_eval_real_space.argtypes = [vp, vp, vp, vp, vp, vp]
             L.se_eval_host.restype = i32
             L.se_eval_host.argtypes = [vp, vp, vp, vp, vp, vp]
             L.se_eval_backward.restype = i32
@@ -75,6 +77,8 @@ def lib():
             L.se_plan_set_timing.argtypes = [vp, i32]
             L.se_plan_stage_times.restype = i32
             L.se_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
+            L.se_plan_launch_count.restype = i64
+            L.se_plan_launch_count.argtypes = [vp]
             L.se_plan_destroy.restype = i32
             L.se_plan_destroy.argtypes = [vp]
             L.se_last_error.restype = ctypes.c_char_p
@@ -147,6 +151,15 @@ class Plan:
             self.check()
         return out
 
+    def eval_real_space(self, x, f, q=None, out=None, stream=None):
+        """The screened real-space part u^R alone (se_eval_real_space)."""
+        x, f, q = self._arg(x, "x"), self._arg(f, "f"), self._arg(q, "q")
+        if out is None:
+            out = torch.empty_like(x)
+        self._arg(out, "out")
+        _check(lib().se_eval_real_space(self._h, _ptr(x), _ptr(f), _ptr(q), _ptr(out), _stream(stream)))
+        return out
+
     def eval_host(self, x: np.ndarray, f: np.ndarray, q: np.ndarray | None = None,
                   out: np.ndarray | None = None, stream=None) -> np.ndarray:
         """se_eval_host: host arrays in, host array out (copies inside the call)."""
@@ -193,6 +206,10 @@ class Plan:
         buf = (ctypes.c_float * 8)()
         n = lib().se_plan_stage_times(self._h, buf, 8)
         return {STAGES[i]: buf[i] for i in range(n)}
+
+    def launch_count(self) -> int:
+        """se_plan_launch_count: kernels of this library launched by the last call."""
+        return int(lib().se_plan_launch_count(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

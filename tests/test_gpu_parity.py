@@ -135,6 +135,27 @@ def test_explicit_parameters_and_strict_deltaL():
     assert rel_l2(u, o2) <= 5e-12
 
 
+@pytest.mark.parametrize("kernel", KN)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_real_space_part_vs_oracle(kernel, prec):
+    """se_eval_real_space against the oracle's brute-force screened sum (Section 6)."""
+    pkg = P()
+    x, f = W.stokeslet_uniform(4000, 13)
+    q = W.unit_vectors(4000, 13) if kernel == "stresslet" else None
+    if prec == "fp32":
+        x, f, q = as32(x), as32(f), as32(q)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    plan = pkg.Plan(kernel, 4000, BOX, prec=prec, tol=1e-10 if prec == "fp64" else 2e-6)
+    prm = plan.params
+    t = lambda a: None if a is None else torch.tensor(a, dtype=dt, device="cuda")  # noqa: E731
+    u = plan.eval_real_space(t(x), t(f), t(q)).double().cpu().numpy()
+    plan.check()
+    ref = ose.real_space(ose.KERNEL_IDS[kernel], x, f, q,
+                         ose.SEParams(L=1.0, M=prm["M"], P=prm["P"], xi=prm["xi"], rc=prm["rc"]))
+    assert rel_l2(u, ref) <= (1e-12 if prec == "fp64" else 1e-6)
+    plan.close()
+
+
 def test_eval_host_matches_device():
     pkg = P()
     x, f = W.stokeslet_uniform(2000, 8)
@@ -197,7 +218,8 @@ def test_stage_timing_reported():
     plan.eval(torch.tensor(x, dtype=torch.float32, device="cuda"),
               torch.tensor(f, dtype=torch.float32, device="cuda"))
     t = plan.stage_times()
-    assert set(t) == {"bin", "spread", "fft", "scale", "ifft", "gather", "real"}
+    assert set(t) == {"bin", "spread", "fft", "scale", "ifft", "gather", "real_setup", "real"}
+    assert plan.launch_count() >= 9
     assert all(v >= 0 for v in t.values())
     plan.close()
 
