@@ -119,6 +119,22 @@ se_status_t se_eval_backward(se_plan_t plan, const void *x, const void *f, const
  * cell-list workspaces.  Asynchronous on `stream`. */
 se_status_t se_eval_real_space(se_plan_t plan, const void *x, const void *f, const void *q, void *u, void *stream);
 
+/* The real-space sum of se_eval_real_space for callers that cannot allocate
+ * device memory (their host program's arena owns all of it, or they run in a
+ * loop that must never call the allocator).  No plan: the method parameters
+ * xi and rc and the box are passed directly; x, f (, q for the stresslet) and u
+ * are N x 3 device arrays of the precision `prec`, u is overwritten.  All
+ * temporaries live in one fixed-size __device__ array inside the library
+ * (about 9 MB, held on every GPU that loads the library until the process
+ * exits); nothing is allocated.  Limits: N <= 32768 and L / rc <= 25 (the cell
+ * list's size); larger requests return SE_ERR_INVALID_ARG.  The first call on a
+ * device looks up the array's address (make it before any stream capture).
+ * Calls whose GPU work overlaps race on the shared array.  Device-side flags
+ * (points outside the box, coincident points) are not reported.  The paper has
+ * no counterpart to this entry point.  Asynchronous on `stream`. */
+se_status_t se_real_space_noalloc(se_kernel_t kernel, se_prec_t prec, int64_t N, const double box[4], double xi,
+                                  double rc, const void *x, const void *f, const void *q, void *u, void *stream);
+
 /* Parameter selection without a device (host only; the same rules as
  * se_plan_create, Section 8.2 with Tables 2 and 3): fills M, P, xi and rc of
  * *out from the overrides in *in (may be NULL), the box side L, N, tol and
