@@ -135,6 +135,57 @@ se_status_t se_eval_real_space(se_plan_t plan, const void *x, const void *f, con
 se_status_t se_real_space_noalloc(se_kernel_t kernel, se_prec_t prec, int64_t N, const double box[4], double xi,
                                   double rc, const void *x, const void *f, const void *q, void *u, void *stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent systems, each with several right-hand sides, in one call.
+ * The paper evaluates one system at a time; it notes that the FFT of the
+ * truncated Green's function is done once for several right-hand sides
+ * (Section 4.3) and that the precomputation is amortised over many calls
+ * (Section 9).  A batch applies Section 8 to every system: the precomputed
+ * kernel of each system is made once, at creation, and every stage runs as one
+ * launch over all systems (the FFTs as one batched transform per FFT size).
+ * Stokeslet and rotlet only.
+ *
+ * Layout: system s owns points [off_s, off_s + N_s) of the concatenated arrays
+ * (off_s = N_0 + ... + N_{s-1}).  x: sumN x 3, f and u: sumN x n_rhs x 3
+ * (right-hand side r of point i at ((i * n_rhs + r) * 3)), row-major, device
+ * memory, in the batch's precision; u is overwritten.  box_s: S x 4 (x0, y0,
+ * z0, L) on the host.  Each system's points must lie in its half-open box. */
+typedef struct se_batch_s *se_batch_t;
+
+/* Create a batch of S systems with N_s[s] points and box box_s[4 s ..] each,
+ * n_rhs in [1, 64] right-hand sides, target relative error tol.  Each system
+ * gets M, xi and rc from the single-plan parameter selection (params: NULL or
+ * overrides common to all systems, e.g. max_fft); the support P is the largest
+ * chosen and is common to the batch (P <= 16, so tol >= about 1e-8).  Allocates
+ * all device memory and runs every system's FP64 precomputation.
+ * SE_ERR_NOT_SUPPORTED for the stresslet or P > 16. */
+se_status_t se_batch_create(se_kernel_t kernel, int S, const int64_t *N_s, const double *box_s, int n_rhs,
+                            double tol, se_prec_t prec, const se_params_t *params, se_batch_t *out);
+
+/* Evaluate all systems and right-hand sides: u = u^R + u^F + u^self per system.
+ * With graph mode on (the default) the first call for a given (x, f, u)
+ * captures the whole sequence into a CUDA graph (on an internal stream) and
+ * every call launches that graph on `stream`; new pointers re-capture.
+ * Asynchronous on `stream`. */
+se_status_t se_batch_eval(se_batch_t batch, const void *x, const void *f, void *u, void *stream);
+
+/* Graph mode on (1, default) or off (0: every call launches the kernels). */
+se_status_t se_batch_set_graph(se_batch_t batch, int on);
+
+/* Parameters chosen for system s (as se_plan_get_params). */
+se_status_t se_batch_get_params(se_batch_t batch, int s, se_params_t *out);
+
+/* Synchronise the stream of the last call; return (and clear) the device-side
+ * status: SE_OK, SE_ERR_OUT_OF_BOX or SE_ERR_COINCIDENT. */
+se_status_t se_batch_check(se_batch_t batch);
+
+/* Number of this library's kernels in one evaluation of the batch (cuFFT's
+ * transforms and memsets not counted); -1 for NULL. */
+int64_t se_batch_launch_count(se_batch_t batch);
+
+/* Free everything the batch holds (synchronises the device). */
+se_status_t se_batch_destroy(se_batch_t batch);
+
 /* Parameter selection without a device (host only; the same rules as
  * se_plan_create, Section 8.2 with Tables 2 and 3): fills M, P, xi and rc of
  * *out from the overrides in *in (may be NULL), the box side L, N, tol and

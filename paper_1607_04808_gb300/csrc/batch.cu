@@ -1,0 +1,430 @@
+// Batched evaluation: S independent systems, each with its own cube, its own
+// points and n_rhs right-hand sides, evaluated by one launch per stage over
+// all systems (the method of Section 8 applied to every system; the
+// precomputed kernel of Section 4.3 is computed once per system and reused
+// for all its right-hand sides, as Section 4.3 notes for repeated solves).
+//
+//   bin (one counting sort over all systems: keys offset per system)
+//   zero octants -> spread (items: system x tile x right-hand side)
+//   R2C FFTs (one batched cuFFT plan per FFT size class)
+//   scale (blocks: system x k-range, all right-hand sides per k-point)
+//   C2R FFTs -> gather + self (warp per point, all right-hand sides)
+//   real-space sum (clusters of all systems, up to 8 right-hand sides a pass)
+//
+// Every system gets its own M, xi and rc from the same parameter selection as
+// a single plan; P (and the spreading tile) is common to the batch.  The whole
+// sequence is captured once into a CUDA graph and replayed while the caller's
+// pointers stay the same.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "se_internal.cuh"
+
+using namespace se;
+
+struct se_batch_s {
+    int kernel = 0, prec = 0, S = 0, R = 1;
+    int64_t Ntot = 0;
+    int P = 0, T_ = 8;
+    std::vector<se_plan_s *> sub;  // per system: parameters, geometry, precomputed kernel
+    std::vector<int> off_h;        // S + 1 point offsets
+    int ntiles_tot = 0, ncells_tot = 0, nrows_tot = 0, nitems = 0, nblk_scale = 0, nblk_zero = 0;
+    void *sys_d = nullptr;  // BSys<T>[S]
+    int *off_d = nullptr, *row_base_d = nullptr, *blk_base_d = nullptr, *zblk_base_d = nullptr;
+    int4 *items_d = nullptr;
+    int *cl_sys = nullptr;
+    Buffers b;
+    struct SizeClass {
+        int Mf = 0, count = 0;
+        void *grid = nullptr, *spec = nullptr, *wgrid = nullptr;
+        cufftHandle fwd = 0, inv = 0;
+        bool have_fwd = false, have_inv = false;
+    };
+    std::vector<SizeClass> classes;
+    void *work = nullptr;
+    // CUDA graph of one evaluation, valid for the pointers it was captured with
+    bool use_graph = true;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *gx = nullptr, *gf = nullptr;
+    void *gu = nullptr;
+    int64_t launches = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+void free_batch(se_batch_s *B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    for (auto &c : B->classes) {
+        if (c.have_fwd) cufftDestroy(c.fwd);
+        if (c.have_inv) cufftDestroy(c.inv);
+        cudaFree(c.grid);
+        cudaFree(c.spec);
+        cudaFree(c.wgrid);
+    }
+    void *ptrs[] = {B->work, B->sys_d, B->off_d, B->row_base_d, B->blk_base_d, B->zblk_base_d, B->items_d,
+                    B->cl_sys, B->b.xs_t, B->b.fs_t, B->b.perm_t, B->b.cnt_t, B->b.slot_t, B->b.key_t,
+                    B->b.xs_r, B->b.fs_r, B->b.perm_r, B->b.cnt_r, B->b.slot_r, B->b.key_r, B->b.tag_t,
+                    B->b.tag_r, B->b.ncl, B->b.clusters, B->b.status};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (se_plan_s *p : B->sub) free_plan(p);
+    delete B;
+}
+
+template <typename T>
+void fill_sys(se_batch_s *B, std::vector<BSys<T>> &sys, const std::vector<int> &tile_base,
+              const std::vector<int> &cell_base, const std::vector<int> &row_base, const std::vector<int> &blk_base,
+              const std::vector<int> &zblk_base, const std::vector<void *> &grid, const std::vector<void *> &spec,
+              const std::vector<void *> &wgrid) {
+    sys.resize(B->S);
+    for (int s = 0; s < B->S; s++) {
+        se_plan_s *p = B->sub[s];
+        BSys<T> &Y = sys[s];
+        memset(&Y, 0, sizeof(Y));
+        Y.g = gp<T>(p);
+        Y.rk = make_rc<T>(p);
+        Y.sc = make_scale_const(p);
+        Y.ghat = (const T *)p->ghat;
+        Y.grid = (T *)grid[s];
+        Y.spec = (cplx<T> *)spec[s];
+        Y.wgrid = (T *)wgrid[s];
+        Y.self_coef = (B->kernel == SE_STOKESLET) ? -4.0 * p->xi / sqrt(M_PI) : 0.0;
+        Y.off = B->off_h[s];
+        Y.n = B->off_h[s + 1] - B->off_h[s];
+        Y.tile_base = tile_base[s];
+        Y.cell_base = cell_base[s];
+        Y.row_base = row_base[s];
+        Y.blk_base = blk_base[s];
+        Y.zblk_base = zblk_base[s];
+    }
+}
+
+#define BCK(expr)                                                                        \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return fail(SE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+#define BCF(expr)                                                                             \
+    do {                                                                                      \
+        cufftResult _r = (expr);                                                              \
+        if (_r != CUFFT_SUCCESS)                                                              \
+            return fail(SE_ERR_CUFFT, std::string(#expr) + " failed, code " + std::to_string((int)_r)); \
+    } while (0)
+
+template <typename T>
+se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t st) {
+    const BSys<T> *sys = (const BSys<T> *)B->sys_d;
+    const int S = B->S, R = B->R, Ntot = (int)B->Ntot;
+    B->launches = 0;
+    BCK(launch_bbin<T>(sys, B->off_d, S, Ntot, R, B->ntiles_tot, B->ncells_tot, x, f, B->b, st, &B->launches));
+    BCK(launch_bzero<T>(sys, B->zblk_base_d, S, B->nblk_zero, R, st));
+    BCK(launch_bspread<T>(sys, B->items_d, B->nitems, B->P, B->T_, R, B->b, st));
+    B->launches += 2;
+    for (auto &c : B->classes) {
+        BCF(cufftSetStream(c.fwd, st));
+        if (sizeof(T) == 4)
+            BCF(cufftExecR2C(c.fwd, (cufftReal *)c.grid, (cufftComplex *)c.spec));
+        else
+            BCF(cufftExecD2Z(c.fwd, (cufftDoubleReal *)c.grid, (cufftDoubleComplex *)c.spec));
+    }
+    BCK(launch_bscale<T>(B->kernel, sys, B->blk_base_d, S, B->nblk_scale, R, st));
+    B->launches += 1;
+    for (auto &c : B->classes) {
+        BCF(cufftSetStream(c.inv, st));
+        if (sizeof(T) == 4)
+            BCF(cufftExecC2R(c.inv, (cufftComplex *)c.spec, (cufftReal *)c.wgrid));
+        else
+            BCF(cufftExecZ2D(c.inv, (cufftDoubleComplex *)c.spec, (cufftDoubleReal *)c.wgrid));
+    }
+    BCK(launch_bgather<T>(sys, B->off_d, S, Ntot, B->P, R, B->b, f, u, st));
+    B->launches += 1;
+    BCK(launch_breal<T>(B->kernel, sys, B->row_base_d, S, B->nrows_tot, Ntot, R, B->b, B->cl_sys, u, st,
+                        &B->launches));
+    return SE_OK;
+}
+
+se_status_t enqueue(se_batch_s *B, const void *x, const void *f, void *u, cudaStream_t st) {
+    if (B->prec == SE_FP32) return enqueue_t<float>(B, (const float *)x, (const float *)f, (float *)u, st);
+    return enqueue_t<double>(B, (const double *)x, (const double *)f, (double *)u, st);
+}
+
+template <typename P_>
+cudaError_t bmalloc(P_ **ptr, size_t bytes) {
+    return cudaMalloc((void **)ptr, bytes ? bytes : 16);
+}
+
+se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, double tol, const se_params_t *params) {
+    const int S = B->S, kernel = B->kernel, prec = B->prec, R = B->R;
+    // parameters per system, then a common P (the largest chosen)
+    std::vector<se_params_t> pr(S);
+    int Pmax = 0;
+    for (int s = 0; s < S; s++) {
+        se_status_t st = choose_params(kernel, prec, N_s[s], box_s[4 * s + 3], tol, params, 0.0, &pr[s]);
+        if (st != SE_OK) return st;
+        Pmax = std::max(Pmax, pr[s].P);
+    }
+    for (int s = 0; s < S; s++) {
+        if (pr[s].P == Pmax) continue;
+        se_params_t in;
+        memset(&in, 0, sizeof(in));
+        if (params) in = *params;
+        in.P = Pmax;
+        se_status_t st = choose_params(kernel, prec, N_s[s], box_s[4 * s + 3], tol, &in, 0.0, &pr[s]);
+        if (st != SE_OK) return st;
+    }
+    B->P = Pmax;
+    // geometry and the precomputed kernel of every system
+    for (int s = 0; s < S; s++) {
+        se_plan_s *p = new se_plan_s();
+        B->sub.push_back(p);
+        if (!(pr[s].xi > 0) || !(pr[s].rc > 0) || pr[s].M < 1)
+            return fail(SE_ERR_INVALID_ARG, "batch: invalid parameters for system " + std::to_string(s));
+        se_status_t st = setup_plan(p, kernel, prec, N_s[s], box_s + 4 * s, pr[s]);
+        if (st != SE_OK) return st;
+        if (!p->tiled || p->P > 16)
+            return fail(SE_ERR_NOT_SUPPORTED, "batch: the support P must be <= 16 (tolerance too small)");
+        if (make_rc<double>(p).reach > 5)
+            return fail(SE_ERR_NOT_SUPPORTED, "batch: real-space reach above 5 cells");
+        if (s > 0 && p->geom.T != B->sub[0]->geom.T)
+            return fail(SE_ERR_NOT_SUPPORTED, "batch: spreading tiles differ between systems");
+        const size_t O3 = (size_t)(p->Mt + 1) * (p->Mt + 1) * (p->Mt + 1);
+        if (bmalloc(&p->ghat64, O3 * sizeof(double)) ||
+            (prec == SE_FP32 && bmalloc((float **)&p->ghat, O3 * sizeof(float)))) {
+            cudaGetLastError();
+            return fail(SE_ERR_OOM, "batch: precompute allocation failed");
+        }
+        st = precompute(p);
+        if (st != SE_OK) return st;
+    }
+    B->T_ = B->sub[0]->geom.T;
+    // offsets and tables
+    B->off_h.assign(S + 1, 0);
+    for (int s = 0; s < S; s++) B->off_h[s + 1] = B->off_h[s] + (int)N_s[s];
+    B->Ntot = B->off_h[S];
+    std::vector<int> tile_base(S + 1), cell_base(S + 1), row_base(S + 1), blk_base(S + 1), zblk_base(S + 1);
+    std::vector<int4> items;
+    for (int s = 0; s < S; s++) {
+        se_plan_s *p = B->sub[s];
+        tile_base[s + 1] = tile_base[s] + p->ntiles;
+        cell_base[s + 1] = cell_base[s] + p->ncells;
+        row_base[s + 1] = row_base[s] + p->geom.ncd * p->geom.ncd;
+        const size_t nk = (size_t)p->Mf * p->Mf * (p->Mf / 2 + 1);
+        blk_base[s + 1] = blk_base[s] + (int)((nk + SCALE_BS - 1) / SCALE_BS);
+        const size_t zrows = (size_t)3 * R * p->Mt * p->Mt;
+        zblk_base[s + 1] = zblk_base[s] + (int)((zrows + 7) / 8);
+        for (int t = 0; t < p->ntiles; t++)
+            for (int r = 0; r < R; r++) items.push_back(make_int4(s, t, r, 0));
+    }
+    B->ntiles_tot = tile_base[S];
+    B->ncells_tot = cell_base[S];
+    B->nrows_tot = row_base[S];
+    B->nblk_scale = blk_base[S];
+    B->nblk_zero = zblk_base[S];
+    B->nitems = (int)items.size();
+    // FFT size classes: systems with equal Mf share one batched transform
+    std::map<int, std::vector<int>> by_mf;
+    for (int s = 0; s < S; s++) by_mf[B->sub[s]->Mf].push_back(s);
+    const size_t esz = (prec == SE_FP32) ? 4 : 8;
+    std::vector<void *> grid(S), spec(S), wgrid(S);
+    size_t work_max = 0;
+    for (auto &kv : by_mf) {
+        se_batch_s::SizeClass c;
+        c.Mf = kv.first;
+        c.count = (int)kv.second.size();
+        B->classes.push_back(c);
+        se_batch_s::SizeClass &C = B->classes.back();
+        const size_t Mf3 = (size_t)C.Mf * C.Mf * C.Mf, nk = (size_t)C.Mf * C.Mf * (C.Mf / 2 + 1);
+        const size_t per = (size_t)3 * R;
+        if (bmalloc(&C.grid, C.count * per * Mf3 * esz) || bmalloc(&C.spec, C.count * per * nk * 2 * esz) ||
+            bmalloc(&C.wgrid, C.count * per * Mf3 * esz) || cudaMemset(C.grid, 0, C.count * per * Mf3 * esz)) {
+            cudaGetLastError();
+            return fail(SE_ERR_OOM, "batch: grid allocation failed");
+        }
+        for (int j = 0; j < C.count; j++) {
+            const int s = kv.second[j];
+            grid[s] = (char *)C.grid + j * per * Mf3 * esz;
+            spec[s] = (char *)C.spec + j * per * nk * 2 * esz;
+            wgrid[s] = (char *)C.wgrid + j * per * Mf3 * esz;
+        }
+        long long n[3] = {C.Mf, C.Mf, C.Mf};
+        const long long batch = (long long)C.count * per;
+        size_t ws = 0;
+        BCF(cufftCreate(&C.fwd));
+        C.have_fwd = true;
+        BCF(cufftSetAutoAllocation(C.fwd, 0));
+        BCF(cufftMakePlanMany64(C.fwd, 3, n, nullptr, 1, (long long)Mf3, nullptr, 1, (long long)nk,
+                                prec == SE_FP32 ? CUFFT_R2C : CUFFT_D2Z, batch, &ws));
+        work_max = std::max(work_max, ws);
+        BCF(cufftCreate(&C.inv));
+        C.have_inv = true;
+        BCF(cufftSetAutoAllocation(C.inv, 0));
+        BCF(cufftMakePlanMany64(C.inv, 3, n, nullptr, 1, (long long)nk, nullptr, 1, (long long)Mf3,
+                                prec == SE_FP32 ? CUFFT_C2R : CUFFT_Z2D, batch, &ws));
+        work_max = std::max(work_max, ws);
+    }
+    // the transforms run one after another on one stream: one shared work area
+    if (bmalloc(&B->work, work_max)) {
+        cudaGetLastError();
+        return fail(SE_ERR_OOM, "batch: cuFFT work area allocation failed");
+    }
+    for (auto &C : B->classes) {
+        BCF(cufftSetWorkArea(C.fwd, B->work));
+        BCF(cufftSetWorkArea(C.inv, B->work));
+    }
+    // point buffers
+    const size_t Nn = (size_t)B->Ntot, v4 = 4 * esz;
+    auto scan_len = [](size_t n) { return n + 2 + (n + 4095) / 4096 + 1; };
+    const size_t max_cl = Nn / 4 + B->nrows_tot + 1;  // clusters hold at least 4 targets (or end a row)
+    Buffers &b = B->b;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = bmalloc(&b.xs_t, Nn * v4)) || (e = bmalloc(&b.fs_t, Nn * R * v4)) ||
+            (e = bmalloc(&b.perm_t, Nn * 4)) || (e = bmalloc(&b.slot_t, Nn * 4)) ||
+            (e = bmalloc(&b.key_t, Nn * 4)) || (e = bmalloc(&b.tag_t, Nn * 4)))
+            break;
+        if ((e = bmalloc(&b.xs_r, Nn * v4)) || (e = bmalloc(&b.fs_r, Nn * R * v4)) ||
+            (e = bmalloc(&b.perm_r, Nn * 4)) || (e = bmalloc(&b.slot_r, Nn * 4)) ||
+            (e = bmalloc(&b.key_r, Nn * 4)) || (e = bmalloc(&b.tag_r, Nn * 4)))
+            break;
+        if ((e = bmalloc(&b.cnt_t, scan_len(B->ntiles_tot) * 4)) || (e = bmalloc(&b.cnt_r, scan_len(B->ncells_tot) * 4)) ||
+            (e = bmalloc(&b.ncl, scan_len(B->nrows_tot) * 4)) || (e = bmalloc(&b.clusters, max_cl * sizeof(int2))) ||
+            (e = bmalloc(&B->cl_sys, max_cl * 4)) || (e = bmalloc(&b.status, 16)))
+            break;
+        if ((e = cudaMemset(b.status, 0, 16))) break;
+        if ((e = bmalloc(&B->off_d, (S + 1) * 4)) || (e = bmalloc(&B->row_base_d, (S + 1) * 4)) ||
+            (e = bmalloc(&B->blk_base_d, (S + 1) * 4)) || (e = bmalloc(&B->zblk_base_d, (S + 1) * 4)) ||
+            (e = bmalloc(&B->items_d, items.size() * sizeof(int4))))
+            break;
+        if ((e = cudaMemcpy(B->off_d, B->off_h.data(), (S + 1) * 4, cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(B->row_base_d, row_base.data(), (S + 1) * 4, cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(B->blk_base_d, blk_base.data(), (S + 1) * 4, cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(B->zblk_base_d, zblk_base.data(), (S + 1) * 4, cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(B->items_d, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice)))
+            break;
+        if (prec == SE_FP32) {
+            std::vector<BSys<float>> sys;
+            fill_sys<float>(B, sys, tile_base, cell_base, row_base, blk_base, zblk_base, grid, spec, wgrid);
+            if ((e = bmalloc(&B->sys_d, S * sizeof(BSys<float>)))) break;
+            e = cudaMemcpy(B->sys_d, sys.data(), S * sizeof(BSys<float>), cudaMemcpyHostToDevice);
+        } else {
+            std::vector<BSys<double>> sys;
+            fill_sys<double>(B, sys, tile_base, cell_base, row_base, blk_base, zblk_base, grid, spec, wgrid);
+            if ((e = bmalloc(&B->sys_d, S * sizeof(BSys<double>)))) break;
+            e = cudaMemcpy(B->sys_d, sys.data(), S * sizeof(BSys<double>), cudaMemcpyHostToDevice);
+        }
+        if (e) break;
+        e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    } while (0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SE_ERR_OOM : SE_ERR_CUDA,
+                    std::string("batch allocation: ") + cudaGetErrorString(e));
+    }
+    return SE_OK;
+}
+
+}  // namespace
+
+extern "C" se_status_t se_batch_create(se_kernel_t kernel, int S, const int64_t *N_s, const double *box_s, int n_rhs,
+                                       double tol, se_prec_t prec, const se_params_t *params, se_batch_t *out) {
+    if (!out) return fail(SE_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (kernel != SE_STOKESLET && kernel != SE_ROTLET)
+        return fail(SE_ERR_NOT_SUPPORTED, "se_batch_create: stokeslet and rotlet only");
+    if (prec != SE_FP32 && prec != SE_FP64) return fail(SE_ERR_INVALID_ARG, "unknown precision");
+    if (S < 1 || !N_s || !box_s) return fail(SE_ERR_INVALID_ARG, "se_batch_create: need S >= 1 systems");
+    if (n_rhs < 1 || n_rhs > 64) return fail(SE_ERR_INVALID_ARG, "se_batch_create: n_rhs must be in [1, 64]");
+    int64_t tot = 0;
+    for (int s = 0; s < S; s++) {
+        if (N_s[s] < 1) return fail(SE_ERR_INVALID_ARG, "se_batch_create: every system needs N >= 1");
+        if (!(box_s[4 * s + 3] > 0)) return fail(SE_ERR_INVALID_ARG, "se_batch_create: box side must be positive");
+        tot += N_s[s];
+    }
+    if (tot * n_rhs > (int64_t)INT32_MAX / 4) return fail(SE_ERR_INVALID_ARG, "se_batch_create: too many points");
+    se_batch_s *B = new se_batch_s();
+    B->kernel = kernel;
+    B->prec = prec;
+    B->S = S;
+    B->R = n_rhs;
+    se_status_t s = create(B, N_s, box_s, tol, params);
+    if (s != SE_OK) {
+        free_batch(B);
+        return s;
+    }
+    *out = B;
+    return SE_OK;
+}
+
+extern "C" se_status_t se_batch_eval(se_batch_t B, const void *x, const void *f, void *u, void *stream) {
+    if (!B || !x || !f || !u) return fail(SE_ERR_INVALID_ARG, "se_batch_eval: NULL pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    B->last_stream = st;
+    if (!B->use_graph) return enqueue(B, x, f, u, st);
+    if (!B->exec || B->gx != x || B->gf != f || B->gu != u) {
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        if (B->graph) cudaGraphDestroy(B->graph);
+        B->exec = nullptr;
+        B->graph = nullptr;
+        BCK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+        se_status_t s = enqueue(B, x, f, u, B->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+        if (s != SE_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(SE_ERR_CUDA, std::string("se_batch_eval: capture: ") + cudaGetErrorString(e));
+        B->graph = g;
+        BCK(cudaGraphInstantiate(&B->exec, g, 0));
+        B->gx = x;
+        B->gf = f;
+        B->gu = u;
+    }
+    BCK(cudaGraphLaunch(B->exec, st));
+    return SE_OK;
+}
+
+extern "C" se_status_t se_batch_set_graph(se_batch_t B, int on) {
+    if (!B) return fail(SE_ERR_INVALID_ARG, "NULL batch");
+    B->use_graph = on != 0;
+    return SE_OK;
+}
+
+extern "C" se_status_t se_batch_get_params(se_batch_t B, int s, se_params_t *out) {
+    if (!B || !out || s < 0 || s >= B->S) return fail(SE_ERR_INVALID_ARG, "se_batch_get_params: bad argument");
+    return se_plan_get_params(B->sub[s], out);
+}
+
+extern "C" se_status_t se_batch_check(se_batch_t B) {
+    if (!B) return fail(SE_ERR_INVALID_ARG, "NULL batch");
+    cudaError_t e = B->last_stream ? cudaStreamSynchronize(B->last_stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(SE_ERR_CUDA, std::string("se_batch_check: ") + cudaGetErrorString(e));
+    int flags = 0;
+    if ((e = cudaMemcpy(&flags, B->b.status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(SE_ERR_CUDA, std::string("se_batch_check: ") + cudaGetErrorString(e));
+    cudaMemset(B->b.status, 0, sizeof(int));
+    if (flags & FLAG_OOB) return fail(SE_ERR_OUT_OF_BOX, "a point lies outside its system's box");
+    if (flags & FLAG_COINCIDENT) return fail(SE_ERR_COINCIDENT, "coincident points were skipped");
+    return SE_OK;
+}
+
+extern "C" int64_t se_batch_launch_count(se_batch_t B) { return B ? B->launches : -1; }
+
+extern "C" se_status_t se_batch_destroy(se_batch_t B) {
+    if (!B) return SE_OK;
+    cudaDeviceSynchronize();
+    free_batch(B);
+    return SE_OK;
+}

@@ -90,7 +90,95 @@ __global__ void k_bin_scatter(int N, const T *__restrict__ x, const T *__restric
     if (q) { qs_t[pt] = qv; qs_r[pr] = qv; }
 }
 
+// Batched: the point's system is the range of `off` holding its index; its
+// keys are offset by the system's first tile and first cell, so one counting
+// sort orders the points by system, then by tile (or cell).
+template <typename T>
+__global__ void k_bbin_count(int Ntot, const BSys<T> *__restrict__ sys, const int *__restrict__ off, int S,
+                             const T *__restrict__ x, int *__restrict__ cnt_t, int *__restrict__ slot_t,
+                             int *__restrict__ key_t, int *__restrict__ cnt_r, int *__restrict__ slot_r,
+                             int *__restrict__ key_r, int *__restrict__ tag_t, int *__restrict__ tag_r,
+                             int *__restrict__ status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ntot) return;
+    const BSys<T> &B = sys[find_range(off, S, i)];
+    const GP<T> g = B.g;
+    int i0[3], cc[3];
+    bool oob = false;
+    for (int d = 0; d < 3; d++) {
+        T rel = x[3 * (size_t)i + d] - g.x0[d];
+        if (!(rel >= T(0) && rel < g.L)) oob = true;
+        rel = clamp_rel(rel, g.L);
+        i0[d] = window_start(rel, g);
+        cc[d] = (d == 0) ? min(max((int)(rel * g.inv_cwx), 0), g.ncdx - 1)
+                         : min(max((int)(rel * g.inv_cw), 0), g.ncd - 1);
+    }
+    if (oob) atomicOr(status, FLAG_OOB);
+    int kt = B.tile_base + (min(i0[2] / g.T_, g.ntd - 1) * g.ntd + min(i0[1] / g.T_, g.ntd - 1)) * g.ntd +
+             min(i0[0] / g.T_, g.ntd - 1);
+    int kr = B.cell_base + (cc[2] * g.ncd + cc[1]) * g.ncdx + cc[0];
+    key_t[i] = kt;
+    key_r[i] = kr;
+    tag_t[i] = pack3(i0[0], i0[1], i0[2]);
+    tag_r[i] = pack3(cc[0], cc[1], cc[2]);
+    slot_t[i] = atomicAdd(&cnt_t[kt], 1);
+    slot_r[i] = atomicAdd(&cnt_r[kr], 1);
+}
+
+// Batched scatter: n_rhs source three-vectors per point, stored as n_rhs
+// consecutive 4-vectors of the sorted point.
+template <typename T>
+__global__ void k_bbin_scatter(int Ntot, int n_rhs, const T *__restrict__ x, const T *__restrict__ f,
+                               const int *__restrict__ start_t, const int *__restrict__ slot_t,
+                               const int *__restrict__ key_t, const int *__restrict__ start_r,
+                               const int *__restrict__ slot_r, const int *__restrict__ key_r,
+                               const int *__restrict__ tag_t, const int *__restrict__ tag_r,
+                               vec4<T> *__restrict__ xs_t, vec4<T> *__restrict__ fs_t, int *__restrict__ perm_t,
+                               vec4<T> *__restrict__ xs_r, vec4<T> *__restrict__ fs_r, int *__restrict__ perm_r) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ntot) return;
+    vec4<T> xv;
+    xv.x = x[3 * (size_t)i]; xv.y = x[3 * (size_t)i + 1]; xv.z = x[3 * (size_t)i + 2];
+    const int pt = start_t[key_t[i]] + slot_t[i];
+    const int pr = start_r[key_r[i]] + slot_r[i];
+    vec4<T> xr = xv;
+    set_tag(xv, tag_t[i]);
+    set_tag(xr, tag_r[i]);
+    xs_t[pt] = xv; perm_t[pt] = i;
+    xs_r[pr] = xr; perm_r[pr] = i;
+    for (int r = 0; r < n_rhs; r++) {
+        const T *fr = f + ((size_t)i * n_rhs + r) * 3;
+        vec4<T> fv;
+        fv.x = fr[0]; fv.y = fr[1]; fv.z = fr[2]; fv.w = 0;
+        fs_t[(size_t)pt * n_rhs + r] = fv;
+        fs_r[(size_t)pr * n_rhs + r] = fv;
+    }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_bbin(const BSys<T> *sys, const int *off, int S, int Ntot, int n_rhs, int ntiles_tot,
+                        int ncells_tot, const T *x, const T *f, Buffers &b, cudaStream_t st, int64_t *launches) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.cnt_t, 0, sizeof(int) * (ntiles_tot + 1), st))) return e;
+    if ((e = cudaMemsetAsync(b.cnt_r, 0, sizeof(int) * (ncells_tot + 1), st))) return e;
+    const int bs = 256, gs = (Ntot + bs - 1) / bs;
+    k_bbin_count<T><<<gs, bs, 0, st>>>(Ntot, sys, off, S, x, b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r,
+                                       b.tag_t, b.tag_r, b.status);
+    if ((e = launch_scan(b.cnt_t, ntiles_tot, st))) return e;
+    if ((e = launch_scan(b.cnt_r, ncells_tot, st))) return e;
+    k_bbin_scatter<T><<<gs, bs, 0, st>>>(Ntot, n_rhs, x, f, b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r,
+                                         b.tag_t, b.tag_r, (vec4<T> *)b.xs_t, (vec4<T> *)b.fs_t, b.perm_t,
+                                         (vec4<T> *)b.xs_r, (vec4<T> *)b.fs_r, b.perm_r);
+    *launches += 2 + scan_launch_count(ntiles_tot) + scan_launch_count(ncells_tot);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_bbin<float>(const BSys<float> *, const int *, int, int, int, int, int, const float *,
+                                        const float *, Buffers &, cudaStream_t, int64_t *);
+template cudaError_t launch_bbin<double>(const BSys<double> *, const int *, int, int, int, int, int, const double *,
+                                         const double *, Buffers &, cudaStream_t, int64_t *);
 
 template <typename T>
 cudaError_t launch_bin(se_plan_s *p, const T *x, const T *f, const T *q, cudaStream_t st) {

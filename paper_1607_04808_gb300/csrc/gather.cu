@@ -38,7 +38,67 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// lane's columns of the support: NIT static slots (P <= 16) or a strided loop
+// One target (sorted position n, original index m): lanes cover the (x, y)
+// columns of the support (NIT static slots, P <= 16, or a strided loop) and
+// loop over z; the weights are computed once and applied to the n_rhs groups
+// of three grids (group r at w + 3 r Mf^3).  u and f_orig hold n_rhs
+// three-vectors per point.
+template <typename T, int NIT>
+__device__ __forceinline__ void gather_point(const GP<T> &g, const vec4<T> &xv, int m, const T *__restrict__ w,
+                                             int n_rhs, const T *__restrict__ f_orig, double self_coef,
+                                             T *__restrict__ u, int lane, T (*sw)[32]) {
+    const int P = g.P, P2 = P * P;
+    int i0[3];
+    T fr[3];
+    warp_weights<T>(xv, g, lane, i0, sw, fr);
+    const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+    for (int r = 0; r < n_rhs; r++) {
+        const T *base = w + (size_t)r * 3 * Mf3 + ((size_t)i0[2] * Mf + i0[1]) * Mf + i0[0];
+        T acc0 = 0, acc1 = 0, acc2 = 0;
+        auto column = [&](int kx, int ky) {
+            const T wxy = sw[0][kx] * sw[1][ky];
+            const T *col = base + (size_t)ky * Mf + kx;
+            T a0 = 0, a1 = 0, a2 = 0;
+            for (int kz = 0; kz < P; kz++) {
+                const T wz = sw[2][kz];
+                const T *pz = col + kz * Mf2;
+                a0 += __ldg(pz) * wz;
+                a1 += __ldg(pz + Mf3) * wz;
+                a2 += __ldg(pz + 2 * Mf3) * wz;
+            }
+            acc0 += a0 * wxy;
+            acc1 += a1 * wxy;
+            acc2 += a2 * wxy;
+        };
+        if (NIT > 0) {
+#pragma unroll
+            for (int it = 0; it < (NIT > 0 ? NIT : 1); it++) {
+                int idx = it * 32 + lane;
+                if (idx < P2) {
+                    int ky = idx / P;
+                    column(idx - ky * P, ky);
+                }
+            }
+        } else {
+            for (int idx = lane; idx < P2; idx += 32) {
+                int ky = idx / P;
+                column(idx - ky * P, ky);
+            }
+        }
+        acc0 = warp_sum(acc0);
+        acc1 = warp_sum(acc1);
+        acc2 = warp_sum(acc2);
+        if (lane < 3) {
+            // lanes 0..2 each finish one component (FP64 self-interaction correction)
+            const size_t o3 = ((size_t)m * n_rhs + r) * 3 + lane;
+            const T a = lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2);
+            double o = (double)a;
+            if (self_coef != 0.0) o += self_coef * (double)f_orig[o3];
+            u[o3] = (T)o;
+        }
+    }
+}
+
 template <typename T, int NIT>
 __global__ void __launch_bounds__(WPB * 32) k_gather(GP<T> g, int N, const vec4<T> *__restrict__ xs,
                                                      const int *__restrict__ perm, const T *__restrict__ w,
@@ -48,55 +108,23 @@ __global__ void __launch_bounds__(WPB * 32) k_gather(GP<T> g, int N, const vec4<
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = blockIdx.x * WPB + wib;
     if (n >= N) return;
-    T(*sw)[32] = sw_all[wib];
-    const int P = g.P, P2 = P * P;
-    int i0[3];
-    T fr[3];
-    warp_weights<T>(xs[n], g, lane, i0, sw, fr);
-    const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
-    const T *base = w + ((size_t)i0[2] * Mf + i0[1]) * Mf + i0[0];
-    T acc0 = 0, acc1 = 0, acc2 = 0;
-    auto column = [&](int kx, int ky) {
-        const T wxy = sw[0][kx] * sw[1][ky];
-        const T *col = base + (size_t)ky * Mf + kx;
-        T a0 = 0, a1 = 0, a2 = 0;
-        for (int kz = 0; kz < P; kz++) {
-            const T wz = sw[2][kz];
-            const T *pz = col + kz * Mf2;
-            a0 += __ldg(pz) * wz;
-            a1 += __ldg(pz + Mf3) * wz;
-            a2 += __ldg(pz + 2 * Mf3) * wz;
-        }
-        acc0 += a0 * wxy;
-        acc1 += a1 * wxy;
-        acc2 += a2 * wxy;
-    };
-    if (NIT > 0) {
-#pragma unroll
-        for (int it = 0; it < (NIT > 0 ? NIT : 1); it++) {
-            int idx = it * 32 + lane;
-            if (idx < P2) {
-                int ky = idx / P;
-                column(idx - ky * P, ky);
-            }
-        }
-    } else {
-        for (int idx = lane; idx < P2; idx += 32) {
-            int ky = idx / P;
-            column(idx - ky * P, ky);
-        }
-    }
-    acc0 = warp_sum(acc0);
-    acc1 = warp_sum(acc1);
-    acc2 = warp_sum(acc2);
-    if (lane < 3) {
-        // lanes 0..2 each finish one component (FP64 self-interaction correction)
-        const int m = perm[n];
-        const T a = lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2);
-        double o = (double)a;
-        if (self_coef != 0.0) o += self_coef * (double)f_orig[3 * m + lane];
-        u[3 * m + lane] = (T)o;
-    }
+    gather_point<T, NIT>(g, xs[n], perm[n], w, 1, f_orig, self_coef, u, lane, sw_all[wib]);
+}
+
+// Batched: one warp per sorted point of the concatenated systems; the point's
+// system is the range of `off` that holds its sorted position.
+template <typename T, int NIT>
+__global__ void __launch_bounds__(WPB * 32) k_bgather(const BSys<T> *__restrict__ sys, const int *__restrict__ off,
+                                                      int S, int Ntot, int n_rhs, const vec4<T> *__restrict__ xs,
+                                                      const int *__restrict__ perm, const T *__restrict__ f_orig,
+                                                      T *__restrict__ u) {
+    __shared__ T sw_all[WPB][3][32];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * WPB + wib;
+    if (n >= Ntot) return;
+    const BSys<T> &B = sys[find_range(off, S, n)];
+    const GP<T> g = B.g;
+    gather_point<T, NIT>(g, xs[n], perm[n], B.wgrid, n_rhs, f_orig, B.self_coef, u, lane, sw_all[wib]);
 }
 
 // Position gradient of the Fourier part of L = sum_m g_m . u_m:
@@ -188,6 +216,29 @@ cudaError_t launch_gather_grad(se_plan_s *p, cudaStream_t st, const void *w_fwd,
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_bgather(const BSys<T> *sys, const int *off, int S, int Ntot, int P, int n_rhs, const Buffers &b,
+                           const T *f, T *u, cudaStream_t st) {
+    dim3 gs((Ntot + WPB - 1) / WPB), bs(WPB * 32);
+    const vec4<T> *xs = (const vec4<T> *)b.xs_t;
+    switch ((P * P + 31) / 32) {
+        case 1: k_bgather<T, 1><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+        case 2: k_bgather<T, 2><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+        case 3: k_bgather<T, 3><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+        case 4: k_bgather<T, 4><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+        case 5: k_bgather<T, 5><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+        case 6: k_bgather<T, 6><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+        case 7: k_bgather<T, 7><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+        case 8: k_bgather<T, 8><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+        default: k_bgather<T, 0><<<gs, bs, 0, st>>>(sys, off, S, Ntot, n_rhs, xs, b.perm_t, f, u); break;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_bgather<float>(const BSys<float> *, const int *, int, int, int, int, const Buffers &,
+                                           const float *, float *, cudaStream_t);
+template cudaError_t launch_bgather<double>(const BSys<double> *, const int *, int, int, int, int, const Buffers &,
+                                            const double *, double *, cudaStream_t);
 template cudaError_t launch_gather<float>(se_plan_s *, cudaStream_t, const void *, const float *, float *);
 template cudaError_t launch_gather<double>(se_plan_s *, cudaStream_t, const void *, const double *, double *);
 template cudaError_t launch_gather_grad<float>(se_plan_s *, cudaStream_t, const void *, const void *,

@@ -169,7 +169,7 @@ se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol,
 
 using namespace se;
 
-static void free_plan(se_plan_s *p) {
+void free_plan(se_plan_s *p) {
     if (!p) return;
     if (p->have_fwd) cufftDestroy(p->fwd);
     if (p->have_inv) cufftDestroy(p->inv);
@@ -191,21 +191,9 @@ static cudaError_t dmalloc(P_ **ptr, size_t bytes) {
     return cudaMalloc((void **)ptr, bytes ? bytes : 16);
 }
 
-extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const double box[4], double tol,
-                                      se_prec_t prec, const se_params_t *params, se_plan_t *plan_out) {
-    if (!plan_out) return fail(SE_ERR_INVALID_ARG, "plan_out is NULL");
-    *plan_out = nullptr;
-    if (kernel < SE_STOKESLET || kernel > SE_ROTLET) return fail(SE_ERR_INVALID_ARG, "unknown kernel");
-    if (prec != SE_FP32 && prec != SE_FP64) return fail(SE_ERR_INVALID_ARG, "unknown precision");
-    if (N < 1 || N > (int64_t)INT32_MAX / 4) return fail(SE_ERR_INVALID_ARG, "N out of range");
-    if (!box || !(box[3] > 0)) return fail(SE_ERR_INVALID_ARG, "box side L must be positive");
-    se_params_t pr;
-    se_status_t s = choose_params(kernel, prec, N, box[3], tol, params, xi, &pr);
-    if (s != SE_OK) return s;
-    if (pr.P < 1 || pr.P > 32) return fail(SE_ERR_INVALID_ARG, "P must be in [1, 32]");
-    if (pr.M < 1 || !(pr.xi > 0) || !(pr.rc > 0)) return fail(SE_ERR_INVALID_ARG, "invalid M, xi or rc");
-
-    se_plan_s *p = new se_plan_s();
+// Parameters, grid sizes and geometry of a plan (no device work).
+se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[4],
+                           const se_params_t &pr) {
     p->kernel = kernel;
     p->prec = prec;
     p->N = N;
@@ -237,10 +225,7 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     p->Mg = 2 * (int)floor((1.0 + sqrt(3.0)) * p->Mt / 2.0) + 2;
     while (!good_fft(p->Mg, SE_FP64) || (p->Mg & 1)) p->Mg++;
     p->nc = (kernel == SE_STRESSLET) ? 6 : 3;
-    if (p->max_fft > 0 && p->Mf > p->max_fft) {
-        free_plan(p);
-        return fail(SE_ERR_INVALID_ARG, "FFT size 2*Mtilde exceeds max_fft");
-    }
+    if (p->max_fft > 0 && p->Mf > p->max_fft) return fail(SE_ERR_INVALID_ARG, "FFT size 2*Mtilde exceeds max_fft");
     // geometry
     Geom &g = p->geom;
     for (int dd = 0; dd < 3; dd++) g.x0[dd] = p->x0[dd];
@@ -290,10 +275,7 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     g.cwx = p->L / ncdx;
     g.inv_cwx = ncdx / p->L;
     p->ncells = ncd * ncd * ncdx;
-    if (p->Mt > 1023) {
-        free_plan(p);
-        return fail(SE_ERR_INVALID_ARG, "extended grid above 1023 points per dimension");
-    }
+    if (p->Mt > 1023) return fail(SE_ERR_INVALID_ARG, "extended grid above 1023 points per dimension");
     // the same geometry in each arithmetic precision
     auto fill = [&](auto &G) {
         using TT = std::remove_reference_t<decltype(G.L)>;
@@ -317,6 +299,30 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     fill(p->gpf);
     fill(p->gpd);
 
+    return SE_OK;
+}
+
+extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const double box[4], double tol,
+                                      se_prec_t prec, const se_params_t *params, se_plan_t *plan_out) {
+    if (!plan_out) return fail(SE_ERR_INVALID_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    if (kernel < SE_STOKESLET || kernel > SE_ROTLET) return fail(SE_ERR_INVALID_ARG, "unknown kernel");
+    if (prec != SE_FP32 && prec != SE_FP64) return fail(SE_ERR_INVALID_ARG, "unknown precision");
+    if (N < 1 || N > (int64_t)INT32_MAX / 4) return fail(SE_ERR_INVALID_ARG, "N out of range");
+    if (!box || !(box[3] > 0)) return fail(SE_ERR_INVALID_ARG, "box side L must be positive");
+    se_params_t pr;
+    se_status_t s = choose_params(kernel, prec, N, box[3], tol, params, xi, &pr);
+    if (s != SE_OK) return s;
+    if (pr.P < 1 || pr.P > 32) return fail(SE_ERR_INVALID_ARG, "P must be in [1, 32]");
+    if (pr.M < 1 || !(pr.xi > 0) || !(pr.rc > 0)) return fail(SE_ERR_INVALID_ARG, "invalid M, xi or rc");
+
+    se_plan_s *p = new se_plan_s();
+    s = setup_plan(p, kernel, prec, N, box, pr);
+    if (s != SE_OK) {
+        free_plan(p);
+        return s;
+    }
+    size_t esz = (prec == SE_FP32) ? 4 : 8;
     // allocations
     cudaError_t e = cudaSuccess;
     const size_t Nn = (size_t)N;

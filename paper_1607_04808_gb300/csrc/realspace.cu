@@ -48,13 +48,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int QCAP = 64;
 constexpr int MAXROWS = 121;  // reach <= 5 cells across rows
 
-template <typename T>
-struct RC {
-    T xi, xi2, c, c3, rc2;  // xi, xi^2, 2 xi/sqrt(pi), 4 xi^3/sqrt(pi), rc^2
-    T tab_scale;            // xi / (table interval width in x)
-    int reach;              // rows of cells within reach on each side (y, z)
-};
-
 // The two radial functions at r: erfc(x) = exp(-x^2) Q(2/(2+x)) with the
 // fitted erfcx polynomial Q
 template <int KERNEL>
@@ -253,21 +246,64 @@ __global__ void k_cluster_fill(int nrows, int ncdx, int tpw, const int *__restri
     for (int s = a; s < b; s += tpw) cl[o++] = make_int2(s, min(tpw, b - s));
 }
 
+// K^R(d) applied to NR sources at once (the radial functions are evaluated
+// once per pair): acc[r] += K^R(d) . f[r] (stokeslet, rotlet).
+template <typename T, int KERNEL, int NR>
+__device__ __forceinline__ void pair_multi(const RC<T> &rk, const QTab &qt, T dx, T dy, T dz, T r2,
+                                           const vec4<T> *f, const vec4<T> &q, T (*acc)[3], int nq) {
+    if (NR == 1) {
+        pair_tab<T, KERNEL>(rk, qt, dx, dy, dz, r2, f[0], q, acc[0]);
+        return;
+    }
+    T rinv, t1, t2;
+    radial2_tab<KERNEL>(rk, qt, r2, rinv, t1, t2);
+    const T rinv2 = rinv * rinv;
+    if (KERNEL == SE_STOKESLET) {
+        const T A = t1 * rinv;
+        const T B = t2 * rinv2 * rinv;
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            if (r >= nq) break;
+            const vec4<T> fv = f[r];
+            const T Brf = B * (dx * fv.x + dy * fv.y + dz * fv.z);
+            acc[r][0] += A * fv.x + Brf * dx;
+            acc[r][1] += A * fv.y + Brf * dy;
+            acc[r][2] += A * fv.z + Brf * dz;
+        }
+    } else {
+        const T B = t2 * rinv2 * rinv;
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            if (r >= nq) break;
+            const vec4<T> fv = f[r];
+            acc[r][0] += B * (fv.y * dz - fv.z * dy);
+            acc[r][1] += B * (fv.z * dx - fv.x * dz);
+            acc[r][2] += B * (fv.x * dy - fv.y * dx);
+        }
+    }
+}
+
 // One warp per cluster: lane = (target k = lane % TPW, candidate stream
 // s = lane / TPW).  Candidates of every row within reach are loaded 32 at a
 // time into shared memory and stream s takes every NS-th of them, so each lane
 // tests and evaluates (target k, candidate) pairs without any compaction.
-template <typename T, int KERNEL, int TPW>
-__global__ void __launch_bounds__(256) k_real_cl(GP<T> g, RC<T> rk, const vec4<T> *__restrict__ xs,
+// Sources: right-hand sides q0 .. q0 + nq - 1 (nq <= NR) of the fstride
+// 4-vectors stored per sorted point in fs; u holds fstride three-vectors per
+// original point.  BATCH: the cluster's system
+// (cl_sys) supplies the geometry, the screening constants and the offset of
+// its cells; otherwise g0, rk0 and cell_start0 are the one system's.
+template <typename T, int KERNEL, int TPW, int NR, bool BATCH>
+__global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys<T> *__restrict__ sys,
+                                                 const int *__restrict__ cl_sys, const vec4<T> *__restrict__ xs,
                                                  const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
-                                                 const int *__restrict__ cell_start,
+                                                 const int *__restrict__ cell_start0,
                                                  const int2 *__restrict__ clusters, const int *__restrict__ ncl_total,
                                                  const int *__restrict__ perm, const float4 *__restrict__ qa_g,
                                                  const float2 *__restrict__ qb_g, T *__restrict__ u,
-                                                 int *__restrict__ status) {
+                                                 int *__restrict__ status, int fstride, int q0, int nq) {
     constexpr int WPB = 8, NS = 32 / TPW;
     __shared__ vec4<T> sx_all[WPB][32];
-    __shared__ vec4<T> sf_all[WPB][32];
+    __shared__ vec4<T> sf_all[WPB][32 * NR];
     __shared__ vec4<T> sq_all[KERNEL == SE_STRESSLET ? WPB : 1][32];
     __shared__ int2 seg_all[WPB][MAXROWS];
     __shared__ int pre_all[WPB][MAXROWS + 1];
@@ -292,6 +328,19 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g, RC<T> rk, const vec4<T
     const int per_blk = SE_RS_PERSIST ? (ntot + gridDim.x - 1) / gridDim.x : WPB;
     const int c_end = min(ntot, (blockIdx.x + 1) * per_blk);
     for (int c = blockIdx.x * per_blk + wib; c < c_end; c += WPB) {
+    GP<T> g;
+    RC<T> rk;
+    const int *cell_start;
+    if constexpr (BATCH) {
+        const BSys<T> &B = sys[cl_sys[c]];
+        g = B.g;
+        rk = B.rk;
+        cell_start = cell_start0 + B.cell_base;
+    } else {
+        g = g0;
+        rk = rk0;
+        cell_start = cell_start0;
+    }
     const int2 cl = clusters[c];
     const int k = lane % TPW, s = lane / TPW;
     const bool has = k < cl.y;
@@ -341,7 +390,10 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g, RC<T> rk, const vec4<T
     if (lane == 0) pre[nrows] = run;
     __syncwarp();
     const int total = run;
-    T acc[3] = {0, 0, 0}, ks[3] = {0, 0, 0}, kc[3] = {0, 0, 0};
+    T acc[NR][3], ks[NR][3], kc[NR][3];
+#pragma unroll
+    for (int q = 0; q < NR; q++)
+        for (int d = 0; d < 3; d++) acc[q][d] = ks[q][d] = kc[q][d] = T(0);
     int zeros = 0;  // candidates at distance 0 seen by this lane (its own target included once)
     vec4<T> zero4;
     zero4.x = zero4.y = zero4.z = zero4.w = 0;
@@ -357,7 +409,9 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g, RC<T> rk, const vec4<T
             vec4<T> xv = xs[m];
             xv.w = T(0);
             sx[lane] = xv;
-            sf[lane] = fs[m];
+#pragma unroll
+            for (int q = 0; q < NR; q++)
+                if (q < nq) sf[lane * NR + q] = fs[(size_t)m * fstride + q0 + q];
             if (KERNEL == SE_STRESSLET) sq[lane] = qs[m];
         }
         __syncwarp();
@@ -370,7 +424,7 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g, RC<T> rk, const vec4<T
             zeros += (r2 == T(0)) ? 1 : 0;
             if (has && r2 > T(0) && r2 <= rk.rc2) {
                 const vec4<T> qv = (KERNEL == SE_STRESSLET) ? sq[j] : zero4;
-                pair_tab<T, KERNEL>(rk, qt, dx, dy, dz, r2, sf[j], qv, acc);
+                pair_multi<T, KERNEL, NR>(rk, qt, dx, dy, dz, r2, sf + j * NR, qv, acc, nq);
             }
         };
         if (nch == 32) {
@@ -380,29 +434,74 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g, RC<T> rk, const vec4<T
             for (int j = s; j < nch; j += NS) step(j);
         }
         __syncwarp();
-        for (int d = 0; d < 3; d++) {
-            kahan_add(ks[d], kc[d], acc[d]);
-            acc[d] = 0;
-        }
+#pragma unroll
+        for (int q = 0; q < NR; q++)
+            for (int d = 0; d < 3; d++) {
+                kahan_add(ks[q][d], kc[q][d], acc[q][d]);
+                acc[q][d] = 0;
+            }
     }
     // combine the NS streams of each target (lanes k, k + TPW, ...)
-    T tot[3];
-    for (int d = 0; d < 3; d++) {
-        T sm_ = ks[d], cm_ = kc[d];
-        for (int o = TPW; o < 32; o <<= 1) {
-            const T so = __shfl_xor_sync(FULL, sm_, o), co = __shfl_xor_sync(FULL, cm_, o);
-            kahan_add(sm_, cm_, so);  // sm_ - cm_ now holds the own and the partner's sums
-            cm_ += co;                // minus the partner's compensation
+    T tot[NR][3];
+#pragma unroll
+    for (int q = 0; q < NR; q++)
+        for (int d = 0; d < 3; d++) {
+            T sm_ = ks[q][d], cm_ = kc[q][d];
+            for (int o = TPW; o < 32; o <<= 1) {
+                const T so = __shfl_xor_sync(FULL, sm_, o), co = __shfl_xor_sync(FULL, cm_, o);
+                kahan_add(sm_, cm_, so);  // sm_ - cm_ now holds the own and the partner's sums
+                cm_ += co;                // minus the partner's compensation
+            }
+            tot[q][d] = sm_ - cm_;
         }
-        tot[d] = sm_ - cm_;
-    }
     for (int o = TPW; o < 32; o <<= 1) zeros += __shfl_xor_sync(FULL, zeros, o);
     if (__any_sync(FULL, has && zeros > 1) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
     if (s == 0 && has) {
-        const int mi = perm[t];
-        for (int d = 0; d < 3; d++) u[3 * mi + d] = (T)((double)u[3 * mi + d] + (double)tot[d]);
+        const size_t mi = perm[t];
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            if (q >= nq) break;
+            for (int d = 0; d < 3; d++) {
+                T *ud = u + (mi * fstride + q0 + q) * 3 + d;
+                *ud = (T)((double)*ud + (double)tot[q][d]);
+            }
+        }
     }
     __syncwarp();
+    }
+}
+
+// Batched cluster lists: row `row` of all systems' cell rows belongs to the
+// system s with row_base[s] <= row < row_base[s+1].
+template <typename T>
+__global__ void k_bcluster_count(int nrows_tot, const BSys<T> *__restrict__ sys, const int *__restrict__ row_base,
+                                 int S, int tpw, const int *__restrict__ cell_start, int *ncl) {
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nrows_tot) return;
+    const int s = find_range(row_base, S, row);
+    const BSys<T> &B = sys[s];
+    const int ncdx = B.g.ncdx, lr = row - row_base[s];
+    const int *cs = cell_start + B.cell_base;
+    const int len = cs[(lr + 1) * ncdx] - cs[lr * ncdx];
+    ncl[row] = (len + tpw - 1) / tpw;
+}
+
+template <typename T>
+__global__ void k_bcluster_fill(int nrows_tot, const BSys<T> *__restrict__ sys, const int *__restrict__ row_base,
+                                int S, int tpw, const int *__restrict__ cell_start,
+                                const int *__restrict__ ncl_start, int2 *__restrict__ cl, int *__restrict__ cl_sys) {
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nrows_tot) return;
+    const int s = find_range(row_base, S, row);
+    const BSys<T> &B = sys[s];
+    const int ncdx = B.g.ncdx, lr = row - row_base[s];
+    const int *cs = cell_start + B.cell_base;
+    const int a = cs[lr * ncdx], b = cs[(lr + 1) * ncdx];
+    int o = ncl_start[row];
+    for (int q = a; q < b; q += tpw) {
+        cl[o] = make_int2(q, min(tpw, b - q));
+        cl_sys[o] = s;
+        o++;
     }
 }
 
@@ -621,19 +720,6 @@ __global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, con
         for (int d = 0; d < 3; d++) gx[3 * mp + d] = (T)((double)gx[3 * mp + d] + tot[d]);
 }
 
-template <typename T>
-RC<T> make_rc(const se_plan_s *p) {
-    RC<T> rk;
-    rk.xi = (T)p->xi;
-    rk.xi2 = (T)(p->xi * p->xi);
-    rk.c = (T)(2.0 * p->xi / sqrt(M_PI));
-    rk.c3 = (T)(4.0 * p->xi * p->xi * p->xi / sqrt(M_PI));
-    rk.rc2 = (T)(p->rc * p->rc);
-    rk.tab_scale = (T)(p->xi * RQ_N / (p->xi * p->rc * (1.0 + 1e-3)));
-    rk.reach = (int)ceil(p->rc * p->geom.inv_cw - 1e-9);
-    return rk;
-}
-
 #ifndef SE_RS_TPW
 #define SE_RS_TPW 16
 #endif
@@ -663,14 +749,73 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long nblk = SE_RS_PERSIST ? std::min<long>((max_cl + 7) / 8, 4L * nsm) : (max_cl + 7) / 8;
     if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
-    k_real_cl<T, KERNEL, TPW><<<(unsigned)nblk, 256, 0, st>>>(g, rk, xs, fs, qs, p->b.cnt_r, p->b.clusters,
+    k_real_cl<T, KERNEL, TPW, 1, false><<<(unsigned)nblk, 256, 0, st>>>(g, rk, nullptr, nullptr, xs, fs, qs,
+                                                                      p->b.cnt_r, p->b.clusters,
                                                               p->b.ncl + nrows, p->b.perm_r, p->rq_a, p->rq_b, u,
-                                                              p->b.status);
+                                                              p->b.status, 1, 0, 1);
     p->launches += 3 + scan_launch_count(nrows);
     return cudaGetLastError();
 }
 
+// Batched real-space sum: cluster lists of all systems, then one pass of the
+// clustered kernel per group of up to NRMAX right-hand sides (8 in FP32, 2 in
+// FP64, so that the staged candidates fit in the 48 KB of static shared memory).
+
+template <typename T, int KERNEL>
+cudaError_t launch_breal_k(const BSys<T> *sys, const int *row_base, int S, int nrows_tot, int Ntot, int n_rhs,
+                           const Buffers &b, int *cl_sys, T *u, cudaStream_t st, int64_t *launches) {
+    constexpr int TPW = SE_RS_TPW;
+    const unsigned rb = (unsigned)((nrows_tot + 255) / 256);
+    k_bcluster_count<T><<<rb, 256, 0, st>>>(nrows_tot, sys, row_base, S, TPW, b.cnt_r, b.ncl);
+    cudaError_t e = launch_scan(b.ncl, nrows_tot, st);
+    if (e) return e;
+    k_bcluster_fill<T><<<rb, 256, 0, st>>>(nrows_tot, sys, row_base, S, TPW, b.cnt_r, b.ncl, b.clusters, cl_sys);
+    *launches += 2 + scan_launch_count(nrows_tot);
+    const long max_cl = Ntot / TPW + nrows_tot + 1;
+    const unsigned nblk = (unsigned)((max_cl + 7) / 8);
+    constexpr int NRMAX = sizeof(T) == 4 ? 8 : 2;
+    for (int q0 = 0; q0 < n_rhs; q0 += NRMAX) {
+        const int nq = std::min(NRMAX, n_rhs - q0);
+        k_real_cl<T, KERNEL, TPW, NRMAX, true><<<nblk, 256, 0, st>>>(
+            GP<T>{}, RC<T>{}, sys, cl_sys, (const vec4<T> *)b.xs_r, (const vec4<T> *)b.fs_r, nullptr, b.cnt_r,
+            b.clusters, b.ncl + nrows_tot, b.perm_r, nullptr, nullptr, u, b.status, n_rhs, q0, nq);
+        *launches += 1;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+template <typename T>
+RC<T> make_rc(const se_plan_s *p) {
+    RC<T> rk;
+    rk.xi = (T)p->xi;
+    rk.xi2 = (T)(p->xi * p->xi);
+    rk.c = (T)(2.0 * p->xi / sqrt(M_PI));
+    rk.c3 = (T)(4.0 * p->xi * p->xi * p->xi / sqrt(M_PI));
+    rk.rc2 = (T)(p->rc * p->rc);
+    rk.tab_scale = (T)(p->xi * RQ_N / (p->xi * p->rc * (1.0 + 1e-3)));
+    rk.reach = (int)ceil(p->rc * p->geom.inv_cw - 1e-9);
+    return rk;
+}
+
+template RC<float> make_rc<float>(const se_plan_s *);
+template RC<double> make_rc<double>(const se_plan_s *);
+
+template <typename T>
+cudaError_t launch_breal(int kernel, const BSys<T> *sys, const int *row_base, int S, int nrows_tot, int Ntot,
+                         int n_rhs, const Buffers &b, int *cl_sys, T *u, cudaStream_t st, int64_t *launches) {
+    if (kernel == SE_STOKESLET)
+        return launch_breal_k<T, SE_STOKESLET>(sys, row_base, S, nrows_tot, Ntot, n_rhs, b, cl_sys, u, st, launches);
+    if (kernel == SE_ROTLET)
+        return launch_breal_k<T, SE_ROTLET>(sys, row_base, S, nrows_tot, Ntot, n_rhs, b, cl_sys, u, st, launches);
+    return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_breal<float>(int, const BSys<float> *, const int *, int, int, int, int, const Buffers &,
+                                         int *, float *, cudaStream_t, int64_t *);
+template cudaError_t launch_breal<double>(int, const BSys<double> *, const int *, int, int, int, int,
+                                          const Buffers &, int *, double *, cudaStream_t, int64_t *);
 
 // Host construction of the FP32 quadratic table (FP64 arithmetic): on each
 // interval the quadratic through the values at u = 0, 1/2, 1.

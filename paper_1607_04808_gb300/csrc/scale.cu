@@ -18,23 +18,16 @@ namespace se {
 
 namespace {
 
-struct ScaleConst {
-    double dk;       // 2 pi / (Mf h)
-    double inv4xi2;  // 1 / (4 xi^2)
-    double ecoef;    // -(1 - eta) / (4 xi^2)
-    double norm;     // h^3 / Mf^3 * pre^2
-    int Mt, Mf, nxh; // nxh = Mf/2 + 1
-};
-
 __device__ __forceinline__ float sexp(float v) { return expf(v); }
 __device__ __forceinline__ double sexp(double v) { return exp(v); }
 
+// The multiplier at half-spectrum point idx applied to ngroups groups of
+// source components (each group nc consecutive spectra of nk points).
 template <typename T, int KERNEL>
-__global__ void k_scale(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__restrict__ spec) {
+__device__ __forceinline__ void scale_point(const ScaleConst &sc, const T *__restrict__ ghat,
+                                            cplx<T> *__restrict__ spec, size_t idx, int ngroups) {
     using C = cplx<T>;
     const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nk) return;
     int kx = idx % sc.nxh;
     int ky = (idx / sc.nxh) % sc.Mf;
     int kz = idx / ((size_t)sc.nxh * sc.Mf);
@@ -49,68 +42,91 @@ __global__ void k_scale(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__re
     T k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
     T F = (T)sc.norm * G * sexp((T)sc.ecoef * k2);
     if (KERNEL != SE_ROTLET) F *= (T(1) + k2 * (T)sc.inv4xi2);
-    C *w0 = spec + idx;
-    if (KERNEL == SE_STOKESLET) {
-        C g[3];
-        for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
-        C kg;
-        kg.x = kv[0] * g[0].x + kv[1] * g[1].x + kv[2] * g[2].x;
-        kg.y = kv[0] * g[0].y + kv[1] * g[1].y + kv[2] * g[2].y;
-        for (int j = 0; j < 3; j++) {
-            C o;
-            o.x = -F * (k2 * g[j].x - kv[j] * kg.x);
-            o.y = -F * (k2 * g[j].y - kv[j] * kg.y);
-            w0[j * nk] = o;
-        }
-    } else if (KERNEL == SE_ROTLET) {
-        C g[3];
-        for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
-        // (g x k)_j = eps_jlm g_l k_m ; multiply by -i F: (a + ib)(-i) = b - ia
-        C cr[3];
-        cr[0].x = g[1].x * kv[2] - g[2].x * kv[1];
-        cr[0].y = g[1].y * kv[2] - g[2].y * kv[1];
-        cr[1].x = g[2].x * kv[0] - g[0].x * kv[2];
-        cr[1].y = g[2].y * kv[0] - g[0].y * kv[2];
-        cr[2].x = g[0].x * kv[1] - g[1].x * kv[0];
-        cr[2].y = g[0].y * kv[1] - g[1].y * kv[0];
-        for (int j = 0; j < 3; j++) {
-            C o;
-            o.x = F * cr[j].y;
-            o.y = -F * cr[j].x;
-            w0[j * nk] = o;
-        }
-    } else {
-        // symmetric source s: xx, yy, zz, xy, xz, yz
-        C s[6];
-        for (int c = 0; c < 6; c++) s[c] = w0[c * nk];
-        C sk[3], tr, ksk;
-        sk[0].x = s[0].x * kv[0] + s[3].x * kv[1] + s[4].x * kv[2];
-        sk[0].y = s[0].y * kv[0] + s[3].y * kv[1] + s[4].y * kv[2];
-        sk[1].x = s[3].x * kv[0] + s[1].x * kv[1] + s[5].x * kv[2];
-        sk[1].y = s[3].y * kv[0] + s[1].y * kv[1] + s[5].y * kv[2];
-        sk[2].x = s[4].x * kv[0] + s[5].x * kv[1] + s[2].x * kv[2];
-        sk[2].y = s[4].y * kv[0] + s[5].y * kv[1] + s[2].y * kv[2];
-        tr.x = s[0].x + s[1].x + s[2].x;
-        tr.y = s[0].y + s[1].y + s[2].y;
-        ksk.x = kv[0] * sk[0].x + kv[1] * sk[1].x + kv[2] * sk[2].x;
-        ksk.y = kv[0] * sk[0].y + kv[1] * sk[1].y + kv[2] * sk[2].y;
-        for (int j = 0; j < 3; j++) {
-            // b = k^2 (2 (s k)_j + k_j tr s) - 2 k_j (k.s.k); out = -i F b
-            T bx_ = k2 * (T(2) * sk[j].x + kv[j] * tr.x) - T(2) * kv[j] * ksk.x;
-            T by_ = k2 * (T(2) * sk[j].y + kv[j] * tr.y) - T(2) * kv[j] * ksk.y;
-            C o;
-            o.x = F * by_;
-            o.y = -F * bx_;
-            w0[j * nk] = o;
+    constexpr int NCG = (KERNEL == SE_STRESSLET) ? 6 : 3;
+    for (int grp = 0; grp < ngroups; grp++) {
+        C *w0 = spec + (size_t)grp * NCG * nk + idx;
+        if (KERNEL == SE_STOKESLET) {
+            C g[3];
+            for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
+            C kg;
+            kg.x = kv[0] * g[0].x + kv[1] * g[1].x + kv[2] * g[2].x;
+            kg.y = kv[0] * g[0].y + kv[1] * g[1].y + kv[2] * g[2].y;
+            for (int j = 0; j < 3; j++) {
+                C o;
+                o.x = -F * (k2 * g[j].x - kv[j] * kg.x);
+                o.y = -F * (k2 * g[j].y - kv[j] * kg.y);
+                w0[j * nk] = o;
+            }
+        } else if (KERNEL == SE_ROTLET) {
+            C g[3];
+            for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
+            // (g x k)_j = eps_jlm g_l k_m ; multiply by -i F: (a + ib)(-i) = b - ia
+            C cr[3];
+            cr[0].x = g[1].x * kv[2] - g[2].x * kv[1];
+            cr[0].y = g[1].y * kv[2] - g[2].y * kv[1];
+            cr[1].x = g[2].x * kv[0] - g[0].x * kv[2];
+            cr[1].y = g[2].y * kv[0] - g[0].y * kv[2];
+            cr[2].x = g[0].x * kv[1] - g[1].x * kv[0];
+            cr[2].y = g[0].y * kv[1] - g[1].y * kv[0];
+            for (int j = 0; j < 3; j++) {
+                C o;
+                o.x = F * cr[j].y;
+                o.y = -F * cr[j].x;
+                w0[j * nk] = o;
+            }
+        } else {
+            // symmetric source s: xx, yy, zz, xy, xz, yz
+            C s[6];
+            for (int c = 0; c < 6; c++) s[c] = w0[c * nk];
+            C sk[3], tr, ksk;
+            sk[0].x = s[0].x * kv[0] + s[3].x * kv[1] + s[4].x * kv[2];
+            sk[0].y = s[0].y * kv[0] + s[3].y * kv[1] + s[4].y * kv[2];
+            sk[1].x = s[3].x * kv[0] + s[1].x * kv[1] + s[5].x * kv[2];
+            sk[1].y = s[3].y * kv[0] + s[1].y * kv[1] + s[5].y * kv[2];
+            sk[2].x = s[4].x * kv[0] + s[5].x * kv[1] + s[2].x * kv[2];
+            sk[2].y = s[4].y * kv[0] + s[5].y * kv[1] + s[2].y * kv[2];
+            tr.x = s[0].x + s[1].x + s[2].x;
+            tr.y = s[0].y + s[1].y + s[2].y;
+            ksk.x = kv[0] * sk[0].x + kv[1] * sk[1].x + kv[2] * sk[2].x;
+            ksk.y = kv[0] * sk[0].y + kv[1] * sk[1].y + kv[2] * sk[2].y;
+            for (int j = 0; j < 3; j++) {
+                // b = k^2 (2 (s k)_j + k_j tr s) - 2 k_j (k.s.k); out = -i F b
+                T bx_ = k2 * (T(2) * sk[j].x + kv[j] * tr.x) - T(2) * kv[j] * ksk.x;
+                T by_ = k2 * (T(2) * sk[j].y + kv[j] * tr.y) - T(2) * kv[j] * ksk.y;
+                C o;
+                o.x = F * by_;
+                o.y = -F * bx_;
+                w0[j * nk] = o;
+            }
         }
     }
 }
 
+template <typename T, int KERNEL>
+__global__ void k_scale(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__restrict__ spec) {
+    const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nk) return;
+    scale_point<T, KERNEL>(sc, ghat, spec, idx, 1);
+}
+
+// Batched: block b belongs to the system s with blk_base[s] <= b < blk_base[s+1];
+// each thread scales one k-point of that system for all n_rhs right-hand sides,
+// reading the precomputed kernel once.
+template <typename T, int KERNEL>
+__global__ void k_bscale(const BSys<T> *__restrict__ sys, const int *__restrict__ blk_base, int S, int n_rhs) {
+    const int s = find_range(blk_base, S, (int)blockIdx.x);
+    const BSys<T> &B = sys[s];
+    const ScaleConst sc = B.sc;
+    const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
+    const size_t idx = (size_t)(blockIdx.x - blk_base[s]) * blockDim.x + threadIdx.x;
+    if (idx >= nk) return;
+    scale_point<T, KERNEL>(sc, B.ghat, B.spec, idx, n_rhs);
+}
+
 }  // namespace
 
-template <typename T>
-cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpose) {
-    (void)transpose;  // the stokeslet and rotlet multipliers equal their transposes
+ScaleConst make_scale_const(const se_plan_s *p) {
     ScaleConst sc;
     sc.Mt = p->Mt;
     sc.Mf = p->Mf;
@@ -120,8 +136,15 @@ cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpos
     sc.ecoef = -(1.0 - p->eta) / (4.0 * p->xi * p->xi);
     double pre = pow(2.0 * p->xi * p->xi / (M_PI * p->eta), 1.5);
     sc.norm = p->h * p->h * p->h / ((double)p->Mf * p->Mf * p->Mf) * pre * pre;
+    return sc;
+}
+
+template <typename T>
+cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpose) {
+    (void)transpose;  // the stokeslet and rotlet multipliers equal their transposes
+    const ScaleConst sc = make_scale_const(p);
     size_t nk = (size_t)p->Mf * p->Mf * sc.nxh;
-    int bs = 256;
+    int bs = SCALE_BS;
     unsigned gs = (unsigned)((nk + bs - 1) / bs);
     const T *gh = (const T *)p->ghat;
     cplx<T> *sp = (cplx<T> *)spec;
@@ -135,6 +158,20 @@ cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpos
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_bscale(int kernel, const BSys<T> *sys, const int *blk_base, int S, int nblk, int n_rhs,
+                          cudaStream_t st) {
+    if (kernel == SE_STOKESLET)
+        k_bscale<T, SE_STOKESLET><<<nblk, SCALE_BS, 0, st>>>(sys, blk_base, S, n_rhs);
+    else if (kernel == SE_ROTLET)
+        k_bscale<T, SE_ROTLET><<<nblk, SCALE_BS, 0, st>>>(sys, blk_base, S, n_rhs);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_bscale<float>(int, const BSys<float> *, const int *, int, int, int, cudaStream_t);
+template cudaError_t launch_bscale<double>(int, const BSys<double> *, const int *, int, int, int, cudaStream_t);
 template cudaError_t launch_scale<float>(se_plan_s *, cudaStream_t, void *, int);
 template cudaError_t launch_scale<double>(se_plan_s *, cudaStream_t, void *, int);
 

@@ -78,6 +78,52 @@ struct GP {
     int P, Mt, Mf, T_, ntd, ncd, ncdx;
 };
 
+// Screened real-space constants of one system (x = xi r).
+template <typename T>
+struct RC {
+    T xi, xi2, c, c3, rc2;  // xi, xi^2, 2 xi/sqrt(pi), 4 xi^3/sqrt(pi), rc^2
+    T tab_scale;            // xi / (table interval width in x)
+    int reach;              // rows of cells within reach on each side (y, z)
+};
+
+// Constants of the k-space scaling of one system.
+struct ScaleConst {
+    double dk;        // 2 pi / (Mf h)
+    double inv4xi2;   // 1 / (4 xi^2)
+    double ecoef;     // -(1 - eta) / (4 xi^2)
+    double norm;      // h^3 / Mf^3 * pre^2
+    int Mt, Mf, nxh;  // nxh = Mf/2 + 1
+};
+
+// One system of a batch as the batched kernels see it: its geometry and
+// method constants, where its grids live and where its points, tiles, cells
+// and cell rows start in the concatenated (and sorted) arrays.
+template <typename T>
+struct BSys {
+    GP<T> g;
+    RC<T> rk;
+    ScaleConst sc;
+    const T *ghat;     // (Mt+1)^3 octant of the precomputed kernel
+    T *grid;           // spread grids: 3 n_rhs x Mf^3 (zero padded)
+    cplx<T> *spec;     // their spectra: 3 n_rhs x Mf x Mf x (Mf/2+1)
+    T *wgrid;          // inverse transforms: 3 n_rhs x Mf^3
+    double self_coef;  // -4 xi / sqrt(pi) (stokeslet), 0 otherwise
+    int off, n;        // points [off, off + n) of the concatenated and of the sorted order
+    int tile_base, cell_base, row_base;
+    int blk_base;      // first block of this system in the scaling launch
+    int zblk_base;     // first block of this system in the octant-zeroing launch
+};
+
+// Index s of the range holding v, for ascending bases b[0..S) with b[0] = 0.
+__host__ __device__ inline int find_range(const int *b, int S, int v) {
+    int lo = 0, hi = S;  // b[lo] <= v < b[hi] (b[S] taken as infinity)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (b[mid] <= v) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // Coordinate relative to the box corner, clamped into [0, L) for points outside
 // the box (they are flagged by the binning kernel; clamping keeps every kernel's
 // indexing in bounds).
@@ -178,7 +224,13 @@ struct se_plan_s {
     void *dx = nullptr, *df = nullptr, *dq = nullptr, *du = nullptr;
 };
 
+// Free a plan's device memory, cuFFT plans and events, then the plan.
+void free_plan(se_plan_s *p);
+
 namespace se {
+
+// Parameters, grid sizes and geometry of a plan from chosen parameters (host only).
+se_status_t setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[4], const se_params_t &pr);
 
 // launchers (defined in the .cu files); all asynchronous on `st`
 template <typename T>
@@ -199,6 +251,29 @@ cudaError_t launch_gather_grad(se_plan_s *p, cudaStream_t st, const void *w_fwd,
                                const T *f_orig, const T *g_orig, T *gx);
 template <typename T>
 cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *gx);
+
+// batched launchers (one launch over all systems of a batch)
+constexpr int SCALE_BS = 256;  // threads per block of the scaling kernels
+ScaleConst make_scale_const(const se_plan_s *p);
+template <typename T>
+RC<T> make_rc(const se_plan_s *p);
+template <typename T>
+cudaError_t launch_bscale(int kernel, const BSys<T> *sys, const int *blk_base, int S, int nblk, int n_rhs,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_bzero(const BSys<T> *sys, const int *zblk_base, int S, int nblk, int n_rhs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bbin(const BSys<T> *sys, const int *off, int S, int Ntot, int n_rhs, int ntiles_tot,
+                        int ncells_tot, const T *x, const T *f, Buffers &b, cudaStream_t st, int64_t *launches);
+template <typename T>
+cudaError_t launch_bspread(const BSys<T> *sys, const int4 *items, int nitems, int P, int T_, int n_rhs,
+                           const Buffers &b, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bgather(const BSys<T> *sys, const int *off, int S, int Ntot, int P, int n_rhs, const Buffers &b,
+                           const T *f, T *u, cudaStream_t st);
+template <typename T>
+cudaError_t launch_breal(int kernel, const BSys<T> *sys, const int *row_base, int S, int nrows_tot, int Ntot,
+                         int n_rhs, const Buffers &b, int *cl_sys, T *u, cudaStream_t st, int64_t *launches);
 
 se_status_t precompute(se_plan_s *p);
 cudaError_t launch_scan(int *cnt, int n, cudaStream_t st);

@@ -53,19 +53,18 @@ __device__ __forceinline__ T weight(T rel, int i0, int k, const GP<T> &g) {
     return gexp(-g.ah2 * fr * fr);
 }
 
+// The CTA's work on one spreading tile: sorted points [beg, end) (sources
+// fs[n * fstride + foff]) into the padded tile, then into grid.
 template <typename T, int NIT>
-__global__ void __launch_bounds__(NW * 32) k_spread_tile(GP<T> g, int nc, const int *__restrict__ tile_start,
-                                                         const vec4<T> *__restrict__ xs,
-                                                         const vec4<T> *__restrict__ fs,
-                                                         const vec4<T> *__restrict__ qs, T *__restrict__ grid) {
+__device__ __forceinline__ void spread_tile_body(const GP<T> &g, int tile, int beg, int end, int nc,
+                                                 const vec4<T> *__restrict__ xs, const vec4<T> *__restrict__ fs,
+                                                 int fstride, int foff, const vec4<T> *__restrict__ qs,
+                                                 T *__restrict__ grid) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T sw[NB][3][32];
     __shared__ T ssrc[NB][6];
     __shared__ int soff[NB];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    const int tile = blockIdx.x;
-    const int beg = tile_start[tile], end = tile_start[tile + 1];
-    if (beg == end) return;
     const int P = g.P, PT = g.T_ + P - 1, PT2 = PT * PT, PT3 = PT2 * PT;
     const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
     const int gx0 = tx * g.T_, gy0 = ty * g.T_, gz0 = tz * g.T_;
@@ -97,7 +96,7 @@ __global__ void __launch_bounds__(NW * 32) k_spread_tile(GP<T> g, int nc, const 
                 sw[j][2][lane] = weight(xv.z - g.x0[2], i0[2], lane, g);
             }
             if (lane < nc) {
-                const vec4<T> fv = fs[n];
+                const vec4<T> fv = fs[(size_t)n * fstride + foff];
                 ssrc[j][lane] = (nc == 6) ? stress_comp<T>(lane, fv, qs[n]) : source_comp<T>(lane, fv);
             }
             if (lane == 0) {
@@ -153,6 +152,36 @@ __global__ void __launch_bounds__(NW * 32) k_spread_tile(GP<T> g, int nc, const 
     }
 }
 
+template <typename T, int NIT>
+__global__ void __launch_bounds__(NW * 32) k_spread_tile(GP<T> g, int nc, const int *__restrict__ tile_start,
+                                                         const vec4<T> *__restrict__ xs,
+                                                         const vec4<T> *__restrict__ fs,
+                                                         const vec4<T> *__restrict__ qs, T *__restrict__ grid) {
+    const int tile = blockIdx.x;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    spread_tile_body<T, NIT>(g, tile, beg, end, nc, xs, fs, 1, 0, qs, grid);
+}
+
+// Batched: one CTA per item (system, tile of that system, right-hand side);
+// the tile's points are the system's, their sources the item's right-hand
+// side, and the grid that right-hand side's three components.
+template <typename T, int NIT>
+__global__ void __launch_bounds__(NW * 32) k_bspread_tile(const BSys<T> *__restrict__ sys,
+                                                          const int4 *__restrict__ items,
+                                                          const int *__restrict__ tile_start, int n_rhs,
+                                                          const vec4<T> *__restrict__ xs,
+                                                          const vec4<T> *__restrict__ fs) {
+    const int4 it = items[blockIdx.x];  // (system, local tile, right-hand side, -)
+    const BSys<T> &B = sys[it.x];
+    const int key = B.tile_base + it.y;
+    const int beg = tile_start[key], end = tile_start[key + 1];
+    if (beg == end) return;
+    const GP<T> g = B.g;
+    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    spread_tile_body<T, NIT>(g, it.y, beg, end, 3, xs, fs, n_rhs, it.z, nullptr, B.grid + (size_t)it.z * 3 * Mf3);
+}
+
 template <typename T>
 __global__ void k_spread_atomic(GP<T> g, int nc, int N, const vec4<T> *__restrict__ xs,
                                 const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
@@ -195,6 +224,23 @@ __global__ void k_zero_octant(T *__restrict__ grid, int Mt, int Mf, int nc) {
     if (row >= nrows) return;
     int y = row % Mt, z = (row / Mt) % Mt, c = row / ((size_t)Mt * Mt);
     T *p = grid + (size_t)c * Mf * Mf * Mf + ((size_t)z * Mf + y) * Mf;
+    for (int x = threadIdx.x; x < Mt; x += blockDim.x) p[x] = T(0);
+}
+
+// Batched: zero the octant of every grid of every system (rows of Mt values;
+// block b belongs to the system s with zblk_base[s] <= b < zblk_base[s+1]).
+template <typename T>
+__global__ void k_bzero_octant(const BSys<T> *__restrict__ sys, const int *__restrict__ zblk_base, int S,
+                               int n_rhs) {
+    const int s = find_range(zblk_base, S, (int)blockIdx.x);
+    const BSys<T> &B = sys[s];
+    const int Mt = B.g.Mt, Mf = B.g.Mf;
+    const size_t row = (size_t)(blockIdx.x - zblk_base[s]) * blockDim.y + threadIdx.y;
+    const size_t nrows = (size_t)3 * n_rhs * Mt * Mt;
+    if (row >= nrows) return;
+    const int y = row % Mt, z = (row / Mt) % Mt;
+    const size_t c = row / ((size_t)Mt * Mt);
+    T *p = B.grid + c * Mf * Mf * Mf + ((size_t)z * Mf + y) * Mf;
     for (int x = threadIdx.x; x < Mt; x += blockDim.x) p[x] = T(0);
 }
 
@@ -254,6 +300,48 @@ cudaError_t launch_spread(se_plan_s *p, cudaStream_t st, const void *xs, const v
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_bzero(const BSys<T> *sys, const int *zblk_base, int S, int nblk, int n_rhs, cudaStream_t st) {
+    k_bzero_octant<T><<<nblk, dim3(32, 8), 0, st>>>(sys, zblk_base, S, n_rhs);
+    return cudaGetLastError();
+}
+
+template <typename T, int NIT>
+static cudaError_t bspread_nit(const BSys<T> *sys, const int4 *items, int nitems, size_t smem, int n_rhs,
+                               const Buffers &b, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_bspread_tile<T, NIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e) return e;
+    k_bspread_tile<T, NIT><<<nitems, NW * 32, smem, st>>>(sys, items, b.cnt_t, n_rhs, (const vec4<T> *)b.xs_t,
+                                                          (const vec4<T> *)b.fs_t);
+    return cudaGetLastError();
+}
+
+// Batched spreading: P and the tile edge T_ are common to all systems.
+template <typename T>
+cudaError_t launch_bspread(const BSys<T> *sys, const int4 *items, int nitems, int P, int T_, int n_rhs,
+                           const Buffers &b, cudaStream_t st) {
+    const size_t PT = T_ + P - 1;
+    const size_t smem = 3 * PT * PT * PT * sizeof(T);
+    if (P > 16 || smem > 190 * 1024) return cudaErrorInvalidValue;
+    switch ((P * P + 31) / 32) {
+        case 1: return bspread_nit<T, 1>(sys, items, nitems, smem, n_rhs, b, st);
+        case 2: return bspread_nit<T, 2>(sys, items, nitems, smem, n_rhs, b, st);
+        case 3: return bspread_nit<T, 3>(sys, items, nitems, smem, n_rhs, b, st);
+        case 4: return bspread_nit<T, 4>(sys, items, nitems, smem, n_rhs, b, st);
+        case 5: return bspread_nit<T, 5>(sys, items, nitems, smem, n_rhs, b, st);
+        case 6: return bspread_nit<T, 6>(sys, items, nitems, smem, n_rhs, b, st);
+        case 7: return bspread_nit<T, 7>(sys, items, nitems, smem, n_rhs, b, st);
+        default: return bspread_nit<T, 8>(sys, items, nitems, smem, n_rhs, b, st);
+    }
+}
+
+template cudaError_t launch_bzero<float>(const BSys<float> *, const int *, int, int, int, cudaStream_t);
+template cudaError_t launch_bzero<double>(const BSys<double> *, const int *, int, int, int, cudaStream_t);
+template cudaError_t launch_bspread<float>(const BSys<float> *, const int4 *, int, int, int, int, const Buffers &,
+                                           cudaStream_t);
+template cudaError_t launch_bspread<double>(const BSys<double> *, const int4 *, int, int, int, int, const Buffers &,
+                                            cudaStream_t);
 template cudaError_t launch_spread<float>(se_plan_s *, cudaStream_t, const void *, const void *, const void *,
                                           void *, int);
 template cudaError_t launch_spread<double>(se_plan_s *, cudaStream_t, const void *, const void *, const void *,

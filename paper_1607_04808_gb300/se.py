@@ -80,6 +80,21 @@ def lib():
             L.se_plan_launch_count.restype = i64
             L.se_plan_launch_count.argtypes = [vp]
             L.se_plan_destroy.restype = i32
+            L.se_batch_create.restype = i32
+            L.se_batch_create.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                          i32, dbl, i32, ctypes.POINTER(SEParams), ctypes.POINTER(vp)]
+            L.se_batch_eval.restype = i32
+            L.se_batch_eval.argtypes = [vp, vp, vp, vp, vp]
+            L.se_batch_set_graph.restype = i32
+            L.se_batch_set_graph.argtypes = [vp, i32]
+            L.se_batch_get_params.restype = i32
+            L.se_batch_get_params.argtypes = [vp, i32, ctypes.POINTER(SEParams)]
+            L.se_batch_check.restype = i32
+            L.se_batch_check.argtypes = [vp]
+            L.se_batch_launch_count.restype = i64
+            L.se_batch_launch_count.argtypes = [vp]
+            L.se_batch_destroy.restype = i32
+            L.se_batch_destroy.argtypes = [vp]
             L.se_plan_destroy.argtypes = [vp]
             L.se_last_error.restype = ctypes.c_char_p
             L.se_last_error.argtypes = []
@@ -214,6 +229,75 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             lib().se_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent systems with several right-hand sides each (se_batch_create).
+
+    sizes[s] points of system s in the cube boxes[s] = (x0, y0, z0, L); the
+    points of all systems are concatenated in x (sumN, 3), the forces in
+    f (sumN, n_rhs, 3).
+    """
+
+    def __init__(self, kernel: str, sizes, boxes=None, n_rhs: int = 1, *, tol: float = 0.0,
+                 prec: str = "fp32", max_fft: int = 0, graph: bool = True):
+        self.kernel = kernel
+        self.sizes = [int(n) for n in sizes]
+        self.S = len(self.sizes)
+        self.R = int(n_rhs)
+        self.N = sum(self.sizes)
+        self.prec = prec
+        self.dtype = torch.float32 if prec == "fp32" else torch.float64
+        if boxes is None:
+            boxes = [(0.0, 0.0, 0.0, 1.0)] * self.S
+        flat = [float(v) for b in boxes for v in b]
+        if len(flat) != 4 * self.S:
+            raise ValueError("boxes: one (x0, y0, z0, L) per system")
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        ns = (ctypes.c_int64 * self.S)(*self.sizes)
+        bx = (ctypes.c_double * (4 * self.S))(*flat)
+        prm = SEParams(max_fft=int(max_fft))
+        h = ctypes.c_void_p()
+        _check(lib().se_batch_create(KERNELS[kernel], self.S, ns, bx, self.R, float(tol), PRECS[prec],
+                                     ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h
+        _check(lib().se_batch_set_graph(self._h, 1 if graph else 0))
+
+    def params(self, s: int) -> dict:
+        p = SEParams()
+        _check(lib().se_batch_get_params(self._h, int(s), ctypes.byref(p)))
+        return {k: getattr(p, k) for k, _ in SEParams._fields_}
+
+    def eval(self, x, f, out=None, stream=None, check=False):
+        """u for every system and right-hand side (se_batch_eval)."""
+        if not (x.is_cuda and x.dtype == self.dtype and x.is_contiguous() and x.shape == (self.N, 3)):
+            raise ValueError(f"x: expected a contiguous CUDA tensor ({self.N}, 3) of {self.dtype}")
+        shp = (self.N, self.R, 3)
+        if not (f.is_cuda and f.dtype == self.dtype and f.is_contiguous() and tuple(f.shape) == shp):
+            raise ValueError(f"f: expected a contiguous CUDA tensor {shp} of {self.dtype}")
+        if out is None:
+            out = torch.empty_like(f)
+        _check(lib().se_batch_eval(self._h, _ptr(x), _ptr(f), _ptr(out), _stream(stream)))
+        if check:
+            self.check()
+        return out
+
+    def check(self):
+        _check(lib().se_batch_check(self._h))
+
+    def launch_count(self) -> int:
+        return int(lib().se_batch_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().se_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

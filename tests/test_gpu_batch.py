@@ -1,0 +1,190 @@
+"""Batched systems (se_batch_*): every system of a batch, for every right-hand
+side, must equal the same system evaluated alone with the same parameters (to
+roundoff), and match the FP64 direct sum within the tolerance.  The full-size
+case is the 64-system, 8-right-hand-side workload (lognormal sizes around 1e4)
+checked at sampled targets of every system.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import direct
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_04808_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+
+
+def P():
+    import paper_1607_04808_gb300 as pkg
+    return pkg
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def small_batch(seed, sizes, boxes, n_rhs):
+    xs, fs = [], []
+    for s, (n, b) in enumerate(zip(sizes, boxes)):
+        x = W.uniform_points(n, seed * 100 + s, L=b[3], x0=b[:3])
+        f = W._rng(seed * 100 + s, 9).standard_normal((n, n_rhs, 3))
+        xs.append(x)
+        fs.append(f)
+    return xs, fs
+
+
+def round32(x, box):
+    """x rounded to FP32 and kept inside the half-open box."""
+    top = np.nextafter(np.float32(np.asarray(box[:3]) + box[3]), np.float32(-np.inf))
+    return np.minimum(x.astype(np.float32), top).astype(np.float64)
+
+
+def to_dev(a, prec):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32 if prec == "fp32" else torch.float64,
+                        device="cuda")
+
+
+SIZES = [300, 2500, 1, 777, 1600]
+BOXES = [(0.0, 0.0, 0.0, 1.0), (-0.5, 0.25, 2.0, 1.5), (0.0, 0.0, 0.0, 1.0), (3.0, 3.0, 3.0, 0.7),
+         (0.0, 0.0, 0.0, 1.0)]
+
+
+@pytest.mark.parametrize("kernel", ["stokeslet", "rotlet"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_matches_single_plans(kernel, prec):
+    pkg = P()
+    R = 3
+    tol = 1e-6 if prec == "fp64" else 2e-6  # FP64: P = 14 (batches need P <= 16)
+    xs, fs = small_batch(11, SIZES, BOXES, R)
+    B = pkg.Batch(kernel, SIZES, BOXES, R, tol=tol, prec=prec)
+    x = to_dev(np.concatenate(xs), prec)
+    f = to_dev(np.concatenate(fs), prec)
+    u = B.eval(x, f, check=True).double().cpu().numpy()
+    assert B.launch_count() >= 10
+    bound = 1e-12 if prec == "fp64" else 2e-6
+    for s in range(len(SIZES)):
+        prm = B.params(s)
+        plan = pkg.Plan(kernel, SIZES[s], BOXES[s], prec=prec, xi=prm["xi"], M=prm["M"], P=prm["P"],
+                        rc=prm["rc"])
+        xs_d = to_dev(xs[s], prec)
+        o0, o1 = B.offsets[s], B.offsets[s + 1]
+        for r in range(R):
+            ref = plan.eval(xs_d, to_dev(fs[s][:, r, :], prec), check=True).double().cpu().numpy()
+            got = u[o0:o1, r, :]
+            if SIZES[s] == 1:
+                # a lone point: no pair, no self term for the rotlet; the
+                # stokeslet's Fourier part cancels its self term to the tolerance
+                assert np.abs(got - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+                continue
+            assert rel_l2(got, ref) <= bound, (s, r, rel_l2(got, ref))
+        plan.close()
+    B.close()
+
+
+@pytest.mark.parametrize("kernel", ["stokeslet", "rotlet"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_vs_direct(kernel, prec):
+    pkg = P()
+    R = 2
+    tol = 1e-6 if prec == "fp64" else 2e-6
+    sizes = [400, 1200, 900]
+    boxes = [(0.0, 0.0, 0.0, 1.0), (1.0, -2.0, 0.5, 2.0), (0.0, 0.0, 0.0, 0.5)]
+    xs, fs = small_batch(12, sizes, boxes, R)
+    if prec == "fp32":
+        xs = [round32(x, b) for x, b in zip(xs, boxes)]
+        fs = [f.astype(np.float32).astype(np.float64) for f in fs]
+    B = pkg.Batch(kernel, sizes, boxes, R, tol=tol, prec=prec)
+    u = B.eval(to_dev(np.concatenate(xs), prec), to_dev(np.concatenate(fs), prec), check=True)
+    u = u.double().cpu().numpy()
+    for s in range(len(sizes)):
+        o0, o1 = B.offsets[s], B.offsets[s + 1]
+        for r in range(R):
+            ref = direct.direct(kernel, xs[s], fs[s][:, r, :])
+            err = rel_l2(u[o0:o1, r, :], ref)
+            assert err <= tol, (s, r, err)
+    B.close()
+
+
+def test_batch_graph_replay_and_recapture():
+    pkg = P()
+    R = 2
+    xs, fs = small_batch(13, [500, 800], [(0.0, 0.0, 0.0, 1.0)] * 2, R)
+    x = to_dev(np.concatenate(xs), "fp32")
+    f1 = to_dev(np.concatenate(fs), "fp32")
+    f2 = to_dev(-2.0 * np.concatenate(fs), "fp32")
+    G = pkg.Batch("stokeslet", [500, 800], None, R, tol=2e-6, prec="fp32", graph=True)
+    E = pkg.Batch("stokeslet", [500, 800], None, R, tol=2e-6, prec="fp32", graph=False)
+    ref1 = E.eval(x, f1, check=True).double().cpu().numpy()
+    out = torch.empty_like(f1)
+    a = G.eval(x, f1, out=out, check=True).double().cpu().numpy()  # capture
+    b = G.eval(x, f1, out=out, check=True).double().cpu().numpy()  # replay
+    assert rel_l2(a, ref1) <= 2e-6 and rel_l2(b, ref1) <= 2e-6
+    c = G.eval(x, f2, check=True).double().cpu().numpy()  # new pointers: re-capture
+    assert rel_l2(c, -2.0 * ref1) <= 2e-6
+    G.close()
+    E.close()
+
+
+def test_batch_rejects_unsupported():
+    pkg = P()
+    with pytest.raises(pkg.SEError):
+        pkg.Batch("stresslet", [100], None, 1)
+    with pytest.raises(pkg.SEError):
+        pkg.Batch("stokeslet", [100], None, 0)
+    with pytest.raises(pkg.SEError):
+        pkg.Batch("stokeslet", [100], None, 1, tol=1e-12, prec="fp64")  # P > 16
+
+
+def test_batch_out_of_box_flag():
+    pkg = P()
+    xs, fs = small_batch(14, [200, 300], [(0.0, 0.0, 0.0, 1.0)] * 2, 1)
+    xs[1][5] = [1.2, 0.5, 0.5]
+    B = pkg.Batch("stokeslet", [200, 300], None, 1, tol=2e-6, prec="fp32")
+    B.eval(to_dev(np.concatenate(xs), "fp32"), to_dev(np.concatenate(fs), "fp32"))
+    with pytest.raises(pkg.SEError):
+        B.check()
+    B.close()
+
+
+def test_batch_full_size_64_systems_8_rhs():
+    """The 64-system workload: sizes lognormal(ln 1e4, 1) clipped to [1e3, 1e5],
+    8 right-hand sides each, every system in its own unit cube, FP32 at 2e-6;
+    16 sampled targets per system against the FP64 direct sum."""
+    pkg = P()
+    R = 8
+    systems = W.batched_systems(64, R, 5)
+    sizes = [len(x) for x, _ in systems]
+    xs = [round32(x, (0.0, 0.0, 0.0, 1.0)) for x, _ in systems]
+    fs = [f.astype(np.float32).astype(np.float64) for _, f in systems]
+    B = pkg.Batch("stokeslet", sizes, None, R, tol=2e-6, prec="fp32")
+    u = B.eval(to_dev(np.concatenate(xs), "fp32"), to_dev(np.concatenate(fs), "fp32"), check=True)
+    u = u.double().cpu().numpy()
+    rng = np.random.default_rng(5)
+    num = den = 0.0
+    worst = 0.0
+    for s in range(64):
+        o0 = B.offsets[s]
+        idx = rng.choice(sizes[s], 16, replace=False)
+        d_s = n_s = 0.0
+        for r in range(R):
+            ref = direct.direct("stokeslet", xs[s], fs[s][:, r, :], targets=idx)
+            got = u[o0 + idx, r, :]
+            d_s += float(np.sum((got - ref) ** 2))
+            n_s += float(np.sum(ref ** 2))
+        num += d_s
+        den += n_s
+        worst = max(worst, np.sqrt(d_s / n_s))
+    assert np.sqrt(num / den) <= 2e-6, np.sqrt(num / den)
+    assert worst <= 5e-6, worst
+    B.close()
