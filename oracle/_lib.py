@@ -49,6 +49,8 @@ def lib():
             L.o1_grad_x.argtypes = [i32, i64, _D, _D, _D, _D, i64, _I64, _D]
             L.o1_grad_f.restype = None
             L.o1_grad_f.argtypes = [i32, i64, _D, _D, i64, _I64, _D]
+            L.o1_grad_fq.restype = None
+            L.o1_grad_fq.argtypes = [i64, _D, _D, _D, _D, i64, _I64, _D, _D]
             L.o_kernel_full.restype = None
             L.o_kernel_full.argtypes = [i32, i64, _D, _D]
             L.o_kernel_real.restype = None

@@ -265,6 +265,38 @@ void o1_grad_f(int kernel, int64_t N, const double *x, const double *g, int64_t 
     }
 }
 
+/* Gradients of L = sum_m g_m . u_m with respect to the stresslet strengths f
+ * and q (u_j(x_m) = sum_n T_jlk(x_m - x_n) f_nl q_nk):
+ *   gf_nl = sum_{m != n} g_mj T_jlk(x_m - x_n) q_nk,
+ *   gq_nk = sum_{m != n} g_mj T_jlk(x_m - x_n) f_nl. */
+void o1_grad_fq(int64_t N, const double *x, const double *f, const double *q, const double *g, int64_t nt,
+                const int64_t *tidx, double *gf, double *gq) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t n = tidx[t];
+        double V[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  /* V_lk = sum_m g_mj T_jlk(x_m - x_n) */
+        for (int64_t m = 0; m < N; m++) {
+            if (m == n) continue;
+            double r[3] = {x[3 * m] - x[3 * n], x[3 * m + 1] - x[3 * n + 1], x[3 * m + 2] - x[3 * n + 2]};
+            if (r[0] == 0.0 && r[1] == 0.0 && r[2] == 0.0) continue;
+            double G[3][3][3];
+            kernel_full(K_STRESSLET, r, G);
+            for (int l = 0; l < 3; l++)
+                for (int k = 0; k < 3; k++)
+                    for (int j = 0; j < 3; j++) V[l][k] += g[3 * m + j] * G[j][l][k];
+        }
+        for (int l = 0; l < 3; l++) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < 3; k++) {
+                a += V[l][k] * q[3 * n + k];
+                b += V[k][l] * f[3 * n + k];
+            }
+            gf[3 * t + l] = a;
+            gq[3 * t + l] = b;
+        }
+    }
+}
+
 /* Single-kernel evaluation helpers (vectorised over r) for tests. */
 void o_kernel_full(int kernel, int64_t n, const double *r, double *G27) {
     for (int64_t i = 0; i < n; i++) {

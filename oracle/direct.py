@@ -51,6 +51,17 @@ def grad_f(kernel, x, g, targets=None):
     return out
 
 
+def grad_fq(x, f, q, g, targets=None):
+    """Stresslet: d/df_n and d/dq_n of L = sum_m g_m . u_m (exact direct sums)."""
+    x, f, q, g = f64(x), f64(f), f64(q), f64(g)
+    tidx = np.arange(len(x), dtype=np.int64) if targets is None else np.ascontiguousarray(
+        np.asarray(targets, dtype=np.int64))
+    gf = np.zeros((len(tidx), 3))
+    gq = np.zeros((len(tidx), 3))
+    lib().o1_grad_fq(len(x), dptr(x), dptr(f), dptr(q), dptr(g), len(tidx), iptr(tidx), dptr(gf), dptr(gq))
+    return gf, gq
+
+
 def kernel_full(kernel, r):
     """K(r) as (n, 3, 3, 3) (S and Omega use [..., 0])."""
     r = f64(np.atleast_2d(r))

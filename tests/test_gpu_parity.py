@@ -292,3 +292,69 @@ def test_full_size_fp64_stokeslet_sampled():
     idx = np.random.default_rng(1).choice(N, 96, replace=False)
     ref = direct.direct("stokeslet", x, f, targets=idx)
     assert rel_l2(u[idx], ref) <= 1e-10
+
+
+def test_full_size_fp32_stresslet_blobs_sampled():
+    """N = 5e5 stresslet, 16 Gaussian blobs plus a uniform background, FP32 at
+    2e-6; 256 sampled targets against the exact direct sum."""
+    N = 500_000
+    x, f, q = W.stresslet_blobs(N, 2)
+    x32, f32, q32 = as32(x), as32(f), as32(q)
+    x32 = np.minimum(x32, np.nextafter(np.float32(1.0), np.float32(0)))
+    u, prm = gpu_eval("stresslet", x32, f32, q32, "fp32", tol=2e-6)
+    idx = np.random.default_rng(2).choice(N, 256, replace=False)
+    ref = direct.direct("stresslet", x32, f32, q32, targets=idx)
+    assert rel_l2(u[idx], ref) <= 2e-6
+
+
+def test_full_size_fp32_rotlet_backward_sampled():
+    """N = 2e5 rotlet, FP32 forward and backward (grid recomputed): u, dL/df and
+    dL/dx at 256 sampled points against the exact direct sums, and dL/dx
+    against central differences (h = 1e-4, FP64) of the exact L at three
+    coordinates whose nearest neighbour is farther than 50 h."""
+    N = 200_000
+    x, f, g = W.rotlet_uniform(N, 3)
+    x32, f32, g32 = as32(x), as32(f), as32(g)
+    x32 = np.minimum(x32, np.nextafter(np.float32(1.0), np.float32(0)))
+    pkg = P()
+    plan = pkg.Plan("rotlet", N, BOX, prec="fp32", tol=2e-6)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")  # noqa: E731
+    u = plan.eval(t(x32), t(f32), check=True).double().cpu().numpy()
+    gf, gx = plan.backward(t(x32), t(f32), t(g32))
+    plan.check()
+    gf, gx = gf.double().cpu().numpy(), gx.double().cpu().numpy()
+    plan.close()
+    idx = np.random.default_rng(3).choice(N, 256, replace=False)
+    assert rel_l2(u[idx], direct.direct("rotlet", x32, f32, targets=idx)) <= 2e-6
+    assert rel_l2(gf[idx], direct.grad_f("rotlet", x32, g32, targets=idx)) <= 2e-6
+    ref_gx = direct.grad_x("rotlet", x32, f32, g32, targets=idx)
+    assert rel_l2(gx[idx], ref_gx) <= 2e-5
+    # central differences of L restricted to the terms that involve point p,
+    # L_p(x_p) = g_p . u_p + f_p . (K^T g)_p, at h = 1e-4 and h/2 combined by
+    # Richardson extrapolation (the O(h^2) term of a nearest neighbour at 50 h
+    # alone would be about 1e-3 relative)
+    h = 1e-4
+
+    def L_p(p_, a, delta):
+        xx = x32.copy()
+        xx[p_, a] += delta
+        up = direct.direct("rotlet", xx, f32, targets=[p_])[0]
+        kg = direct.grad_f("rotlet", xx, g32, targets=[p_])[0]
+        return float(g32[p_] @ up + f32[p_] @ kg)
+
+    scale = np.sqrt(np.mean(ref_gx ** 2))
+    checked = 0
+    for p_ in idx:
+        d = np.sqrt(np.sum((x32 - x32[p_]) ** 2, axis=1))
+        d[p_] = np.inf
+        if d.min() <= 50 * h:
+            continue
+        a = checked % 3
+        d1 = (L_p(p_, a, h) - L_p(p_, a, -h)) / (2 * h)
+        d2 = (L_p(p_, a, h / 2) - L_p(p_, a, -h / 2)) / h
+        fd = (4 * d2 - d1) / 3
+        assert abs(gx[p_, a] - fd) <= 5e-5 * scale, (p_, a, gx[p_, a], fd)
+        checked += 1
+        if checked == 3:
+            break
+    assert checked == 3

@@ -163,6 +163,31 @@ def test_direct_gradients_fd(kernel):
                 assert abs(fd - gf[p, a]) <= 1e-10 * max(1.0, abs(fd))
 
 
+def test_direct_stresslet_strength_gradients():
+    """O1 stresslet gradients in f and q: L is linear in each f_p and each q_p, so a
+    unit step gives the derivative exactly, and Euler's relation for the
+    bilinear L gives sum f.dL/df = sum q.dL/dq = L."""
+    x, f = W.stokeslet_uniform(30, 16)
+    q = W.unit_vectors(30, 16)
+    g = W.normal_vectors(30, 17)
+    L0 = np.sum(g * direct.direct(1, x, f, q))
+    gf, gq = direct.grad_fq(x, f, q, g)
+    for p in (0, 13, 29):
+        for a in range(3):
+            fp = f.copy()
+            fp[p, a] += 1.0
+            qp = q.copy()
+            qp[p, a] += 1.0
+            dfd = np.sum(g * direct.direct(1, x, fp, q)) - L0
+            dqd = np.sum(g * direct.direct(1, x, f, qp)) - L0
+            assert abs(dfd - gf[p, a]) <= 1e-10 * max(1.0, abs(dfd))
+            assert abs(dqd - gq[p, a]) <= 1e-10 * max(1.0, abs(dqd))
+    assert abs(np.sum(f * gf) - L0) <= 1e-10 * abs(L0)
+    assert abs(np.sum(q * gq) - L0) <= 1e-10 * abs(L0)
+    sub = direct.grad_fq(x, f, q, g, targets=[4, 9])
+    np.testing.assert_allclose(sub[0], gf[[4, 9]], rtol=1e-14, atol=0)
+
+
 # ------------------------------------------------------ Ewald split (Section 3)
 
 def _phi_hasimoto(xi):
