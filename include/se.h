@@ -102,13 +102,24 @@ se_status_t se_eval(se_plan_t plan, const void *x, const void *f, const void *q,
 se_status_t se_eval_host(se_plan_t plan, const void *x_host, const void *f_host, const void *q_host,
                          void *u_host, void *stream);
 
-/* Gradients of L = sum_m grad_u_m . u_m for the stokeslet and the rotlet:
- *   grad_f_n = sum_m K(x_m - x_n)^T grad_u_m      (the transposed sum; equal to the
- *              same kernel applied to grad_u, since both operators are symmetric)
- *   grad_x_p = d L / d x_p                          (Gaussian-derivative quadrature on the
- *              forward and adjoint grids plus the real-space kernel derivative)
- * Either output may be NULL.  The forward grid is recomputed, not stored.
- * Returns SE_ERR_NOT_SUPPORTED for the stresslet. */
+/* Gradients of L = sum_m grad_u_m . u_m (no counterpart in the paper; derived
+ * from the Fourier representation of Section 5.2, eqs. Hx and u_integr, and the
+ * real-space kernels of Section 3.2):
+ *   stokeslet, rotlet: grad_f_n = sum_m K(x_m - x_n)^T grad_u_m (the same SE
+ *              operator applied to grad_u, since both operators are symmetric)
+ *   stresslet: grad_f_n,l = V_lk(x_n) q_n,k, grad_q_n,k = V_lk(x_n) f_n,l with the
+ *              adjoint field V_lk(y) = sum_m T_jlk(x_m - y) grad_u_m,j (the
+ *              negated stresslet symbol on 3 -> 6 grids)
+ *   grad_x_p = d L / d x_p: Gaussian-derivative quadrature on the forward grid
+ *              and on the adjoint grid, plus the derivative of the real-space
+ *              kernel (the self term does not depend on x).
+ * Same arrays as se_eval (q: the stresslet's q, else NULL); grad_u, grad_f,
+ * grad_q, grad_x are N x 3 device arrays in the plan's precision, overwritten.
+ * Any output may be NULL.  The forward grid is recomputed, not stored.
+ * se_eval_backward is se_eval_backward_q without grad_q.  grad_q must be NULL
+ * for the stokeslet and the rotlet (SE_ERR_INVALID_ARG). */
+se_status_t se_eval_backward_q(se_plan_t plan, const void *x, const void *f, const void *q, const void *grad_u,
+                               void *grad_f, void *grad_q, void *grad_x, void *stream);
 se_status_t se_eval_backward(se_plan_t plan, const void *x, const void *f, const void *q,
                              const void *grad_u, void *grad_f, void *grad_x, void *stream);
 

@@ -100,32 +100,51 @@ se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaS
 }
 
 template <typename T>
-se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *gu, T *gf, T *gx, cudaStream_t st) {
+se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *q, const T *gu, T *gf, T *gq, T *gx,
+                       cudaStream_t st) {
     p->last_stream = st;
     p->launches = 0;
     const size_t Mf3 = (size_t)p->Mf * p->Mf * p->Mf;
+    const bool stress = (p->kernel == SE_STRESSLET);
     if (!p->wgrid2) {
-        cudaError_t e = cudaMalloc(&p->wgrid2, 3 * Mf3 * sizeof(T));
+        cudaError_t e = cudaMalloc(&p->wgrid2, (stress ? 6 : 3) * Mf3 * sizeof(T));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(SE_ERR_OOM, "backward: adjoint grid allocation failed");
         }
     }
-    // adjoint grid w' = A^T spread(g); the stokeslet and rotlet multipliers are
-    // their own transposes (A_jl(-k) = A_lj(k))
+    // adjoint field from the upstream gradient g: w' = K^T g on the grid (the
+    // stokeslet and rotlet multipliers are their own transposes); for the
+    // stresslet the symmetric tensor field V_lk = sum_m T_jlk(x_m - y) g_mj
     CK(launch_bin<T>(p, x, gu, nullptr, st));
-    se_status_t s = fourier_grid<T>(p, st, p->wgrid2, 3, nullptr);
-    if (s != SE_OK) return s;
-    if (gf) {
-        // transposed operator applied to g: same kernel (S and Omega are symmetric operators)
-        CK(launch_gather<T>(p, st, p->wgrid2, gu, gf));
-        CK(launch_real<T>(p, st, gf));
+    se_status_t s;
+    if (stress) {
+        const size_t nk = (size_t)p->Mf * p->Mf * (p->Mf / 2 + 1);
+        CK(launch_spread<T>(p, st, p->b.xs_t, p->b.fs_t, nullptr, p->grid, 3));
+        CF(cufftSetStream(p->fwd3, st));
+        CF(exec_fwd<T>(p->fwd3, p->grid, p->spec));
+        CK(launch_scale_adj_stresslet<T>(p, st, p->spec));
+        CF(cufftSetStream(p->inv, st));
+        CF(exec_inv<T>(p->inv, p->spec, p->wgrid2));
+        CF(exec_inv<T>(p->inv, (cplx<T> *)p->spec + 3 * nk, (T *)p->wgrid2 + 3 * Mf3));
+        if (gf || gq) {
+            CK(launch_gather_adjT<T>(p, st, p->wgrid2, f, q, gf, gq));
+            CK(launch_real_adjT<T>(p, st, f, q, gf, gq));
+        }
+    } else {
+        s = fourier_grid<T>(p, st, p->wgrid2, 3, nullptr);
+        if (s != SE_OK) return s;
+        if (gf) {
+            // transposed operator applied to g: same kernel (S and Omega are symmetric operators)
+            CK(launch_gather<T>(p, st, p->wgrid2, gu, gf));
+            CK(launch_real<T>(p, st, gf));
+        }
     }
     if (gx) {
-        CK(launch_bin<T>(p, x, f, nullptr, st));
-        s = fourier_grid<T>(p, st, p->wgrid, 3, nullptr);
+        CK(launch_bin<T>(p, x, f, q, st));
+        s = fourier_grid<T>(p, st, p->wgrid, p->nc, nullptr);
         if (s != SE_OK) return s;
-        CK(launch_gather_grad<T>(p, st, p->wgrid, p->wgrid2, f, gu, gx));
+        CK(launch_gather_grad<T>(p, st, p->wgrid, p->wgrid2, f, q, gu, gx));
         CK(launch_real_grad<T>(p, st, gu, gx));
     }
     return SE_OK;
@@ -184,17 +203,23 @@ extern "C" se_status_t se_eval_host(se_plan_t p, const void *x, const void *f, c
     return SE_OK;
 }
 
-extern "C" se_status_t se_eval_backward(se_plan_t p, const void *x, const void *f, const void *q, const void *grad_u,
-                                        void *grad_f, void *grad_x, void *stream) {
-    (void)q;
+extern "C" se_status_t se_eval_backward_q(se_plan_t p, const void *x, const void *f, const void *q,
+                                          const void *grad_u, void *grad_f, void *grad_q, void *grad_x,
+                                          void *stream) {
     if (!p || !x || !f || !grad_u) return fail(SE_ERR_INVALID_ARG, "se_eval_backward: NULL pointer");
-    if (p->kernel == SE_STRESSLET)
-        return fail(SE_ERR_NOT_SUPPORTED, "se_eval_backward: the stresslet gradient is not implemented");
-    if (!grad_f && !grad_x) return SE_OK;
+    if (p->kernel == SE_STRESSLET && !q) return fail(SE_ERR_INVALID_ARG, "se_eval_backward: the stresslet needs q");
+    if (p->kernel != SE_STRESSLET && grad_q)
+        return fail(SE_ERR_INVALID_ARG, "se_eval_backward: grad_q is for the stresslet only");
+    if (!grad_f && !grad_q && !grad_x) return SE_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (p->prec == SE_FP32)
-        return backward_t<float>(p, (const float *)x, (const float *)f, (const float *)grad_u, (float *)grad_f,
-                                 (float *)grad_x, st);
-    return backward_t<double>(p, (const double *)x, (const double *)f, (const double *)grad_u, (double *)grad_f,
-                              (double *)grad_x, st);
+        return backward_t<float>(p, (const float *)x, (const float *)f, (const float *)q, (const float *)grad_u,
+                                 (float *)grad_f, (float *)grad_q, (float *)grad_x, st);
+    return backward_t<double>(p, (const double *)x, (const double *)f, (const double *)q, (const double *)grad_u,
+                              (double *)grad_f, (double *)grad_q, (double *)grad_x, st);
+}
+
+extern "C" se_status_t se_eval_backward(se_plan_t p, const void *x, const void *f, const void *q, const void *grad_u,
+                                        void *grad_f, void *grad_x, void *stream) {
+    return se_eval_backward_q(p, x, f, q, grad_u, grad_f, nullptr, grad_x, stream);
 }

@@ -127,16 +127,68 @@ __global__ void __launch_bounds__(WPB * 32) k_bgather(const BSys<T> *__restrict_
     gather_point<T, NIT>(g, xs[n], perm[n], B.wgrid, n_rhs, f_orig, B.self_coef, u, lane, sw_all[wib]);
 }
 
+// Stresslet backward, strengths: the adjoint tensor field V_lk (6 grids: xx, yy,
+// zz, xy, xz, yz) gathered at each point and contracted,
+//   gf_p,l = V_lk(x_p) q_p,k,   gq_p,k = V_lk(x_p) f_p,l  (V symmetric).
+// Outputs are overwritten (either may be NULL).
+template <typename T>
+__global__ void __launch_bounds__(WPB * 32) k_gather_adjT(GP<T> g, int N, const vec4<T> *__restrict__ xs,
+                                                          const int *__restrict__ perm, const T *__restrict__ V,
+                                                          const T *__restrict__ f_orig,
+                                                          const T *__restrict__ q_orig, T *__restrict__ gf,
+                                                          T *__restrict__ gq) {
+    __shared__ T sw_all[WPB][3][32];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = blockIdx.x * WPB + wib;
+    if (n >= N) return;
+    T(*sw)[32] = sw_all[wib];
+    const int P = g.P, P2 = P * P;
+    int i0[3];
+    T fr[3];
+    warp_weights<T>(xs[n], g, lane, i0, sw, fr);
+    const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+    const T *base = V + ((size_t)i0[2] * Mf + i0[1]) * Mf + i0[0];
+    T acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int idx = lane; idx < P2; idx += 32) {
+        const int ky = idx / P, kx = idx - ky * P;
+        const T wxy = sw[0][kx] * sw[1][ky];
+        const T *col = base + (size_t)ky * Mf + kx;
+        T a[6] = {0, 0, 0, 0, 0, 0};
+        for (int kz = 0; kz < P; kz++) {
+            const T wz = sw[2][kz];
+            const T *pz = col + kz * Mf2;
+#pragma unroll
+            for (int c = 0; c < 6; c++) a[c] += __ldg(pz + c * Mf3) * wz;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; c++) acc[c] += a[c] * wxy;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; c++) acc[c] = warp_sum(acc[c]);
+    if (lane < 3) {
+        const int m = perm[n];
+        // row `lane` of the symmetric V: (xx, xy, xz), (xy, yy, yz), (xz, yz, zz)
+        const T row[3] = {lane == 0 ? acc[0] : (lane == 1 ? acc[3] : acc[4]),
+                          lane == 0 ? acc[3] : (lane == 1 ? acc[1] : acc[5]),
+                          lane == 0 ? acc[4] : (lane == 1 ? acc[5] : acc[2])};
+        if (gf) gf[3 * m + lane] = row[0] * q_orig[3 * m] + row[1] * q_orig[3 * m + 1] + row[2] * q_orig[3 * m + 2];
+        if (gq) gq[3 * m + lane] = row[0] * f_orig[3 * m] + row[1] * f_orig[3 * m + 1] + row[2] * f_orig[3 * m + 2];
+    }
+}
+
 // Position gradient of the Fourier part of L = sum_m g_m . u_m:
 //   gx_p = h^3 sum_i [g_p . w_i + f_p . w'_i] grad Gauss(x_p - y_i),
 // grad Gauss(r) = -(4 xi^2/eta) r Gauss(r); w (forward grid from f) and w'
 // (adjoint grid from g) already carry h^3 and the prefactors.  In grid units
 // x - y = (t - i) h, so d/dx_d Gauss = -2 a h (fr_d - k) Gauss.
-template <typename T>
+// Stresslet (NA = 6): w' is the adjoint tensor field V (xx, yy, zz, xy, xz,
+// yz) and f_p . w' becomes sum_lk f_p,l q_p,k V_lk.
+template <typename T, int NA>
 __global__ void __launch_bounds__(WPB * 32) k_gather_grad(GP<T> g, T c_grad, int N, const vec4<T> *__restrict__ xs,
                                                           const int *__restrict__ perm,
                                                           const T *__restrict__ wf, const T *__restrict__ wa,
                                                           const T *__restrict__ f_orig,
+                                                          const T *__restrict__ q_orig,
                                                           const T *__restrict__ g_orig, T *__restrict__ gx) {
     __shared__ T sw_all[WPB][3][32];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -150,6 +202,15 @@ __global__ void __launch_bounds__(WPB * 32) k_gather_grad(GP<T> g, T c_grad, int
     const int m = perm[n];
     const T gm[3] = {g_orig[3 * m], g_orig[3 * m + 1], g_orig[3 * m + 2]};
     const T fm[3] = {f_orig[3 * m], f_orig[3 * m + 1], f_orig[3 * m + 2]};
+    T cm[NA];
+    if (NA == 3) {
+        for (int c = 0; c < NA; c++) cm[c] = fm[c % 3];
+    } else {
+        const T qm[3] = {q_orig[3 * m], q_orig[3 * m + 1], q_orig[3 * m + 2]};
+        const int L_[6] = {0, 1, 2, 0, 0, 1}, K_[6] = {0, 1, 2, 1, 2, 2};
+        for (int c = 0; c < NA; c++)
+            cm[c] = (c < 3) ? fm[c] * qm[c] : fm[L_[c]] * qm[K_[c]] + fm[K_[c]] * qm[L_[c]];
+    }
     const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
     T acc[3] = {0, 0, 0};
     for (int idx = lane; idx < P2; idx += 32) {
@@ -161,8 +222,9 @@ __global__ void __launch_bounds__(WPB * 32) k_gather_grad(GP<T> g, T c_grad, int
         for (int kz = 0; kz < P; kz++) {
             T wz = sw[2][kz];
             size_t o = off + kz * Mf2;
-            T s = gm[0] * __ldg(wf + o) + gm[1] * __ldg(wf + o + Mf3) + gm[2] * __ldg(wf + o + 2 * Mf3) +
-                  fm[0] * __ldg(wa + o) + fm[1] * __ldg(wa + o + Mf3) + fm[2] * __ldg(wa + o + 2 * Mf3);
+            T s = gm[0] * __ldg(wf + o) + gm[1] * __ldg(wf + o + Mf3) + gm[2] * __ldg(wf + o + 2 * Mf3);
+#pragma unroll
+            for (int c = 0; c < NA; c++) s += cm[c] * __ldg(wa + o + c * Mf3);
             s0 += s * wz;
             sz += s * wz * (fr[2] - (T)kz);
         }
@@ -206,12 +268,18 @@ cudaError_t launch_gather(se_plan_s *p, cudaStream_t st, const void *wgrid, cons
 
 template <typename T>
 cudaError_t launch_gather_grad(se_plan_s *p, cudaStream_t st, const void *w_fwd, const void *w_adj,
-                               const T *f_orig, const T *g_orig, T *gx) {
+                               const T *f_orig, const T *q_orig, const T *g_orig, T *gx) {
     int N = (int)p->N;
     T c_grad = (T)(-2.0 * p->geom.a * p->h);
-    k_gather_grad<T><<<(N + WPB - 1) / WPB, WPB * 32, 0, st>>>(gp<T>(p), c_grad, N, (const vec4<T> *)p->b.xs_t,
-                                                               p->b.perm_t, (const T *)w_fwd, (const T *)w_adj,
-                                                               f_orig, g_orig, gx);
+    const unsigned gs = (N + WPB - 1) / WPB;
+    if (p->kernel == SE_STRESSLET)
+        k_gather_grad<T, 6><<<gs, WPB * 32, 0, st>>>(gp<T>(p), c_grad, N, (const vec4<T> *)p->b.xs_t, p->b.perm_t,
+                                                     (const T *)w_fwd, (const T *)w_adj, f_orig, q_orig, g_orig,
+                                                     gx);
+    else
+        k_gather_grad<T, 3><<<gs, WPB * 32, 0, st>>>(gp<T>(p), c_grad, N, (const vec4<T> *)p->b.xs_t, p->b.perm_t,
+                                                     (const T *)w_fwd, (const T *)w_adj, f_orig, q_orig, g_orig,
+                                                     gx);
     p->launches++;
     return cudaGetLastError();
 }
@@ -239,11 +307,25 @@ template cudaError_t launch_bgather<float>(const BSys<float> *, const int *, int
                                            const float *, float *, cudaStream_t);
 template cudaError_t launch_bgather<double>(const BSys<double> *, const int *, int, int, int, int, const Buffers &,
                                             const double *, double *, cudaStream_t);
+template <typename T>
+cudaError_t launch_gather_adjT(se_plan_s *p, cudaStream_t st, const void *V, const T *f_orig, const T *q_orig,
+                               T *gf, T *gq) {
+    const int N = (int)p->N;
+    k_gather_adjT<T><<<(N + WPB - 1) / WPB, WPB * 32, 0, st>>>(gp<T>(p), N, (const vec4<T> *)p->b.xs_t, p->b.perm_t,
+                                                              (const T *)V, f_orig, q_orig, gf, gq);
+    p->launches++;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gather_adjT<float>(se_plan_s *, cudaStream_t, const void *, const float *,
+                                               const float *, float *, float *);
+template cudaError_t launch_gather_adjT<double>(se_plan_s *, cudaStream_t, const void *, const double *,
+                                                const double *, double *, double *);
 template cudaError_t launch_gather<float>(se_plan_s *, cudaStream_t, const void *, const float *, float *);
 template cudaError_t launch_gather<double>(se_plan_s *, cudaStream_t, const void *, const double *, double *);
 template cudaError_t launch_gather_grad<float>(se_plan_s *, cudaStream_t, const void *, const void *,
-                                               const float *, const float *, float *);
+                                               const float *, const float *, const float *, float *);
 template cudaError_t launch_gather_grad<double>(se_plan_s *, cudaStream_t, const void *, const void *,
-                                                const double *, const double *, double *);
+                                                const double *, const double *, const double *, double *);
 
 }  // namespace se

@@ -510,11 +510,18 @@ __global__ void k_bcluster_fill(int nrows_tot, const BSys<T> *__restrict__ sys, 
 // candidates of the target's rows 32 at a time, those inside the cutoff are
 // appended to a per-warp queue, and every full queue of 32 pairs is evaluated
 // with all lanes busy.
-template <typename T, int KERNEL>
+// ADJ (stresslet backward, fs holding the upstream gradient g in cell order):
+// the strength gradients of the real-space part, for target p
+//   u[p]  += gf_p = -sum_m T^R(x_p - x_m)(g_m, q_p),
+//   gq[p] += gq_p = -sum_m T^R(x_p - x_m)(g_m, f_p)
+// (T^R(x_m - x_p) = -T^R(x_p - x_m); T^R(r)(a, b)_j = T^R_jlk a_l b_k).
+template <typename T, int KERNEL, bool ADJ = false>
 __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, const vec4<T> *__restrict__ xs,
                                                   const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
                                                   const int *__restrict__ cell_start, const int *__restrict__ perm,
-                                                  T *__restrict__ u, int *__restrict__ status) {
+                                                  T *__restrict__ u, int *__restrict__ status,
+                                                  const T *__restrict__ f_orig = nullptr,
+                                                  const T *__restrict__ q_orig = nullptr, T *__restrict__ gq = nullptr) {
     constexpr int WPB = 8;
     __shared__ vec4<T> qd_all[WPB][QCAP];
     __shared__ int qn_all[WPB][QCAP];
@@ -527,15 +534,26 @@ __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, cons
     int2 *seg = seg_all[wib];
     const vec4<T> xt = xs[t];
     const int nrows = row_segments(g, rk, xt, cell_start, lane, seg);
-    T acc[3] = {0, 0, 0};
+    T acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
     int cnt = 0;
     bool coinc = false;
     const unsigned lt = (1u << lane) - 1u;
     vec4<T> zero4;
     zero4.x = zero4.y = zero4.z = zero4.w = 0;
+    vec4<T> fp4 = zero4, qp4 = zero4;
+    if (ADJ) {
+        const int mp = perm[t];
+        fp4.x = f_orig[3 * mp]; fp4.y = f_orig[3 * mp + 1]; fp4.z = f_orig[3 * mp + 2];
+        qp4.x = q_orig[3 * mp]; qp4.y = q_orig[3 * mp + 1]; qp4.z = q_orig[3 * mp + 2];
+    }
     auto eval = [&](int slot) {
         const vec4<T> v = qd[slot];
         const int m = qn[slot];
+        if (ADJ) {
+            pair<T, SE_STRESSLET>(rk, v.x, v.y, v.z, v.w, fs[m], qp4, acc);
+            pair<T, SE_STRESSLET>(rk, v.x, v.y, v.z, v.w, fs[m], fp4, acc2);
+            return;
+        }
         const vec4<T> qv = (KERNEL == SE_STRESSLET) ? qs[m] : zero4;
         pair<T, KERNEL>(rk, v.x, v.y, v.z, v.w, fs[m], qv, acc);
     };
@@ -580,17 +598,27 @@ __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, cons
         }
     }
     if (lane < cnt) eval(lane);
-    double tot[3];
+    double tot[3], tot2[3];
     for (int d = 0; d < 3; d++) {
-        double v = (double)acc[d];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        double v = (double)acc[d], w = (double)acc2[d];
+        for (int o = 16; o > 0; o >>= 1) {
+            v += __shfl_xor_sync(FULL, v, o);
+            if (ADJ) w += __shfl_xor_sync(FULL, w, o);
+        }
         tot[d] = v;
+        tot2[d] = w;
     }
     if (__any_sync(FULL, coinc) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
     if (lane < 3) {
         const int m = perm[t];
         const double v = lane == 0 ? tot[0] : (lane == 1 ? tot[1] : tot[2]);
-        u[3 * m + lane] = (T)((double)u[3 * m + lane] + v);
+        if (ADJ) {
+            const double w = lane == 0 ? tot2[0] : (lane == 1 ? tot2[1] : tot2[2]);
+            if (u) u[3 * m + lane] = (T)((double)u[3 * m + lane] - v);
+            if (gq) gq[3 * m + lane] = (T)((double)gq[3 * m + lane] - w);
+        } else {
+            u[3 * m + lane] = (T)((double)u[3 * m + lane] + v);
+        }
     }
 }
 
@@ -614,7 +642,7 @@ __device__ __forceinline__ double s_rsqrt(double v) { return rsqrt(v); }
 
 template <typename T, int KERNEL>
 __global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, const vec4<T> *__restrict__ xs,
-                                                   const vec4<T> *__restrict__ fs,
+                                                   const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
                                                    const int *__restrict__ cell_start,
                                                    const int *__restrict__ perm, const T *__restrict__ g_orig,
                                                    T *__restrict__ gx) {
@@ -630,6 +658,8 @@ __global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, con
     int2 *seg = seg_all[wib];
     const vec4<T> xt = xs[t];
     const vec4<T> fp = fs[t];
+    vec4<T> qp;
+    if (KERNEL == SE_STRESSLET) qp = qs[t];
     const int mp = perm[t];
     const T gp_[3] = {g_orig[3 * mp], g_orig[3 * mp + 1], g_orig[3 * mp + 2]};
     const int nrows = row_segments(g, rk, xt, cell_start, lane, seg);
@@ -664,6 +694,39 @@ __global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, con
             const T rad = (ap * (gpf + gnf) + bp * (gpr * rfn + gnr * rfp)) * rinv;
             for (int a = 0; a < 3; a++)
                 acc[a] += rad * d[a] + b * (gp_[a] * rfn + f_n[a] * gpr + gn[a] * rfp + f_p[a] * gnr);
+        } else if (KERNEL == SE_STRESSLET) {
+            // Phi(r; g, f, q) = T^R_jlk g_j f_l q_k = a (g.r)(f.r)(q.r) + b [(g.f)(q.r) + (f.q)(g.r) + (q.g)(f.r)],
+            // a = t1 / rho^5, b = xi^2 t2 / rho with t1, t2 the stresslet radial functions of x = xi rho,
+            // dt1/drho = 8 c1 x^4 e, dt2/drho = 2 c1 (1 - 2 x^2) e; gx_p += grad Phi(r; g_p, f_n, q_n)
+            // - grad Phi(r; g_n, f_p, q_p)
+            const vec4<T> qn4 = qs[n];
+            const T xx = rk.xi * r, x2 = xx * xx;
+            const T G2 = c1 * r * e;
+            const T t1 = -T(2) * (T(3) * ec + G2 * (T(3) + T(2) * x2));
+            const T t2 = T(2) * G2;
+            const T dt1 = T(8) * c1 * x2 * x2 * e;
+            const T dt2 = T(2) * c1 * (T(1) - T(2) * x2) * e;
+            const T r5 = rinv2 * rinv2 * rinv;
+            const T aT = t1 * r5;
+            const T apT = (dt1 - T(5) * t1 * rinv) * r5 * rinv;
+            const T bT = rk.xi2 * t2 * rinv;
+            const T bpT = rk.xi2 * (dt2 - t2 * rinv) * rinv2;
+            auto gphi = [&](const T gv[3], const T fv[3], const T qv[3], T sgn) {
+                const T gd = gv[0] * d[0] + gv[1] * d[1] + gv[2] * d[2];
+                const T fd = fv[0] * d[0] + fv[1] * d[1] + fv[2] * d[2];
+                const T qd = qv[0] * d[0] + qv[1] * d[1] + qv[2] * d[2];
+                const T gf = gv[0] * fv[0] + gv[1] * fv[1] + gv[2] * fv[2];
+                const T fq = fv[0] * qv[0] + fv[1] * qv[1] + fv[2] * qv[2];
+                const T qg = qv[0] * gv[0] + qv[1] * gv[1] + qv[2] * gv[2];
+                const T cr = apT * gd * fd * qd + bpT * (gf * qd + fq * gd + qg * fd);
+                for (int a = 0; a < 3; a++)
+                    acc[a] += sgn * (cr * d[a] + aT * (fd * qd * gv[a] + gd * qd * fv[a] + gd * fd * qv[a]) +
+                                     bT * (gf * qv[a] + fq * gv[a] + qg * fv[a]));
+            };
+            const T f_n[3] = {fn.x, fn.y, fn.z}, q_n[3] = {qn4.x, qn4.y, qn4.z};
+            const T f_p[3] = {fp.x, fp.y, fp.z}, q_p[3] = {qp.x, qp.y, qp.z};
+            gphi(gp_, f_n, q_n, T(1));
+            gphi(gn, f_p, q_p, T(-1));
         } else {
             T c[3];
             c[0] = (gp_[1] * fn.z - gp_[2] * fn.y) - (gn[1] * fp.z - gn[2] * fp.y);
@@ -875,18 +938,36 @@ cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *
     unsigned gs = (N + 7) / 8;
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r;
     const GP<T> &g = gp<T>(p);
+    const vec4<T> *qs = (const vec4<T> *)p->b.qs_r;
     if (p->kernel == SE_STOKESLET)
-        k_real_grad<T, SE_STOKESLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
+        k_real_grad<T, SE_STOKESLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
     else if (p->kernel == SE_ROTLET)
-        k_real_grad<T, SE_ROTLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
+        k_real_grad<T, SE_ROTLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
     else
-        return cudaErrorInvalidValue;
+        k_real_grad<T, SE_STRESSLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, g_orig,
+                                                          gx);
     p->launches++;
     return cudaGetLastError();
 }
 
 template cudaError_t launch_real<float>(se_plan_s *, cudaStream_t, float *);
 template cudaError_t launch_real<double>(se_plan_s *, cudaStream_t, double *);
+template <typename T>
+cudaError_t launch_real_adjT(se_plan_s *p, cudaStream_t st, const T *f_orig, const T *q_orig, T *gf, T *gq) {
+    const int N = (int)p->N;
+    const RC<T> rk = make_rc<T>(p);
+    if (rk.reach > 5) return cudaErrorInvalidValue;
+    k_real_cmp<T, SE_STRESSLET, true><<<(N + 7) / 8, 256, 0, st>>>(
+        gp<T>(p), rk, N, (const vec4<T> *)p->b.xs_r, (const vec4<T> *)p->b.fs_r, nullptr, p->b.cnt_r,
+        p->b.perm_r, gf, p->b.status, f_orig, q_orig, gq);
+    p->launches++;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_real_adjT<float>(se_plan_s *, cudaStream_t, const float *, const float *, float *,
+                                             float *);
+template cudaError_t launch_real_adjT<double>(se_plan_s *, cudaStream_t, const double *, const double *, double *,
+                                              double *);
 template cudaError_t launch_real_grad<float>(se_plan_s *, cudaStream_t, const float *, float *);
 template cudaError_t launch_real_grad<double>(se_plan_s *, cudaStream_t, const double *, double *);
 

@@ -110,6 +110,50 @@ __global__ void k_scale(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__re
     scale_point<T, KERNEL>(sc, ghat, spec, idx, 1);
 }
 
+// Adjoint of the stresslet (backward pass): from the spread upstream gradient
+// g^ (3 spectra) to the symmetric tensor field V_lk(y) = sum_m T_jlk(x_m - y) g_mj
+// (6 spectra: xx, yy, zz, xy, xz, yz).  T is odd, so its adjoint symbol is
+// minus the forward one contracted on its first index:
+//   V^_lk = i F [k^2 (k_k g^_l + k_l g^_k + (k.g^) d_lk) - 2 (k.g^) k_l k_k],
+// with F the forward stresslet factor (1 + k^2/4xi^2) G~^ and the Gaussians.
+template <typename T>
+__global__ void k_scale_adj_stresslet(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__restrict__ spec) {
+    using C = cplx<T>;
+    const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nk) return;
+    int kx = idx % sc.nxh;
+    int ky = (idx / sc.nxh) % sc.Mf;
+    int kz = idx / ((size_t)sc.nxh * sc.Mf);
+    int bx = (kx == sc.Mt) ? -sc.Mt : kx;
+    int by = (ky < sc.Mt) ? ky : ky - sc.Mf;
+    int bz = (kz < sc.Mt) ? kz : kz - sc.Mf;
+    const int O = sc.Mt + 1;
+    const T G = ghat[((size_t)abs(bz) * O + abs(by)) * O + abs(bx)];
+    const T k1 = (T)sc.dk;
+    const T kv[3] = {k1 * bx, k1 * by, k1 * bz};
+    const T k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+    const T F = (T)sc.norm * G * sexp((T)sc.ecoef * k2) * (T(1) + k2 * (T)sc.inv4xi2);
+    C *w0 = spec + idx;
+    C g[3];
+    for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
+    C kg;
+    kg.x = kv[0] * g[0].x + kv[1] * g[1].x + kv[2] * g[2].x;
+    kg.y = kv[0] * g[0].y + kv[1] * g[1].y + kv[2] * g[2].y;
+    const int L_[6] = {0, 1, 2, 0, 0, 1}, K_[6] = {0, 1, 2, 1, 2, 2};
+    for (int c = 0; c < 6; c++) {
+        const int l = L_[c], k = K_[c];
+        C v;
+        v.x = k2 * (kv[k] * g[l].x + kv[l] * g[k].x + (l == k ? kg.x : T(0))) - T(2) * kg.x * kv[l] * kv[k];
+        v.y = k2 * (kv[k] * g[l].y + kv[l] * g[k].y + (l == k ? kg.y : T(0))) - T(2) * kg.y * kv[l] * kv[k];
+        // multiply by i F: (a + ib) i = -b + ia
+        C o;
+        o.x = -F * v.y;
+        o.y = F * v.x;
+        w0[c * nk] = o;
+    }
+}
+
 // Batched: block b belongs to the system s with blk_base[s] <= b < blk_base[s+1];
 // each thread scales one k-point of that system for all n_rhs right-hand sides,
 // reading the precomputed kernel once.
@@ -157,6 +201,19 @@ cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpos
     p->launches++;
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_scale_adj_stresslet(se_plan_s *p, cudaStream_t st, void *spec) {
+    const ScaleConst sc = make_scale_const(p);
+    const size_t nk = (size_t)p->Mf * p->Mf * sc.nxh;
+    k_scale_adj_stresslet<T><<<(unsigned)((nk + SCALE_BS - 1) / SCALE_BS), SCALE_BS, 0, st>>>(
+        sc, (const T *)p->ghat, (cplx<T> *)spec);
+    p->launches++;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_scale_adj_stresslet<float>(se_plan_s *, cudaStream_t, void *);
+template cudaError_t launch_scale_adj_stresslet<double>(se_plan_s *, cudaStream_t, void *);
 
 template <typename T>
 cudaError_t launch_bscale(int kernel, const BSys<T> *sys, const int *blk_base, int S, int nblk, int n_rhs,

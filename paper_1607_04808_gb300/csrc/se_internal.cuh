@@ -248,9 +248,18 @@ template <typename T>
 cudaError_t launch_zero_octant(se_plan_s *p, cudaStream_t st, void *grid, int nc);
 template <typename T>
 cudaError_t launch_gather_grad(se_plan_s *p, cudaStream_t st, const void *w_fwd, const void *w_adj,
-                               const T *f_orig, const T *g_orig, T *gx);
+                               const T *f_orig, const T *q_orig, const T *g_orig, T *gx);
 template <typename T>
 cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *gx);
+// stresslet backward: adjoint scaling (3 -> 6 spectra), adjoint gather and the
+// adjoint real-space sum for the strength gradients
+template <typename T>
+cudaError_t launch_scale_adj_stresslet(se_plan_s *p, cudaStream_t st, void *spec);
+template <typename T>
+cudaError_t launch_gather_adjT(se_plan_s *p, cudaStream_t st, const void *V, const T *f_orig, const T *q_orig,
+                               T *gf, T *gq);
+template <typename T>
+cudaError_t launch_real_adjT(se_plan_s *p, cudaStream_t st, const T *f_orig, const T *q_orig, T *gf, T *gq);
 
 // batched launchers (one launch over all systems of a batch)
 constexpr int SCALE_BS = 256;  // threads per block of the scaling kernels

@@ -66,6 +66,8 @@ def lib():
             L.se_eval_host.argtypes = [vp, vp, vp, vp, vp, vp]
             L.se_eval_backward.restype = i32
             L.se_eval_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+            L.se_eval_backward_q.restype = i32
+            L.se_eval_backward_q.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.se_choose_params.restype = i32
             L.se_choose_params.argtypes = [i32, i32, i64, dbl, dbl, dbl, ctypes.POINTER(SEParams),
                                            ctypes.POINTER(SEParams)]
@@ -201,14 +203,17 @@ class Plan:
         _check(lib().se_eval_host(self._h, p(x), p(f), p(q), p(out), _stream(stream)))
         return out
 
-    def backward(self, x, f, grad_u, want_f=True, want_x=True, stream=None):
-        """Gradients of L = sum grad_u . u: (grad_f, grad_x) (se_eval_backward)."""
+    def backward(self, x, f, grad_u, want_f=True, want_x=True, stream=None, q=None, want_q=False):
+        """Gradients of L = sum grad_u . u (se_eval_backward_q): (grad_f, grad_x), or
+        (grad_f, grad_x, grad_q) when want_q (stresslet, which also needs q)."""
         x, f, grad_u = self._arg(x, "x"), self._arg(f, "f"), self._arg(grad_u, "grad_u")
+        q = self._arg(q, "q")
         gf = torch.empty_like(x) if want_f else None
         gx = torch.empty_like(x) if want_x else None
-        _check(lib().se_eval_backward(self._h, _ptr(x), _ptr(f), None, _ptr(grad_u), _ptr(gf),
-                                      _ptr(gx), _stream(stream)))
-        return gf, gx
+        gq = torch.empty_like(x) if want_q else None
+        _check(lib().se_eval_backward_q(self._h, _ptr(x), _ptr(f), _ptr(q), _ptr(grad_u), _ptr(gf),
+                                        _ptr(gq), _ptr(gx), _stream(stream)))
+        return (gf, gx, gq) if want_q else (gf, gx)
 
     def check(self):
         """se_plan_check: synchronise and raise on a device-side error."""
@@ -308,25 +313,32 @@ class Batch:
 
 
 class SEFunction(torch.autograd.Function):
-    """u = SE(x, f) with gradients for x and f (stokeslet, rotlet) through se_eval_backward."""
+    """u = SE(x, f[, q]) with gradients for x, f and q through se_eval_backward_q."""
 
     @staticmethod
-    def forward(ctx, x, f, plan: Plan):
+    def forward(ctx, x, f, q, plan: Plan):
         ctx.plan = plan
-        ctx.save_for_backward(x, f)
-        return plan.eval(x.contiguous(), f.contiguous())
+        ctx.has_q = q is not None
+        ctx.save_for_backward(x, f, q) if q is not None else ctx.save_for_backward(x, f)
+        return plan.eval(x.contiguous(), f.contiguous(), None if q is None else q.contiguous())
 
     @staticmethod
     def backward(ctx, grad_u):
+        if ctx.has_q:
+            x, f, q = ctx.saved_tensors
+            gf, gx, gq = ctx.plan.backward(x, f, grad_u.contiguous(), want_f=ctx.needs_input_grad[1],
+                                           want_x=ctx.needs_input_grad[0], q=q,
+                                           want_q=ctx.needs_input_grad[2])
+            return gx, gf, gq, None
         x, f = ctx.saved_tensors
         gf, gx = ctx.plan.backward(x, f, grad_u.contiguous(), want_f=ctx.needs_input_grad[1],
                                    want_x=ctx.needs_input_grad[0])
-        return gx, gf, None
+        return gx, gf, None, None
 
 
-def se_sum(x, f, plan: Plan):
-    """Differentiable u = sum K(x_m - x_n) f_n."""
-    return SEFunction.apply(x, f, plan)
+def se_sum(x, f, plan: Plan, q=None):
+    """Differentiable u = sum K(x_m - x_n) f_n (stresslet: T(x_m - x_n) f_n q_n)."""
+    return SEFunction.apply(x, f, q, plan)
 
 
 def choose_params(kernel: str, N: int, L: float = 1.0, tol: float = 0.0, prec: str = "fp32",

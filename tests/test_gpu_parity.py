@@ -246,6 +246,54 @@ def test_backward_vs_direct_gradients(kernel, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_stresslet_backward_vs_direct_gradients(prec):
+    """Stresslet: dL/df, dL/dq (adjoint tensor field on 6 grids, contracted with
+    q and f) and dL/dx against the exact direct-sum gradients."""
+    N = 2000
+    x, f, g = W.rotlet_uniform(N, 21)
+    q = W.unit_vectors(N, 21)
+    if prec == "fp32":
+        x, f, g, q = as32(x), as32(f), as32(g), as32(q)
+    pkg = P()
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    plan = pkg.Plan("stresslet", N, BOX, prec=prec, tol=1e-10 if prec == "fp64" else 2e-6)
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")  # noqa: E731
+    gf, gx, gq = plan.backward(t(x), t(f), t(g), q=t(q), want_q=True)
+    plan.check()
+    ref_gf, ref_gq = direct.grad_fq(x, f, q, g)
+    ref_gx = direct.grad_x("stresslet", x, f, g, q)
+    tol_f, tol_x = (1e-9, 1e-8) if prec == "fp64" else (2e-6, 2e-5)
+    assert rel_l2(gf.double().cpu().numpy(), ref_gf) <= tol_f
+    assert rel_l2(gq.double().cpu().numpy(), ref_gq) <= tol_f
+    assert rel_l2(gx.double().cpu().numpy(), ref_gx) <= tol_x
+    # grad_q is refused for the other kernels
+    plan2 = pkg.Plan("rotlet", N, BOX, prec=prec, tol=2e-6)
+    with pytest.raises(pkg.SEError):
+        plan2.backward(t(x), t(f), t(g), q=t(q), want_q=True)
+    plan.close()
+    plan2.close()
+
+
+def test_stresslet_autograd():
+    """torch.autograd through SEFunction with q: all three gradients."""
+    pkg = P()
+    N = 400
+    x, f, g = W.rotlet_uniform(N, 22)
+    q = W.unit_vectors(N, 22)
+    plan = pkg.Plan("stresslet", N, BOX, prec="fp64", tol=1e-10)
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    ft = torch.tensor(f, device="cuda", requires_grad=True)
+    qt = torch.tensor(q, device="cuda", requires_grad=True)
+    u = pkg.se_sum(xt, ft, plan, q=qt)
+    (u * torch.tensor(g, device="cuda")).sum().backward()
+    ref_gf, ref_gq = direct.grad_fq(x, f, q, g)
+    assert rel_l2(ft.grad.cpu().numpy(), ref_gf) <= 1e-9
+    assert rel_l2(qt.grad.cpu().numpy(), ref_gq) <= 1e-9
+    assert rel_l2(xt.grad.cpu().numpy(), direct.grad_x("stresslet", x, f, g, q)) <= 1e-8
+    plan.close()
+
+
 def test_autograd_function_matches_fd():
     """torch.autograd through SEFunction; central differences of the FP64 forward."""
     pkg = P()
