@@ -31,6 +31,7 @@ struct se_batch_s {
     int kernel = 0, prec = 0, S = 0, R = 1;
     int64_t Ntot = 0;
     int P = 0, T_ = 8;
+    bool colk = false;  // FP32 register-column spreading and gather
     std::vector<se_plan_s *> sub;  // per system: parameters, geometry, precomputed kernel
     std::vector<int> off_h;        // S + 1 point offsets
     int ntiles_tot = 0, ncells_tot = 0, nrows_tot = 0, nitems = 0, nblk_scale = 0, nblk_zero = 0;
@@ -130,7 +131,10 @@ se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t 
     B->launches = 0;
     BCK(launch_bbin<T>(sys, B->off_d, S, Ntot, R, B->ntiles_tot, B->ncells_tot, x, f, B->b, st, &B->launches));
     BCK(launch_bzero<T>(sys, B->zblk_base_d, S, B->nblk_zero, R, st));
-    BCK(launch_bspread<T>(sys, B->items_d, B->nitems, B->P, B->T_, R, B->b, st));
+    if (sizeof(T) == 4 && B->colk)
+        BCK(launch_bspread_col((const BSys<float> *)sys, B->items_d, B->nitems, B->P, R, B->b, st));
+    else
+        BCK(launch_bspread<T>(sys, B->items_d, B->nitems, B->P, B->T_, R, B->b, st));
     B->launches += 2;
     for (auto &c : B->classes) {
         BCF(cufftSetStream(c.fwd, st));
@@ -148,7 +152,11 @@ se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t 
         else
             BCF(cufftExecZ2D(c.inv, (cufftDoubleComplex *)c.spec, (cufftDoubleReal *)c.wgrid));
     }
-    BCK(launch_bgather<T>(sys, B->off_d, S, Ntot, B->P, R, B->b, f, u, st));
+    if (sizeof(T) == 4 && B->colk)
+        BCK(launch_bgather_col((const BSys<float> *)sys, B->items_d, B->nitems, B->P, R, B->b, (const float *)f,
+                               (float *)u, st));
+    else
+        BCK(launch_bgather<T>(sys, B->off_d, S, Ntot, B->P, R, B->b, f, u, st));
     B->launches += 1;
     BCK(launch_breal<T>(B->kernel, sys, B->row_base_d, S, B->nrows_tot, Ntot, R, B->b, B->cl_sys, u, st,
                         &B->launches));
@@ -209,6 +217,7 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
         if (st != SE_OK) return st;
     }
     B->T_ = B->sub[0]->geom.T;
+    B->colk = B->sub[0]->colk;
     // offsets and tables
     B->off_h.assign(S + 1, 0);
     for (int s = 0; s < S; s++) B->off_h[s + 1] = B->off_h[s] + (int)N_s[s];

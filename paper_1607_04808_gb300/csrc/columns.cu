@@ -1,0 +1,415 @@
+// FP32 spreading (step 1, eq. Hx) and gather (step 5, eq. u_integr) with the
+// padded grid block of a tile held in registers.
+//
+// A tile is TE^3 window starts; the grid points its points touch form the
+// padded block of PT = TE + P - 1 points per dimension.  Thread (cx, cy) of
+// the CTA owns the column of PT grid values at (cx, cy) for the three source
+// components, in registers.  Points of the tile are taken NB at a time: their
+// separable Gaussian weights are computed once into shared memory (the z
+// weights already shifted to the point's position in the column, zero
+// elsewhere), then every thread whose column lies in a point's P x P support
+// updates (spreading) or reads (gather) its whole column with register FMAs.
+// Compared with a shared-memory accumulator this removes the read-modify-write
+// traffic of the P^3 updates; the columns are written to the zero-padded FFT
+// input once per tile (global atomics: neighbouring tiles overlap in their
+// halos) or read from the inverse transform once per tile.
+//
+// Gather reduces each point's contributions over the CTA: a warp shuffle sum,
+// then one shared-memory atomic per warp and component.
+#include "se_internal.cuh"
+
+namespace se {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <int P, int TE>
+struct ColCfg {
+    static constexpr int PT = TE + P - 1;       // padded block edge
+    static constexpr int PTP = (PT + 3) / 4 * 4;  // z weights padded for 16-byte loads
+    static constexpr int NT = (PT * PT + 31) / 32 * 32;
+    static constexpr int NB = 32;                 // points staged per batch
+};
+
+// Shared staging of a batch of points: fractional positions relative to the
+// window start (grid units), offsets of the window in the padded block, the
+// three 1-D weight vectors (z shifted into the column).
+template <int P, int TE>
+struct ColStage {
+    using C = ColCfg<P, TE>;
+    float wz[C::NB][C::PTP];
+    float wx[C::NB][P];
+    float wy[C::NB][P];
+    float4 src[C::NB];
+    float fr[C::NB][3];
+    int oxy[C::NB];
+    int oz[C::NB];
+    int m[C::NB];
+    float out[C::NB][3];
+};
+
+// Stage 1 (thread j < nb): point b0 + j.
+template <int P, int TE>
+__device__ __forceinline__ void stage_point(ColStage<P, TE> &S, const GP<float> &g, int j, int n, int gx0, int gy0,
+                                            int gz0, const float4 *__restrict__ xs) {
+    const float4 xv = xs[n];
+    int i0[3];
+    unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+    S.fr[j][0] = ((xv.x - g.x0[0]) * g.inv_h + g.half_ext) - (float)i0[0];
+    S.fr[j][1] = ((xv.y - g.x0[1]) * g.inv_h + g.half_ext) - (float)i0[1];
+    S.fr[j][2] = ((xv.z - g.x0[2]) * g.inv_h + g.half_ext) - (float)i0[2];
+    const int ox = min(max(i0[0] - gx0, 0), TE - 1), oy = min(max(i0[1] - gy0, 0), TE - 1),
+              oz = min(max(i0[2] - gz0, 0), TE - 1);
+    S.oxy[j] = ox | (oy << 8);
+    S.oz[j] = oz;
+}
+
+// Stage 2 (all threads): the weights of the nb staged points.
+template <int P, int TE>
+__device__ __forceinline__ void stage_weights(ColStage<P, TE> &S, const GP<float> &g, int nb) {
+    constexpr int PT = ColCfg<P, TE>::PT, PER = 2 * P + PT;
+    for (int e = threadIdx.x; e < nb * PER; e += blockDim.x) {
+        const int j = e / PER, k = e - j * PER;
+        if (k < P) {
+            const float t = S.fr[j][0] - (float)k;
+            S.wx[j][k] = __expf(-g.ah2 * t * t);
+        } else if (k < 2 * P) {
+            const float t = S.fr[j][1] - (float)(k - P);
+            S.wy[j][k - P] = __expf(-g.ah2 * t * t);
+        } else {
+            const int z = k - 2 * P, kz = z - S.oz[j];
+            const float t = S.fr[j][2] - (float)kz;
+            S.wz[j][z] = (kz >= 0 && kz < P) ? __expf(-g.ah2 * t * t) : 0.0f;
+        }
+    }
+}
+
+template <int P, int TE>
+__device__ __forceinline__ void spread_col_body(const GP<float> &g, int tile, int beg, int end, int c0, bool stress,
+                                                const float4 *__restrict__ xs, const float4 *__restrict__ fs,
+                                                int fstride, int foff, const float4 *__restrict__ qs,
+                                                float *__restrict__ grid) {
+    using C = ColCfg<P, TE>;
+    constexpr int PT = C::PT, PTP = C::PTP, NB = C::NB;
+    __shared__ __align__(16) ColStage<P, TE> S;
+    const int tid = threadIdx.x;
+    const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
+    const bool own = tid < PT * PT;
+    const int cx = tid % PT, cy = tid / PT;
+    float a0[PT], a1[PT], a2[PT];
+#pragma unroll
+    for (int z = 0; z < PT; z++) a0[z] = a1[z] = a2[z] = 0.0f;
+    for (int b0 = beg; b0 < end; b0 += NB) {
+        const int nb = min(NB, end - b0);
+        if (tid < nb) {
+            const int n = b0 + tid;
+            stage_point<P, TE>(S, g, tid, n, gx0, gy0, gz0, xs);
+            const float4 fv = fs[(size_t)n * fstride + foff];
+            float4 sv = fv;
+            if (stress) {
+                // components c0 .. c0+2 of the symmetric source (xx, yy, zz, xy, xz, yz)
+                const float4 qv = qs[n];
+                if (c0 == 0) {
+                    sv = make_float4(fv.x * qv.x, fv.y * qv.y, fv.z * qv.z, 0.0f);
+                } else {
+                    sv = make_float4(0.5f * (fv.x * qv.y + fv.y * qv.x), 0.5f * (fv.x * qv.z + fv.z * qv.x),
+                                     0.5f * (fv.y * qv.z + fv.z * qv.y), 0.0f);
+                }
+            }
+            S.src[tid] = sv;
+        }
+        __syncthreads();
+        stage_weights<P, TE>(S, g, nb);
+        __syncthreads();
+        if (own) {
+            for (int j = 0; j < nb; j++) {
+                const int oxy = S.oxy[j];
+                const int kx = cx - (oxy & 255), ky = cy - (oxy >> 8);
+                if ((unsigned)kx < (unsigned)P && (unsigned)ky < (unsigned)P) {
+                    const float w = S.wx[j][kx] * S.wy[j][ky];
+                    const float4 sv = S.src[j];
+                    const float s0 = sv.x * w, s1 = sv.y * w, s2 = sv.z * w;
+                    const float4 *wz4 = reinterpret_cast<const float4 *>(S.wz[j]);
+#pragma unroll
+                    for (int q = 0; q < PTP / 4; q++) {
+                        const float4 v = wz4[q];
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            const int z = 4 * q + i;
+                            if (z < PT) {
+                                a0[z] = fmaf(s0, vv[i], a0[z]);
+                                a1[z] = fmaf(s1, vv[i], a1[z]);
+                                a2[z] = fmaf(s2, vv[i], a2[z]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (own) {
+        const int gx = gx0 + cx, gy = gy0 + cy;
+        if (gx < g.Mt && gy < g.Mt) {
+            const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+            float *base = grid + (size_t)c0 * Mf3 + ((size_t)gz0 * Mf + gy) * Mf + gx;
+#pragma unroll
+            for (int z = 0; z < PT; z++) {
+                if (gz0 + z < g.Mt) {
+                    float *pz = base + (size_t)z * Mf2;
+                    if (a0[z] != 0.0f) atomicAdd(pz, a0[z]);
+                    if (a1[z] != 0.0f) atomicAdd(pz + Mf3, a1[z]);
+                    if (a2[z] != 0.0f) atomicAdd(pz + 2 * Mf3, a2[z]);
+                }
+            }
+        }
+    }
+}
+
+// w: three grids (the group of right-hand side r); u, f_orig: n_rhs three-vectors per point.
+template <int P, int TE>
+__device__ __forceinline__ void gather_col_body(const GP<float> &g, int tile, int beg, int end,
+                                                const float4 *__restrict__ xs, const int *__restrict__ perm,
+                                                const float *__restrict__ w, int n_rhs, int r,
+                                                const float *__restrict__ f_orig, double self_coef,
+                                                float *__restrict__ u) {
+    using C = ColCfg<P, TE>;
+    constexpr int PT = C::PT, PTP = C::PTP, NB = C::NB;
+    __shared__ __align__(16) ColStage<P, TE> S;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
+    const bool own = tid < PT * PT;
+    const int cx = tid % PT, cy = tid / PT;
+    // the thread's column of the three grids (zero outside the extended grid)
+    float w0[PT], w1[PT], w2[PT];
+    {
+        const int gx = gx0 + cx, gy = gy0 + cy;
+        const bool in = own && gx < g.Mt && gy < g.Mt;
+        const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+        const float *base = w + ((size_t)gz0 * Mf + gy) * Mf + gx;
+#pragma unroll
+        for (int z = 0; z < PT; z++) {
+            const bool ok = in && (gz0 + z < g.Mt);
+            const float *pz = base + (size_t)z * Mf2;
+            w0[z] = ok ? __ldg(pz) : 0.0f;
+            w1[z] = ok ? __ldg(pz + Mf3) : 0.0f;
+            w2[z] = ok ? __ldg(pz + 2 * Mf3) : 0.0f;
+        }
+    }
+    for (int b0 = beg; b0 < end; b0 += NB) {
+        const int nb = min(NB, end - b0);
+        if (tid < nb) {
+            stage_point<P, TE>(S, g, tid, b0 + tid, gx0, gy0, gz0, xs);
+            S.m[tid] = perm[b0 + tid];
+        }
+        if (tid < 3 * NB) S.out[tid / 3][tid % 3] = 0.0f;
+        __syncthreads();
+        stage_weights<P, TE>(S, g, nb);
+        __syncthreads();
+        for (int j = 0; j < nb; j++) {
+            const int oxy = S.oxy[j];
+            const int kx = cx - (oxy & 255), ky = cy - (oxy >> 8);
+            const bool act = own && (unsigned)kx < (unsigned)P && (unsigned)ky < (unsigned)P;
+            if (!__any_sync(FULL, act)) continue;
+            float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+            if (act) {
+                const float4 *wz4 = reinterpret_cast<const float4 *>(S.wz[j]);
+#pragma unroll
+                for (int q = 0; q < PTP / 4; q++) {
+                    const float4 v = wz4[q];
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const int z = 4 * q + i;
+                        if (z < PT) {
+                            p0 = fmaf(vv[i], w0[z], p0);
+                            p1 = fmaf(vv[i], w1[z], p1);
+                            p2 = fmaf(vv[i], w2[z], p2);
+                        }
+                    }
+                }
+                const float wxy = S.wx[j][kx] * S.wy[j][ky];
+                p0 *= wxy;
+                p1 *= wxy;
+                p2 *= wxy;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                p0 += __shfl_xor_sync(FULL, p0, o);
+                p1 += __shfl_xor_sync(FULL, p1, o);
+                p2 += __shfl_xor_sync(FULL, p2, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&S.out[j][0], p0);
+                atomicAdd(&S.out[j][1], p1);
+                atomicAdd(&S.out[j][2], p2);
+            }
+        }
+        __syncthreads();
+        if (tid < 3 * nb) {
+            const int j = tid / 3, c = tid - 3 * j;
+            const size_t o3 = ((size_t)S.m[j] * n_rhs + r) * 3 + c;
+            double o = (double)S.out[j][c];
+            if (self_coef != 0.0) o += self_coef * (double)f_orig[o3];
+            u[o3] = (float)o;
+        }
+        __syncthreads();
+    }
+}
+
+template <int P, int TE>
+__global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_spread_col(GP<float> g, int c0, bool stress,
+                                                                    const int *__restrict__ tile_start,
+                                                                    const float4 *__restrict__ xs,
+                                                                    const float4 *__restrict__ fs,
+                                                                    const float4 *__restrict__ qs,
+                                                                    float *__restrict__ grid) {
+    const int tile = blockIdx.x;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    spread_col_body<P, TE>(g, tile, beg, end, c0, stress, xs, fs, 1, 0, qs, grid);
+}
+
+template <int P, int TE>
+__global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_gather_col(GP<float> g, const int *__restrict__ tile_start,
+                                                                    const float4 *__restrict__ xs,
+                                                                    const int *__restrict__ perm,
+                                                                    const float *__restrict__ w,
+                                                                    const float *__restrict__ f_orig,
+                                                                    double self_coef, float *__restrict__ u) {
+    const int tile = blockIdx.x;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    gather_col_body<P, TE>(g, tile, beg, end, xs, perm, w, 1, 0, f_orig, self_coef, u);
+}
+
+// Batched: one CTA per item (system, tile, right-hand side).
+template <int P, int TE>
+__global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_bspread_col(const BSys<float> *__restrict__ sys,
+                                                                     const int4 *__restrict__ items,
+                                                                     const int *__restrict__ tile_start, int n_rhs,
+                                                                     const float4 *__restrict__ xs,
+                                                                     const float4 *__restrict__ fs) {
+    const int4 it = items[blockIdx.x];
+    const BSys<float> &B = sys[it.x];
+    const int key = B.tile_base + it.y;
+    const int beg = tile_start[key], end = tile_start[key + 1];
+    if (beg == end) return;
+    const GP<float> g = B.g;
+    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    spread_col_body<P, TE>(g, it.y, beg, end, 0, false, xs, fs, n_rhs, it.z, nullptr,
+                           B.grid + (size_t)it.z * 3 * Mf3);
+}
+
+template <int P, int TE>
+__global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_bgather_col(const BSys<float> *__restrict__ sys,
+                                                                     const int4 *__restrict__ items,
+                                                                     const int *__restrict__ tile_start, int n_rhs,
+                                                                     const float4 *__restrict__ xs,
+                                                                     const int *__restrict__ perm,
+                                                                     const float *__restrict__ f_orig,
+                                                                     float *__restrict__ u) {
+    const int4 it = items[blockIdx.x];
+    const BSys<float> &B = sys[it.x];
+    const int key = B.tile_base + it.y;
+    const int beg = tile_start[key], end = tile_start[key + 1];
+    if (beg == end) return;
+    const GP<float> g = B.g;
+    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    gather_col_body<P, TE>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * Mf3, n_rhs, it.z, f_orig,
+                           B.self_coef, u);
+}
+
+// Dispatch on the (even) support P, 4 <= P <= 16.
+template <template <int, int> class F, typename... A>
+cudaError_t with_p(int P, A... a) {
+    switch (P) {
+        case 4: return F<4, COL_TE>::run(a...);
+        case 6: return F<6, COL_TE>::run(a...);
+        case 8: return F<8, COL_TE>::run(a...);
+        case 10: return F<10, COL_TE>::run(a...);
+        case 12: return F<12, COL_TE>::run(a...);
+        case 14: return F<14, COL_TE>::run(a...);
+        case 16: return F<16, COL_TE>::run(a...);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int P, int TE>
+struct SpreadRun {
+    static cudaError_t run(const GP<float> g, int ntiles, int c0, bool stress, const int *ts, const float4 *xs,
+                           const float4 *fs, const float4 *qs, float *grid, cudaStream_t st) {
+        k_spread_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, c0, stress, ts, xs, fs, qs, grid);
+        return cudaGetLastError();
+    }
+};
+
+template <int P, int TE>
+struct GatherRun {
+    static cudaError_t run(const GP<float> g, int ntiles, const int *ts, const float4 *xs, const int *perm,
+                           const float *w, const float *f, double self_coef, float *u, cudaStream_t st) {
+        k_gather_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, ts, xs, perm, w, f, self_coef, u);
+        return cudaGetLastError();
+    }
+};
+
+template <int P, int TE>
+struct BSpreadRun {
+    static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
+                           const float4 *xs, const float4 *fs, cudaStream_t st) {
+        k_bspread_col<P, TE><<<nitems, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
+        return cudaGetLastError();
+    }
+};
+
+template <int P, int TE>
+struct BGatherRun {
+    static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
+                           const float4 *xs, const int *perm, const float *f, float *u, cudaStream_t st) {
+        k_bgather_col<P, TE><<<nitems, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, perm, f, u);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace
+
+bool col_supported(int prec, int P) { return prec == SE_FP32 && P >= 4 && P <= 16 && (P % 2) == 0; }
+
+cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
+                              void *grid, int nc) {
+    // nc = 3: f; nc = 6: the symmetric stresslet source in two passes of three
+    for (int c0 = 0; c0 < nc; c0 += 3) {
+        cudaError_t e = with_p<SpreadRun>(p->P, p->gpf, p->ntiles, c0, nc == 6, (const int *)p->b.cnt_t,
+                                          (const float4 *)xs, (const float4 *)fs, (const float4 *)qs,
+                                          (float *)grid, st);
+        if (e) return e;
+        p->launches++;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, const float *f_orig, float *u) {
+    const double self_coef = (p->kernel == SE_STOKESLET) ? -4.0 * p->xi / sqrt(M_PI) : 0.0;
+    cudaError_t e = with_p<GatherRun>(p->P, p->gpf, p->ntiles, (const int *)p->b.cnt_t, (const float4 *)p->b.xs_t,
+                                      (const int *)p->b.perm_t, (const float *)wgrid, f_orig, self_coef, u, st);
+    if (!e) p->launches++;
+    return e;
+}
+
+cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
+                               const Buffers &b, cudaStream_t st) {
+    return with_p<BSpreadRun>(P, sys, items, nitems, (const int *)b.cnt_t, n_rhs, (const float4 *)b.xs_t,
+                              (const float4 *)b.fs_t, st);
+}
+
+cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
+                               const Buffers &b, const float *f, float *u, cudaStream_t st) {
+    return with_p<BGatherRun>(P, sys, items, nitems, (const int *)b.cnt_t, n_rhs, (const float4 *)b.xs_t,
+                              (const int *)b.perm_t, f, u, st);
+}
+
+}  // namespace se

@@ -245,6 +245,8 @@ __global__ void __launch_bounds__(WPB * 32) k_gather_grad(GP<T> g, T c_grad, int
 
 template <typename T>
 cudaError_t launch_gather(se_plan_s *p, cudaStream_t st, const void *wgrid, const T *f_orig, T *u) {
+    if (sizeof(T) == 4 && p->colk)
+        return launch_gather_col(p, st, wgrid, (const float *)f_orig, (float *)u);
     int N = (int)p->N;
     double self_coef = (p->kernel == SE_STOKESLET) ? -4.0 * p->xi / sqrt(M_PI) : 0.0;
     dim3 gs((N + WPB - 1) / WPB), bs(WPB * 32);

@@ -250,6 +250,15 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
     }
     p->tiled = (T > 0);
     g.T = (T > 0) ? T : 8;
+#ifndef SE_USE_COL
+#define SE_USE_COL 1
+#endif
+    if (SE_USE_COL && col_supported(prec, p->P)) {
+        // register-column kernels: their own tile edge, no shared-memory limit
+        p->colk = true;
+        p->tiled = true;
+        g.T = COL_TE;
+    }
     g.ntd = (p->Mt - p->P + 1 + g.T - 1) / g.T;
     p->ntiles = g.ntd * g.ntd * g.ntd;
     // real-space cells: width >= rc/5 (FP32) or rc/3 (FP64) across rows (y, z;

@@ -198,6 +198,7 @@ struct se_plan_s {
     se::GP<double> gpd{};
     int ntiles = 0, ncells = 0;
     bool tiled = true;  // tiled shared-memory spreading (else global atomics)
+    bool colk = false;  // FP32 register-column spreading and gather (columns.cu)
     // device memory
     float4 *rq_a = nullptr;    // FP32 real-space quadratic table (see realspace.cu)
     float2 *rq_b = nullptr;
@@ -260,6 +261,18 @@ cudaError_t launch_gather_adjT(se_plan_s *p, cudaStream_t st, const void *V, con
                                T *gf, T *gq);
 template <typename T>
 cudaError_t launch_real_adjT(se_plan_s *p, cudaStream_t st, const T *f_orig, const T *q_orig, T *gf, T *gq);
+
+// FP32 register-column spreading and gather (columns.cu): tiles of COL_TE^3
+// window starts, even P in [4, 16]
+constexpr int COL_TE = 8;
+bool col_supported(int prec, int P);
+cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
+                              void *grid, int nc);
+cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, const float *f_orig, float *u);
+cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
+                               const Buffers &b, cudaStream_t st);
+cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
+                               const Buffers &b, const float *f, float *u, cudaStream_t st);
 
 // batched launchers (one launch over all systems of a batch)
 constexpr int SCALE_BS = 256;  // threads per block of the scaling kernels

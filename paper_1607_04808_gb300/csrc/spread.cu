@@ -279,6 +279,7 @@ cudaError_t launch_spread(se_plan_s *p, cudaStream_t st, const void *xs, const v
                           void *grid, int nc) {
     cudaError_t e;
     if ((e = launch_zero_octant<T>(p, st, grid, nc))) return e;
+    if (sizeof(T) == 4 && p->colk) return launch_spread_col(p, st, xs, fs, qs, grid, nc);
     size_t smem = spread_smem_bytes(p, nc, sizeof(T));
     const int nit = (p->P * p->P + 31) / 32;
     if (p->tiled && p->P <= 16 && smem <= 190 * 1024) {
