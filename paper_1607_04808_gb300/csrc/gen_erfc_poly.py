@@ -1,31 +1,30 @@
-"""Generate erfc_poly.cuh: a polynomial Q(t) ~ erfcx(x) = exp(x^2) erfc(x) in the
-variable t = 2 / (2 + x) for x in [0, X_MAX], so that the FP32 real-space kernel
-evaluates erfc(x) = exp(-x^2) Q(t) and shares exp(-x^2) with the Gaussian term of
-the screened kernels (Section 3.2).  The coefficients are a weighted
-least-squares fit on Chebyshev nodes (relative error), computed here with
-numpy/scipy; run this script to regenerate the header.
+"""Generate erfc_poly.cuh: polynomials Q(t) ~ erfcx(x) = exp(x^2) erfc(x) in the
+variable t = 1 / (2 + x), so that the FP32 real-space kernel evaluates
+erfc(x) = exp(-x^2) Q(t) and shares exp(-x^2) with the Gaussian terms of the
+screened kernels (Section 3.2).  Two fits: degree 8 on x in [0, 5] (enough for
+the cutoffs the parameter selection gives at FP32 tolerances) and degree 10 on
+[0, 8] (beyond 8, erfc(x) < 1e-28).  Weighted least squares on Chebyshev nodes
+(relative error), with numpy; run this script to regenerate the header.
 """
 import os
 
 import numpy as np
 from scipy.special import erfcx
 
-X_MAX = 8.0
-DEG = 10
+FITS = [("Q5", 5.0, 8), ("Q8", 8.0, 10)]
 
 
-def fit():
-    tmin = 2.0 / (2.0 + X_MAX)
+def fit(xmax, deg):
+    tmin, tmax = 1.0 / (2.0 + xmax), 0.5
     k = np.arange(4000)
-    tn = 0.5 * (1 + tmin) + 0.5 * (1 - tmin) * np.cos(np.pi * (k + 0.5) / len(k))
-    x = 2.0 / tn - 2.0
+    tn = 0.5 * (tmax + tmin) + 0.5 * (tmax - tmin) * np.cos(np.pi * (k + 0.5) / len(k))
+    x = 1.0 / tn - 2.0
     y = erfcx(x)
-    V = np.vander(tn, DEG + 1, increasing=True)
+    V = np.vander(tn, deg + 1, increasing=True)
     c, *_ = np.linalg.lstsq(V / y[:, None], np.ones_like(y), rcond=None)
-    xs = np.linspace(0, X_MAX, 200001)
-    ts = 2.0 / (2.0 + xs)
-    approx = np.polyval(c[::-1], ts)
-    err = np.max(np.abs(approx / erfcx(xs) - 1.0))
+    xs = np.linspace(0, xmax, 200001)
+    ts = 1.0 / (2.0 + xs)
+    err = np.max(np.abs(np.polyval(c[::-1], ts) / erfcx(xs) - 1.0))
     # error after rounding the coefficients and evaluating in float32 (Horner)
     c32 = c.astype(np.float32)
     t32 = ts.astype(np.float32)
@@ -37,20 +36,21 @@ def fit():
 
 
 def main():
-    c, err, err32 = fit()
     here = os.path.dirname(os.path.abspath(__file__))
-    lines = [
-        "// Generated by gen_erfc_poly.py: erfcx(x) ~ sum_k ERFC_Q[k] t^k, t = 2/(2+x), x in [0, %g]." % X_MAX,
-        "// Max relative error of the fit %.2e (FP64), %.2e (FP32 Horner)." % (err, err32),
-        "#pragma once",
-        "#define SE_ERFC_XMAX %.1ff" % X_MAX,
-        "#define SE_ERFC_DEG %d" % DEG,
-        "__device__ __constant__ const float ERFC_Q[%d] = {" % (DEG + 1),
-    ]
-    lines += ["    %.9ef," % v for v in c]
-    lines += ["};", ""]
+    lines = ["// Generated by gen_erfc_poly.py: erfcx(x) ~ sum_k Q[k] t^k, t = 1/(2+x).", "#pragma once"]
+    for name, xmax, deg in FITS:
+        c, err, err32 = fit(xmax, deg)
+        lines += [
+            "// x in [0, %g], degree %d: max relative error %.2e (FP64 fit), %.2e (FP32 Horner)."
+            % (xmax, deg, err, err32),
+            "#define SE_ERFC_DEG%s %d" % (name[1:], deg),
+            "__device__ __constant__ const float ERFC_%s[%d] = {" % (name, deg + 1),
+        ]
+        lines += ["    %.9ef," % v for v in c]
+        lines += ["};"]
+        print("%s: max rel err fp64 %.3e, fp32 %.3e" % (name, err, err32))
+    lines.append("")
     open(os.path.join(here, "erfc_poly.cuh"), "w").write("\n".join(lines))
-    print("max rel err fp64 %.3e, fp32 %.3e" % (err, err32))
 
 
 if __name__ == "__main__":

@@ -6,23 +6,24 @@
 //             A2 = xi^2 (4/sqrt(pi)) x e   (eq. TR_Op; A2 with the factor r that the third
 //             derivative of r - Phi^H gives)
 //   Omega^R = eps_jlm r_m B                                                (eq. RR_Op / 2)
-// Each kernel needs two smooth functions of x only (T1 = A r or A1 r^2, T2 = B r^3
-// or A2/xi^2).  FP32 evaluates erfc(x) = e Q(2/(2+x)) with the fitted erfcx
-// polynomial Q of erfc_poly.cuh, sharing the exponential; FP64 uses erfc and exp.
+// Each kernel needs two radial multipliers (a, b below), functions of r.  FP32
+// evaluates erfc(x) = e Q(1/(2+x)) with a fitted erfcx polynomial Q
+// (erfc_poly.cuh), sharing the exponential e; FP64 uses erfc and exp.
 //
-// Cell list: points are sorted by cell (cells of width >= rc/3 across rows and
-// >= rc/8 along x, x fastest), so each (y, z) row of cells is a contiguous
-// range of sorted points.  Forward sum: every row is cut into clusters of 8
-// consecutive targets (a cluster never crosses a row, so it spans a few cells
-// along x and one across); one warp per cluster, lane = (target, candidate
-// stream).  The candidates of every row of cells within reach, trimmed along x
-// to the cutoff sphere around the cluster's cells, are staged 32 at a time in
-// shared memory and each of the 4 streams takes every 4th one: every lane tests
-// and evaluates its own (target, candidate) pairs, with no compaction.  FP32
-// partial sums are folded into Kahan-compensated totals after each row; the
-// streams are combined with a compensated shuffle sum and u (which already holds
-// u^F + u^self) is updated in FP64.  The backward kernel keeps one warp per
-// target with ballot compaction of the candidates.
+// Cell list: points are sorted by cell (cells of width >= rc/5 across rows in
+// FP32, rc/3 in FP64, and >= rc/16 along x, x fastest), so each (y, z) row of
+// cells is a contiguous range of sorted points.  FP32 forward sum: every row is
+// cut into clusters of 16 consecutive targets (a cluster never crosses a row,
+// so it spans a few cells along x and one across); one warp per cluster, lane
+// = (target, candidate stream).  The candidates of every row of cells within
+// reach, trimmed along x to the cutoff sphere around the cluster's cells, form
+// one flat stream, staged 32 at a time in shared memory; each of the 2 streams
+// takes every other one, so every lane tests and evaluates its own (target,
+// candidate) pairs with no compaction.  Partial sums are folded into
+// Kahan-compensated totals after each staged chunk; the streams are combined
+// with a compensated shuffle sum and u (which already holds u^F + u^self) is
+// updated in FP64.  The FP64 forward sum and the backward kernels keep one warp
+// per target with ballot compaction of the candidates.
 #include <math.h>
 
 #include <vector>
@@ -34,152 +35,97 @@ namespace se {
 
 namespace {
 
-// Build-time layout of the FP32 clustered kernel: radial functions from the
-// quadratic table (1) or the fitted erfcx polynomial (0); persistent blocks
-// sweeping contiguous cluster ranges (1) or one cluster per warp (0).
-#ifndef SE_RS_QTAB
-#define SE_RS_QTAB 0
-#endif
-#ifndef SE_RS_PERSIST
-#define SE_RS_PERSIST 0
-#endif
-
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int QCAP = 64;
 constexpr int MAXROWS = 121;  // reach <= 5 cells across rows
 
-// The two radial functions at r: erfc(x) = exp(-x^2) Q(2/(2+x)) with the
-// fitted erfcx polynomial Q
-template <int KERNEL>
-__device__ __forceinline__ void radial2(const RC<float> &rk, float r2, float &rinv, float &t1, float &t2) {
-    rinv = rsqrtf(r2);
-    const float x = rk.xi * r2 * rinv;
-    const float e = __expf(-rk.xi2 * r2);
-    const float t = __fdividef(2.0f, 2.0f + x);
-    float q = ERFC_Q[SE_ERFC_DEG];
+__device__ __forceinline__ float ex2_approx(float v) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// erfcx(x) ~ Q(t), t = 1/(2 + x), from the fits of erfc_poly.cuh: PV = 1 for
+// x <= 5 (degree 8), PV = 0 for x <= 8 (degree 10).
+template <int PV>
+__device__ __forceinline__ float erfcx_poly(float t) {
+    if (PV == 1) {
+        float q = ERFC_Q5[SE_ERFC_DEG5];
 #pragma unroll
-    for (int k = SE_ERFC_DEG - 1; k >= 0; k--) q = fmaf(q, t, ERFC_Q[k]);
-    const float ec = e * q;
-    const float g = 1.12837917f * x * e;  // (2/sqrt(pi)) x e
+        for (int k = SE_ERFC_DEG5 - 1; k >= 0; k--) q = fmaf(q, t, ERFC_Q5[k]);
+        return q;
+    }
+    float q = ERFC_Q8[SE_ERFC_DEG8];
+#pragma unroll
+    for (int k = SE_ERFC_DEG8 - 1; k >= 0; k--) q = fmaf(q, t, ERFC_Q8[k]);
+    return q;
+}
+
+// The two radial multipliers of a pair at distance r (r2 = r^2 > 0):
+//   stokeslet, rotlet: a = (erfc(x) - (2/sqrt(pi)) x e) / r,  b = (erfc(x) + (2/sqrt(pi)) x e) / r^3
+//   stresslet:         a = A1 = -2 [3 erfc(x) + (2/sqrt(pi)) x (3 + 2 x^2) e] / r^2,  b = A2 = 2 xi^2 (2/sqrt(pi)) x e
+// FP32: erfc(x) = e Q(1/(2+x)) shares e = exp(-xi^2 r^2) with the Gaussian
+// terms, so a = (e / r)(Q - c r) and b = (e / r^3)(Q + c r), c = 2 xi/sqrt(pi).
+template <int KERNEL, int PV>
+__device__ __forceinline__ void radial_ab(const RC<float> &rk, float r2, float &rinv, float &a, float &b) {
+    rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float x = rk.xi * r;
+    const float e = ex2_approx(rk.ce * r2);
+    const float q = erfcx_poly<PV>(__fdividef(1.0f, 2.0f + x));
+    const float cr = rk.c * r;  // (2/sqrt(pi)) x
     if (KERNEL == SE_STRESSLET) {
-        t1 = -2.0f * (3.0f * ec + g * (3.0f + 2.0f * x * x));
-        t2 = 2.0f * g;
+        a = -2.0f * e * fmaf(cr, fmaf(2.0f * x, x, 3.0f), 3.0f * q) * (rinv * rinv);
+        b = 2.0f * rk.xi2 * cr * e;
     } else {
-        t1 = ec - g;
-        t2 = ec + g;
+        const float er = e * rinv;
+        a = er * (q - cr);
+        b = er * (rinv * rinv) * (q + cr);
     }
 }
 
-// FP64: the same two functions from erfc and exp
-template <int KERNEL>
-__device__ __forceinline__ void radial2(const RC<double> &rk, double r2, double &rinv, double &t1, double &t2) {
+// FP64: the same multipliers from erfc and exp
+template <int KERNEL, int PV>
+__device__ __forceinline__ void radial_ab(const RC<double> &rk, double r2, double &rinv, double &a, double &b) {
     rinv = rsqrt(r2);
-    const double x = rk.xi * r2 * rinv;
+    const double r = r2 * rinv;
+    const double x = rk.xi * r;
     const double e = exp(-x * x);
     const double ec = erfc(x);
     const double g = 1.1283791670955126 * x * e;  // (2/sqrt(pi)) x e
     if (KERNEL == SE_STRESSLET) {
-        t1 = -2.0 * (3.0 * ec + g * (3.0 + 2.0 * x * x));
-        t2 = 2.0 * g;
+        a = -2.0 * (3.0 * ec + g * (3.0 + 2.0 * x * x)) * (rinv * rinv);
+        b = 2.0 * rk.xi2 * g;
     } else {
-        t1 = ec - g;
-        t2 = ec + g;
+        a = (ec - g) * rinv;
+        b = (ec + g) * (rinv * rinv * rinv);
     }
 }
 
 // K^R(d) . source, added to acc (d = x_target - x_source, r2 = |d|^2 > 0)
-template <typename T, int KERNEL>
+template <typename T, int KERNEL, int PV = 0>
 __device__ __forceinline__ void pair(const RC<T> &rk, T dx, T dy, T dz, T r2, const vec4<T> &f, const vec4<T> &q,
                                      T acc[3]) {
-    T rinv, t1, t2;
-    radial2<KERNEL>(rk, r2, rinv, t1, t2);
-    const T rinv2 = rinv * rinv;
+    T rinv, a, b;
+    radial_ab<KERNEL, PV>(rk, r2, rinv, a, b);
     if (KERNEL == SE_STOKESLET) {
-        const T A = t1 * rinv;
-        const T Brf = t2 * rinv2 * rinv * (dx * f.x + dy * f.y + dz * f.z);
-        acc[0] += A * f.x + Brf * dx;
-        acc[1] += A * f.y + Brf * dy;
-        acc[2] += A * f.z + Brf * dz;
+        const T Brf = b * (dx * f.x + dy * f.y + dz * f.z);
+        acc[0] += a * f.x + Brf * dx;
+        acc[1] += a * f.y + Brf * dy;
+        acc[2] += a * f.z + Brf * dz;
     } else if (KERNEL == SE_ROTLET) {
-        const T B = t2 * rinv2 * rinv;
-        acc[0] += B * (f.y * dz - f.z * dy);
-        acc[1] += B * (f.z * dx - f.x * dz);
-        acc[2] += B * (f.x * dy - f.y * dx);
+        acc[0] += b * (f.y * dz - f.z * dy);
+        acc[1] += b * (f.z * dx - f.x * dz);
+        acc[2] += b * (f.x * dy - f.y * dx);
     } else {
         const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
-        const T A1 = t1 * rinv2;
-        const T A2 = rk.xi2 * t2;
         const T hf = hx * f.x + hy * f.y + hz * f.z;
         const T hq = hx * q.x + hy * q.y + hz * q.z;
         const T fq = f.x * q.x + f.y * q.y + f.z * q.z;
-        const T a1 = A1 * hf * hq;
-        acc[0] += a1 * hx + A2 * (hx * fq + f.x * hq + q.x * hf);
-        acc[1] += a1 * hy + A2 * (hy * fq + f.y * hq + q.y * hf);
-        acc[2] += a1 * hz + A2 * (hz * fq + f.z * hq + q.z * hf);
-    }
-}
-
-// FP32 quadratic table of the two radial functions of x = xi r (see the
-// header): interval j of RQ_N on [0, xi rc (1 + 1e-3)] holds c0 + c1 u + c2 u^2,
-// u in [0, 1), for both functions: a = (c0_1, c0_2, c1_1, c1_2), b = (c2_1, c2_2).
-constexpr int RQ_N = 1024;
-struct QTab {
-    const float4 *a;
-    const float2 *b;
-};
-
-template <int KERNEL>
-__device__ __forceinline__ void radial2_tab(const RC<float> &rk, const QTab &qt, float r2, float &rinv, float &t1,
-                                            float &t2) {
-    if (!SE_RS_QTAB) {
-        radial2<KERNEL>(rk, r2, rinv, t1, t2);
-        return;
-    }
-    rinv = rsqrtf(r2);
-    const float sx = r2 * rinv * rk.tab_scale;
-    // floor without a conversion unit: round (s - 1/2) in the mantissa of 1.5 * 2^23
-    const float v = (sx - 0.5f) + 12582912.0f;
-    const int j = min(__float_as_int(v) - 0x4B400000, RQ_N - 1);
-    const float u = sx - (v - 12582912.0f);
-    const float4 a = qt.a[j];
-    const float2 b = qt.b[j];
-    t1 = fmaf(u, fmaf(u, b.x, a.z), a.x);
-    t2 = fmaf(u, fmaf(u, b.y, a.w), a.y);
-}
-template <int KERNEL>
-__device__ __forceinline__ void radial2_tab(const RC<double> &rk, const QTab &, double r2, double &rinv, double &t1,
-                                            double &t2) {
-    radial2<KERNEL>(rk, r2, rinv, t1, t2);
-}
-
-template <typename T, int KERNEL>
-__device__ __forceinline__ void pair_tab(const RC<T> &rk, const QTab &qt, T dx, T dy, T dz, T r2, const vec4<T> &f,
-                                         const vec4<T> &q, T acc[3]) {
-    T rinv, t1, t2;
-    radial2_tab<KERNEL>(rk, qt, r2, rinv, t1, t2);
-    const T rinv2 = rinv * rinv;
-    if (KERNEL == SE_STOKESLET) {
-        const T A = t1 * rinv;
-        const T Brf = t2 * rinv2 * rinv * (dx * f.x + dy * f.y + dz * f.z);
-        acc[0] += A * f.x + Brf * dx;
-        acc[1] += A * f.y + Brf * dy;
-        acc[2] += A * f.z + Brf * dz;
-    } else if (KERNEL == SE_ROTLET) {
-        const T B = t2 * rinv2 * rinv;
-        acc[0] += B * (f.y * dz - f.z * dy);
-        acc[1] += B * (f.z * dx - f.x * dz);
-        acc[2] += B * (f.x * dy - f.y * dx);
-    } else {
-        const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
-        const T A1 = t1 * rinv2;
-        const T A2 = rk.xi2 * t2;
-        const T hf = hx * f.x + hy * f.y + hz * f.z;
-        const T hq = hx * q.x + hy * q.y + hz * q.z;
-        const T fq = f.x * q.x + f.y * q.y + f.z * q.z;
-        const T a1 = A1 * hf * hq;
-        acc[0] += a1 * hx + A2 * (hx * fq + f.x * hq + q.x * hf);
-        acc[1] += a1 * hy + A2 * (hy * fq + f.y * hq + q.y * hf);
-        acc[2] += a1 * hz + A2 * (hz * fq + f.z * hq + q.z * hf);
+        const T a1 = a * hf * hq;
+        acc[0] += a1 * hx + b * (hx * fq + f.x * hq + q.x * hf);
+        acc[1] += a1 * hy + b * (hy * fq + f.y * hq + q.y * hf);
+        acc[2] += a1 * hz + b * (hz * fq + f.z * hq + q.z * hf);
     }
 }
 
@@ -246,39 +192,35 @@ __global__ void k_cluster_fill(int nrows, int ncdx, int tpw, const int *__restri
     for (int s = a; s < b; s += tpw) cl[o++] = make_int2(s, min(tpw, b - s));
 }
 
-// K^R(d) applied to NR sources at once (the radial functions are evaluated
+// K^R(d) applied to NR sources at once (the radial multipliers are evaluated
 // once per pair): acc[r] += K^R(d) . f[r] (stokeslet, rotlet).
-template <typename T, int KERNEL, int NR>
-__device__ __forceinline__ void pair_multi(const RC<T> &rk, const QTab &qt, T dx, T dy, T dz, T r2,
-                                           const vec4<T> *f, const vec4<T> &q, T (*acc)[3], int nq) {
+template <typename T, int KERNEL, int NR, int PV>
+__device__ __forceinline__ void pair_multi(const RC<T> &rk, T dx, T dy, T dz, T r2, const vec4<T> *f,
+                                           const vec4<T> &q, T (*acc)[3], int nq) {
     if (NR == 1) {
-        pair_tab<T, KERNEL>(rk, qt, dx, dy, dz, r2, f[0], q, acc[0]);
+        pair<T, KERNEL, PV>(rk, dx, dy, dz, r2, f[0], q, acc[0]);
         return;
     }
-    T rinv, t1, t2;
-    radial2_tab<KERNEL>(rk, qt, r2, rinv, t1, t2);
-    const T rinv2 = rinv * rinv;
+    T rinv, a, b;
+    radial_ab<KERNEL, PV>(rk, r2, rinv, a, b);
     if (KERNEL == SE_STOKESLET) {
-        const T A = t1 * rinv;
-        const T B = t2 * rinv2 * rinv;
 #pragma unroll
         for (int r = 0; r < NR; r++) {
             if (r >= nq) break;
             const vec4<T> fv = f[r];
-            const T Brf = B * (dx * fv.x + dy * fv.y + dz * fv.z);
-            acc[r][0] += A * fv.x + Brf * dx;
-            acc[r][1] += A * fv.y + Brf * dy;
-            acc[r][2] += A * fv.z + Brf * dz;
+            const T Brf = b * (dx * fv.x + dy * fv.y + dz * fv.z);
+            acc[r][0] += a * fv.x + Brf * dx;
+            acc[r][1] += a * fv.y + Brf * dy;
+            acc[r][2] += a * fv.z + Brf * dz;
         }
     } else {
-        const T B = t2 * rinv2 * rinv;
 #pragma unroll
         for (int r = 0; r < NR; r++) {
             if (r >= nq) break;
             const vec4<T> fv = f[r];
-            acc[r][0] += B * (fv.y * dz - fv.z * dy);
-            acc[r][1] += B * (fv.z * dx - fv.x * dz);
-            acc[r][2] += B * (fv.x * dy - fv.y * dx);
+            acc[r][0] += b * (fv.y * dz - fv.z * dy);
+            acc[r][1] += b * (fv.z * dx - fv.x * dz);
+            acc[r][2] += b * (fv.x * dy - fv.y * dx);
         }
     }
 }
@@ -292,14 +234,14 @@ __device__ __forceinline__ void pair_multi(const RC<T> &rk, const QTab &qt, T dx
 // original point.  BATCH: the cluster's system
 // (cl_sys) supplies the geometry, the screening constants and the offset of
 // its cells; otherwise g0, rk0 and cell_start0 are the one system's.
-template <typename T, int KERNEL, int TPW, int NR, bool BATCH>
+// PV selects the FP32 erfcx fit (1: x = xi r <= 5, 0: x <= 8).
+template <typename T, int KERNEL, int TPW, int NR, bool BATCH, int PV>
 __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys<T> *__restrict__ sys,
                                                  const int *__restrict__ cl_sys, const vec4<T> *__restrict__ xs,
                                                  const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
                                                  const int *__restrict__ cell_start0,
                                                  const int2 *__restrict__ clusters, const int *__restrict__ ncl_total,
-                                                 const int *__restrict__ perm, const float4 *__restrict__ qa_g,
-                                                 const float2 *__restrict__ qb_g, T *__restrict__ u,
+                                                 const int *__restrict__ perm, T *__restrict__ u,
                                                  int *__restrict__ status, int fstride, int q0, int nq) {
     constexpr int WPB = 8, NS = 32 / TPW;
     __shared__ vec4<T> sx_all[WPB][32];
@@ -307,27 +249,15 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
     __shared__ vec4<T> sq_all[KERNEL == SE_STRESSLET ? WPB : 1][32];
     __shared__ int2 seg_all[WPB][MAXROWS];
     __shared__ int pre_all[WPB][MAXROWS + 1];
-    __shared__ float4 qa_s[SE_RS_QTAB ? RQ_N : 1];
-    __shared__ float2 qb_s[SE_RS_QTAB ? RQ_N : 1];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (sizeof(T) == 4 && SE_RS_QTAB) {
-        for (int i = threadIdx.x; i < RQ_N; i += blockDim.x) {
-            qa_s[i] = qa_g[i];
-            qb_s[i] = qb_g[i];
-        }
-        __syncthreads();
-    }
-    const QTab qt{qa_s, qb_s};
-    const int ntot = *ncl_total;
+    // one cluster per warp; consecutive clusters (neighbours in space) share a
+    // block, so their candidate loads share the L1 cache
+    const int c = blockIdx.x * WPB + wib;
+    if (c >= *ncl_total) return;
     vec4<T> *sx = sx_all[wib];
     vec4<T> *sf = sf_all[wib];
     vec4<T> *sq = sq_all[KERNEL == SE_STRESSLET ? wib : 0];
     int2 *seg = seg_all[wib];
-    // each block sweeps a contiguous range of clusters (neighbours in space, so
-    // the candidate loads of its warps share the L1 cache)
-    const int per_blk = SE_RS_PERSIST ? (ntot + gridDim.x - 1) / gridDim.x : WPB;
-    const int c_end = min(ntot, (blockIdx.x + 1) * per_blk);
-    for (int c = blockIdx.x * per_blk + wib; c < c_end; c += WPB) {
     GP<T> g;
     RC<T> rk;
     const int *cell_start;
@@ -420,11 +350,13 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
             const vec4<T> xv = sx[j];
             const T dx = xt.x - xv.x, dy = xt.y - xv.y, dz = xt.z - xv.z;
             const T r2 = dx * dx + dy * dy + dz * dz;
-            // the target itself (and any coincident point) has r2 = 0
-            zeros += (r2 == T(0)) ? 1 : 0;
-            if (has && r2 > T(0) && r2 <= rk.rc2) {
-                const vec4<T> qv = (KERNEL == SE_STRESSLET) ? sq[j] : zero4;
-                pair_multi<T, KERNEL, NR>(rk, qt, dx, dy, dz, r2, sf + j * NR, qv, acc, nq);
+            if (has && r2 <= rk.rc2) {
+                if (r2 > T(0)) {
+                    const vec4<T> qv = (KERNEL == SE_STRESSLET) ? sq[j] : zero4;
+                    pair_multi<T, KERNEL, NR, PV>(rk, dx, dy, dz, r2, sf + j * NR, qv, acc, nq);
+                } else {
+                    zeros++;  // the target itself, or a coincident point
+                }
             }
         };
         if (nch == 32) {
@@ -455,7 +387,7 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
             tot[q][d] = sm_ - cm_;
         }
     for (int o = TPW; o < 32; o <<= 1) zeros += __shfl_xor_sync(FULL, zeros, o);
-    if (__any_sync(FULL, has && zeros > 1) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
+    if (__any_sync(FULL, zeros > 1) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
     if (s == 0 && has) {
         const size_t mi = perm[t];
 #pragma unroll
@@ -466,8 +398,6 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
                 *ud = (T)((double)*ud + (double)tot[q][d]);
             }
         }
-    }
-    __syncwarp();
     }
 }
 
@@ -783,6 +713,10 @@ __global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, con
         for (int d = 0; d < 3; d++) gx[3 * mp + d] = (T)((double)gx[3 * mp + d] + tot[d]);
 }
 
+// The FP32 erfcx fit that covers x = xi r up to xi rc: degree 8 up to 5, else
+// degree 10 up to 8 (beyond 8, erfc(x) < 1e-28 and the pair terms vanish in FP32).
+inline int real_pv(double xi_rc) { return xi_rc <= 5.0 ? 1 : 0; }
+
 #ifndef SE_RS_TPW
 #define SE_RS_TPW 16
 #endif
@@ -807,15 +741,16 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
     k_cluster_fill<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, TPW, p->b.cnt_r, p->b.ncl,
                                                          p->b.clusters);
     const long max_cl = N / TPW + nrows + 1;
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long nblk = SE_RS_PERSIST ? std::min<long>((max_cl + 7) / 8, 4L * nsm) : (max_cl + 7) / 8;
+    const unsigned nblk = (unsigned)((max_cl + 7) / 8);
     if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
-    k_real_cl<T, KERNEL, TPW, 1, false><<<(unsigned)nblk, 256, 0, st>>>(g, rk, nullptr, nullptr, xs, fs, qs,
-                                                                      p->b.cnt_r, p->b.clusters,
-                                                              p->b.ncl + nrows, p->b.perm_r, p->rq_a, p->rq_b, u,
-                                                              p->b.status, 1, 0, 1);
+    if (real_pv(p->xi * p->rc) == 1)
+        k_real_cl<T, KERNEL, TPW, 1, false, 1><<<nblk, 256, 0, st>>>(g, rk, nullptr, nullptr, xs, fs, qs, p->b.cnt_r,
+                                                                     p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                                                                     u, p->b.status, 1, 0, 1);
+    else
+        k_real_cl<T, KERNEL, TPW, 1, false, 0><<<nblk, 256, 0, st>>>(g, rk, nullptr, nullptr, xs, fs, qs, p->b.cnt_r,
+                                                                     p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                                                                     u, p->b.status, 1, 0, 1);
     p->launches += 3 + scan_launch_count(nrows);
     return cudaGetLastError();
 }
@@ -839,9 +774,10 @@ cudaError_t launch_breal_k(const BSys<T> *sys, const int *row_base, int S, int n
     constexpr int NRMAX = sizeof(T) == 4 ? 8 : 2;
     for (int q0 = 0; q0 < n_rhs; q0 += NRMAX) {
         const int nq = std::min(NRMAX, n_rhs - q0);
-        k_real_cl<T, KERNEL, TPW, NRMAX, true><<<nblk, 256, 0, st>>>(
+        // the general erfcx fit: systems of a batch may have any xi rc
+        k_real_cl<T, KERNEL, TPW, NRMAX, true, 0><<<nblk, 256, 0, st>>>(
             GP<T>{}, RC<T>{}, sys, cl_sys, (const vec4<T> *)b.xs_r, (const vec4<T> *)b.fs_r, nullptr, b.cnt_r,
-            b.clusters, b.ncl + nrows_tot, b.perm_r, nullptr, nullptr, u, b.status, n_rhs, q0, nq);
+            b.clusters, b.ncl + nrows_tot, b.perm_r, u, b.status, n_rhs, q0, nq);
         *launches += 1;
     }
     return cudaGetLastError();
@@ -857,7 +793,7 @@ RC<T> make_rc(const se_plan_s *p) {
     rk.c = (T)(2.0 * p->xi / sqrt(M_PI));
     rk.c3 = (T)(4.0 * p->xi * p->xi * p->xi / sqrt(M_PI));
     rk.rc2 = (T)(p->rc * p->rc);
-    rk.tab_scale = (T)(p->xi * RQ_N / (p->xi * p->rc * (1.0 + 1e-3)));
+    rk.ce = (T)(-p->xi * p->xi / log(2.0));  // exp(-xi^2 r^2) = 2^(ce r^2)
     rk.reach = (int)ceil(p->rc * p->geom.inv_cw - 1e-9);
     return rk;
 }
@@ -879,47 +815,6 @@ template cudaError_t launch_breal<float>(int, const BSys<float> *, const int *, 
                                          int *, float *, cudaStream_t, int64_t *);
 template cudaError_t launch_breal<double>(int, const BSys<double> *, const int *, int, int, int, int,
                                           const Buffers &, int *, double *, cudaStream_t, int64_t *);
-
-// Host construction of the FP32 quadratic table (FP64 arithmetic): on each
-// interval the quadratic through the values at u = 0, 1/2, 1.
-se_status_t build_real_table(se_plan_s *p) {
-    const double xmax = p->xi * p->rc * (1.0 + 1e-3);
-    const double hx = xmax / RQ_N;
-    auto fns = [&](double x, double &t1, double &t2) {
-        const double e = exp(-x * x), ec = erfc(x), gg = 2.0 / sqrt(M_PI) * x * e;
-        if (p->kernel == SE_STRESSLET) {
-            t1 = -2.0 * (3.0 * ec + gg * (3.0 + 2.0 * x * x));
-            t2 = 2.0 * gg;
-        } else {
-            t1 = ec - gg;
-            t2 = ec + gg;
-        }
-    };
-    std::vector<float4> a(RQ_N);
-    std::vector<float2> b(RQ_N);
-    for (int j = 0; j < RQ_N; j++) {
-        double f0[2], fm[2], f1[2];
-        fns(j * hx, f0[0], f0[1]);
-        fns((j + 0.5) * hx, fm[0], fm[1]);
-        fns((j + 1) * hx, f1[0], f1[1]);
-        double c1[2], c2[2];
-        for (int k = 0; k < 2; k++) {
-            c2[k] = 2.0 * (f1[k] - 2.0 * fm[k] + f0[k]);
-            c1[k] = f1[k] - f0[k] - c2[k];
-        }
-        a[j] = make_float4((float)f0[0], (float)f0[1], (float)c1[0], (float)c1[1]);
-        b[j] = make_float2((float)c2[0], (float)c2[1]);
-    }
-    if (!p->rq_a && (cudaMalloc(&p->rq_a, RQ_N * sizeof(float4)) != cudaSuccess ||
-                     cudaMalloc(&p->rq_b, RQ_N * sizeof(float2)) != cudaSuccess)) {
-        cudaGetLastError();
-        return fail(SE_ERR_OOM, "real-space table allocation failed");
-    }
-    if (cudaMemcpy(p->rq_a, a.data(), RQ_N * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(p->rq_b, b.data(), RQ_N * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(SE_ERR_CUDA, "real-space table upload failed");
-    return SE_OK;
-}
 
 template <typename T>
 cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u) {

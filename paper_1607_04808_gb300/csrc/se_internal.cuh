@@ -82,7 +82,7 @@ struct GP {
 template <typename T>
 struct RC {
     T xi, xi2, c, c3, rc2;  // xi, xi^2, 2 xi/sqrt(pi), 4 xi^3/sqrt(pi), rc^2
-    T tab_scale;            // xi / (table interval width in x)
+    T ce;                   // -xi^2 / ln 2: exp(-xi^2 r^2) = 2^(ce r^2)
     int reach;              // rows of cells within reach on each side (y, z)
 };
 
@@ -200,8 +200,6 @@ struct se_plan_s {
     bool tiled = true;  // tiled shared-memory spreading (else global atomics)
     bool colk = false;  // FP32 register-column spreading and gather (columns.cu)
     // device memory
-    float4 *rq_a = nullptr;    // FP32 real-space quadratic table (see realspace.cu)
-    float2 *rq_b = nullptr;
     double *ghat64 = nullptr;  // (Mt+1)^3 octant of the precomputed kernel, FP64
     void *ghat = nullptr;      // same in the plan precision
     void *grid = nullptr;      // nc x Mf^3 real, zero padded (R2C input)
@@ -301,7 +299,6 @@ se_status_t precompute(se_plan_s *p);
 cudaError_t launch_scan(int *cnt, int n, cudaStream_t st);
 // number of kernels launch_scan issues for an array of n counts
 inline int scan_launch_count(int n) { return n <= 64 * 1024 ? 1 : 3; }
-se_status_t build_real_table(se_plan_s *p);  // exclusive scan, cnt[n] = total
 template <typename T> const GP<T> &gp(const se_plan_s *p);
 template <> inline const GP<float> &gp<float>(const se_plan_s *p) { return p->gpf; }
 template <> inline const GP<double> &gp<double>(const se_plan_s *p) { return p->gpd; }
