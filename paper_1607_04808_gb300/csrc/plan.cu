@@ -174,7 +174,7 @@ void free_plan(se_plan_s *p) {
     if (p->have_fwd) cufftDestroy(p->fwd);
     if (p->have_inv) cufftDestroy(p->inv);
     if (p->have_fwd3) cufftDestroy(p->fwd3);
-    void *ptrs[] = {p->b.ncl, p->b.clusters, p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
+    void *ptrs[] = {p->b.uj, p->b.ncl, p->b.clusters, p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
                     p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
                     p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
                     p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du};
@@ -369,6 +369,7 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
             if ((e = dmalloc(&p->b.clusters, (Nn / 4 + nrows + 1) * sizeof(int2)))) break;
         }
         if ((e = dmalloc(&p->b.cnt_r, scan_len(p->ncells) * 4))) break;
+        if (prec == SE_FP32 && (e = dmalloc(&p->b.uj, Nn * sizeof(float4)))) break;
         if ((e = dmalloc(&p->b.status, 16))) break;
         if ((e = cudaMemset(p->grid, 0, (size_t)p->nc * Mf3 * esz))) break;
         if ((e = cudaMemset(p->b.status, 0, 16))) break;
