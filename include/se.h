@@ -97,6 +97,19 @@ se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const doubl
  * Asynchronous on `stream`. */
 se_status_t se_eval(se_plan_t plan, const void *x, const void *f, const void *q, void *u, void *stream);
 
+/* u at separate targets: ut(y_i) = sum_n K(y_i - x_n) . f_n for Nt target
+ * points y (the paper evaluates the sums at the sources or at any other points,
+ * Section 2 below eq. usumfree): the Fourier part gathered at the targets plus
+ * the real-space sum over the sources within rc of each target, with no self
+ * term and no excluded pair.  x, f (, q): the plan's N sources as in se_eval;
+ * xt: Nt x 3 targets in the plan's box, ut: Nt x 3 output (overwritten); device
+ * arrays in the plan's precision.  A source at distance zero from a target is
+ * skipped and reported by se_plan_check as SE_ERR_COINCIDENT.  The first call
+ * with a larger Nt than before allocates the plan's target buffers (and
+ * synchronises the device).  Asynchronous on `stream` otherwise. */
+se_status_t se_eval_targets(se_plan_t plan, const void *x, const void *f, const void *q, int64_t Nt, const void *xt,
+                            void *ut, void *stream);
+
 /* Same as se_eval with HOST arrays: copies x, f (, q) to the device, evaluates,
  * copies u back and synchronises `stream` before returning. */
 se_status_t se_eval_host(se_plan_t plan, const void *x_host, const void *f_host, const void *q_host,

@@ -78,15 +78,16 @@ __global__ void k_bin_scatter(int N, const T *__restrict__ x, const T *__restric
     if (i >= N) return;
     vec4<T> xv, fv, qv;
     xv.x = x[3 * i]; xv.y = x[3 * i + 1]; xv.z = x[3 * i + 2];
-    fv.x = f[3 * i]; fv.y = f[3 * i + 1]; fv.z = f[3 * i + 2]; fv.w = 0;
+    if (f) { fv.x = f[3 * i]; fv.y = f[3 * i + 1]; fv.z = f[3 * i + 2]; fv.w = 0; }
     if (q) { qv.x = q[3 * i]; qv.y = q[3 * i + 1]; qv.z = q[3 * i + 2]; qv.w = 0; }
     int pt = start_t[key_t[i]] + slot_t[i];
     int pr = start_r[key_r[i]] + slot_r[i];
     vec4<T> xr = xv;
     set_tag(xv, tag_t[i]);
     set_tag(xr, tag_r[i]);
-    xs_t[pt] = xv; fs_t[pt] = fv; perm_t[pt] = i;
-    xs_r[pr] = xr; fs_r[pr] = fv; perm_r[pr] = i;
+    xs_t[pt] = xv; perm_t[pt] = i;
+    xs_r[pr] = xr; perm_r[pr] = i;
+    if (f) { fs_t[pt] = fv; fs_r[pr] = fv; }
     if (q) { qs_t[pt] = qv; qs_r[pr] = qv; }
 }
 
@@ -182,8 +183,13 @@ template cudaError_t launch_bbin<double>(const BSys<double> *, const int *, int,
 
 template <typename T>
 cudaError_t launch_bin(se_plan_s *p, const T *x, const T *f, const T *q, cudaStream_t st) {
-    Buffers &b = p->b;
-    int N = (int)p->N;
+    return launch_bin_set<T>(p, p->b, (int)p->N, x, f, q, st);
+}
+
+// Bin N points into the buffer set b with the plan's tiles and cells (f and q
+// may be NULL: positions only, e.g. evaluation targets).
+template <typename T>
+cudaError_t launch_bin_set(se_plan_s *p, Buffers &b, int N, const T *x, const T *f, const T *q, cudaStream_t st) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(b.cnt_t, 0, sizeof(int) * (p->ntiles + 1), st))) return e;
     if ((e = cudaMemsetAsync(b.cnt_r, 0, sizeof(int) * (p->ncells + 1), st))) return e;
@@ -275,6 +281,10 @@ cudaError_t launch_scan(int *cnt, int n, cudaStream_t st) {
 }
 
 template cudaError_t launch_bin<float>(se_plan_s *, const float *, const float *, const float *, cudaStream_t);
+template cudaError_t launch_bin_set<float>(se_plan_s *, Buffers &, int, const float *, const float *, const float *,
+                                           cudaStream_t);
+template cudaError_t launch_bin_set<double>(se_plan_s *, Buffers &, int, const double *, const double *,
+                                            const double *, cudaStream_t);
 template cudaError_t launch_bin<double>(se_plan_s *, const double *, const double *, const double *,
                                         cudaStream_t);
 

@@ -394,8 +394,13 @@ cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, con
 
 cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, const float *f_orig, float *u) {
     const double self_coef = (p->kernel == SE_STOKESLET) ? -4.0 * p->xi / sqrt(M_PI) : 0.0;
-    cudaError_t e = with_p<GatherRun>(p->P, p->gpf, p->ntiles, (const int *)p->b.cnt_t, (const float4 *)p->b.xs_t,
-                                      (const int *)p->b.perm_t, (const float *)wgrid, f_orig, self_coef, u, st);
+    return launch_gather_col_set(p, st, p->b, wgrid, f_orig, self_coef, u);
+}
+
+cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &b, const void *wgrid,
+                                  const float *f_orig, double self_coef, float *u) {
+    cudaError_t e = with_p<GatherRun>(p->P, p->gpf, p->ntiles, (const int *)b.cnt_t, (const float4 *)b.xs_t,
+                                      (const int *)b.perm_t, (const float *)wgrid, f_orig, self_coef, u, st);
     if (!e) p->launches++;
     return e;
 }

@@ -180,6 +180,64 @@ extern "C" se_status_t se_eval_real_space(se_plan_t p, const void *x, const void
     return SE_OK;
 }
 
+// Room for Nt evaluation targets in the plan's target buffers (grown on demand).
+static se_status_t ensure_targets(se_plan_s *p, int64_t Nt) {
+    if (Nt <= p->nt_cap) return SE_OK;
+    Buffers &b = p->bt;
+    void *old[] = {b.xs_t, b.perm_t, b.slot_t, b.key_t, b.tag_t, b.cnt_t, b.xs_r, b.perm_r, b.slot_r, b.key_r,
+                   b.tag_r, b.cnt_r, b.ncl, b.clusters};
+    cudaDeviceSynchronize();
+    for (void *q : old)
+        if (q) cudaFree(q);
+    b = Buffers();
+    p->nt_cap = 0;
+    const size_t n = (size_t)Nt, v4 = (p->prec == SE_FP32 ? 16 : 32);
+    const size_t nrows = (size_t)p->geom.ncd * p->geom.ncd;
+    auto scan_len = [](size_t k) { return k + 2 + (k + 4095) / 4096 + 1; };
+    cudaError_t e;
+    if ((e = cudaMalloc(&b.xs_t, n * v4)) || (e = cudaMalloc(&b.perm_t, n * 4)) || (e = cudaMalloc(&b.slot_t, n * 4)) ||
+        (e = cudaMalloc(&b.key_t, n * 4)) || (e = cudaMalloc(&b.tag_t, n * 4)) ||
+        (e = cudaMalloc(&b.cnt_t, scan_len(p->ntiles) * 4)) || (e = cudaMalloc(&b.xs_r, n * v4)) ||
+        (e = cudaMalloc(&b.perm_r, n * 4)) || (e = cudaMalloc(&b.slot_r, n * 4)) || (e = cudaMalloc(&b.key_r, n * 4)) ||
+        (e = cudaMalloc(&b.tag_r, n * 4)) || (e = cudaMalloc(&b.cnt_r, scan_len(p->ncells) * 4)) ||
+        (e = cudaMalloc(&b.ncl, scan_len(nrows) * 4)) || (e = cudaMalloc(&b.clusters, (n / 4 + nrows + 1) * sizeof(int2)))) {
+        cudaGetLastError();
+        return fail(SE_ERR_OOM, "se_eval_targets: target buffer allocation failed");
+    }
+    b.status = p->b.status;
+    p->nt_cap = Nt;
+    return SE_OK;
+}
+
+template <typename T>
+se_status_t eval_targets_t(se_plan_s *p, const T *x, const T *f, const T *q, int Nt, const T *xt, T *ut,
+                           cudaStream_t st) {
+    p->last_stream = st;
+    p->launches = 0;
+    CK(launch_bin<T>(p, x, f, q, st));
+    CK(launch_bin_set<T>(p, p->bt, Nt, xt, nullptr, nullptr, st));
+    se_status_t s = fourier_grid<T>(p, st, p->wgrid, p->nc, nullptr);
+    if (s != SE_OK) return s;
+    CK(launch_gather_targets<T>(p, st, p->bt, Nt, p->wgrid, ut));
+    CK(launch_real_targets<T>(p, st, p->bt, Nt, ut));
+    return SE_OK;
+}
+
+extern "C" se_status_t se_eval_targets(se_plan_t p, const void *x, const void *f, const void *q, int64_t Nt,
+                                       const void *xt, void *ut, void *stream) {
+    if (!p || !x || !f || !xt || !ut) return fail(SE_ERR_INVALID_ARG, "se_eval_targets: NULL pointer");
+    if (p->kernel == SE_STRESSLET && !q) return fail(SE_ERR_INVALID_ARG, "se_eval_targets: the stresslet needs q");
+    if (Nt < 1 || Nt > (int64_t)INT32_MAX / 4) return fail(SE_ERR_INVALID_ARG, "se_eval_targets: Nt out of range");
+    se_status_t s = ensure_targets(p, Nt);
+    if (s != SE_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prec == SE_FP32)
+        return eval_targets_t<float>(p, (const float *)x, (const float *)f, (const float *)q, (int)Nt,
+                                     (const float *)xt, (float *)ut, st);
+    return eval_targets_t<double>(p, (const double *)x, (const double *)f, (const double *)q, (int)Nt,
+                                  (const double *)xt, (double *)ut, st);
+}
+
 extern "C" se_status_t se_eval_host(se_plan_t p, const void *x, const void *f, const void *q, void *u,
                                     void *stream) {
     if (!p || !x || !f || !u) return fail(SE_ERR_INVALID_ARG, "se_eval_host: NULL pointer");

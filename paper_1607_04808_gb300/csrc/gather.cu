@@ -323,6 +323,34 @@ template cudaError_t launch_gather_adjT<float>(se_plan_s *, cudaStream_t, const 
                                                const float *, float *, float *);
 template cudaError_t launch_gather_adjT<double>(se_plan_s *, cudaStream_t, const void *, const double *,
                                                 const double *, double *, double *);
+// Gather at separate targets (binned into bt): the Fourier part only, no self term.
+template <typename T>
+cudaError_t launch_gather_targets(se_plan_s *p, cudaStream_t st, const Buffers &bt, int Nt, const void *wgrid,
+                                  T *ut) {
+    if (sizeof(T) == 4 && p->colk) return launch_gather_col_set(p, st, bt, wgrid, nullptr, 0.0, (float *)ut);
+    dim3 gs((Nt + WPB - 1) / WPB), bs(WPB * 32);
+    const vec4<T> *xs = (const vec4<T> *)bt.xs_t;
+    const T *w = (const T *)wgrid;
+    const GP<T> &g = gp<T>(p);
+    switch ((p->P * p->P + 31) / 32) {
+        case 1: k_gather<T, 1><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+        case 2: k_gather<T, 2><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+        case 3: k_gather<T, 3><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+        case 4: k_gather<T, 4><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+        case 5: k_gather<T, 5><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+        case 6: k_gather<T, 6><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+        case 7: k_gather<T, 7><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+        case 8: k_gather<T, 8><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+        default: k_gather<T, 0><<<gs, bs, 0, st>>>(g, Nt, xs, bt.perm_t, w, nullptr, 0.0, ut); break;
+    }
+    p->launches++;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gather_targets<float>(se_plan_s *, cudaStream_t, const Buffers &, int, const void *,
+                                                  float *);
+template cudaError_t launch_gather_targets<double>(se_plan_s *, cudaStream_t, const Buffers &, int, const void *,
+                                                   double *);
 template cudaError_t launch_gather<float>(se_plan_s *, cudaStream_t, const void *, const float *, float *);
 template cudaError_t launch_gather<double>(se_plan_s *, cudaStream_t, const void *, const double *, double *);
 template cudaError_t launch_gather_grad<float>(se_plan_s *, cudaStream_t, const void *, const void *,

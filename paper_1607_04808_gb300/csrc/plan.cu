@@ -180,6 +180,10 @@ void free_plan(se_plan_s *p) {
                     p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    void *tptrs[] = {p->bt.xs_t, p->bt.perm_t, p->bt.slot_t, p->bt.key_t, p->bt.tag_t, p->bt.cnt_t, p->bt.xs_r,
+                     p->bt.perm_r, p->bt.slot_r, p->bt.key_r, p->bt.tag_r, p->bt.cnt_r, p->bt.ncl, p->bt.clusters};
+    for (void *q : tptrs)
+        if (q) cudaFree(q);
     for (int i = 0; i < 9; i++)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     if (p->ev_real) cudaEventDestroy(p->ev_real);

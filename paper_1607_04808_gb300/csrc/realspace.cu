@@ -234,15 +234,20 @@ __device__ __forceinline__ void pair_multi(const RC<T> &rk, T dx, T dy, T dz, T 
 // original point.  BATCH: the cluster's system
 // (cl_sys) supplies the geometry, the screening constants and the offset of
 // its cells; otherwise g0, rk0 and cell_start0 are the one system's.
-// PV selects the FP32 erfcx fit (1: x = xi r <= 5, 0: x <= 8).
-template <typename T, int KERNEL, int TPW, int NR, bool BATCH, int PV>
+// PV selects the FP32 erfcx fit (1: x = xi r <= 5, 0: x <= 8).  TGT: the
+// targets are separate points (sorted by cell in xtg, permutation tperm, the
+// clusters built over their rows): no pair is excluded, and any candidate at
+// distance zero is reported as coincident.
+template <typename T, int KERNEL, int TPW, int NR, bool BATCH, int PV, bool TGT = false>
 __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys<T> *__restrict__ sys,
                                                  const int *__restrict__ cl_sys, const vec4<T> *__restrict__ xs,
                                                  const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
                                                  const int *__restrict__ cell_start0,
                                                  const int2 *__restrict__ clusters, const int *__restrict__ ncl_total,
                                                  const int *__restrict__ perm, T *__restrict__ u,
-                                                 int *__restrict__ status, int fstride, int q0, int nq) {
+                                                 int *__restrict__ status, int fstride, int q0, int nq,
+                                                 const vec4<T> *__restrict__ xtg = nullptr,
+                                                 const int *__restrict__ tperm = nullptr) {
     constexpr int WPB = 8, NS = 32 / TPW;
     __shared__ vec4<T> sx_all[WPB][32];
     __shared__ vec4<T> sf_all[WPB][32 * NR];
@@ -275,11 +280,12 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
     const int k = lane % TPW, s = lane / TPW;
     const bool has = k < cl.y;
     const int t = cl.x + min(k, cl.y - 1);
-    const vec4<T> xt = xs[t];
+    const vec4<T> *xT = TGT ? xtg : xs;
+    const vec4<T> xt = xT[t];
     // rows of cells within reach of the cluster's cells
     int c0[3], c1[3];
-    unpack3(get_tag(xs[cl.x]), c0[0], c0[1], c0[2]);
-    unpack3(get_tag(xs[cl.x + cl.y - 1]), c1[0], c1[1], c1[2]);
+    unpack3(get_tag(xT[cl.x]), c0[0], c0[1], c0[2]);
+    unpack3(get_tag(xT[cl.x + cl.y - 1]), c1[0], c1[1], c1[2]);
     const int R = rk.reach, W = 2 * R + 1, nrows = W * W;
     const T rc2m = rk.rc2 * T(1.0001);
     for (int r = lane; r < nrows; r += 32) {
@@ -387,9 +393,9 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
             tot[q][d] = sm_ - cm_;
         }
     for (int o = TPW; o < 32; o <<= 1) zeros += __shfl_xor_sync(FULL, zeros, o);
-    if (__any_sync(FULL, zeros > 1) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
+    if (__any_sync(FULL, zeros > (TGT ? 0 : 1)) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
     if (s == 0 && has) {
-        const size_t mi = perm[t];
+        const size_t mi = (TGT ? tperm : perm)[t];
 #pragma unroll
         for (int q = 0; q < NR; q++) {
             if (q >= nq) break;
@@ -1087,6 +1093,45 @@ cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u) {
     if (p->kernel == SE_STRESSLET) return launch_real_k<T, SE_STRESSLET>(p, st, rk, u);
     return launch_real_k<T, SE_ROTLET>(p, st, rk, u);
 }
+
+// Real-space sum at separate targets (binned into bt, Nt points): clusters of
+// the targets' cell rows, candidates from the plan's sources; adds to ut.
+template <typename T, int KERNEL>
+cudaError_t launch_real_targets_k(se_plan_s *p, cudaStream_t st, Buffers &bt, int Nt, T *ut) {
+    constexpr int TPW = SE_RS_TPW;
+    const int nrows = p->geom.ncd * p->geom.ncd;
+    k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, TPW, bt.cnt_r, bt.ncl);
+    cudaError_t e = launch_scan(bt.ncl, nrows, st);
+    if (e) return e;
+    k_cluster_fill<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, TPW, bt.cnt_r, bt.ncl, bt.clusters);
+    const long max_cl = Nt / TPW + nrows + 1;
+    const unsigned nblk = (unsigned)((max_cl + 7) / 8);
+    const RC<T> rk = make_rc<T>(p);
+    const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r,
+                  *qs = (const vec4<T> *)p->b.qs_r, *xt = (const vec4<T> *)bt.xs_r;
+    const GP<T> &g = gp<T>(p);
+    if (real_pv(p->xi * p->rc) == 1)
+        k_real_cl<T, KERNEL, TPW, 1, false, 1, true><<<nblk, 256, 0, st>>>(
+            g, rk, nullptr, nullptr, xs, fs, qs, p->b.cnt_r, bt.clusters, bt.ncl + nrows, p->b.perm_r, ut, p->b.status,
+            1, 0, 1, xt, bt.perm_r);
+    else
+        k_real_cl<T, KERNEL, TPW, 1, false, 0, true><<<nblk, 256, 0, st>>>(
+            g, rk, nullptr, nullptr, xs, fs, qs, p->b.cnt_r, bt.clusters, bt.ncl + nrows, p->b.perm_r, ut, p->b.status,
+            1, 0, 1, xt, bt.perm_r);
+    p->launches += 3 + scan_launch_count(nrows);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_real_targets(se_plan_s *p, cudaStream_t st, Buffers &bt, int Nt, T *ut) {
+    if (make_rc<T>(p).reach > 5) return cudaErrorInvalidValue;
+    if (p->kernel == SE_STOKESLET) return launch_real_targets_k<T, SE_STOKESLET>(p, st, bt, Nt, ut);
+    if (p->kernel == SE_STRESSLET) return launch_real_targets_k<T, SE_STRESSLET>(p, st, bt, Nt, ut);
+    return launch_real_targets_k<T, SE_ROTLET>(p, st, bt, Nt, ut);
+}
+
+template cudaError_t launch_real_targets<float>(se_plan_s *, cudaStream_t, Buffers &, int, float *);
+template cudaError_t launch_real_targets<double>(se_plan_s *, cudaStream_t, Buffers &, int, double *);
 
 template <typename T>
 cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *gx) {

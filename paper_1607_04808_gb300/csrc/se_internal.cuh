@@ -210,6 +210,8 @@ struct se_plan_s {
     void *spec2 = nullptr;     // backward spectrum
     void *tmp3 = nullptr;      // N x 3 scratch in plan precision (backward)
     se::Buffers b;
+    se::Buffers bt;          // evaluation targets (positions only), allocated on first use
+    int64_t nt_cap = 0;      // targets bt holds room for
     cufftHandle fwd = 0, inv = 0, fwd3 = 0;
     bool have_fwd = false, have_inv = false, have_fwd3 = false;
     cudaStream_t last_stream = nullptr;
@@ -235,6 +237,15 @@ se_status_t setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const doub
 // launchers (defined in the .cu files); all asynchronous on `st`
 template <typename T>
 cudaError_t launch_bin(se_plan_s *p, const T *x, const T *f, const T *q, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bin_set(se_plan_s *p, Buffers &b, int N, const T *x, const T *f, const T *q, cudaStream_t st);
+// evaluation at separate targets: gather (no self term) and real-space sum
+// with the targets binned into bt (Nt points) and the sources in the plan's set
+template <typename T>
+cudaError_t launch_gather_targets(se_plan_s *p, cudaStream_t st, const Buffers &bt, int Nt, const void *wgrid,
+                                  T *ut);
+template <typename T>
+cudaError_t launch_real_targets(se_plan_s *p, cudaStream_t st, Buffers &bt, int Nt, T *ut);
 template <typename T>
 cudaError_t launch_spread(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
                           void *grid, int nc_mode);
@@ -268,6 +279,8 @@ bool col_supported(int prec, int P);
 cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
                               void *grid, int nc);
 cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, const float *f_orig, float *u);
+cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &b, const void *wgrid,
+                                  const float *f_orig, double self_coef, float *u);
 cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const Buffers &b, cudaStream_t st);
 cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,

@@ -62,6 +62,8 @@ def lib():
             L.se_eval.argtypes = [vp, vp, vp, vp, vp, vp]
             L.se_eval_real_space.restype = i32
             L.se_eval_real_space.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.se_eval_targets.restype = i32
+            L.se_eval_targets.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
             L.se_eval_host.restype = i32
             L.se_eval_host.argtypes = [vp, vp, vp, vp, vp, vp]
             L.se_eval_backward.restype = i32
@@ -166,6 +168,17 @@ class Plan:
         _check(lib().se_eval(self._h, _ptr(x), _ptr(f), _ptr(q), _ptr(out), _stream(stream)))
         if check:
             self.check()
+        return out
+
+    def eval_targets(self, x, f, xt, q=None, out=None, stream=None):
+        """u at separate target points xt (Nt, 3) from the plan's sources (se_eval_targets)."""
+        x, f, q = self._arg(x, "x"), self._arg(f, "f"), self._arg(q, "q")
+        if not (xt.is_cuda and xt.dtype == self.dtype and xt.is_contiguous() and xt.dim() == 2 and xt.shape[1] == 3):
+            raise ValueError(f"xt: expected a contiguous CUDA tensor (Nt, 3) of {self.dtype}")
+        if out is None:
+            out = torch.empty_like(xt)
+        _check(lib().se_eval_targets(self._h, _ptr(x), _ptr(f), _ptr(q), int(xt.shape[0]), _ptr(xt), _ptr(out),
+                                     _stream(stream)))
         return out
 
     def eval_real_space(self, x, f, q=None, out=None, stream=None):

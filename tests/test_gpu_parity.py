@@ -406,3 +406,56 @@ def test_full_size_fp32_rotlet_backward_sampled():
         if checked == 3:
             break
     assert checked == 3
+
+
+# ------------------------------------------------------------------ separate targets
+
+@pytest.mark.parametrize("kernel", KN)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_targets_vs_direct(kernel, prec):
+    """u at targets that are not sources: Fourier part gathered at the targets
+    plus the real-space sum over the sources, no self term, against the direct
+    sum at arbitrary points."""
+    N, Nt = 2000, 777
+    x, f = W.stokeslet_uniform(N, 31)
+    q = W.unit_vectors(N, 31) if kernel == "stresslet" else None
+    y = W.uniform_points(Nt, 32)
+    if prec == "fp32":
+        x, f, q, y = as32(x), as32(f), as32(q), as32(y)
+        x = np.minimum(x, np.nextafter(np.float32(1.0), np.float32(0)))
+        y = np.minimum(y, np.nextafter(np.float32(1.0), np.float32(0)))
+    pkg = P()
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    t = lambda a: None if a is None else torch.tensor(a, dtype=dt, device="cuda")  # noqa: E731
+    plan = pkg.Plan(kernel, N, BOX, prec=prec, tol=1e-10 if prec == "fp64" else 2e-6)
+    ut = plan.eval_targets(t(x), t(f), t(y), q=t(q))
+    plan.check()
+    ref = direct.direct(kernel, x, f, q, xt=y)
+    tol = 1e-10 if prec == "fp64" else 2e-6
+    assert rel_l2(ut.double().cpu().numpy(), ref) <= tol
+    # a second call with fewer targets reuses the buffers
+    ut2 = plan.eval_targets(t(x), t(f), t(y[:5]), q=t(q))
+    plan.check()
+    assert rel_l2(ut2.double().cpu().numpy(), ref[:5]) <= 10 * tol
+    plan.close()
+
+
+@pytest.mark.parametrize("kernel", KN)
+def test_targets_at_the_sources(kernel):
+    """Targets placed on the sources: the zero-distance pair is skipped and
+    reported, and the result is se_eval's without the self term
+    (ut = u + 4 xi/sqrt(pi) f for the stokeslet, ut = u otherwise)."""
+    N = 1500
+    x, f = W.stokeslet_uniform(N, 33)
+    q = W.unit_vectors(N, 33) if kernel == "stresslet" else None
+    pkg = P()
+    t = lambda a: None if a is None else torch.tensor(a, device="cuda")  # noqa: E731
+    plan = pkg.Plan(kernel, N, BOX, prec="fp64", tol=1e-10)
+    u = plan.eval(t(x), t(f), t(q), check=True).cpu().numpy()
+    ut = plan.eval_targets(t(x), t(f), t(x), q=t(q)).cpu().numpy()
+    with pytest.raises(pkg.SEError) as ei:
+        plan.check()
+    assert ei.value.code == 3  # SE_ERR_COINCIDENT
+    self_term = 4.0 * plan.params["xi"] / np.sqrt(np.pi) * f if kernel == "stokeslet" else 0.0 * f
+    assert rel_l2(ut, u + self_term) <= 1e-12
+    plan.close()
