@@ -333,14 +333,11 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
     int zeros = 0;  // candidates at distance 0 seen by this lane (its own target included once)
     vec4<T> zero4;
     zero4.x = zero4.y = zero4.z = zero4.w = 0;
+    int lo = 0;  // the lane's segment: pre[lo] <= v < pre[lo + 1] (positions only grow)
     for (int cb = 0; cb < total; cb += 32) {
         const int v = cb + lane;
         if (v < total) {
-            int lo = 0, hi = nrows;  // pre[lo] <= v < pre[hi]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (pre[mid] <= v) lo = mid; else hi = mid;
-            }
+            while (pre[lo + 1] <= v) lo++;
             const int m = seg[lo].x + (v - pre[lo]);
             vec4<T> xv = xs[m];
             xv.w = T(0);
@@ -505,14 +502,11 @@ __global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, R
     const int total = run;
     float acc[3] = {0.f, 0.f, 0.f}, ks[3] = {0.f, 0.f, 0.f}, kc[3] = {0.f, 0.f, 0.f};
     bool coinc = false;
+    int lo = 0;  // the lane's segment: pre[lo] <= v < pre[lo + 1] (positions only grow)
     for (int cb = 0; cb < total; cb += 32) {
         const int v = cb + lane;
         if (v < total) {
-            int lo = 0, hi = nrows;  // pre[lo] <= v < pre[hi]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (pre[mid] <= v) lo = mid; else hi = mid;
-            }
+            while (pre[lo + 1] <= v) lo++;
             const int m = seg[lo].x + (v - pre[lo]);
             sx[lane] = xs[m];
             sf[lane] = fs[m];
