@@ -24,21 +24,25 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+#ifndef SE_COL_NB
+#define SE_COL_NB 64
+#endif
+
 template <int P, int TE>
 struct ColCfg {
     static constexpr int PT = TE + P - 1;       // padded block edge
-    static constexpr int PTP = (PT + 3) / 4 * 4;  // z weights padded for 16-byte loads
+    static constexpr int PZ = (P + 3) / 4 * 4;  // z weights padded for 16-byte loads
     static constexpr int NT = (PT * PT + 31) / 32 * 32;
-    static constexpr int NB = 32;                 // points staged per batch
+    static constexpr int NB = SE_COL_NB;        // points staged per batch
 };
 
 // Shared staging of a batch of points: fractional positions relative to the
 // window start (grid units), offsets of the window in the padded block, the
-// three 1-D weight vectors (z shifted into the column).
+// three 1-D weight vectors.
 template <int P, int TE>
 struct ColStage {
     using C = ColCfg<P, TE>;
-    float wz[C::NB][C::PTP];
+    float wz[C::NB][C::PZ];
     float wx[C::NB][P];
     float wy[C::NB][P];
     float4 src[C::NB];
@@ -68,22 +72,72 @@ __device__ __forceinline__ void stage_point(ColStage<P, TE> &S, const GP<float> 
 // Stage 2 (all threads): the weights of the nb staged points.
 template <int P, int TE>
 __device__ __forceinline__ void stage_weights(ColStage<P, TE> &S, const GP<float> &g, int nb) {
-    constexpr int PT = ColCfg<P, TE>::PT, PER = 2 * P + PT;
+    constexpr int PER = 3 * P;
     for (int e = threadIdx.x; e < nb * PER; e += blockDim.x) {
-        const int j = e / PER, k = e - j * PER;
-        if (k < P) {
-            const float t = S.fr[j][0] - (float)k;
-            S.wx[j][k] = __expf(-g.ah2 * t * t);
-        } else if (k < 2 * P) {
-            const float t = S.fr[j][1] - (float)(k - P);
-            S.wy[j][k - P] = __expf(-g.ah2 * t * t);
-        } else {
-            const int z = k - 2 * P, kz = z - S.oz[j];
-            const float t = S.fr[j][2] - (float)kz;
-            S.wz[j][z] = (kz >= 0 && kz < P) ? __expf(-g.ah2 * t * t) : 0.0f;
+        const int j = e / PER, k = e - j * PER, d = k / P, kk = k - d * P;
+        const float t = S.fr[j][d] - (float)kk;
+        const float wv = __expf(-g.ah2 * t * t);
+        if (d == 0) S.wx[j][kk] = wv;
+        else if (d == 1) S.wy[j][kk] = wv;
+        else S.wz[j][kk] = wv;
+    }
+}
+
+// a_c[OZ + kz] += s_c wz[kz] for kz < P (the point's z support at offset OZ of the column)
+template <int P, int PT, int OZ>
+__device__ __forceinline__ void col_add(float (&a0)[PT], float (&a1)[PT], float (&a2)[PT], float s0, float s1,
+                                        float s2, const float *wz) {
+    const float4 *wz4 = reinterpret_cast<const float4 *>(wz);
+#pragma unroll
+    for (int q = 0; q < (P + 3) / 4; q++) {
+        const float4 v = wz4[q];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int kz = 4 * q + i;
+            if (kz < P) {
+                a0[OZ + kz] = fmaf(s0, vv[i], a0[OZ + kz]);
+                a1[OZ + kz] = fmaf(s1, vv[i], a1[OZ + kz]);
+                a2[OZ + kz] = fmaf(s2, vv[i], a2[OZ + kz]);
+            }
         }
     }
 }
+
+// p_c += sum_kz wz[kz] w_c[OZ + kz]
+template <int P, int PT, int OZ>
+__device__ __forceinline__ void col_dot(const float (&w0)[PT], const float (&w1)[PT], const float (&w2)[PT],
+                                        const float *wz, float &p0, float &p1, float &p2) {
+    const float4 *wz4 = reinterpret_cast<const float4 *>(wz);
+#pragma unroll
+    for (int q = 0; q < (P + 3) / 4; q++) {
+        const float4 v = wz4[q];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int kz = 4 * q + i;
+            if (kz < P) {
+                p0 = fmaf(vv[i], w0[OZ + kz], p0);
+                p1 = fmaf(vv[i], w1[OZ + kz], p1);
+                p2 = fmaf(vv[i], w2[OZ + kz], p2);
+            }
+        }
+    }
+}
+
+// the z offset of a point's support in the column selects a fully unrolled
+// copy (register indices must be compile-time constants)
+#define SE_COL_CASES(F, ...)                  \
+    switch (oz) {                             \
+        case 0: F<P, PT, 0>(__VA_ARGS__); break; \
+        case 1: F<P, PT, 1>(__VA_ARGS__); break; \
+        case 2: F<P, PT, 2>(__VA_ARGS__); break; \
+        case 3: F<P, PT, 3>(__VA_ARGS__); break; \
+        case 4: F<P, PT, 4>(__VA_ARGS__); break; \
+        case 5: F<P, PT, 5>(__VA_ARGS__); break; \
+        case 6: F<P, PT, 6>(__VA_ARGS__); break; \
+        default: F<P, PT, 7>(__VA_ARGS__); break; \
+    }
 
 template <int P, int TE>
 __device__ __forceinline__ void spread_col_body(const GP<float> &g, int tile, int beg, int end, int c0, bool stress,
@@ -91,7 +145,8 @@ __device__ __forceinline__ void spread_col_body(const GP<float> &g, int tile, in
                                                 int fstride, int foff, const float4 *__restrict__ qs,
                                                 float *__restrict__ grid) {
     using C = ColCfg<P, TE>;
-    constexpr int PT = C::PT, PTP = C::PTP, NB = C::NB;
+    constexpr int PT = C::PT, NB = C::NB;
+    static_assert(TE == 8, "the unrolled z offsets cover tiles of 8");
     __shared__ __align__(16) ColStage<P, TE> S;
     const int tid = threadIdx.x;
     const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
@@ -131,21 +186,8 @@ __device__ __forceinline__ void spread_col_body(const GP<float> &g, int tile, in
                     const float w = S.wx[j][kx] * S.wy[j][ky];
                     const float4 sv = S.src[j];
                     const float s0 = sv.x * w, s1 = sv.y * w, s2 = sv.z * w;
-                    const float4 *wz4 = reinterpret_cast<const float4 *>(S.wz[j]);
-#pragma unroll
-                    for (int q = 0; q < PTP / 4; q++) {
-                        const float4 v = wz4[q];
-                        const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int i = 0; i < 4; i++) {
-                            const int z = 4 * q + i;
-                            if (z < PT) {
-                                a0[z] = fmaf(s0, vv[i], a0[z]);
-                                a1[z] = fmaf(s1, vv[i], a1[z]);
-                                a2[z] = fmaf(s2, vv[i], a2[z]);
-                            }
-                        }
-                    }
+                    const int oz = S.oz[j];
+                    SE_COL_CASES(col_add, a0, a1, a2, s0, s1, s2, S.wz[j])
                 }
             }
         }
@@ -177,7 +219,8 @@ __device__ __forceinline__ void gather_col_body(const GP<float> &g, int tile, in
                                                 const float *__restrict__ f_orig, double self_coef,
                                                 float *__restrict__ u) {
     using C = ColCfg<P, TE>;
-    constexpr int PT = C::PT, PTP = C::PTP, NB = C::NB;
+    constexpr int PT = C::PT, NB = C::NB;
+    static_assert(TE == 8, "the unrolled z offsets cover tiles of 8");
     __shared__ __align__(16) ColStage<P, TE> S;
     const int tid = threadIdx.x, lane = tid & 31;
     const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
@@ -217,21 +260,8 @@ __device__ __forceinline__ void gather_col_body(const GP<float> &g, int tile, in
             if (!__any_sync(FULL, act)) continue;
             float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
             if (act) {
-                const float4 *wz4 = reinterpret_cast<const float4 *>(S.wz[j]);
-#pragma unroll
-                for (int q = 0; q < PTP / 4; q++) {
-                    const float4 v = wz4[q];
-                    const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int i = 0; i < 4; i++) {
-                        const int z = 4 * q + i;
-                        if (z < PT) {
-                            p0 = fmaf(vv[i], w0[z], p0);
-                            p1 = fmaf(vv[i], w1[z], p1);
-                            p2 = fmaf(vv[i], w2[z], p2);
-                        }
-                    }
-                }
+                const int oz = S.oz[j];
+                SE_COL_CASES(col_dot, w0, w1, w2, S.wz[j], p0, p1, p2)
                 const float wxy = S.wx[j][kx] * S.wy[j][ky];
                 p0 *= wxy;
                 p1 *= wxy;
