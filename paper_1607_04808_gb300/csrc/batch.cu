@@ -179,7 +179,7 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
     std::vector<se_params_t> pr(S);
     int Pmax = 0;
     for (int s = 0; s < S; s++) {
-        se_status_t st = choose_params(kernel, prec, N_s[s], box_s[4 * s + 3], tol, params, 0.0, &pr[s]);
+        se_status_t st = choose_params(kernel, prec, N_s[s], box_s[4 * s + 3], tol, params, 0.0, &pr[s], R);
         if (st != SE_OK) return st;
         Pmax = std::max(Pmax, pr[s].P);
     }
@@ -189,7 +189,7 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
         memset(&in, 0, sizeof(in));
         if (params) in = *params;
         in.P = Pmax;
-        se_status_t st = choose_params(kernel, prec, N_s[s], box_s[4 * s + 3], tol, &in, 0.0, &pr[s]);
+        se_status_t st = choose_params(kernel, prec, N_s[s], box_s[4 * s + 3], tol, &in, 0.0, &pr[s], R);
         if (st != SE_OK) return st;
     }
     B->P = Pmax;

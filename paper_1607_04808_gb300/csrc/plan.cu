@@ -85,7 +85,7 @@ bool good_fft(int n, int prec) {
 // FFT size, xi is the largest value whose Fourier estimate at the largest
 // admissible M meets the budget; otherwise xi minimises a work model.
 se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
-                          double xi_arg, se_params_t *out) {
+                          double xi_arg, se_params_t *out, int n_rhs) {
     se_params_t p;
     memset(&p, 0, sizeof(p));
     if (in) p = *in;
@@ -118,18 +118,28 @@ se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol,
             }
             xi = lo;
         } else {
-            // work model (relative units per GB300 stage): real-space pairs,
-            // spreading+gather grid updates, FFT points * log
+            // work model: time per ordered real-space pair, per spread+gather
+            // grid update (N P^3, twice) and per FFT point and level (Mf^3 log2 Mf,
+            // six transforms, the scaling folded in), relative to a pair.  FP64:
+            // measured on GB300 at N = 1e6 (200 ps per pair, 7.2 ps per update,
+            // 21 ps per FFT unit).  FP32 keeps weights that favour smaller xi: a
+            // larger xi moves more of the sum into the FP32 Fourier part, whose
+            // rounding error grows with it
             double best = 1e300, bxi = 1.0 / L;
-            double cpair = (prec == SE_FP32) ? 1.0 : 1.0, cgrid = 0.12, cfft = 0.6;
+            const double cpair = 1.0, cgrid = (prec == SE_FP32) ? 0.12 : 0.036,
+                         cfft = (prec == SE_FP32) ? 0.6 : 0.11;
             for (double x = 0.5 / L; x < 4000.0 / L; x *= 1.03) {
                 int M = min_M(kernel, Q, x, L, p.P, budget);
                 double rc = min_rc(kernel, Q, x, L, budget);
                 if (rc > L) continue;
                 double Mf = 2.0 * (M + p.P);
                 double pairs = (double)N * (double)N * 4.18879 * rc * rc * rc / (L * L * L);
-                double cost = cpair * pairs + cgrid * (double)N * p.P * p.P * p.P * 2.0 +
-                              cfft * Mf * Mf * Mf * log2(Mf) * 6.0;
+                // several right-hand sides: the grid and FFT work repeats per
+                // right-hand side, a pair's radial functions are shared (batches
+                // evaluate full candidate lists: 1.5 x a pair, +1/3 per extra side)
+                const double wpair = (n_rhs > 1) ? 1.5 * (1.0 + (n_rhs - 1) / 3.0) : 1.0;
+                double cost = cpair * wpair * pairs +
+                              n_rhs * (cgrid * (double)N * p.P * p.P * p.P * 2.0 + cfft * Mf * Mf * Mf * log2(Mf) * 6.0);
                 if (cost < best) { best = cost; bxi = x; }
             }
             xi = bxi;

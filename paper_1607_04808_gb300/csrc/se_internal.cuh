@@ -317,6 +317,6 @@ template <typename T> const GP<T> &gp(const se_plan_s *p);
 template <> inline const GP<float> &gp<float>(const se_plan_s *p) { return p->gpf; }
 template <> inline const GP<double> &gp<double>(const se_plan_s *p) { return p->gpd; }
 se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
-                          double xi_arg, se_params_t *out);
+                          double xi_arg, se_params_t *out, int n_rhs = 1);
 
 }  // namespace se
