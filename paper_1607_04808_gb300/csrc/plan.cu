@@ -285,7 +285,10 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
 #define SE_RS_XDIV 16.0
 #endif
     // FP32 (clustered evaluation): rc/5 across rows; FP64 (per-target rows): rc/3
-    const double yzdiv = (prec == SE_FP32) ? SE_RS_YZDIV32 : 3.0;
+#ifndef SE_RS_YZDIV64
+#define SE_RS_YZDIV64 3.0
+#endif
+    const double yzdiv = (prec == SE_FP32) ? SE_RS_YZDIV32 : SE_RS_YZDIV64;
     int ncd = (int)floor(yzdiv * p->L / p->rc);
     ncd = std::max(1, std::min(ncd, 200));
     int ncdx = (int)floor(SE_RS_XDIV * p->L / p->rc);
@@ -383,7 +386,7 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
             if ((e = dmalloc(&p->b.clusters, (Nn / 4 + nrows + 1) * sizeof(int2)))) break;
         }
         if ((e = dmalloc(&p->b.cnt_r, scan_len(p->ncells) * 4))) break;
-        if (prec == SE_FP32 && (e = dmalloc(&p->b.uj, Nn * sizeof(float4)))) break;
+        if ((e = dmalloc(&p->b.uj, Nn * 4 * esz))) break;
         if ((e = dmalloc(&p->b.status, 16))) break;
         if ((e = cudaMemset(p->grid, 0, (size_t)p->nc * Mf3 * esz))) break;
         if ((e = cudaMemset(p->b.status, 0, 16))) break;

@@ -420,44 +420,46 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
 #ifndef SE_RS_SYM_MINB
 #define SE_RS_SYM_MINB 4
 #endif
-template <int KERNEL, int PV, int TPW>
-__global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, RC<float> rk, const float4 *__restrict__ xs,
-                                                  const float4 *__restrict__ fs, const float4 *__restrict__ qs,
-                                                  const int *__restrict__ cell_start,
-                                                  const int2 *__restrict__ clusters, const int *__restrict__ ncl_total,
-                                                  const int *__restrict__ perm, float *__restrict__ u,
-                                                  float4 *__restrict__ uj, int *__restrict__ status) {
+// uj holds 4 values of T per sorted point (x, y, z, unused).  FP64 keeps two
+// blocks per SM (its accumulators need twice the registers).
+template <typename T, int KERNEL, int PV, int TPW>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
+    k_real_sym(GP<T> g, RC<T> rk, const vec4<T> *__restrict__ xs, const vec4<T> *__restrict__ fs,
+               const vec4<T> *__restrict__ qs, const int *__restrict__ cell_start, const int2 *__restrict__ clusters,
+               const int *__restrict__ ncl_total, const int *__restrict__ perm, T *__restrict__ u,
+               T *__restrict__ uj, int *__restrict__ status) {
     // lane = (target k = lane % TPW, stream s = lane / TPW); each staged chunk of
     // 32 candidates gives every stream NC = TPW of them
     constexpr int WPB = 8, NS = 32 / TPW, NC = TPW;
-    __shared__ float4 sx_all[WPB][32];
-    __shared__ float4 sf_all[WPB][32];
-    __shared__ float4 sq_all[KERNEL == SE_STRESSLET ? WPB : 1][32];
+    __shared__ vec4<T> sx_all[WPB][32];
+    __shared__ vec4<T> sf_all[WPB][32];
+    __shared__ vec4<T> sq_all[KERNEL == SE_STRESSLET ? WPB : 1][32];
     __shared__ int sm_all[WPB][32];
     __shared__ int2 seg_all[WPB][MAXROWS];
     __shared__ int pre_all[WPB][MAXROWS + 1];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * WPB + wib;
     if (c >= *ncl_total) return;
-    float4 *sx = sx_all[wib];
-    float4 *sf = sf_all[wib];
-    float4 *sq = sq_all[KERNEL == SE_STRESSLET ? wib : 0];
+    vec4<T> *sx = sx_all[wib];
+    vec4<T> *sf = sf_all[wib];
+    vec4<T> *sq = sq_all[KERNEL == SE_STRESSLET ? wib : 0];
     int *smi = sm_all[wib];
     int2 *seg = seg_all[wib];
     const int2 cl = clusters[c];
     const int k = lane % TPW, s = lane / TPW;
     const bool has = k < cl.y;
     const int t = cl.x + min(k, cl.y - 1);
-    float4 xt = xs[t];
-    if (!has) xt.x = __int_as_float(0x7f800000);  // +inf: no candidate passes the cutoff test
-    const float4 ft = fs[t];
-    float4 qt = make_float4(0.f, 0.f, 0.f, 0.f);
+    vec4<T> xt = xs[t];
+    if (!has) xt.x = T(INFINITY);  // no candidate passes the cutoff test
+    const vec4<T> ft = fs[t];
+    vec4<T> qt;
+    qt.x = qt.y = qt.z = qt.w = T(0);
     if (KERNEL == SE_STRESSLET) qt = qs[t];
     int c0[3], c1[3];
     unpack3(get_tag(xs[cl.x]), c0[0], c0[1], c0[2]);
     unpack3(get_tag(xs[cl.x + cl.y - 1]), c1[0], c1[1], c1[2]);
     const int R = rk.reach, W = 2 * R + 1, nrows = W * W;
-    const float rc2m = rk.rc2 * 1.0001f;
+    const T rc2m = rk.rc2 * T(1.0001);
     const int own_row = c0[2] * g.ncd + c0[1];
     // rows at or after the cluster's row in the sorted order; the own row from
     // the cluster's first point on, so that it leads the stream and stream
@@ -468,12 +470,12 @@ __global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, R
         int2 sg = make_int2(0, 0);
         const int row = iz * g.ncd + iy;
         if (iy >= 0 && iy < g.ncd && iz >= 0 && iz < g.ncd && row >= own_row) {
-            const float dy = float(max(abs(dyc) - 1, 0)) * g.cw, dz = float(max(abs(dzc) - 1, 0)) * g.cw;
-            const float d2 = dy * dy + dz * dz;
+            const T dy = T(max(abs(dyc) - 1, 0)) * g.cw, dz = T(max(abs(dzc) - 1, 0)) * g.cw;
+            const T d2 = dy * dy + dz * dz;
             if (d2 <= rc2m) {
-                const float del = sqrtf(rc2m - d2) + 1e-4f * g.cwx;
-                const int ixl = max(0, (int)floorf((float(c0[0]) * g.cwx - del) * g.inv_cwx));
-                const int ixh = min(g.ncdx - 1, (int)floorf((float(c1[0] + 1) * g.cwx + del) * g.inv_cwx));
+                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cwx;
+                const int ixl = max(0, (int)floor((T(c0[0]) * g.cwx - del) * g.inv_cwx));
+                const int ixh = min(g.ncdx - 1, (int)floor((T(c1[0] + 1) * g.cwx + del) * g.inv_cwx));
                 if (ixl <= ixh) {
                     const int base = row * g.ncdx;
                     sg = make_int2(cell_start[base + ixl], cell_start[base + ixh + 1]);
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, R
     if (lane == 0) pre[nrows] = run;
     __syncwarp();
     const int total = run;
-    float acc[3] = {0.f, 0.f, 0.f}, ks[3] = {0.f, 0.f, 0.f}, kc[3] = {0.f, 0.f, 0.f};
+    T acc[3] = {0, 0, 0}, ks[3] = {0, 0, 0}, kc[3] = {0, 0, 0};
     bool coinc = false;
     int lo = 0;  // the lane's segment: pre[lo] <= v < pre[lo + 1] (positions only grow)
     for (int cb = 0; cb < total; cb += 32) {
@@ -515,26 +517,26 @@ __global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, R
         }
         __syncwarp();
         const int nch = min(32, total - cb);
-        float aj[NC][3];
+        T aj[NC][3];
 #pragma unroll
-        for (int i = 0; i < NC; i++) aj[i][0] = aj[i][1] = aj[i][2] = 0.f;
+        for (int i = 0; i < NC; i++) aj[i][0] = aj[i][1] = aj[i][2] = T(0);
         // one (target, candidate) pair: candidate slot j, stream position cb + j;
         // it counts when the candidate comes after the target (position > k)
         auto step = [&](int i, int j) {
-            const float4 xv = sx[j];
-            const float dx = xt.x - xv.x, dy = xt.y - xv.y, dz = xt.z - xv.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
+            const vec4<T> xv = sx[j];
+            const T dx = xt.x - xv.x, dy = xt.y - xv.y, dz = xt.z - xv.z;
+            const T r2 = dx * dx + dy * dy + dz * dz;
             if (r2 <= rk.rc2 && cb + j > k) {
-                if (r2 > 0.f) {
-                    float rinv, a, b;
+                if (r2 > T(0)) {
+                    T rinv, a, b;
                     radial_ab<KERNEL, PV>(rk, r2, rinv, a, b);
-                    const float4 fv = sf[j];
+                    const vec4<T> fv = sf[j];
                     if (KERNEL == SE_STOKESLET) {
-                        const float bj = b * (dx * fv.x + dy * fv.y + dz * fv.z);
+                        const T bj = b * (dx * fv.x + dy * fv.y + dz * fv.z);
                         acc[0] += a * fv.x + bj * dx;
                         acc[1] += a * fv.y + bj * dy;
                         acc[2] += a * fv.z + bj * dz;
-                        const float bt = b * (dx * ft.x + dy * ft.y + dz * ft.z);
+                        const T bt = b * (dx * ft.x + dy * ft.y + dz * ft.z);
                         aj[i][0] += a * ft.x + bt * dx;
                         aj[i][1] += a * ft.y + bt * dy;
                         aj[i][2] += a * ft.z + bt * dz;
@@ -546,22 +548,22 @@ __global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, R
                         aj[i][1] -= b * (ft.z * dx - ft.x * dz);
                         aj[i][2] -= b * (ft.x * dy - ft.y * dx);
                     } else {
-                        const float4 qv = sq[j];
-                        const float hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
+                        const vec4<T> qv = sq[j];
+                        const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
                         {
-                            const float hf = hx * fv.x + hy * fv.y + hz * fv.z;
-                            const float hq = hx * qv.x + hy * qv.y + hz * qv.z;
-                            const float fq = fv.x * qv.x + fv.y * qv.y + fv.z * qv.z;
-                            const float a1 = a * hf * hq;
+                            const T hf = hx * fv.x + hy * fv.y + hz * fv.z;
+                            const T hq = hx * qv.x + hy * qv.y + hz * qv.z;
+                            const T fq = fv.x * qv.x + fv.y * qv.y + fv.z * qv.z;
+                            const T a1 = a * hf * hq;
                             acc[0] += a1 * hx + b * (hx * fq + fv.x * hq + qv.x * hf);
                             acc[1] += a1 * hy + b * (hy * fq + fv.y * hq + qv.y * hf);
                             acc[2] += a1 * hz + b * (hz * fq + fv.z * hq + qv.z * hf);
                         }
                         {
-                            const float hf = hx * ft.x + hy * ft.y + hz * ft.z;
-                            const float hq = hx * qt.x + hy * qt.y + hz * qt.z;
-                            const float fq = ft.x * qt.x + ft.y * qt.y + ft.z * qt.z;
-                            const float a1 = a * hf * hq;
+                            const T hf = hx * ft.x + hy * ft.y + hz * ft.z;
+                            const T hq = hx * qt.x + hy * qt.y + hz * qt.z;
+                            const T fq = ft.x * qt.x + ft.y * qt.y + ft.z * qt.z;
+                            const T a1 = a * hf * hq;
                             aj[i][0] -= a1 * hx + b * (hx * fq + ft.x * hq + qt.x * hf);
                             aj[i][1] -= a1 * hy + b * (hy * fq + ft.y * hq + qt.y * hf);
                             aj[i][2] -= a1 * hz + b * (hz * fq + ft.z * hq + qt.z * hf);
@@ -582,7 +584,7 @@ __global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, R
         }
         for (int d = 0; d < 3; d++) {
             kahan_add(ks[d], kc[d], acc[d]);
-            acc[d] = 0.f;
+            acc[d] = T(0);
         }
         // reduce-scatter over the TPW lanes of the stream: afterwards aj[0] of
         // lane k holds the total of candidate i = k (slot s + NS k)
@@ -593,22 +595,30 @@ __global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, R
             for (int q = 0; q < h; q++)
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    const float send = up ? aj[q][d] : aj[q + h][d];
-                    const float keep = up ? aj[q + h][d] : aj[q][d];
+                    const T send = up ? aj[q][d] : aj[q + h][d];
+                    const T keep = up ? aj[q + h][d] : aj[q][d];
                     aj[q][d] = keep + __shfl_xor_sync(FULL, send, h);
                 }
         }
         const int jm = s + NS * k;
-        if (jm < nch && (aj[0][0] != 0.f || aj[0][1] != 0.f || aj[0][2] != 0.f))
-            atomicAdd(uj + smi[jm], make_float4(aj[0][0], aj[0][1], aj[0][2], 0.f));
+        if (jm < nch && (aj[0][0] != T(0) || aj[0][1] != T(0) || aj[0][2] != T(0))) {
+            T *dst = uj + 4 * (size_t)smi[jm];
+            if constexpr (sizeof(T) == 4) {
+                atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(aj[0][0], aj[0][1], aj[0][2], 0.f));
+            } else {
+                atomicAdd(dst, aj[0][0]);
+                atomicAdd(dst + 1, aj[0][1]);
+                atomicAdd(dst + 2, aj[0][2]);
+            }
+        }
         __syncwarp();
     }
     // combine the NS streams of each target
-    float tot[3];
+    T tot[3];
     for (int d = 0; d < 3; d++) {
-        float sm_ = ks[d], cm_ = kc[d];
+        T sm_ = ks[d], cm_ = kc[d];
         for (int o = TPW; o < 32; o <<= 1) {
-            const float so = __shfl_xor_sync(FULL, sm_, o), co = __shfl_xor_sync(FULL, cm_, o);
+            const T so = __shfl_xor_sync(FULL, sm_, o), co = __shfl_xor_sync(FULL, cm_, o);
             kahan_add(sm_, cm_, so);
             cm_ += co;
         }
@@ -617,19 +627,17 @@ __global__ void __launch_bounds__(256, SE_RS_SYM_MINB) k_real_sym(GP<float> g, R
     if (__any_sync(FULL, coinc) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
     if (s == 0 && has) {
         const int mi = perm[t];
-        for (int d = 0; d < 3; d++) u[3 * mi + d] = (float)((double)u[3 * mi + d] + (double)tot[d]);
+        for (int d = 0; d < 3; d++) u[3 * mi + d] = (T)((double)u[3 * mi + d] + (double)tot[d]);
     }
 }
 
 // u[perm[n]] += uj[n] (the contributions scattered to the candidates)
-__global__ void k_add_uj(int N, const float4 *__restrict__ uj, const int *__restrict__ perm, float *__restrict__ u) {
+template <typename T>
+__global__ void k_add_uj(int N, const T *__restrict__ uj, const int *__restrict__ perm, T *__restrict__ u) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const float4 v = uj[n];
     const int m = perm[n];
-    u[3 * m] = (float)((double)u[3 * m] + (double)v.x);
-    u[3 * m + 1] = (float)((double)u[3 * m + 1] + (double)v.y);
-    u[3 * m + 2] = (float)((double)u[3 * m + 2] + (double)v.z);
+    for (int d = 0; d < 3; d++) u[3 * m + d] = (T)((double)u[3 * m + d] + (double)uj[4 * (size_t)n + d]);
 }
 
 // Batched cluster lists: row `row` of all systems' cell rows belongs to the
@@ -956,6 +964,9 @@ inline int real_pv(double xi_rc) { return xi_rc <= 5.0 ? 1 : 0; }
 #ifndef SE_RS_SYM_TPW
 #define SE_RS_SYM_TPW 8
 #endif
+#ifndef SE_RS_SYM_TPW64
+#define SE_RS_SYM_TPW64 8
+#endif
 
 #ifndef SE_RS_TPW
 #define SE_RS_TPW 16
@@ -967,16 +978,16 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r,
                   *qs = (const vec4<T> *)p->b.qs_r;
     const GP<T> &g = gp<T>(p);
-    if (sizeof(T) == 8) {
+    if (sizeof(T) == 8 && !(p->b.uj && SE_RS_SYM)) {
         if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
         k_real_cmp<T, KERNEL><<<(N + 7) / 8, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, u,
                                                            p->b.status);
         p->launches++;
         return cudaGetLastError();
     }
-    const bool sym = sizeof(T) == 4 && p->b.uj && SE_RS_SYM;
+    const bool sym = p->b.uj && SE_RS_SYM;
     // targets per cluster: the symmetric kernel's or the full-list kernel's
-    constexpr int TPW = SE_RS_TPW, TPWS = SE_RS_SYM_TPW;
+    constexpr int TPW = SE_RS_TPW, TPWS = sizeof(T) == 4 ? SE_RS_SYM_TPW : SE_RS_SYM_TPW64;
     const int tpw = sym ? TPWS : TPW;
     const int nrows = p->geom.ncd * p->geom.ncd;
     k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, tpw, p->b.cnt_r, p->b.ncl);
@@ -987,21 +998,17 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
     const unsigned nblk = (unsigned)((max_cl + 7) / 8);
     if (sym) {
         // each pair once, the candidate's share through uj
-        cudaError_t e = cudaMemsetAsync(p->b.uj, 0, sizeof(float4) * (size_t)N, st);
+        cudaError_t e = cudaMemsetAsync(p->b.uj, 0, 4 * sizeof(T) * (size_t)N, st);
         if (e) return e;
         if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
-        const GP<float> &gf = p->gpf;
-        const RC<float> rkf = make_rc<float>(p);
-        const float4 *x4 = (const float4 *)xs, *f4 = (const float4 *)fs, *q4 = (const float4 *)qs;
+        T *ujt = (T *)p->b.uj;
         if (real_pv(p->xi * p->rc) == 1)
-            k_real_sym<KERNEL, 1, TPWS><<<nblk, 256, 0, st>>>(gf, rkf, x4, f4, q4, p->b.cnt_r, p->b.clusters,
-                                                             p->b.ncl + nrows, p->b.perm_r, (float *)u, p->b.uj,
-                                                             p->b.status);
+            k_real_sym<T, KERNEL, 1, TPWS><<<nblk, 256, 0, st>>>(g, rk, xs, fs, qs, p->b.cnt_r, p->b.clusters,
+                                                                p->b.ncl + nrows, p->b.perm_r, u, ujt, p->b.status);
         else
-            k_real_sym<KERNEL, 0, TPWS><<<nblk, 256, 0, st>>>(gf, rkf, x4, f4, q4, p->b.cnt_r, p->b.clusters,
-                                                             p->b.ncl + nrows, p->b.perm_r, (float *)u, p->b.uj,
-                                                             p->b.status);
-        k_add_uj<<<(N + 255) / 256, 256, 0, st>>>(N, p->b.uj, p->b.perm_r, (float *)u);
+            k_real_sym<T, KERNEL, 0, TPWS><<<nblk, 256, 0, st>>>(g, rk, xs, fs, qs, p->b.cnt_r, p->b.clusters,
+                                                                p->b.ncl + nrows, p->b.perm_r, u, ujt, p->b.status);
+        k_add_uj<T><<<(N + 255) / 256, 256, 0, st>>>(N, ujt, p->b.perm_r, u);
         p->launches += 4 + scan_launch_count(nrows);
         return cudaGetLastError();
     }

@@ -178,7 +178,7 @@ struct Buffers {
     int *tag_r = nullptr;   // N packed cell coordinates (original order)
     int *ncl = nullptr;     // clusters per row of cells, then their exclusive scan (+ total)
     int2 *clusters = nullptr;  // (first sorted index, count) of each real-space cluster
-    float4 *uj = nullptr;      // FP32: real-space contributions scattered to candidates (sorted order)
+    void *uj = nullptr;        // real-space contributions scattered to candidates (4 values per sorted point)
     int *status = nullptr;  // device flags
 };
 
