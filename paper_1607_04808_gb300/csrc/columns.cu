@@ -291,6 +291,182 @@ __device__ __forceinline__ void gather_col_body(const GP<float> &g, int tile, in
     }
 }
 
+// Gather with the tile's padded block in shared memory: the CTA stages the
+// PT^3 block of the three grids once (coalesced rows), then each warp takes
+// one point at a time, its lanes covering the (x, y) columns of the P x P
+// support and reading the P values of each column from shared memory.  Every
+// grid value is read from L2 once per tile and from shared memory once per
+// point that uses it; no cross-warp reduction.
+#ifndef SE_GS_WARPS
+#define SE_GS_WARPS 16
+#endif
+constexpr int GS_WARPS = SE_GS_WARPS;
+
+// Row pitch of the staged block and the largest number of support columns per
+// lane: the lanes of a warp read column (kx, ky) at offset ky * pitch + kx, so
+// each lane takes the columns whose offset is its own lane id mod 32 (one
+// shared-memory bank per lane, no conflicts); the pitch >= PT minimising the
+// largest such class.
+template <int P, int PT>
+struct GsLayout {
+    static constexpr int count(int pitch) {
+        int worst = 0;
+        for (int r = 0; r < 32; r++) {
+            int n = 0;
+            for (int ky = 0; ky < P; ky++)
+                for (int kx = 0; kx < P; kx++)
+                    if ((ky * pitch + kx) % 32 == r) n++;
+            worst = n > worst ? n : worst;
+        }
+        return worst;
+    }
+    static constexpr int best_pitch() {
+        int bp = PT, bn = count(PT);
+        for (int q = PT + 1; q <= PT + 8; q++)
+            if (count(q) < bn) { bn = count(q); bp = q; }
+        return bp;
+    }
+    static constexpr int PX = best_pitch();
+    static constexpr int NIT = count(PX);
+};
+
+template <int P, int TE>
+__device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, int beg, int end,
+                                                 const float4 *__restrict__ xs, const int *__restrict__ perm,
+                                                 const float *__restrict__ w, int n_rhs, int r,
+                                                 const float *__restrict__ f_orig, double self_coef,
+                                                 float *__restrict__ u) {
+    constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
+    constexpr int ROWS = 3 * PT * PT, PLANE = PT * PX, COMP = PT * PLANE;
+    extern __shared__ __align__(16) float sg[];  // [c][z][y][x], x pitch PX
+    __shared__ float swt[GS_WARPS][3][P];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
+    const size_t Mf = g.Mf, Mf3 = Mf * Mf * Mf;
+    // flat copy of the block (x fastest), several independent loads in flight per thread
+#pragma unroll 8
+    for (int e = threadIdx.x; e < ROWS * PT; e += GS_WARPS * 32) {
+        const int row = e / PT, x = e - row * PT, c = row / (PT * PT), zy = row - c * PT * PT, z = zy / PT,
+                  y = zy - z * PT;
+        const int gz = gz0 + z, gy = gy0 + y, gx = gx0 + x;
+        sg[row * PX + x] = (gz < g.Mt && gy < g.Mt && gx < g.Mt)
+                               ? __ldg(w + (size_t)c * Mf3 + ((size_t)gz * Mf + gy) * Mf + gx)
+                               : 0.0f;
+    }
+    __syncthreads();
+    // this lane's support columns: those at offset ky * PX + kx = lane (mod 32)
+    int kxs[NIT], kys[NIT];
+    bool val[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; it++) {
+        val[it] = false;
+        kxs[it] = kys[it] = 0;
+    }
+    {
+        int it = 0;
+        for (int ky = 0; ky < P; ky++)
+            for (int kx = 0; kx < P; kx++)
+                if ((ky * PX + kx) % 32 == lane) {
+#pragma unroll
+                    for (int q = 0; q < NIT; q++)
+                        if (q == it) {
+                            kxs[q] = kx;
+                            kys[q] = ky;
+                            val[q] = true;
+                        }
+                    it++;
+                }
+    }
+    for (int n = beg + warp; n < end; n += GS_WARPS) {
+        const float4 xv = xs[n];
+        int i0[3];
+        unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+        if (lane < P) {
+            const float fr0 = ((xv.x - g.x0[0]) * g.inv_h + g.half_ext) - (float)i0[0] - (float)lane;
+            const float fr1 = ((xv.y - g.x0[1]) * g.inv_h + g.half_ext) - (float)i0[1] - (float)lane;
+            const float fr2 = ((xv.z - g.x0[2]) * g.inv_h + g.half_ext) - (float)i0[2] - (float)lane;
+            swt[warp][0][lane] = __expf(-g.ah2 * fr0 * fr0);
+            swt[warp][1][lane] = __expf(-g.ah2 * fr1 * fr1);
+            swt[warp][2][lane] = __expf(-g.ah2 * fr2 * fr2);
+        }
+        __syncwarp();
+        const int ox = min(max(i0[0] - gx0, 0), TE - 1), oy = min(max(i0[1] - gy0, 0), TE - 1),
+                  oz = min(max(i0[2] - gz0, 0), TE - 1);
+        float wz[P];
+#pragma unroll
+        for (int kz = 0; kz < P; kz++) wz[kz] = swt[warp][2][kz];
+        float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
+#pragma unroll
+        for (int it = 0; it < NIT; it++) {
+            if (val[it]) {
+                const float wxy = swt[warp][0][kxs[it]] * swt[warp][1][kys[it]];
+                const float *col = sg + oz * PLANE + (oy + kys[it]) * PX + ox + kxs[it];
+                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+#pragma unroll
+                for (int kz = 0; kz < P; kz++) {
+                    a0 = fmaf(col[kz * PLANE], wz[kz], a0);
+                    a1 = fmaf(col[COMP + kz * PLANE], wz[kz], a1);
+                    a2 = fmaf(col[2 * COMP + kz * PLANE], wz[kz], a2);
+                }
+                acc0 = fmaf(a0, wxy, acc0);
+                acc1 = fmaf(a1, wxy, acc1);
+                acc2 = fmaf(a2, wxy, acc2);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc0 += __shfl_xor_sync(FULL, acc0, o);
+            acc1 += __shfl_xor_sync(FULL, acc1, o);
+            acc2 += __shfl_xor_sync(FULL, acc2, o);
+        }
+        if (lane < 3) {
+            const size_t o3 = ((size_t)perm[n] * n_rhs + r) * 3 + lane;
+            double o = (double)(lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2));
+            if (self_coef != 0.0) o += self_coef * (double)f_orig[o3];
+            u[o3] = (float)o;
+        }
+        __syncwarp();
+    }
+}
+
+template <int P, int TE>
+__global__ void __launch_bounds__(GS_WARPS * 32) k_gather_smem(GP<float> g, const int *__restrict__ tile_start,
+                                                               const float4 *__restrict__ xs,
+                                                               const int *__restrict__ perm,
+                                                               const float *__restrict__ w,
+                                                               const float *__restrict__ f_orig, double self_coef,
+                                                               float *__restrict__ u) {
+    const int tile = blockIdx.x;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    gather_smem_body<P, TE>(g, tile, beg, end, xs, perm, w, 1, 0, f_orig, self_coef, u);
+}
+
+template <int P, int TE>
+__global__ void __launch_bounds__(GS_WARPS * 32) k_bgather_smem(const BSys<float> *__restrict__ sys,
+                                                                const int4 *__restrict__ items,
+                                                                const int *__restrict__ tile_start, int n_rhs,
+                                                                const float4 *__restrict__ xs,
+                                                                const int *__restrict__ perm,
+                                                                const float *__restrict__ f_orig,
+                                                                float *__restrict__ u) {
+    const int4 it = items[blockIdx.x];
+    const BSys<float> &B = sys[it.x];
+    const int key = B.tile_base + it.y;
+    const int beg = tile_start[key], end = tile_start[key + 1];
+    if (beg == end) return;
+    const GP<float> g = B.g;
+    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    gather_smem_body<P, TE>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * Mf3, n_rhs, it.z, f_orig,
+                            B.self_coef, u);
+}
+
+template <int P, int TE>
+constexpr size_t gather_smem_bytes() {
+    return (size_t)3 * (TE + P - 1) * (TE + P - 1) * GsLayout<P, TE + P - 1>::PX * sizeof(float);
+}
+
 template <int P, int TE>
 __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_spread_col(GP<float> g, int c0, bool stress,
                                                                     const int *__restrict__ tile_start,
@@ -378,11 +554,23 @@ struct SpreadRun {
     }
 };
 
+#ifndef SE_GATHER_SMEM
+#define SE_GATHER_SMEM 1
+#endif
+
 template <int P, int TE>
 struct GatherRun {
     static cudaError_t run(const GP<float> g, int ntiles, const int *ts, const float4 *xs, const int *perm,
                            const float *w, const float *f, double self_coef, float *u, cudaStream_t st) {
-        k_gather_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, ts, xs, perm, w, f, self_coef, u);
+        if (SE_GATHER_SMEM) {
+            const size_t smem = gather_smem_bytes<P, TE>();
+            cudaError_t e = cudaFuncSetAttribute(k_gather_smem<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e) return e;
+            k_gather_smem<P, TE><<<ntiles, GS_WARPS * 32, smem, st>>>(g, ts, xs, perm, w, f, self_coef, u);
+        } else {
+            k_gather_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, ts, xs, perm, w, f, self_coef, u);
+        }
         return cudaGetLastError();
     }
 };
@@ -400,7 +588,15 @@ template <int P, int TE>
 struct BGatherRun {
     static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
                            const float4 *xs, const int *perm, const float *f, float *u, cudaStream_t st) {
-        k_bgather_col<P, TE><<<nitems, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, perm, f, u);
+        if (SE_GATHER_SMEM) {
+            const size_t smem = gather_smem_bytes<P, TE>();
+            cudaError_t e = cudaFuncSetAttribute(k_bgather_smem<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e) return e;
+            k_bgather_smem<P, TE><<<nitems, GS_WARPS * 32, smem, st>>>(sys, items, ts, n_rhs, xs, perm, f, u);
+        } else {
+            k_bgather_col<P, TE><<<nitems, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, perm, f, u);
+        }
         return cudaGetLastError();
     }
 };
