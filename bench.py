@@ -36,7 +36,7 @@ FLOP_PER_PAIR = 58
 # DRAM bytes (read + write) of one launch of the FP32 stokeslet real-space kernel on
 # this workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 # Set to None whenever that kernel changes, until it is captured again.
-REAL_TRAFFIC_BYTES = None
+REAL_TRAFFIC_BYTES = 67_270_656 + 3_860_992
 
 
 def pair_fraction_unit_cube(r: float) -> float:
