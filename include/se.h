@@ -238,6 +238,17 @@ se_status_t se_plan_set_timing(se_plan_t plan, int on);
  * Returns -1 for a NULL plan. */
 int64_t se_plan_launch_count(se_plan_t plan);
 
+/* The precomputed kernel (Section 4.3) depends only on the Green's function,
+ * the grid sizes and h, not on xi, P or the points, so plans with equal grids
+ * share it: a host-side cache (on by default, `memory` = 1; 0 turns it off and
+ * empties it) and, when `dir` is not NULL, one file per grid in that directory
+ * (read before computing, written after).  Process-wide; thread-safe. */
+se_status_t se_set_precompute_cache(int memory, const char *dir);
+
+/* Time the plan's precomputation took (ms; for a cache hit, the time of the
+ * lookup and upload) and whether it came from the cache (1) or was computed. */
+se_status_t se_plan_precompute_info(se_plan_t plan, double *ms, int *cached);
+
 /* Destroy the plan and free its device memory (synchronises the device). */
 se_status_t se_plan_destroy(se_plan_t plan);
 

@@ -7,6 +7,13 @@
 //     stored wrap-ordered on the (2 Mt)^3 grid;
 //  4. forward FFT (real-to-complex); the result is real and even, so the
 //     (Mt+1)^3 octant of its real part is all the scaling step needs.
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "se_internal.cuh"
@@ -83,9 +90,7 @@ __global__ void k_octant(int Mt, const cufftDoubleComplex *spec, double *oct64, 
     if (oct32) oct32[idx] = (float)v;
 }
 
-}  // namespace
-
-se_status_t precompute(se_plan_s *p) {
+se_status_t precompute_compute(se_plan_s *p) {
     const int Mg = p->Mg, Mt = p->Mt, Mf = p->Mf;
     const size_t nkg = (size_t)Mg * Mg * (Mg / 2 + 1);
     const size_t ng = (size_t)Mg * Mg * Mg;
@@ -162,4 +167,150 @@ se_status_t precompute(se_plan_s *p) {
     return st;
 }
 
+// ---------------------------------------------------------------- cache
+// The precomputed octant depends only on the Green's function (harmonic or
+// biharmonic), Mg, Mt and h (R = sqrt(3) Mt h): not on xi, P or the points.
+// Plans with the same grid reuse it from a host-side cache, and optionally
+// from files in a directory (one file per key, written after computing).
+struct CacheEntry {
+    std::vector<double> oct;
+    uint64_t stamp = 0;
+};
+std::mutex g_cache_mu;
+std::map<std::string, CacheEntry> g_cache;
+bool g_cache_on = true;
+std::string g_cache_dir;
+uint64_t g_stamp = 0;
+constexpr size_t CACHE_MAX_BYTES = size_t(2) << 30;  // evict the oldest entries beyond 2 GB
+
+std::string cache_key(const se_plan_s *p) {
+    uint64_t hb;
+    memcpy(&hb, &p->h, sizeof(hb));
+    char buf[128];
+    snprintf(buf, sizeof(buf), "%s_Mg%d_Mt%d_h%016llx", p->kernel == SE_ROTLET ? "H" : "B", p->Mg, p->Mt,
+             (unsigned long long)hb);
+    return buf;
+}
+
+constexpr uint64_t FILE_MAGIC = 0x5345474841543031ull;  // file format tag
+
+bool read_file(const std::string &path, size_t n, std::vector<double> &out) {
+    FILE *fp = fopen(path.c_str(), "rb");
+    if (!fp) return false;
+    uint64_t hdr[2] = {0, 0};
+    bool ok = fread(hdr, sizeof(uint64_t), 2, fp) == 2 && hdr[0] == FILE_MAGIC && hdr[1] == n;
+    if (ok) {
+        out.resize(n);
+        ok = fread(out.data(), sizeof(double), n, fp) == n;
+    }
+    fclose(fp);
+    return ok;
+}
+
+void write_file(const std::string &path, const std::vector<double> &v) {
+    const std::string tmp = path + ".tmp";
+    FILE *fp = fopen(tmp.c_str(), "wb");
+    if (!fp) return;
+    const uint64_t hdr[2] = {FILE_MAGIC, (uint64_t)v.size()};
+    bool ok = fwrite(hdr, sizeof(uint64_t), 2, fp) == 2 && fwrite(v.data(), sizeof(double), v.size(), fp) == v.size();
+    ok = (fclose(fp) == 0) && ok;
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else remove(tmp.c_str());
+}
+
+// upload a cached octant into the plan (and its FP32 copy)
+se_status_t upload(se_plan_s *p, const std::vector<double> &oct) {
+    const size_t n = oct.size();
+    if (cudaMemcpy(p->ghat64, oct.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(SE_ERR_CUDA, "precompute: cache upload failed");
+    if (p->prec == SE_FP32) {
+        std::vector<float> o32(n);
+        for (size_t i = 0; i < n; i++) o32[i] = (float)oct[i];
+        if (cudaMemcpy(p->ghat, o32.data(), n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(SE_ERR_CUDA, "precompute: cache upload failed");
+    } else {
+        p->ghat = p->ghat64;
+    }
+    return SE_OK;
+}
+
+}  // namespace
+
+se_status_t precompute(se_plan_s *p) {
+    const size_t n = (size_t)(p->Mt + 1) * (p->Mt + 1) * (p->Mt + 1);
+    const auto t0 = std::chrono::steady_clock::now();
+    const std::string key = cache_key(p);
+    std::vector<double> oct;
+    bool hit = false;
+    std::string dir;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        dir = g_cache_dir;
+        if (g_cache_on) {
+            auto it = g_cache.find(key);
+            if (it != g_cache.end() && it->second.oct.size() == n) {
+                oct = it->second.oct;
+                it->second.stamp = ++g_stamp;
+                hit = true;
+            }
+        }
+    }
+    if (!hit && !dir.empty()) hit = read_file(dir + "/se_ghat_" + key + ".bin", n, oct);
+    se_status_t st;
+    if (hit) {
+        st = upload(p, oct);
+        p->precompute_cached = true;
+    } else {
+        st = precompute_compute(p);
+        if (st != SE_OK) return st;
+        p->precompute_cached = false;
+        if (g_cache_on || !dir.empty()) {
+            oct.resize(n);
+            if (cudaMemcpy(oct.data(), p->ghat64, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(SE_ERR_CUDA, "precompute: cache download failed");
+            if (!dir.empty()) write_file(dir + "/se_ghat_" + key + ".bin", oct);
+        }
+    }
+    if (st == SE_OK && g_cache_on && !oct.empty()) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        CacheEntry &e = g_cache[key];
+        if (e.oct.size() != n) e.oct = oct;
+        e.stamp = ++g_stamp;
+        size_t total = 0;
+        for (auto &kv : g_cache) total += kv.second.oct.size() * sizeof(double);
+        while (total > CACHE_MAX_BYTES && g_cache.size() > 1) {
+            auto oldest = g_cache.begin();
+            for (auto it = g_cache.begin(); it != g_cache.end(); ++it)
+                if (it->second.stamp < oldest->second.stamp) oldest = it;
+            total -= oldest->second.oct.size() * sizeof(double);
+            g_cache.erase(oldest);
+        }
+    }
+    if (hit)
+        p->precompute_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+void set_precompute_cache(bool memory, const char *dir) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache_on = memory;
+    if (!memory) g_cache.clear();
+    g_cache_dir = dir ? dir : "";
+}
+
 }  // namespace se
+
+using namespace se;
+
+extern "C" se_status_t se_set_precompute_cache(int memory, const char *dir) {
+    set_precompute_cache(memory != 0, dir);
+    return SE_OK;
+}
+
+extern "C" se_status_t se_plan_precompute_info(se_plan_t p, double *ms, int *cached) {
+    if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
+    if (ms) *ms = p->precompute_ms;
+    if (cached) *cached = p->precompute_cached ? 1 : 0;
+    return SE_OK;
+}

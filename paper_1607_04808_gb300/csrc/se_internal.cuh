@@ -222,6 +222,7 @@ struct se_plan_s {
     int n_stage = 0;
     int64_t launches = 0;  // kernels of this library launched by the last evaluation call
     double precompute_ms = 0;
+    bool precompute_cached = false;  // the precomputed kernel came from the cache
     // host staging for se_eval_host
     void *dx = nullptr, *df = nullptr, *dq = nullptr, *du = nullptr;
 };

@@ -83,6 +83,10 @@ def lib():
             L.se_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
             L.se_plan_launch_count.restype = i64
             L.se_plan_launch_count.argtypes = [vp]
+            L.se_set_precompute_cache.restype = i32
+            L.se_set_precompute_cache.argtypes = [i32, ctypes.c_char_p]
+            L.se_plan_precompute_info.restype = i32
+            L.se_plan_precompute_info.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
             L.se_plan_destroy.restype = i32
             L.se_batch_create.restype = i32
             L.se_batch_create.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
@@ -240,6 +244,12 @@ class Plan:
         n = lib().se_plan_stage_times(self._h, buf, 8)
         return {STAGES[i]: buf[i] for i in range(n)}
 
+    def precompute_info(self) -> tuple[float, bool]:
+        """(milliseconds, from the cache) of the plan's precomputation."""
+        ms, cached = ctypes.c_double(), ctypes.c_int()
+        _check(lib().se_plan_precompute_info(self._h, ctypes.byref(ms), ctypes.byref(cached)))
+        return ms.value, bool(cached.value)
+
     def launch_count(self) -> int:
         """se_plan_launch_count: kernels of this library launched by the last call."""
         return int(lib().se_plan_launch_count(self._h))
@@ -352,6 +362,12 @@ class SEFunction(torch.autograd.Function):
 def se_sum(x, f, plan: Plan, q=None):
     """Differentiable u = sum K(x_m - x_n) f_n (stresslet: T(x_m - x_n) f_n q_n)."""
     return SEFunction.apply(x, f, q, plan)
+
+
+def set_precompute_cache(memory: bool = True, directory: str | None = None):
+    """se_set_precompute_cache: share precomputed kernels between plans with equal grids."""
+    _check(lib().se_set_precompute_cache(1 if memory else 0,
+                                         None if directory is None else str(directory).encode()))
 
 
 def choose_params(kernel: str, N: int, L: float = 1.0, tol: float = 0.0, prec: str = "fp32",

@@ -459,3 +459,44 @@ def test_targets_at_the_sources(kernel):
     self_term = 4.0 * plan.params["xi"] / np.sqrt(np.pi) * f if kernel == "stokeslet" else 0.0 * f
     assert rel_l2(ut, u + self_term) <= 1e-12
     plan.close()
+
+
+# ------------------------------------------------------------------ precompute cache
+
+def test_precompute_cache_memory_and_disk(tmp_path):
+    """Plans with the same grid reuse the precomputed kernel (host cache, or a
+    file per grid in a directory) and give the same results."""
+    pkg = P()
+    N = 3000
+    x, f = W.stokeslet_uniform(N, 41)
+    t = lambda a: torch.tensor(a, device="cuda")  # noqa: E731
+    kw = dict(prec="fp64", xi=9.0, M=37, P=16, rc=0.3)
+    try:
+        pkg.set_precompute_cache(True, None)
+        a = pkg.Plan("stokeslet", N, BOX, **kw)
+        b = pkg.Plan("stokeslet", N, BOX, **kw)
+        ms_a, cached_a = a.precompute_info()
+        ms_b, cached_b = b.precompute_info()
+        assert cached_b and ms_b >= 0
+        # equal up to the summation order of the atomic accumulations
+        ua = a.eval(t(x), t(f), check=True).cpu().numpy()
+        ub = b.eval(t(x), t(f), check=True).cpu().numpy()
+        assert rel_l2(ub, ua) <= 1e-14
+        a.close()
+        b.close()
+        # disk only: the first plan computes and writes, the second reads the file
+        pkg.set_precompute_cache(False, str(tmp_path))
+        c = pkg.Plan("rotlet", N, BOX, prec="fp32", xi=9.0, M=41, P=12, rc=0.3)
+        assert not c.precompute_info()[1]
+        assert any(p.name.startswith("se_ghat_H_") for p in tmp_path.iterdir())
+        d = pkg.Plan("rotlet", N, BOX, prec="fp32", xi=9.0, M=41, P=12, rc=0.3)
+        assert d.precompute_info()[1]
+        xc, fc = torch.tensor(x, dtype=torch.float32, device="cuda"), torch.tensor(f, dtype=torch.float32,
+                                                                                   device="cuda")
+        uc = c.eval(xc, fc, check=True).double().cpu().numpy()
+        ud = d.eval(xc, fc, check=True).double().cpu().numpy()
+        assert rel_l2(ud, uc) <= 1e-6
+        c.close()
+        d.close()
+    finally:
+        pkg.set_precompute_cache(True, None)
