@@ -90,6 +90,16 @@ typedef struct {
 se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const double box[4], double tol,
                            se_prec_t prec, const se_params_t *params, se_plan_t *plan_out);
 
+/* As se_plan_create for a rectangular box: box = (x0, y0, z0, Lx, Ly, Lz).
+ * One grid spacing h in all dimensions (M of se_params_t counts the intervals
+ * along the longest side; the others take the smallest M covering their side
+ * with an FFT-friendly length), the truncation radius R is the diagonal of the
+ * extended box and the precompute grid is oversampled by 1 + R/Ltilde_d per
+ * dimension (Section 4.2).  Parameters are selected as for the cube of the
+ * longest side at the same point density. */
+se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double xi, const double box[6], double tol,
+                               se_prec_t prec, const se_params_t *params, se_plan_t *plan_out);
+
 /* u = sum_{n != m} K(x_m - x_n) . f_n at every point (Section 8).
  *   x  N x 3 device positions; f N x 3 device strengths (forces, dipoles or torques)
  *   q  N x 3 device second source vector for the stresslet (u_j = T_jlm f_l q_m), else NULL
@@ -219,6 +229,10 @@ se_status_t se_choose_params(se_kernel_t kernel, se_prec_t prec, int64_t N, doub
 
 /* Fill *out with the plan's parameters (chosen or given, plus derived values). */
 se_status_t se_plan_get_params(se_plan_t plan, se_params_t *out);
+
+/* Grid sizes per dimension (x, y, z): M (box), Mtilde (extended grid), the FFT
+ * size 2 Mtilde and the precompute grid; any pointer may be NULL. */
+se_status_t se_plan_get_grid(se_plan_t plan, int M[3], int Mtilde[3], int Mf[3], int Mg[3]);
 
 /* Synchronise the stream of the plan's last call and return (and clear) the
  * device-side status: SE_OK, SE_ERR_OUT_OF_BOX or SE_ERR_COINCIDENT. */

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <map>
 #include <string>
 #include <vector>
@@ -41,7 +42,7 @@ struct se_batch_s {
     int *cl_sys = nullptr;
     Buffers b;
     struct SizeClass {
-        int Mf = 0, count = 0;
+        int mf[3] = {0, 0, 0}, count = 0;
         void *grid = nullptr, *spec = nullptr, *wgrid = nullptr;
         cufftHandle fwd = 0, inv = 0;
         bool have_fwd = false, have_inv = false;
@@ -199,15 +200,18 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
         B->sub.push_back(p);
         if (!(pr[s].xi > 0) || !(pr[s].rc > 0) || pr[s].M < 1)
             return fail(SE_ERR_INVALID_ARG, "batch: invalid parameters for system " + std::to_string(s));
-        se_status_t st = setup_plan(p, kernel, prec, N_s[s], box_s + 4 * s, pr[s]);
+        const double *bx = box_s + 4 * s;
+        const double box6[6] = {bx[0], bx[1], bx[2], bx[3], bx[3], bx[3]};
+        se_status_t st = setup_plan(p, kernel, prec, N_s[s], box6, pr[s]);
         if (st != SE_OK) return st;
         if (!p->tiled || p->P > 16)
             return fail(SE_ERR_NOT_SUPPORTED, "batch: the support P must be <= 16 (tolerance too small)");
-        if (make_rc<double>(p).reach > 5)
+        const RC<double> rk = make_rc<double>(p);
+        if ((2 * rk.reach[0] + 1) * (2 * rk.reach[1] + 1) > 121)
             return fail(SE_ERR_NOT_SUPPORTED, "batch: real-space reach above 5 cells");
         if (s > 0 && p->geom.T != B->sub[0]->geom.T)
             return fail(SE_ERR_NOT_SUPPORTED, "batch: spreading tiles differ between systems");
-        const size_t O3 = (size_t)(p->Mt + 1) * (p->Mt + 1) * (p->Mt + 1);
+        const size_t O3 = (size_t)(p->mt[0] + 1) * (p->mt[1] + 1) * (p->mt[2] + 1);
         if (bmalloc(&p->ghat64, O3 * sizeof(double)) ||
             (prec == SE_FP32 && bmalloc((float **)&p->ghat, O3 * sizeof(float)))) {
             cudaGetLastError();
@@ -228,10 +232,10 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
         se_plan_s *p = B->sub[s];
         tile_base[s + 1] = tile_base[s] + p->ntiles;
         cell_base[s + 1] = cell_base[s] + p->ncells;
-        row_base[s + 1] = row_base[s] + p->geom.ncd * p->geom.ncd;
-        const size_t nk = (size_t)p->Mf * p->Mf * (p->Mf / 2 + 1);
+        row_base[s + 1] = row_base[s] + p->geom.ncel[1] * p->geom.ncel[2];
+        const size_t nk = (size_t)p->mf[2] * p->mf[1] * (p->mf[0] / 2 + 1);
         blk_base[s + 1] = blk_base[s] + (int)((nk + SCALE_BS - 1) / SCALE_BS);
-        const size_t zrows = (size_t)3 * R * p->Mt * p->Mt;
+        const size_t zrows = (size_t)3 * R * p->mt[1] * p->mt[2];
         zblk_base[s + 1] = zblk_base[s] + (int)((zrows + 7) / 8);
         for (int t = 0; t < p->ntiles; t++)
             for (int r = 0; r < R; r++) items.push_back(make_int4(s, t, r, 0));
@@ -242,19 +246,22 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
     B->nblk_scale = blk_base[S];
     B->nblk_zero = zblk_base[S];
     B->nitems = (int)items.size();
-    // FFT size classes: systems with equal Mf share one batched transform
-    std::map<int, std::vector<int>> by_mf;
-    for (int s = 0; s < S; s++) by_mf[B->sub[s]->Mf].push_back(s);
+    // FFT size classes: systems with equal FFT sizes share one batched transform
+    std::map<std::array<int, 3>, std::vector<int>> by_mf;
+    for (int s = 0; s < S; s++) {
+        const int *m = B->sub[s]->mf;
+        by_mf[{m[0], m[1], m[2]}].push_back(s);
+    }
     const size_t esz = (prec == SE_FP32) ? 4 : 8;
     std::vector<void *> grid(S), spec(S), wgrid(S);
     size_t work_max = 0;
     for (auto &kv : by_mf) {
         se_batch_s::SizeClass c;
-        c.Mf = kv.first;
+        for (int d = 0; d < 3; d++) c.mf[d] = kv.first[d];
         c.count = (int)kv.second.size();
         B->classes.push_back(c);
         se_batch_s::SizeClass &C = B->classes.back();
-        const size_t Mf3 = (size_t)C.Mf * C.Mf * C.Mf, nk = (size_t)C.Mf * C.Mf * (C.Mf / 2 + 1);
+        const size_t Mf3 = (size_t)C.mf[0] * C.mf[1] * C.mf[2], nk = (size_t)C.mf[2] * C.mf[1] * (C.mf[0] / 2 + 1);
         const size_t per = (size_t)3 * R;
         if (bmalloc(&C.grid, C.count * per * Mf3 * esz) || bmalloc(&C.spec, C.count * per * nk * 2 * esz) ||
             bmalloc(&C.wgrid, C.count * per * Mf3 * esz) || cudaMemset(C.grid, 0, C.count * per * Mf3 * esz)) {
@@ -267,7 +274,7 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
             spec[s] = (char *)C.spec + j * per * nk * 2 * esz;
             wgrid[s] = (char *)C.wgrid + j * per * Mf3 * esz;
         }
-        long long n[3] = {C.Mf, C.Mf, C.Mf};
+        long long n[3] = {C.mf[2], C.mf[1], C.mf[0]};
         const long long batch = (long long)C.count * per;
         size_t ws = 0;
         BCF(cufftCreate(&C.fwd));

@@ -8,6 +8,30 @@ namespace se {
 
 namespace {
 
+// Window starts and real-space cell of a point; true when it lies outside the
+// half-open box (it is then clamped inside so that all indexing stays in
+// bounds; NaN fails both tests).
+template <typename T>
+__device__ __forceinline__ bool place_point(const GP<T> &g, const T *xp, int i0[3], int cc[3]) {
+    bool oob = false;
+    for (int d = 0; d < 3; d++) {
+        T rel = xp[d] - g.x0[d];
+        if (!(rel >= T(0) && rel < g.len[d])) oob = true;
+        rel = clamp_rel(rel, g.len[d]);
+        i0[d] = window_start(rel, g, d);
+        cc[d] = min(max((int)(rel * g.icw[d]), 0), g.ncel[d] - 1);
+    }
+    return oob;
+}
+
+// Spreading tile of a window start (tiles of T_^3 window starts, x fastest)
+template <typename T>
+__device__ __forceinline__ int tile_key(const GP<T> &g, const int i0[3]) {
+    const int t0 = min(i0[0] / g.T_, g.nt[0] - 1), t1 = min(i0[1] / g.T_, g.nt[1] - 1),
+              t2 = min(i0[2] / g.T_, g.nt[2] - 1);
+    return (t2 * g.nt[1] + t1) * g.nt[0] + t0;
+}
+
 template <typename T>
 __global__ void k_bin_count(int N, const T *__restrict__ x, GP<T> g, int *__restrict__ cnt_t,
                             int *__restrict__ slot_t, int *__restrict__ key_t, int *__restrict__ cnt_r,
@@ -16,20 +40,9 @@ __global__ void k_bin_count(int N, const T *__restrict__ x, GP<T> g, int *__rest
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int i0[3], cc[3];
-    bool oob = false;
-    for (int d = 0; d < 3; d++) {
-        T rel = x[3 * i + d] - g.x0[d];
-        // half-open box [x0, x0 + L); NaN fails both tests
-        if (!(rel >= T(0) && rel < g.L)) oob = true;
-        rel = clamp_rel(rel, g.L);
-        i0[d] = window_start(rel, g);
-        cc[d] = (d == 0) ? min(max((int)(rel * g.inv_cwx), 0), g.ncdx - 1)
-                         : min(max((int)(rel * g.inv_cw), 0), g.ncd - 1);
-    }
-    if (oob) atomicOr(status, FLAG_OOB);
-    int kt = (min(i0[2] / g.T_, g.ntd - 1) * g.ntd + min(i0[1] / g.T_, g.ntd - 1)) * g.ntd +
-             min(i0[0] / g.T_, g.ntd - 1);
-    int kr = (cc[2] * g.ncd + cc[1]) * g.ncdx + cc[0];
+    if (place_point(g, x + 3 * (size_t)i, i0, cc)) atomicOr(status, FLAG_OOB);
+    int kt = tile_key(g, i0);
+    int kr = (cc[2] * g.ncel[1] + cc[1]) * g.ncel[0] + cc[0];
     key_t[i] = kt;
     key_r[i] = kr;
     tag_t[i] = pack3(i0[0], i0[1], i0[2]);
@@ -105,19 +118,9 @@ __global__ void k_bbin_count(int Ntot, const BSys<T> *__restrict__ sys, const in
     const BSys<T> &B = sys[find_range(off, S, i)];
     const GP<T> g = B.g;
     int i0[3], cc[3];
-    bool oob = false;
-    for (int d = 0; d < 3; d++) {
-        T rel = x[3 * (size_t)i + d] - g.x0[d];
-        if (!(rel >= T(0) && rel < g.L)) oob = true;
-        rel = clamp_rel(rel, g.L);
-        i0[d] = window_start(rel, g);
-        cc[d] = (d == 0) ? min(max((int)(rel * g.inv_cwx), 0), g.ncdx - 1)
-                         : min(max((int)(rel * g.inv_cw), 0), g.ncd - 1);
-    }
-    if (oob) atomicOr(status, FLAG_OOB);
-    int kt = B.tile_base + (min(i0[2] / g.T_, g.ntd - 1) * g.ntd + min(i0[1] / g.T_, g.ntd - 1)) * g.ntd +
-             min(i0[0] / g.T_, g.ntd - 1);
-    int kr = B.cell_base + (cc[2] * g.ncd + cc[1]) * g.ncdx + cc[0];
+    if (place_point(g, x + 3 * (size_t)i, i0, cc)) atomicOr(status, FLAG_OOB);
+    int kt = B.tile_base + tile_key(g, i0);
+    int kr = B.cell_base + (cc[2] * g.ncel[1] + cc[1]) * g.ncel[0] + cc[0];
     key_t[i] = kt;
     key_r[i] = kr;
     tag_t[i] = pack3(i0[0], i0[1], i0[2]);

@@ -149,7 +149,7 @@ __device__ __forceinline__ void spread_col_body(const GP<float> &g, int tile, in
     static_assert(TE == 8, "the unrolled z offsets cover tiles of 8");
     __shared__ __align__(16) ColStage<P, TE> S;
     const int tid = threadIdx.x;
-    const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
     const bool own = tid < PT * PT;
     const int cx = tid % PT, cy = tid / PT;
@@ -195,12 +195,12 @@ __device__ __forceinline__ void spread_col_body(const GP<float> &g, int tile, in
     }
     if (own) {
         const int gx = gx0 + cx, gy = gy0 + cy;
-        if (gx < g.Mt && gy < g.Mt) {
-            const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
-            float *base = grid + (size_t)c0 * Mf3 + ((size_t)gz0 * Mf + gy) * Mf + gx;
+        if (gx < g.mt[0] && gy < g.mt[1]) {
+            const size_t Mf = g.mf[0], Mf2 = Mf * g.mf[1], Mf3 = vol(g);
+            float *base = grid + (size_t)c0 * Mf3 + ((size_t)gz0 * g.mf[1] + gy) * Mf + gx;
 #pragma unroll
             for (int z = 0; z < PT; z++) {
-                if (gz0 + z < g.Mt) {
+                if (gz0 + z < g.mt[2]) {
                     float *pz = base + (size_t)z * Mf2;
                     if (a0[z] != 0.0f) atomicAdd(pz, a0[z]);
                     if (a1[z] != 0.0f) atomicAdd(pz + Mf3, a1[z]);
@@ -223,7 +223,7 @@ __device__ __forceinline__ void gather_col_body(const GP<float> &g, int tile, in
     static_assert(TE == 8, "the unrolled z offsets cover tiles of 8");
     __shared__ __align__(16) ColStage<P, TE> S;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
     const bool own = tid < PT * PT;
     const int cx = tid % PT, cy = tid / PT;
@@ -231,12 +231,12 @@ __device__ __forceinline__ void gather_col_body(const GP<float> &g, int tile, in
     float w0[PT], w1[PT], w2[PT];
     {
         const int gx = gx0 + cx, gy = gy0 + cy;
-        const bool in = own && gx < g.Mt && gy < g.Mt;
-        const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
-        const float *base = w + ((size_t)gz0 * Mf + gy) * Mf + gx;
+        const bool in = own && gx < g.mt[0] && gy < g.mt[1];
+        const size_t Mf = g.mf[0], Mf2 = Mf * g.mf[1], Mf3 = vol(g);
+        const float *base = w + ((size_t)gz0 * g.mf[1] + gy) * Mf + gx;
 #pragma unroll
         for (int z = 0; z < PT; z++) {
-            const bool ok = in && (gz0 + z < g.Mt);
+            const bool ok = in && (gz0 + z < g.mt[2]);
             const float *pz = base + (size_t)z * Mf2;
             w0[z] = ok ? __ldg(pz) : 0.0f;
             w1[z] = ok ? __ldg(pz + Mf3) : 0.0f;
@@ -341,17 +341,17 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
     extern __shared__ __align__(16) float sg[];  // [c][z][y][x], x pitch PX
     __shared__ float swt[GS_WARPS][3][P];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
-    const size_t Mf = g.Mf, Mf3 = Mf * Mf * Mf;
+    const size_t Mf = g.mf[0], Mf3 = vol(g);
     // flat copy of the block (x fastest), several independent loads in flight per thread
 #pragma unroll 8
     for (int e = threadIdx.x; e < ROWS * PT; e += GS_WARPS * 32) {
         const int row = e / PT, x = e - row * PT, c = row / (PT * PT), zy = row - c * PT * PT, z = zy / PT,
                   y = zy - z * PT;
         const int gz = gz0 + z, gy = gy0 + y, gx = gx0 + x;
-        sg[row * PX + x] = (gz < g.Mt && gy < g.Mt && gx < g.Mt)
-                               ? __ldg(w + (size_t)c * Mf3 + ((size_t)gz * Mf + gy) * Mf + gx)
+        sg[row * PX + x] = (gz < g.mt[2] && gy < g.mt[1] && gx < g.mt[0])
+                               ? __ldg(w + (size_t)c * Mf3 + ((size_t)gz * g.mf[1] + gy) * Mf + gx)
                                : 0.0f;
     }
     __syncthreads();
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_bgather_smem(const BSys<float
     const int beg = tile_start[key], end = tile_start[key + 1];
     if (beg == end) return;
     const GP<float> g = B.g;
-    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    const size_t Mf3 = vol(g);
     gather_smem_body<P, TE>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * Mf3, n_rhs, it.z, f_orig,
                             B.self_coef, u);
 }
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_bspread_col(const BSys<fl
     const int beg = tile_start[key], end = tile_start[key + 1];
     if (beg == end) return;
     const GP<float> g = B.g;
-    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    const size_t Mf3 = vol(g);
     spread_col_body<P, TE>(g, it.y, beg, end, 0, false, xs, fs, n_rhs, it.z, nullptr,
                            B.grid + (size_t)it.z * 3 * Mf3);
 }
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_bgather_col(const BSys<fl
     const int beg = tile_start[key], end = tile_start[key + 1];
     if (beg == end) return;
     const GP<float> g = B.g;
-    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    const size_t Mf3 = vol(g);
     gather_col_body<P, TE>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * Mf3, n_rhs, it.z, f_orig,
                            B.self_coef, u);
 }

@@ -104,7 +104,7 @@ se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *q, const T
                        cudaStream_t st) {
     p->last_stream = st;
     p->launches = 0;
-    const size_t Mf3 = (size_t)p->Mf * p->Mf * p->Mf;
+    const size_t Mf3 = (size_t)p->mf[0] * p->mf[1] * p->mf[2];
     const bool stress = (p->kernel == SE_STRESSLET);
     if (!p->wgrid2) {
         cudaError_t e = cudaMalloc(&p->wgrid2, (stress ? 6 : 3) * Mf3 * sizeof(T));
@@ -119,7 +119,7 @@ se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *q, const T
     CK(launch_bin<T>(p, x, gu, nullptr, st));
     se_status_t s;
     if (stress) {
-        const size_t nk = (size_t)p->Mf * p->Mf * (p->Mf / 2 + 1);
+        const size_t nk = (size_t)p->mf[2] * p->mf[1] * (p->mf[0] / 2 + 1);
         CK(launch_spread<T>(p, st, p->b.xs_t, p->b.fs_t, nullptr, p->grid, 3));
         CF(cufftSetStream(p->fwd3, st));
         CF(exec_fwd<T>(p->fwd3, p->grid, p->spec));
@@ -192,7 +192,7 @@ static se_status_t ensure_targets(se_plan_s *p, int64_t Nt) {
     b = Buffers();
     p->nt_cap = 0;
     const size_t n = (size_t)Nt, v4 = (p->prec == SE_FP32 ? 16 : 32);
-    const size_t nrows = (size_t)p->geom.ncd * p->geom.ncd;
+    const size_t nrows = (size_t)p->geom.ncel[1] * p->geom.ncel[2];
     auto scan_len = [](size_t k) { return k + 2 + (k + 4095) / 4096 + 1; };
     cudaError_t e;
     if ((e = cudaMalloc(&b.xs_t, n * v4)) || (e = cudaMalloc(&b.perm_t, n * 4)) || (e = cudaMalloc(&b.slot_t, n * 4)) ||

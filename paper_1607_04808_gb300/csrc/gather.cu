@@ -41,7 +41,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 // One target (sorted position n, original index m): lanes cover the (x, y)
 // columns of the support (NIT static slots, P <= 16, or a strided loop) and
 // loop over z; the weights are computed once and applied to the n_rhs groups
-// of three grids (group r at w + 3 r Mf^3).  u and f_orig hold n_rhs
+// of three grids (group r at w + 3 r mf_x mf_y mf_z).  u and f_orig hold n_rhs
 // three-vectors per point.
 template <typename T, int NIT>
 __device__ __forceinline__ void gather_point(const GP<T> &g, const vec4<T> &xv, int m, const T *__restrict__ w,
@@ -51,9 +51,9 @@ __device__ __forceinline__ void gather_point(const GP<T> &g, const vec4<T> &xv, 
     int i0[3];
     T fr[3];
     warp_weights<T>(xv, g, lane, i0, sw, fr);
-    const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+    const size_t Mf = g.mf[0], Mfy = g.mf[1], Mf2 = Mf * Mfy, Mf3 = vol(g);
     for (int r = 0; r < n_rhs; r++) {
-        const T *base = w + (size_t)r * 3 * Mf3 + ((size_t)i0[2] * Mf + i0[1]) * Mf + i0[0];
+        const T *base = w + (size_t)r * 3 * Mf3 + ((size_t)i0[2] * Mfy + i0[1]) * Mf + i0[0];
         T acc0 = 0, acc1 = 0, acc2 = 0;
         auto column = [&](int kx, int ky) {
             const T wxy = sw[0][kx] * sw[1][ky];
@@ -146,8 +146,8 @@ __global__ void __launch_bounds__(WPB * 32) k_gather_adjT(GP<T> g, int N, const 
     int i0[3];
     T fr[3];
     warp_weights<T>(xs[n], g, lane, i0, sw, fr);
-    const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
-    const T *base = V + ((size_t)i0[2] * Mf + i0[1]) * Mf + i0[0];
+    const size_t Mf = g.mf[0], Mfy = g.mf[1], Mf2 = Mf * Mfy, Mf3 = vol(g);
+    const T *base = V + ((size_t)i0[2] * Mfy + i0[1]) * Mf + i0[0];
     T acc[6] = {0, 0, 0, 0, 0, 0};
     for (int idx = lane; idx < P2; idx += 32) {
         const int ky = idx / P, kx = idx - ky * P;
@@ -211,13 +211,13 @@ __global__ void __launch_bounds__(WPB * 32) k_gather_grad(GP<T> g, T c_grad, int
         for (int c = 0; c < NA; c++)
             cm[c] = (c < 3) ? fm[c] * qm[c] : fm[L_[c]] * qm[K_[c]] + fm[K_[c]] * qm[L_[c]];
     }
-    const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+    const size_t Mf = g.mf[0], Mfy = g.mf[1], Mf2 = Mf * Mfy, Mf3 = vol(g);
     T acc[3] = {0, 0, 0};
     for (int idx = lane; idx < P2; idx += 32) {
         int ky = idx / P, kx = idx - ky * P;
         T wx = sw[0][kx], wy = sw[1][ky];
         T dx = fr[0] - (T)kx, dy = fr[1] - (T)ky;
-        const size_t off = ((size_t)i0[2] * Mf + (i0[1] + ky)) * Mf + (i0[0] + kx);
+        const size_t off = ((size_t)i0[2] * Mfy + (i0[1] + ky)) * Mf + (i0[0] + kx);
         T s0 = 0, sz = 0;  // sum_kz s wz, sum_kz s wz dz
         for (int kz = 0; kz < P; kz++) {
             T wz = sw[2][kz];

@@ -93,12 +93,14 @@ extern "C" se_status_t se_real_space_noalloc(se_kernel_t kernel, se_prec_t prec,
     p.prec = prec;
     p.N = N;
     for (int d = 0; d < 3; d++) p.x0[d] = box[d];
-    p.L = box[3];
+    for (int d = 0; d < 3; d++) p.len[d] = box[3];
     p.xi = xi;
     p.rc = rc;
     p.P = 2;
-    p.Mt = 2;
-    p.Mf = 4;
+    for (int d = 0; d < 3; d++) {
+        p.mt[d] = 2;
+        p.mf[d] = 4;
+    }
     const double L = box[3];
     int ncd = std::max(1, std::min((int)floor(5.0 * L / rc), 200));
     int ncdx = std::max(1, std::min((int)floor(16.0 * L / rc), 1000));
@@ -107,44 +109,43 @@ extern "C" se_status_t se_real_space_noalloc(se_kernel_t kernel, se_prec_t prec,
     while ((int64_t)ncd * ncd * ncdx > NOALLOC_MAX_CELLS && ncdx > 1) ncdx--;
     if ((int64_t)ncd * ncd * ncdx > NOALLOC_MAX_CELLS)
         return fail(SE_ERR_INVALID_ARG, "se_real_space_noalloc: cell list exceeds the fixed size");
+    const int ncel[3] = {ncdx, ncd, ncd};
     Geom &g = p.geom;
-    for (int d = 0; d < 3; d++) g.x0[d] = box[d];
-    g.L = L;
+    for (int d = 0; d < 3; d++) {
+        g.x0[d] = box[d];
+        g.len[d] = L;
+        g.mt[d] = 2;
+        g.mf[d] = 4;
+        g.nt[d] = 1;
+        g.ncel[d] = ncel[d];
+        g.cw[d] = L / ncel[d];
+        g.icw[d] = ncel[d] / L;
+    }
     g.h = L;
     g.inv_h = 1.0 / L;
     g.P = 2;
-    g.Mt = 2;
-    g.Mf = 4;
     g.T = 8;
-    g.ntd = 1;
-    g.ncd = ncd;
-    g.cw = L / ncd;
-    g.inv_cw = ncd / L;
-    g.ncdx = ncdx;
-    g.cwx = L / ncdx;
-    g.inv_cwx = ncdx / L;
     g.rc = rc;
     g.xi = xi;
     p.ntiles = 1;
     p.ncells = ncd * ncd * ncdx;
     auto fill = [&](auto &G) {
-        using TT = std::remove_reference_t<decltype(G.L)>;
-        for (int d = 0; d < 3; d++) G.x0[d] = (TT)box[d];
-        G.L = (TT)L;
+        using TT = std::remove_reference_t<decltype(G.inv_h)>;
+        for (int d = 0; d < 3; d++) {
+            G.x0[d] = (TT)box[d];
+            G.len[d] = (TT)L;
+            G.icw[d] = (TT)g.icw[d];
+            G.cw[d] = (TT)g.cw[d];
+            G.mt[d] = 2;
+            G.mf[d] = 4;
+            G.nt[d] = 1;
+            G.ncel[d] = ncel[d];
+        }
         G.inv_h = (TT)(1.0 / L);
         G.half_ext = (TT)0;
         G.ah2 = (TT)0;
-        G.inv_cw = (TT)g.inv_cw;
-        G.cw = (TT)g.cw;
-        G.inv_cwx = (TT)g.inv_cwx;
-        G.cwx = (TT)g.cwx;
         G.P = 2;
-        G.Mt = 2;
-        G.Mf = 4;
         G.T_ = 8;
-        G.ntd = 1;
-        G.ncd = ncd;
-        G.ncdx = ncdx;
     };
     fill(p.gpf);
     fill(p.gpd);

@@ -206,21 +206,25 @@ static cudaError_t dmalloc(P_ **ptr, size_t bytes) {
 }
 
 // Parameters, grid sizes and geometry of a plan (no device work).
-se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[4],
+se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[6],
                            const se_params_t &pr) {
     p->kernel = kernel;
     p->prec = prec;
     p->N = N;
-    for (int d = 0; d < 3; d++) p->x0[d] = box[d];
-    p->L = box[3];
+    double lmax = 0;
+    for (int d = 0; d < 3; d++) {
+        p->x0[d] = box[d];
+        p->len[d] = box[3 + d];
+        lmax = std::max(lmax, p->len[d]);
+    }
     p->xi = pr.xi;
     p->rc = pr.rc;
-    p->M = pr.M;
     p->P = pr.P;
     p->deltaL_policy = pr.deltaL_policy;
     p->max_fft = pr.max_fft;
-    // Sections 5.2-5.3: h = L/M, d = hP, m = C sqrt(pi P), eta = (xi d / m)^2
-    p->h = p->L / p->M;
+    // Sections 5.2-5.3: h = L/M (M points along the longest side), d = hP,
+    // m = C sqrt(pi P), eta = (xi d / m)^2
+    p->h = lmax / pr.M;
     double d = p->h * p->P;
     p->m = 0.976 * sqrt(M_PI * p->P);
     p->eta = (p->xi * d / p->m) * (p->xi * d / p->m);
@@ -229,27 +233,50 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
         need = std::max(d, sqrt(2.0 * (1.0 - p->eta) * p->m * p->m / (p->xi * p->xi)));
     p->n_ext = (int)ceil(need / p->h - 1e-9);
     p->deltaL = p->n_ext * p->h;
-    p->Mt = p->M + p->n_ext;
-    p->Mf = 2 * p->Mt;
-    p->R = sqrt(3.0) * p->Mt * p->h;
-    // precompute grid: the smallest even size above (1 + sqrt 3) Mt (Section 9),
-    // rounded up to a length with prime factors 2, 3, 5, 7 (a larger
-    // oversampling factor is still valid, Section 4.2, and avoids cuFFT's slow
-    // path for lengths with large prime factors)
-    p->Mg = 2 * (int)floor((1.0 + sqrt(3.0)) * p->Mt / 2.0) + 2;
-    while (!good_fft(p->Mg, SE_FP64) || (p->Mg & 1)) p->Mg++;
+    double r2 = 0;
+    for (int dd = 0; dd < 3; dd++) {
+        // the shorter sides: the smallest M covering the side whose FFT length
+        // 2 (M + n_ext) has prime factors 2, 3, 5, 7 (the grid may extend past
+        // the box; the points only need to lie inside it)
+        int M = (p->len[dd] == lmax) ? pr.M : (int)ceil(p->len[dd] / p->h - 1e-9);
+        if (p->len[dd] != lmax)
+            while (!good_fft(2 * (M + p->n_ext), prec)) M++;
+        p->mm[dd] = M;
+        p->mt[dd] = M + p->n_ext;
+        p->mf[dd] = 2 * p->mt[dd];
+        r2 += (p->mt[dd] * p->h) * (p->mt[dd] * p->h);
+    }
+    // truncation radius: the diagonal of the extended box (Section 4.1;
+    // sqrt(3) Ltilde for a cube)
+    p->R = sqrt(r2);
+    // precompute grid per dimension: the smallest even size above
+    // (1 + R / Ltilde_d) mt_d, the oversampling of Section 4.2 ((1 + sqrt 3) mt
+    // for a cube, Section 9), rounded up to a length with prime factors 2, 3, 5,
+    // 7 (a larger oversampling factor is still valid and avoids cuFFT's slow path)
+    for (int dd = 0; dd < 3; dd++) {
+        const double sf = 1.0 + p->R / (p->mt[dd] * p->h);
+        int Mg = 2 * (int)floor(sf * p->mt[dd] / 2.0) + 2;
+        while (!good_fft(Mg, SE_FP64) || (Mg & 1)) Mg++;
+        p->mg[dd] = Mg;
+    }
     p->nc = (kernel == SE_STRESSLET) ? 6 : 3;
-    if (p->max_fft > 0 && p->Mf > p->max_fft) return fail(SE_ERR_INVALID_ARG, "FFT size 2*Mtilde exceeds max_fft");
+    for (int dd = 0; dd < 3; dd++) {
+        if (p->max_fft > 0 && p->mf[dd] > p->max_fft)
+            return fail(SE_ERR_INVALID_ARG, "FFT size 2*Mtilde exceeds max_fft");
+        if (p->mt[dd] > 1023) return fail(SE_ERR_INVALID_ARG, "extended grid above 1023 points per dimension");
+    }
     // geometry
     Geom &g = p->geom;
-    for (int dd = 0; dd < 3; dd++) g.x0[dd] = p->x0[dd];
-    g.L = p->L;
+    for (int dd = 0; dd < 3; dd++) {
+        g.x0[dd] = p->x0[dd];
+        g.len[dd] = p->len[dd];
+        g.mt[dd] = p->mt[dd];
+        g.mf[dd] = p->mf[dd];
+    }
     g.h = p->h;
     g.inv_h = 1.0 / p->h;
     g.half_ext = 0.5 * p->n_ext;
     g.P = p->P;
-    g.Mt = p->Mt;
-    g.Mf = p->Mf;
     g.a = 2.0 * p->xi * p->xi / p->eta;
     g.xi = p->xi;
     g.rc = p->rc;
@@ -273,8 +300,11 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
         p->tiled = true;
         g.T = COL_TE;
     }
-    g.ntd = (p->Mt - p->P + 1 + g.T - 1) / g.T;
-    p->ntiles = g.ntd * g.ntd * g.ntd;
+    p->ntiles = 1;
+    for (int dd = 0; dd < 3; dd++) {
+        g.nt[dd] = (p->mt[dd] - p->P + 1 + g.T - 1) / g.T;
+        p->ntiles *= g.nt[dd];
+    }
     // real-space cells: width >= rc/5 (FP32) or rc/3 (FP64) across rows (y, z;
     // at most 200) and >= rc/16 along the rows (x; at most 1000), so that
     // trimming each row to the cutoff sphere wastes little
@@ -284,60 +314,73 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
 #ifndef SE_RS_XDIV
 #define SE_RS_XDIV 16.0
 #endif
-    // FP32 (clustered evaluation): rc/5 across rows; FP64 (per-target rows): rc/3
 #ifndef SE_RS_YZDIV64
 #define SE_RS_YZDIV64 3.0
 #endif
     const double yzdiv = (prec == SE_FP32) ? SE_RS_YZDIV32 : SE_RS_YZDIV64;
-    int ncd = (int)floor(yzdiv * p->L / p->rc);
-    ncd = std::max(1, std::min(ncd, 200));
-    int ncdx = (int)floor(SE_RS_XDIV * p->L / p->rc);
-    ncdx = std::max(1, std::min(ncdx, 1000));
-    if ((long)ncd * ncd * ncdx > (1L << 26)) ncdx = std::max(1L, (1L << 26) / ((long)ncd * ncd));
-    g.ncd = ncd;
-    g.cw = p->L / ncd;
-    g.inv_cw = ncd / p->L;
-    g.ncdx = ncdx;
-    g.cwx = p->L / ncdx;
-    g.inv_cwx = ncdx / p->L;
-    p->ncells = ncd * ncd * ncdx;
-    if (p->Mt > 1023) return fail(SE_ERR_INVALID_ARG, "extended grid above 1023 points per dimension");
+    for (int dd = 1; dd < 3; dd++) g.ncel[dd] = std::max(1, std::min((int)floor(yzdiv * p->len[dd] / p->rc), 200));
+    g.ncel[0] = std::max(1, std::min((int)floor(SE_RS_XDIV * p->len[0] / p->rc), 1000));
+    const long rows = (long)g.ncel[1] * g.ncel[2];
+    if (rows * g.ncel[0] > (1L << 26)) g.ncel[0] = (int)std::max(1L, (1L << 26) / rows);
+    for (int dd = 0; dd < 3; dd++) {
+        g.cw[dd] = p->len[dd] / g.ncel[dd];
+        g.icw[dd] = g.ncel[dd] / p->len[dd];
+    }
+    p->ncells = g.ncel[0] * g.ncel[1] * g.ncel[2];
     // the same geometry in each arithmetic precision
     auto fill = [&](auto &G) {
-        using TT = std::remove_reference_t<decltype(G.L)>;
-        for (int dd = 0; dd < 3; dd++) G.x0[dd] = (TT)p->x0[dd];
-        G.L = (TT)p->L;
+        using TT = std::remove_reference_t<decltype(G.inv_h)>;
+        for (int dd = 0; dd < 3; dd++) {
+            G.x0[dd] = (TT)p->x0[dd];
+            G.len[dd] = (TT)p->len[dd];
+            G.icw[dd] = (TT)g.icw[dd];
+            G.cw[dd] = (TT)g.cw[dd];
+            G.mt[dd] = g.mt[dd];
+            G.mf[dd] = g.mf[dd];
+            G.nt[dd] = g.nt[dd];
+            G.ncel[dd] = g.ncel[dd];
+        }
         G.inv_h = (TT)(1.0 / p->h);
         G.half_ext = (TT)(0.5 * p->n_ext);
         G.ah2 = (TT)(g.a * p->h * p->h);
-        G.inv_cw = (TT)g.inv_cw;
-        G.cw = (TT)g.cw;
-        G.inv_cwx = (TT)g.inv_cwx;
-        G.cwx = (TT)g.cwx;
-        G.ncdx = g.ncdx;
         G.P = p->P;
-        G.Mt = p->Mt;
-        G.Mf = p->Mf;
         G.T_ = g.T;
-        G.ntd = g.ntd;
-        G.ncd = g.ncd;
     };
     fill(p->gpf);
     fill(p->gpd);
-
     return SE_OK;
+}
+
+// Parameters for a box with sides (Lx, Ly, Lz): the selection for the cube of
+// the longest side at the same point density (the error estimates depend on
+// the density, xi and h), so M counts grid intervals along the longest side.
+se_status_t se::choose_box_params(int kernel, int prec, int64_t N, const double box[6], double tol,
+                                  const se_params_t *params, double xi, se_params_t *out, int n_rhs) {
+    const double lmax = std::max(box[3], std::max(box[4], box[5]));
+    const double vol = box[3] * box[4] * box[5];
+    const double neff = std::max(1.0, (double)N * lmax * lmax * lmax / vol);
+    return choose_params(kernel, prec, (int64_t)llround(neff), lmax, tol, params, xi, out, n_rhs);
 }
 
 extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const double box[4], double tol,
                                       se_prec_t prec, const se_params_t *params, se_plan_t *plan_out) {
+    if (!box) return fail(SE_ERR_INVALID_ARG, "box is NULL");
+    const double b6[6] = {box[0], box[1], box[2], box[3], box[3], box[3]};
+    return se_plan_create_box(kernel, N, xi, b6, tol, prec, params, plan_out);
+}
+
+extern "C" se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double xi, const double box[6],
+                                          double tol, se_prec_t prec, const se_params_t *params,
+                                          se_plan_t *plan_out) {
     if (!plan_out) return fail(SE_ERR_INVALID_ARG, "plan_out is NULL");
     *plan_out = nullptr;
     if (kernel < SE_STOKESLET || kernel > SE_ROTLET) return fail(SE_ERR_INVALID_ARG, "unknown kernel");
     if (prec != SE_FP32 && prec != SE_FP64) return fail(SE_ERR_INVALID_ARG, "unknown precision");
     if (N < 1 || N > (int64_t)INT32_MAX / 4) return fail(SE_ERR_INVALID_ARG, "N out of range");
-    if (!box || !(box[3] > 0)) return fail(SE_ERR_INVALID_ARG, "box side L must be positive");
+    if (!box || !(box[3] > 0) || !(box[4] > 0) || !(box[5] > 0))
+        return fail(SE_ERR_INVALID_ARG, "box sides must be positive");
     se_params_t pr;
-    se_status_t s = choose_params(kernel, prec, N, box[3], tol, params, xi, &pr);
+    se_status_t s = choose_box_params(kernel, prec, N, box, tol, params, xi, &pr);
     if (s != SE_OK) return s;
     if (pr.P < 1 || pr.P > 32) return fail(SE_ERR_INVALID_ARG, "P must be in [1, 32]");
     if (pr.M < 1 || !(pr.xi > 0) || !(pr.rc > 0)) return fail(SE_ERR_INVALID_ARG, "invalid M, xi or rc");
@@ -352,9 +395,9 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     // allocations
     cudaError_t e = cudaSuccess;
     const size_t Nn = (size_t)N;
-    const size_t Mf3 = (size_t)p->Mf * p->Mf * p->Mf;
-    const size_t nk = (size_t)p->Mf * p->Mf * (p->Mf / 2 + 1);
-    const size_t O3 = (size_t)(p->Mt + 1) * (p->Mt + 1) * (p->Mt + 1);
+    const size_t Mf3 = (size_t)p->mf[0] * p->mf[1] * p->mf[2];
+    const size_t nk = (size_t)p->mf[2] * p->mf[1] * (p->mf[0] / 2 + 1);
+    const size_t O3 = (size_t)(p->mt[0] + 1) * (p->mt[1] + 1) * (p->mt[2] + 1);
     const size_t v4 = 4 * esz;
     int tile_keys = p->ntiles;
     do {
@@ -381,7 +424,7 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
         if ((e = dmalloc(&p->b.tag_t, Nn * 4))) break;
         if ((e = dmalloc(&p->b.tag_r, Nn * 4))) break;
         {
-            const size_t nrows = (size_t)p->geom.ncd * p->geom.ncd;
+            const size_t nrows = (size_t)p->geom.ncel[1] * p->geom.ncel[2];
             if ((e = dmalloc(&p->b.ncl, scan_len(nrows) * 4))) break;
             if ((e = dmalloc(&p->b.clusters, (Nn / 4 + nrows + 1) * sizeof(int2)))) break;
         }
@@ -399,7 +442,7 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     }
     // cuFFT plans: forward R2C batched over nc components, inverse C2R over 3
     {
-        int n[3] = {p->Mf, p->Mf, p->Mf};
+        int n[3] = {p->mf[2], p->mf[1], p->mf[0]};
         cufftType tf = (prec == SE_FP32) ? CUFFT_R2C : CUFFT_D2Z;
         cufftType ti = (prec == SE_FP32) ? CUFFT_C2R : CUFFT_Z2D;
         int idist = (int)Mf3, odist = (int)nk;
@@ -452,14 +495,26 @@ extern "C" se_status_t se_plan_get_params(se_plan_t p, se_params_t *out) {
     memset(out, 0, sizeof(*out));
     out->xi = p->xi;
     out->rc = p->rc;
-    out->M = p->M;
+    // the longest dimension's sizes (all equal for a cube; se_plan_get_grid has each)
+    out->M = std::max(p->mm[0], std::max(p->mm[1], p->mm[2]));
     out->P = p->P;
     out->deltaL_policy = p->deltaL_policy;
     out->max_fft = p->max_fft;
-    out->Mtilde = p->Mt;
-    out->Mg = p->Mg;
+    out->Mtilde = std::max(p->mt[0], std::max(p->mt[1], p->mt[2]));
+    out->Mg = std::max(p->mg[0], std::max(p->mg[1], p->mg[2]));
     out->eta = p->eta;
     out->h = p->h;
+    return SE_OK;
+}
+
+extern "C" se_status_t se_plan_get_grid(se_plan_t p, int M[3], int Mtilde[3], int Mf[3], int Mg[3]) {
+    if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
+    for (int d = 0; d < 3; d++) {
+        if (M) M[d] = p->mm[d];
+        if (Mtilde) Mtilde[d] = p->mt[d];
+        if (Mf) Mf[d] = p->mf[d];
+        if (Mg) Mg[d] = p->mg[d];
+    }
     return SE_OK;
 }
 

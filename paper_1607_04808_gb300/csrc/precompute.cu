@@ -1,12 +1,13 @@
 // Precomputation of the mollified truncated Green's function (Section 4.3), FP64:
 //  1. B^R(k) (eq. BhatR; stokeslet, stresslet) or H^R(k) (eq. HhatR; rotlet) on
-//     the oversampled Mg^3 grid, k = 2 pi kbar / (Mg h), R = sqrt(3) Ltilde;
-//     only the half spectrum kx in [0, Mg/2] is formed (the data are real and even);
-//  2. inverse FFT (complex-to-real), normalised by 1/Mg^3;
-//  3. keep the 2 Mt values per dimension centred at zero (j in [-Mt, Mt-1]),
-//     stored wrap-ordered on the (2 Mt)^3 grid;
+//     the oversampled Mg0 x Mg1 x Mg2 grid, k_d = 2 pi kbar_d / (Mg_d h), R the
+//     diagonal of the extended box; only the half spectrum kx in [0, Mg0/2] is
+//     formed (the data are real and even);
+//  2. inverse FFT (complex-to-real), normalised by 1/(Mg0 Mg1 Mg2);
+//  3. keep the 2 Mt_d values per dimension centred at zero (j in [-Mt_d, Mt_d-1]),
+//     stored wrap-ordered on the (2 Mt0) x (2 Mt1) x (2 Mt2) grid;
 //  4. forward FFT (real-to-complex); the result is real and even, so the
-//     (Mt+1)^3 octant of its real part is all the scaling step needs.
+//     (Mt0+1)(Mt1+1)(Mt2+1) octant of its real part is all the scaling step needs.
 #include <stdio.h>
 #include <string.h>
 
@@ -49,53 +50,59 @@ __device__ double hhat_trunc(double k, double R) {
     return 8.0 * M_PI * s * s;
 }
 
-__global__ void k_eval_truncated(int Mg, double dk, double R, int harmonic, cufftDoubleComplex *out) {
-    const int nxh = Mg / 2 + 1;
-    size_t nk = (size_t)Mg * Mg * nxh;
+struct Dims3 {
+    int n[3];
+};
+
+__global__ void k_eval_truncated(Dims3 mg, double3 dk, double R, int harmonic, cufftDoubleComplex *out) {
+    const int nxh = mg.n[0] / 2 + 1;
+    size_t nk = (size_t)mg.n[2] * mg.n[1] * nxh;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nk) return;
     int kx = idx % nxh;
-    int ky = (idx / nxh) % Mg;
-    int kz = idx / ((size_t)nxh * Mg);
-    int by = (ky < Mg / 2) ? ky : ky - Mg;
-    int bz = (kz < Mg / 2) ? kz : kz - Mg;
-    double kk = dk * sqrt((double)kx * kx + (double)by * by + (double)bz * bz);
+    int ky = (idx / nxh) % mg.n[1];
+    int kz = idx / ((size_t)nxh * mg.n[1]);
+    int by = (ky < mg.n[1] / 2) ? ky : ky - mg.n[1];
+    int bz = (kz < mg.n[2] / 2) ? kz : kz - mg.n[2];
+    const double qx = dk.x * kx, qy = dk.y * by, qz = dk.z * bz;
+    double kk = sqrt(qx * qx + qy * qy + qz * qz);
     double v = harmonic ? hhat_trunc(kk, R) : bhat_trunc(kk, R);
     out[idx] = make_cuDoubleComplex(v, 0.0);
 }
 
-// Gt[j mod Mf] = G[j mod Mg] / Mg^3 for j in [-Mt, Mt-1]^3
-__global__ void k_truncate(int Mg, int Mt, double scale, const double *G, double *Gt) {
-    const int Mf = 2 * Mt;
-    size_t n = (size_t)Mf * Mf * Mf;
+// Gt[j mod Mf] = G[j mod Mg] / (Mg0 Mg1 Mg2) for j_d in [-Mt_d, Mt_d-1]
+__global__ void k_truncate(Dims3 mg, Dims3 mt, double scale, const double *G, double *Gt) {
+    const int fx = 2 * mt.n[0], fy = 2 * mt.n[1], fz = 2 * mt.n[2];
+    size_t n = (size_t)fx * fy * fz;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
-    int ix = idx % Mf, iy = (idx / Mf) % Mf, iz = idx / ((size_t)Mf * Mf);
+    int ix = idx % fx, iy = (idx / fx) % fy, iz = idx / ((size_t)fx * fy);
     // destination index i holds j = i (i < Mt) or i - Mf (i >= Mt)
-    int jx = ix < Mt ? ix : ix - Mf;
-    int jy = iy < Mt ? iy : iy - Mf;
-    int jz = iz < Mt ? iz : iz - Mf;
-    int sx = (jx + Mg) % Mg, sy = (jy + Mg) % Mg, sz = (jz + Mg) % Mg;
-    Gt[idx] = G[((size_t)sz * Mg + sy) * Mg + sx] * scale;
+    int jx = ix < mt.n[0] ? ix : ix - fx;
+    int jy = iy < mt.n[1] ? iy : iy - fy;
+    int jz = iz < mt.n[2] ? iz : iz - fz;
+    int sx = (jx + mg.n[0]) % mg.n[0], sy = (jy + mg.n[1]) % mg.n[1], sz = (jz + mg.n[2]) % mg.n[2];
+    Gt[idx] = G[((size_t)sz * mg.n[1] + sy) * mg.n[0] + sx] * scale;
 }
 
-__global__ void k_octant(int Mt, const cufftDoubleComplex *spec, double *oct64, float *oct32) {
-    const int Mf = 2 * Mt, nxh = Mt + 1, O = Mt + 1;
-    size_t n = (size_t)O * O * O;
+__global__ void k_octant(Dims3 mt, const cufftDoubleComplex *spec, double *oct64, float *oct32) {
+    const int fy = 2 * mt.n[1], nxh = mt.n[0] + 1;
+    const int ox = mt.n[0] + 1, oy = mt.n[1] + 1, oz = mt.n[2] + 1;
+    size_t n = (size_t)ox * oy * oz;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
-    int ax = idx % O, ay = (idx / O) % O, az = idx / ((size_t)O * O);
-    double v = spec[((size_t)az * Mf + ay) * nxh + ax].x;
+    int ax = idx % ox, ay = (idx / ox) % oy, az = idx / ((size_t)ox * oy);
+    double v = spec[((size_t)az * fy + ay) * nxh + ax].x;
     oct64[idx] = v;
     if (oct32) oct32[idx] = (float)v;
 }
 
 se_status_t precompute_compute(se_plan_s *p) {
-    const int Mg = p->Mg, Mt = p->Mt, Mf = p->Mf;
-    const size_t nkg = (size_t)Mg * Mg * (Mg / 2 + 1);
-    const size_t ng = (size_t)Mg * Mg * Mg;
-    const size_t nf = (size_t)Mf * Mf * Mf;
-    const size_t nkf = (size_t)Mf * Mf * (Mf / 2 + 1);
+    const Dims3 mg{{p->mg[0], p->mg[1], p->mg[2]}}, mt{{p->mt[0], p->mt[1], p->mt[2]}};
+    const size_t nkg = (size_t)mg.n[2] * mg.n[1] * (mg.n[0] / 2 + 1);
+    const size_t ng = (size_t)mg.n[2] * mg.n[1] * mg.n[0];
+    const size_t nf = (size_t)p->mf[0] * p->mf[1] * p->mf[2];
+    const size_t nkf = (size_t)p->mf[2] * p->mf[1] * (p->mf[0] / 2 + 1);
     cufftDoubleComplex *spec = nullptr;
     double *G = nullptr;
     cufftHandle plan = 0;
@@ -116,10 +123,11 @@ se_status_t precompute_compute(se_plan_s *p) {
         cudaGetLastError();
         return fail(SE_ERR_OOM, "precompute: device allocation failed");
     }
-    double dk = 2.0 * M_PI / (Mg * p->h);
+    const double3 dk = make_double3(2.0 * M_PI / (mg.n[0] * p->h), 2.0 * M_PI / (mg.n[1] * p->h),
+                                    2.0 * M_PI / (mg.n[2] * p->h));
     int harmonic = (p->kernel == SE_ROTLET);
-    k_eval_truncated<<<(unsigned)((nkg + 255) / 256), 256>>>(Mg, dk, p->R, harmonic, spec);
-    if (cufftPlan3d(&plan, Mg, Mg, Mg, CUFFT_Z2D) != CUFFT_SUCCESS) {
+    k_eval_truncated<<<(unsigned)((nkg + 255) / 256), 256>>>(mg, dk, p->R, harmonic, spec);
+    if (cufftPlan3d(&plan, mg.n[2], mg.n[1], mg.n[0], CUFFT_Z2D) != CUFFT_SUCCESS) {
         cleanup();
         return fail(SE_ERR_CUFFT, "precompute: Z2D plan failed");
     }
@@ -129,7 +137,7 @@ se_status_t precompute_compute(se_plan_s *p) {
     }
     cufftDestroy(plan);
     plan = 0;
-    double *Gt = (double *)spec;  // reuse: Mf^3 doubles fit in the spectrum buffer? use a fresh area
+    double *Gt = nullptr;
     double *Gt_buf = nullptr;
     if (cudaMalloc(&Gt_buf, nf * sizeof(double)) != cudaSuccess) {
         cleanup();
@@ -137,8 +145,8 @@ se_status_t precompute_compute(se_plan_s *p) {
         return fail(SE_ERR_OOM, "precompute: device allocation failed");
     }
     Gt = Gt_buf;
-    k_truncate<<<(unsigned)((nf + 255) / 256), 256>>>(Mg, Mt, 1.0 / (double)ng, G, Gt);
-    if (cufftPlan3d(&plan, Mf, Mf, Mf, CUFFT_D2Z) != CUFFT_SUCCESS) {
+    k_truncate<<<(unsigned)((nf + 255) / 256), 256>>>(mg, mt, 1.0 / (double)ng, G, Gt);
+    if (cufftPlan3d(&plan, p->mf[2], p->mf[1], p->mf[0], CUFFT_D2Z) != CUFFT_SUCCESS) {
         cudaFree(Gt_buf);
         cleanup();
         return fail(SE_ERR_CUFFT, "precompute: D2Z plan failed");
@@ -148,8 +156,8 @@ se_status_t precompute_compute(se_plan_s *p) {
         cleanup();
         return fail(SE_ERR_CUFFT, "precompute: D2Z failed");
     }
-    size_t no = (size_t)(Mt + 1) * (Mt + 1) * (Mt + 1);
-    k_octant<<<(unsigned)((no + 255) / 256), 256>>>(Mt, spec, p->ghat64,
+    size_t no = (size_t)(mt.n[0] + 1) * (mt.n[1] + 1) * (mt.n[2] + 1);
+    k_octant<<<(unsigned)((no + 255) / 256), 256>>>(mt, spec, p->ghat64,
                                                     p->prec == SE_FP32 ? (float *)p->ghat : nullptr);
     cudaError_t ce = cudaDeviceSynchronize();
     cudaEventRecord(e1, 0);
@@ -169,7 +177,8 @@ se_status_t precompute_compute(se_plan_s *p) {
 
 // ---------------------------------------------------------------- cache
 // The precomputed octant depends only on the Green's function (harmonic or
-// biharmonic), Mg, Mt and h (R = sqrt(3) Mt h): not on xi, P or the points.
+// biharmonic), Mg, Mt and h per dimension (R is their diagonal): not on xi, P
+// or the points.
 // Plans with the same grid reuse it from a host-side cache, and optionally
 // from files in a directory (one file per key, written after computing).
 struct CacheEntry {
@@ -186,9 +195,9 @@ constexpr size_t CACHE_MAX_BYTES = size_t(2) << 30;  // evict the oldest entries
 std::string cache_key(const se_plan_s *p) {
     uint64_t hb;
     memcpy(&hb, &p->h, sizeof(hb));
-    char buf[128];
-    snprintf(buf, sizeof(buf), "%s_Mg%d_Mt%d_h%016llx", p->kernel == SE_ROTLET ? "H" : "B", p->Mg, p->Mt,
-             (unsigned long long)hb);
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%s_Mg%dx%dx%d_Mt%dx%dx%d_h%016llx", p->kernel == SE_ROTLET ? "H" : "B", p->mg[0],
+             p->mg[1], p->mg[2], p->mt[0], p->mt[1], p->mt[2], (unsigned long long)hb);
     return buf;
 }
 
@@ -237,7 +246,7 @@ se_status_t upload(se_plan_s *p, const std::vector<double> &oct) {
 }  // namespace
 
 se_status_t precompute(se_plan_s *p) {
-    const size_t n = (size_t)(p->Mt + 1) * (p->Mt + 1) * (p->Mt + 1);
+    const size_t n = (size_t)(p->mt[0] + 1) * (p->mt[1] + 1) * (p->mt[2] + 1);
     const auto t0 = std::chrono::steady_clock::now();
     const std::string key = cache_key(p);
     std::vector<double> oct;

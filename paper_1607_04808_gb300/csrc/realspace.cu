@@ -26,6 +26,7 @@
 // per target with ballot compaction of the candidates.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "erfc_poly.cuh"
@@ -37,7 +38,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int QCAP = 64;
-constexpr int MAXROWS = 121;  // reach <= 5 cells across rows
+constexpr int MAXROWS = 121;  // (2 reach_y + 1)(2 reach_z + 1) rows of cells at most
 
 __device__ __forceinline__ float ex2_approx(float v) {
     float r;
@@ -148,21 +149,21 @@ __device__ __forceinline__ int row_segments(const GP<T> &g, const RC<T> &rk, con
     unpack3(get_tag(xt), cc[0], cc[1], cc[2]);
     const T rel[3] = {xt.x - g.x0[0], xt.y - g.x0[1], xt.z - g.x0[2]};
     const T rc2m = rk.rc2 * T(1.0001);
-    const int R = rk.reach, W = 2 * R + 1, nrows = W * W;
+    const int Ry = rk.reach[0], Rz = rk.reach[1], Wy = 2 * Ry + 1, nrows = Wy * (2 * Rz + 1);
     for (int r = lane; r < nrows; r += 32) {
-        int iy = cc[1] + (r % W) - R, iz = cc[2] + (r / W) - R;
+        int iy = cc[1] + (r % Wy) - Ry, iz = cc[2] + (r / Wy) - Rz;
         int2 sg = make_int2(0, 0);
-        if (iy >= 0 && iy < g.ncd && iz >= 0 && iz < g.ncd) {
-            const T ylo = iy * g.cw, zlo = iz * g.cw;
-            const T dy = max(T(0), max(ylo - rel[1], rel[1] - (ylo + g.cw)));
-            const T dz = max(T(0), max(zlo - rel[2], rel[2] - (zlo + g.cw)));
+        if (iy >= 0 && iy < g.ncel[1] && iz >= 0 && iz < g.ncel[2]) {
+            const T ylo = iy * g.cw[1], zlo = iz * g.cw[2];
+            const T dy = max(T(0), max(ylo - rel[1], rel[1] - (ylo + g.cw[1])));
+            const T dz = max(T(0), max(zlo - rel[2], rel[2] - (zlo + g.cw[2])));
             const T d2 = dy * dy + dz * dz;
             if (d2 <= rc2m) {
-                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cwx;
-                const int ixl = max(0, (int)floor((rel[0] - del) * g.inv_cwx));
-                const int ixh = min(g.ncdx - 1, (int)floor((rel[0] + del) * g.inv_cwx));
+                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cw[0];
+                const int ixl = max(0, (int)floor((rel[0] - del) * g.icw[0]));
+                const int ixh = min(g.ncel[0] - 1, (int)floor((rel[0] + del) * g.icw[0]));
                 if (ixl <= ixh) {
-                    const int base = (iz * g.ncd + iy) * g.ncdx;
+                    const int base = (iz * g.ncel[1] + iy) * g.ncel[0];
                     sg = make_int2(cell_start[base + ixl], cell_start[base + ixh + 1]);
                 }
             }
@@ -286,21 +287,21 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
     int c0[3], c1[3];
     unpack3(get_tag(xT[cl.x]), c0[0], c0[1], c0[2]);
     unpack3(get_tag(xT[cl.x + cl.y - 1]), c1[0], c1[1], c1[2]);
-    const int R = rk.reach, W = 2 * R + 1, nrows = W * W;
+    const int Ry = rk.reach[0], Rz = rk.reach[1], Wy = 2 * Ry + 1, nrows = Wy * (2 * Rz + 1);
     const T rc2m = rk.rc2 * T(1.0001);
     for (int r = lane; r < nrows; r += 32) {
-        const int dyc = (r % W) - R, dzc = (r / W) - R;
+        const int dyc = (r % Wy) - Ry, dzc = (r / Wy) - Rz;
         const int iy = c0[1] + dyc, iz = c0[2] + dzc;
         int2 sg = make_int2(0, 0);
-        if (iy >= 0 && iy < g.ncd && iz >= 0 && iz < g.ncd) {
-            const T dy = T(max(abs(dyc) - 1, 0)) * g.cw, dz = T(max(abs(dzc) - 1, 0)) * g.cw;
+        if (iy >= 0 && iy < g.ncel[1] && iz >= 0 && iz < g.ncel[2]) {
+            const T dy = T(max(abs(dyc) - 1, 0)) * g.cw[1], dz = T(max(abs(dzc) - 1, 0)) * g.cw[2];
             const T d2 = dy * dy + dz * dz;
             if (d2 <= rc2m) {
-                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cwx;
-                const int ixl = max(0, (int)floor((T(c0[0]) * g.cwx - del) * g.inv_cwx));
-                const int ixh = min(g.ncdx - 1, (int)floor((T(c1[0] + 1) * g.cwx + del) * g.inv_cwx));
+                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cw[0];
+                const int ixl = max(0, (int)floor((T(c0[0]) * g.cw[0] - del) * g.icw[0]));
+                const int ixh = min(g.ncel[0] - 1, (int)floor((T(c1[0] + 1) * g.cw[0] + del) * g.icw[0]));
                 if (ixl <= ixh) {
-                    const int base = (iz * g.ncd + iy) * g.ncdx;
+                    const int base = (iz * g.ncel[1] + iy) * g.ncel[0];
                     sg = make_int2(cell_start[base + ixl], cell_start[base + ixh + 1]);
                 }
             }
@@ -458,26 +459,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
     int c0[3], c1[3];
     unpack3(get_tag(xs[cl.x]), c0[0], c0[1], c0[2]);
     unpack3(get_tag(xs[cl.x + cl.y - 1]), c1[0], c1[1], c1[2]);
-    const int R = rk.reach, W = 2 * R + 1, nrows = W * W;
+    const int Ry = rk.reach[0], Rz = rk.reach[1], Wy = 2 * Ry + 1, nrows = Wy * (2 * Rz + 1);
     const T rc2m = rk.rc2 * T(1.0001);
-    const int own_row = c0[2] * g.ncd + c0[1];
+    const int own_row = c0[2] * g.ncel[1] + c0[1];
     // rows at or after the cluster's row in the sorted order; the own row from
     // the cluster's first point on, so that it leads the stream and stream
     // position v < cl.y is the cluster's own point cl.x + v
     for (int r = lane; r < nrows; r += 32) {
-        const int dyc = (r % W) - R, dzc = (r / W) - R;
+        const int dyc = (r % Wy) - Ry, dzc = (r / Wy) - Rz;
         const int iy = c0[1] + dyc, iz = c0[2] + dzc;
         int2 sg = make_int2(0, 0);
-        const int row = iz * g.ncd + iy;
-        if (iy >= 0 && iy < g.ncd && iz >= 0 && iz < g.ncd && row >= own_row) {
-            const T dy = T(max(abs(dyc) - 1, 0)) * g.cw, dz = T(max(abs(dzc) - 1, 0)) * g.cw;
+        const int row = iz * g.ncel[1] + iy;
+        if (iy >= 0 && iy < g.ncel[1] && iz >= 0 && iz < g.ncel[2] && row >= own_row) {
+            const T dy = T(max(abs(dyc) - 1, 0)) * g.cw[1], dz = T(max(abs(dzc) - 1, 0)) * g.cw[2];
             const T d2 = dy * dy + dz * dz;
             if (d2 <= rc2m) {
-                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cwx;
-                const int ixl = max(0, (int)floor((T(c0[0]) * g.cwx - del) * g.inv_cwx));
-                const int ixh = min(g.ncdx - 1, (int)floor((T(c1[0] + 1) * g.cwx + del) * g.inv_cwx));
+                const T del = sqrt(rc2m - d2) + T(1e-4) * g.cw[0];
+                const int ixl = max(0, (int)floor((T(c0[0]) * g.cw[0] - del) * g.icw[0]));
+                const int ixh = min(g.ncel[0] - 1, (int)floor((T(c1[0] + 1) * g.cw[0] + del) * g.icw[0]));
                 if (ixl <= ixh) {
-                    const int base = row * g.ncdx;
+                    const int base = row * g.ncel[0];
                     sg = make_int2(cell_start[base + ixl], cell_start[base + ixh + 1]);
                     if (row == own_row) sg.x = cl.x;
                 }
@@ -649,7 +650,7 @@ __global__ void k_bcluster_count(int nrows_tot, const BSys<T> *__restrict__ sys,
     if (row >= nrows_tot) return;
     const int s = find_range(row_base, S, row);
     const BSys<T> &B = sys[s];
-    const int ncdx = B.g.ncdx, lr = row - row_base[s];
+    const int ncdx = B.g.ncel[0], lr = row - row_base[s];
     const int *cs = cell_start + B.cell_base;
     const int len = cs[(lr + 1) * ncdx] - cs[lr * ncdx];
     ncl[row] = (len + tpw - 1) / tpw;
@@ -663,7 +664,7 @@ __global__ void k_bcluster_fill(int nrows_tot, const BSys<T> *__restrict__ sys, 
     if (row >= nrows_tot) return;
     const int s = find_range(row_base, S, row);
     const BSys<T> &B = sys[s];
-    const int ncdx = B.g.ncdx, lr = row - row_base[s];
+    const int ncdx = B.g.ncel[0], lr = row - row_base[s];
     const int *cs = cell_start + B.cell_base;
     const int a = cs[lr * ncdx], b = cs[(lr + 1) * ncdx];
     int o = ncl_start[row];
@@ -989,10 +990,10 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
     // targets per cluster: the symmetric kernel's or the full-list kernel's
     constexpr int TPW = SE_RS_TPW, TPWS = sizeof(T) == 4 ? SE_RS_SYM_TPW : SE_RS_SYM_TPW64;
     const int tpw = sym ? TPWS : TPW;
-    const int nrows = p->geom.ncd * p->geom.ncd;
-    k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, tpw, p->b.cnt_r, p->b.ncl);
+    const int nrows = p->geom.ncel[1] * p->geom.ncel[2];
+    k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], tpw, p->b.cnt_r, p->b.ncl);
     launch_scan(p->b.ncl, nrows, st);
-    k_cluster_fill<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, tpw, p->b.cnt_r, p->b.ncl,
+    k_cluster_fill<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], tpw, p->b.cnt_r, p->b.ncl,
                                                          p->b.clusters);
     const long max_cl = N / tpw + nrows + 1;
     const unsigned nblk = (unsigned)((max_cl + 7) / 8);
@@ -1064,8 +1065,16 @@ RC<T> make_rc(const se_plan_s *p) {
     rk.c3 = (T)(4.0 * p->xi * p->xi * p->xi / sqrt(M_PI));
     rk.rc2 = (T)(p->rc * p->rc);
     rk.ce = (T)(-p->xi * p->xi / log(2.0));  // exp(-xi^2 r^2) = 2^(ce r^2)
-    rk.reach = (int)ceil(p->rc * p->geom.inv_cw - 1e-9);
+    // rows farther than the last cell of a side hold nothing: cap the reach
+    rk.reach[0] = std::min((int)ceil(p->rc * p->geom.icw[1] - 1e-9), p->geom.ncel[1] - 1);
+    rk.reach[1] = std::min((int)ceil(p->rc * p->geom.icw[2] - 1e-9), p->geom.ncel[2] - 1);
     return rk;
+}
+
+// The row lists of the real-space kernels hold at most MAXROWS rows of cells.
+template <typename T>
+static bool reach_ok(const RC<T> &rk) {
+    return (2 * rk.reach[0] + 1) * (2 * rk.reach[1] + 1) <= MAXROWS;
 }
 
 template RC<float> make_rc<float>(const se_plan_s *);
@@ -1089,7 +1098,7 @@ template cudaError_t launch_breal<double>(int, const BSys<double> *, const int *
 template <typename T>
 cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u) {
     RC<T> rk = make_rc<T>(p);
-    if (rk.reach > 5) return cudaErrorInvalidValue;
+    if (!reach_ok(rk)) return cudaErrorInvalidValue;
     if (p->kernel == SE_STOKESLET) return launch_real_k<T, SE_STOKESLET>(p, st, rk, u);
     if (p->kernel == SE_STRESSLET) return launch_real_k<T, SE_STRESSLET>(p, st, rk, u);
     return launch_real_k<T, SE_ROTLET>(p, st, rk, u);
@@ -1100,11 +1109,11 @@ cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u) {
 template <typename T, int KERNEL>
 cudaError_t launch_real_targets_k(se_plan_s *p, cudaStream_t st, Buffers &bt, int Nt, T *ut) {
     constexpr int TPW = SE_RS_TPW;
-    const int nrows = p->geom.ncd * p->geom.ncd;
-    k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, TPW, bt.cnt_r, bt.ncl);
+    const int nrows = p->geom.ncel[1] * p->geom.ncel[2];
+    k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], TPW, bt.cnt_r, bt.ncl);
     cudaError_t e = launch_scan(bt.ncl, nrows, st);
     if (e) return e;
-    k_cluster_fill<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncdx, TPW, bt.cnt_r, bt.ncl, bt.clusters);
+    k_cluster_fill<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], TPW, bt.cnt_r, bt.ncl, bt.clusters);
     const long max_cl = Nt / TPW + nrows + 1;
     const unsigned nblk = (unsigned)((max_cl + 7) / 8);
     const RC<T> rk = make_rc<T>(p);
@@ -1125,7 +1134,7 @@ cudaError_t launch_real_targets_k(se_plan_s *p, cudaStream_t st, Buffers &bt, in
 
 template <typename T>
 cudaError_t launch_real_targets(se_plan_s *p, cudaStream_t st, Buffers &bt, int Nt, T *ut) {
-    if (make_rc<T>(p).reach > 5) return cudaErrorInvalidValue;
+    if (!reach_ok(make_rc<T>(p))) return cudaErrorInvalidValue;
     if (p->kernel == SE_STOKESLET) return launch_real_targets_k<T, SE_STOKESLET>(p, st, bt, Nt, ut);
     if (p->kernel == SE_STRESSLET) return launch_real_targets_k<T, SE_STRESSLET>(p, st, bt, Nt, ut);
     return launch_real_targets_k<T, SE_ROTLET>(p, st, bt, Nt, ut);
@@ -1138,7 +1147,7 @@ template <typename T>
 cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *gx) {
     int N = (int)p->N;
     RC<T> rk = make_rc<T>(p);
-    if (rk.reach > 5) return cudaErrorInvalidValue;
+    if (!reach_ok(rk)) return cudaErrorInvalidValue;
     unsigned gs = (N + 7) / 8;
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r;
     const GP<T> &g = gp<T>(p);
@@ -1160,7 +1169,7 @@ template <typename T>
 cudaError_t launch_real_adjT(se_plan_s *p, cudaStream_t st, const T *f_orig, const T *q_orig, T *gf, T *gq) {
     const int N = (int)p->N;
     const RC<T> rk = make_rc<T>(p);
-    if (rk.reach > 5) return cudaErrorInvalidValue;
+    if (!reach_ok(rk)) return cudaErrorInvalidValue;
     k_real_cmp<T, SE_STRESSLET, true><<<(N + 7) / 8, 256, 0, st>>>(
         gp<T>(p), rk, N, (const vec4<T> *)p->b.xs_r, (const vec4<T> *)p->b.fs_r, nullptr, p->b.cnt_r,
         p->b.perm_r, gf, p->b.status, f_orig, q_orig, gq);

@@ -21,24 +21,35 @@ namespace {
 __device__ __forceinline__ float sexp(float v) { return expf(v); }
 __device__ __forceinline__ double sexp(double v) { return exp(v); }
 
+// Half-spectrum point idx of the [kz][ky][kx] R2C layout: its wave vector and
+// the index of |k| in the stored octant of the precomputed kernel.
+template <typename T>
+__device__ __forceinline__ size_t kpoint(const ScaleConst &sc, size_t idx, T kv[3]) {
+    const int kx = idx % sc.nxh;
+    const int ky = (idx / sc.nxh) % sc.mf[1];
+    const int kz = idx / ((size_t)sc.nxh * sc.mf[1]);
+    const int bx = (kx == sc.mt[0]) ? -sc.mt[0] : kx;
+    const int by = (ky < sc.mt[1]) ? ky : ky - sc.mf[1];
+    const int bz = (kz < sc.mt[2]) ? kz : kz - sc.mf[2];
+    kv[0] = (T)sc.dk[0] * bx;
+    kv[1] = (T)sc.dk[1] * by;
+    kv[2] = (T)sc.dk[2] * bz;
+    return ((size_t)abs(bz) * (sc.mt[1] + 1) + abs(by)) * (sc.mt[0] + 1) + abs(bx);
+}
+
+__host__ __device__ inline size_t half_spectrum(const ScaleConst &sc) {
+    return (size_t)sc.mf[2] * sc.mf[1] * sc.nxh;
+}
+
 // The multiplier at half-spectrum point idx applied to ngroups groups of
 // source components (each group nc consecutive spectra of nk points).
 template <typename T, int KERNEL>
 __device__ __forceinline__ void scale_point(const ScaleConst &sc, const T *__restrict__ ghat,
                                             cplx<T> *__restrict__ spec, size_t idx, int ngroups) {
     using C = cplx<T>;
-    const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
-    int kx = idx % sc.nxh;
-    int ky = (idx / sc.nxh) % sc.Mf;
-    int kz = idx / ((size_t)sc.nxh * sc.Mf);
-    int bx = (kx == sc.Mt) ? -sc.Mt : kx;
-    int by = (ky < sc.Mt) ? ky : ky - sc.Mf;
-    int bz = (kz < sc.Mt) ? kz : kz - sc.Mf;
-    int ax = abs(bx), ay = abs(by), az = abs(bz);
-    const int O = sc.Mt + 1;
-    T G = ghat[((size_t)az * O + ay) * O + ax];
-    T k1 = (T)sc.dk;
-    T kv[3] = {k1 * bx, k1 * by, k1 * bz};
+    const size_t nk = half_spectrum(sc);
+    T kv[3];
+    const T G = ghat[kpoint<T>(sc, idx, kv)];
     T k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
     T F = (T)sc.norm * G * sexp((T)sc.ecoef * k2);
     if (KERNEL != SE_ROTLET) F *= (T(1) + k2 * (T)sc.inv4xi2);
@@ -104,7 +115,7 @@ __device__ __forceinline__ void scale_point(const ScaleConst &sc, const T *__res
 
 template <typename T, int KERNEL>
 __global__ void k_scale(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__restrict__ spec) {
-    const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
+    const size_t nk = half_spectrum(sc);
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nk) return;
     scale_point<T, KERNEL>(sc, ghat, spec, idx, 1);
@@ -119,19 +130,11 @@ __global__ void k_scale(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__re
 template <typename T>
 __global__ void k_scale_adj_stresslet(ScaleConst sc, const T *__restrict__ ghat, cplx<T> *__restrict__ spec) {
     using C = cplx<T>;
-    const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
+    const size_t nk = half_spectrum(sc);
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nk) return;
-    int kx = idx % sc.nxh;
-    int ky = (idx / sc.nxh) % sc.Mf;
-    int kz = idx / ((size_t)sc.nxh * sc.Mf);
-    int bx = (kx == sc.Mt) ? -sc.Mt : kx;
-    int by = (ky < sc.Mt) ? ky : ky - sc.Mf;
-    int bz = (kz < sc.Mt) ? kz : kz - sc.Mf;
-    const int O = sc.Mt + 1;
-    const T G = ghat[((size_t)abs(bz) * O + abs(by)) * O + abs(bx)];
-    const T k1 = (T)sc.dk;
-    const T kv[3] = {k1 * bx, k1 * by, k1 * bz};
+    T kv[3];
+    const T G = ghat[kpoint<T>(sc, idx, kv)];
     const T k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
     const T F = (T)sc.norm * G * sexp((T)sc.ecoef * k2) * (T(1) + k2 * (T)sc.inv4xi2);
     C *w0 = spec + idx;
@@ -162,7 +165,7 @@ __global__ void k_bscale(const BSys<T> *__restrict__ sys, const int *__restrict_
     const int s = find_range(blk_base, S, (int)blockIdx.x);
     const BSys<T> &B = sys[s];
     const ScaleConst sc = B.sc;
-    const size_t nk = (size_t)sc.Mf * sc.Mf * sc.nxh;
+    const size_t nk = half_spectrum(sc);
     const size_t idx = (size_t)(blockIdx.x - blk_base[s]) * blockDim.x + threadIdx.x;
     if (idx >= nk) return;
     scale_point<T, KERNEL>(sc, B.ghat, B.spec, idx, n_rhs);
@@ -172,14 +175,16 @@ __global__ void k_bscale(const BSys<T> *__restrict__ sys, const int *__restrict_
 
 ScaleConst make_scale_const(const se_plan_s *p) {
     ScaleConst sc;
-    sc.Mt = p->Mt;
-    sc.Mf = p->Mf;
-    sc.nxh = p->Mf / 2 + 1;
-    sc.dk = 2.0 * M_PI / (p->Mf * p->h);
+    for (int d = 0; d < 3; d++) {
+        sc.mt[d] = p->mt[d];
+        sc.mf[d] = p->mf[d];
+        sc.dk[d] = 2.0 * M_PI / (p->mf[d] * p->h);
+    }
+    sc.nxh = p->mf[0] / 2 + 1;
     sc.inv4xi2 = 1.0 / (4.0 * p->xi * p->xi);
     sc.ecoef = -(1.0 - p->eta) / (4.0 * p->xi * p->xi);
     double pre = pow(2.0 * p->xi * p->xi / (M_PI * p->eta), 1.5);
-    sc.norm = p->h * p->h * p->h / ((double)p->Mf * p->Mf * p->Mf) * pre * pre;
+    sc.norm = p->h * p->h * p->h / ((double)p->mf[0] * p->mf[1] * p->mf[2]) * pre * pre;
     return sc;
 }
 
@@ -187,7 +192,7 @@ template <typename T>
 cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpose) {
     (void)transpose;  // the stokeslet and rotlet multipliers equal their transposes
     const ScaleConst sc = make_scale_const(p);
-    size_t nk = (size_t)p->Mf * p->Mf * sc.nxh;
+    size_t nk = half_spectrum(sc);
     int bs = SCALE_BS;
     unsigned gs = (unsigned)((nk + bs - 1) / bs);
     const T *gh = (const T *)p->ghat;
@@ -205,7 +210,7 @@ cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpos
 template <typename T>
 cudaError_t launch_scale_adj_stresslet(se_plan_s *p, cudaStream_t st, void *spec) {
     const ScaleConst sc = make_scale_const(p);
-    const size_t nk = (size_t)p->Mf * p->Mf * sc.nxh;
+    const size_t nk = half_spectrum(sc);
     k_scale_adj_stresslet<T><<<(unsigned)((nk + SCALE_BS - 1) / SCALE_BS), SCALE_BS, 0, st>>>(
         sc, (const T *)p->ghat, (cplx<T> *)spec);
     p->launches++;

@@ -46,22 +46,22 @@ template <typename T> using cplx = typename Cplx<T>::type;
 
 // ---------------------------------------------------------------- geometry shared by kernels
 // Everything a kernel needs to place a point on the grids and in the cells.
+// Per-dimension arrays are indexed x, y, z; grids are stored z-major with x
+// fastest.  The box is a rectangular cuboid with one grid spacing h.
 struct Geom {
     double x0[3];      // box corner
-    double L;          // box side
+    double len[3];     // box sides
     double h, inv_h;   // grid spacing and its inverse
     double half_ext;   // n_ext / 2 (grid units): t = (x - x0)/h + n_ext/2 is (x - y0)/h
     int P;             // Gaussian support (grid points per dimension)
-    int Mt;            // extended grid points per dimension
-    int Mf;            // FFT size per dimension (2 Mt)
+    int mt[3];         // extended grid points per dimension
+    int mf[3];         // FFT size per dimension (2 mt)
     int T;             // spreading tile edge (window starts per tile per dimension)
-    int ntd;           // tiles per dimension
+    int nt[3];         // tiles per dimension
     double a;          // Gaussian exponent 2 xi^2 / eta (per unit length^2)
-    // real-space cells
-    int ncd;           // cells per dimension across rows (y, z)
-    double cw, inv_cw; // cell width and inverse (y, z)
-    int ncdx;          // cells along x (rows are split finer along x)
-    double cwx, inv_cwx;
+    // real-space cells: rows of cells run along x (split finer along x)
+    int ncel[3];       // cells per dimension
+    double cw[3], icw[3];  // cell widths and their inverses
     double rc;         // cutoff
     double xi;
 };
@@ -70,12 +70,12 @@ struct Geom {
 // never touch the (slow on this part) FP64 pipe for bookkeeping.
 template <typename T>
 struct GP {
-    T x0[3], L;        // box corner and side
+    T x0[3], len[3];   // box corner and sides
     T inv_h, half_ext; // t = (x - x0) / h + n_ext / 2 = (x - y0) / h (grid units)
     T ah2;             // a h^2 = 2 xi^2 h^2 / eta: Gaussian exponent per grid unit^2
-    T inv_cw, cw;      // real-space cell width across rows (y, z)
-    T inv_cwx, cwx;    // real-space cell width along x (the row direction)
-    int P, Mt, Mf, T_, ntd, ncd, ncdx;
+    T icw[3], cw[3];   // real-space cell widths (x: along the rows) and inverses
+    int P, T_;
+    int mt[3], mf[3], nt[3], ncel[3];
 };
 
 // Screened real-space constants of one system (x = xi r).
@@ -83,16 +83,16 @@ template <typename T>
 struct RC {
     T xi, xi2, c, c3, rc2;  // xi, xi^2, 2 xi/sqrt(pi), 4 xi^3/sqrt(pi), rc^2
     T ce;                   // -xi^2 / ln 2: exp(-xi^2 r^2) = 2^(ce r^2)
-    int reach;              // rows of cells within reach on each side (y, z)
+    int reach[2];           // rows of cells within reach on each side in y and in z
 };
 
 // Constants of the k-space scaling of one system.
 struct ScaleConst {
-    double dk;        // 2 pi / (Mf h)
+    double dk[3];     // 2 pi / (mf h) per dimension
     double inv4xi2;   // 1 / (4 xi^2)
     double ecoef;     // -(1 - eta) / (4 xi^2)
-    double norm;      // h^3 / Mf^3 * pre^2
-    int Mt, Mf, nxh;  // nxh = Mf/2 + 1
+    double norm;      // h^3 / (mf_x mf_y mf_z) * pre^2
+    int mt[3], mf[3], nxh;  // nxh = mf_x/2 + 1
 };
 
 // One system of a batch as the batched kernels see it: its geometry and
@@ -103,10 +103,10 @@ struct BSys {
     GP<T> g;
     RC<T> rk;
     ScaleConst sc;
-    const T *ghat;     // (Mt+1)^3 octant of the precomputed kernel
-    T *grid;           // spread grids: 3 n_rhs x Mf^3 (zero padded)
-    cplx<T> *spec;     // their spectra: 3 n_rhs x Mf x Mf x (Mf/2+1)
-    T *wgrid;          // inverse transforms: 3 n_rhs x Mf^3
+    const T *ghat;     // (mt+1) octant of the precomputed kernel
+    T *grid;           // spread grids: 3 n_rhs grids of mf_x mf_y mf_z (zero padded)
+    cplx<T> *spec;     // their spectra: 3 n_rhs x mf_z x mf_y x (mf_x/2+1)
+    T *wgrid;          // inverse transforms: 3 n_rhs grids
     double self_coef;  // -4 xi / sqrt(pi) (stokeslet), 0 otherwise
     int off, n;        // points [off, off + n) of the concatenated and of the sorted order
     int tile_base, cell_base, row_base;
@@ -128,7 +128,7 @@ __host__ __device__ inline int find_range(const int *b, int S, int v) {
 // the box (they are flagged by the binning kernel; clamping keeps every kernel's
 // indexing in bounds).
 template <typename T>
-__host__ __device__ inline T clamp_rel(T rel, T L) {
+__host__ __device__ inline T clamp_rel(T rel, T L) {  // L: the box side in this dimension
     if (!(rel >= T(0) && rel < L)) rel = (rel >= L) ? L * T(1.0 - 1e-6) : T(0);
     return rel;
 }
@@ -138,11 +138,15 @@ __host__ __device__ inline T clamp_rel(T rel, T L) {
 // clamped to [0, Mt - P].  Computed once, in the binning kernel, and stored
 // with the sorted point so that every later kernel uses the same support.
 template <typename T>
-__host__ __device__ inline int window_start(T rel, const GP<T> &g) {
+__host__ __device__ inline int window_start(T rel, const GP<T> &g, int d) {
     T t = rel * g.inv_h + g.half_ext;
     int i0 = ((g.P & 1) == 0) ? (int)floor(t) - g.P / 2 + 1 : (int)floor(t + T(0.5)) - (g.P - 1) / 2;
-    return min(max(i0, 0), g.Mt - g.P);
+    return min(max(i0, 0), g.mt[d] - g.P);
 }
+
+// Grid sizes as 64-bit products
+template <typename G>
+__host__ __device__ inline size_t vol(const G &g) { return (size_t)g.mf[0] * g.mf[1] * g.mf[2]; }
 
 // Three indices < 1024 packed into the spare 4th component of a sorted point.
 __host__ __device__ inline int pack3(int a, int b, int c) { return a | (b << 10) | (c << 20); }
@@ -189,10 +193,14 @@ struct se_plan_s {
     int prec = 0;
     int64_t N = 0;
     double x0[3] = {0, 0, 0};
-    double L = 1;
+    double len[3] = {1, 1, 1};  // box sides
     // method parameters
     double xi = 0, rc = 0, h = 0, eta = 0, m = 0, deltaL = 0, R = 0;
-    int M = 0, P = 0, n_ext = 0, Mt = 0, Mf = 0, Mg = 0, deltaL_policy = 0, max_fft = 0;
+    int mm[3] = {0, 0, 0};  // M per dimension (grid points on the box)
+    int mt[3] = {0, 0, 0};  // extended grid M + n_ext
+    int mf[3] = {0, 0, 0};  // FFT sizes 2 mt
+    int mg[3] = {0, 0, 0};  // precompute grid
+    int P = 0, n_ext = 0, deltaL_policy = 0, max_fft = 0;
     int nc = 3;  // spread components (3; stresslet 6)
     se::Geom geom{};
     se::GP<float> gpf{};
@@ -233,7 +241,8 @@ void free_plan(se_plan_s *p);
 namespace se {
 
 // Parameters, grid sizes and geometry of a plan from chosen parameters (host only).
-se_status_t setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[4], const se_params_t &pr);
+// box: x0, y0, z0, Lx, Ly, Lz
+se_status_t setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[6], const se_params_t &pr);
 
 // launchers (defined in the .cu files); all asynchronous on `st`
 template <typename T>
@@ -319,5 +328,7 @@ template <> inline const GP<float> &gp<float>(const se_plan_s *p) { return p->gp
 template <> inline const GP<double> &gp<double>(const se_plan_s *p) { return p->gpd; }
 se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
                           double xi_arg, se_params_t *out, int n_rhs = 1);
+se_status_t choose_box_params(int kernel, int prec, int64_t N, const double box[6], double tol,
+                              const se_params_t *params, double xi, se_params_t *out, int n_rhs = 1);
 
 }  // namespace se

@@ -66,7 +66,7 @@ __device__ __forceinline__ void spread_tile_body(const GP<T> &g, int tile, int b
     __shared__ int soff[NB];
     T *sm = reinterpret_cast<T *>(smem_raw);
     const int P = g.P, PT = g.T_ + P - 1, PT2 = PT * PT, PT3 = PT2 * PT;
-    const int tx = tile % g.ntd, ty = (tile / g.ntd) % g.ntd, tz = tile / (g.ntd * g.ntd);
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * g.T_, gy0 = ty * g.T_, gz0 = tz * g.T_;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // this lane's (kx, ky) positions of the P x P support plane
@@ -139,12 +139,12 @@ __device__ __forceinline__ void spread_tile_body(const GP<T> &g, int tile, int b
         }
     }
     __syncthreads();
-    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    const size_t Mf3 = vol(g);
     for (int e = threadIdx.x; e < PT3; e += blockDim.x) {
         int px = e % PT, py = (e / PT) % PT, pz = e / PT2;
         int gx = gx0 + px, gy = gy0 + py, gz = gz0 + pz;
-        if (gx >= g.Mt || gy >= g.Mt || gz >= g.Mt) continue;
-        size_t gi = ((size_t)gz * g.Mf + gy) * g.Mf + gx;
+        if (gx >= g.mt[0] || gy >= g.mt[1] || gz >= g.mt[2]) continue;
+        size_t gi = ((size_t)gz * g.mf[1] + gy) * g.mf[0] + gx;
         for (int c = 0; c < nc; c++) {
             T v = sm[c * PT3 + e];
             if (v != T(0)) atomicAdd(grid + c * Mf3 + gi, v);
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(NW * 32) k_bspread_tile(const BSys<T> *__restr
     const int beg = tile_start[key], end = tile_start[key + 1];
     if (beg == end) return;
     const GP<T> g = B.g;
-    const size_t Mf3 = (size_t)g.Mf * g.Mf * g.Mf;
+    const size_t Mf3 = vol(g);
     spread_tile_body<T, NIT>(g, it.y, beg, end, 3, xs, fs, n_rhs, it.z, nullptr, B.grid + (size_t)it.z * 3 * Mf3);
 }
 
@@ -204,11 +204,11 @@ __global__ void k_spread_atomic(GP<T> g, int nc, int N, const vec4<T> *__restric
     const vec4<T> fv = fs[n];
     T s[6];
     for (int c = 0; c < nc; c++) s[c] = (nc == 6) ? stress_comp<T>(c, fv, qs[n]) : source_comp<T>(c, fv);
-    const size_t Mf = g.Mf, Mf2 = Mf * Mf, Mf3 = Mf2 * Mf;
+    const size_t Mfx = g.mf[0], Mf2 = Mfx * g.mf[1], Mf3 = vol(g);
     for (int idx = lane; idx < P2; idx += 32) {
         int ky = idx / P, kx = idx - ky * P;
         const T wxy = sw[0][kx] * sw[1][ky];
-        const size_t base = ((size_t)i0[2] * Mf + (i0[1] + ky)) * Mf + (i0[0] + kx);
+        const size_t base = ((size_t)i0[2] * g.mf[1] + (i0[1] + ky)) * Mfx + (i0[0] + kx);
         for (int kz = 0; kz < P; kz++) {
             const T wt = wxy * sw[2][kz];
             for (int c = 0; c < nc; c++) atomicAdd(grid + c * Mf3 + base + kz * Mf2, s[c] * wt);
@@ -216,15 +216,21 @@ __global__ void k_spread_atomic(GP<T> g, int nc, int N, const vec4<T> *__restric
     }
 }
 
+// Zero the mt_x x mt_y x mt_z corner of nc grids (one warp-row per (c, z, y)
+// row of mt_x values); the rest of the padded grids stays zero.
 template <typename T>
-__global__ void k_zero_octant(T *__restrict__ grid, int Mt, int Mf, int nc) {
-    // one warp-row per (c, z, y) row of Mt values
+__device__ __forceinline__ void zero_rows(T *__restrict__ grid, const int mt[3], const int mf[3], size_t row) {
+    const int y = row % mt[1], z = (row / mt[1]) % mt[2];
+    const size_t c = row / ((size_t)mt[1] * mt[2]);
+    T *p = grid + c * mf[0] * mf[1] * mf[2] + ((size_t)z * mf[1] + y) * mf[0];
+    for (int x = threadIdx.x; x < mt[0]; x += blockDim.x) p[x] = T(0);
+}
+
+template <typename T>
+__global__ void k_zero_octant(T *__restrict__ grid, GP<T> g, int nc) {
     size_t row = (size_t)blockIdx.x * blockDim.y + threadIdx.y;
-    size_t nrows = (size_t)nc * Mt * Mt;
-    if (row >= nrows) return;
-    int y = row % Mt, z = (row / Mt) % Mt, c = row / ((size_t)Mt * Mt);
-    T *p = grid + (size_t)c * Mf * Mf * Mf + ((size_t)z * Mf + y) * Mf;
-    for (int x = threadIdx.x; x < Mt; x += blockDim.x) p[x] = T(0);
+    if (row >= (size_t)nc * g.mt[1] * g.mt[2]) return;
+    zero_rows(grid, g.mt, g.mf, row);
 }
 
 // Batched: zero the octant of every grid of every system (rows of Mt values;
@@ -234,14 +240,9 @@ __global__ void k_bzero_octant(const BSys<T> *__restrict__ sys, const int *__res
                                int n_rhs) {
     const int s = find_range(zblk_base, S, (int)blockIdx.x);
     const BSys<T> &B = sys[s];
-    const int Mt = B.g.Mt, Mf = B.g.Mf;
     const size_t row = (size_t)(blockIdx.x - zblk_base[s]) * blockDim.y + threadIdx.y;
-    const size_t nrows = (size_t)3 * n_rhs * Mt * Mt;
-    if (row >= nrows) return;
-    const int y = row % Mt, z = (row / Mt) % Mt;
-    const size_t c = row / ((size_t)Mt * Mt);
-    T *p = B.grid + c * Mf * Mf * Mf + ((size_t)z * Mf + y) * Mf;
-    for (int x = threadIdx.x; x < Mt; x += blockDim.x) p[x] = T(0);
+    if (row >= (size_t)3 * n_rhs * B.g.mt[1] * B.g.mt[2]) return;
+    zero_rows(B.grid, B.g.mt, B.g.mf, row);
 }
 
 template <typename T, int NIT>
@@ -266,9 +267,9 @@ size_t spread_smem_bytes(const se_plan_s *p, int nc, size_t elem) {
 template <typename T>
 cudaError_t launch_zero_octant(se_plan_s *p, cudaStream_t st, void *grid, int nc) {
     dim3 bs(32, 8);
-    size_t nrows = (size_t)nc * p->Mt * p->Mt;
+    size_t nrows = (size_t)nc * p->mt[1] * p->mt[2];
     dim3 gs((unsigned)((nrows + bs.y - 1) / bs.y));
-    k_zero_octant<T><<<gs, bs, 0, st>>>((T *)grid, p->Mt, p->Mf, nc);
+    k_zero_octant<T><<<gs, bs, 0, st>>>((T *)grid, gp<T>(p), nc);
     p->launches++;
     return cudaGetLastError();
 }

@@ -58,6 +58,11 @@ def lib():
             L.se_plan_create.restype = i32
             L.se_plan_create.argtypes = [i32, i64, dbl, ctypes.POINTER(ctypes.c_double), dbl, i32,
                                          ctypes.POINTER(SEParams), ctypes.POINTER(vp)]
+            L.se_plan_create_box.restype = i32
+            L.se_plan_create_box.argtypes = [i32, i64, dbl, ctypes.POINTER(ctypes.c_double), dbl, i32,
+                                             ctypes.POINTER(SEParams), ctypes.POINTER(vp)]
+            L.se_plan_get_grid.restype = i32
+            L.se_plan_get_grid.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 4
             L.se_eval.restype = i32
             L.se_eval.argtypes = [vp, vp, vp, vp, vp, vp]
             L.se_eval_real_space.restype = i32
@@ -127,7 +132,9 @@ def _stream(stream=None):
 
 
 class Plan:
-    """A Spectral Ewald plan for N points in the cube [x0, x0+L)^3 (se_plan_create)."""
+    """A Spectral Ewald plan for N points in a box: box = (x0, y0, z0, L) for the
+    cube [x0, x0+L) x [y0, y0+L) x [z0, z0+L) (se_plan_create), or
+    (x0, y0, z0, Lx, Ly, Lz) for a rectangular box (se_plan_create_box)."""
 
     def __init__(self, kernel: str, N: int, box=(0.0, 0.0, 0.0, 1.0), *, xi: float = 0.0,
                  tol: float = 0.0, prec: str = "fp32", M: int = 0, P: int = 0, rc: float = 0.0,
@@ -138,12 +145,15 @@ class Plan:
         self.prec = prec
         self.dtype = torch.float32 if prec == "fp32" else torch.float64
         self.box = tuple(float(b) for b in box)
+        if len(self.box) not in (4, 6):
+            raise ValueError("box: (x0, y0, z0, L) or (x0, y0, z0, Lx, Ly, Lz)")
         prm = SEParams(xi=float(xi), rc=float(rc), M=int(M), P=int(P),
                        deltaL_policy=int(deltaL_policy), max_fft=int(max_fft))
-        boxa = (ctypes.c_double * 4)(*self.box)
+        boxa = (ctypes.c_double * len(self.box))(*self.box)
+        create = lib().se_plan_create if len(self.box) == 4 else lib().se_plan_create_box
         h = ctypes.c_void_p()
-        _check(lib().se_plan_create(self.kid, self.N, float(xi), boxa, float(tol), PRECS[prec],
-                                    ctypes.byref(prm), ctypes.byref(h)))
+        _check(create(self.kid, self.N, float(xi), boxa, float(tol), PRECS[prec],
+                      ctypes.byref(prm), ctypes.byref(h)))
         self._h = h
 
     @property
@@ -155,6 +165,13 @@ class Plan:
         p = SEParams()
         _check(lib().se_plan_get_params(self._h, ctypes.byref(p)))
         return {k: getattr(p, k) for k, _ in SEParams._fields_}
+
+    @property
+    def grid(self) -> dict:
+        """Grid sizes per dimension (se_plan_get_grid): M, Mtilde, Mf, Mg."""
+        arrs = [(ctypes.c_int * 3)() for _ in range(4)]
+        _check(lib().se_plan_get_grid(self._h, *arrs))
+        return {k: tuple(a) for k, a in zip(("M", "Mtilde", "Mf", "Mg"), arrs)}
 
     def _arg(self, t, name):
         if t is None:

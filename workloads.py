@@ -32,8 +32,9 @@ def _rng(seed: int, stream: int = 0) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64([SEED_BASE + int(seed), int(stream)]))
 
 
-def uniform_points(n: int, seed: int, L: float = 1.0, x0=(0.0, 0.0, 0.0)) -> np.ndarray:
-    """n points iid uniform in the half-open cube [x0, x0+L)^3, float64 (n, 3)."""
+def uniform_points(n: int, seed: int, L=1.0, x0=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """n points iid uniform in the half-open box [x0, x0+L), float64 (n, 3);
+    L is one side (a cube) or three sides (Lx, Ly, Lz)."""
     x = _rng(seed, 1).random((n, 3)) * L + np.asarray(x0, dtype=np.float64)
     # random() is in [0, 1); scaling can round up to exactly x0+L, keep it half-open
     top = np.nextafter(np.asarray(x0, dtype=np.float64) + L, -np.inf)
