@@ -36,7 +36,7 @@ FLOP_PER_PAIR = 58
 # DRAM bytes (read + write) of one launch of the FP32 stokeslet real-space kernel on
 # this workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 # Set to None whenever that kernel changes, until it is captured again.
-REAL_TRAFFIC_BYTES = 67_270_656 + 3_860_992
+REAL_TRAFFIC_BYTES = 67_404_800 + 3_914_752
 
 
 def pair_fraction_unit_cube(r: float) -> float:
@@ -363,7 +363,7 @@ def run_ours(args, rank, world, dist):
         "stages_ms": stages,
         "stage_algorithmic_gbs": stage_gbs,
         "stage_roofline": stage_roofline,
-        "roofline": {"bound": "alu", "kernel": "k_real_sym (real-space pair sum, each pair once)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_real_symc (real-space pair sum, each pair once)", "achieved": achieved,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": REAL_TRAFFIC_BYTES,
                      "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                      "pairs_per_launch": pairs, "flop_per_pair": FLOP_PER_PAIR},

@@ -632,6 +632,271 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
     }
 }
 
+// FP32, one system, one right-hand side, each pair within the cutoff once,
+// with the lanes transposed relative to k_real_sym: a warp owns a cluster of up
+// to TC = 8 consecutive targets, held in shared memory and read as broadcasts,
+// and each lane evaluates one candidate against all TC targets in turn.  The
+// candidate stream is the one of k_real_sym (rows at or after the cluster's row,
+// the own row from the cluster's first point on).  Each streamed candidate is
+// first tested against the bounding box of the cluster's targets (farther than
+// rc from the box means farther than rc from every target; the box test rounds
+// the same way as the pair test, so it never drops a pair), and the survivors
+// are queued in shared memory with their stream position.  Each queue of 32 is
+// evaluated one candidate per lane:
+//   u_t += K^R(x_t - x_m) . s_m   in TC x 3 register accumulators per lane,
+//                                  summed over the lanes once per cluster, and
+//   u_m += sign K^R(x_t - x_m) . s_t  in 3 registers, added to uj with one
+//                                  vector atomic per candidate (sign -1 for the
+//                                  odd stresslet and rotlet).
+// A pair counts when the candidate's stream position exceeds the target's slot
+// (positions below the cluster's size are the cluster's own points).
+#ifndef SE_RS_SYMC_MINB
+#define SE_RS_SYMC_MINB 4
+#endif
+template <int KERNEL, int PV>
+__global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
+    k_real_symc(GP<float> g, RC<float> rk, const float4 *__restrict__ xs, const float4 *__restrict__ fs,
+                const float4 *__restrict__ qs, const int *__restrict__ cell_start, const int2 *__restrict__ clusters,
+                const int *__restrict__ ncl_total, const int *__restrict__ perm, float *__restrict__ u,
+                float *__restrict__ uj, int *__restrict__ status) {
+    constexpr int WPB = 8, TC = 8, QN = 64;
+    constexpr bool STR = (KERNEL == SE_STRESSLET);
+    __shared__ float4 tx_all[WPB][TC];
+    __shared__ float4 tf_all[WPB][TC];
+    __shared__ float4 tq_all[STR ? WPB : 1][TC];
+    __shared__ float4 qx_all[WPB][QN];
+    __shared__ float4 qf_all[WPB][QN];
+    __shared__ float4 qq_all[STR ? WPB : 1][QN];
+    __shared__ int qm_all[WPB][QN];
+    __shared__ int2 seg_all[WPB][MAXROWS];
+    __shared__ int pre_all[WPB][MAXROWS + 1];
+    __shared__ float box_all[WPB][6];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * WPB + wib;
+    if (c >= *ncl_total) return;
+    float4 *tx = tx_all[wib], *tf = tf_all[wib], *tq = tq_all[STR ? wib : 0];
+    float *box = box_all[wib];
+    float4 *qx = qx_all[wib], *qf = qf_all[wib], *qq = qq_all[STR ? wib : 0];
+    int *qm = qm_all[wib];
+    int2 *seg = seg_all[wib];
+    int *pre = pre_all[wib];
+    const int2 cl = clusters[c];
+    const float INF = __int_as_float(0x7f800000);
+    // the cluster's targets (slots beyond its size at infinity: no pair) and
+    // their bounding box
+    float blo[3] = {INF, INF, INF}, bhi[3] = {-INF, -INF, -INF};
+    if (lane < TC) {
+        float4 xo = make_float4(INF, INF, INF, 0.f), fo = make_float4(0.f, 0.f, 0.f, 0.f), qo = fo;
+        if (lane < cl.y) {
+            xo = xs[cl.x + lane];
+            fo = fs[cl.x + lane];
+            if (STR) qo = qs[cl.x + lane];
+            blo[0] = bhi[0] = xo.x;
+            blo[1] = bhi[1] = xo.y;
+            blo[2] = bhi[2] = xo.z;
+        }
+        tx[lane] = xo;
+        tf[lane] = fo;
+        if (STR) tq[lane] = qo;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            blo[d] = fminf(blo[d], __shfl_xor_sync(FULL, blo[d], o));
+            bhi[d] = fmaxf(bhi[d], __shfl_xor_sync(FULL, bhi[d], o));
+        }
+        if (lane == 0) {
+            box[d] = blo[d];
+            box[3 + d] = bhi[d];
+        }
+    }
+    int c0[3], c1[3];
+    unpack3(get_tag(xs[cl.x]), c0[0], c0[1], c0[2]);
+    unpack3(get_tag(xs[cl.x + cl.y - 1]), c1[0], c1[1], c1[2]);
+    const int Ry = rk.reach[0], Rz = rk.reach[1], Wy = 2 * Ry + 1, nrows = Wy * (2 * Rz + 1);
+    const float rc2m = rk.rc2 * 1.0001f;
+    const int own_row = c0[2] * g.ncel[1] + c0[1];
+    for (int r = lane; r < nrows; r += 32) {
+        const int dyc = (r % Wy) - Ry, dzc = (r / Wy) - Rz;
+        const int iy = c0[1] + dyc, iz = c0[2] + dzc;
+        int2 sg = make_int2(0, 0);
+        const int row = iz * g.ncel[1] + iy;
+        if (iy >= 0 && iy < g.ncel[1] && iz >= 0 && iz < g.ncel[2] && row >= own_row) {
+            const float dy = float(max(abs(dyc) - 1, 0)) * g.cw[1], dz = float(max(abs(dzc) - 1, 0)) * g.cw[2];
+            const float d2 = dy * dy + dz * dz;
+            if (d2 <= rc2m) {
+                const float del = sqrtf(rc2m - d2) + 1e-4f * g.cw[0];
+                const int ixl = max(0, (int)floorf((float(c0[0]) * g.cw[0] - del) * g.icw[0]));
+                const int ixh = min(g.ncel[0] - 1, (int)floorf((float(c1[0] + 1) * g.cw[0] + del) * g.icw[0]));
+                if (ixl <= ixh) {
+                    const int base = row * g.ncel[0];
+                    sg = make_int2(cell_start[base + ixl], cell_start[base + ixh + 1]);
+                    if (row == own_row) sg.x = cl.x;
+                }
+            }
+        }
+        seg[r] = sg;
+    }
+    __syncwarp();
+    int run = 0;
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+        const int r = r0 + lane;
+        const int len = (r < nrows) ? seg[r].y - seg[r].x : 0;
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (r < nrows) pre[r] = run + incl - len;
+        run += __shfl_sync(FULL, incl, 31);
+    }
+    if (lane == 0) pre[nrows] = run;
+    __syncwarp();
+    const int total = run;
+    float acc[TC][3];
+#pragma unroll
+    for (int t = 0; t < TC; t++) acc[t][0] = acc[t][1] = acc[t][2] = 0.f;
+    bool coinc = false;
+    int lo = 0, fill = 0, cb = 0;
+    while (true) {
+        // queue candidates until 32 wait or the stream ends
+        while (fill < 32 && cb < total) {
+            const int v = cb + lane;
+            bool keep = false;
+            int m = 0;
+            float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (v < total) {
+                while (pre[lo + 1] <= v) lo++;
+                m = seg[lo].x + (v - pre[lo]);
+                xm = xs[m];
+                const float ex = fmaxf(fmaxf(box[0] - xm.x, xm.x - box[3]), 0.f);
+                const float ey = fmaxf(fmaxf(box[1] - xm.y, xm.y - box[4]), 0.f);
+                const float ez = fmaxf(fmaxf(box[2] - xm.z, xm.z - box[5]), 0.f);
+                keep = ex * ex + ey * ey + ez * ez <= rc2m;
+            }
+            const unsigned bal = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int pos = fill + __popc(bal & ((1u << lane) - 1u));
+                xm.w = __int_as_float(min(v, TC));  // the stream position, capped
+                qx[pos] = xm;
+                qf[pos] = fs[m];
+                if (STR) qq[pos] = qs[m];
+                qm[pos] = m;
+            }
+            fill += __popc(bal);
+            cb += 32;
+        }
+        if (fill == 0) break;
+        __syncwarp();
+        const int nq = min(fill, 32);
+        {
+            const bool valid = lane < nq;
+            float4 xj = make_float4(INF, INF, INF, 0.f);
+            float4 fj = make_float4(0.f, 0.f, 0.f, 0.f), qj = fj;
+            int vs = 0, mj = 0;
+            if (valid) {
+                xj = qx[lane];
+                fj = qf[lane];
+                if (STR) qj = qq[lane];
+                vs = __float_as_int(xj.w);
+                mj = qm[lane];
+            }
+            float cj[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int t = 0; t < TC; t++) {
+                const float4 xt = tx[t];
+                const float dx = xt.x - xj.x, dy = xt.y - xj.y, dz = xt.z - xj.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 <= rk.rc2 && t < vs) {
+                    if (r2 > 0.f) {
+                        float rinv, a, b;
+                        radial_ab<KERNEL, PV>(rk, r2, rinv, a, b);
+                        const float4 ft = tf[t];
+                        if (KERNEL == SE_STOKESLET) {
+                            const float bj = b * (dx * fj.x + dy * fj.y + dz * fj.z);
+                            acc[t][0] += a * fj.x + bj * dx;
+                            acc[t][1] += a * fj.y + bj * dy;
+                            acc[t][2] += a * fj.z + bj * dz;
+                            const float bt = b * (dx * ft.x + dy * ft.y + dz * ft.z);
+                            cj[0] += a * ft.x + bt * dx;
+                            cj[1] += a * ft.y + bt * dy;
+                            cj[2] += a * ft.z + bt * dz;
+                        } else if (KERNEL == SE_ROTLET) {
+                            acc[t][0] += b * (fj.y * dz - fj.z * dy);
+                            acc[t][1] += b * (fj.z * dx - fj.x * dz);
+                            acc[t][2] += b * (fj.x * dy - fj.y * dx);
+                            cj[0] -= b * (ft.y * dz - ft.z * dy);
+                            cj[1] -= b * (ft.z * dx - ft.x * dz);
+                            cj[2] -= b * (ft.x * dy - ft.y * dx);
+                        } else {
+                            const float4 qt = tq[t];
+                            const float hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
+                            {
+                                const float hf = hx * fj.x + hy * fj.y + hz * fj.z;
+                                const float hq = hx * qj.x + hy * qj.y + hz * qj.z;
+                                const float fq = fj.x * qj.x + fj.y * qj.y + fj.z * qj.z;
+                                const float a1 = a * hf * hq;
+                                acc[t][0] += a1 * hx + b * (hx * fq + fj.x * hq + qj.x * hf);
+                                acc[t][1] += a1 * hy + b * (hy * fq + fj.y * hq + qj.y * hf);
+                                acc[t][2] += a1 * hz + b * (hz * fq + fj.z * hq + qj.z * hf);
+                            }
+                            {
+                                const float hf = hx * ft.x + hy * ft.y + hz * ft.z;
+                                const float hq = hx * qt.x + hy * qt.y + hz * qt.z;
+                                const float fq = ft.x * qt.x + ft.y * qt.y + ft.z * qt.z;
+                                const float a1 = a * hf * hq;
+                                cj[0] -= a1 * hx + b * (hx * fq + ft.x * hq + qt.x * hf);
+                                cj[1] -= a1 * hy + b * (hy * fq + ft.y * hq + qt.y * hf);
+                                cj[2] -= a1 * hz + b * (hz * fq + ft.z * hq + qt.z * hf);
+                            }
+                        }
+                    } else {
+                        coinc = true;  // a distinct point at the same position
+                    }
+                }
+            }
+            if (valid && (cj[0] != 0.f || cj[1] != 0.f || cj[2] != 0.f))
+                atomicAdd(reinterpret_cast<float4 *>(uj + 4 * (size_t)mj), make_float4(cj[0], cj[1], cj[2], 0.f));
+        }
+        __syncwarp();
+        // keep the queue's tail
+        if (lane < fill - nq) {
+            qx[lane] = qx[nq + lane];
+            qf[lane] = qf[nq + lane];
+            if (STR) qq[lane] = qq[nq + lane];
+            qm[lane] = qm[nq + lane];
+        }
+        fill -= nq;
+        __syncwarp();
+    }
+    // sum the accumulators over the lanes: a reduce-scatter over lane bits 4,
+    // 3, 2 leaves lane l with the 3 components of target ((l >> 2) & 7) summed
+    // over 8 lanes, then butterflies over bits 1, 0 finish the sums
+    float* a = &acc[0][0];
+#pragma unroll
+    for (int h = 16, len = 3 * TC; h >= 4; h >>= 1, len >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < len / 2; i++) {
+            const float send = up ? a[i] : a[i + len / 2];
+            const float keep = up ? a[i + len / 2] : a[i];
+            a[i] = keep + __shfl_xor_sync(FULL, send, h);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        a[d] += __shfl_xor_sync(FULL, a[d], 2);
+        a[d] += __shfl_xor_sync(FULL, a[d], 1);
+    }
+    if (__any_sync(FULL, coinc) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
+    const int tt = (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && tt < cl.y) {
+        const int mi = perm[cl.x + tt];
+        for (int d = 0; d < 3; d++) u[3 * mi + d] = (float)((double)u[3 * mi + d] + (double)a[d]);
+    }
+}
+
 // u[perm[n]] += uj[n] (the contributions scattered to the candidates)
 template <typename T>
 __global__ void k_add_uj(int N, const T *__restrict__ uj, const int *__restrict__ perm, T *__restrict__ u) {
@@ -962,6 +1227,9 @@ inline int real_pv(double xi_rc) { return xi_rc <= 5.0 ? 1 : 0; }
 #ifndef SE_RS_SYM
 #define SE_RS_SYM 1
 #endif
+#ifndef SE_RS_SYMC
+#define SE_RS_SYMC 1
+#endif
 #ifndef SE_RS_SYM_TPW
 #define SE_RS_SYM_TPW 8
 #endif
@@ -988,7 +1256,9 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
     }
     const bool sym = p->b.uj && SE_RS_SYM;
     // targets per cluster: the symmetric kernel's or the full-list kernel's
-    constexpr int TPW = SE_RS_TPW, TPWS = sizeof(T) == 4 ? SE_RS_SYM_TPW : SE_RS_SYM_TPW64;
+    // (FP32 runs the transposed symmetric kernel, clusters of 8 targets)
+    constexpr bool symc = sizeof(T) == 4 && SE_RS_SYMC;
+    constexpr int TPW = SE_RS_TPW, TPWS = symc ? 8 : sizeof(T) == 4 ? SE_RS_SYM_TPW : SE_RS_SYM_TPW64;
     const int tpw = sym ? TPWS : TPW;
     const int nrows = p->geom.ncel[1] * p->geom.ncel[2];
     k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], tpw, p->b.cnt_r, p->b.ncl);
@@ -1003,7 +1273,17 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
         if (e) return e;
         if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
         T *ujt = (T *)p->b.uj;
-        if (real_pv(p->xi * p->rc) == 1)
+        if constexpr (symc) {
+            const float4 *xf = (const float4 *)xs, *ff = (const float4 *)fs, *qf = (const float4 *)qs;
+            if (real_pv(p->xi * p->rc) == 1)
+                k_real_symc<KERNEL, 1><<<nblk, 256, 0, st>>>(p->gpf, rk, xf, ff, qf, p->b.cnt_r, p->b.clusters,
+                                                             p->b.ncl + nrows, p->b.perm_r, (float *)u,
+                                                             (float *)ujt, p->b.status);
+            else
+                k_real_symc<KERNEL, 0><<<nblk, 256, 0, st>>>(p->gpf, rk, xf, ff, qf, p->b.cnt_r, p->b.clusters,
+                                                             p->b.ncl + nrows, p->b.perm_r, (float *)u,
+                                                             (float *)ujt, p->b.status);
+        } else if (real_pv(p->xi * p->rc) == 1)
             k_real_sym<T, KERNEL, 1, TPWS><<<nblk, 256, 0, st>>>(g, rk, xs, fs, qs, p->b.cnt_r, p->b.clusters,
                                                                 p->b.ncl + nrows, p->b.perm_r, u, ujt, p->b.status);
         else
