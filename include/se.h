@@ -100,6 +100,26 @@ se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const doubl
 se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double xi, const double box[6], double tol,
                                se_prec_t prec, const se_params_t *params, se_plan_t *plan_out);
 
+/* A plan for the triply periodic sums in the cube box = (x0, y0, z0, L): u(x_m)
+ * = sum over n and over all periodic images of K(x_m - x_n + p L) . f_n (the
+ * n = m term of the unshifted image excluded), split as the free-space sum
+ * (Section 3, Table 1) with the Fourier part summed over k = 2 pi j / L, j !=
+ * 0 (the periodic problem of Section 1.1; the k = 0 term is left out, i.e. the
+ * mean force is balanced by a mean pressure gradient, Hasimoto's convention).
+ * The Fourier part runs on the unpadded periodic M^3 grid with the exact
+ * transforms 4 pi/k^2 and -8 pi/k^4 in place of the precomputed truncated
+ * ones (no precomputation); the real-space part takes nearest images.
+ * Arguments as for se_plan_create.  Parameters are selected as for the
+ * free-space cube, then M is rounded up to an even FFT-friendly size and xi is
+ * raised until rc < L/2 (an explicit params->rc must satisfy rc < L/2 and an
+ * explicit params->M must be even: SE_ERR_INVALID_ARG otherwise).  Points must
+ * lie in the half-open box (SE_ERR_OUT_OF_BOX from se_plan_check otherwise).
+ * Supported calls on such a plan: se_eval, se_eval_host, se_eval_real_space,
+ * the status, timing and parameter queries; se_eval_targets and the backward
+ * calls return SE_ERR_NOT_SUPPORTED. */
+se_status_t se_plan_create_periodic(se_kernel_t kernel, int64_t N, double xi, const double box[4], double tol,
+                                    se_prec_t prec, const se_params_t *params, se_plan_t *plan_out);
+
 /* u = sum_{n != m} K(x_m - x_n) . f_n at every point (Section 8).
  *   x  N x 3 device positions; f N x 3 device strengths (forces, dipoles or torques)
  *   q  N x 3 device second source vector for the stresslet (u_j = T_jlm f_l q_m), else NULL
@@ -231,7 +251,8 @@ se_status_t se_choose_params(se_kernel_t kernel, se_prec_t prec, int64_t N, doub
 se_status_t se_plan_get_params(se_plan_t plan, se_params_t *out);
 
 /* Grid sizes per dimension (x, y, z): M (box), Mtilde (extended grid), the FFT
- * size 2 Mtilde and the precompute grid; any pointer may be NULL. */
+ * size (2 Mtilde; M for a periodic plan) and the precompute grid (0 for a
+ * periodic plan); any pointer may be NULL. */
 se_status_t se_plan_get_grid(se_plan_t plan, int M[3], int Mtilde[3], int Mf[3], int Mg[3]);
 
 /* Synchronise the stream of the plan's last call and return (and clear) the

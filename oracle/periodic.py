@@ -79,10 +79,12 @@ def multiply(kid: int, k: tuple, S: np.ndarray, xi: float) -> np.ndarray:
     return W
 
 
-def fourier_part(kernel, x, f, q, L: float, xi: float, chunk: int = 4096) -> np.ndarray:
-    """(1/L^3) sum_{k != 0} A(k) e^{-k^2/4xi^2} . sum_n s_n e^{i k.(x_m - x_n)}."""
+def fourier_part(kernel, x, f, q, L: float, xi: float, chunk: int = 4096, targets=None) -> np.ndarray:
+    """(1/L^3) sum_{k != 0} A(k) e^{-k^2/4xi^2} . sum_n s_n e^{i k.(x_m - x_n)} at the
+    targets m (indices into x; default all)."""
     kid = _kid(kernel)
     x, f = f64(x), f64(f)
+    xm = x if targets is None else x[np.asarray(targets, dtype=np.int64)]
     s = sources(kid, f, f64(q) if q is not None else None)
     kmax = 2.0 * xi * math.sqrt(math.log(1e17))
     jmax = int(math.ceil(kmax * L / (2.0 * math.pi)))
@@ -91,29 +93,31 @@ def fourier_part(kernel, x, f, q, L: float, xi: float, chunk: int = 4096) -> np.
     J = J[np.any(J != 0, axis=1)]
     kk = 2.0 * math.pi / L * J.astype(np.float64)
     kk = kk[np.einsum("ij,ij->i", kk, kk) <= kmax * kmax]
-    u = np.zeros((len(x), 3))
+    u = np.zeros((len(xm), 3))
     for c0 in range(0, len(kk), chunk):
         kc = kk[c0:c0 + chunk]
         ph = np.exp(-1j * (x @ kc.T))                     # (N, nk): e^{-i k.x_n}
         S = s.T @ ph                                      # (ncomp, nk)
         W = multiply(kid, (kc[:, 0], kc[:, 1], kc[:, 2]), S, xi)
-        u += np.real(np.conj(ph) @ W.T)                   # sum_k W(k) e^{i k.x_m}
+        pm = ph if targets is None else np.exp(-1j * (xm @ kc.T))
+        u += np.real(np.conj(pm) @ W.T)                   # sum_k W(k) e^{i k.x_m}
     return u / L**3
 
 
-def real_part(kernel, x, f, q, L: float, xi: float, rc: float) -> np.ndarray:
+def real_part(kernel, x, f, q, L: float, xi: float, rc: float, targets=None) -> np.ndarray:
     """Sum over all images within rc of the screened kernel K^R (Section 6), n = m
-    excluded for the unshifted image."""
+    excluded for the unshifted image, at the targets m (indices; default all)."""
     kid = _kid(kernel)
     if not rc < L:
         raise ValueError("rc must be below L")
     x, f = f64(x), f64(f)
     q = f64(q) if q is not None else None
     N = len(x)
-    u = np.zeros((N, 3))
-    mi, ni = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    tid = np.arange(N) if targets is None else np.asarray(targets, dtype=np.int64)
+    u = np.zeros((len(tid), 3))
+    mi, ni = np.meshgrid(np.arange(len(tid)), np.arange(N), indexing="ij")
     mi, ni = mi.ravel(), ni.ravel()
-    base = x[mi] - x[ni]
+    base = x[tid[mi]] - x[ni]
     for sx in (-1, 0, 1):
         for sy in (-1, 0, 1):
             for sz in (-1, 0, 1):
@@ -121,7 +125,7 @@ def real_part(kernel, x, f, q, L: float, xi: float, rc: float) -> np.ndarray:
                 r2 = np.einsum("ij,ij->i", r, r)
                 keep = (r2 <= rc * rc) & (r2 > 0.0)
                 if sx == 0 and sy == 0 and sz == 0:
-                    keep &= mi != ni
+                    keep &= tid[mi] != ni
                 if not keep.any():
                     continue
                 rk = np.ascontiguousarray(r[keep])
@@ -137,12 +141,14 @@ def real_part(kernel, x, f, q, L: float, xi: float, rc: float) -> np.ndarray:
     return u
 
 
-def ewald(kernel, x, f, q=None, *, L: float = 1.0, xi: float, rc: float, parts: bool = False):
-    """The periodic sum at every point: real-space + Fourier + self parts."""
+def ewald(kernel, x, f, q=None, *, L: float = 1.0, xi: float, rc: float, parts: bool = False, targets=None):
+    """The periodic sum at every point (or at the points with indices ``targets``):
+    real-space + Fourier + self parts."""
     kid = _kid(kernel)
-    uR = real_part(kid, x, f, q, L, xi, rc)
-    uF = fourier_part(kid, x, f, q, L, xi)
-    uS = greens.self_coefficient(kid, xi) * f64(f) if kid == STOKESLET else np.zeros_like(uF)
+    uR = real_part(kid, x, f, q, L, xi, rc, targets=targets)
+    uF = fourier_part(kid, x, f, q, L, xi, targets=targets)
+    fm = f64(f) if targets is None else f64(f)[np.asarray(targets, dtype=np.int64)]
+    uS = greens.self_coefficient(kid, xi) * fm if kid == STOKESLET else np.zeros_like(uF)
     if parts:
         return {"R": uR, "F": uF, "self": uS}
     return uR + uF + uS

@@ -68,15 +68,18 @@ struct StageTimer {
 template <typename T>
 se_status_t fourier_grid(se_plan_s *p, cudaStream_t st, void *wout, int nc, StageTimer *tm) {
     CK(launch_spread<T>(p, st, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->grid, nc));
+    // periodic plans: the halo of the extended grid folded onto the periodic grid
+    if (p->periodic) CK(launch_fold<T>(p, st, p->grid, p->pgrid, nc));
     if (tm) tm->mark();
     cufftHandle fwd = (nc == p->nc) ? p->fwd : p->fwd3;
     CF(cufftSetStream(fwd, st));
-    CF(exec_fwd<T>(fwd, p->grid, p->spec));
+    CF(exec_fwd<T>(fwd, p->periodic ? p->pgrid : p->grid, p->spec));
     if (tm) tm->mark();
     CK(launch_scale<T>(p, st, p->spec, 0));
     if (tm) tm->mark();
     CF(cufftSetStream(p->inv, st));
-    CF(exec_inv<T>(p->inv, p->spec, wout));
+    CF(exec_inv<T>(p->inv, p->spec, p->periodic ? p->pgrid : wout));
+    if (p->periodic) CK(launch_unfold<T>(p, st, p->pgrid, wout, 3));
     if (tm) tm->mark();
     return SE_OK;
 }
@@ -228,6 +231,7 @@ extern "C" se_status_t se_eval_targets(se_plan_t p, const void *x, const void *f
     if (!p || !x || !f || !xt || !ut) return fail(SE_ERR_INVALID_ARG, "se_eval_targets: NULL pointer");
     if (p->kernel == SE_STRESSLET && !q) return fail(SE_ERR_INVALID_ARG, "se_eval_targets: the stresslet needs q");
     if (Nt < 1 || Nt > (int64_t)INT32_MAX / 4) return fail(SE_ERR_INVALID_ARG, "se_eval_targets: Nt out of range");
+    if (p->periodic) return fail(SE_ERR_NOT_SUPPORTED, "se_eval_targets: not available for periodic plans");
     se_status_t s = ensure_targets(p, Nt);
     if (s != SE_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
@@ -269,6 +273,7 @@ extern "C" se_status_t se_eval_backward_q(se_plan_t p, const void *x, const void
     if (p->kernel != SE_STRESSLET && grad_q)
         return fail(SE_ERR_INVALID_ARG, "se_eval_backward: grad_q is for the stresslet only");
     if (!grad_f && !grad_q && !grad_x) return SE_OK;
+    if (p->periodic) return fail(SE_ERR_NOT_SUPPORTED, "se_eval_backward: not available for periodic plans");
     cudaStream_t st = (cudaStream_t)stream;
     if (p->prec == SE_FP32)
         return backward_t<float>(p, (const float *)x, (const float *)f, (const float *)q, (const float *)grad_u,

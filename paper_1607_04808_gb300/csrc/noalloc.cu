@@ -135,6 +135,7 @@ extern "C" se_status_t se_real_space_noalloc(se_kernel_t kernel, se_prec_t prec,
             G.x0[d] = (TT)box[d];
             G.len[d] = (TT)L;
             G.icw[d] = (TT)g.icw[d];
+            G.ilen[d] = (TT)(1.0 / L);
             G.cw[d] = (TT)g.cw[d];
             G.mt[d] = 2;
             G.mf[d] = 4;

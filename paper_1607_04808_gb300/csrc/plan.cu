@@ -187,7 +187,7 @@ void free_plan(se_plan_s *p) {
     void *ptrs[] = {p->b.uj, p->b.ncl, p->b.clusters, p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
                     p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
                     p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
-                    p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du};
+                    p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du, p->pgrid};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     void *tptrs[] = {p->bt.xs_t, p->bt.perm_t, p->bt.slot_t, p->bt.key_t, p->bt.tag_t, p->bt.cnt_t, p->bt.xs_r,
@@ -207,7 +207,7 @@ static cudaError_t dmalloc(P_ **ptr, size_t bytes) {
 
 // Parameters, grid sizes and geometry of a plan (no device work).
 se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[6],
-                           const se_params_t &pr) {
+                           const se_params_t &pr, bool periodic) {
     p->kernel = kernel;
     p->prec = prec;
     p->N = N;
@@ -232,6 +232,15 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
     if (p->deltaL_policy == 1 && p->eta < 1.0)
         need = std::max(d, sqrt(2.0 * (1.0 - p->eta) * p->m * p->m / (p->xi * p->xi)));
     p->n_ext = (int)ceil(need / p->h - 1e-9);
+    p->periodic = periodic;
+    if (periodic) {
+        // a halo of P points (rounded up to even, so that the extended grid
+        // points fall on the periodic ones) holds every point's support; the
+        // fold wraps it once, so it may not exceed the grid
+        p->n_ext = p->P + (p->P & 1);
+        p->mp = pr.M;
+        if (p->n_ext > 2 * p->mp) return fail(SE_ERR_INVALID_ARG, "periodic plan: P above 2 M");
+    }
     p->deltaL = p->n_ext * p->h;
     double r2 = 0;
     for (int dd = 0; dd < 3; dd++) {
@@ -241,9 +250,11 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
         int M = (p->len[dd] == lmax) ? pr.M : (int)ceil(p->len[dd] / p->h - 1e-9);
         if (p->len[dd] != lmax)
             while (!good_fft(2 * (M + p->n_ext), prec)) M++;
+        if (periodic) M = pr.M;
         p->mm[dd] = M;
         p->mt[dd] = M + p->n_ext;
-        p->mf[dd] = 2 * p->mt[dd];
+        // the periodic plan's spreading grid is the extended grid itself
+        p->mf[dd] = periodic ? p->mt[dd] : 2 * p->mt[dd];
         r2 += (p->mt[dd] * p->h) * (p->mt[dd] * p->h);
     }
     // truncation radius: the diagonal of the extended box (Section 4.1;
@@ -253,16 +264,17 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
     // (1 + R / Ltilde_d) mt_d, the oversampling of Section 4.2 ((1 + sqrt 3) mt
     // for a cube, Section 9), rounded up to a length with prime factors 2, 3, 5,
     // 7 (a larger oversampling factor is still valid and avoids cuFFT's slow path)
-    for (int dd = 0; dd < 3; dd++) {
+    for (int dd = 0; dd < 3 && !periodic; dd++) {
         const double sf = 1.0 + p->R / (p->mt[dd] * p->h);
         int Mg = 2 * (int)floor(sf * p->mt[dd] / 2.0) + 2;
         while (!good_fft(Mg, SE_FP64) || (Mg & 1)) Mg++;
         p->mg[dd] = Mg;
     }
+    if (periodic) p->R = 0;
     p->nc = (kernel == SE_STRESSLET) ? 6 : 3;
     for (int dd = 0; dd < 3; dd++) {
-        if (p->max_fft > 0 && p->mf[dd] > p->max_fft)
-            return fail(SE_ERR_INVALID_ARG, "FFT size 2*Mtilde exceeds max_fft");
+        if (p->max_fft > 0 && (periodic ? p->mp : p->mf[dd]) > p->max_fft)
+            return fail(SE_ERR_INVALID_ARG, "FFT size exceeds max_fft");
         if (p->mt[dd] > 1023) return fail(SE_ERR_INVALID_ARG, "extended grid above 1023 points per dimension");
     }
     // geometry
@@ -334,6 +346,7 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
             G.x0[dd] = (TT)p->x0[dd];
             G.len[dd] = (TT)p->len[dd];
             G.icw[dd] = (TT)g.icw[dd];
+            G.ilen[dd] = (TT)(1.0 / p->len[dd]);
             G.cw[dd] = (TT)g.cw[dd];
             G.mt[dd] = g.mt[dd];
             G.mf[dd] = g.mf[dd];
@@ -369,9 +382,39 @@ extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, 
     return se_plan_create_box(kernel, N, xi, b6, tol, prec, params, plan_out);
 }
 
-extern "C" se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double xi, const double box[6],
-                                          double tol, se_prec_t prec, const se_params_t *params,
-                                          se_plan_t *plan_out) {
+// Parameters of a triply periodic plan in the cube of side L: the selection of
+// the free-space plan (the estimates of Tables 2 and 3 hold for the periodic
+// sums they were derived for), then M rounded up to an even FFT-friendly size
+// and, when the cutoff is not below L/2 (minimum images), xi raised until it is.
+static se_status_t choose_periodic_params(int kernel, int prec, int64_t N, double L, double tol,
+                                          const se_params_t *params, double xi, se_params_t *out) {
+    se_status_t s = choose_params(kernel, prec, N, L, tol, params, xi, out);
+    if (s != SE_OK) return s;
+    const bool fixed_rc = params && params->rc > 0;
+    for (int it = 0; it < 8 && !(out->rc < 0.5 * L); it++) {
+        if (fixed_rc) break;
+        se_params_t in;
+        memset(&in, 0, sizeof(in));
+        if (params) in = *params;
+        in.xi = 0;
+        in.M = 0;
+        s = choose_params(kernel, prec, N, L, tol, &in, out->xi * out->rc / (0.45 * L), out);
+        if (s != SE_OK) return s;
+    }
+    if (!(out->rc < 0.5 * L)) return fail(SE_ERR_INVALID_ARG, "periodic plan: rc must be below L/2");
+    int M = out->M;
+    if (params && params->M > 0) {
+        if (M & 1) return fail(SE_ERR_INVALID_ARG, "periodic plan: M must be even");
+    } else {
+        while ((M & 1) || !good_fft(M, prec)) M++;
+    }
+    out->M = M;
+    return SE_OK;
+}
+
+// Plan creation shared by the free-space and the periodic entry points.
+static se_status_t create_plan(se_kernel_t kernel, int64_t N, double xi, const double box[6], double tol,
+                               se_prec_t prec, const se_params_t *params, bool periodic, se_plan_t *plan_out) {
     if (!plan_out) return fail(SE_ERR_INVALID_ARG, "plan_out is NULL");
     *plan_out = nullptr;
     if (kernel < SE_STOKESLET || kernel > SE_ROTLET) return fail(SE_ERR_INVALID_ARG, "unknown kernel");
@@ -380,13 +423,14 @@ extern "C" se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double 
     if (!box || !(box[3] > 0) || !(box[4] > 0) || !(box[5] > 0))
         return fail(SE_ERR_INVALID_ARG, "box sides must be positive");
     se_params_t pr;
-    se_status_t s = choose_box_params(kernel, prec, N, box, tol, params, xi, &pr);
+    se_status_t s = periodic ? choose_periodic_params(kernel, prec, N, box[3], tol, params, xi, &pr)
+                             : choose_box_params(kernel, prec, N, box, tol, params, xi, &pr);
     if (s != SE_OK) return s;
     if (pr.P < 1 || pr.P > 32) return fail(SE_ERR_INVALID_ARG, "P must be in [1, 32]");
     if (pr.M < 1 || !(pr.xi > 0) || !(pr.rc > 0)) return fail(SE_ERR_INVALID_ARG, "invalid M, xi or rc");
 
     se_plan_s *p = new se_plan_s();
-    s = setup_plan(p, kernel, prec, N, box, pr);
+    s = setup_plan(p, kernel, prec, N, box, pr, periodic);
     if (s != SE_OK) {
         free_plan(p);
         return s;
@@ -396,8 +440,12 @@ extern "C" se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double 
     cudaError_t e = cudaSuccess;
     const size_t Nn = (size_t)N;
     const size_t Mf3 = (size_t)p->mf[0] * p->mf[1] * p->mf[2];
-    const size_t nk = (size_t)p->mf[2] * p->mf[1] * (p->mf[0] / 2 + 1);
-    const size_t O3 = (size_t)(p->mt[0] + 1) * (p->mt[1] + 1) * (p->mt[2] + 1);
+    // FFT sizes (z, y, x): the zero-padded 2 Mtilde, or the periodic M
+    const int fn[3] = {periodic ? p->mp : p->mf[2], periodic ? p->mp : p->mf[1], periodic ? p->mp : p->mf[0]};
+    const size_t nfft = (size_t)fn[0] * fn[1] * fn[2];
+    const size_t nk = (size_t)fn[0] * fn[1] * (fn[2] / 2 + 1);
+    const size_t O3 = periodic ? (size_t)(p->mp / 2 + 1) * (p->mp / 2 + 1) * (p->mp / 2 + 1)
+                               : (size_t)(p->mt[0] + 1) * (p->mt[1] + 1) * (p->mt[2] + 1);
     const size_t v4 = 4 * esz;
     int tile_keys = p->ntiles;
     do {
@@ -433,6 +481,7 @@ extern "C" se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double 
         if ((e = dmalloc(&p->b.status, 16))) break;
         if ((e = cudaMemset(p->grid, 0, (size_t)p->nc * Mf3 * esz))) break;
         if ((e = cudaMemset(p->b.status, 0, 16))) break;
+        if (periodic && (e = dmalloc(&p->pgrid, (size_t)p->nc * nfft * esz))) break;
     } while (0);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -442,10 +491,10 @@ extern "C" se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double 
     }
     // cuFFT plans: forward R2C batched over nc components, inverse C2R over 3
     {
-        int n[3] = {p->mf[2], p->mf[1], p->mf[0]};
+        int n[3] = {fn[0], fn[1], fn[2]};
         cufftType tf = (prec == SE_FP32) ? CUFFT_R2C : CUFFT_D2Z;
         cufftType ti = (prec == SE_FP32) ? CUFFT_C2R : CUFFT_Z2D;
-        int idist = (int)Mf3, odist = (int)nk;
+        int idist = (int)nfft, odist = (int)nk;
         if (cufftPlanMany(&p->fwd, 3, n, nullptr, 1, idist, nullptr, 1, odist, tf, p->nc) != CUFFT_SUCCESS) {
             free_plan(p);
             return fail(SE_ERR_CUFFT, "cufftPlanMany (forward) failed");
@@ -466,13 +515,27 @@ extern "C" se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double 
     }
     for (int i = 0; i < 9; i++) cudaEventCreate(&p->ev[i]);
     cudaEventCreate(&p->ev_real);
-    s = precompute(p);
+    s = periodic ? periodic_octant(p) : precompute(p);
     if (s != SE_OK) {
         free_plan(p);
         return s;
     }
     *plan_out = p;
     return SE_OK;
+}
+
+extern "C" se_status_t se_plan_create_box(se_kernel_t kernel, int64_t N, double xi, const double box[6],
+                                          double tol, se_prec_t prec, const se_params_t *params,
+                                          se_plan_t *plan_out) {
+    return create_plan(kernel, N, xi, box, tol, prec, params, false, plan_out);
+}
+
+extern "C" se_status_t se_plan_create_periodic(se_kernel_t kernel, int64_t N, double xi, const double box[4],
+                                               double tol, se_prec_t prec, const se_params_t *params,
+                                               se_plan_t *plan_out) {
+    if (!box) return fail(SE_ERR_INVALID_ARG, "box is NULL");
+    const double b6[6] = {box[0], box[1], box[2], box[3], box[3], box[3]};
+    return create_plan(kernel, N, xi, b6, tol, prec, params, true, plan_out);
 }
 
 extern "C" se_status_t se_choose_params(se_kernel_t kernel, se_prec_t prec, int64_t N, double L, double tol,
@@ -512,7 +575,7 @@ extern "C" se_status_t se_plan_get_grid(se_plan_t p, int M[3], int Mtilde[3], in
     for (int d = 0; d < 3; d++) {
         if (M) M[d] = p->mm[d];
         if (Mtilde) Mtilde[d] = p->mt[d];
-        if (Mf) Mf[d] = p->mf[d];
+        if (Mf) Mf[d] = p->periodic ? p->mp : p->mf[d];  // the FFT size
         if (Mg) Mg[d] = p->mg[d];
     }
     return SE_OK;

@@ -177,6 +177,54 @@ __device__ __forceinline__ int row_segments(const GP<T> &g, const RC<T> &rk, con
 // Clusters: each (y, z) row of cells is a contiguous range of sorted points;
 // it is cut into clusters of at most TPW consecutive points (never crossing a
 // row), so a cluster is compact (at most a few cells along x, one cell across).
+// Periodic plans (rc < L/2): the rows of cells within reach wrap around the
+// box in y and z, each row at most once (all rows once when the reach spans the
+// box, and then without pruning by the row's distance, which the unwrapped
+// index could overestimate); each row's x-range wraps into at most two
+// segments (the whole row once when it spans the box).  Two entries of seg per
+// row; the pair test takes the nearest image.
+template <typename T>
+__device__ __forceinline__ int row_segments_per(const GP<T> &g, const RC<T> &rk, const vec4<T> &xt,
+                                                const int *__restrict__ cell_start, int lane, int2 *seg) {
+    int cc[3];
+    unpack3(get_tag(xt), cc[0], cc[1], cc[2]);
+    const T rel[3] = {xt.x - g.x0[0], xt.y - g.x0[1], xt.z - g.x0[2]};
+    const T rc2m = rk.rc2 * T(1.0001);
+    const int ny = g.ncel[1], nz = g.ncel[2], nx = g.ncel[0];
+    const int Wy = min(2 * rk.reach[0] + 1, ny), Wz = min(2 * rk.reach[1] + 1, nz);
+    const int oy = (Wy - 1) / 2, oz = (Wz - 1) / 2, nrows = Wy * Wz;
+    for (int r = lane; r < nrows; r += 32) {
+        const int iyu = cc[1] + (r % Wy) - oy, izu = cc[2] + (r / Wy) - oz;  // unwrapped
+        const int iy = (iyu + ny) % ny, iz = (izu + nz) % nz;
+        int2 s0 = make_int2(0, 0), s1 = make_int2(0, 0);
+        const T ylo = iyu * g.cw[1], zlo = izu * g.cw[2];
+        const T dy = (Wy == ny) ? T(0) : max(T(0), max(ylo - rel[1], rel[1] - (ylo + g.cw[1])));
+        const T dz = (Wz == nz) ? T(0) : max(T(0), max(zlo - rel[2], rel[2] - (zlo + g.cw[2])));
+        const T d2 = dy * dy + dz * dz;
+        if (d2 <= rc2m) {
+            const T del = sqrt(rc2m - d2) + T(1e-4) * g.cw[0];
+            const int ixl = (int)floor((rel[0] - del) * g.icw[0]);
+            const int ixh = (int)floor((rel[0] + del) * g.icw[0]);
+            const int base = (iz * ny + iy) * nx;
+            if (ixh - ixl + 1 >= nx) {
+                s0 = make_int2(cell_start[base], cell_start[base + nx]);
+            } else {
+                const int a = ((ixl % nx) + nx) % nx, b = ((ixh % nx) + nx) % nx;
+                if (a <= b) {
+                    s0 = make_int2(cell_start[base + a], cell_start[base + b + 1]);
+                } else {
+                    s0 = make_int2(cell_start[base + a], cell_start[base + nx]);
+                    s1 = make_int2(cell_start[base], cell_start[base + b + 1]);
+                }
+            }
+        }
+        seg[2 * r] = s0;
+        seg[2 * r + 1] = s1;
+    }
+    __syncwarp();
+    return 2 * nrows;
+}
+
 __global__ void k_cluster_count(int nrows, int ncdx, int tpw, const int *__restrict__ cell_start, int *ncl) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
@@ -950,7 +998,8 @@ __global__ void k_bcluster_fill(int nrows_tot, const BSys<T> *__restrict__ sys, 
 //   u[p]  += gf_p = -sum_m T^R(x_p - x_m)(g_m, q_p),
 //   gq[p] += gq_p = -sum_m T^R(x_p - x_m)(g_m, f_p)
 // (T^R(x_m - x_p) = -T^R(x_p - x_m); T^R(r)(a, b)_j = T^R_jlk a_l b_k).
-template <typename T, int KERNEL, bool ADJ = false>
+// PER: periodic plan, nearest images (rc < L/2).
+template <typename T, int KERNEL, bool ADJ = false, bool PER = false>
 __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, const vec4<T> *__restrict__ xs,
                                                   const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
                                                   const int *__restrict__ cell_start, const int *__restrict__ perm,
@@ -960,7 +1009,7 @@ __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, cons
     constexpr int WPB = 8;
     __shared__ vec4<T> qd_all[WPB][QCAP];
     __shared__ int qn_all[WPB][QCAP];
-    __shared__ int2 seg_all[WPB][MAXROWS];
+    __shared__ int2 seg_all[WPB][PER ? 2 * MAXROWS : MAXROWS];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * WPB + wib;
     if (t >= N) return;
@@ -968,7 +1017,11 @@ __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, cons
     int *qn = qn_all[wib];
     int2 *seg = seg_all[wib];
     const vec4<T> xt = xs[t];
-    const int nrows = row_segments(g, rk, xt, cell_start, lane, seg);
+    int nrows;
+    if constexpr (PER)
+        nrows = row_segments_per(g, rk, xt, cell_start, lane, seg);
+    else
+        nrows = row_segments(g, rk, xt, cell_start, lane, seg);
     T acc[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
     int cnt = 0;
     bool coinc = false;
@@ -1003,6 +1056,11 @@ __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, cons
                 dx = xt.x - xv.x;
                 dy = xt.y - xv.y;
                 dz = xt.z - xv.z;
+                if constexpr (PER) {
+                    dx -= g.len[0] * rint(dx * g.ilen[0]);
+                    dy -= g.len[1] * rint(dy * g.ilen[1]);
+                    dz -= g.len[2] * rint(dz * g.ilen[2]);
+                }
                 r2 = dx * dx + dy * dy + dz * dz;
                 in = (r2 <= rk.rc2) && (n != t);
                 if (in && r2 == T(0)) {
@@ -1247,6 +1305,14 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r,
                   *qs = (const vec4<T> *)p->b.qs_r;
     const GP<T> &g = gp<T>(p);
+    if (p->periodic) {
+        // periodic plans: one warp per target over the wrapped rows, nearest images
+        if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
+        k_real_cmp<T, KERNEL, false, true><<<(N + 7) / 8, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r,
+                                                                      p->b.perm_r, u, p->b.status);
+        p->launches++;
+        return cudaGetLastError();
+    }
     if (sizeof(T) == 8 && !(p->b.uj && SE_RS_SYM)) {
         if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
         k_real_cmp<T, KERNEL><<<(N + 7) / 8, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, u,

@@ -185,6 +185,16 @@ ScaleConst make_scale_const(const se_plan_s *p) {
     sc.ecoef = -(1.0 - p->eta) / (4.0 * p->xi * p->xi);
     double pre = pow(2.0 * p->xi * p->xi / (M_PI * p->eta), 1.5);
     sc.norm = p->h * p->h * p->h / ((double)p->mf[0] * p->mf[1] * p->mf[2]) * pre * pre;
+    if (p->periodic) {
+        // the unpadded periodic grid M^3: k = 2 pi j / (M h), octant of M/2 + 1
+        for (int d = 0; d < 3; d++) {
+            sc.mt[d] = p->mp / 2;
+            sc.mf[d] = p->mp;
+            sc.dk[d] = 2.0 * M_PI / (p->mp * p->h);
+        }
+        sc.nxh = p->mp / 2 + 1;
+        sc.norm = p->h * p->h * p->h / ((double)p->mp * p->mp * p->mp) * pre * pre;
+    }
     return sc;
 }
 

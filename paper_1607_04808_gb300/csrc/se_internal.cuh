@@ -74,6 +74,7 @@ struct GP {
     T inv_h, half_ext; // t = (x - x0) / h + n_ext / 2 = (x - y0) / h (grid units)
     T ah2;             // a h^2 = 2 xi^2 h^2 / eta: Gaussian exponent per grid unit^2
     T icw[3], cw[3];   // real-space cell widths (x: along the rows) and inverses
+    T ilen[3];         // inverse box sides (minimum images of periodic plans)
     int P, T_;
     int mt[3], mf[3], nt[3], ncel[3];
 };
@@ -201,6 +202,12 @@ struct se_plan_s {
     int mf[3] = {0, 0, 0};  // FFT sizes 2 mt
     int mg[3] = {0, 0, 0};  // precompute grid
     int P = 0, n_ext = 0, deltaL_policy = 0, max_fft = 0;
+    // triply periodic plan: the sources are spread onto the extended grid
+    // (mt = M + n_ext points, no zero padding), folded onto the periodic M^3
+    // grid `pgrid` for the FFTs, and the inverse transform is unfolded back
+    bool periodic = false;
+    int mp = 0;               // periodic grid size M (even)
+    void *pgrid = nullptr;    // nc x M^3 real (FFT input, then the C2R output)
     int nc = 3;  // spread components (3; stresslet 6)
     se::Geom geom{};
     se::GP<float> gpf{};
@@ -242,7 +249,16 @@ namespace se {
 
 // Parameters, grid sizes and geometry of a plan from chosen parameters (host only).
 // box: x0, y0, z0, Lx, Ly, Lz
-se_status_t setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[6], const se_params_t &pr);
+se_status_t setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const double box[6], const se_params_t &pr,
+                       bool periodic = false);
+// Periodic plans: fold the extended spreading grid onto the periodic grid,
+// unfold the periodic grid onto the extended layout the gather reads, and
+// fill the octant of the exact transforms (4 pi / k^2 or -8 pi / k^4, zero at k = 0).
+template <typename T>
+cudaError_t launch_fold(se_plan_s *p, cudaStream_t st, const void *ext, void *per, int nc);
+template <typename T>
+cudaError_t launch_unfold(se_plan_s *p, cudaStream_t st, const void *per, void *ext, int nc);
+se_status_t periodic_octant(se_plan_s *p);
 
 // launchers (defined in the .cu files); all asynchronous on `st`
 template <typename T>

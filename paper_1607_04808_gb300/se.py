@@ -61,6 +61,9 @@ def lib():
             L.se_plan_create_box.restype = i32
             L.se_plan_create_box.argtypes = [i32, i64, dbl, ctypes.POINTER(ctypes.c_double), dbl, i32,
                                              ctypes.POINTER(SEParams), ctypes.POINTER(vp)]
+            L.se_plan_create_periodic.restype = i32
+            L.se_plan_create_periodic.argtypes = [i32, i64, dbl, ctypes.POINTER(ctypes.c_double), dbl, i32,
+                                                  ctypes.POINTER(SEParams), ctypes.POINTER(vp)]
             L.se_plan_get_grid.restype = i32
             L.se_plan_get_grid.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 4
             L.se_eval.restype = i32
@@ -134,23 +137,29 @@ def _stream(stream=None):
 class Plan:
     """A Spectral Ewald plan for N points in a box: box = (x0, y0, z0, L) for the
     cube [x0, x0+L) x [y0, y0+L) x [z0, z0+L) (se_plan_create), or
-    (x0, y0, z0, Lx, Ly, Lz) for a rectangular box (se_plan_create_box)."""
+    (x0, y0, z0, Lx, Ly, Lz) for a rectangular box (se_plan_create_box).
+    periodic=True: the triply periodic sums in the cube (x0, y0, z0, L)
+    (se_plan_create_periodic)."""
 
     def __init__(self, kernel: str, N: int, box=(0.0, 0.0, 0.0, 1.0), *, xi: float = 0.0,
                  tol: float = 0.0, prec: str = "fp32", M: int = 0, P: int = 0, rc: float = 0.0,
-                 deltaL_policy: int = 0, max_fft: int = 0):
+                 deltaL_policy: int = 0, max_fft: int = 0, periodic: bool = False):
         self.kernel = kernel
         self.kid = KERNELS[kernel]
         self.N = int(N)
         self.prec = prec
         self.dtype = torch.float32 if prec == "fp32" else torch.float64
         self.box = tuple(float(b) for b in box)
-        if len(self.box) not in (4, 6):
-            raise ValueError("box: (x0, y0, z0, L) or (x0, y0, z0, Lx, Ly, Lz)")
+        if len(self.box) not in (4, 6) or (periodic and len(self.box) != 4):
+            raise ValueError("box: (x0, y0, z0, L) or (x0, y0, z0, Lx, Ly, Lz); periodic plans take a cube")
+        self.periodic = bool(periodic)
         prm = SEParams(xi=float(xi), rc=float(rc), M=int(M), P=int(P),
                        deltaL_policy=int(deltaL_policy), max_fft=int(max_fft))
         boxa = (ctypes.c_double * len(self.box))(*self.box)
-        create = lib().se_plan_create if len(self.box) == 4 else lib().se_plan_create_box
+        if self.periodic:
+            create = lib().se_plan_create_periodic
+        else:
+            create = lib().se_plan_create if len(self.box) == 4 else lib().se_plan_create_box
         h = ctypes.c_void_p()
         _check(create(self.kid, self.N, float(xi), boxa, float(tol), PRECS[prec],
                       ctypes.byref(prm), ctypes.byref(h)))
