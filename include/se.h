@@ -267,6 +267,17 @@ se_status_t se_plan_check(se_plan_t plan);
 int se_plan_stage_times(se_plan_t plan, float *ms, int max_n);
 se_status_t se_plan_set_timing(se_plan_t plan, int on);
 
+/* Overlapped evaluation (FP32 free-space plans; on by default there): se_eval
+ * runs the Fourier part (spreading to gather) on an internal high-priority
+ * stream, forked from and joined back to the caller's stream, while the
+ * real-space sum runs on the caller's stream; the real-space sums are added
+ * to u after the join.  The call stays asynchronous on the caller's stream
+ * and may be captured into a CUDA graph.  With stage timing on, or with
+ * overlap off, the stages run one after another on the caller's stream.
+ * Returns SE_ERR_NOT_SUPPORTED when turning it on for a plan without it
+ * (FP64 and periodic plans). */
+se_status_t se_plan_set_overlap(se_plan_t plan, int on);
+
 /* Number of this library's kernels launched by the plan's last se_eval,
  * se_eval_host, se_eval_real_space or se_eval_backward call (cuFFT's kernels
  * and memsets are not counted; the count is taken on the host at launch).

@@ -88,6 +88,22 @@ template <typename T>
 se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaStream_t st) {
     p->last_stream = st;
     p->launches = 0;
+    if (p->overlap && !p->timing && p->s_four && real_can_defer(p)) {
+        // the Fourier part (spread ... gather, which writes u) on the internal
+        // high-priority stream, the real-space sum (into b.rt and b.uj) on st;
+        // both read the sorted points, then st adds the real-space sums to u
+        CK(launch_bin<T>(p, x, f, q, st));
+        CK(cudaEventRecord(p->ev_fork, st));
+        CK(cudaStreamWaitEvent(p->s_four, p->ev_fork, 0));
+        se_status_t s = fourier_grid<T>(p, p->s_four, p->wgrid, p->nc, nullptr);
+        if (s != SE_OK) return s;
+        CK(launch_gather<T>(p, p->s_four, p->wgrid, f, u));
+        CK(cudaEventRecord(p->ev_join, p->s_four));
+        CK(launch_real<T>(p, st, u, true));
+        CK(cudaStreamWaitEvent(st, p->ev_join, 0));
+        CK(launch_add_uj<T>(p, st, u));
+        return SE_OK;
+    }
     StageTimer tm{p, st};
     tm.mark();
     CK(launch_bin<T>(p, x, f, q, st));

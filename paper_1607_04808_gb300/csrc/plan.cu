@@ -95,8 +95,13 @@ se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol,
     double uabs = sqrt(33.6 * (double)N) / pow(L, deg);
     double budget = 0.5 * tol * uabs;  // each of the three error sources within tol/2
     if (p.P <= 0) {
+        // the stresslet's window error is larger (its multiplier grows one power
+        // of k faster than the stokeslet's; measured at N = 4e4 and 1e5, P = 12
+        // leaves 2.6e-6 and 4.8e-6 where P = 14 leaves 4e-8 and 7e-8): a
+        // quarter of the stokeslet's budget
+        const double ptol = (kernel == SE_STRESSLET) ? tol / 16.0 : tol / 4.0;
         int P = 4;
-        while (P < 32 && pow(10.0, -0.5 * P - 0.5) > tol / 4.0) P += 2;
+        while (P < 32 && pow(10.0, -0.5 * P - 0.5) > ptol) P += 2;
         p.P = P;
     }
     double xi = (p.xi > 0) ? p.xi : xi_arg;
@@ -187,7 +192,7 @@ void free_plan(se_plan_s *p) {
     void *ptrs[] = {p->b.uj, p->b.ncl, p->b.clusters, p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
                     p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
                     p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
-                    p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du, p->pgrid};
+                    p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du, p->pgrid, p->b.rt};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     void *tptrs[] = {p->bt.xs_t, p->bt.perm_t, p->bt.slot_t, p->bt.key_t, p->bt.tag_t, p->bt.cnt_t, p->bt.xs_r,
@@ -197,6 +202,9 @@ void free_plan(se_plan_s *p) {
     for (int i = 0; i < 9; i++)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
     if (p->ev_real) cudaEventDestroy(p->ev_real);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->s_four) cudaStreamDestroy(p->s_four);
     delete p;
 }
 
@@ -482,6 +490,16 @@ static se_status_t create_plan(se_kernel_t kernel, int64_t N, double xi, const d
         if ((e = cudaMemset(p->grid, 0, (size_t)p->nc * Mf3 * esz))) break;
         if ((e = cudaMemset(p->b.status, 0, 16))) break;
         if (periodic && (e = dmalloc(&p->pgrid, (size_t)p->nc * nfft * esz))) break;
+        if (prec == SE_FP32 && !periodic) {
+            // overlapped evaluation: real-space target sums, internal stream
+            if ((e = dmalloc(&p->b.rt, Nn * 4 * esz))) break;
+            int least = 0, greatest = 0;
+            if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest))) break;
+            if ((e = cudaStreamCreateWithPriority(&p->s_four, cudaStreamNonBlocking, greatest))) break;
+            if ((e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming))) break;
+            if ((e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming))) break;
+            p->overlap = true;
+        }
     } while (0);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -597,6 +615,13 @@ extern "C" se_status_t se_plan_check(se_plan_t p) {
 extern "C" se_status_t se_plan_set_timing(se_plan_t p, int on) {
     if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
     p->timing = on != 0;
+    return SE_OK;
+}
+
+extern "C" se_status_t se_plan_set_overlap(se_plan_t p, int on) {
+    if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
+    if (on && !p->s_four) return fail(SE_ERR_NOT_SUPPORTED, "overlapped evaluation needs an FP32 free-space plan");
+    p->overlap = on != 0;
     return SE_OK;
 }
 

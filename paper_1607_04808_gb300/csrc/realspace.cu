@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     k_real_symc(GP<float> g, RC<float> rk, const float4 *__restrict__ xs, const float4 *__restrict__ fs,
                 const float4 *__restrict__ qs, const int *__restrict__ cell_start, const int2 *__restrict__ clusters,
                 const int *__restrict__ ncl_total, const int *__restrict__ perm, float *__restrict__ u,
-                float *__restrict__ uj, int *__restrict__ status) {
+                float *__restrict__ uj, int *__restrict__ status, float *__restrict__ rt) {
     constexpr int WPB = 8, TC = 8, QN = 64;
     constexpr bool STR = (KERNEL == SE_STRESSLET);
     __shared__ float4 tx_all[WPB][TC];
@@ -940,17 +940,29 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     if (__any_sync(FULL, coinc) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
     const int tt = (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
     if ((lane & 3) == 0 && tt < cl.y) {
-        const int mi = perm[cl.x + tt];
-        for (int d = 0; d < 3; d++) u[3 * mi + d] = (float)((double)u[3 * mi + d] + (double)a[d]);
+        if (rt) {
+            // overlapped evaluation: u is being written by the gather meanwhile
+            *reinterpret_cast<float4 *>(rt + 4 * (size_t)(cl.x + tt)) = make_float4(a[0], a[1], a[2], 0.f);
+        } else {
+            const int mi = perm[cl.x + tt];
+            for (int d = 0; d < 3; d++) u[3 * mi + d] = (float)((double)u[3 * mi + d] + (double)a[d]);
+        }
     }
 }
 
 // u[perm[n]] += uj[n] (the contributions scattered to the candidates)
 template <typename T>
-__global__ void k_add_uj(int N, const T *__restrict__ uj, const int *__restrict__ perm, T *__restrict__ u) {
+__global__ void k_add_uj(int N, const T *__restrict__ uj, const int *__restrict__ perm, T *__restrict__ u,
+                         const T *__restrict__ rt = nullptr) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int m = perm[n];
+    if (rt) {
+        // u[perm[n]] += rt[n] + uj[n] (the target and the candidate sums)
+        for (int d = 0; d < 3; d++)
+            u[3 * m + d] = (T)((double)u[3 * m + d] + (double)rt[4 * (size_t)n + d] + (double)uj[4 * (size_t)n + d]);
+        return;
+    }
     for (int d = 0; d < 3; d++) u[3 * m + d] = (T)((double)u[3 * m + d] + (double)uj[4 * (size_t)n + d]);
 }
 
@@ -1300,7 +1312,7 @@ inline int real_pv(double xi_rc) { return xi_rc <= 5.0 ? 1 : 0; }
 #endif
 
 template <typename T, int KERNEL>
-cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) {
+cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u, bool defer) {
     const int N = (int)p->N;
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r,
                   *qs = (const vec4<T> *)p->b.qs_r;
@@ -1341,14 +1353,19 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u) 
         T *ujt = (T *)p->b.uj;
         if constexpr (symc) {
             const float4 *xf = (const float4 *)xs, *ff = (const float4 *)fs, *qf = (const float4 *)qs;
+            float *rtf = defer ? (float *)p->b.rt : nullptr;
             if (real_pv(p->xi * p->rc) == 1)
                 k_real_symc<KERNEL, 1><<<nblk, 256, 0, st>>>(p->gpf, rk, xf, ff, qf, p->b.cnt_r, p->b.clusters,
                                                              p->b.ncl + nrows, p->b.perm_r, (float *)u,
-                                                             (float *)ujt, p->b.status);
+                                                             (float *)ujt, p->b.status, rtf);
             else
                 k_real_symc<KERNEL, 0><<<nblk, 256, 0, st>>>(p->gpf, rk, xf, ff, qf, p->b.cnt_r, p->b.clusters,
                                                              p->b.ncl + nrows, p->b.perm_r, (float *)u,
-                                                             (float *)ujt, p->b.status);
+                                                             (float *)ujt, p->b.status, rtf);
+            if (defer) {
+                p->launches += 3 + scan_launch_count(nrows);
+                return cudaGetLastError();
+            }
         } else if (real_pv(p->xi * p->rc) == 1)
             k_real_sym<T, KERNEL, 1, TPWS><<<nblk, 256, 0, st>>>(g, rk, xs, fs, qs, p->b.cnt_r, p->b.clusters,
                                                                 p->b.ncl + nrows, p->b.perm_r, u, ujt, p->b.status);
@@ -1442,13 +1459,30 @@ template cudaError_t launch_breal<double>(int, const BSys<double> *, const int *
                                           const Buffers &, int *, double *, cudaStream_t, int64_t *);
 
 template <typename T>
-cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u) {
+cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u, bool defer) {
     RC<T> rk = make_rc<T>(p);
     if (!reach_ok(rk)) return cudaErrorInvalidValue;
-    if (p->kernel == SE_STOKESLET) return launch_real_k<T, SE_STOKESLET>(p, st, rk, u);
-    if (p->kernel == SE_STRESSLET) return launch_real_k<T, SE_STRESSLET>(p, st, rk, u);
-    return launch_real_k<T, SE_ROTLET>(p, st, rk, u);
+    if (defer && !real_can_defer(p)) return cudaErrorInvalidValue;
+    if (p->kernel == SE_STOKESLET) return launch_real_k<T, SE_STOKESLET>(p, st, rk, u, defer);
+    if (p->kernel == SE_STRESSLET) return launch_real_k<T, SE_STRESSLET>(p, st, rk, u, defer);
+    return launch_real_k<T, SE_ROTLET>(p, st, rk, u, defer);
 }
+
+// The FP32 symmetric kernel can leave u alone (its sums in b.rt and b.uj).
+bool real_can_defer(const se_plan_s *p) {
+    return p->prec == SE_FP32 && !p->periodic && SE_RS_SYM && SE_RS_SYMC && p->b.uj && p->b.rt;
+}
+
+template <typename T>
+cudaError_t launch_add_uj(se_plan_s *p, cudaStream_t st, T *u) {
+    const int N = (int)p->N;
+    k_add_uj<T><<<(N + 255) / 256, 256, 0, st>>>(N, (const T *)p->b.uj, p->b.perm_r, u, (const T *)p->b.rt);
+    p->launches++;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_add_uj<float>(se_plan_s *, cudaStream_t, float *);
+template cudaError_t launch_add_uj<double>(se_plan_s *, cudaStream_t, double *);
 
 // Real-space sum at separate targets (binned into bt, Nt points): clusters of
 // the targets' cell rows, candidates from the plan's sources; adds to ut.
@@ -1509,8 +1543,8 @@ cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *
     return cudaGetLastError();
 }
 
-template cudaError_t launch_real<float>(se_plan_s *, cudaStream_t, float *);
-template cudaError_t launch_real<double>(se_plan_s *, cudaStream_t, double *);
+template cudaError_t launch_real<float>(se_plan_s *, cudaStream_t, float *, bool);
+template cudaError_t launch_real<double>(se_plan_s *, cudaStream_t, double *, bool);
 template <typename T>
 cudaError_t launch_real_adjT(se_plan_s *p, cudaStream_t st, const T *f_orig, const T *q_orig, T *gf, T *gq) {
     const int N = (int)p->N;

@@ -176,6 +176,7 @@ struct Buffers {
     void *fs_r = nullptr;
     void *qs_r = nullptr;
     int *perm_r = nullptr;
+    void *rt = nullptr;     // N x 4 T: real-space sums at the targets (overlapped evaluation)
     int *cnt_r = nullptr;
     int *slot_r = nullptr;
     int *key_r = nullptr;
@@ -230,6 +231,11 @@ struct se_plan_s {
     cufftHandle fwd = 0, inv = 0, fwd3 = 0;
     bool have_fwd = false, have_inv = false, have_fwd3 = false;
     cudaStream_t last_stream = nullptr;
+    // overlapped evaluation (FP32): the Fourier part on a high-priority internal
+    // stream while the real-space sum runs on the caller's stream
+    bool overlap = false;
+    cudaStream_t s_four = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool timing = false;
     cudaEvent_t ev[9] = {};
     cudaEvent_t ev_real = nullptr;  // recorded before the main real-space kernel when timing
@@ -279,8 +285,13 @@ template <typename T>
 cudaError_t launch_scale(se_plan_s *p, cudaStream_t st, void *spec, int transpose);
 template <typename T>
 cudaError_t launch_gather(se_plan_s *p, cudaStream_t st, const void *wgrid, const T *f_orig, T *u);
+// defer: the target sums go to b.rt and nothing is added to u; launch_add_uj
+// adds them (and the candidate sums b.uj) later.  Only where real_can_defer.
 template <typename T>
-cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u);
+cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u, bool defer = false);
+template <typename T>
+cudaError_t launch_add_uj(se_plan_s *p, cudaStream_t st, T *u);
+bool real_can_defer(const se_plan_s *p);
 template <typename T>
 cudaError_t launch_zero_octant(se_plan_s *p, cudaStream_t st, void *grid, int nc);
 template <typename T>

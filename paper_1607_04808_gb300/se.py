@@ -87,6 +87,8 @@ def lib():
             L.se_plan_check.argtypes = [vp]
             L.se_plan_set_timing.restype = i32
             L.se_plan_set_timing.argtypes = [vp, i32]
+            L.se_plan_set_overlap.restype = i32
+            L.se_plan_set_overlap.argtypes = [vp, i32]
             L.se_plan_stage_times.restype = i32
             L.se_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
             L.se_plan_launch_count.restype = i64
@@ -264,6 +266,10 @@ class Plan:
 
     def set_timing(self, on: bool = True):
         _check(lib().se_plan_set_timing(self._h, 1 if on else 0))
+
+    def set_overlap(self, on: bool = True):
+        """se_plan_set_overlap: Fourier part and real-space sum on two streams (FP32)."""
+        _check(lib().se_plan_set_overlap(self._h, 1 if on else 0))
 
     def stage_times(self) -> dict:
         buf = (ctypes.c_float * 8)()
