@@ -62,6 +62,41 @@ __device__ __forceinline__ float erfcx_poly(float t) {
     return q;
 }
 
+// Two values at once with the paired FP32 instructions of sm_100 and later
+// (per component the same rounding as the scalar operations).
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+template <int PV>
+__device__ __forceinline__ float2 erfcx_poly2(float2 t) {
+    if (PV == 1) {
+        float2 q = f2(ERFC_Q5[SE_ERFC_DEG5]);
+#pragma unroll
+        for (int k = SE_ERFC_DEG5 - 1; k >= 0; k--) q = __ffma2_rn(q, t, f2(ERFC_Q5[k]));
+        return q;
+    }
+    float2 q = f2(ERFC_Q8[SE_ERFC_DEG8]);
+#pragma unroll
+    for (int k = SE_ERFC_DEG8 - 1; k >= 0; k--) q = __ffma2_rn(q, t, f2(ERFC_Q8[k]));
+    return q;
+}
+
+// radial_ab (stokeslet, rotlet) for two distances at once, r2 > 0 in both slots
+template <int PV>
+__device__ __forceinline__ void radial_ab2(const RC<float> &rk, float2 r2, float2 &a, float2 &b) {
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 r = __fmul2_rn(r2, rinv);
+    const float2 x = __fmul2_rn(f2(rk.xi), r);
+    const float2 ce = __fmul2_rn(f2(rk.ce), r2);
+    const float2 e = make_float2(ex2_approx(ce.x), ex2_approx(ce.y));
+    const float2 y = __fadd2_rn(f2(2.0f), x);
+    const float2 q = erfcx_poly2<PV>(make_float2(__fdividef(1.0f, y.x), __fdividef(1.0f, y.y)));
+    const float2 cr = __fmul2_rn(f2(rk.c), r);
+    const float2 ncr = __fmul2_rn(f2(-rk.c), r);
+    const float2 er = __fmul2_rn(e, rinv);
+    a = __fmul2_rn(er, __fadd2_rn(q, ncr));
+    b = __fmul2_rn(__fmul2_rn(er, __fmul2_rn(rinv, rinv)), __fadd2_rn(q, cr));
+}
+
 // The two radial multipliers of a pair at distance r (r2 = r^2 > 0):
 //   stokeslet, rotlet: a = (erfc(x) - (2/sqrt(pi)) x e) / r,  b = (erfc(x) + (2/sqrt(pi)) x e) / r^3
 //   stresslet:         a = A1 = -2 [3 erfc(x) + (2/sqrt(pi)) x (3 + 2 x^2) e] / r^2,  b = A2 = 2 xi^2 (2/sqrt(pi)) x e
@@ -698,6 +733,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
 //                                  odd stresslet and rotlet).
 // A pair counts when the candidate's stream position exceeds the target's slot
 // (positions below the cluster's size are the cluster's own points).
+#ifndef SE_RS_PAIR
+#define SE_RS_PAIR 1
+#endif
 #ifndef SE_RS_SYMC_MINB
 #define SE_RS_SYMC_MINB 4
 #endif
@@ -719,10 +757,14 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     __shared__ int2 seg_all[WPB][MAXROWS];
     __shared__ int pre_all[WPB][MAXROWS + 1];
     __shared__ float box_all[WPB][6];
+    // PAIR (stokeslet, rotlet): targets t and t + 4 side by side, [component][2 p + slot]
+    constexpr bool PAIR = !STR && SE_RS_PAIR;
+    __shared__ __align__(8) float tp_all[PAIR ? WPB : 1][6][TC];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * WPB + wib;
     if (c >= *ncl_total) return;
     float4 *tx = tx_all[wib], *tf = tf_all[wib], *tq = tq_all[STR ? wib : 0];
+    float (*tp)[TC] = tp_all[PAIR ? wib : 0];
     float *box = box_all[wib];
     float4 *qx = qx_all[wib], *qf = qf_all[wib], *qq = qq_all[STR ? wib : 0];
     int *qm = qm_all[wib];
@@ -746,6 +788,17 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
         tx[lane] = xo;
         tf[lane] = fo;
         if (STR) tq[lane] = qo;
+        if (PAIR) {
+            // empty slots far away but finite: a masked slot's products stay 0
+            const int o = 2 * (lane & 3) + (lane >> 2);  // pair p = t mod 4, slot t / 4
+            const bool real = lane < cl.y;
+            tp[0][o] = real ? xo.x : 1e18f;
+            tp[1][o] = real ? xo.y : 1e18f;
+            tp[2][o] = real ? xo.z : 1e18f;
+            tp[3][o] = fo.x;
+            tp[4][o] = fo.y;
+            tp[5][o] = fo.z;
+        }
     }
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -805,6 +858,9 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     float acc[TC][3];
 #pragma unroll
     for (int t = 0; t < TC; t++) acc[t][0] = acc[t][1] = acc[t][2] = 0.f;
+    float2 accp[TC / 2][3];  // PAIR: targets (p, p + 4)
+#pragma unroll
+    for (int p2 = 0; p2 < TC / 2; p2++) accp[p2][0] = accp[p2][1] = accp[p2][2] = f2(0.f);
     bool coinc = false;
     int lo = 0, fill = 0, cb = 0;
     while (true) {
@@ -840,7 +896,9 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
         const int nq = min(fill, 32);
         {
             const bool valid = lane < nq;
-            float4 xj = make_float4(INF, INF, INF, 0.f);
+            // an idle lane's candidate: at infinity, or far but finite on the paired path
+            const float far = PAIR ? 1e18f : INF;
+            float4 xj = make_float4(far, far, far, 0.f);
             float4 fj = make_float4(0.f, 0.f, 0.f, 0.f), qj = fj;
             int vs = 0, mj = 0;
             if (valid) {
@@ -851,6 +909,52 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
                 mj = qm[lane];
             }
             float cj[3] = {0.f, 0.f, 0.f};
+            if constexpr (PAIR) {
+                const float2 nx = f2(-xj.x), ny = f2(-xj.y), nz = f2(-xj.z);
+                const float2 fx = f2(fj.x), fy = f2(fj.y), fz = f2(fj.z);
+                float2 c2[3] = {f2(0.f), f2(0.f), f2(0.f)};
+#pragma unroll
+                for (int p2 = 0; p2 < TC / 2; p2++) {
+                    const float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[0][2 * p2]), nx);
+                    const float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[1][2 * p2]), ny);
+                    const float2 dz = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[2][2 * p2]), nz);
+                    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                    const bool ia = r2.x <= rk.rc2 && p2 < vs, ib = r2.y <= rk.rc2 && p2 + TC / 2 < vs;
+                    if (ia || ib) {
+                        // zero distance: a distinct point at the same position, skipped
+                        const bool ua = ia && r2.x > 0.f, ub = ib && r2.y > 0.f;
+                        coinc |= (ia && !ua) || (ib && !ub);
+                        float2 a, b;
+                        radial_ab2<PV>(rk, make_float2(ua ? r2.x : 1.f, ub ? r2.y : 1.f), a, b);
+                        a = make_float2(ua ? a.x : 0.f, ub ? a.y : 0.f);
+                        b = make_float2(ua ? b.x : 0.f, ub ? b.y : 0.f);
+                        const float2 gx = *reinterpret_cast<const float2 *>(&tp[3][2 * p2]);
+                        const float2 gy = *reinterpret_cast<const float2 *>(&tp[4][2 * p2]);
+                        const float2 gz = *reinterpret_cast<const float2 *>(&tp[5][2 * p2]);
+                        if (KERNEL == SE_STOKESLET) {
+                            const float2 bj = __fmul2_rn(b, __ffma2_rn(dz, fz, __ffma2_rn(dy, fy, __fmul2_rn(dx, fx))));
+                            accp[p2][0] = __ffma2_rn(a, fx, __ffma2_rn(bj, dx, accp[p2][0]));
+                            accp[p2][1] = __ffma2_rn(a, fy, __ffma2_rn(bj, dy, accp[p2][1]));
+                            accp[p2][2] = __ffma2_rn(a, fz, __ffma2_rn(bj, dz, accp[p2][2]));
+                            const float2 bt = __fmul2_rn(b, __ffma2_rn(dz, gz, __ffma2_rn(dy, gy, __fmul2_rn(dx, gx))));
+                            c2[0] = __ffma2_rn(a, gx, __ffma2_rn(bt, dx, c2[0]));
+                            c2[1] = __ffma2_rn(a, gy, __ffma2_rn(bt, dy, c2[1]));
+                            c2[2] = __ffma2_rn(a, gz, __ffma2_rn(bt, dz, c2[2]));
+                        } else {
+                            // rotlet: u_t += b (f_j x d), u_j -= b (f_t x d)
+                            const float2 nb = __fmul2_rn(f2(-1.f), b);
+                            accp[p2][0] = __ffma2_rn(b, __ffma2_rn(fy, dz, __fmul2_rn(f2(-fj.z), dy)), accp[p2][0]);
+                            accp[p2][1] = __ffma2_rn(b, __ffma2_rn(fz, dx, __fmul2_rn(f2(-fj.x), dz)), accp[p2][1]);
+                            accp[p2][2] = __ffma2_rn(b, __ffma2_rn(fx, dy, __fmul2_rn(f2(-fj.y), dx)), accp[p2][2]);
+                            c2[0] = __ffma2_rn(nb, __ffma2_rn(gy, dz, __fmul2_rn(__fmul2_rn(f2(-1.f), gz), dy)), c2[0]);
+                            c2[1] = __ffma2_rn(nb, __ffma2_rn(gz, dx, __fmul2_rn(__fmul2_rn(f2(-1.f), gx), dz)), c2[1]);
+                            c2[2] = __ffma2_rn(nb, __ffma2_rn(gx, dy, __fmul2_rn(__fmul2_rn(f2(-1.f), gy), dx)), c2[2]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < 3; d++) cj[d] = c2[d].x + c2[d].y;
+            } else
 #pragma unroll
             for (int t = 0; t < TC; t++) {
                 const float4 xt = tx[t];
@@ -917,6 +1021,15 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
         }
         fill -= nq;
         __syncwarp();
+    }
+    if constexpr (PAIR) {
+#pragma unroll
+        for (int p2 = 0; p2 < TC / 2; p2++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                acc[p2][d] = accp[p2][d].x;
+                acc[p2 + TC / 2][d] = accp[p2][d].y;
+            }
     }
     // sum the accumulators over the lanes: a reduce-scatter over lane bits 4,
     // 3, 2 leaves lane l with the 3 components of target ((l >> 2) & 7) summed
