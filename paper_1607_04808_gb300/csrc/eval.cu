@@ -21,6 +21,16 @@ cufftResult exec_fwd<double>(cufftHandle h, void *in, void *out) {
     return cufftExecD2Z(h, (cufftDoubleReal *)in, (cufftDoubleComplex *)out);
 }
 template <typename T>
+cufftResult exec_z(cufftHandle h, void *data, int dir);
+template <>
+cufftResult exec_z<float>(cufftHandle h, void *data, int dir) {
+    return cufftExecC2C(h, (cufftComplex *)data, (cufftComplex *)data, dir);
+}
+template <>
+cufftResult exec_z<double>(cufftHandle h, void *data, int dir) {
+    return cufftExecZ2Z(h, (cufftDoubleComplex *)data, (cufftDoubleComplex *)data, dir);
+}
+template <typename T>
 cufftResult exec_inv(cufftHandle h, void *in, void *out);
 template <>
 cufftResult exec_inv<float>(cufftHandle h, void *in, void *out) {
@@ -71,6 +81,29 @@ se_status_t fourier_grid(se_plan_s *p, cudaStream_t st, void *wout, int nc, Stag
     // periodic plans: the halo of the extended grid folded onto the periodic grid
     if (p->periodic) CK(launch_fold<T>(p, st, p->grid, p->pgrid, nc));
     if (tm) tm->mark();
+    if (p->pruned) {
+        // zero-padding-aware transforms: 2D (y, x) on the Mtilde nonzero z-planes,
+        // the upper z-planes of the spectrum zeroed, then the transform along z;
+        // back along z, then 2D on the Mtilde planes the gather reads
+        const size_t vol_r = vol(p->geom), plane_c = (size_t)p->mf[1] * (p->mf[0] / 2 + 1);
+        const size_t nk = plane_c * p->mf[2], cs = sizeof(cplx<T>);
+        CF(cufftSetStream(p->f2d, st));
+        CF(cufftSetStream(p->zc, st));
+        CF(cufftSetStream(p->i2d, st));
+        for (int c = 0; c < nc; c++)
+            CF(exec_fwd<T>(p->f2d, (T *)p->grid + c * vol_r, (cplx<T> *)p->spec + c * nk));
+        CK(cudaMemset2DAsync((char *)p->spec + p->mt[2] * plane_c * cs, nk * cs, 0,
+                             (p->mf[2] - p->mt[2]) * plane_c * cs, nc, st));
+        for (int c = 0; c < nc; c++) CF(exec_z<T>(p->zc, (cplx<T> *)p->spec + c * nk, CUFFT_FORWARD));
+        if (tm) tm->mark();
+        CK(launch_scale<T>(p, st, p->spec, 0));
+        if (tm) tm->mark();
+        for (int c = 0; c < 3; c++) CF(exec_z<T>(p->zc, (cplx<T> *)p->spec + c * nk, CUFFT_INVERSE));
+        for (int c = 0; c < 3; c++)
+            CF(exec_inv<T>(p->i2d, (cplx<T> *)p->spec + c * nk, (T *)wout + c * vol_r));
+        if (tm) tm->mark();
+        return SE_OK;
+    }
     cufftHandle fwd = (nc == p->nc) ? p->fwd : p->fwd3;
     CF(cufftSetStream(fwd, st));
     CF(exec_fwd<T>(fwd, p->periodic ? p->pgrid : p->grid, p->spec));

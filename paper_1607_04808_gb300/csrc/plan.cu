@@ -189,6 +189,9 @@ void free_plan(se_plan_s *p) {
     if (p->have_fwd) cufftDestroy(p->fwd);
     if (p->have_inv) cufftDestroy(p->inv);
     if (p->have_fwd3) cufftDestroy(p->fwd3);
+    if (p->f2d) cufftDestroy(p->f2d);
+    if (p->i2d) cufftDestroy(p->i2d);
+    if (p->zc) cufftDestroy(p->zc);
     void *ptrs[] = {p->b.uj, p->b.ncl, p->b.clusters, p->ghat64, (p->ghat != p->ghat64) ? p->ghat : nullptr, p->grid, p->spec, p->wgrid, p->wgrid2,
                     p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
                     p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
@@ -529,6 +532,26 @@ static se_status_t create_plan(se_kernel_t kernel, int64_t N, double xi, const d
                 return fail(SE_ERR_CUFFT, "cufftPlanMany (forward, 3) failed");
             }
             p->have_fwd3 = true;
+        }
+#ifndef SE_PRUNED_FFT
+#define SE_PRUNED_FFT 1
+#endif
+        if (SE_PRUNED_FFT && !periodic) {
+            // the spread grid is zero outside z, y, x < Mtilde and the gather reads
+            // only that corner: the 2D (y, x) transforms run on the Mtilde planes
+            // z < Mtilde, the transform along z on every (ky, kx) column
+            int n2[2] = {p->mf[1], p->mf[0]};
+            int re2[2] = {p->mf[1], p->mf[0]}, ce2[2] = {p->mf[1], p->mf[0] / 2 + 1};
+            const int plane_r = p->mf[1] * p->mf[0], plane_c = p->mf[1] * (p->mf[0] / 2 + 1);
+            int nz[1] = {p->mf[2]};
+            cufftType tz = (prec == SE_FP32) ? CUFFT_C2C : CUFFT_Z2Z;
+            if (cufftPlanMany(&p->f2d, 2, n2, re2, 1, plane_r, ce2, 1, plane_c, tf, p->mt[2]) != CUFFT_SUCCESS ||
+                cufftPlanMany(&p->i2d, 2, n2, ce2, 1, plane_c, re2, 1, plane_r, ti, p->mt[2]) != CUFFT_SUCCESS ||
+                cufftPlanMany(&p->zc, 1, nz, nz, plane_c, 1, nz, plane_c, 1, tz, plane_c) != CUFFT_SUCCESS) {
+                free_plan(p);
+                return fail(SE_ERR_CUFFT, "cufftPlanMany (zero-padding-aware transforms) failed");
+            }
+            p->pruned = true;
         }
     }
     for (int i = 0; i < 9; i++) cudaEventCreate(&p->ev[i]);

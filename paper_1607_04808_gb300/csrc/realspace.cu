@@ -38,6 +38,10 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int QCAP = 64;
+// SE_RS_PAIR: paired FP32 arithmetic (sm_100+) in the FP32 pair sums
+#ifndef SE_RS_PAIR
+#define SE_RS_PAIR 1
+#endif
 constexpr int MAXROWS = 121;  // (2 reach_y + 1)(2 reach_z + 1) rows of cells at most
 
 __device__ __forceinline__ float ex2_approx(float v) {
@@ -309,6 +313,42 @@ __device__ __forceinline__ void pair_multi(const RC<T> &rk, T dx, T dy, T dz, T 
     }
 }
 
+// pair_multi for 8 right-hand sides in pairs (r, r + 4) with the paired FP32
+// instructions: fp holds the candidate's sources as [3 p + d] = (f_p.d, f_{p+4}.d).
+template <int KERNEL, int PV>
+__device__ __forceinline__ void pair_multi8p(const RC<float> &rk, float dx, float dy, float dz, float r2,
+                                             const float2 *fp, float2 (*acc)[3]) {
+    float rinv, a, b;
+    radial_ab<KERNEL, PV>(rk, r2, rinv, a, b);
+    const float2 A = f2(a), Bm = f2(b), DX = f2(dx), DY = f2(dy), DZ = f2(dz);
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        const float2 fx = fp[3 * p], fy = fp[3 * p + 1], fz = fp[3 * p + 2];
+        if (KERNEL == SE_STOKESLET) {
+            const float2 brf = __fmul2_rn(Bm, __ffma2_rn(DZ, fz, __ffma2_rn(DY, fy, __fmul2_rn(DX, fx))));
+            acc[p][0] = __ffma2_rn(A, fx, __ffma2_rn(brf, DX, acc[p][0]));
+            acc[p][1] = __ffma2_rn(A, fy, __ffma2_rn(brf, DY, acc[p][1]));
+            acc[p][2] = __ffma2_rn(A, fz, __ffma2_rn(brf, DZ, acc[p][2]));
+        } else {
+            // rotlet: b (f x d)
+            const float2 NX = f2(-dx), NY = f2(-dy), NZ = f2(-dz);
+            acc[p][0] = __ffma2_rn(Bm, __ffma2_rn(fy, DZ, __fmul2_rn(fz, NY)), acc[p][0]);
+            acc[p][1] = __ffma2_rn(Bm, __ffma2_rn(fz, DX, __fmul2_rn(fx, NZ)), acc[p][1]);
+            acc[p][2] = __ffma2_rn(Bm, __ffma2_rn(fx, DY, __fmul2_rn(fy, NX)), acc[p][2]);
+        }
+    }
+}
+
+// Kahan addition of x into (s, c) for two values at once (t - s and y - c as
+// fused multiply-adds with -1, exact like the subtractions they replace)
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 x) {
+    const float2 m1 = f2(-1.f);
+    const float2 y = __ffma2_rn(m1, c, x);
+    const float2 t = __fadd2_rn(s, y);
+    c = __ffma2_rn(m1, y, __ffma2_rn(m1, s, t));
+    s = t;
+}
+
 // One warp per cluster: lane = (target k = lane % TPW, candidate stream
 // s = lane / TPW).  Candidates of every row within reach are loaded 32 at a
 // time into shared memory and stream s takes every NS-th of them, so each lane
@@ -333,6 +373,8 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
                                                  const vec4<T> *__restrict__ xtg = nullptr,
                                                  const int *__restrict__ tperm = nullptr) {
     constexpr int WPB = 8, NS = 32 / TPW;
+    // 8 right-hand sides of the stokeslet or rotlet in FP32: pairs (r, r + 4)
+    constexpr bool PAIRRHS = sizeof(T) == 4 && NR == 8 && KERNEL != SE_STRESSLET && SE_RS_PAIR;
     __shared__ vec4<T> sx_all[WPB][32];
     __shared__ vec4<T> sf_all[WPB][32 * NR];
     __shared__ vec4<T> sq_all[KERNEL == SE_STRESSLET ? WPB : 1][32];
@@ -414,6 +456,12 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
 #pragma unroll
     for (int q = 0; q < NR; q++)
         for (int d = 0; d < 3; d++) acc[q][d] = ks[q][d] = kc[q][d] = T(0);
+    float2 acc2[4][3], ks2[4][3], kc2[4][3];  // PAIRRHS: right-hand sides (p, p + 4)
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        for (int d = 0; d < 3; d++) acc2[q][d] = ks2[q][d] = kc2[q][d] = f2(0.f);
+    // PAIRRHS staging of the candidates' sources: 12 float2 per candidate
+    float2 *sp = reinterpret_cast<float2 *>(sf);
     int zeros = 0;  // candidates at distance 0 seen by this lane (its own target included once)
     vec4<T> zero4;
     zero4.x = zero4.y = zero4.z = zero4.w = 0;
@@ -426,9 +474,21 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
             vec4<T> xv = xs[m];
             xv.w = T(0);
             sx[lane] = xv;
+            if constexpr (PAIRRHS) {
+                const vec4<T> *fm = fs + (size_t)m * fstride + q0;
 #pragma unroll
-            for (int q = 0; q < NR; q++)
-                if (q < nq) sf[lane * NR + q] = fs[(size_t)m * fstride + q0 + q];
+                for (int q = 0; q < 4; q++) {
+                    const float4 lo = (q < nq) ? fm[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 hi = (q + 4 < nq) ? fm[q + 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    sp[lane * 12 + 3 * q] = make_float2(lo.x, hi.x);
+                    sp[lane * 12 + 3 * q + 1] = make_float2(lo.y, hi.y);
+                    sp[lane * 12 + 3 * q + 2] = make_float2(lo.z, hi.z);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NR; q++)
+                    if (q < nq) sf[lane * NR + q] = fs[(size_t)m * fstride + q0 + q];
+            }
             if (KERNEL == SE_STRESSLET) sq[lane] = qs[m];
         }
         __syncwarp();
@@ -439,8 +499,12 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (has && r2 <= rk.rc2) {
                 if (r2 > T(0)) {
-                    const vec4<T> qv = (KERNEL == SE_STRESSLET) ? sq[j] : zero4;
-                    pair_multi<T, KERNEL, NR, PV>(rk, dx, dy, dz, r2, sf + j * NR, qv, acc, nq);
+                    if constexpr (PAIRRHS) {
+                        pair_multi8p<KERNEL, PV>(rk, dx, dy, dz, r2, sp + j * 12, acc2);
+                    } else {
+                        const vec4<T> qv = (KERNEL == SE_STRESSLET) ? sq[j] : zero4;
+                        pair_multi<T, KERNEL, NR, PV>(rk, dx, dy, dz, r2, sf + j * NR, qv, acc, nq);
+                    }
                 } else {
                     zeros++;  // the target itself, or a coincident point
                 }
@@ -453,11 +517,30 @@ __global__ void __launch_bounds__(256) k_real_cl(GP<T> g0, RC<T> rk0, const BSys
             for (int j = s; j < nch; j += NS) step(j);
         }
         __syncwarp();
+        if constexpr (PAIRRHS) {
 #pragma unroll
-        for (int q = 0; q < NR; q++)
+            for (int q = 0; q < 4; q++)
+                for (int d = 0; d < 3; d++) {
+                    kahan_add2(ks2[q][d], kc2[q][d], acc2[q][d]);
+                    acc2[q][d] = f2(0.f);
+                }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NR; q++)
+                for (int d = 0; d < 3; d++) {
+                    kahan_add(ks[q][d], kc[q][d], acc[q][d]);
+                    acc[q][d] = 0;
+                }
+        }
+    }
+    if constexpr (PAIRRHS) {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
             for (int d = 0; d < 3; d++) {
-                kahan_add(ks[q][d], kc[q][d], acc[q][d]);
-                acc[q][d] = 0;
+                ks[q][d] = ks2[q][d].x;
+                ks[q + 4][d] = ks2[q][d].y;
+                kc[q][d] = kc2[q][d].x;
+                kc[q + 4][d] = kc2[q][d].y;
             }
     }
     // combine the NS streams of each target (lanes k, k + TPW, ...)
@@ -733,9 +816,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
 //                                  odd stresslet and rotlet).
 // A pair counts when the candidate's stream position exceeds the target's slot
 // (positions below the cluster's size are the cluster's own points).
-#ifndef SE_RS_PAIR
-#define SE_RS_PAIR 1
-#endif
 #ifndef SE_RS_SYMC_MINB
 #define SE_RS_SYMC_MINB 4
 #endif

@@ -229,6 +229,10 @@ struct se_plan_s {
     se::Buffers bt;          // evaluation targets (positions only), allocated on first use
     int64_t nt_cap = 0;      // targets bt holds room for
     cufftHandle fwd = 0, inv = 0, fwd3 = 0;
+    // zero-padding-aware transforms (free-space plans): 2D transforms of the
+    // Mtilde planes that hold data or are read, and a 1D transform along z
+    bool pruned = false;
+    cufftHandle f2d = 0, i2d = 0, zc = 0;
     bool have_fwd = false, have_inv = false, have_fwd3 = false;
     cudaStream_t last_stream = nullptr;
     // overlapped evaluation (FP32): the Fourier part on a high-priority internal
