@@ -380,19 +380,22 @@ def run_ours(args, rank, world, dist):
         "real": N_POINTS * (32 + 24),
     }
     stage_gbs = {k: stage_bytes[k] / (stages[k] * 1e-3) / 1e9 for k in stage_bytes if stages.get(k)}
-    # each hand-written stage against the roofline that binds it: spreading and
-    # gather are FP32 FMA work (3 P^3 FMA per point), the scaling streams the
-    # spectrum through HBM, the real-space sum is FP32 ALU work (58 flop per pair)
+    # each hand-written stage against the roofline that binds it: spreading is
+    # FP32 FMA work in registers (3 P^3 FMA per point), the gather reads each
+    # point's 3 P^3 grid values from shared memory (one 128-byte wavefront per
+    # SM clock), the scaling streams the spectrum through HBM, the real-space
+    # sum is FP32 ALU work (58 flop per pair)
     P = prm["P"]
     grid_flop = N_POINTS * 3 * P**3 * 2
+    smem_peak = 152 * 128 * sm_max * 1e6 / 1e12  # TB/s
     stage_roofline = {}
     for k, bound, work, unit, peak in (
             ("spread", "fma", grid_flop, "TFLOP/s", alu_peak),
-            ("gather", "fma", grid_flop, "TFLOP/s", alu_peak),
+            ("gather", "smem", N_POINTS * 3 * P**3 * 4, "TB/s", smem_peak),
             ("scale", "hbm", stage_bytes["scale"], "GB/s", hbm),
             ("real", "alu", pairs * FLOP_PER_PAIR, "TFLOP/s", alu_peak)):
         if stages.get(k):
-            a = work / (stages[k] * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
+            a = work / (stages[k] * 1e-3) / (1e9 if unit == "GB/s" else 1e12)
             stage_roofline[k] = {"bound": bound, "achieved": a, "peak": peak, "unit": unit, "frac": a / peak}
     cpu = None if args.no_cpu else cpu_baseline(x64, f64)
     line = {
