@@ -819,7 +819,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
 #ifndef SE_RS_SYMC_MINB
 #define SE_RS_SYMC_MINB 4
 #endif
-template <int KERNEL, int PV>
+// PER (periodic plans, stokeslet and rotlet): the rows of cells wrap around
+// the box, each at most once, the own row rotated to the front of the stream;
+// each row's x-range wraps into at most two segments (in the own row only the
+// positions from the cluster's first point on).  Every candidate is moved to
+// its image nearest the centre of the targets' box, which is every target's
+// nearest image when the box's half-width plus rc stays below L/2; a wider
+// cluster takes nearest images pair by pair instead.
+template <int KERNEL, int PV, bool PER = false>
 __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     k_real_symc(GP<float> g, RC<float> rk, const float4 *__restrict__ xs, const float4 *__restrict__ fs,
                 const float4 *__restrict__ qs, const int *__restrict__ cell_start, const int2 *__restrict__ clusters,
@@ -827,6 +834,7 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
                 float *__restrict__ uj, int *__restrict__ status, float *__restrict__ rt) {
     constexpr int WPB = 8, TC = 8, QN = 64;
     constexpr bool STR = (KERNEL == SE_STRESSLET);
+    static_assert(!(PER && STR), "periodic plans sum the stresslet with k_real_cmp");
     __shared__ float4 tx_all[WPB][TC];
     __shared__ float4 tf_all[WPB][TC];
     __shared__ float4 tq_all[STR ? WPB : 1][TC];
@@ -834,8 +842,9 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     __shared__ float4 qf_all[WPB][QN];
     __shared__ float4 qq_all[STR ? WPB : 1][QN];
     __shared__ int qm_all[WPB][QN];
-    __shared__ int2 seg_all[WPB][MAXROWS];
-    __shared__ int pre_all[WPB][MAXROWS + 1];
+    constexpr int NSEG = PER ? 2 * MAXROWS : MAXROWS;  // entries of the segment list
+    __shared__ int2 seg_all[WPB][NSEG];
+    __shared__ int pre_all[WPB][NSEG + 1];
     __shared__ float box_all[WPB][6];
     // PAIR (stokeslet, rotlet): targets t and t + 4 side by side, [component][2 p + slot]
     constexpr bool PAIR = !STR && SE_RS_PAIR;
@@ -895,9 +904,60 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     int c0[3], c1[3];
     unpack3(get_tag(xs[cl.x]), c0[0], c0[1], c0[2]);
     unpack3(get_tag(xs[cl.x + cl.y - 1]), c1[0], c1[1], c1[2]);
-    const int Ry = rk.reach[0], Rz = rk.reach[1], Wy = 2 * Ry + 1, nrows = Wy * (2 * Rz + 1);
     const float rc2m = rk.rc2 * 1.0001f;
     const int own_row = c0[2] * g.ncel[1] + c0[1];
+    // PER: the centre of the targets' box and whether one image shift per
+    // candidate serves every target
+    float ctr[3] = {0.f, 0.f, 0.f};
+    bool wide = false;
+    if constexpr (PER) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            ctr[d] = 0.5f * (blo[d] + bhi[d]);
+            wide |= 0.5f * (bhi[d] - blo[d]) + sqrtf(rk.rc2) >= 0.49f * g.len[d];
+        }
+    }
+    int nseg;
+    if constexpr (PER) {
+        const int ny = g.ncel[1], nz = g.ncel[2], nx = g.ncel[0];
+        const int Wy = min(2 * rk.reach[0] + 1, ny), Wz = min(2 * rk.reach[1] + 1, nz);
+        const int oy = (Wy - 1) / 2, oz = (Wz - 1) / 2, nrows = Wy * Wz, centre = oz * Wy + oy;
+        for (int r = lane; r < nrows; r += 32) {
+            const int rr = (r + centre) % nrows;  // r = 0: the own row
+            const int dyc = (rr % Wy) - oy, dzc = (rr / Wy) - oz;
+            const int iy = (c0[1] + dyc + ny) % ny, iz = (c0[2] + dzc + nz) % nz;
+            const int row = iz * ny + iy;
+            int2 s0 = make_int2(0, 0), s1 = make_int2(0, 0);
+            if (row >= own_row) {
+                const float dy = (Wy == ny) ? 0.f : float(max(abs(dyc) - 1, 0)) * g.cw[1];
+                const float dz = (Wz == nz) ? 0.f : float(max(abs(dzc) - 1, 0)) * g.cw[2];
+                const float d2 = dy * dy + dz * dz;
+                if (d2 <= rc2m) {
+                    const float del = sqrtf(rc2m - d2) + 1e-4f * g.cw[0];
+                    const int ixl = (int)floorf((float(c0[0]) * g.cw[0] - del) * g.icw[0]);
+                    const int ixh = (int)floorf((float(c1[0] + 1) * g.cw[0] + del) * g.icw[0]);
+                    const int base = row * nx;
+                    const bool own = (row == own_row);
+                    if (ixh - ixl + 1 >= nx) {
+                        s0 = make_int2(own ? cl.x : cell_start[base], cell_start[base + nx]);
+                    } else {
+                        // the unwrapped core (it holds the cluster in the own row)
+                        const int a = max(ixl, 0), b = min(ixh, nx - 1);
+                        s0 = make_int2(own ? cl.x : cell_start[base + a], cell_start[base + b + 1]);
+                        if (ixl < 0)  // cells at the end of the row (later positions)
+                            s1 = make_int2(cell_start[base + nx + ixl], cell_start[base + nx]);
+                        else if (ixh >= nx && !own)  // cells at its start (earlier positions)
+                            s1 = make_int2(cell_start[base], cell_start[base + ixh - nx + 1]);
+                    }
+                }
+            }
+            seg[2 * r] = s0;
+            seg[2 * r + 1] = s1;
+        }
+        nseg = 2 * nrows;
+    } else {
+    const int Ry = rk.reach[0], Rz = rk.reach[1], Wy = 2 * Ry + 1, nrows = Wy * (2 * Rz + 1);
+    nseg = nrows;
     for (int r = lane; r < nrows; r += 32) {
         const int dyc = (r % Wy) - Ry, dzc = (r / Wy) - Rz;
         const int iy = c0[1] + dyc, iz = c0[2] + dzc;
@@ -919,20 +979,21 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
         }
         seg[r] = sg;
     }
+    }
     __syncwarp();
     int run = 0;
-    for (int r0 = 0; r0 < nrows; r0 += 32) {
+    for (int r0 = 0; r0 < nseg; r0 += 32) {
         const int r = r0 + lane;
-        const int len = (r < nrows) ? seg[r].y - seg[r].x : 0;
+        const int len = (r < nseg) ? seg[r].y - seg[r].x : 0;
         int incl = len;
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += v;
         }
-        if (r < nrows) pre[r] = run + incl - len;
+        if (r < nseg) pre[r] = run + incl - len;
         run += __shfl_sync(FULL, incl, 31);
     }
-    if (lane == 0) pre[nrows] = run;
+    if (lane == 0) pre[nseg] = run;
     __syncwarp();
     const int total = run;
     float acc[TC][3];
@@ -954,10 +1015,16 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
                 while (pre[lo + 1] <= v) lo++;
                 m = seg[lo].x + (v - pre[lo]);
                 xm = xs[m];
+                if (PER && !wide) {
+                    // the image nearest the centre of the targets' box
+                    xm.x += g.len[0] * rintf((ctr[0] - xm.x) * g.ilen[0]);
+                    xm.y += g.len[1] * rintf((ctr[1] - xm.y) * g.ilen[1]);
+                    xm.z += g.len[2] * rintf((ctr[2] - xm.z) * g.ilen[2]);
+                }
                 const float ex = fmaxf(fmaxf(box[0] - xm.x, xm.x - box[3]), 0.f);
                 const float ey = fmaxf(fmaxf(box[1] - xm.y, xm.y - box[4]), 0.f);
                 const float ez = fmaxf(fmaxf(box[2] - xm.z, xm.z - box[5]), 0.f);
-                keep = ex * ex + ey * ey + ez * ez <= rc2m;
+                keep = (PER && wide) || ex * ex + ey * ey + ez * ez <= rc2m;
             }
             const unsigned bal = __ballot_sync(FULL, keep);
             if (keep) {
@@ -995,11 +1062,25 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
                 float2 c2[3] = {f2(0.f), f2(0.f), f2(0.f)};
 #pragma unroll
                 for (int p2 = 0; p2 < TC / 2; p2++) {
-                    const float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[0][2 * p2]), nx);
-                    const float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[1][2 * p2]), ny);
-                    const float2 dz = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[2][2 * p2]), nz);
+                    float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[0][2 * p2]), nx);
+                    float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[1][2 * p2]), ny);
+                    float2 dz = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[2][2 * p2]), nz);
+                    if (PER && wide) {
+                        // nearest images pair by pair
+                        dx.x -= g.len[0] * rintf(dx.x * g.ilen[0]);
+                        dx.y -= g.len[0] * rintf(dx.y * g.ilen[0]);
+                        dy.x -= g.len[1] * rintf(dy.x * g.ilen[1]);
+                        dy.y -= g.len[1] * rintf(dy.y * g.ilen[1]);
+                        dz.x -= g.len[2] * rintf(dz.x * g.ilen[2]);
+                        dz.y -= g.len[2] * rintf(dz.y * g.ilen[2]);
+                    }
                     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-                    const bool ia = r2.x <= rk.rc2 && p2 < vs, ib = r2.y <= rk.rc2 && p2 + TC / 2 < vs;
+                    bool ia = r2.x <= rk.rc2 && p2 < vs, ib = r2.y <= rk.rc2 && p2 + TC / 2 < vs;
+                    if (PER && wide) {
+                        // the empty slots' far position folds back under nearest images
+                        ia = ia && p2 < cl.y;
+                        ib = ib && p2 + TC / 2 < cl.y;
+                    }
                     if (ia || ib) {
                         // zero distance: a distinct point at the same position, skipped
                         const bool ua = ia && r2.x > 0.f, ub = ib && r2.y > 0.f;
@@ -1510,8 +1591,10 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u, 
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r,
                   *qs = (const vec4<T> *)p->b.qs_r;
     const GP<T> &g = gp<T>(p);
-    if (p->periodic) {
-        // periodic plans: one warp per target over the wrapped rows, nearest images
+    // periodic plans: the symmetric kernel for the FP32 stokeslet and rotlet,
+    // otherwise one warp per target over the wrapped rows
+    constexpr bool per_sym = sizeof(T) == 4 && KERNEL != SE_STRESSLET && SE_RS_SYM && SE_RS_SYMC;
+    if (p->periodic && !per_sym) {
         if (p->timing && p->ev_real) cudaEventRecord(p->ev_real, st);
         k_real_cmp<T, KERNEL, false, true><<<(N + 7) / 8, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r,
                                                                       p->b.perm_r, u, p->b.status);
@@ -1547,6 +1630,21 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u, 
         if constexpr (symc) {
             const float4 *xf = (const float4 *)xs, *ff = (const float4 *)fs, *qf = (const float4 *)qs;
             float *rtf = defer ? (float *)p->b.rt : nullptr;
+            if constexpr (KERNEL != SE_STRESSLET) {
+                if (p->periodic) {
+                    if (real_pv(p->xi * p->rc) == 1)
+                        k_real_symc<KERNEL, 1, true><<<nblk, 256, 0, st>>>(
+                            p->gpf, rk, xf, ff, qf, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                            (float *)u, (float *)ujt, p->b.status, nullptr);
+                    else
+                        k_real_symc<KERNEL, 0, true><<<nblk, 256, 0, st>>>(
+                            p->gpf, rk, xf, ff, qf, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                            (float *)u, (float *)ujt, p->b.status, nullptr);
+                    k_add_uj<T><<<(N + 255) / 256, 256, 0, st>>>(N, ujt, p->b.perm_r, u);
+                    p->launches += 4 + scan_launch_count(nrows);
+                    return cudaGetLastError();
+                }
+            }
             if (real_pv(p->xi * p->rc) == 1)
                 k_real_symc<KERNEL, 1><<<nblk, 256, 0, st>>>(p->gpf, rk, xf, ff, qf, p->b.cnt_r, p->b.clusters,
                                                              p->b.ncl + nrows, p->b.perm_r, (float *)u,

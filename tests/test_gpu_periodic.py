@@ -107,6 +107,18 @@ def test_offset_box_and_side():
     assert rel_l2(u, ref) <= 1e-10
 
 
+@pytest.mark.parametrize("kernel", ["stokeslet", "rotlet"])
+def test_fp32_offset_box_symmetric_path(kernel):
+    """FP32 stokeslet and rotlet run the symmetric periodic kernel (wrapped rows,
+    candidates moved to the image nearest their cluster); an offset box of side 1.7."""
+    box = (-1.0, 0.5, 2.0, 1.7)
+    x, f, _ = inputs(3000, 58, "fp32", box=box)
+    u, _ = run(kernel, x, f, None, "fp32", box=box, tol=2e-6)
+    ref = oracle(kernel, x - np.asarray(box[:3]), f, L=box[3])
+    assert rel_l2(u, ref) <= 2e-6
+    assert rel_max(u, ref) <= 2e-6
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 5e-8), ("fp32", 5e-6)])
 def test_hasimoto_single_point(prec, tol):
     """One point force: its images give -(4/3) 2.8372975 f / L (Hasimoto 1959; the
