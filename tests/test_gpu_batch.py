@@ -95,10 +95,11 @@ def test_batch_matches_single_plans(kernel, prec):
 
 
 @pytest.mark.parametrize("kernel", ["stokeslet", "rotlet"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batch_vs_direct(kernel, prec):
+@pytest.mark.parametrize("prec,R", [("fp64", 2), ("fp32", 2), ("fp32", 5)])
+def test_batch_vs_direct(kernel, prec, R):
+    """R = 5 in FP32 leaves the right-hand-side pairs (r, r + 4) of the real-space
+    sum partly filled."""
     pkg = P()
-    R = 2
     tol = 1e-6 if prec == "fp64" else 2e-6
     sizes = [400, 1200, 900]
     boxes = [(0.0, 0.0, 0.0, 1.0), (1.0, -2.0, 0.5, 2.0), (0.0, 0.0, 0.0, 0.5)]
