@@ -84,21 +84,22 @@ __device__ __forceinline__ float2 erfcx_poly2(float2 t) {
     return q;
 }
 
-// radial_ab (stokeslet, rotlet) for two distances at once, r2 > 0 in both slots
+// radial_ab (stokeslet, rotlet) for two distances at once.  A slot whose mask
+// is off gets 1/r = 0 and so a = b = 0 (r2 finite in every slot: the paired
+// path keeps empty slots at a far but finite position); q -+ c r and 2 + xi r
+// are fused multiply-adds.
 template <int PV>
-__device__ __forceinline__ void radial_ab2(const RC<float> &rk, float2 r2, float2 &a, float2 &b) {
-    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+__device__ __forceinline__ void radial_ab2(const RC<float> &rk, float2 r2, bool ua, bool ub, float2 &a,
+                                           float2 &b) {
+    const float2 rinv = make_float2(ua ? rsqrtf(r2.x) : 0.f, ub ? rsqrtf(r2.y) : 0.f);
     const float2 r = __fmul2_rn(r2, rinv);
-    const float2 x = __fmul2_rn(f2(rk.xi), r);
     const float2 ce = __fmul2_rn(f2(rk.ce), r2);
     const float2 e = make_float2(ex2_approx(ce.x), ex2_approx(ce.y));
-    const float2 y = __fadd2_rn(f2(2.0f), x);
+    const float2 y = __ffma2_rn(f2(rk.xi), r, f2(2.0f));
     const float2 q = erfcx_poly2<PV>(make_float2(__fdividef(1.0f, y.x), __fdividef(1.0f, y.y)));
-    const float2 cr = __fmul2_rn(f2(rk.c), r);
-    const float2 ncr = __fmul2_rn(f2(-rk.c), r);
     const float2 er = __fmul2_rn(e, rinv);
-    a = __fmul2_rn(er, __fadd2_rn(q, ncr));
-    b = __fmul2_rn(__fmul2_rn(er, __fmul2_rn(rinv, rinv)), __fadd2_rn(q, cr));
+    a = __fmul2_rn(er, __ffma2_rn(f2(-rk.c), r, q));
+    b = __fmul2_rn(__fmul2_rn(er, __fmul2_rn(rinv, rinv)), __ffma2_rn(f2(rk.c), r, q));
 }
 
 // The two radial multipliers of a pair at distance r (r2 = r^2 > 0):
@@ -1086,9 +1087,7 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
                         const bool ua = ia && r2.x > 0.f, ub = ib && r2.y > 0.f;
                         coinc |= (ia && !ua) || (ib && !ub);
                         float2 a, b;
-                        radial_ab2<PV>(rk, make_float2(ua ? r2.x : 1.f, ub ? r2.y : 1.f), a, b);
-                        a = make_float2(ua ? a.x : 0.f, ub ? a.y : 0.f);
-                        b = make_float2(ua ? b.x : 0.f, ub ? b.y : 0.f);
+                        radial_ab2<PV>(rk, r2, ua, ub, a, b);
                         const float2 gx = *reinterpret_cast<const float2 *>(&tp[3][2 * p2]);
                         const float2 gy = *reinterpret_cast<const float2 *>(&tp[4][2 * p2]);
                         const float2 gz = *reinterpret_cast<const float2 *>(&tp[5][2 * p2]);
