@@ -378,8 +378,25 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
                     it++;
                 }
     }
+    // the next point's position, index and self-term source are loaded one
+    // iteration ahead
+    float4 xnext = make_float4(0.f, 0.f, 0.f, 0.f);
+    int mnext = 0;
+    float fnext = 0.f;
+    if (beg + warp < end) {
+        xnext = xs[beg + warp];
+        mnext = perm[beg + warp];
+        if (lane < 3 && self_coef != 0.0) fnext = f_orig[((size_t)mnext * n_rhs + r) * 3 + lane];
+    }
     for (int n = beg + warp; n < end; n += GS_WARPS) {
-        const float4 xv = xs[n];
+        const float4 xv = xnext;
+        const int mcur = mnext;
+        const float fcur = fnext;
+        if (n + GS_WARPS < end) {
+            xnext = xs[n + GS_WARPS];
+            mnext = perm[n + GS_WARPS];
+            if (lane < 3 && self_coef != 0.0) fnext = f_orig[((size_t)mnext * n_rhs + r) * 3 + lane];
+        }
         int i0[3];
         unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
         if (lane < P) {
@@ -421,9 +438,9 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
             acc2 += __shfl_xor_sync(FULL, acc2, o);
         }
         if (lane < 3) {
-            const size_t o3 = ((size_t)perm[n] * n_rhs + r) * 3 + lane;
+            const size_t o3 = ((size_t)mcur * n_rhs + r) * 3 + lane;
             double o = (double)(lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2));
-            if (self_coef != 0.0) o += self_coef * (double)f_orig[o3];
+            if (self_coef != 0.0) o += self_coef * (double)fcur;
             u[o3] = (float)o;
         }
         __syncwarp();
