@@ -25,7 +25,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 
 #ifndef SE_COL_NB
-#define SE_COL_NB 64
+#define SE_COL_NB 128
 #endif
 
 template <int P, int TE>
@@ -528,6 +528,88 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_bspread_col(const BSys<fl
                            B.grid + (size_t)it.z * 3 * Mf3);
 }
 
+// Batched spreading with the right-hand sides inside the item: one CTA per
+// (system, tile), the points' positions and Gaussian weights staged once when
+// the tile holds at most NB points (else once per batch of NB), then per
+// right-hand side only the sources are loaded, the columns accumulated and
+// added to that right-hand side's grids.  items: the (system, tile, rhs)
+// list with the right-hand side innermost; block b takes item b * n_rhs.
+template <int P, int TE>
+__global__ void __launch_bounds__(ColCfg<P, TE>::NT, 2) k_bspread_col_rhs(const BSys<float> *__restrict__ sys,
+                                                                         const int4 *__restrict__ items,
+                                                                         const int *__restrict__ tile_start,
+                                                                         int n_rhs, const float4 *__restrict__ xs,
+                                                                         const float4 *__restrict__ fs) {
+    using C = ColCfg<P, TE>;
+    constexpr int PT = C::PT, NB = C::NB;
+    static_assert(TE == 8, "the unrolled z offsets cover tiles of 8");
+    __shared__ __align__(16) ColStage<P, TE> S;
+    const int4 it = items[(size_t)blockIdx.x * n_rhs];
+    const BSys<float> &B = sys[it.x];
+    const int key = B.tile_base + it.y;
+    const int beg = tile_start[key], end = tile_start[key + 1];
+    if (beg == end) return;
+    const GP<float> g = B.g;
+    const int tile = it.y, tid = threadIdx.x;
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
+    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
+    const bool own = tid < PT * PT;
+    const int cx = tid % PT, cy = tid / PT;
+    const bool once = end - beg <= NB;
+    if (once) {
+        if (tid < end - beg) stage_point<P, TE>(S, g, tid, beg + tid, gx0, gy0, gz0, xs);
+        __syncthreads();
+        stage_weights<P, TE>(S, g, end - beg);
+    }
+    const size_t Mf = g.mf[0], Mf2 = Mf * g.mf[1], Mf3 = vol(g);
+    for (int r = 0; r < n_rhs; r++) {
+        float a0[PT], a1[PT], a2[PT];
+#pragma unroll
+        for (int z = 0; z < PT; z++) a0[z] = a1[z] = a2[z] = 0.0f;
+        for (int b0 = beg; b0 < end; b0 += NB) {
+            const int nb = min(NB, end - b0);
+            if (tid < nb) {
+                if (!once) stage_point<P, TE>(S, g, tid, b0 + tid, gx0, gy0, gz0, xs);
+                S.src[tid] = fs[(size_t)(b0 + tid) * n_rhs + r];
+            }
+            __syncthreads();
+            if (!once) {
+                stage_weights<P, TE>(S, g, nb);
+                __syncthreads();
+            }
+            if (own) {
+                for (int j = 0; j < nb; j++) {
+                    const int oxy = S.oxy[j];
+                    const int kx = cx - (oxy & 255), ky = cy - (oxy >> 8);
+                    if ((unsigned)kx < (unsigned)P && (unsigned)ky < (unsigned)P) {
+                        const float w = S.wx[j][kx] * S.wy[j][ky];
+                        const float4 sv = S.src[j];
+                        const float s0 = sv.x * w, s1 = sv.y * w, s2 = sv.z * w;
+                        const int oz = S.oz[j];
+                        SE_COL_CASES(col_add, a0, a1, a2, s0, s1, s2, S.wz[j])
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (own) {
+            const int gx = gx0 + cx, gy = gy0 + cy;
+            if (gx < g.mt[0] && gy < g.mt[1]) {
+                float *base = B.grid + (size_t)r * 3 * Mf3 + ((size_t)gz0 * g.mf[1] + gy) * Mf + gx;
+#pragma unroll
+                for (int z = 0; z < PT; z++) {
+                    if (gz0 + z < g.mt[2]) {
+                        float *pz = base + (size_t)z * Mf2;
+                        if (a0[z] != 0.0f) atomicAdd(pz, a0[z]);
+                        if (a1[z] != 0.0f) atomicAdd(pz + Mf3, a1[z]);
+                        if (a2[z] != 0.0f) atomicAdd(pz + 2 * Mf3, a2[z]);
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <int P, int TE>
 __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_bgather_col(const BSys<float> *__restrict__ sys,
                                                                      const int4 *__restrict__ items,
@@ -593,10 +675,16 @@ struct GatherRun {
 };
 
 template <int P, int TE>
+#ifndef SE_BSPREAD_RHS
+#define SE_BSPREAD_RHS 1
+#endif
 struct BSpreadRun {
     static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
                            const float4 *xs, const float4 *fs, cudaStream_t st) {
-        k_bspread_col<P, TE><<<nitems, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
+        if (SE_BSPREAD_RHS)
+            k_bspread_col_rhs<P, TE><<<nitems / n_rhs, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
+        else
+            k_bspread_col<P, TE><<<nitems, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
         return cudaGetLastError();
     }
 };
