@@ -847,7 +847,8 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     __shared__ int2 seg_all[WPB][NSEG];
     __shared__ int pre_all[WPB][NSEG + 1];
     __shared__ float box_all[WPB][6];
-    // PAIR (stokeslet, rotlet): targets t and t + 4 side by side, [component][2 p + slot]
+    // PAIR (stokeslet, rotlet): neighbouring targets 2p and 2p + 1 side by side
+    // (their cutoff tests mostly agree), [component][2 p + slot] = [component][t]
     constexpr bool PAIR = !STR && SE_RS_PAIR;
     __shared__ __align__(8) float tp_all[PAIR ? WPB : 1][6][TC];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -880,7 +881,7 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
         if (STR) tq[lane] = qo;
         if (PAIR) {
             // empty slots far away but finite: a masked slot's products stay 0
-            const int o = 2 * (lane & 3) + (lane >> 2);  // pair p = t mod 4, slot t / 4
+            const int o = lane;  // pair p = t / 2, slot t mod 2
             const bool real = lane < cl.y;
             tp[0][o] = real ? xo.x : 1e18f;
             tp[1][o] = real ? xo.y : 1e18f;
@@ -1000,7 +1001,7 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     float acc[TC][3];
 #pragma unroll
     for (int t = 0; t < TC; t++) acc[t][0] = acc[t][1] = acc[t][2] = 0.f;
-    float2 accp[TC / 2][3];  // PAIR: targets (p, p + 4)
+    float2 accp[TC / 2][3];  // PAIR: targets (2p, 2p + 1)
 #pragma unroll
     for (int p2 = 0; p2 < TC / 2; p2++) accp[p2][0] = accp[p2][1] = accp[p2][2] = f2(0.f);
     bool coinc = false;
@@ -1076,11 +1077,11 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
                         dz.y -= g.len[2] * rintf(dz.y * g.ilen[2]);
                     }
                     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-                    bool ia = r2.x <= rk.rc2 && p2 < vs, ib = r2.y <= rk.rc2 && p2 + TC / 2 < vs;
+                    bool ia = r2.x <= rk.rc2 && 2 * p2 < vs, ib = r2.y <= rk.rc2 && 2 * p2 + 1 < vs;
                     if (PER && wide) {
                         // the empty slots' far position folds back under nearest images
-                        ia = ia && p2 < cl.y;
-                        ib = ib && p2 + TC / 2 < cl.y;
+                        ia = ia && 2 * p2 < cl.y;
+                        ib = ib && 2 * p2 + 1 < cl.y;
                     }
                     if (ia || ib) {
                         // zero distance: a distinct point at the same position, skipped
@@ -1187,8 +1188,8 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
         for (int p2 = 0; p2 < TC / 2; p2++)
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                acc[p2][d] = accp[p2][d].x;
-                acc[p2 + TC / 2][d] = accp[p2][d].y;
+                acc[2 * p2][d] = accp[p2][d].x;
+                acc[2 * p2 + 1][d] = accp[p2][d].y;
             }
     }
     // sum the accumulators over the lanes: a reduce-scatter over lane bits 4,
