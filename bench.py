@@ -36,7 +36,7 @@ FLOP_PER_PAIR = 58
 # DRAM bytes (read + write) of one launch of the FP32 stokeslet real-space kernel on
 # this workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 # Set to None whenever that kernel changes, until it is captured again.
-REAL_TRAFFIC_BYTES = 51_192_320 + 3_144_960
+REAL_TRAFFIC_BYTES = None
 
 
 def pair_fraction_unit_cube(r: float) -> float:

@@ -46,7 +46,11 @@ struct se_batch_s {
         void *grid = nullptr, *spec = nullptr, *wgrid = nullptr;
         cufftHandle fwd = 0, inv = 0;
         bool have_fwd = false, have_inv = false;
+        // FP32 (ilv): grids interleaved plane by plane, zero-padding-aware transforms
+        cufftHandle f2d = 0, i2d = 0, zc = 0;
+        size_t G = 0, mt2 = 0;  // grids of the class, nonzero z-planes
     };
+    bool ilv = false;
     std::vector<SizeClass> classes;
     void *work = nullptr;
     // CUDA graph of one evaluation, valid for the pointers it was captured with
@@ -70,6 +74,9 @@ void free_batch(se_batch_s *B) {
     for (auto &c : B->classes) {
         if (c.have_fwd) cufftDestroy(c.fwd);
         if (c.have_inv) cufftDestroy(c.inv);
+        if (c.f2d) cufftDestroy(c.f2d);
+        if (c.i2d) cufftDestroy(c.i2d);
+        if (c.zc) cufftDestroy(c.zc);
         cudaFree(c.grid);
         cudaFree(c.spec);
         cudaFree(c.wgrid);
@@ -88,7 +95,7 @@ template <typename T>
 void fill_sys(se_batch_s *B, std::vector<BSys<T>> &sys, const std::vector<int> &tile_base,
               const std::vector<int> &cell_base, const std::vector<int> &row_base, const std::vector<int> &blk_base,
               const std::vector<int> &zblk_base, const std::vector<void *> &grid, const std::vector<void *> &spec,
-              const std::vector<void *> &wgrid) {
+              const std::vector<void *> &wgrid, const std::vector<std::array<size_t, 4>> &strides) {
     sys.resize(B->S);
     for (int s = 0; s < B->S; s++) {
         se_plan_s *p = B->sub[s];
@@ -101,6 +108,10 @@ void fill_sys(se_batch_s *B, std::vector<BSys<T>> &sys, const std::vector<int> &
         Y.grid = (T *)grid[s];
         Y.spec = (cplx<T> *)spec[s];
         Y.wgrid = (T *)wgrid[s];
+        Y.gzs = strides[s][0];
+        Y.gcs = strides[s][1];
+        Y.szs = strides[s][2];
+        Y.scs = strides[s][3];
         Y.self_coef = (B->kernel == SE_STOKESLET) ? -4.0 * p->xi / sqrt(M_PI) : 0.0;
         Y.off = B->off_h[s];
         Y.n = B->off_h[s + 1] - B->off_h[s];
@@ -138,6 +149,18 @@ se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t 
         BCK(launch_bspread<T>(sys, B->items_d, B->nitems, B->P, B->T_, R, B->b, st));
     B->launches += 2;
     for (auto &c : B->classes) {
+        if (B->ilv) {
+            // 2D (y, x) transforms of the nonzero planes of all the class's grids,
+            // the spectra's upper z-planes zeroed, then the transform along z
+            const size_t plane_c = (size_t)c.mf[1] * (c.mf[0] / 2 + 1);
+            BCF(cufftSetStream(c.f2d, st));
+            BCF(cufftSetStream(c.zc, st));
+            BCF(cufftExecR2C(c.f2d, (cufftReal *)c.grid, (cufftComplex *)c.spec));
+            BCK(cudaMemsetAsync((cufftComplex *)c.spec + c.mt2 * c.G * plane_c, 0,
+                                (c.mf[2] - c.mt2) * c.G * plane_c * sizeof(cufftComplex), st));
+            BCF(cufftExecC2C(c.zc, (cufftComplex *)c.spec, (cufftComplex *)c.spec, CUFFT_FORWARD));
+            continue;
+        }
         BCF(cufftSetStream(c.fwd, st));
         if (sizeof(T) == 4)
             BCF(cufftExecR2C(c.fwd, (cufftReal *)c.grid, (cufftComplex *)c.spec));
@@ -147,6 +170,14 @@ se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t 
     BCK(launch_bscale<T>(B->kernel, sys, B->blk_base_d, S, B->nblk_scale, R, st));
     B->launches += 1;
     for (auto &c : B->classes) {
+        if (B->ilv) {
+            // back along z, then 2D on only the planes the gather reads
+            BCF(cufftSetStream(c.zc, st));
+            BCF(cufftSetStream(c.i2d, st));
+            BCF(cufftExecC2C(c.zc, (cufftComplex *)c.spec, (cufftComplex *)c.spec, CUFFT_INVERSE));
+            BCF(cufftExecC2R(c.i2d, (cufftComplex *)c.spec, (cufftReal *)c.wgrid));
+            continue;
+        }
         BCF(cufftSetStream(c.inv, st));
         if (sizeof(T) == 4)
             BCF(cufftExecC2R(c.inv, (cufftComplex *)c.spec, (cufftReal *)c.wgrid));
@@ -254,6 +285,10 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
     }
     const size_t esz = (prec == SE_FP32) ? 4 : 8;
     std::vector<void *> grid(S), spec(S), wgrid(S);
+    std::vector<std::array<size_t, 4>> strides(S);
+    // FP32 with the register-column and shared-memory kernels: grids of a size
+    // class interleaved plane by plane, zero-padding-aware transforms
+    B->ilv = (prec == SE_FP32) && B->colk;
     size_t work_max = 0;
     for (auto &kv : by_mf) {
         se_batch_s::SizeClass c;
@@ -263,6 +298,45 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
         se_batch_s::SizeClass &C = B->classes.back();
         const size_t Mf3 = (size_t)C.mf[0] * C.mf[1] * C.mf[2], nk = (size_t)C.mf[2] * C.mf[1] * (C.mf[0] / 2 + 1);
         const size_t per = (size_t)3 * R;
+        if (B->ilv) {
+            C.G = (size_t)C.count * per;
+            C.mt2 = (size_t)B->sub[kv.second[0]]->mt[2];
+            const size_t plane_r = (size_t)C.mf[1] * C.mf[0], plane_c = (size_t)C.mf[1] * (C.mf[0] / 2 + 1);
+            const size_t nreal = C.G * C.mt2 * plane_r;  // [z < mt2][grid][y][x]
+            if (bmalloc(&C.grid, nreal * esz) || bmalloc(&C.spec, C.G * C.mf[2] * plane_c * 2 * esz) ||
+                bmalloc(&C.wgrid, nreal * esz) || cudaMemset(C.grid, 0, nreal * esz)) {
+                cudaGetLastError();
+                return fail(SE_ERR_OOM, "batch: grid allocation failed");
+            }
+            for (int j = 0; j < C.count; j++) {
+                const int s = kv.second[j];
+                grid[s] = (char *)C.grid + j * per * plane_r * esz;
+                spec[s] = (char *)C.spec + j * per * plane_c * 2 * esz;
+                wgrid[s] = (char *)C.wgrid + j * per * plane_r * esz;
+                strides[s] = {C.G * plane_r, plane_r, C.G * plane_c, plane_c};
+            }
+            long long n2[2] = {C.mf[1], C.mf[0]}, re2[2] = {C.mf[1], C.mf[0]}, ce2[2] = {C.mf[1], C.mf[0] / 2 + 1};
+            long long nz[1] = {C.mf[2]};
+            const long long np = (long long)(C.G * C.mt2), ncol = (long long)(C.G * plane_c);
+            size_t ws = 0;
+            BCF(cufftCreate(&C.f2d));
+            BCF(cufftSetAutoAllocation(C.f2d, 0));
+            BCF(cufftMakePlanMany64(C.f2d, 2, n2, re2, 1, (long long)plane_r, ce2, 1, (long long)plane_c, CUFFT_R2C,
+                                    np, &ws));
+            work_max = std::max(work_max, ws);
+            BCF(cufftCreate(&C.i2d));
+            BCF(cufftSetAutoAllocation(C.i2d, 0));
+            BCF(cufftMakePlanMany64(C.i2d, 2, n2, ce2, 1, (long long)plane_c, re2, 1, (long long)plane_r, CUFFT_C2R,
+                                    np, &ws));
+            work_max = std::max(work_max, ws);
+            BCF(cufftCreate(&C.zc));
+            BCF(cufftSetAutoAllocation(C.zc, 0));
+            BCF(cufftMakePlanMany64(C.zc, 1, nz, nz, ncol, 1, nz, ncol, 1, CUFFT_C2C, ncol, &ws));
+            work_max = std::max(work_max, ws);
+            continue;
+        }
+        for (int j = 0; j < C.count; j++)
+            strides[kv.second[j]] = {(size_t)C.mf[0] * C.mf[1], Mf3, (size_t)C.mf[1] * (C.mf[0] / 2 + 1), nk};
         if (bmalloc(&C.grid, C.count * per * Mf3 * esz) || bmalloc(&C.spec, C.count * per * nk * 2 * esz) ||
             bmalloc(&C.wgrid, C.count * per * Mf3 * esz) || cudaMemset(C.grid, 0, C.count * per * Mf3 * esz)) {
             cudaGetLastError();
@@ -296,6 +370,12 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
         return fail(SE_ERR_OOM, "batch: cuFFT work area allocation failed");
     }
     for (auto &C : B->classes) {
+        if (B->ilv) {
+            BCF(cufftSetWorkArea(C.f2d, B->work));
+            BCF(cufftSetWorkArea(C.i2d, B->work));
+            BCF(cufftSetWorkArea(C.zc, B->work));
+            continue;
+        }
         BCF(cufftSetWorkArea(C.fwd, B->work));
         BCF(cufftSetWorkArea(C.inv, B->work));
     }
@@ -331,12 +411,12 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
             break;
         if (prec == SE_FP32) {
             std::vector<BSys<float>> sys;
-            fill_sys<float>(B, sys, tile_base, cell_base, row_base, blk_base, zblk_base, grid, spec, wgrid);
+            fill_sys<float>(B, sys, tile_base, cell_base, row_base, blk_base, zblk_base, grid, spec, wgrid, strides);
             if ((e = bmalloc(&B->sys_d, S * sizeof(BSys<float>)))) break;
             e = cudaMemcpy(B->sys_d, sys.data(), S * sizeof(BSys<float>), cudaMemcpyHostToDevice);
         } else {
             std::vector<BSys<double>> sys;
-            fill_sys<double>(B, sys, tile_base, cell_base, row_base, blk_base, zblk_base, grid, spec, wgrid);
+            fill_sys<double>(B, sys, tile_base, cell_base, row_base, blk_base, zblk_base, grid, spec, wgrid, strides);
             if ((e = bmalloc(&B->sys_d, S * sizeof(BSys<double>)))) break;
             e = cudaMemcpy(B->sys_d, sys.data(), S * sizeof(BSys<double>), cudaMemcpyHostToDevice);
         }

@@ -335,7 +335,8 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
                                                  const float4 *__restrict__ xs, const int *__restrict__ perm,
                                                  const float *__restrict__ w, int n_rhs, int r,
                                                  const float *__restrict__ f_orig, double self_coef,
-                                                 float *__restrict__ u) {
+                                                 float *__restrict__ u, size_t gzs, size_t gcs) {
+    // gzs, gcs: the grids' z-plane and component strides
     constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
     constexpr int ROWS = 3 * PT * PT, PLANE = PT * PX, COMP = PT * PLANE;
     extern __shared__ __align__(16) float sg[];  // [c][z][y][x], x pitch PX
@@ -343,7 +344,7 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
-    const size_t Mf = g.mf[0], Mf3 = vol(g);
+    const size_t Mf = g.mf[0];
     // flat copy of the block (x fastest), several independent loads in flight per thread
 #pragma unroll 8
     for (int e = threadIdx.x; e < ROWS * PT; e += GS_WARPS * 32) {
@@ -351,7 +352,7 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
                   y = zy - z * PT;
         const int gz = gz0 + z, gy = gy0 + y, gx = gx0 + x;
         sg[row * PX + x] = (gz < g.mt[2] && gy < g.mt[1] && gx < g.mt[0])
-                               ? __ldg(w + (size_t)c * Mf3 + ((size_t)gz * g.mf[1] + gy) * Mf + gx)
+                               ? __ldg(w + (size_t)c * gcs + (size_t)gz * gzs + (size_t)gy * Mf + gx)
                                : 0.0f;
     }
     __syncthreads();
@@ -457,7 +458,8 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_gather_smem(GP<float> g, cons
     const int tile = blockIdx.x;
     const int beg = tile_start[tile], end = tile_start[tile + 1];
     if (beg == end) return;
-    gather_smem_body<P, TE>(g, tile, beg, end, xs, perm, w, 1, 0, f_orig, self_coef, u);
+    gather_smem_body<P, TE>(g, tile, beg, end, xs, perm, w, 1, 0, f_orig, self_coef, u,
+                            (size_t)g.mf[0] * g.mf[1], vol(g));
 }
 
 template <int P, int TE>
@@ -474,9 +476,8 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_bgather_smem(const BSys<float
     const int beg = tile_start[key], end = tile_start[key + 1];
     if (beg == end) return;
     const GP<float> g = B.g;
-    const size_t Mf3 = vol(g);
-    gather_smem_body<P, TE>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * Mf3, n_rhs, it.z, f_orig,
-                            B.self_coef, u);
+    gather_smem_body<P, TE>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * B.gcs, n_rhs, it.z, f_orig,
+                            B.self_coef, u, B.gzs, B.gcs);
 }
 
 template <int P, int TE>
@@ -511,23 +512,6 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_gather_col(GP<float> g, c
 }
 
 // Batched: one CTA per item (system, tile, right-hand side).
-template <int P, int TE>
-__global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_bspread_col(const BSys<float> *__restrict__ sys,
-                                                                     const int4 *__restrict__ items,
-                                                                     const int *__restrict__ tile_start, int n_rhs,
-                                                                     const float4 *__restrict__ xs,
-                                                                     const float4 *__restrict__ fs) {
-    const int4 it = items[blockIdx.x];
-    const BSys<float> &B = sys[it.x];
-    const int key = B.tile_base + it.y;
-    const int beg = tile_start[key], end = tile_start[key + 1];
-    if (beg == end) return;
-    const GP<float> g = B.g;
-    const size_t Mf3 = vol(g);
-    spread_col_body<P, TE>(g, it.y, beg, end, 0, false, xs, fs, n_rhs, it.z, nullptr,
-                           B.grid + (size_t)it.z * 3 * Mf3);
-}
-
 // Batched spreading with the right-hand sides inside the item: one CTA per
 // (system, tile), the points' positions and Gaussian weights staged once when
 // the tile holds at most NB points (else once per batch of NB), then per
@@ -561,7 +545,7 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT, 2) k_bspread_col_rhs(const 
         __syncthreads();
         stage_weights<P, TE>(S, g, end - beg);
     }
-    const size_t Mf = g.mf[0], Mf2 = Mf * g.mf[1], Mf3 = vol(g);
+    const size_t Mf = g.mf[0], Mf2 = B.gzs, Mf3 = B.gcs;  // z-plane and component strides
     for (int r = 0; r < n_rhs; r++) {
         float a0[PT], a1[PT], a2[PT];
 #pragma unroll
@@ -595,7 +579,7 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT, 2) k_bspread_col_rhs(const 
         if (own) {
             const int gx = gx0 + cx, gy = gy0 + cy;
             if (gx < g.mt[0] && gy < g.mt[1]) {
-                float *base = B.grid + (size_t)r * 3 * Mf3 + ((size_t)gz0 * g.mf[1] + gy) * Mf + gx;
+                float *base = B.grid + (size_t)r * 3 * Mf3 + (size_t)gz0 * Mf2 + (size_t)gy * Mf + gx;
 #pragma unroll
                 for (int z = 0; z < PT; z++) {
                     if (gz0 + z < g.mt[2]) {
@@ -608,25 +592,6 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT, 2) k_bspread_col_rhs(const 
             }
         }
     }
-}
-
-template <int P, int TE>
-__global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_bgather_col(const BSys<float> *__restrict__ sys,
-                                                                     const int4 *__restrict__ items,
-                                                                     const int *__restrict__ tile_start, int n_rhs,
-                                                                     const float4 *__restrict__ xs,
-                                                                     const int *__restrict__ perm,
-                                                                     const float *__restrict__ f_orig,
-                                                                     float *__restrict__ u) {
-    const int4 it = items[blockIdx.x];
-    const BSys<float> &B = sys[it.x];
-    const int key = B.tile_base + it.y;
-    const int beg = tile_start[key], end = tile_start[key + 1];
-    if (beg == end) return;
-    const GP<float> g = B.g;
-    const size_t Mf3 = vol(g);
-    gather_col_body<P, TE>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * Mf3, n_rhs, it.z, f_orig,
-                           B.self_coef, u);
 }
 
 // Dispatch on the (even) support P, 4 <= P <= 16.
@@ -675,33 +640,24 @@ struct GatherRun {
 };
 
 template <int P, int TE>
-#ifndef SE_BSPREAD_RHS
-#define SE_BSPREAD_RHS 1
-#endif
 struct BSpreadRun {
     static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
                            const float4 *xs, const float4 *fs, cudaStream_t st) {
-        if (SE_BSPREAD_RHS)
-            k_bspread_col_rhs<P, TE><<<nitems / n_rhs, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
-        else
-            k_bspread_col<P, TE><<<nitems, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
+        k_bspread_col_rhs<P, TE><<<nitems / n_rhs, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
         return cudaGetLastError();
     }
 };
 
 template <int P, int TE>
 struct BGatherRun {
+    // the plane-interleaved FP32 batch grids are read by the shared-memory gather
     static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
                            const float4 *xs, const int *perm, const float *f, float *u, cudaStream_t st) {
-        if (SE_GATHER_SMEM) {
-            const size_t smem = gather_smem_bytes<P, TE>();
-            cudaError_t e = cudaFuncSetAttribute(k_bgather_smem<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e) return e;
-            k_bgather_smem<P, TE><<<nitems, GS_WARPS * 32, smem, st>>>(sys, items, ts, n_rhs, xs, perm, f, u);
-        } else {
-            k_bgather_col<P, TE><<<nitems, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, perm, f, u);
-        }
+        const size_t smem = gather_smem_bytes<P, TE>();
+        cudaError_t e = cudaFuncSetAttribute(k_bgather_smem<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e) return e;
+        k_bgather_smem<P, TE><<<nitems, GS_WARPS * 32, smem, st>>>(sys, items, ts, n_rhs, xs, perm, f, u);
         return cudaGetLastError();
     }
 };

@@ -45,9 +45,18 @@ __host__ __device__ inline size_t half_spectrum(const ScaleConst &sc) {
 // source components (each group nc consecutive spectra of nk points).
 template <typename T, int KERNEL>
 __device__ __forceinline__ void scale_point(const ScaleConst &sc, const T *__restrict__ ghat,
-                                            cplx<T> *__restrict__ spec, size_t idx, int ngroups) {
+                                            cplx<T> *__restrict__ spec, size_t idx, int ngroups,
+                                            size_t scs = 0, size_t szs = 0) {
+    // scs, szs: the spectra's component and z-plane strides (0: one whole
+    // spectrum after the other, idx its own offset)
     using C = cplx<T>;
-    const size_t nk = half_spectrum(sc);
+    const size_t plane = (size_t)sc.mf[1] * sc.nxh;
+    const size_t nk = scs ? scs : half_spectrum(sc);
+    size_t off = idx;
+    if (szs) {
+        const size_t kz = idx / plane;
+        off = kz * szs + (idx - kz * plane);
+    }
     T kv[3];
     const T G = ghat[kpoint<T>(sc, idx, kv)];
     T k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
@@ -55,7 +64,7 @@ __device__ __forceinline__ void scale_point(const ScaleConst &sc, const T *__res
     if (KERNEL != SE_ROTLET) F *= (T(1) + k2 * (T)sc.inv4xi2);
     constexpr int NCG = (KERNEL == SE_STRESSLET) ? 6 : 3;
     for (int grp = 0; grp < ngroups; grp++) {
-        C *w0 = spec + (size_t)grp * NCG * nk + idx;
+        C *w0 = spec + (size_t)grp * NCG * nk + off;
         if (KERNEL == SE_STOKESLET) {
             C g[3];
             for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
@@ -168,7 +177,7 @@ __global__ void k_bscale(const BSys<T> *__restrict__ sys, const int *__restrict_
     const size_t nk = half_spectrum(sc);
     const size_t idx = (size_t)(blockIdx.x - blk_base[s]) * blockDim.x + threadIdx.x;
     if (idx >= nk) return;
-    scale_point<T, KERNEL>(sc, B.ghat, B.spec, idx, n_rhs);
+    scale_point<T, KERNEL>(sc, B.ghat, B.spec, idx, n_rhs, B.scs, B.szs);
 }
 
 }  // namespace

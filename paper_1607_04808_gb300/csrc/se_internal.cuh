@@ -108,6 +108,14 @@ struct BSys {
     T *grid;           // spread grids: 3 n_rhs grids of mf_x mf_y mf_z (zero padded)
     cplx<T> *spec;     // their spectra: 3 n_rhs x mf_z x mf_y x (mf_x/2+1)
     T *wgrid;          // inverse transforms: 3 n_rhs grids
+    // strides (elements): real grids (grid, wgrid) between z-planes and between
+    // the system's 3 n_rhs components, and the same for the spectra.  FP64
+    // batches store each grid whole (z stride mf_x mf_y, component stride
+    // mf_x mf_y mf_z); FP32 batches interleave the grids of an FFT size class
+    // plane by plane, [z][grid][y][x], keeping only the z < mt_z planes of the
+    // real grids (z stride: the class's grids times a plane, component stride:
+    // a plane)
+    size_t gzs, gcs, szs, scs;
     double self_coef;  // -4 xi / sqrt(pi) (stokeslet), 0 otherwise
     int off, n;        // points [off, off + n) of the concatenated and of the sorted order
     int tile_base, cell_base, row_base;

@@ -242,7 +242,10 @@ __global__ void k_bzero_octant(const BSys<T> *__restrict__ sys, const int *__res
     const BSys<T> &B = sys[s];
     const size_t row = (size_t)(blockIdx.x - zblk_base[s]) * blockDim.y + threadIdx.y;
     if (row >= (size_t)3 * n_rhs * B.g.mt[1] * B.g.mt[2]) return;
-    zero_rows(B.grid, B.g.mt, B.g.mf, row);
+    const int y = row % B.g.mt[1], z = (row / B.g.mt[1]) % B.g.mt[2];
+    const size_t c = row / ((size_t)B.g.mt[1] * B.g.mt[2]);
+    T *p = B.grid + c * B.gcs + z * B.gzs + (size_t)y * B.g.mf[0];
+    for (int x = threadIdx.x; x < B.g.mt[0]; x += blockDim.x) p[x] = T(0);
 }
 
 template <typename T, int NIT>
