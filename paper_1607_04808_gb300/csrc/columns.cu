@@ -365,19 +365,21 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
         kxs[it] = kys[it] = 0;
     }
     {
+        // offsets o = ky * PX + kx = lane (mod 32), in increasing order
         int it = 0;
-        for (int ky = 0; ky < P; ky++)
-            for (int kx = 0; kx < P; kx++)
-                if ((ky * PX + kx) % 32 == lane) {
+        for (int o = lane; o < P * PX; o += 32) {
+            const int ky = o / PX, kx = o - ky * PX;
+            if (kx < P) {
 #pragma unroll
-                    for (int q = 0; q < NIT; q++)
-                        if (q == it) {
-                            kxs[q] = kx;
-                            kys[q] = ky;
-                            val[q] = true;
-                        }
-                    it++;
-                }
+                for (int q = 0; q < NIT; q++)
+                    if (q == it) {
+                        kxs[q] = kx;
+                        kys[q] = ky;
+                        val[q] = true;
+                    }
+                it++;
+            }
+        }
     }
     // the next point's position, index and self-term source are loaded one
     // iteration ahead
