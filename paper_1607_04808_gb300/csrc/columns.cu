@@ -18,6 +18,11 @@
 // then one shared-memory atomic per warp and component.
 #include "se_internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 namespace se {
 
 namespace {
@@ -306,7 +311,8 @@ constexpr int GS_WARPS = SE_GS_WARPS;
 // lane: the lanes of a warp read column (kx, ky) at offset ky * pitch + kx, so
 // each lane takes the columns whose offset is its own lane id mod 32 (one
 // shared-memory bank per lane, no conflicts); the pitch >= PT minimising the
-// largest such class.
+// largest such class, a multiple of 4 floats (the 16-byte rows of a tensor
+// copy's box).
 template <int P, int PT>
 struct GsLayout {
     static constexpr int count(int pitch) {
@@ -321,8 +327,9 @@ struct GsLayout {
         return worst;
     }
     static constexpr int best_pitch() {
-        int bp = PT, bn = count(PT);
-        for (int q = PT + 1; q <= PT + 8; q++)
+        const int q0 = (PT + 3) / 4 * 4;
+        int bp = q0, bn = count(q0);
+        for (int q = q0 + 4; q <= q0 + 8; q += 4)
             if (count(q) < bn) { bn = count(q); bp = q; }
         return bp;
     }
@@ -330,32 +337,85 @@ struct GsLayout {
     static constexpr int NIT = count(PX);
 };
 
-template <int P, int TE>
+// Bounded wait on phase `phase` of a shared-memory mbarrier; false when the
+// iteration limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int limit) {
+    for (int it = 0; it < limit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+constexpr int GS_WAIT_LIMIT = 1 << 20;
+
+// TMA (TMA = true): the block arrives by one tensor copy, a box of PX x PT x PT
+// x 3 floats at (gx0, gy0, gz0, 0) of the grids seen as a 4-D tensor of extent
+// (Mt_x, Mt_y, Mt_z, 3); the copy engine fills the part outside with zeros.
+// gx0 is a multiple of TE = 8, so the box starts on a 32-byte boundary.
+template <int P, int TE, bool TMA>
 __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, int beg, int end,
                                                  const float4 *__restrict__ xs, const int *__restrict__ perm,
                                                  const float *__restrict__ w, int n_rhs, int r,
                                                  const float *__restrict__ f_orig, double self_coef,
-                                                 float *__restrict__ u, size_t gzs, size_t gcs) {
+                                                 float *__restrict__ u, size_t gzs, size_t gcs,
+                                                 const void *tmap = nullptr, int *status = nullptr) {
     // gzs, gcs: the grids' z-plane and component strides
     constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
     constexpr int ROWS = 3 * PT * PT, PLANE = PT * PX, COMP = PT * PLANE;
-    extern __shared__ __align__(16) float sg[];  // [c][z][y][x], x pitch PX
+    extern __shared__ __align__(128) float sg_raw[];  // [c][z][y][x], x pitch PX
     __shared__ float swt[GS_WARPS][3][P];
+    __shared__ __align__(8) uint64_t bar_mem;
+    // the tensor copy's destination starts on a 128-byte boundary
+    float *sg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(sg_raw) + 127) & ~uintptr_t(127));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
     const size_t Mf = g.mf[0];
-    // flat copy of the block (x fastest), several independent loads in flight per thread
+    if constexpr (TMA) {
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_mem);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            constexpr uint32_t bytes = (uint32_t)(3 * PT * PT * PX * sizeof(float));
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"((uint32_t)__cvta_generic_to_shared(sg)),
+                "l"(reinterpret_cast<uint64_t>(tmap)), "r"(gx0), "r"(gy0), "r"(gz0), "r"(0), "r"(bar)
+                : "memory");
+        }
+        if (!mbar_wait(bar, 0, GS_WAIT_LIMIT)) {
+            // the copy did not land: report, give it one more bounded wait, leave
+            if (threadIdx.x == 0) atomicOr(status, FLAG_TIMEOUT);
+            mbar_wait(bar, 0, GS_WAIT_LIMIT);
+            return;
+        }
+    } else {
+        // flat copy of the block (x fastest), several independent loads in flight per thread
 #pragma unroll 8
-    for (int e = threadIdx.x; e < ROWS * PT; e += GS_WARPS * 32) {
-        const int row = e / PT, x = e - row * PT, c = row / (PT * PT), zy = row - c * PT * PT, z = zy / PT,
-                  y = zy - z * PT;
-        const int gz = gz0 + z, gy = gy0 + y, gx = gx0 + x;
-        sg[row * PX + x] = (gz < g.mt[2] && gy < g.mt[1] && gx < g.mt[0])
-                               ? __ldg(w + (size_t)c * gcs + (size_t)gz * gzs + (size_t)gy * Mf + gx)
-                               : 0.0f;
+        for (int e = threadIdx.x; e < ROWS * PT; e += GS_WARPS * 32) {
+            const int row = e / PT, x = e - row * PT, c = row / (PT * PT), zy = row - c * PT * PT, z = zy / PT,
+                      y = zy - z * PT;
+            const int gz = gz0 + z, gy = gy0 + y, gx = gx0 + x;
+            sg[row * PX + x] = (gz < g.mt[2] && gy < g.mt[1] && gx < g.mt[0])
+                                   ? __ldg(w + (size_t)c * gcs + (size_t)gz * gzs + (size_t)gy * Mf + gx)
+                                   : 0.0f;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // this lane's support columns: those at offset ky * PX + kx = lane (mod 32)
     int kxs[NIT], kys[NIT];
     bool val[NIT];
@@ -450,18 +510,20 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
     }
 }
 
-template <int P, int TE>
+template <int P, int TE, bool TMA>
 __global__ void __launch_bounds__(GS_WARPS * 32) k_gather_smem(GP<float> g, const int *__restrict__ tile_start,
                                                                const float4 *__restrict__ xs,
                                                                const int *__restrict__ perm,
                                                                const float *__restrict__ w,
                                                                const float *__restrict__ f_orig, double self_coef,
-                                                               float *__restrict__ u) {
+                                                               float *__restrict__ u,
+                                                               const __grid_constant__ CUtensorMap tmap,
+                                                               int *__restrict__ status) {
     const int tile = blockIdx.x;
     const int beg = tile_start[tile], end = tile_start[tile + 1];
     if (beg == end) return;
-    gather_smem_body<P, TE>(g, tile, beg, end, xs, perm, w, 1, 0, f_orig, self_coef, u,
-                            (size_t)g.mf[0] * g.mf[1], vol(g));
+    gather_smem_body<P, TE, TMA>(g, tile, beg, end, xs, perm, w, 1, 0, f_orig, self_coef, u,
+                                 (size_t)g.mf[0] * g.mf[1], vol(g), &tmap, status);
 }
 
 template <int P, int TE>
@@ -478,13 +540,14 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_bgather_smem(const BSys<float
     const int beg = tile_start[key], end = tile_start[key + 1];
     if (beg == end) return;
     const GP<float> g = B.g;
-    gather_smem_body<P, TE>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * B.gcs, n_rhs, it.z, f_orig,
-                            B.self_coef, u, B.gzs, B.gcs);
+    gather_smem_body<P, TE, false>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * B.gcs, n_rhs, it.z,
+                                   f_orig, B.self_coef, u, B.gzs, B.gcs);
 }
 
 template <int P, int TE>
 constexpr size_t gather_smem_bytes() {
-    return (size_t)3 * (TE + P - 1) * (TE + P - 1) * GsLayout<P, TE + P - 1>::PX * sizeof(float);
+    // + 128: room to align the block to 128 bytes
+    return (size_t)3 * (TE + P - 1) * (TE + P - 1) * GsLayout<P, TE + P - 1>::PX * sizeof(float) + 128;
 }
 
 template <int P, int TE>
@@ -624,16 +687,62 @@ struct SpreadRun {
 #define SE_GATHER_SMEM 1
 #endif
 
+#ifndef SE_GATHER_TMA
+#define SE_GATHER_TMA 1
+#endif
+
+// cuTensorMapEncodeTiled from the driver (through the runtime: no link to libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        }
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    return fn;
+}
+
+// The gather grids as a 4-D FP32 tensor (x, y, z, component) of extent
+// (Mt_x, Mt_y, Mt_z, 3) with row, plane and component strides Mf_x, gzs, gcs
+// (elements), read in boxes of PX x PT x PT x 3.  False when a tensor copy
+// cannot describe it (strides or base not 16-byte aligned, a box wider than
+// the grid, no encoder): the caller stages with plain loads instead.
+static bool encode_gather_map(CUtensorMap *map, const GP<float> &g, const float *w, size_t gzs, size_t gcs, int PX,
+                              int PT) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const size_t rs = (size_t)g.mf[0] * sizeof(float), ps = gzs * sizeof(float), cs = gcs * sizeof(float);
+    if ((reinterpret_cast<uintptr_t>(w) & 15) || (rs & 15) || (ps & 15) || (cs & 15)) return false;
+    if (g.mt[0] < PX || g.mt[1] < PT || g.mt[2] < PT) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.mt[0], (cuuint64_t)g.mt[1], (cuuint64_t)g.mt[2], 3};
+    const cuuint64_t strides[3] = {rs, ps, cs};
+    const cuuint32_t box[4] = {(cuuint32_t)PX, (cuuint32_t)PT, (cuuint32_t)PT, 3};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(w), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int P, int TE>
 struct GatherRun {
     static cudaError_t run(const GP<float> g, int ntiles, const int *ts, const float4 *xs, const int *perm,
-                           const float *w, const float *f, double self_coef, float *u, cudaStream_t st) {
+                           const float *w, const float *f, double self_coef, float *u, int *status,
+                           cudaStream_t st) {
         if (SE_GATHER_SMEM) {
+            constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX;
             const size_t smem = gather_smem_bytes<P, TE>();
-            cudaError_t e = cudaFuncSetAttribute(k_gather_smem<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
+            alignas(64) CUtensorMap map;
+            memset(&map, 0, sizeof(map));
+            const bool tma = SE_GATHER_TMA && encode_gather_map(&map, g, w, (size_t)g.mf[0] * g.mf[1], vol(g), PX, PT);
+            auto kern = tma ? k_gather_smem<P, TE, true> : k_gather_smem<P, TE, false>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e) return e;
-            k_gather_smem<P, TE><<<ntiles, GS_WARPS * 32, smem, st>>>(g, ts, xs, perm, w, f, self_coef, u);
+            kern<<<ntiles, GS_WARPS * 32, smem, st>>>(g, ts, xs, perm, w, f, self_coef, u, map, status);
         } else {
             k_gather_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, ts, xs, perm, w, f, self_coef, u);
         }
@@ -689,7 +798,8 @@ cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, 
 cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &b, const void *wgrid,
                                   const float *f_orig, double self_coef, float *u) {
     cudaError_t e = with_p<GatherRun>(p->P, p->gpf, p->ntiles, (const int *)b.cnt_t, (const float4 *)b.xs_t,
-                                      (const int *)b.perm_t, (const float *)wgrid, f_orig, self_coef, u, st);
+                                      (const int *)b.perm_t, (const float *)wgrid, f_orig, self_coef, u,
+                                      p->b.status, st);
     if (!e) p->launches++;
     return e;
 }

@@ -630,6 +630,7 @@ extern "C" se_status_t se_plan_check(se_plan_t p) {
     if ((e = cudaMemcpy(&flags, p->b.status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return fail(SE_ERR_CUDA, std::string("se_plan_check: ") + cudaGetErrorString(e));
     cudaMemset(p->b.status, 0, sizeof(int));
+    if (flags & FLAG_TIMEOUT) return fail(SE_ERR_TIMEOUT, "a bounded device wait ran out (tensor copy)");
     if (flags & FLAG_OOB) return fail(SE_ERR_OUT_OF_BOX, "a point lies outside the plan's box");
     if (flags & FLAG_COINCIDENT) return fail(SE_ERR_COINCIDENT, "coincident points were skipped");
     return SE_OK;

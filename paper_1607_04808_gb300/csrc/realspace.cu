@@ -42,6 +42,10 @@ constexpr int QCAP = 64;
 #ifndef SE_RS_PAIR
 #define SE_RS_PAIR 1
 #endif
+// SE_RS_PAIR_STR: the same for the stresslet's symmetric pair sum
+#ifndef SE_RS_PAIR_STR
+#define SE_RS_PAIR_STR 1
+#endif
 constexpr int MAXROWS = 121;  // (2 reach_y + 1)(2 reach_z + 1) rows of cells at most
 
 __device__ __forceinline__ float ex2_approx(float v) {
@@ -100,6 +104,30 @@ __device__ __forceinline__ void radial_ab2(const RC<float> &rk, float2 r2, bool 
     const float2 er = __fmul2_rn(e, rinv);
     a = __fmul2_rn(er, __ffma2_rn(f2(-rk.c), r, q));
     b = __fmul2_rn(__fmul2_rn(er, __fmul2_rn(rinv, rinv)), __ffma2_rn(f2(rk.c), r, q));
+}
+
+// Stresslet multipliers of two pairs at once, scaled for the displacement d
+// itself instead of the unit vector d/r:  A = A1 / r^3 and B = A2 / r, so that
+//   T(d) . (f, q) = A (d.f)(d.q) d + B [(f.q) d + (d.q) f + (d.f) q]
+// (Eq. for T^R in Section 6).  A masked slot gets 1/r = 0, hence A = B = 0.
+template <int PV>
+__device__ __forceinline__ void radial_ab2_str(const RC<float> &rk, float2 r2, bool ua, bool ub, float2 &A,
+                                               float2 &B) {
+    const float2 rinv = make_float2(ua ? rsqrtf(r2.x) : 0.f, ub ? rsqrtf(r2.y) : 0.f);
+    const float2 r = __fmul2_rn(r2, rinv);
+    const float2 ce = __fmul2_rn(f2(rk.ce), r2);
+    const float2 e = make_float2(ex2_approx(ce.x), ex2_approx(ce.y));
+    const float2 y = __ffma2_rn(f2(rk.xi), r, f2(2.0f));
+    const float2 q = erfcx_poly2<PV>(make_float2(__fdividef(1.0f, y.x), __fdividef(1.0f, y.y)));
+    // A1 = -2 e [c r (2 x^2 + 3) + 3 Q] / r^2,  A2 = 2 xi^2 c r e,  x = xi r (from r,
+    // not r2: a masked slot far away has r = 0, and 0 * (2 xi^2 r2) could be 0 * inf)
+    const float2 cr = __fmul2_rn(f2(rk.c), r);
+    const float2 x = __fmul2_rn(f2(rk.xi), r);
+    const float2 poly = __ffma2_rn(cr, __ffma2_rn(__fmul2_rn(f2(2.0f), x), x, f2(3.0f)), __fmul2_rn(f2(3.0f), q));
+    const float2 ri2 = __fmul2_rn(rinv, rinv);
+    const float2 ri5 = __fmul2_rn(__fmul2_rn(ri2, ri2), rinv);
+    A = __fmul2_rn(__fmul2_rn(f2(-2.0f), e), __fmul2_rn(poly, ri5));
+    B = __fmul2_rn(__fmul2_rn(f2(2.0f * rk.xi2 * rk.c), e), __fmul2_rn(r, rinv));
 }
 
 // The two radial multipliers of a pair at distance r (r2 = r^2 > 0):
@@ -820,6 +848,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
 #ifndef SE_RS_SYMC_MINB
 #define SE_RS_SYMC_MINB 4
 #endif
+// the stresslet's paired pair sum needs more registers: 2 blocks of 256 (128 each)
+#ifndef SE_RS_SYMC_MINB_STR
+#define SE_RS_SYMC_MINB_STR 2
+#endif
 // PER (periodic plans, stokeslet and rotlet): the rows of cells wrap around
 // the box, each at most once, the own row rotated to the front of the stream;
 // each row's x-range wraps into at most two segments (in the own row only the
@@ -828,7 +860,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
 // nearest image when the box's half-width plus rc stays below L/2; a wider
 // cluster takes nearest images pair by pair instead.
 template <int KERNEL, int PV, bool PER = false>
-__global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
+__global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_STR : SE_RS_SYMC_MINB)
     k_real_symc(GP<float> g, RC<float> rk, const float4 *__restrict__ xs, const float4 *__restrict__ fs,
                 const float4 *__restrict__ qs, const int *__restrict__ cell_start, const int2 *__restrict__ clusters,
                 const int *__restrict__ ncl_total, const int *__restrict__ perm, float *__restrict__ u,
@@ -847,10 +879,12 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
     __shared__ int2 seg_all[WPB][NSEG];
     __shared__ int pre_all[WPB][NSEG + 1];
     __shared__ float box_all[WPB][6];
-    // PAIR (stokeslet, rotlet): neighbouring targets 2p and 2p + 1 side by side
-    // (their cutoff tests mostly agree), [component][2 p + slot] = [component][t]
-    constexpr bool PAIR = !STR && SE_RS_PAIR;
-    __shared__ __align__(8) float tp_all[PAIR ? WPB : 1][6][TC];
+    // PAIR: neighbouring targets 2p and 2p + 1 side by side (their cutoff
+    // tests mostly agree), [component][2 p + slot] = [component][t]; the
+    // components are x, f and, for the stresslet, q and f.q
+    constexpr bool PAIR = SE_RS_PAIR && (!STR || SE_RS_PAIR_STR);
+    constexpr int NTP = STR ? 10 : 6;
+    __shared__ __align__(8) float tp_all[PAIR ? WPB : 1][NTP][TC];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * WPB + wib;
     if (c >= *ncl_total) return;
@@ -889,6 +923,12 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
             tp[3][o] = fo.x;
             tp[4][o] = fo.y;
             tp[5][o] = fo.z;
+            if (STR) {
+                tp[6][o] = qo.x;
+                tp[7][o] = qo.y;
+                tp[8][o] = qo.z;
+                tp[9][o] = fo.x * qo.x + fo.y * qo.y + fo.z * qo.z;
+            }
         }
     }
 #pragma unroll
@@ -1061,6 +1101,8 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
             if constexpr (PAIR) {
                 const float2 nx = f2(-xj.x), ny = f2(-xj.y), nz = f2(-xj.z);
                 const float2 fx = f2(fj.x), fy = f2(fj.y), fz = f2(fj.z);
+                const float2 qx = f2(qj.x), qy = f2(qj.y), qz = f2(qj.z);
+                const float2 fqj = f2(fj.x * qj.x + fj.y * qj.y + fj.z * qj.z);
                 float2 c2[3] = {f2(0.f), f2(0.f), f2(0.f)};
 #pragma unroll
                 for (int p2 = 0; p2 < TC / 2; p2++) {
@@ -1088,11 +1130,38 @@ __global__ void __launch_bounds__(256, SE_RS_SYMC_MINB)
                         const bool ua = ia && r2.x > 0.f, ub = ib && r2.y > 0.f;
                         coinc |= (ia && !ua) || (ib && !ub);
                         float2 a, b;
-                        radial_ab2<PV>(rk, r2, ua, ub, a, b);
+                        if constexpr (!STR) radial_ab2<PV>(rk, r2, ua, ub, a, b);
                         const float2 gx = *reinterpret_cast<const float2 *>(&tp[3][2 * p2]);
                         const float2 gy = *reinterpret_cast<const float2 *>(&tp[4][2 * p2]);
                         const float2 gz = *reinterpret_cast<const float2 *>(&tp[5][2 * p2]);
-                        if (KERNEL == SE_STOKESLET) {
+                        if constexpr (STR) {
+                            // u_t += T(d).(f_j, q_j),  u_j -= T(d).(f_t, q_t)
+                            float2 A, B;
+                            radial_ab2_str<PV>(rk, r2, ua, ub, A, B);
+                            const float2 df = __ffma2_rn(dz, fz, __ffma2_rn(dy, fy, __fmul2_rn(dx, fx)));
+                            const float2 dq = __ffma2_rn(dz, qz, __ffma2_rn(dy, qy, __fmul2_rn(dx, qx)));
+                            const float2 s = __fmul2_rn(__fmul2_rn(A, df), dq);
+                            const float2 w0 = __ffma2_rn(df, qx, __ffma2_rn(dq, fx, __fmul2_rn(fqj, dx)));
+                            const float2 w1 = __ffma2_rn(df, qy, __ffma2_rn(dq, fy, __fmul2_rn(fqj, dy)));
+                            const float2 w2 = __ffma2_rn(df, qz, __ffma2_rn(dq, fz, __fmul2_rn(fqj, dz)));
+                            accp[p2][0] = __ffma2_rn(s, dx, __ffma2_rn(B, w0, accp[p2][0]));
+                            accp[p2][1] = __ffma2_rn(s, dy, __ffma2_rn(B, w1, accp[p2][1]));
+                            accp[p2][2] = __ffma2_rn(s, dz, __ffma2_rn(B, w2, accp[p2][2]));
+                            const float2 hx = *reinterpret_cast<const float2 *>(&tp[6][2 * p2]);
+                            const float2 hy = *reinterpret_cast<const float2 *>(&tp[7][2 * p2]);
+                            const float2 hz = *reinterpret_cast<const float2 *>(&tp[8][2 * p2]);
+                            const float2 fqt = *reinterpret_cast<const float2 *>(&tp[9][2 * p2]);
+                            const float2 dg = __ffma2_rn(dz, gz, __ffma2_rn(dy, gy, __fmul2_rn(dx, gx)));
+                            const float2 dh = __ffma2_rn(dz, hz, __ffma2_rn(dy, hy, __fmul2_rn(dx, hx)));
+                            const float2 nB = __fmul2_rn(f2(-1.f), B);
+                            const float2 ns = __fmul2_rn(__fmul2_rn(__fmul2_rn(f2(-1.f), A), dg), dh);
+                            const float2 v0 = __ffma2_rn(dg, hx, __ffma2_rn(dh, gx, __fmul2_rn(fqt, dx)));
+                            const float2 v1 = __ffma2_rn(dg, hy, __ffma2_rn(dh, gy, __fmul2_rn(fqt, dy)));
+                            const float2 v2 = __ffma2_rn(dg, hz, __ffma2_rn(dh, gz, __fmul2_rn(fqt, dz)));
+                            c2[0] = __ffma2_rn(ns, dx, __ffma2_rn(nB, v0, c2[0]));
+                            c2[1] = __ffma2_rn(ns, dy, __ffma2_rn(nB, v1, c2[1]));
+                            c2[2] = __ffma2_rn(ns, dz, __ffma2_rn(nB, v2, c2[2]));
+                        } else if (KERNEL == SE_STOKESLET) {
                             const float2 bj = __fmul2_rn(b, __ffma2_rn(dz, fz, __ffma2_rn(dy, fy, __fmul2_rn(dx, fx))));
                             accp[p2][0] = __ffma2_rn(a, fx, __ffma2_rn(bj, dx, accp[p2][0]));
                             accp[p2][1] = __ffma2_rn(a, fy, __ffma2_rn(bj, dy, accp[p2][1]));

@@ -13,7 +13,7 @@
 namespace se {
 
 // ---------------------------------------------------------------- status
-enum : int { FLAG_OOB = 1, FLAG_COINCIDENT = 2 };
+enum : int { FLAG_OOB = 1, FLAG_COINCIDENT = 2, FLAG_TIMEOUT = 4 };
 
 void set_error(const std::string &msg);
 se_status_t fail(se_status_t st, const std::string &msg);
