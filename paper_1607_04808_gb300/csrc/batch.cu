@@ -37,6 +37,7 @@ struct se_batch_s {
     std::vector<int> off_h;        // S + 1 point offsets
     int ntiles_tot = 0, ncells_tot = 0, nrows_tot = 0, nitems = 0, nblk_scale = 0, nblk_zero = 0;
     void *sys_d = nullptr;  // BSys<T>[S]
+    void *maps_d = nullptr; // FP32 interleaved grids: S tensor maps of the batched gather
     int *off_d = nullptr, *row_base_d = nullptr, *blk_base_d = nullptr, *zblk_base_d = nullptr;
     int4 *items_d = nullptr;
     int *cl_sys = nullptr;
@@ -81,7 +82,7 @@ void free_batch(se_batch_s *B) {
         cudaFree(c.spec);
         cudaFree(c.wgrid);
     }
-    void *ptrs[] = {B->work, B->sys_d, B->off_d, B->row_base_d, B->blk_base_d, B->zblk_base_d, B->items_d,
+    void *ptrs[] = {B->work, B->sys_d, B->maps_d, B->off_d, B->row_base_d, B->blk_base_d, B->zblk_base_d, B->items_d,
                     B->cl_sys, B->b.xs_t, B->b.fs_t, B->b.perm_t, B->b.cnt_t, B->b.slot_t, B->b.key_t,
                     B->b.xs_r, B->b.fs_r, B->b.perm_r, B->b.cnt_r, B->b.slot_r, B->b.key_r, B->b.tag_t,
                     B->b.tag_r, B->b.ncl, B->b.clusters, B->b.status};
@@ -186,7 +187,7 @@ se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t 
     }
     if (sizeof(T) == 4 && B->colk)
         BCK(launch_bgather_col((const BSys<float> *)sys, B->items_d, B->nitems, B->P, R, B->b, (const float *)f,
-                               (float *)u, st));
+                               (float *)u, B->maps_d, st));
     else
         BCK(launch_bgather<T>(sys, B->off_d, S, Ntot, B->P, R, B->b, f, u, st));
     B->launches += 1;
@@ -412,6 +413,15 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
         if (prec == SE_FP32) {
             std::vector<BSys<float>> sys;
             fill_sys<float>(B, sys, tile_base, cell_base, row_base, blk_base, zblk_base, grid, spec, wgrid, strides);
+            if (B->ilv) {
+                // the batched gather copies its tiles with one tensor map per system
+                std::vector<unsigned char> maps(S * TENSOR_MAP_BYTES, 0);
+                for (int s = 0; s < S; s++)
+                    sys[s].tma = encode_bgather_map(maps.data() + s * TENSOR_MAP_BYTES, sys[s].g, sys[s].wgrid,
+                                                    sys[s].gzs, sys[s].gcs, R, B->P) ? 1 : 0;
+                if ((e = bmalloc(&B->maps_d, maps.size()))) break;
+                if ((e = cudaMemcpy(B->maps_d, maps.data(), maps.size(), cudaMemcpyHostToDevice))) break;
+            }
             if ((e = bmalloc(&B->sys_d, S * sizeof(BSys<float>)))) break;
             e = cudaMemcpy(B->sys_d, sys.data(), S * sizeof(BSys<float>), cudaMemcpyHostToDevice);
         } else {

@@ -360,7 +360,10 @@ constexpr int GS_WAIT_LIMIT = 1 << 20;
 // x 3 floats at (gx0, gy0, gz0, 0) of the grids seen as a 4-D tensor of extent
 // (Mt_x, Mt_y, Mt_z, 3); the copy engine fills the part outside with zeros.
 // gx0 is a multiple of TE = 8, so the box starts on a 32-byte boundary.
-template <int P, int TE, bool TMA>
+// ZC (batches, with TMA): the interleaved batch grids are copied as a tensor
+// (x, y, component, z), so the staged block is [z][c][y][x] instead of
+// [c][z][y][x]; the box starts at component 3 r (right-hand side r).
+template <int P, int TE, bool TMA, bool ZC = false>
 __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, int beg, int end,
                                                  const float4 *__restrict__ xs, const int *__restrict__ perm,
                                                  const float *__restrict__ w, int n_rhs, int r,
@@ -368,8 +371,11 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
                                                  float *__restrict__ u, size_t gzs, size_t gcs,
                                                  const void *tmap = nullptr, int *status = nullptr) {
     // gzs, gcs: the grids' z-plane and component strides
+    static_assert(TMA || !ZC, "the z-major block comes from a tensor copy");
     constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
-    constexpr int ROWS = 3 * PT * PT, PLANE = PT * PX, COMP = PT * PLANE;
+    constexpr int ROWS = 3 * PT * PT, PLANE = PT * PX;
+    // shared-memory strides of a z step and of a component step
+    constexpr int ZS = ZC ? 3 * PLANE : PLANE, CS = ZC ? PLANE : PT * PLANE;
     extern __shared__ __align__(128) float sg_raw[];  // [c][z][y][x], x pitch PX
     __shared__ float swt[GS_WARPS][3][P];
     __shared__ __align__(8) uint64_t bar_mem;
@@ -391,10 +397,11 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
             constexpr uint32_t bytes = (uint32_t)(3 * PT * PT * PX * sizeof(float));
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                          : "memory");
+            const int k2 = ZC ? 3 * r : gz0, k3 = ZC ? gz0 : 0;
             asm volatile(
                 "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                 " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"((uint32_t)__cvta_generic_to_shared(sg)),
-                "l"(reinterpret_cast<uint64_t>(tmap)), "r"(gx0), "r"(gy0), "r"(gz0), "r"(0), "r"(bar)
+                "l"(reinterpret_cast<uint64_t>(tmap)), "r"(gx0), "r"(gy0), "r"(k2), "r"(k3), "r"(bar)
                 : "memory");
         }
         if (!mbar_wait(bar, 0, GS_WAIT_LIMIT)) {
@@ -481,13 +488,13 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
         for (int it = 0; it < NIT; it++) {
             if (val[it]) {
                 const float wxy = swt[warp][0][kxs[it]] * swt[warp][1][kys[it]];
-                const float *col = sg + oz * PLANE + (oy + kys[it]) * PX + ox + kxs[it];
+                const float *col = sg + oz * ZS + (oy + kys[it]) * PX + ox + kxs[it];
                 float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
 #pragma unroll
                 for (int kz = 0; kz < P; kz++) {
-                    a0 = fmaf(col[kz * PLANE], wz[kz], a0);
-                    a1 = fmaf(col[COMP + kz * PLANE], wz[kz], a1);
-                    a2 = fmaf(col[2 * COMP + kz * PLANE], wz[kz], a2);
+                    a0 = fmaf(col[kz * ZS], wz[kz], a0);
+                    a1 = fmaf(col[CS + kz * ZS], wz[kz], a1);
+                    a2 = fmaf(col[2 * CS + kz * ZS], wz[kz], a2);
                 }
                 acc0 = fmaf(a0, wxy, acc0);
                 acc1 = fmaf(a1, wxy, acc1);
@@ -533,15 +540,21 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_bgather_smem(const BSys<float
                                                                 const float4 *__restrict__ xs,
                                                                 const int *__restrict__ perm,
                                                                 const float *__restrict__ f_orig,
-                                                                float *__restrict__ u) {
+                                                                float *__restrict__ u,
+                                                                const CUtensorMap *__restrict__ maps,
+                                                                int *__restrict__ status) {
     const int4 it = items[blockIdx.x];
     const BSys<float> &B = sys[it.x];
     const int key = B.tile_base + it.y;
     const int beg = tile_start[key], end = tile_start[key + 1];
     if (beg == end) return;
     const GP<float> g = B.g;
-    gather_smem_body<P, TE, false>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * B.gcs, n_rhs, it.z,
-                                   f_orig, B.self_coef, u, B.gzs, B.gcs);
+    if (maps && B.tma)
+        gather_smem_body<P, TE, true, true>(g, it.y, beg, end, xs, perm, B.wgrid, n_rhs, it.z, f_orig, B.self_coef,
+                                            u, B.gzs, B.gcs, maps + it.x, status);
+    else
+        gather_smem_body<P, TE, false>(g, it.y, beg, end, xs, perm, B.wgrid + (size_t)it.z * 3 * B.gcs, n_rhs,
+                                       it.z, f_orig, B.self_coef, u, B.gzs, B.gcs);
 }
 
 template <int P, int TE>
@@ -763,12 +776,14 @@ template <int P, int TE>
 struct BGatherRun {
     // the plane-interleaved FP32 batch grids are read by the shared-memory gather
     static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
-                           const float4 *xs, const int *perm, const float *f, float *u, cudaStream_t st) {
+                           const float4 *xs, const int *perm, const float *f, float *u, const CUtensorMap *maps,
+                           int *status, cudaStream_t st) {
         const size_t smem = gather_smem_bytes<P, TE>();
         cudaError_t e = cudaFuncSetAttribute(k_bgather_smem<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e) return e;
-        k_bgather_smem<P, TE><<<nitems, GS_WARPS * 32, smem, st>>>(sys, items, ts, n_rhs, xs, perm, f, u);
+        k_bgather_smem<P, TE><<<nitems, GS_WARPS * 32, smem, st>>>(sys, items, ts, n_rhs, xs, perm, f, u, maps,
+                                                                    status);
         return cudaGetLastError();
     }
 };
@@ -811,9 +826,42 @@ cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int ni
 }
 
 cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
-                               const Buffers &b, const float *f, float *u, cudaStream_t st) {
+                               const Buffers &b, const float *f, float *u, const void *maps, cudaStream_t st) {
     return with_p<BGatherRun>(P, sys, items, nitems, (const int *)b.cnt_t, n_rhs, (const float4 *)b.xs_t,
-                              (const int *)b.perm_t, f, u, st);
+                              (const int *)b.perm_t, f, u, (const CUtensorMap *)maps, (int *)b.status, st);
+}
+
+// The tensor map of one system's interleaved batch grids (FP32): a 4-D FP32
+// tensor (x, y, component, z) of extent (Mt_x, Mt_y, 3 n_rhs, Mt_z) with
+// strides (1, Mf_x, gcs, gzs) elements, read in boxes of PX x PT x 3 x PT.
+bool encode_bgather_map(void *map, const GP<float> &g, const float *wgrid, size_t gzs, size_t gcs, int n_rhs,
+                        int P) {
+    if (!SE_GATHER_TMA || !col_supported(SE_FP32, P)) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const int PT = COL_TE + P - 1;
+    int PX = 0;
+    switch (P) {
+        case 4: PX = GsLayout<4, COL_TE + 3>::PX; break;
+        case 6: PX = GsLayout<6, COL_TE + 5>::PX; break;
+        case 8: PX = GsLayout<8, COL_TE + 7>::PX; break;
+        case 10: PX = GsLayout<10, COL_TE + 9>::PX; break;
+        case 12: PX = GsLayout<12, COL_TE + 11>::PX; break;
+        case 14: PX = GsLayout<14, COL_TE + 13>::PX; break;
+        case 16: PX = GsLayout<16, COL_TE + 15>::PX; break;
+        default: return false;
+    }
+    const size_t rs = (size_t)g.mf[0] * sizeof(float), cs = gcs * sizeof(float), zs = gzs * sizeof(float);
+    if ((reinterpret_cast<uintptr_t>(wgrid) & 15) || (rs & 15) || (cs & 15) || (zs & 15)) return false;
+    if (g.mt[0] < PX || g.mt[1] < PT || g.mt[2] < PT) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.mt[0], (cuuint64_t)g.mt[1], (cuuint64_t)(3 * n_rhs),
+                                (cuuint64_t)g.mt[2]};
+    const cuuint64_t strides[3] = {rs, cs, zs};
+    const cuuint32_t box[4] = {(cuuint32_t)PX, (cuuint32_t)PT, 3, (cuuint32_t)PT};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc((CUtensorMap *)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(wgrid), dims, strides,
+               box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace se

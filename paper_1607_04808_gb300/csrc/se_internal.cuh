@@ -121,6 +121,7 @@ struct BSys {
     int tile_base, cell_base, row_base;
     int blk_base;      // first block of this system in the scaling launch
     int zblk_base;     // first block of this system in the octant-zeroing launch
+    int tma;           // the batched gather stages tiles by tensor copy (map s of the batch)
 };
 
 // Index s of the range holding v, for ascending bases b[0..S) with b[0] = 0.
@@ -333,7 +334,11 @@ cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &
 cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const Buffers &b, cudaStream_t st);
 cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
-                               const Buffers &b, const float *f, float *u, cudaStream_t st);
+                               const Buffers &b, const float *f, float *u, const void *maps, cudaStream_t st);
+// one system's tensor map (128 bytes at `map`, 64-byte aligned) for the batched
+// gather's tile copies; false when the grids do not allow one
+constexpr size_t TENSOR_MAP_BYTES = 128;
+bool encode_bgather_map(void *map, const GP<float> &g, const float *wgrid, size_t gzs, size_t gcs, int n_rhs, int P);
 
 // batched launchers (one launch over all systems of a batch)
 constexpr int SCALE_BS = 256;  // threads per block of the scaling kernels
