@@ -259,11 +259,15 @@ se_status_t se_plan_get_grid(se_plan_t plan, int M[3], int Mtilde[3], int Mf[3],
  * device-side status: SE_OK, SE_ERR_OUT_OF_BOX or SE_ERR_COINCIDENT. */
 se_status_t se_plan_check(se_plan_t plan);
 
-/* Per-stage device times of the plan's last se_eval, in milliseconds, when
- * stage timing was enabled with se_plan_set_timing(plan, 1).  Order:
- * bin, spread, fft, scale, ifft, gather, real_setup (the real-space cluster
- * list; 0 in FP64), real (the real-space pair-sum kernel alone).  Returns the
- * number written (8, or 0 before the first timed se_eval). */
+/* Per-stage device times of the plan's last se_eval or se_eval_backward, in
+ * milliseconds, when stage timing was enabled with se_plan_set_timing(plan, 1).
+ * se_eval order: bin, spread, fft, scale, ifft, gather, real_setup (the
+ * real-space cluster list; 0 in FP64), real (the real-space pair-sum kernel
+ * alone).  se_eval_backward order: adj_bin (g sorted as the source), adj_fourier
+ * (spread of g, transforms and scaling), adj_gather, adj_real (du/df, du/dq),
+ * bin, fourier (the forward grid, recomputed), grad_gather, grad_real (du/dx);
+ * a step the call skips takes 0.  Returns the number written (8, or 0 before
+ * the first timed call). */
 int se_plan_stage_times(se_plan_t plan, float *ms, int max_n);
 se_status_t se_plan_set_timing(se_plan_t plan, int on);
 

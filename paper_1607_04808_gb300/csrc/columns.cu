@@ -356,37 +356,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int limi
 
 constexpr int GS_WAIT_LIMIT = 1 << 20;
 
-// TMA (TMA = true): the block arrives by one tensor copy, a box of PX x PT x PT
-// x 3 floats at (gx0, gy0, gz0, 0) of the grids seen as a 4-D tensor of extent
-// (Mt_x, Mt_y, Mt_z, 3); the copy engine fills the part outside with zeros.
-// gx0 is a multiple of TE = 8, so the box starts on a 32-byte boundary.
-// ZC (batches, with TMA): the interleaved batch grids are copied as a tensor
-// (x, y, component, z), so the staged block is [z][c][y][x] instead of
-// [c][z][y][x]; the box starts at component 3 r (right-hand side r).
-template <int P, int TE, bool TMA, bool ZC = false>
-__device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, int beg, int end,
-                                                 const float4 *__restrict__ xs, const int *__restrict__ perm,
-                                                 const float *__restrict__ w, int n_rhs, int r,
-                                                 const float *__restrict__ f_orig, double self_coef,
-                                                 float *__restrict__ u, size_t gzs, size_t gcs,
-                                                 const void *tmap = nullptr, int *status = nullptr) {
-    // gzs, gcs: the grids' z-plane and component strides
+// Staging of a tile's padded block of three grids in shared memory (sg,
+// 128-byte aligned): TMA = true by one tensor copy, a box of PX x PT x PT x 3
+// floats at (gx0, gy0, gz0, 0) of the grids seen as a 4-D tensor of extent
+// (Mt_x, Mt_y, Mt_z, 3) (the copy engine fills the part outside with zeros;
+// gx0 is a multiple of TE = 8, so the box starts on a 32-byte boundary);
+// otherwise by plain loads.  ZC (batches, with TMA): the interleaved batch
+// grids are copied as a tensor (x, y, component, z), so the staged block is
+// [z][c][y][x] instead of [c][z][y][x]; the box starts at component 3 r
+// (right-hand side r).  False when the copy did not land within the wait limit
+// (reported in status).
+template <int P, int TE, bool TMA, bool ZC>
+__device__ __forceinline__ bool stage_block(float *sg, uint64_t *bar_mem, const GP<float> &g, int gx0, int gy0,
+                                            int gz0, int r, const float *__restrict__ w, size_t gzs, size_t gcs,
+                                            const void *tmap, int *status) {
     static_assert(TMA || !ZC, "the z-major block comes from a tensor copy");
-    constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
-    constexpr int ROWS = 3 * PT * PT, PLANE = PT * PX;
-    // shared-memory strides of a z step and of a component step
-    constexpr int ZS = ZC ? 3 * PLANE : PLANE, CS = ZC ? PLANE : PT * PLANE;
-    extern __shared__ __align__(128) float sg_raw[];  // [c][z][y][x], x pitch PX
-    __shared__ float swt[GS_WARPS][3][P];
-    __shared__ __align__(8) uint64_t bar_mem;
-    // the tensor copy's destination starts on a 128-byte boundary
-    float *sg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(sg_raw) + 127) & ~uintptr_t(127));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
-    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
-    const size_t Mf = g.mf[0];
+    constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, ROWS = 3 * PT * PT;
     if constexpr (TMA) {
-        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_mem);
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(bar_mem);
         if (threadIdx.x == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -408,9 +395,10 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
             // the copy did not land: report, give it one more bounded wait, leave
             if (threadIdx.x == 0) atomicOr(status, FLAG_TIMEOUT);
             mbar_wait(bar, 0, GS_WAIT_LIMIT);
-            return;
+            return false;
         }
     } else {
+        const size_t Mf = g.mf[0];
         // flat copy of the block (x fastest), several independent loads in flight per thread
 #pragma unroll 8
         for (int e = threadIdx.x; e < ROWS * PT; e += GS_WARPS * 32) {
@@ -423,31 +411,58 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
         }
         __syncthreads();
     }
-    // this lane's support columns: those at offset ky * PX + kx = lane (mod 32)
-    int kxs[NIT], kys[NIT];
-    bool val[NIT];
+    return true;
+}
+
+// This lane's support columns (kx, ky): those at offset ky * PX + kx = lane
+// (mod 32), in increasing order, NIT slots.
+template <int P, int PX, int NIT>
+__device__ __forceinline__ void lane_columns(int lane, int (&kxs)[NIT], int (&kys)[NIT], bool (&val)[NIT]) {
 #pragma unroll
     for (int it = 0; it < NIT; it++) {
         val[it] = false;
         kxs[it] = kys[it] = 0;
     }
-    {
-        // offsets o = ky * PX + kx = lane (mod 32), in increasing order
-        int it = 0;
-        for (int o = lane; o < P * PX; o += 32) {
-            const int ky = o / PX, kx = o - ky * PX;
-            if (kx < P) {
+    int it = 0;
+    for (int o = lane; o < P * PX; o += 32) {
+        const int ky = o / PX, kx = o - ky * PX;
+        if (kx < P) {
 #pragma unroll
-                for (int q = 0; q < NIT; q++)
-                    if (q == it) {
-                        kxs[q] = kx;
-                        kys[q] = ky;
-                        val[q] = true;
-                    }
-                it++;
-            }
+            for (int q = 0; q < NIT; q++)
+                if (q == it) {
+                    kxs[q] = kx;
+                    kys[q] = ky;
+                    val[q] = true;
+                }
+            it++;
         }
     }
+}
+
+template <int P, int TE, bool TMA, bool ZC = false>
+__device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, int beg, int end,
+                                                 const float4 *__restrict__ xs, const int *__restrict__ perm,
+                                                 const float *__restrict__ w, int n_rhs, int r,
+                                                 const float *__restrict__ f_orig, double self_coef,
+                                                 float *__restrict__ u, size_t gzs, size_t gcs,
+                                                 const void *tmap = nullptr, int *status = nullptr) {
+    // gzs, gcs: the grids' z-plane and component strides
+    constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
+    constexpr int PLANE = PT * PX;
+    // shared-memory strides of a z step and of a component step
+    constexpr int ZS = ZC ? 3 * PLANE : PLANE, CS = ZC ? PLANE : PT * PLANE;
+    extern __shared__ __align__(128) float sg_raw[];  // [c][z][y][x] (ZC: [z][c][y][x]), x pitch PX
+    __shared__ float swt[GS_WARPS][3][P];
+    __shared__ __align__(8) uint64_t bar_mem;
+    // the tensor copy's destination starts on a 128-byte boundary
+    float *sg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(sg_raw) + 127) & ~uintptr_t(127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
+    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
+    if (!stage_block<P, TE, TMA, ZC>(sg, &bar_mem, g, gx0, gy0, gz0, r, w, gzs, gcs, tmap, status)) return;
+    int kxs[NIT], kys[NIT];
+    bool val[NIT];
+    lane_columns<P, PX, NIT>(lane, kxs, kys, val);
     // the next point's position, index and self-term source are loaded one
     // iteration ahead
     float4 xnext = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -531,6 +546,128 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_gather_smem(GP<float> g, cons
     if (beg == end) return;
     gather_smem_body<P, TE, TMA>(g, tile, beg, end, xs, perm, w, 1, 0, f_orig, self_coef, u,
                                  (size_t)g.mf[0] * g.mf[1], vol(g), &tmap, status);
+}
+
+// Position gradient of the Fourier part (du/dx, se_eval_backward), one group
+// of three grids per launch: for the points of a tile, with the block staged as
+// for the gather, gx_m (+)= c_grad sum_k grad W(x_m - x_k) (c_m . w_k) where c_m
+// are the point's coefficients of the three grids (mode 0: g_m against the
+// forward field; mode 1: f_m against the adjoint field; stresslet modes 2 and
+// 3: the symmetric f_m q_m pairs of the adjoint tensor field, diagonal and
+// off-diagonal) and grad W the Gaussian's derivative, W' = -2 a h (t) W per
+// dimension (c_grad = -2 a h).  Mode 0 writes gx, the others add to it.
+template <int P, int TE, bool TMA>
+__device__ __forceinline__ void grad_smem_body(const GP<float> &g, int tile, int beg, int end,
+                                               const float4 *__restrict__ xs, const int *__restrict__ perm,
+                                               const float *__restrict__ w, int mode, const float *__restrict__ ca,
+                                               const float *__restrict__ cb, float c_grad, float *__restrict__ gx,
+                                               const void *tmap, int *status) {
+    constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
+    constexpr int PLANE = PT * PX, ZS = PLANE, CS = PT * PLANE;
+    extern __shared__ __align__(128) float sg_raw[];  // [c][z][y][x], x pitch PX
+    __shared__ float swt[GS_WARPS][3][P];
+    __shared__ __align__(8) uint64_t bar_mem;
+    float *sg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(sg_raw) + 127) & ~uintptr_t(127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
+    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
+    if (!stage_block<P, TE, TMA, false>(sg, &bar_mem, g, gx0, gy0, gz0, 0, w, (size_t)g.mf[0] * g.mf[1], vol(g),
+                                        tmap, status))
+        return;
+    int kxs[NIT], kys[NIT];
+    bool val[NIT];
+    lane_columns<P, PX, NIT>(lane, kxs, kys, val);
+    for (int n = beg + warp; n < end; n += GS_WARPS) {
+        const float4 xv = xs[n];
+        const int m = perm[n];
+        const float *A = ca + 3 * (size_t)m;
+        float c0, c1, c2;
+        if (mode <= 1) {
+            c0 = A[0];
+            c1 = A[1];
+            c2 = A[2];
+        } else {
+            const float *B = cb + 3 * (size_t)m;
+            if (mode == 2) {
+                c0 = A[0] * B[0];
+                c1 = A[1] * B[1];
+                c2 = A[2] * B[2];
+            } else {
+                c0 = A[0] * B[1] + A[1] * B[0];
+                c1 = A[0] * B[2] + A[2] * B[0];
+                c2 = A[1] * B[2] + A[2] * B[1];
+            }
+        }
+        int i0[3];
+        unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+        // offsets of the point from the first grid point of its support, per dimension
+        const float t0 = ((xv.x - g.x0[0]) * g.inv_h + g.half_ext) - (float)i0[0];
+        const float t1 = ((xv.y - g.x0[1]) * g.inv_h + g.half_ext) - (float)i0[1];
+        const float t2 = ((xv.z - g.x0[2]) * g.inv_h + g.half_ext) - (float)i0[2];
+        if (lane < P) {
+            const float d0 = t0 - (float)lane, d1 = t1 - (float)lane, d2 = t2 - (float)lane;
+            swt[warp][0][lane] = __expf(-g.ah2 * d0 * d0);
+            swt[warp][1][lane] = __expf(-g.ah2 * d1 * d1);
+            swt[warp][2][lane] = __expf(-g.ah2 * d2 * d2);
+        }
+        __syncwarp();
+        const int ox = min(max(i0[0] - gx0, 0), TE - 1), oy = min(max(i0[1] - gy0, 0), TE - 1),
+                  oz = min(max(i0[2] - gz0, 0), TE - 1);
+        float wz[P], wzd[P];
+#pragma unroll
+        for (int kz = 0; kz < P; kz++) {
+            wz[kz] = swt[warp][2][kz];
+            wzd[kz] = wz[kz] * (t2 - (float)kz);
+        }
+        float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f;
+#pragma unroll
+        for (int it = 0; it < NIT; it++) {
+            if (val[it]) {
+                const int kx = kxs[it], ky = kys[it];
+                const float wxy = swt[warp][0][kx] * swt[warp][1][ky];
+                const float *col = sg + oz * ZS + (oy + ky) * PX + ox + kx;
+                float a = 0.0f, az = 0.0f;
+#pragma unroll
+                for (int kz = 0; kz < P; kz++) {
+                    const float sv = fmaf(c2, col[2 * CS + kz * ZS], fmaf(c1, col[CS + kz * ZS], c0 * col[kz * ZS]));
+                    a = fmaf(wz[kz], sv, a);
+                    az = fmaf(wzd[kz], sv, az);
+                }
+                const float aw = a * wxy;
+                acc0 = fmaf(aw, t0 - (float)kx, acc0);
+                acc1 = fmaf(aw, t1 - (float)ky, acc1);
+                acc2 = fmaf(az, wxy, acc2);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc0 += __shfl_xor_sync(FULL, acc0, o);
+            acc1 += __shfl_xor_sync(FULL, acc1, o);
+            acc2 += __shfl_xor_sync(FULL, acc2, o);
+        }
+        if (lane < 3) {
+            const size_t o3 = 3 * (size_t)m + lane;
+            const float v = c_grad * (lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2));
+            gx[o3] = (mode == 0) ? v : gx[o3] + v;
+        }
+        __syncwarp();
+    }
+}
+
+template <int P, int TE, bool TMA>
+__global__ void __launch_bounds__(GS_WARPS * 32) k_grad_smem(GP<float> g, const int *__restrict__ tile_start,
+                                                             const float4 *__restrict__ xs,
+                                                             const int *__restrict__ perm,
+                                                             const float *__restrict__ w, int mode,
+                                                             const float *__restrict__ ca,
+                                                             const float *__restrict__ cb, float c_grad,
+                                                             float *__restrict__ gx,
+                                                             const __grid_constant__ CUtensorMap tmap,
+                                                             int *__restrict__ status) {
+    const int tile = blockIdx.x;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    grad_smem_body<P, TE, TMA>(g, tile, beg, end, xs, perm, w, mode, ca, cb, c_grad, gx, &tmap, status);
 }
 
 template <int P, int TE>
@@ -764,6 +901,24 @@ struct GatherRun {
 };
 
 template <int P, int TE>
+struct GradRun {
+    static cudaError_t run(const GP<float> g, int ntiles, const int *ts, const float4 *xs, const int *perm,
+                           const float *w, int mode, const float *ca, const float *cb, float c_grad, float *gx,
+                           int *status, cudaStream_t st) {
+        constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX;
+        const size_t smem = gather_smem_bytes<P, TE>();
+        alignas(64) CUtensorMap map;
+        memset(&map, 0, sizeof(map));
+        const bool tma = SE_GATHER_TMA && encode_gather_map(&map, g, w, (size_t)g.mf[0] * g.mf[1], vol(g), PX, PT);
+        auto kern = tma ? k_grad_smem<P, TE, true> : k_grad_smem<P, TE, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e) return e;
+        kern<<<ntiles, GS_WARPS * 32, smem, st>>>(g, ts, xs, perm, w, mode, ca, cb, c_grad, gx, map, status);
+        return cudaGetLastError();
+    }
+};
+
+template <int P, int TE>
 struct BSpreadRun {
     static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
                            const float4 *xs, const float4 *fs, cudaStream_t st) {
@@ -817,6 +972,35 @@ cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &
                                       p->b.status, st);
     if (!e) p->launches++;
     return e;
+}
+
+cudaError_t launch_gather_grad_col(se_plan_s *p, cudaStream_t st, const float *w_fwd, const float *w_adj,
+                                   const float *f_orig, const float *q_orig, const float *g_orig, float *gx) {
+    const float c_grad = (float)(-2.0 * p->geom.a * p->h);
+    const int *ts = (const int *)p->b.cnt_t;
+    const float4 *xs = (const float4 *)p->b.xs_t;
+    const size_t Mf3 = vol(p->gpf);
+    // the forward field against g, then the adjoint field against f (or the
+    // stresslet's f q pairs, in two groups of three)
+    struct Pass {
+        const float *w;
+        int mode;
+        const float *a, *b;
+    };
+    Pass passes[3] = {{w_fwd, 0, g_orig, nullptr}, {w_adj, 1, f_orig, nullptr}, {nullptr, 0, nullptr, nullptr}};
+    int np = 2;
+    if (p->kernel == SE_STRESSLET) {
+        passes[1] = {w_adj, 2, f_orig, q_orig};
+        passes[2] = {w_adj + 3 * Mf3, 3, f_orig, q_orig};
+        np = 3;
+    }
+    for (int i = 0; i < np; i++) {
+        cudaError_t e = with_p<GradRun>(p->P, p->gpf, p->ntiles, ts, xs, (const int *)p->b.perm_t, passes[i].w,
+                                        passes[i].mode, passes[i].a, passes[i].b, c_grad, gx, p->b.status, st);
+        if (e) return e;
+        p->launches++;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,

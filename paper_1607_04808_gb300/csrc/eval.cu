@@ -151,11 +151,30 @@ se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaS
     return SE_OK;
 }
 
+// Stage timing of se_eval_backward: events around its eight steps (a step it
+// skips records an empty interval).
+struct BackTimer {
+    se_plan_s *p;
+    cudaStream_t st;
+    int k = 0;
+    void mark() {
+        if (p->timing && k < 9) cudaEventRecord(p->ev[k++], st);
+    }
+    void finish() {
+        if (!p->timing || k != 9) return;
+        cudaEventSynchronize(p->ev[8]);
+        for (int i = 0; i < 8; i++) cudaEventElapsedTime(&p->stage_ms[i], p->ev[i], p->ev[i + 1]);
+        p->n_stage = 8;
+    }
+};
+
 template <typename T>
 se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *q, const T *gu, T *gf, T *gq, T *gx,
                        cudaStream_t st) {
     p->last_stream = st;
     p->launches = 0;
+    BackTimer tm{p, st};
+    tm.mark();
     const size_t Mf3 = (size_t)p->mf[0] * p->mf[1] * p->mf[2];
     const bool stress = (p->kernel == SE_STRESSLET);
     if (!p->wgrid2) {
@@ -165,10 +184,18 @@ se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *q, const T
             return fail(SE_ERR_OOM, "backward: adjoint grid allocation failed");
         }
     }
+    if (gx && !p->gsort) {
+        cudaError_t e = cudaMalloc(&p->gsort, (size_t)p->N * 4 * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SE_ERR_OOM, "backward: gradient buffer allocation failed");
+        }
+    }
     // adjoint field from the upstream gradient g: w' = K^T g on the grid (the
     // stokeslet and rotlet multipliers are their own transposes); for the
     // stresslet the symmetric tensor field V_lk = sum_m T_jlk(x_m - y) g_mj
     CK(launch_bin<T>(p, x, gu, nullptr, st));
+    tm.mark();
     se_status_t s;
     if (stress) {
         const size_t nk = (size_t)p->mf[2] * p->mf[1] * (p->mf[0] / 2 + 1);
@@ -179,26 +206,33 @@ se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *q, const T
         CF(cufftSetStream(p->inv, st));
         CF(exec_inv<T>(p->inv, p->spec, p->wgrid2));
         CF(exec_inv<T>(p->inv, (cplx<T> *)p->spec + 3 * nk, (T *)p->wgrid2 + 3 * Mf3));
-        if (gf || gq) {
-            CK(launch_gather_adjT<T>(p, st, p->wgrid2, f, q, gf, gq));
-            CK(launch_real_adjT<T>(p, st, f, q, gf, gq));
-        }
+        tm.mark();
+        if (gf || gq) CK(launch_gather_adjT<T>(p, st, p->wgrid2, f, q, gf, gq));
+        tm.mark();
+        if (gf || gq) CK(launch_real_adjT<T>(p, st, f, q, gf, gq));
+        tm.mark();
     } else {
         s = fourier_grid<T>(p, st, p->wgrid2, 3, nullptr);
         if (s != SE_OK) return s;
-        if (gf) {
-            // transposed operator applied to g: same kernel (S and Omega are symmetric operators)
-            CK(launch_gather<T>(p, st, p->wgrid2, gu, gf));
-            CK(launch_real<T>(p, st, gf));
-        }
+        tm.mark();
+        // transposed operator applied to g: same kernel (S and Omega are symmetric operators)
+        if (gf) CK(launch_gather<T>(p, st, p->wgrid2, gu, gf));
+        tm.mark();
+        if (gf) CK(launch_real<T>(p, st, gf));
+        tm.mark();
     }
+    if (gx) CK(launch_bin<T>(p, x, f, q, st));
+    tm.mark();
     if (gx) {
-        CK(launch_bin<T>(p, x, f, q, st));
         s = fourier_grid<T>(p, st, p->wgrid, p->nc, nullptr);
         if (s != SE_OK) return s;
-        CK(launch_gather_grad<T>(p, st, p->wgrid, p->wgrid2, f, q, gu, gx));
-        CK(launch_real_grad<T>(p, st, gu, gx));
     }
+    tm.mark();
+    if (gx) CK(launch_gather_grad<T>(p, st, p->wgrid, p->wgrid2, f, q, gu, gx));
+    tm.mark();
+    if (gx) CK(launch_real_grad<T>(p, st, gu, gx));
+    tm.mark();
+    tm.finish();
     return SE_OK;
 }
 

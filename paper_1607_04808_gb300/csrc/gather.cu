@@ -268,9 +268,18 @@ cudaError_t launch_gather(se_plan_s *p, cudaStream_t st, const void *wgrid, cons
     return cudaGetLastError();
 }
 
+#ifndef SE_GRAD_COL
+#define SE_GRAD_COL 1
+#endif
+
 template <typename T>
 cudaError_t launch_gather_grad(se_plan_s *p, cudaStream_t st, const void *w_fwd, const void *w_adj,
                                const T *f_orig, const T *q_orig, const T *g_orig, T *gx) {
+    // FP32 column plans, stokeslet and rotlet (the stresslet's three passes at
+    // P = 14 cost more than its single pass over the global grids)
+    if (sizeof(T) == 4 && p->colk && SE_GRAD_COL && p->kernel != SE_STRESSLET)
+        return launch_gather_grad_col(p, st, (const float *)w_fwd, (const float *)w_adj, (const float *)f_orig,
+                                      (const float *)q_orig, (const float *)g_orig, (float *)gx);
     int N = (int)p->N;
     T c_grad = (T)(-2.0 * p->geom.a * p->h);
     const unsigned gs = (N + WPB - 1) / WPB;

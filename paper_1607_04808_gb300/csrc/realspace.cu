@@ -1481,18 +1481,38 @@ __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, cons
 // a' = -c1 e/r - erfc/r^2 + 2 c1 xi^2 r e,  b' = -3 c1 e/r^3 - 3 erfc/r^4 - 2 c1 xi^2 e/r.
 // Same cell traversal and compaction as the forward kernel; g of a source is
 // read through the permutation.
-__device__ __forceinline__ float s_erfc(float v) { return erfcf(v); }
-__device__ __forceinline__ double s_erfc(double v) { return erfc(v); }
-__device__ __forceinline__ float s_exp(float v) { return expf(v); }
-__device__ __forceinline__ double s_exp(double v) { return exp(v); }
+// e = exp(-xi^2 r^2) and erfc(xi r): FP32 from one exp2 and the erfcx fit
+// (erfc = e Q(1/(2 + x)), x = xi r <= 8 on FP32 plans), FP64 from the library.
+__device__ __forceinline__ void s_exp_erfc(const RC<float> &rk, float r2, float r, float &e, float &ec) {
+    e = ex2_approx(rk.ce * r2);
+    ec = e * erfcx_poly<0>(__fdividef(1.0f, 2.0f + rk.xi * r));
+}
+__device__ __forceinline__ void s_exp_erfc(const RC<double> &rk, double r2, double r, double &e, double &ec) {
+    e = exp(-rk.xi2 * r2);
+    ec = erfc(rk.xi * r);
+}
 __device__ __forceinline__ float s_rsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double s_rsqrt(double v) { return rsqrt(v); }
+
+// The upstream gradient g in the cell order of the real-space sum (as a source).
+template <typename T>
+__global__ void k_sort_g(int N, const int *__restrict__ perm, const T *__restrict__ g, vec4<T> *__restrict__ gs) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int m = perm[n];
+    vec4<T> v;
+    v.x = g[3 * m];
+    v.y = g[3 * m + 1];
+    v.z = g[3 * m + 2];
+    v.w = T(0);
+    gs[n] = v;
+}
 
 template <typename T, int KERNEL>
 __global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, const vec4<T> *__restrict__ xs,
                                                    const vec4<T> *__restrict__ fs, const vec4<T> *__restrict__ qs,
                                                    const int *__restrict__ cell_start,
-                                                   const int *__restrict__ perm, const T *__restrict__ g_orig,
+                                                   const int *__restrict__ perm, const vec4<T> *__restrict__ gs,
                                                    T *__restrict__ gx) {
     constexpr int WPB = 8;
     __shared__ vec4<T> qd_all[WPB][QCAP];
@@ -1509,7 +1529,8 @@ __global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, con
     vec4<T> qp;
     if (KERNEL == SE_STRESSLET) qp = qs[t];
     const int mp = perm[t];
-    const T gp_[3] = {g_orig[3 * mp], g_orig[3 * mp + 1], g_orig[3 * mp + 2]};
+    const vec4<T> gpv = gs[t];
+    const T gp_[3] = {gpv.x, gpv.y, gpv.z};
     const int nrows = row_segments(g, rk, xt, cell_start, lane, seg);
     T acc[3] = {0, 0, 0};
     int cnt = 0;
@@ -1518,13 +1539,13 @@ __global__ void __launch_bounds__(256) k_real_grad(GP<T> g, RC<T> rk, int N, con
         const vec4<T> v = qd[slot];
         const int n = qn[slot];
         const vec4<T> fn = fs[n];
-        const int mn = perm[n];
-        const T gn[3] = {g_orig[3 * mn], g_orig[3 * mn + 1], g_orig[3 * mn + 2]};
+        const vec4<T> gnv = gs[n];
+        const T gn[3] = {gnv.x, gnv.y, gnv.z};
         const T d[3] = {v.x, v.y, v.z};
         const T rinv = s_rsqrt(v.w);
         const T r = v.w * rinv;
-        const T e = s_exp(-rk.xi2 * v.w);
-        const T ec = s_erfc(rk.xi * r);
+        T e, ec;
+        s_exp_erfc(rk, v.w, r, e, ec);
         const T c1 = rk.c;
         const T ecr = ec * rinv;
         const T rinv2 = rinv * rinv;
@@ -1888,16 +1909,20 @@ cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *
     int N = (int)p->N;
     RC<T> rk = make_rc<T>(p);
     if (!reach_ok(rk)) return cudaErrorInvalidValue;
+    if (!p->gsort) return cudaErrorInvalidValue;
+    vec4<T> *gsort = (vec4<T> *)p->gsort;
+    k_sort_g<T><<<(N + 255) / 256, 256, 0, st>>>(N, p->b.perm_r, g_orig, gsort);
+    p->launches++;
     unsigned gs = (N + 7) / 8;
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r;
     const GP<T> &g = gp<T>(p);
     const vec4<T> *qs = (const vec4<T> *)p->b.qs_r;
     if (p->kernel == SE_STOKESLET)
-        k_real_grad<T, SE_STOKESLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
+        k_real_grad<T, SE_STOKESLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, gsort, gx);
     else if (p->kernel == SE_ROTLET)
-        k_real_grad<T, SE_ROTLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, g_orig, gx);
+        k_real_grad<T, SE_ROTLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, gsort, gx);
     else
-        k_real_grad<T, SE_STRESSLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, g_orig,
+        k_real_grad<T, SE_STRESSLET><<<gs, 256, 0, st>>>(g, rk, N, xs, fs, qs, p->b.cnt_r, p->b.perm_r, gsort,
                                                           gx);
     p->launches++;
     return cudaGetLastError();

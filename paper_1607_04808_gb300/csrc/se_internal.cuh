@@ -232,6 +232,7 @@ struct se_plan_s {
     void *spec = nullptr;      // nc x Mf x Mf x (Mf/2+1) complex
     void *wgrid = nullptr;     // 3 x Mf^3 real (C2R output)
     void *wgrid2 = nullptr;    // 3 x Mf^3 real (backward: adjoint grid)
+    void *gsort = nullptr;     // N x 4 (backward: the upstream gradient in cell order)
     void *spec2 = nullptr;     // backward spectrum
     void *tmp3 = nullptr;      // N x 3 scratch in plan precision (backward)
     se::Buffers b;
@@ -331,6 +332,9 @@ cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, con
 cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, const float *f_orig, float *u);
 cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &b, const void *wgrid,
                                   const float *f_orig, double self_coef, float *u);
+// du/dx of the Fourier part on the shared-memory tiles (FP32 column plans)
+cudaError_t launch_gather_grad_col(se_plan_s *p, cudaStream_t st, const float *w_fwd, const float *w_adj,
+                                   const float *f_orig, const float *q_orig, const float *g_orig, float *gx);
 cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const Buffers &b, cudaStream_t st);
 cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,

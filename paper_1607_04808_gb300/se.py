@@ -24,6 +24,7 @@ STATUS = {
     8: "SE_ERR_NOT_SUPPORTED",
 }
 STAGES = ["bin", "spread", "fft", "scale", "ifft", "gather", "real_setup", "real"]
+BACK_STAGES = ["adj_bin", "adj_fourier", "adj_gather", "adj_real", "bin", "fourier", "grad_gather", "grad_real"]
 
 
 class SEError(RuntimeError):
@@ -271,10 +272,13 @@ class Plan:
         """se_plan_set_overlap: Fourier part and real-space sum on two streams (FP32)."""
         _check(lib().se_plan_set_overlap(self._h, 1 if on else 0))
 
-    def stage_times(self) -> dict:
+    def stage_times(self, backward: bool = False) -> dict:
+        """se_plan_stage_times of the last timed call: se_eval's stages, or with
+        backward=True those of se_eval_backward."""
         buf = (ctypes.c_float * 8)()
         n = lib().se_plan_stage_times(self._h, buf, 8)
-        return {STAGES[i]: buf[i] for i in range(n)}
+        names = BACK_STAGES if backward else STAGES
+        return {names[i]: buf[i] for i in range(n)}
 
     def precompute_info(self) -> tuple[float, bool]:
         """(milliseconds, from the cache) of the plan's precomputation."""
