@@ -42,6 +42,11 @@ constexpr int QCAP = 64;
 #ifndef SE_RS_PAIR
 #define SE_RS_PAIR 1
 #endif
+// SE_GRAD_SYM: the FP32 real-space position gradient (stokeslet, rotlet) by the
+// symmetric cluster kernel, each pair once
+#ifndef SE_GRAD_SYM
+#define SE_GRAD_SYM 1
+#endif
 // SE_RS_PAIR_STR: the same for the stresslet's symmetric pair sum
 #ifndef SE_RS_PAIR_STR
 #define SE_RS_PAIR_STR 1
@@ -150,6 +155,46 @@ __device__ __forceinline__ void radial_ab(const RC<float> &rk, float r2, float &
         const float er = e * rinv;
         a = er * (q - cr);
         b = er * (rinv * rinv) * (q + cr);
+    }
+}
+
+// Gradient with respect to x_t of the pair term of L = sum g . u (stokeslet,
+// rotlet; FP32), d = x_t - x_j, r = |d|, c1 = 2 xi/sqrt(pi), e = exp(-xi^2 r^2):
+//   b = (erfc/r + c1 e)/r^2,  b' = -3 c1 e/r^3 - 3 erfc/r^4 - 2 c1 xi^2 e/r,
+//   stokeslet: a' = -c1 e/r - erfc/r^2 + 2 c1 xi^2 r e,
+//     G = d/r [a' (g_t.f_j + g_j.f_t) + b' ((g_t.d)(d.f_j) + (g_j.d)(d.f_t))]
+//         + b [g_t (d.f_j) + f_j (g_t.d) + g_j (d.f_t) + f_t (g_j.d)]
+//   rotlet: c = g_t x f_j - g_j x f_t,  G = b c + (b'/r)(d.c) d
+template <int KERNEL, int PV>
+__device__ __forceinline__ void grad_pair(const RC<float> &rk, float dx, float dy, float dz, float r2,
+                                          const float4 &ft, const float4 &gt, const float4 &fj, const float4 &gj,
+                                          float G[3]) {
+    const float rinv = rsqrtf(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+    const float e = ex2_approx(rk.ce * r2);
+    const float ec = e * erfcx_poly<PV>(__fdividef(1.0f, 2.0f + rk.xi * r));
+    const float c1 = rk.c;
+    const float b = fmaf(ec, rinv, c1 * e) * rinv2;
+    const float bp = -3.0f * c1 * e * rinv2 * rinv - 3.0f * ec * rinv2 * rinv2 - 2.0f * c1 * rk.xi2 * e * rinv;
+    if (KERNEL == SE_STOKESLET) {
+        const float ap = -c1 * e * rinv - ec * rinv2 + 2.0f * c1 * rk.xi2 * r * e;
+        const float gpf = gt.x * fj.x + gt.y * fj.y + gt.z * fj.z;
+        const float gnf = gj.x * ft.x + gj.y * ft.y + gj.z * ft.z;
+        const float gpr = gt.x * dx + gt.y * dy + gt.z * dz;
+        const float gnr = gj.x * dx + gj.y * dy + gj.z * dz;
+        const float rfn = dx * fj.x + dy * fj.y + dz * fj.z;
+        const float rfp = dx * ft.x + dy * ft.y + dz * ft.z;
+        const float rad = (ap * (gpf + gnf) + bp * (gpr * rfn + gnr * rfp)) * rinv;
+        G[0] = rad * dx + b * (gt.x * rfn + fj.x * gpr + gj.x * rfp + ft.x * gnr);
+        G[1] = rad * dy + b * (gt.y * rfn + fj.y * gpr + gj.y * rfp + ft.y * gnr);
+        G[2] = rad * dz + b * (gt.z * rfn + fj.z * gpr + gj.z * rfp + ft.z * gnr);
+    } else {
+        const float c0 = (gt.y * fj.z - gt.z * fj.y) - (gj.y * ft.z - gj.z * ft.y);
+        const float cy = (gt.z * fj.x - gt.x * fj.z) - (gj.z * ft.x - gj.x * ft.z);
+        const float cz = (gt.x * fj.y - gt.y * fj.x) - (gj.x * ft.y - gj.y * ft.x);
+        const float rcd = (dx * c0 + dy * cy + dz * cz) * bp * rinv;
+        G[0] = b * c0 + rcd * dx;
+        G[1] = b * cy + rcd * dy;
+        G[2] = b * cz + rcd * dz;
     }
 }
 
@@ -859,8 +904,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
 // its image nearest the centre of the targets' box, which is every target's
 // nearest image when the box's half-width plus rc stays below L/2; a wider
 // cluster takes nearest images pair by pair instead.
-template <int KERNEL, int PV, bool PER = false>
-__global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_STR : SE_RS_SYMC_MINB)
+// GRAD: the position gradient of the real-space part of L = sum_m g_m . u_m
+// instead of u (stokeslet, rotlet; qs holds g in cell order): the pair term
+// Phi = g_t . K(d) f_j + g_j . K(-d) f_t, d = x_t - x_j, adds grad Phi to the
+// target and -grad Phi to the candidate.
+template <int KERNEL, int PV, bool PER = false, bool GRAD = false>
+__global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_SYMC_MINB_STR : SE_RS_SYMC_MINB)
     k_real_symc(GP<float> g, RC<float> rk, const float4 *__restrict__ xs, const float4 *__restrict__ fs,
                 const float4 *__restrict__ qs, const int *__restrict__ cell_start, const int2 *__restrict__ clusters,
                 const int *__restrict__ ncl_total, const int *__restrict__ perm, float *__restrict__ u,
@@ -868,12 +917,14 @@ __global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_
     constexpr int WPB = 8, TC = 8, QN = 64;
     constexpr bool STR = (KERNEL == SE_STRESSLET);
     static_assert(!(PER && STR), "periodic plans sum the stresslet with k_real_cmp");
+    static_assert(!(GRAD && (PER || STR)), "the gradient mode is for free-space stokeslet and rotlet plans");
+    constexpr bool HQ = STR || GRAD;  // a third vector per point: q, or g
     __shared__ float4 tx_all[WPB][TC];
     __shared__ float4 tf_all[WPB][TC];
-    __shared__ float4 tq_all[STR ? WPB : 1][TC];
+    __shared__ float4 tq_all[HQ ? WPB : 1][TC];
     __shared__ float4 qx_all[WPB][QN];
     __shared__ float4 qf_all[WPB][QN];
-    __shared__ float4 qq_all[STR ? WPB : 1][QN];
+    __shared__ float4 qq_all[HQ ? WPB : 1][QN];
     __shared__ int qm_all[WPB][QN];
     constexpr int NSEG = PER ? 2 * MAXROWS : MAXROWS;  // entries of the segment list
     __shared__ int2 seg_all[WPB][NSEG];
@@ -882,16 +933,16 @@ __global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_
     // PAIR: neighbouring targets 2p and 2p + 1 side by side (their cutoff
     // tests mostly agree), [component][2 p + slot] = [component][t]; the
     // components are x, f and, for the stresslet, q and f.q
-    constexpr bool PAIR = SE_RS_PAIR && (!STR || SE_RS_PAIR_STR);
+    constexpr bool PAIR = SE_RS_PAIR && (!STR || SE_RS_PAIR_STR) && !GRAD;
     constexpr int NTP = STR ? 10 : 6;
     __shared__ __align__(8) float tp_all[PAIR ? WPB : 1][NTP][TC];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * WPB + wib;
     if (c >= *ncl_total) return;
-    float4 *tx = tx_all[wib], *tf = tf_all[wib], *tq = tq_all[STR ? wib : 0];
+    float4 *tx = tx_all[wib], *tf = tf_all[wib], *tq = tq_all[HQ ? wib : 0];
     float (*tp)[TC] = tp_all[PAIR ? wib : 0];
     float *box = box_all[wib];
-    float4 *qx = qx_all[wib], *qf = qf_all[wib], *qq = qq_all[STR ? wib : 0];
+    float4 *qx = qx_all[wib], *qf = qf_all[wib], *qq = qq_all[HQ ? wib : 0];
     int *qm = qm_all[wib];
     int2 *seg = seg_all[wib];
     int *pre = pre_all[wib];
@@ -905,14 +956,14 @@ __global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_
         if (lane < cl.y) {
             xo = xs[cl.x + lane];
             fo = fs[cl.x + lane];
-            if (STR) qo = qs[cl.x + lane];
+            if (HQ) qo = qs[cl.x + lane];
             blo[0] = bhi[0] = xo.x;
             blo[1] = bhi[1] = xo.y;
             blo[2] = bhi[2] = xo.z;
         }
         tx[lane] = xo;
         tf[lane] = fo;
-        if (STR) tq[lane] = qo;
+        if (HQ) tq[lane] = qo;
         if (PAIR) {
             // empty slots far away but finite: a masked slot's products stay 0
             const int o = lane;  // pair p = t / 2, slot t mod 2
@@ -1074,7 +1125,7 @@ __global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_
                 xm.w = __int_as_float(min(v, TC));  // the stream position, capped
                 qx[pos] = xm;
                 qf[pos] = fs[m];
-                if (STR) qq[pos] = qs[m];
+                if (HQ) qq[pos] = qs[m];
                 qm[pos] = m;
             }
             fill += __popc(bal);
@@ -1093,7 +1144,7 @@ __global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_
             if (valid) {
                 xj = qx[lane];
                 fj = qf[lane];
-                if (STR) qj = qq[lane];
+                if (HQ) qj = qq[lane];
                 vs = __float_as_int(xj.w);
                 mj = qm[lane];
             }
@@ -1191,7 +1242,16 @@ __global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_
                 const float dx = xt.x - xj.x, dy = xt.y - xj.y, dz = xt.z - xj.z;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 <= rk.rc2 && t < vs) {
-                    if (r2 > 0.f) {
+                    if (GRAD && r2 > 0.f) {
+                        float G[3];
+                        grad_pair<KERNEL, PV>(rk, dx, dy, dz, r2, tf[t], tq[t], fj, qj, G);
+                        acc[t][0] += G[0];
+                        acc[t][1] += G[1];
+                        acc[t][2] += G[2];
+                        cj[0] -= G[0];
+                        cj[1] -= G[1];
+                        cj[2] -= G[2];
+                    } else if (r2 > 0.f) {
                         float rinv, a, b;
                         radial_ab<KERNEL, PV>(rk, r2, rinv, a, b);
                         const float4 ft = tf[t];
@@ -1246,7 +1306,7 @@ __global__ void __launch_bounds__(256, KERNEL == SE_STRESSLET ? SE_RS_SYMC_MINB_
         if (lane < fill - nq) {
             qx[lane] = qx[nq + lane];
             qf[lane] = qf[nq + lane];
-            if (STR) qq[lane] = qq[nq + lane];
+            if (HQ) qq[lane] = qq[nq + lane];
             qm[lane] = qm[nq + lane];
         }
         fill -= nq;
@@ -1913,6 +1973,46 @@ cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *
     vec4<T> *gsort = (vec4<T> *)p->gsort;
     k_sort_g<T><<<(N + 255) / 256, 256, 0, st>>>(N, p->b.perm_r, g_orig, gsort);
     p->launches++;
+    if constexpr (sizeof(T) == 4) {
+        if (SE_RS_SYMC && SE_GRAD_SYM && p->kernel != SE_STRESSLET && !p->periodic && p->b.uj) {
+            // each pair once over the clusters of 8 targets, the candidate's share through uj
+            const int nrows = p->geom.ncel[1] * p->geom.ncel[2];
+            k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], 8, p->b.cnt_r, p->b.ncl);
+            launch_scan(p->b.ncl, nrows, st);
+            k_cluster_fill<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], 8, p->b.cnt_r, p->b.ncl,
+                                                                 p->b.clusters);
+            const long max_cl = N / 8 + nrows + 1;
+            const unsigned nblk = (unsigned)((max_cl + 7) / 8);
+            cudaError_t e = cudaMemsetAsync(p->b.uj, 0, 4 * sizeof(float) * (size_t)N, st);
+            if (e) return e;
+            const float4 *xf = (const float4 *)p->b.xs_r, *ff = (const float4 *)p->b.fs_r,
+                         *gf4 = (const float4 *)gsort;
+            float *ujf = (float *)p->b.uj;
+            const bool pv1 = real_pv(p->xi * p->rc) == 1;
+            if (p->kernel == SE_STOKESLET) {
+                if (pv1)
+                    k_real_symc<SE_STOKESLET, 1, false, true><<<nblk, 256, 0, st>>>(
+                        p->gpf, rk, xf, ff, gf4, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                        (float *)gx, ujf, p->b.status, nullptr);
+                else
+                    k_real_symc<SE_STOKESLET, 0, false, true><<<nblk, 256, 0, st>>>(
+                        p->gpf, rk, xf, ff, gf4, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                        (float *)gx, ujf, p->b.status, nullptr);
+            } else {
+                if (pv1)
+                    k_real_symc<SE_ROTLET, 1, false, true><<<nblk, 256, 0, st>>>(
+                        p->gpf, rk, xf, ff, gf4, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                        (float *)gx, ujf, p->b.status, nullptr);
+                else
+                    k_real_symc<SE_ROTLET, 0, false, true><<<nblk, 256, 0, st>>>(
+                        p->gpf, rk, xf, ff, gf4, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                        (float *)gx, ujf, p->b.status, nullptr);
+            }
+            k_add_uj<float><<<(N + 255) / 256, 256, 0, st>>>(N, ujf, p->b.perm_r, (float *)gx);
+            p->launches += 4 + scan_launch_count(nrows);
+            return cudaGetLastError();
+        }
+    }
     unsigned gs = (N + 7) / 8;
     const vec4<T> *xs = (const vec4<T> *)p->b.xs_r, *fs = (const vec4<T> *)p->b.fs_r;
     const GP<T> &g = gp<T>(p);
