@@ -36,7 +36,7 @@ FLOP_PER_PAIR = 58
 # DRAM bytes (read + write) of one launch of the FP32 stokeslet real-space kernel on
 # this workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 # Set to None whenever that kernel changes, until it is captured again.
-REAL_TRAFFIC_BYTES = None
+REAL_TRAFFIC_BYTES = 51060736 + 3102208  # ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch
 
 
 def pair_fraction_unit_cube(r: float) -> float:
@@ -214,6 +214,67 @@ def run_batched(args, rank, world, dist, dev, flush):
     return out
 
 
+def run_other_configs(dev, flush):
+    """The clustered FP32 stresslet (N = 5e5: 16 Gaussian blobs, sigma 0.05,
+    plus 20 % uniform background) and the FP32 rotlet with its backward
+    (N = 2e5 uniform, du/df and du/dx, grid recomputed): median device times
+    of 5 calls each after 2 warm-ups, stage times from one more timed call."""
+    import torch
+
+    import paper_1607_04808_gb300 as se
+    import workloads as W
+
+    def timed(fn, reps=5):
+        fn()
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    out = {}
+    x, f, q = W.stresslet_blobs(500_000, 2)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)  # noqa: E731
+    xd, fd, qd = torch.tensor(f32_in_box(x), device=dev), t(f), t(q)
+    plan = se.Plan("stresslet", len(x), BOX, prec="fp32", tol=2e-6)
+    u = torch.empty_like(xd)
+    ms = timed(lambda: plan.eval(xd, fd, qd, out=u))
+    plan.set_timing(True)
+    plan.eval(xd, fd, qd, out=u)
+    torch.cuda.synchronize()
+    st = plan.stage_times()
+    plan.check()
+    out["stresslet_clustered"] = {
+        "workload": "stresslet sum, N = 5e5: 16 Gaussian blobs (sigma 0.05) + 20 % uniform, FP32 at 2e-6",
+        "value": len(x) / (ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms,
+        "params": {k: plan.params[k] for k in ("M", "P", "xi", "rc")}, "stages_ms": st}
+    plan.close()
+    x, tq, g = W.rotlet_uniform(200_000, 3)
+    xd, td, gd = torch.tensor(f32_in_box(x), device=dev), t(tq), t(g)
+    plan = se.Plan("rotlet", len(x), BOX, prec="fp32", tol=2e-6)
+    u = torch.empty_like(xd)
+    ms_f = timed(lambda: plan.eval(xd, td, out=u))
+    ms_b = timed(lambda: plan.backward(xd, td, gd))
+    plan.set_timing(True)
+    plan.backward(xd, td, gd)
+    torch.cuda.synchronize()
+    st = plan.stage_times(backward=True)
+    plan.check()
+    out["rotlet_backward"] = {
+        "workload": "rotlet sum, N = 2e5 uniform, FP32 at 2e-6: forward, and backward (du/df, du/dx, grid recomputed)",
+        "forward_ms": ms_f, "backward_ms": ms_b, "value": len(x) / ((ms_f + ms_b) * 1e-3) / 1e6,
+        "unit": "Mpoints/s (forward + backward)", "params": {k: plan.params[k] for k in ("M", "P", "xi", "rc")},
+        "backward_stages_ms": st}
+    plan.close()
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -366,6 +427,7 @@ def run_ours(args, rank, world, dist):
 
     if rank != 0:
         return
+    others = None if args.no_extra else run_other_configs(dev, flush)
     value = world * N_POINTS / (ms * 1e-3) / 1e6
     peaks = read_peaks()
     clocks = clk.summary()
@@ -428,6 +490,7 @@ def run_ours(args, rank, world, dist):
         "fp64": fp64,
         "periodic": periodic,
         "batched": batched,
+        "other_configs": others,
         "cpu_baseline": cpu,
         "e2e": {"value": N_POINTS / (e2e_ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": e2e_ms,
                 "mean_ms_per_step": e2e_mean_ms, "calls": len(e2e_t), "statistic": "median of host-clock call times",
@@ -450,6 +513,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-periodic", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the clustered stresslet and rotlet backward lines")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
