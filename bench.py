@@ -17,6 +17,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -58,18 +59,24 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="se_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            # the sampler is running before the timed region starts: wait (3 s at
+            # most) for its first line
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 3.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)
+            self.skip = sum(1 for _ in open(self.path))
         except Exception:
             self.proc = None
         return self
@@ -87,7 +94,11 @@ class ClockSampler:
         if not self.proc:
             return None
         try:
-            rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+            lines = [ln for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+            # samples taken during the timed region (the lines present before it are
+            # dropped unless nothing else came)
+            rows = [ln.split(",") for ln in (lines[self.skip:] or lines)]
+            os.unlink(self.path)
             sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
             mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]

@@ -54,7 +54,7 @@ typedef enum {
     SE_ERR_CUDA = 5,          /* a CUDA runtime call failed                                   */
     SE_ERR_CUFFT = 6,         /* a cuFFT call failed                                          */
     SE_ERR_TIMEOUT = 7,       /* a bounded device wait ran out                                */
-    SE_ERR_NOT_SUPPORTED = 8  /* valid request this build does not implement                  */
+    SE_ERR_NOT_SUPPORTED = 8  /* valid request that the library does not implement            */
 } se_status_t;
 
 typedef struct se_plan_s *se_plan_t;
@@ -256,8 +256,17 @@ se_status_t se_plan_get_params(se_plan_t plan, se_params_t *out);
 se_status_t se_plan_get_grid(se_plan_t plan, int M[3], int Mtilde[3], int Mf[3], int Mg[3]);
 
 /* Synchronise the stream of the plan's last call and return (and clear) the
- * device-side status: SE_OK, SE_ERR_OUT_OF_BOX or SE_ERR_COINCIDENT. */
+ * device-side status: SE_OK, SE_ERR_TIMEOUT (a bounded device wait ran out),
+ * SE_ERR_OUT_OF_BOX or SE_ERR_COINCIDENT. */
 se_status_t se_plan_check(se_plan_t plan);
+
+/* Test flags of a plan (0 restores normal operation).  SE_TEST_SKIP_TILE_COPY:
+ * the FP32 gather does not issue its tiles' tensor copies, so each tile's
+ * bounded wait (one second) runs out; the evaluation then leaves u undefined
+ * and se_plan_check returns SE_ERR_TIMEOUT, with the context still usable.
+ * For tests of the failure path only.  SE_ERR_INVALID_ARG for unknown flags. */
+#define SE_TEST_SKIP_TILE_COPY 1
+se_status_t se_plan_set_test_flags(se_plan_t plan, int flags);
 
 /* Per-stage device times of the plan's last se_eval or se_eval_backward, in
  * milliseconds, when stage timing was enabled with se_plan_set_timing(plan, 1).

@@ -337,10 +337,16 @@ struct GsLayout {
     static constexpr int NIT = count(PX);
 };
 
-// Bounded wait on phase `phase` of a shared-memory mbarrier; false when the
-// iteration limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int limit) {
-    for (int it = 0; it < limit; it++) {
+// Bounded wait on phase `phase` of a shared-memory mbarrier; false when
+// `limit_ns` nanoseconds of the global timer passed first.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    while (true) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -350,11 +356,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int limi
             : "r"(bar), "r"(phase)
             : "memory");
         if (ok) return true;
+        if (global_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
-constexpr int GS_WAIT_LIMIT = 1 << 20;
+// a tile copy takes microseconds; one second means it will not come
+constexpr uint64_t GS_WAIT_NS = 1000000000ull;
 
 // Staging of a tile's padded block of three grids in shared memory (sg,
 // 128-byte aligned): TMA = true by one tensor copy, a box of PX x PT x PT x 3
@@ -366,10 +373,12 @@ constexpr int GS_WAIT_LIMIT = 1 << 20;
 // [z][c][y][x] instead of [c][z][y][x]; the box starts at component 3 r
 // (right-hand side r).  False when the copy did not land within the wait limit
 // (reported in status).
+// skip_copy (tests of the failure path): the copy is not issued, so the wait
+// runs out and the status reports it.
 template <int P, int TE, bool TMA, bool ZC>
 __device__ __forceinline__ bool stage_block(float *sg, uint64_t *bar_mem, const GP<float> &g, int gx0, int gy0,
                                             int gz0, int r, const float *__restrict__ w, size_t gzs, size_t gcs,
-                                            const void *tmap, int *status) {
+                                            const void *tmap, int *status, bool skip_copy = false) {
     static_assert(TMA || !ZC, "the z-major block comes from a tensor copy");
     constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, ROWS = 3 * PT * PT;
     if constexpr (TMA) {
@@ -380,7 +389,7 @@ __device__ __forceinline__ bool stage_block(float *sg, uint64_t *bar_mem, const 
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !skip_copy) {
             constexpr uint32_t bytes = (uint32_t)(3 * PT * PT * PX * sizeof(float));
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                          : "memory");
@@ -391,10 +400,11 @@ __device__ __forceinline__ bool stage_block(float *sg, uint64_t *bar_mem, const 
                 "l"(reinterpret_cast<uint64_t>(tmap)), "r"(gx0), "r"(gy0), "r"(k2), "r"(k3), "r"(bar)
                 : "memory");
         }
-        if (!mbar_wait(bar, 0, GS_WAIT_LIMIT)) {
-            // the copy did not land: report, give it one more bounded wait, leave
+        if (!mbar_wait(bar, 0, GS_WAIT_NS)) {
+            // the copy did not land: report, give a copy in flight one more
+            // bounded wait, leave
             if (threadIdx.x == 0) atomicOr(status, FLAG_TIMEOUT);
-            mbar_wait(bar, 0, GS_WAIT_LIMIT);
+            if (!skip_copy) mbar_wait(bar, 0, GS_WAIT_NS);
             return false;
         }
     } else {
@@ -445,7 +455,8 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
                                                  const float *__restrict__ w, int n_rhs, int r,
                                                  const float *__restrict__ f_orig, double self_coef,
                                                  float *__restrict__ u, size_t gzs, size_t gcs,
-                                                 const void *tmap = nullptr, int *status = nullptr) {
+                                                 const void *tmap = nullptr, int *status = nullptr,
+                                                 bool skip_copy = false) {
     // gzs, gcs: the grids' z-plane and component strides
     constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
     constexpr int PLANE = PT * PX;
@@ -459,7 +470,8 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
-    if (!stage_block<P, TE, TMA, ZC>(sg, &bar_mem, g, gx0, gy0, gz0, r, w, gzs, gcs, tmap, status)) return;
+    if (!stage_block<P, TE, TMA, ZC>(sg, &bar_mem, g, gx0, gy0, gz0, r, w, gzs, gcs, tmap, status, skip_copy))
+        return;
     int kxs[NIT], kys[NIT];
     bool val[NIT];
     lane_columns<P, PX, NIT>(lane, kxs, kys, val);
@@ -540,12 +552,12 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_gather_smem(GP<float> g, cons
                                                                const float *__restrict__ f_orig, double self_coef,
                                                                float *__restrict__ u,
                                                                const __grid_constant__ CUtensorMap tmap,
-                                                               int *__restrict__ status) {
+                                                               int *__restrict__ status, int skip_copy) {
     const int tile = blockIdx.x;
     const int beg = tile_start[tile], end = tile_start[tile + 1];
     if (beg == end) return;
     gather_smem_body<P, TE, TMA>(g, tile, beg, end, xs, perm, w, 1, 0, f_orig, self_coef, u,
-                                 (size_t)g.mf[0] * g.mf[1], vol(g), &tmap, status);
+                                 (size_t)g.mf[0] * g.mf[1], vol(g), &tmap, status, skip_copy != 0);
 }
 
 // Position gradient of the Fourier part (du/dx, se_eval_backward), one group
@@ -881,7 +893,7 @@ static bool encode_gather_map(CUtensorMap *map, const GP<float> &g, const float 
 template <int P, int TE>
 struct GatherRun {
     static cudaError_t run(const GP<float> g, int ntiles, const int *ts, const float4 *xs, const int *perm,
-                           const float *w, const float *f, double self_coef, float *u, int *status,
+                           const float *w, const float *f, double self_coef, float *u, int *status, int skip_copy,
                            cudaStream_t st) {
         if (SE_GATHER_SMEM) {
             constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX;
@@ -892,7 +904,8 @@ struct GatherRun {
             auto kern = tma ? k_gather_smem<P, TE, true> : k_gather_smem<P, TE, false>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e) return e;
-            kern<<<ntiles, GS_WARPS * 32, smem, st>>>(g, ts, xs, perm, w, f, self_coef, u, map, status);
+            kern<<<ntiles, GS_WARPS * 32, smem, st>>>(g, ts, xs, perm, w, f, self_coef, u, map, status,
+                                                      tma ? skip_copy : 0);
         } else {
             k_gather_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, ts, xs, perm, w, f, self_coef, u);
         }
@@ -969,7 +982,7 @@ cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &
                                   const float *f_orig, double self_coef, float *u) {
     cudaError_t e = with_p<GatherRun>(p->P, p->gpf, p->ntiles, (const int *)b.cnt_t, (const float4 *)b.xs_t,
                                       (const int *)b.perm_t, (const float *)wgrid, f_orig, self_coef, u,
-                                      p->b.status, st);
+                                      p->b.status, p->test_flags & SE_TEST_SKIP_TILE_COPY, st);
     if (!e) p->launches++;
     return e;
 }

@@ -643,6 +643,13 @@ extern "C" se_status_t se_plan_set_timing(se_plan_t p, int on) {
     return SE_OK;
 }
 
+extern "C" se_status_t se_plan_set_test_flags(se_plan_t p, int flags) {
+    if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
+    if (flags & ~SE_TEST_SKIP_TILE_COPY) return fail(SE_ERR_INVALID_ARG, "unknown test flag");
+    p->test_flags = flags;
+    return SE_OK;
+}
+
 extern "C" se_status_t se_plan_set_overlap(se_plan_t p, int on) {
     if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
     if (on && !p->s_four) return fail(SE_ERR_NOT_SUPPORTED, "overlapped evaluation needs an FP32 free-space plan");

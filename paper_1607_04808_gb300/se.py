@@ -24,6 +24,7 @@ STATUS = {
     8: "SE_ERR_NOT_SUPPORTED",
 }
 STAGES = ["bin", "spread", "fft", "scale", "ifft", "gather", "real_setup", "real"]
+TEST_SKIP_TILE_COPY = 1  # se.h SE_TEST_SKIP_TILE_COPY
 BACK_STAGES = ["adj_bin", "adj_fourier", "adj_gather", "adj_real", "bin", "fourier", "grad_gather", "grad_real"]
 
 
@@ -90,6 +91,8 @@ def lib():
             L.se_plan_set_timing.argtypes = [vp, i32]
             L.se_plan_set_overlap.restype = i32
             L.se_plan_set_overlap.argtypes = [vp, i32]
+            L.se_plan_set_test_flags.restype = i32
+            L.se_plan_set_test_flags.argtypes = [vp, i32]
             L.se_plan_stage_times.restype = i32
             L.se_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
             L.se_plan_launch_count.restype = i64
@@ -271,6 +274,10 @@ class Plan:
     def set_overlap(self, on: bool = True):
         """se_plan_set_overlap: Fourier part and real-space sum on two streams (FP32)."""
         _check(lib().se_plan_set_overlap(self._h, 1 if on else 0))
+
+    def set_test_flags(self, flags: int):
+        """se_plan_set_test_flags (tests of the failure path; 0 restores normal operation)."""
+        _check(lib().se_plan_set_test_flags(self._h, int(flags)))
 
     def stage_times(self, backward: bool = False) -> dict:
         """se_plan_stage_times of the last timed call: se_eval's stages, or with
