@@ -243,6 +243,33 @@ __device__ __forceinline__ void pair(const RC<T> &rk, T dx, T dy, T dz, T r2, co
     }
 }
 
+// The stresslet pair applied to two strength pairs (a, b) and (a, c) with one
+// evaluation of the radial multipliers: acc += T^R(d)(a, b), acc2 += T^R(d)(a, c).
+template <typename T>
+__device__ __forceinline__ void pair_str2(const RC<T> &rk, T dx, T dy, T dz, T r2, const vec4<T> &a,
+                                          const vec4<T> &b, const vec4<T> &c, T acc[3], T acc2[3]) {
+    T rinv, A1, A2;
+    radial_ab<SE_STRESSLET, 0>(rk, r2, rinv, A1, A2);
+    const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
+    const T ha = hx * a.x + hy * a.y + hz * a.z;
+    {
+        const T hb = hx * b.x + hy * b.y + hz * b.z;
+        const T ab = a.x * b.x + a.y * b.y + a.z * b.z;
+        const T a1 = A1 * ha * hb;
+        acc[0] += a1 * hx + A2 * (hx * ab + a.x * hb + b.x * ha);
+        acc[1] += a1 * hy + A2 * (hy * ab + a.y * hb + b.y * ha);
+        acc[2] += a1 * hz + A2 * (hz * ab + a.z * hb + b.z * ha);
+    }
+    {
+        const T hc = hx * c.x + hy * c.y + hz * c.z;
+        const T ac = a.x * c.x + a.y * c.y + a.z * c.z;
+        const T a1 = A1 * ha * hc;
+        acc2[0] += a1 * hx + A2 * (hx * ac + a.x * hc + c.x * ha);
+        acc2[1] += a1 * hy + A2 * (hy * ac + a.y * hc + c.y * ha);
+        acc2[2] += a1 * hz + A2 * (hz * ac + a.z * hc + c.z * ha);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void kahan_add(T &s, T &comp, T x) {
     T y = x - comp;
@@ -1453,8 +1480,7 @@ __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, cons
         const vec4<T> v = qd[slot];
         const int m = qn[slot];
         if (ADJ) {
-            pair<T, SE_STRESSLET>(rk, v.x, v.y, v.z, v.w, fs[m], qp4, acc);
-            pair<T, SE_STRESSLET>(rk, v.x, v.y, v.z, v.w, fs[m], fp4, acc2);
+            pair_str2<T>(rk, v.x, v.y, v.z, v.w, fs[m], qp4, fp4, acc, acc2);
             return;
         }
         const vec4<T> qv = (KERNEL == SE_STRESSLET) ? qs[m] : zero4;
