@@ -252,20 +252,31 @@ def run_other_configs(dev, flush):
     out = {}
     x, f, q = W.stresslet_blobs(500_000, 2)
     t = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)  # noqa: E731
-    xd, fd, qd = torch.tensor(f32_in_box(x), device=dev), t(f), t(q)
-    plan = se.Plan("stresslet", len(x), BOX, prec="fp32", tol=2e-6)
-    u = torch.empty_like(xd)
-    ms = timed(lambda: plan.eval(xd, fd, qd, out=u))
-    plan.set_timing(True)
-    plan.eval(xd, fd, qd, out=u)
-    torch.cuda.synchronize()
-    st = plan.stage_times()
-    plan.check()
+    x32 = f32_in_box(x)
+    xd, fd, qd = torch.tensor(x32, device=dev), t(f), t(q)
+    # parameters from the points (se_choose_params_points), beside the
+    # selection that assumes uniform points
+    t_sel = time.perf_counter()
+    prm = se.choose_params_points("stresslet", x32, BOX, tol=2e-6)
+    t_sel = time.perf_counter() - t_sel
+    res = {}
+    for name, kw in (("points", {k: prm[k] for k in ("xi", "M", "P", "rc")}), ("uniform", {})):
+        plan = se.Plan("stresslet", len(x), BOX, prec="fp32", tol=2e-6, **kw)
+        u = torch.empty_like(xd)
+        ms = timed(lambda: plan.eval(xd, fd, qd, out=u))
+        plan.set_timing(True)
+        plan.eval(xd, fd, qd, out=u)
+        torch.cuda.synchronize()
+        st = plan.stage_times()
+        plan.check()
+        res[name] = (ms, {k: plan.params[k] for k in ("M", "P", "xi", "rc")}, st)
+        plan.close()
+    ms, pp, st = res["points"]
     out["stresslet_clustered"] = {
         "workload": "stresslet sum, N = 5e5: 16 Gaussian blobs (sigma 0.05) + 20 % uniform, FP32 at 2e-6",
         "value": len(x) / (ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms,
-        "params": {k: plan.params[k] for k in ("M", "P", "xi", "rc")}, "stages_ms": st}
-    plan.close()
+        "params": pp, "params_source": f"se_choose_params_points ({1e3 * t_sel:.0f} ms on the host)",
+        "stages_ms": st, "uniform_params": res["uniform"][1], "uniform_params_ms_per_step": res["uniform"][0]}
     x, tq, g = W.rotlet_uniform(200_000, 3)
     xd, td, gd = torch.tensor(f32_in_box(x), device=dev), t(tq), t(g)
     plan = se.Plan("rotlet", len(x), BOX, prec="fp32", tol=2e-6)

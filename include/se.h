@@ -248,6 +248,20 @@ se_status_t se_choose_params(se_kernel_t kernel, se_prec_t prec, int64_t N, doub
                              const se_params_t *in, se_params_t *out);
 
 /* Fill *out with the plan's parameters (chosen or given, plus derived values). */
+/* Parameter selection that looks at the points: x_host holds the N points
+ * (host memory, N x 3 row-major, float for SE_FP32 and double for SE_FP64) in
+ * the box (x0, y0, z0, Lx, Ly, Lz).  The mean number of neighbours of up to
+ * 4096 sampled points (every (N/4096)-th) is measured at 64 radii up to the
+ * cutoff chosen for uniform points and divided by its value for uniform points
+ * in the box; the work model that balances the real-space pairs against the
+ * grid and FFT work (used when xi, M, rc and max_fft are left to the library)
+ * then counts pairs with that factor, so clustered points get a larger xi and
+ * a smaller cutoff.  With any of xi, M, rc or max_fft fixed in `in`, the
+ * result is that of se_choose_params.  Host only; the points are not kept.
+ * Errors: SE_ERR_INVALID_ARG for NULL pointers, N < 1 or a side <= 0. */
+se_status_t se_choose_params_points(se_kernel_t kernel, se_prec_t prec, int64_t N, const double box[6],
+                                    const void *x_host, double tol, const se_params_t *in, se_params_t *out);
+
 se_status_t se_plan_get_params(se_plan_t plan, se_params_t *out);
 
 /* Grid sizes per dimension (x, y, z): M (box), Mtilde (extended grid), the FFT

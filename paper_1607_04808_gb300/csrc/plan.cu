@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <string>
 #include <type_traits>
+#include <vector>
 
 #include "se_internal.cuh"
 
@@ -74,6 +75,26 @@ bool good_fft(int n, int prec) {
     return m == 1;
 }
 
+// Work model of an evaluation, relative to one ordered real-space pair: the
+// pairs within rc (times the points' neighbour factor), the spreading and
+// gather updates (N P^3, twice) and the FFT work (Mf^3 log2 Mf, six
+// transforms, the scaling folded in).  FP64 weights measured on GB300 at N =
+// 1e6 (200 ps per pair, 7.2 ps per update, 21 ps per FFT unit).  FP32 keeps
+// weights that favour smaller xi: a larger xi moves more of the sum into the
+// FP32 Fourier part, whose rounding error grows with it.  Several right-hand
+// sides: the grid and FFT work repeats per side, a pair's radial functions
+// are shared (batches evaluate full candidate lists: 1.5 x a pair, +1/3 per
+// extra side).
+double model_cost(int prec, int64_t N, double L, int P, int M, double rc, const PairFactor *pf, int n_rhs) {
+    const double cpair = 1.0, cgrid = (prec == SE_FP32) ? 0.12 : 0.036, cfft = (prec == SE_FP32) ? 0.6 : 0.11;
+    const double Mf = 2.0 * (M + P);
+    double pairs = (double)N * (double)N * 4.18879 * rc * rc * rc / (L * L * L);
+    if (pf) pairs *= pf->at(rc);
+    const double wpair = (n_rhs > 1) ? 1.5 * (1.0 + (n_rhs - 1) / 3.0) : 1.0;
+    return cpair * wpair * pairs +
+           n_rhs * (cgrid * (double)N * P * P * P * 2.0 + cfft * Mf * Mf * Mf * log2(Mf) * 6.0);
+}
+
 }  // namespace
 
 // Parameter selection.  Relative tolerances are turned into absolute RMS
@@ -84,8 +105,17 @@ bool good_fft(int n, int prec) {
 // tol/4 (Section 8.2: P = 16 ~ 8 digits, 24 ~ 12 digits).  With a bound on the
 // FFT size, xi is the largest value whose Fourier estimate at the largest
 // admissible M meets the budget; otherwise xi minimises a work model.
+double PairFactor::at(double r) const {
+    if (n <= 0 || !f) return 1.0;
+    const double u = r / dr - 1.0;  // f[i] at r = (i + 1) dr
+    if (u <= 0.0) return f[0];
+    if (u >= n - 1) return f[n - 1];
+    const int i = (int)u;
+    return f[i] + (u - i) * (f[i + 1] - f[i]);
+}
+
 se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
-                          double xi_arg, se_params_t *out, int n_rhs) {
+                          double xi_arg, se_params_t *out, int n_rhs, const PairFactor *pf) {
     se_params_t p;
     memset(&p, 0, sizeof(p));
     if (in) p = *in;
@@ -123,28 +153,13 @@ se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol,
             }
             xi = lo;
         } else {
-            // work model: time per ordered real-space pair, per spread+gather
-            // grid update (N P^3, twice) and per FFT point and level (Mf^3 log2 Mf,
-            // six transforms, the scaling folded in), relative to a pair.  FP64:
-            // measured on GB300 at N = 1e6 (200 ps per pair, 7.2 ps per update,
-            // 21 ps per FFT unit).  FP32 keeps weights that favour smaller xi: a
-            // larger xi moves more of the sum into the FP32 Fourier part, whose
-            // rounding error grows with it
+            // the xi of least modelled work (model_cost)
             double best = 1e300, bxi = 1.0 / L;
-            const double cpair = 1.0, cgrid = (prec == SE_FP32) ? 0.12 : 0.036,
-                         cfft = (prec == SE_FP32) ? 0.6 : 0.11;
             for (double x = 0.5 / L; x < 4000.0 / L; x *= 1.03) {
                 int M = min_M(kernel, Q, x, L, p.P, budget);
                 double rc = min_rc(kernel, Q, x, L, budget);
                 if (rc > L) continue;
-                double Mf = 2.0 * (M + p.P);
-                double pairs = (double)N * (double)N * 4.18879 * rc * rc * rc / (L * L * L);
-                // several right-hand sides: the grid and FFT work repeats per
-                // right-hand side, a pair's radial functions are shared (batches
-                // evaluate full candidate lists: 1.5 x a pair, +1/3 per extra side)
-                const double wpair = (n_rhs > 1) ? 1.5 * (1.0 + (n_rhs - 1) / 3.0) : 1.0;
-                double cost = cpair * wpair * pairs +
-                              n_rhs * (cgrid * (double)N * p.P * p.P * p.P * 2.0 + cfft * Mf * Mf * Mf * log2(Mf) * 6.0);
+                const double cost = model_cost(prec, N, L, p.P, M, rc, pf, n_rhs);
                 if (cost < best) { best = cost; bxi = x; }
             }
             xi = bxi;
@@ -380,11 +395,159 @@ se_status_t se::setup_plan(se_plan_s *p, int kernel, int prec, int64_t N, const 
 // the longest side at the same point density (the error estimates depend on
 // the density, xi and h), so M counts grid intervals along the longest side.
 se_status_t se::choose_box_params(int kernel, int prec, int64_t N, const double box[6], double tol,
-                                  const se_params_t *params, double xi, se_params_t *out, int n_rhs) {
+                                  const se_params_t *params, double xi, se_params_t *out, int n_rhs,
+                                  const PairFactor *pf) {
     const double lmax = std::max(box[3], std::max(box[4], box[5]));
     const double vol = box[3] * box[4] * box[5];
     const double neff = std::max(1.0, (double)N * lmax * lmax * lmax / vol);
-    return choose_params(kernel, prec, (int64_t)llround(neff), lmax, tol, params, xi, out, n_rhs);
+    return choose_params(kernel, prec, (int64_t)llround(neff), lmax, tol, params, xi, out, n_rhs, pf);
+}
+
+// Probability that two independent uniform points of the box a x b x c lie
+// within r of each other (r <= the shortest side): the volume of the
+// difference set's ball, [4 pi r^3 abc / 3 - pi r^4 (ab + bc + ca) / 2 +
+// 8 r^5 (a + b + c) / 15 - r^6 / 6] / (abc)^2.
+static double pair_prob_box(double r, double a, double b, double c) {
+    const double V = a * b * c, r3 = r * r * r;
+    return (4.18879020478639 * r3 * V - 1.5707963267948966 * r3 * r * (a * b + b * c + c * a) +
+            8.0 / 15.0 * r3 * r * r * (a + b + c) - r3 * r3 / 6.0) /
+           (V * V);
+}
+
+// Neighbour counts within r_i = (i + 1) r_max / NR of up to 4096 sampled points
+// (every (N / S)-th), from a cell list of side >= r_max, over the counts that
+// uniform points would give.
+static std::vector<double> pair_factor_table(const double *x, int64_t N, const double box[6], double r_max,
+                                             int NR) {
+    int nc[3];
+    double cs[3];
+    for (int d = 0; d < 3; d++) {
+        nc[d] = (int)std::max(1.0, std::min(256.0, floor(box[3 + d] / r_max)));
+        cs[d] = box[3 + d] / nc[d];
+    }
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    auto cell_of = [&](const double *p, int c[3]) {
+        for (int d = 0; d < 3; d++) c[d] = std::min(nc[d] - 1, std::max(0, (int)((p[d] - box[d]) / cs[d])));
+    };
+    std::vector<int64_t> start(ncell + 1, 0), order(N);
+    std::vector<int64_t> key(N);
+    for (int64_t i = 0; i < N; i++) {
+        int c[3];
+        cell_of(x + 3 * i, c);
+        key[i] = ((int64_t)c[2] * nc[1] + c[1]) * nc[0] + c[0];
+        start[key[i] + 1]++;
+    }
+    for (int64_t k = 0; k < ncell; k++) start[k + 1] += start[k];
+    {
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        for (int64_t i = 0; i < N; i++) order[fill[key[i]]++] = i;
+    }
+    const int64_t S = std::min<int64_t>(N, 4096);
+    std::vector<double> hist(NR, 0.0);
+    const double r2max = r_max * r_max, inv_dr = NR / r_max;
+    for (int64_t k = 0; k < S; k++) {
+        const int64_t s = k * N / S;
+        const double *ps = x + 3 * s;
+        int c[3];
+        cell_of(ps, c);
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int ix = c[0] + dx, iy = c[1] + dy, iz = c[2] + dz;
+                    if (ix < 0 || iy < 0 || iz < 0 || ix >= nc[0] || iy >= nc[1] || iz >= nc[2]) continue;
+                    const int64_t cell = ((int64_t)iz * nc[1] + iy) * nc[0] + ix;
+                    for (int64_t q = start[cell]; q < start[cell + 1]; q++) {
+                        const int64_t j = order[q];
+                        if (j == s) continue;
+                        const double ex = x[3 * j] - ps[0], ey = x[3 * j + 1] - ps[1], ez = x[3 * j + 2] - ps[2];
+                        const double d2 = ex * ex + ey * ey + ez * ez;
+                        if (d2 <= r2max) hist[std::min(NR - 1, (int)(sqrt(d2) * inv_dr))] += 1.0;
+                    }
+                }
+    }
+    std::vector<double> f(NR);
+    double cum = 0.0;
+    for (int i = 0; i < NR; i++) {
+        cum += hist[i];
+        const double r = (i + 1) * r_max / NR;
+        const double expect = (double)(N - 1) * pair_prob_box(r, box[3], box[4], box[5]);
+        f[i] = (expect > 0.0 && cum > 0.0) ? (cum / S) / expect : 1.0;
+    }
+    return f;
+}
+
+extern "C" se_status_t se_choose_params_points(se_kernel_t kernel, se_prec_t prec, int64_t N, const double box[6],
+                                               const void *x_host, double tol, const se_params_t *in,
+                                               se_params_t *out) {
+    if (!out || !box || !x_host) return fail(SE_ERR_INVALID_ARG, "NULL argument");
+    if (kernel < SE_STOKESLET || kernel > SE_ROTLET) return fail(SE_ERR_INVALID_ARG, "unknown kernel");
+    if (N < 1) return fail(SE_ERR_INVALID_ARG, "N must be positive");
+    for (int d = 0; d < 3; d++)
+        if (!(box[3 + d] > 0)) return fail(SE_ERR_INVALID_ARG, "box sides must be positive");
+    // the choice for uniform points first: clustering adds pairs at every
+    // radius, so the work model's optimum moves to a smaller cutoff
+    se_params_t uni;
+    se_status_t s = choose_box_params(kernel, prec, N, box, tol, in, 0.0, &uni);
+    if (s != SE_OK) return s;
+    const bool model = !(in && (in->xi > 0 || in->M > 0 || in->max_fft > 0 || in->rc > 0));
+    const double smin = std::min(box[3], std::min(box[4], box[5]));
+    if (!model || N < 2 || !(uni.rc < smin)) {
+        *out = uni;
+        return SE_OK;
+    }
+    std::vector<double> xd;
+    const double *x = (const double *)x_host;
+    if (prec == SE_FP32) {
+        xd.resize(3 * (size_t)N);
+        const float *xf = (const float *)x_host;
+        for (size_t i = 0; i < xd.size(); i++) xd[i] = xf[i];
+        x = xd.data();
+    }
+    const int NR = 64;
+    const std::vector<double> f = pair_factor_table(x, N, box, uni.rc, NR);
+    PairFactor pf;
+    pf.n = NR;
+    pf.dr = uni.rc / NR;
+    pf.f = f.data();
+    se_params_t pm;
+    s = choose_box_params(kernel, prec, N, box, tol, in, 0.0, &pm, 1, &pf);
+    if (s != SE_OK) return s;
+    // FFT length: of the lengths 2^a 3^b (5) around 2 (M + P) -- those measured
+    // fast with cuFFT on GB300; 350, 400, 420 and 448 took 1.2 to 1.5 times the
+    // time per point of 360, 384 and 432 -- the one of least modelled work
+    auto fast = [](int n) {
+        if (n < 8 || (n & 3)) return false;
+        int m = n, fives = 0;
+        while (m % 2 == 0) m /= 2;
+        while (m % 3 == 0) m /= 3;
+        while (m % 5 == 0) m /= 5, fives++;
+        return m == 1 && fives <= 1;
+    };
+    const int Mf0 = 2 * (pm.M + pm.P);
+    int lo = Mf0, hi = Mf0;
+    while (lo > 2 * (pm.P + 2) && !fast(lo)) lo -= 2;
+    while (!fast(hi)) hi += 2;
+    const double lmax = std::max(box[3], std::max(box[4], box[5]));
+    const int64_t neff = (int64_t)llround(std::max(1.0, (double)N * lmax * lmax * lmax / (box[3] * box[4] * box[5])));
+    double best = 1e300;
+    *out = pm;
+    for (int Mf : {lo, hi}) {
+        if (!fast(Mf)) continue;
+        se_params_t fin;
+        memset(&fin, 0, sizeof(fin));
+        if (in) fin = *in;
+        fin.M = Mf / 2 - pm.P;
+        fin.P = pm.P;
+        if (fin.M < 2) continue;
+        se_params_t c;
+        if (choose_box_params(kernel, prec, N, box, tol, &fin, 0.0, &c, 1, &pf) != SE_OK) continue;
+        const double cost = model_cost(prec, neff, lmax, c.P, c.M, c.rc, &pf, 1);
+        if (cost < best) {
+            best = cost;
+            *out = c;
+        }
+    }
+    return SE_OK;
 }
 
 extern "C" se_status_t se_plan_create(se_kernel_t kernel, int64_t N, double xi, const double box[4], double tol,

@@ -375,9 +375,19 @@ inline int scan_launch_count(int n) { return n <= 64 * 1024 ? 1 : 3; }
 template <typename T> const GP<T> &gp(const se_plan_s *p);
 template <> inline const GP<float> &gp<float>(const se_plan_s *p) { return p->gpf; }
 template <> inline const GP<double> &gp<double>(const se_plan_s *p) { return p->gpd; }
+// Neighbour statistics of actual points for the work model: f[i] is the mean
+// number of neighbours within r_i = (i + 1) dr divided by its value for
+// uniformly distributed points in the same box (1 for uniform points).
+struct PairFactor {
+    int n = 0;
+    double dr = 0.0;
+    const double *f = nullptr;
+    double at(double r) const;
+};
 se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol, const se_params_t *in,
-                          double xi_arg, se_params_t *out, int n_rhs = 1);
+                          double xi_arg, se_params_t *out, int n_rhs = 1, const PairFactor *pf = nullptr);
 se_status_t choose_box_params(int kernel, int prec, int64_t N, const double box[6], double tol,
-                              const se_params_t *params, double xi, se_params_t *out, int n_rhs = 1);
+                              const se_params_t *params, double xi, se_params_t *out, int n_rhs = 1,
+                              const PairFactor *pf = nullptr);
 
 }  // namespace se

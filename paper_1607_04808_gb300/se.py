@@ -80,6 +80,9 @@ def lib():
             L.se_eval_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
             L.se_eval_backward_q.restype = i32
             L.se_eval_backward_q.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.se_choose_params_points.restype = i32
+            L.se_choose_params_points.argtypes = [i32, i32, i64, ctypes.POINTER(dbl), vp, dbl,
+                                                  ctypes.POINTER(SEParams), ctypes.POINTER(SEParams)]
             L.se_choose_params.restype = i32
             L.se_choose_params.argtypes = [i32, i32, i64, dbl, dbl, dbl, ctypes.POINTER(SEParams),
                                            ctypes.POINTER(SEParams)]
@@ -420,6 +423,27 @@ def choose_params(kernel: str, N: int, L: float = 1.0, tol: float = 0.0, prec: s
     pout = SEParams()
     _check(lib().se_choose_params(KERNELS[kernel], PRECS[prec], int(N), float(L), float(tol), float(xi),
                                   ctypes.byref(pin), ctypes.byref(pout)))
+    return {k: getattr(pout, k) for k in ("xi", "rc", "M", "P", "deltaL_policy", "max_fft")}
+
+
+def choose_params_points(kernel: str, x, box=(0.0, 0.0, 0.0, 1.0), tol: float = 0.0, prec: str = "fp32",
+                         **overrides) -> dict:
+    """Parameters for these points (se_choose_params_points; host only): x is an
+    (N, 3) array or CPU tensor, box (x0, y0, z0, L) or (x0, y0, z0, Lx, Ly, Lz)."""
+    import numpy as np
+    xa = np.ascontiguousarray(np.asarray(x.cpu() if hasattr(x, "cpu") else x),
+                              dtype=np.float32 if prec == "fp32" else np.float64)
+    if xa.ndim != 2 or xa.shape[1] != 3:
+        raise ValueError("x must be (N, 3)")
+    b = tuple(float(v) for v in box)
+    if len(b) == 4:
+        b = b + (b[3], b[3])
+    boxa = (ctypes.c_double * 6)(*b)
+    pin = SEParams(**{k: v for k, v in overrides.items()})
+    pout = SEParams()
+    _check(lib().se_choose_params_points(KERNELS[kernel], PRECS[prec], xa.shape[0], boxa,
+                                         xa.ctypes.data_as(ctypes.c_void_p), float(tol), ctypes.byref(pin),
+                                         ctypes.byref(pout)))
     return {k: getattr(pout, k) for k in ("xi", "rc", "M", "P", "deltaL_policy", "max_fft")}
 
 

@@ -355,6 +355,24 @@ def test_full_size_fp32_stresslet_blobs_sampled():
     assert rel_l2(u[idx], ref) <= 2e-6
 
 
+def test_full_size_fp32_stresslet_blobs_point_aware_parameters():
+    """The same clustered workload with the parameters se_choose_params_points
+    picks from the points (a larger xi, a finer grid): 256 sampled targets
+    against the exact direct sum, FP32 bar 2e-6."""
+    pkg = P()
+    N = 500_000
+    x, f, q = W.stresslet_blobs(N, 2)
+    x32 = np.minimum(np.asarray(x, dtype=np.float32), np.nextafter(np.float32(1.0), np.float32(0)))
+    prm = pkg.choose_params_points("stresslet", x32, tol=2e-6)
+    assert prm["M"] > pkg.choose_params("stresslet", N, tol=2e-6)["M"]
+    x64, f32, q32 = x32.astype(np.float64), as32(f), as32(q)
+    u, got = gpu_eval("stresslet", x64, f32, q32, "fp32", xi=prm["xi"], M=prm["M"], P=prm["P"], rc=prm["rc"])
+    assert got["M"] == prm["M"]
+    idx = np.random.default_rng(2).choice(N, 256, replace=False)
+    ref = direct.direct("stresslet", x64, f32, q32, targets=idx)
+    assert rel_l2(u[idx], ref) <= 2e-6
+
+
 def test_full_size_fp32_rotlet_backward_sampled():
     """N = 2e5 rotlet, FP32 forward and backward (grid recomputed): u, dL/df and
     dL/dx at 256 sampled points against the exact direct sums, and dL/dx
