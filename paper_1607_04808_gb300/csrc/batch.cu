@@ -226,6 +226,38 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
         if (st != SE_OK) return st;
     }
     B->P = Pmax;
+#ifndef SE_BATCH_FAST_FFT
+#define SE_BATCH_FAST_FFT 1
+#endif
+    // FFT lengths: each system's moved to the fast length around it (below or
+    // above, the one of least modelled work), so that the size classes are
+    // fewer and their batched transforms faster; explicit M or an FFT cap stay
+    const bool fixed = params && (params->M > 0 || params->max_fft > 0 || params->xi > 0);
+    for (int s = 0; s < S && SE_BATCH_FAST_FFT && !fixed; s++) {
+        const int Mf0 = 2 * (pr[s].M + pr[s].P);
+        if (fast_fft_len(Mf0)) continue;
+        int lo = Mf0, hi = Mf0;
+        while (lo > 2 * (pr[s].P + 2) && !fast_fft_len(lo)) lo -= 2;
+        while (!fast_fft_len(hi)) hi += 2;
+        double best = 1e300;
+        se_params_t pick = pr[s];
+        for (int Mf : {lo, hi}) {
+            if (!fast_fft_len(Mf) || Mf / 2 - pr[s].P < 2) continue;
+            se_params_t in;
+            memset(&in, 0, sizeof(in));
+            if (params) in = *params;
+            in.P = Pmax;
+            in.M = Mf / 2 - Pmax;
+            se_params_t c;
+            if (choose_params(kernel, prec, N_s[s], box_s[4 * s + 3], tol, &in, 0.0, &c, R) != SE_OK) continue;
+            const double cost = model_cost(prec, N_s[s], box_s[4 * s + 3], c.P, c.M, c.rc, nullptr, R);
+            if (cost < best) {
+                best = cost;
+                pick = c;
+            }
+        }
+        pr[s] = pick;
+    }
     // geometry and the precomputed kernel of every system
     for (int s = 0; s < S; s++) {
         se_plan_s *p = new se_plan_s();

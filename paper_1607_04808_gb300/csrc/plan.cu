@@ -85,6 +85,8 @@ bool good_fft(int n, int prec) {
 // sides: the grid and FFT work repeats per side, a pair's radial functions
 // are shared (batches evaluate full candidate lists: 1.5 x a pair, +1/3 per
 // extra side).
+}  // namespace
+
 double model_cost(int prec, int64_t N, double L, int P, int M, double rc, const PairFactor *pf, int n_rhs) {
     const double cpair = 1.0, cgrid = (prec == SE_FP32) ? 0.12 : 0.036, cfft = (prec == SE_FP32) ? 0.6 : 0.11;
     const double Mf = 2.0 * (M + P);
@@ -95,7 +97,17 @@ double model_cost(int prec, int64_t N, double L, int P, int M, double rc, const 
            n_rhs * (cgrid * (double)N * P * P * P * 2.0 + cfft * Mf * Mf * Mf * log2(Mf) * 6.0);
 }
 
-}  // namespace
+// FFT lengths measured fast with cuFFT on GB300: 2^a 3^b, times at most one 5,
+// and a multiple of 4 (350, 400, 420 and 448 took 1.2 to 1.5 times the time
+// per point of 320, 360, 384 and 432).
+bool fast_fft_len(int n) {
+    if (n < 8 || (n & 3)) return false;
+    int m = n, fives = 0;
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    while (m % 5 == 0) m /= 5, fives++;
+    return m == 1 && fives <= 1;
+}
 
 // Parameter selection.  Relative tolerances are turned into absolute RMS
 // budgets with the RMS of u for uniformly distributed points and unit-variance
@@ -512,17 +524,9 @@ extern "C" se_status_t se_choose_params_points(se_kernel_t kernel, se_prec_t pre
     se_params_t pm;
     s = choose_box_params(kernel, prec, N, box, tol, in, 0.0, &pm, 1, &pf);
     if (s != SE_OK) return s;
-    // FFT length: of the lengths 2^a 3^b (5) around 2 (M + P) -- those measured
-    // fast with cuFFT on GB300; 350, 400, 420 and 448 took 1.2 to 1.5 times the
-    // time per point of 360, 384 and 432 -- the one of least modelled work
-    auto fast = [](int n) {
-        if (n < 8 || (n & 3)) return false;
-        int m = n, fives = 0;
-        while (m % 2 == 0) m /= 2;
-        while (m % 3 == 0) m /= 3;
-        while (m % 5 == 0) m /= 5, fives++;
-        return m == 1 && fives <= 1;
-    };
+    // FFT length: of the fast lengths (fast_fft_len) around 2 (M + P), the one
+    // of least modelled work
+    auto fast = fast_fft_len;
     const int Mf0 = 2 * (pm.M + pm.P);
     int lo = Mf0, hi = Mf0;
     while (lo > 2 * (pm.P + 2) && !fast(lo)) lo -= 2;

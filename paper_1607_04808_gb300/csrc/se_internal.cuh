@@ -389,5 +389,9 @@ se_status_t choose_params(int kernel, int prec, int64_t N, double L, double tol,
 se_status_t choose_box_params(int kernel, int prec, int64_t N, const double box[6], double tol,
                               const se_params_t *params, double xi, se_params_t *out, int n_rhs = 1,
                               const PairFactor *pf = nullptr);
+// the work model of the parameter selection (relative to one real-space pair)
+double model_cost(int prec, int64_t N, double L, int P, int M, double rc, const PairFactor *pf, int n_rhs);
+// FFT lengths measured fast with cuFFT on GB300
+bool fast_fft_len(int n);
 
 }  // namespace se
