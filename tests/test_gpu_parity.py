@@ -373,6 +373,23 @@ def test_full_size_fp32_stresslet_blobs_point_aware_parameters():
     assert rel_l2(u[idx], ref) <= 2e-6
 
 
+def test_full_size_fp32_stokeslet_uncapped_point_aware_parameters():
+    """N = 1e6 uniform stokeslet, FP32 at 2e-6, without the FFT cap: the
+    parameters se_choose_params_points picks (a larger xi than under the cap,
+    FFT 360^3); 96 sampled targets against the exact direct sum."""
+    pkg = P()
+    N = 1_000_000
+    x, f = W.stokeslet_uniform(N, 1)
+    x32 = np.minimum(np.asarray(x, dtype=np.float32), np.nextafter(np.float32(1.0), np.float32(0)))
+    prm = pkg.choose_params_points("stokeslet", x32, tol=2e-6)
+    x64, f32 = x32.astype(np.float64), as32(f)
+    u, got = gpu_eval("stokeslet", x64, f32, None, "fp32", xi=prm["xi"], M=prm["M"], P=prm["P"], rc=prm["rc"])
+    assert got["M"] == prm["M"] and got["xi"] > 45.0
+    idx = np.random.default_rng(6).choice(N, 96, replace=False)
+    ref = direct.direct("stokeslet", x64, f32, targets=idx)
+    assert rel_l2(u[idx], ref) <= 2e-6
+
+
 def test_full_size_fp32_rotlet_backward_sampled():
     """N = 2e5 rotlet, FP32 forward and backward (grid recomputed): u, dL/df and
     dL/dx at 256 sampled points against the exact direct sums, and dL/dx
