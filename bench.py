@@ -254,7 +254,7 @@ def run_other_configs(dev, flush, x32=None, f32=None):
         # the headline points without the FFT cap: parameters from the points
         prm = se.choose_params_points("stokeslet", x32.cpu().numpy(), BOX, tol=2e-6)
         plan = se.Plan("stokeslet", x32.shape[0], BOX, prec="fp32", tol=2e-6,
-                       **{k: prm[k] for k in ("xi", "M", "P", "rc")})
+                       **{k: prm[k] for k in ("xi", "M", "P", "rc", "cell_width")})
         u = torch.empty_like(x32)
         ms = timed(lambda: plan.eval(x32, f32, out=u))
         plan.set_timing(True)
@@ -279,7 +279,7 @@ def run_other_configs(dev, flush, x32=None, f32=None):
     prm = se.choose_params_points("stresslet", x32, BOX, tol=2e-6)
     t_sel = time.perf_counter() - t_sel
     res = {}
-    for name, kw in (("points", {k: prm[k] for k in ("xi", "M", "P", "rc")}), ("uniform", {})):
+    for name, kw in (("points", {k: prm[k] for k in ("xi", "M", "P", "rc", "cell_width")}), ("uniform", {})):
         plan = se.Plan("stresslet", len(x), BOX, prec="fp32", tol=2e-6, **kw)
         u = torch.empty_like(xd)
         ms = timed(lambda: plan.eval(xd, fd, qd, out=u))

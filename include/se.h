@@ -69,6 +69,9 @@ typedef struct {
     int P;              /* Gaussian support: P^3 grid points per source (Section 5.2)  */
     int deltaL_policy;  /* 0: delta_L = d = hP;  1: eq. deltaL_cond (Section 5.3)      */
     int max_fft;        /* upper bound on the FFT size 2*Mtilde per dimension (0: none) */
+    double cell_width;  /* FP32 real-space cells across their rows (0: from the mean point
+                           density; se_choose_params_points sets it from the density
+                           around the points' pairs)                                   */
     /* derived, filled by se_plan_get_params (ignored on input) */
     int Mtilde;         /* extended grid points per dimension, M + delta_L/h           */
     int Mg;             /* precompute grid size: smallest even > (1+sqrt 3) Mtilde      */

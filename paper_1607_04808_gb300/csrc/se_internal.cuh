@@ -233,6 +233,7 @@ struct se_plan_s {
     void *wgrid = nullptr;     // 3 x Mf^3 real (C2R output)
     void *wgrid2 = nullptr;    // 3 x Mf^3 real (backward: adjoint grid)
     void *gsort = nullptr;     // N x 4 (backward: the upstream gradient in cell order)
+    double cell_width = 0.0;   // se_params_t.cell_width (0: from the mean density)
     int test_flags = 0;        // se_plan_set_test_flags
     void *spec2 = nullptr;     // backward spectrum
     void *tmp3 = nullptr;      // N x 3 scratch in plan precision (backward)

@@ -37,7 +37,8 @@ class SEError(RuntimeError):
 class SEParams(ctypes.Structure):
     _fields_ = [
         ("xi", ctypes.c_double), ("rc", ctypes.c_double), ("M", ctypes.c_int), ("P", ctypes.c_int),
-        ("deltaL_policy", ctypes.c_int), ("max_fft", ctypes.c_int), ("Mtilde", ctypes.c_int),
+        ("deltaL_policy", ctypes.c_int), ("max_fft", ctypes.c_int), ("cell_width", ctypes.c_double),
+        ("Mtilde", ctypes.c_int),
         ("Mg", ctypes.c_int), ("eta", ctypes.c_double), ("h", ctypes.c_double),
     ]
 
@@ -152,7 +153,7 @@ class Plan:
 
     def __init__(self, kernel: str, N: int, box=(0.0, 0.0, 0.0, 1.0), *, xi: float = 0.0,
                  tol: float = 0.0, prec: str = "fp32", M: int = 0, P: int = 0, rc: float = 0.0,
-                 deltaL_policy: int = 0, max_fft: int = 0, periodic: bool = False):
+                 deltaL_policy: int = 0, max_fft: int = 0, periodic: bool = False, cell_width: float = 0.0):
         self.kernel = kernel
         self.kid = KERNELS[kernel]
         self.N = int(N)
@@ -163,7 +164,7 @@ class Plan:
             raise ValueError("box: (x0, y0, z0, L) or (x0, y0, z0, Lx, Ly, Lz); periodic plans take a cube")
         self.periodic = bool(periodic)
         prm = SEParams(xi=float(xi), rc=float(rc), M=int(M), P=int(P),
-                       deltaL_policy=int(deltaL_policy), max_fft=int(max_fft))
+                       deltaL_policy=int(deltaL_policy), max_fft=int(max_fft), cell_width=float(cell_width))
         boxa = (ctypes.c_double * len(self.box))(*self.box)
         if self.periodic:
             create = lib().se_plan_create_periodic
@@ -444,7 +445,7 @@ def choose_params_points(kernel: str, x, box=(0.0, 0.0, 0.0, 1.0), tol: float = 
     _check(lib().se_choose_params_points(KERNELS[kernel], PRECS[prec], xa.shape[0], boxa,
                                          xa.ctypes.data_as(ctypes.c_void_p), float(tol), ctypes.byref(pin),
                                          ctypes.byref(pout)))
-    return {k: getattr(pout, k) for k in ("xi", "rc", "M", "P", "deltaL_policy", "max_fft")}
+    return {k: getattr(pout, k) for k in ("xi", "rc", "M", "P", "deltaL_policy", "max_fft", "cell_width")}
 
 
 def version() -> str:

@@ -366,7 +366,8 @@ def test_full_size_fp32_stresslet_blobs_point_aware_parameters():
     prm = pkg.choose_params_points("stresslet", x32, tol=2e-6)
     assert prm["M"] > pkg.choose_params("stresslet", N, tol=2e-6)["M"]
     x64, f32, q32 = x32.astype(np.float64), as32(f), as32(q)
-    u, got = gpu_eval("stresslet", x64, f32, q32, "fp32", xi=prm["xi"], M=prm["M"], P=prm["P"], rc=prm["rc"])
+    u, got = gpu_eval("stresslet", x64, f32, q32, "fp32", xi=prm["xi"], M=prm["M"], P=prm["P"], rc=prm["rc"],
+                      cell_width=prm["cell_width"])
     assert got["M"] == prm["M"]
     idx = np.random.default_rng(2).choice(N, 256, replace=False)
     ref = direct.direct("stresslet", x64, f32, q32, targets=idx)
@@ -383,7 +384,8 @@ def test_full_size_fp32_stokeslet_uncapped_point_aware_parameters():
     x32 = np.minimum(np.asarray(x, dtype=np.float32), np.nextafter(np.float32(1.0), np.float32(0)))
     prm = pkg.choose_params_points("stokeslet", x32, tol=2e-6)
     x64, f32 = x32.astype(np.float64), as32(f)
-    u, got = gpu_eval("stokeslet", x64, f32, None, "fp32", xi=prm["xi"], M=prm["M"], P=prm["P"], rc=prm["rc"])
+    u, got = gpu_eval("stokeslet", x64, f32, None, "fp32", xi=prm["xi"], M=prm["M"], P=prm["P"], rc=prm["rc"],
+                      cell_width=prm["cell_width"])
     assert got["M"] == prm["M"] and got["xi"] > 45.0
     idx = np.random.default_rng(6).choice(N, 96, replace=False)
     ref = direct.direct("stokeslet", x64, f32, targets=idx)

@@ -23,6 +23,11 @@ def in_box32(x, top=1.0):
     return np.minimum(x.astype(np.float32), np.nextafter(np.float32(top), np.float32(0)))
 
 
+def same(a, b):
+    """Equal selections (the point-aware one also gives the real-space cell width)."""
+    return all(a[k] == b[k] for k in a)
+
+
 def fast_fft(n):
     m, fives = n, 0
     while m % 2 == 0:
@@ -42,8 +47,11 @@ def test_uniform_points_keep_the_uniform_choice(kernel, n):
     a = p.choose_params(kernel, n, tol=2e-6)
     b = p.choose_params_points(kernel, x, tol=2e-6)
     mfa, mfb = 2 * (a["M"] + a["P"]), 2 * (b["M"] + b["P"])
+    # FP32 real-space cells from the density around the pairs: the mean density here
+    w = 1.1 * (8.0 / n) ** (1.0 / 3.0)
+    assert abs(b["cell_width"] / w - 1.0) < 0.1
     if fast_fft(mfa):
-        assert a == b
+        assert same(a, b)
     else:
         # the point-aware selection moves to one of the two fast FFT lengths
         # around the uniform choice's
@@ -63,6 +71,8 @@ def test_clustered_points_move_work_to_the_grid():
     b = p.choose_params_points("stresslet", x, tol=2e-6)
     assert b["xi"] > 1.15 * a["xi"] and b["rc"] < a["rc"] / 1.15 and b["M"] > a["M"]
     assert b["P"] == a["P"] and fast_fft(2 * (b["M"] + b["P"]))
+    # cells sized for the density around the pairs, well above the mean density
+    assert b["cell_width"] < 0.7 * 1.1 * (8.0 / n) ** (1.0 / 3.0)
     # the same tolerance bookkeeping: xi rc (the real-space error's argument)
     # stays about the same
     assert abs(b["xi"] * b["rc"] - a["xi"] * a["rc"]) < 0.1 * a["xi"] * a["rc"]
@@ -84,7 +94,7 @@ def test_fixed_parameters_and_caps_are_respected():
     n = 100_000
     x = in_box32(W.blob_points(n, 3))
     for kw in ({"max_fft": 256}, {"M": 64}, {"xi": 30.0}):
-        assert p.choose_params_points("stokeslet", x, tol=2e-6, **kw) == p.choose_params("stokeslet", n, tol=2e-6, **kw)
+        assert same(p.choose_params("stokeslet", n, tol=2e-6, **kw), p.choose_params_points("stokeslet", x, tol=2e-6, **kw))
 
 
 def test_fp64_points_and_boxes():
