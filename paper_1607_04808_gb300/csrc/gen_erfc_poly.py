@@ -1,17 +1,22 @@
 """Generate erfc_poly.cuh: polynomials Q(t) ~ erfcx(x) = exp(x^2) erfc(x) in the
 variable t = 1 / (2 + x), so that the FP32 real-space kernel evaluates
 erfc(x) = exp(-x^2) Q(t) and shares exp(-x^2) with the Gaussian terms of the
-screened kernels (Section 3.2).  Two fits: degree 8 on x in [0, 5] (enough for
-the cutoffs the parameter selection gives at FP32 tolerances) and degree 10 on
-[0, 8] (beyond 8, erfc(x) < 1e-28).  Weighted least squares on Chebyshev nodes
+screened kernels (Section 3.2).  Two FP32 fits: degree 8 on x in [0, 5] (enough
+for the cutoffs the parameter selection gives at FP32 tolerances) and degree
+10 on [0, 8] (beyond 8, erfc(x) < 1e-28); one FP64 fit, degree 18 on [0, 8].  Weighted least squares on Chebyshev nodes
 (relative error), with numpy; run this script to regenerate the header.
 """
 import os
 
 import numpy as np
+from numpy.polynomial import chebyshev as cheb
 from scipy.special import erfcx
 
 FITS = [("Q5", 5.0, 8), ("Q8", 8.0, 10)]
+# FP64: degree 18 on x in [0, 8], fitted in the Chebyshev basis of the
+# shifted variable s = (2 t - (t_max + t_min)) / (t_max - t_min) in [-1, 1] and
+# evaluated as a power series in s (coefficients below 0.5: well conditioned)
+FIT64 = (8.0, 18)
 
 
 def fit(xmax, deg):
@@ -35,6 +40,22 @@ def fit(xmax, deg):
     return c, err, err32
 
 
+def fit64(xmax, deg):
+    tmin, tmax = 1.0 / (2.0 + xmax), 0.5
+    k = np.arange(6000)
+    tn = 0.5 * (tmax + tmin) + 0.5 * (tmax - tmin) * np.cos(np.pi * (k + 0.5) / len(k))
+    y = erfcx(1.0 / tn - 2.0)
+    sn = (2.0 * tn - (tmax + tmin)) / (tmax - tmin)
+    c = cheb.cheb2poly(cheb.chebfit(sn, y, deg, w=1.0 / y))
+    xs = np.linspace(0, xmax, 400001)
+    ss = (2.0 / (2.0 + xs) - (tmax + tmin)) / (tmax - tmin)
+    acc = np.zeros_like(ss)
+    for cc in c[::-1]:
+        acc = acc * ss + cc
+    err = np.max(np.abs(acc / erfcx(xs) - 1.0))
+    return c, 2.0 / (tmax - tmin), -(tmax + tmin) / (tmax - tmin), err
+
+
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
     lines = ["// Generated by gen_erfc_poly.py: erfcx(x) ~ sum_k Q[k] t^k, t = 1/(2+x).", "#pragma once"]
@@ -49,6 +70,19 @@ def main():
         lines += ["    %.9ef," % v for v in c]
         lines += ["};"]
         print("%s: max rel err fp64 %.3e, fp32 %.3e" % (name, err, err32))
+    xmax, deg = FIT64
+    c, sa, sb, err = fit64(xmax, deg)
+    lines += [
+        "// FP64: x in [0, %g], degree %d in s = SA t + SB (t = 1/(2+x)): max relative error %.2e." % (xmax, deg, err),
+        "#define SE_ERFC_DEG64 %d" % deg,
+        "#define SE_ERFC_XMAX64 %.1f" % xmax,
+        "#define SE_ERFC_SA64 %.17e" % sa,
+        "#define SE_ERFC_SB64 %.17e" % sb,
+        "__device__ __constant__ const double ERFC_QD[%d] = {" % (deg + 1),
+    ]
+    lines += ["    %.17e," % v for v in c]
+    lines += ["};"]
+    print("QD: max rel err fp64 %.3e" % err)
     lines.append("")
     open(os.path.join(here, "erfc_poly.cuh"), "w").write("\n".join(lines))
 

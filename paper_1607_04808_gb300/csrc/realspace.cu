@@ -8,7 +8,8 @@
 //   Omega^R = eps_jlm r_m B                                                (eq. RR_Op / 2)
 // Each kernel needs two radial multipliers (a, b below), functions of r.  FP32
 // evaluates erfc(x) = e Q(1/(2+x)) with a fitted erfcx polynomial Q
-// (erfc_poly.cuh), sharing the exponential e; FP64 uses erfc and exp.
+// (erfc_poly.cuh), sharing the exponential e; FP64 uses exp and a degree-18
+// fit of erfcx in the same variable (the library erfc beyond x = 8).
 //
 // Cell list: points are sorted by cell (cells of width >= rc/5 across rows in
 // FP32, rc/3 in FP64, and >= rc/16 along x, x fastest), so each (y, z) row of
@@ -198,14 +199,31 @@ __device__ __forceinline__ void grad_pair(const RC<float> &rk, float dx, float d
     }
 }
 
-// FP64: the same multipliers from erfc and exp
+// FP64 erfc(x) = e Q64(s), e = exp(-x^2), s = SA t + SB, t = 1/(2 + x): the
+// degree-18 fit of erfcx (relative error 8e-15 on [0, 8]); the library's erfc
+// beyond (erfc(8) < 1e-28).
+#ifndef SE_ERFC_FIT64
+#define SE_ERFC_FIT64 1
+#endif
+__device__ __forceinline__ double erfc_fit64(double x, double e) {
+    if (SE_ERFC_FIT64 && x <= SE_ERFC_XMAX64) {
+        const double s = fma(SE_ERFC_SA64, 1.0 / (2.0 + x), SE_ERFC_SB64);
+        double q = ERFC_QD[SE_ERFC_DEG64];
+#pragma unroll
+        for (int k = SE_ERFC_DEG64 - 1; k >= 0; k--) q = fma(q, s, ERFC_QD[k]);
+        return e * q;
+    }
+    return erfc(x);
+}
+
+// FP64: the same multipliers from exp and erfc
 template <int KERNEL, int PV>
 __device__ __forceinline__ void radial_ab(const RC<double> &rk, double r2, double &rinv, double &a, double &b) {
     rinv = rsqrt(r2);
     const double r = r2 * rinv;
     const double x = rk.xi * r;
     const double e = exp(-x * x);
-    const double ec = erfc(x);
+    const double ec = erfc_fit64(x, e);
     const double g = 1.1283791670955126 * x * e;  // (2/sqrt(pi)) x e
     if (KERNEL == SE_STRESSLET) {
         a = -2.0 * (3.0 * ec + g * (3.0 + 2.0 * x * x)) * (rinv * rinv);
@@ -1568,14 +1586,15 @@ __global__ void __launch_bounds__(256) k_real_cmp(GP<T> g, RC<T> rk, int N, cons
 // Same cell traversal and compaction as the forward kernel; g of a source is
 // read through the permutation.
 // e = exp(-xi^2 r^2) and erfc(xi r): FP32 from one exp2 and the erfcx fit
-// (erfc = e Q(1/(2 + x)), x = xi r <= 8 on FP32 plans), FP64 from the library.
+// (erfc = e Q(1/(2 + x)), x = xi r <= 8 on FP32 plans), FP64 from exp and the
+// FP64 fit.
 __device__ __forceinline__ void s_exp_erfc(const RC<float> &rk, float r2, float r, float &e, float &ec) {
     e = ex2_approx(rk.ce * r2);
     ec = e * erfcx_poly<0>(__fdividef(1.0f, 2.0f + rk.xi * r));
 }
 __device__ __forceinline__ void s_exp_erfc(const RC<double> &rk, double r2, double r, double &e, double &ec) {
     e = exp(-rk.xi2 * r2);
-    ec = erfc(rk.xi * r);
+    ec = erfc_fit64(rk.xi * r, e);
 }
 __device__ __forceinline__ float s_rsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double s_rsqrt(double v) { return rsqrt(v); }
