@@ -38,6 +38,12 @@ FLOP_PER_PAIR = 58
 # this workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 # Set to None whenever that kernel changes, until it is captured again.
 REAL_TRAFFIC_BYTES = 51060736 + 3102208  # ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch
+# The same kernel's executed work from that capture: the FP32 pipes' (FMA and
+# ALU) busy fractions and the issue-slot utilisation (sm__inst_executed over
+# 4 issue slots per SM cycle).  None whenever the kernel changes, until captured again.
+REAL_EXECUTED = {"fma_pipe": 0.340, "alu_pipe": 0.416, "issue_active": 0.756,
+                 "warp_inst_per_pair": 5.28e9 / 1.47e9,
+                 "source": "ncu --set full, one launch (profiles/k_real_symc_stokeslet_N1e6_fp32.md)"}
 
 
 def pair_fraction_unit_cube(r: float) -> float:
@@ -114,9 +120,21 @@ class ClockSampler:
             return None
 
 
+def rel_errors(got, ref, bar):
+    """Relative L2 (rms) and relative max error of got against ref over all
+    components (reading c10): |d|_2 / |ref|_2 and max|d| / max|ref|."""
+    got, ref = np.asarray(got, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    d = got - ref
+    l2 = float(np.linalg.norm(d) / np.linalg.norm(ref))
+    mx = float(np.abs(d).max() / np.abs(ref).max())
+    return {"rel_l2": l2, "rel_max": mx, "bar": bar, "ok": bool(l2 <= bar and mx <= bar)}
+
+
 def cpu_baseline(x, f, budget_s=12.0):
     """The oracle's FP64 direct sum (all N sources) at a bounded random sample of
-    targets, on the host cores; Mpoints/s = sampled targets / time."""
+    targets, on the host cores; Mpoints/s = sampled targets / time.  Returns the
+    line's object, the sampled targets and the oracle's values there (they also
+    check the FP64 path's result)."""
     from oracle import direct
     rng = np.random.default_rng(123)
     t0 = time.perf_counter()
@@ -127,11 +145,67 @@ def cpu_baseline(x, f, budget_s=12.0):
     nt = int(max(ncal, min(len(x), rate * budget_s)))
     idx = rng.choice(len(x), nt, replace=False)
     t0 = time.perf_counter()
-    direct.direct("stokeslet", x, f, targets=idx)
+    ref = direct.direct("stokeslet", x, f, targets=idx)
     dt = time.perf_counter() - t0
-    return {"value": nt / dt / 1e6, "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 direct sum over all {len(x)} sources at {nt} random targets "
-                      f"({dt:.1f} s), scaled to targets per second"}
+    return ({"value": nt / dt / 1e6, "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"FP64 direct sum over all {len(x)} sources at {nt} random targets "
+                       f"({dt:.1f} s), scaled to targets per second"}, idx, ref)
+
+
+def oracle_checks(chk):
+    """Errors of the timed results against the FP64 direct sums of the oracle,
+    at sampled targets, after every timed region (the oracle is the checker
+    here, never on the timed path).  FP32 results are compared with the sums
+    over the FP32-rounded inputs (reading c11).  `chk` holds, per result, the
+    inputs and the GPU's output at the sampled targets."""
+    from oracle import direct
+    out = {}
+    t0 = time.perf_counter()
+    if "fp32" in chk:
+        c = chk["fp32"]
+        ref = direct.direct("stokeslet", c["x"], c["f"], targets=c["idx"])
+        out["fp32"] = dict(rel_errors(c["u"], ref, 2e-6), targets=len(c["idx"]))
+    if "fp64" in chk:
+        c = chk["fp64"]
+        out["fp64"] = dict(rel_errors(c["u"], c["ref"], 1e-10), targets=len(c["idx"]))
+    if "batched" in chk:
+        c = chk["batched"]
+        num = den = 0.0
+        worst, worst_max, worst_s = 0.0, 0.0, -1
+        for s, (x, f, idx, u) in enumerate(c["systems"]):
+            d_s = n_s = 0.0
+            dmax = rmax = 0.0
+            for r in range(f.shape[1]):
+                ref = direct.direct("stokeslet", x, f[:, r, :], targets=idx)
+                d = u[:, r, :] - ref
+                d_s += float(np.sum(d * d))
+                n_s += float(np.sum(ref * ref))
+                dmax, rmax = max(dmax, float(np.abs(d).max())), max(rmax, float(np.abs(ref).max()))
+            num, den = num + d_s, den + n_s
+            e = float(np.sqrt(d_s / n_s))
+            if e > worst:
+                worst, worst_s = e, c["ids"][s]
+            worst_max = max(worst_max, dmax / rmax)
+        out["batched"] = {"rel_l2_pooled": float(np.sqrt(num / den)), "rel_l2_worst_system": worst,
+                          "worst_system": worst_s, "rel_max_worst_system": worst_max, "bar": 2e-6,
+                          "ok": bool(worst <= 2e-6 and worst_max <= 2e-6),
+                          "targets": c["targets_note"]}
+    if "stresslet" in chk:
+        c = chk["stresslet"]
+        ref = direct.direct("stresslet", c["x"], c["f"], c["q"], targets=c["idx"])
+        out["stresslet_clustered"] = dict(rel_errors(c["u"], ref, 2e-6), targets=len(c["idx"]))
+    if "rotlet" in chk:
+        c = chk["rotlet"]
+        x, t, g, idx = c["x"], c["f"], c["g"], c["idx"]
+        out["rotlet_backward"] = {
+            "u": rel_errors(c["u"], direct.direct("rotlet", x, t, targets=idx), 2e-6),
+            "grad_f": rel_errors(c["gf"], direct.grad_f("rotlet", x, g, targets=idx), 2e-6),
+            # the position gradient's bar: one order above u's (its kernel is one
+            # power of r more singular, so rounding of close pairs weighs more)
+            "grad_x": rel_errors(c["gx"], direct.grad_x("rotlet", x, t, g, targets=idx), 2e-5),
+            "targets": len(idx)}
+    out["oracle_s"] = time.perf_counter() - t0
+    return out
 
 
 def run_reference(args, rank, world):
@@ -214,6 +288,20 @@ def run_batched(args, rank, world, dist, dev, flush):
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    # this rank's systems at sampled targets (all targets of systems up to 2e3
+    # points, 64 otherwise), for the error check after the timed regions
+    uh = u.double().cpu().numpy()
+    rng = np.random.default_rng(17)
+    chk_sys = []
+    for k, s in enumerate(mine):
+        n = sizes[s]
+        idx = np.arange(n) if n <= 2000 else np.sort(rng.choice(n, 64, replace=False))
+        o = B.offsets[k]
+        chk_sys.append((f32_in_box(systems[s][0]).astype(np.float64),
+                        systems[s][1].astype(np.float32).astype(np.float64), idx, uh[o + idx]))
+    check = {"systems": chk_sys, "ids": list(mine),
+             "targets_note": "every target of systems up to 2e3 points, 64 random targets otherwise, "
+                             f"all {R} right-hand sides, {len(mine)} systems of rank {rank}"}
     n_all = int(sum(sizes))
     out = {"value": n_all / (ms * 1e-3) / 1e6, "unit": "Mpoints/s", "rhs_per_point": R,
            "point_rhs_per_s": n_all * R / (ms * 1e-3), "ms_per_step": ms, "systems": 64, "points": n_all,
@@ -222,10 +310,10 @@ def run_batched(args, rank, world, dist, dev, flush):
                                       "each in [0,1)^3, 8 RHS ~ N(0,1)^3, FP32 rel. err 2e-6",
            "sharding": f"{len(mine)} of 64 systems on rank {rank} (cost-balanced), max over {world} ranks"}
     B.close()
-    return out
+    return out, check
 
 
-def run_other_configs(dev, flush, x32=None, f32=None):
+def run_other_configs(dev, flush, checks, x32=None, f32=None):
     """The clustered FP32 stresslet (N = 5e5: 16 Gaussian blobs, sigma 0.05,
     plus 20 % uniform background) and the FP32 rotlet with its backward
     (N = 2e5 uniform, du/df and du/dx, grid recomputed): median device times
@@ -291,6 +379,14 @@ def run_other_configs(dev, flush, x32=None, f32=None):
         res[name] = (ms, {k: plan.params[k] for k in ("M", "P", "xi", "rc")}, st)
         plan.close()
     ms, pp, st = res["points"]
+    # the output of the point-aware parameters at sampled targets (error check)
+    plan = se.Plan("stresslet", len(x), BOX, prec="fp32", tol=2e-6,
+                   **{k: prm[k] for k in ("xi", "M", "P", "rc", "cell_width")})
+    us = plan.eval(xd, fd, qd, check=True).double().cpu().numpy()
+    plan.close()
+    sidx = np.sort(np.random.default_rng(19).choice(len(x), 512, replace=False))
+    checks["stresslet"] = {"x": x32.astype(np.float64), "f": f.astype(np.float32).astype(np.float64),
+                           "q": q.astype(np.float32).astype(np.float64), "idx": sidx, "u": us[sidx]}
     out["stresslet_clustered"] = {
         "workload": "stresslet sum, N = 5e5: 16 Gaussian blobs (sigma 0.05) + 20 % uniform, FP32 at 2e-6",
         "value": len(x) / (ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms,
@@ -302,6 +398,12 @@ def run_other_configs(dev, flush, x32=None, f32=None):
     u = torch.empty_like(xd)
     ms_f = timed(lambda: plan.eval(xd, td, out=u))
     ms_b = timed(lambda: plan.backward(xd, td, gd))
+    gf, gx = plan.backward(xd, td, gd)
+    ridx = np.sort(np.random.default_rng(23).choice(len(x), 256, replace=False))
+    checks["rotlet"] = {"x": f32_in_box(x).astype(np.float64), "f": tq.astype(np.float32).astype(np.float64),
+                        "g": g.astype(np.float32).astype(np.float64), "idx": ridx,
+                        "u": u.double().cpu().numpy()[ridx], "gf": gf.double().cpu().numpy()[ridx],
+                        "gx": gx.double().cpu().numpy()[ridx]}
     plan.set_timing(True)
     plan.backward(xd, td, gd)
     torch.cuda.synchronize()
@@ -371,6 +473,11 @@ def run_ours(args, rank, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     plan.check()
+    checks = {}
+    # the timed steps' output at sampled targets (error check after the timed regions)
+    idx32 = np.sort(np.random.default_rng(29).choice(N_POINTS, 1024, replace=False))
+    checks["fp32"] = {"x": f32_in_box(x64).astype(np.float64), "f": f64.astype(np.float32).astype(np.float64),
+                      "idx": idx32, "u": u.double().cpu().numpy()[idx32]}
     plan.set_timing(True)
     seq_ms = []
     for _ in range(3):
@@ -404,7 +511,9 @@ def run_ours(args, rank, world, dist):
     e2e_ms = 1e3 * float(np.median(e2e_t))
     e2e_mean_ms = 1e3 * float(np.mean(e2e_t))
 
-    batched = None if args.no_batch else run_batched(args, rank, world, dist, dev, flush)
+    batched = None
+    if not args.no_batch:
+        batched, checks["batched"] = run_batched(args, rank, world, dist, dev, flush)
 
     # FP64 path on the same points
     fp64 = None
@@ -430,6 +539,7 @@ def run_ours(args, rank, world, dist):
             for name, v in plan64.stage_times().items():
                 st64.setdefault(name, []).append(v)
         plan64.check()
+        u64_host = u64.cpu().numpy()
         ms64 = float(np.mean(t64))
         fp64 = {"value": N_POINTS / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
                 "tol": 1e-10, "params": {k: p64[k] for k in ("M", "P", "xi", "rc", "Mtilde")},
@@ -468,12 +578,15 @@ def run_ours(args, rank, world, dist):
 
     if rank != 0:
         return
-    others = None if args.no_extra else run_other_configs(dev, flush, x32, f32)
+    others = None if args.no_extra else run_other_configs(dev, flush, checks, x32, f32)
     value = world * N_POINTS / (ms * 1e-3) / 1e6
     peaks = read_peaks()
     clocks = clk.summary()
     sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s FP32 (152 SMs x 128 lanes x FMA)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    # FP32 peak from the unit counts: SMs x 128 FP32 lanes x 2 flop (FMA) x clock
+    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    probe = se.measure_peaks()  # measured FMA rates (register-only kernels), after the timed regions
     pairs = N_POINTS * (N_POINTS - 1) * pair_fraction_unit_cube(prm["rc"] / BOX[3])
     real_ms = stages.get("real", float("nan"))
     achieved = pairs * FLOP_PER_PAIR / (real_ms * 1e-3) / 1e12
@@ -494,7 +607,7 @@ def run_ours(args, rank, world, dist):
     # sum is FP32 ALU work (58 flop per pair)
     P = prm["P"]
     grid_flop = N_POINTS * 3 * P**3 * 2
-    smem_peak = 152 * 128 * sm_max * 1e6 / 1e12  # TB/s
+    smem_peak = n_sm * 128 * sm_max * 1e6 / 1e12  # TB/s: one 128-byte wavefront per SM clock
     stage_roofline = {}
     for k, bound, work, unit, peak in (
             ("spread", "fma", grid_flop, "TFLOP/s", alu_peak),
@@ -504,7 +617,20 @@ def run_ours(args, rank, world, dist):
         if stages.get(k):
             a = work / (stages[k] * 1e-3) / (1e9 if unit == "GB/s" else 1e12)
             stage_roofline[k] = {"bound": bound, "achieved": a, "peak": peak, "unit": unit, "frac": a / peak}
-    cpu = None if args.no_cpu else cpu_baseline(x64, f64)
+    cpu = None
+    if not args.no_cpu:
+        cpu, cidx, cref = cpu_baseline(x64, f64)
+        if fp64 is not None:
+            checks["fp64"] = {"idx": cidx, "ref": cref, "u": u64_host[cidx]}
+    errors = oracle_checks(checks) if not args.no_cpu else None
+    if errors:
+        for key, obj in (("fp64", fp64), ("batched", batched)):
+            if obj is not None and key in errors:
+                obj["error"] = errors[key]
+        if others:
+            for key in ("stresslet_clustered", "rotlet_backward"):
+                if key in others and key in errors:
+                    others[key]["error"] = errors[key]
     line = {
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -522,8 +648,21 @@ def run_ours(args, rank, world, dist):
         "stage_roofline": stage_roofline,
         "roofline": {"bound": "alu", "kernel": "k_real_symc (real-space pair sum, each pair once)", "achieved": achieved,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": REAL_TRAFFIC_BYTES,
-                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                     "peak_source": f"derived: {n_sm} SMs (device attribute) x 128 FP32 lanes x 2 flop x "
+                                    f"{sm_max:.0f} MHz",
+                     "peak_measured": probe["fp32_fma_tflops"],
+                     "frac_of_measured": achieved / probe["fp32_fma_tflops"],
+                     "work": "algorithmic: ordered pairs within rc (expected count for uniform points) x "
+                             f"{FLOP_PER_PAIR} flop, as a direct evaluation of every ordered pair needs; the kernel "
+                             "evaluates each unordered pair once",
+                     "executed": REAL_EXECUTED,
                      "pairs_per_launch": pairs, "flop_per_pair": FLOP_PER_PAIR},
+        "measured_peaks": dict(probe, source="se_measure_peaks: register-only FMA kernels on this GPU, "
+                                             "after the timed regions"),
+        "error": errors.get("fp32") if errors else None,
+        "errors_note": ("relative L2 and relative max error against the oracle's FP64 direct sum at sampled "
+                        "targets (FP32 results against the sums over the FP32-rounded inputs), taken after "
+                        f"the timed regions ({errors['oracle_s']:.1f} s)") if errors else None,
         "hbm_peak_gbs": hbm,
         "plan": {"create_ms": 1e3 * t_plan, "precompute_ms": pre_ms,
                  "note": "plan creation (parameter choice, allocation, cuFFT plans, FP64 precompute of "

@@ -185,7 +185,9 @@ se_status_t se_eval_real_space(se_plan_t plan, const void *x, const void *f, con
  * (about 9 MB, held on every GPU that loads the library until the process
  * exits); nothing is allocated.  Limits: N <= 32768 and L / rc <= 25 (the cell
  * list's size); larger requests return SE_ERR_INVALID_ARG.  The first call on a
- * device looks up the array's address (make it before any stream capture).
+ * device looks up the array's address (make it before any stream capture);
+ * later calls outside a capture look it up again, so a context destroyed and
+ * created again (cudaDeviceReset) is followed.
  * Calls whose GPU work overlaps race on the shared array.  Device-side flags
  * (points outside the box, coincident points) are not reported.  The paper has
  * no counterpart to this entry point.  Asynchronous on `stream`. */
@@ -333,6 +335,28 @@ const char *se_last_error(void);
 
 /* Library version string. */
 const char *se_version(void);
+
+/* Arithmetic rates of the current device, measured (no counterpart in the
+ * paper, which reports CPU times only): the denominators of the roofline
+ * fractions of the kernels bound by arithmetic rather than memory.  Each rate
+ * is the best of three launches, timed with CUDA events, of a register-only
+ * kernel in which every thread of 8 blocks of 256 per SM runs 8 independent
+ * chains of fused multiply-adds; the iteration count is calibrated so that
+ * one launch takes about 20 ms.  Flops count 2 per FMA (4 per paired FMA).
+ *   fp32_fma_tflops    scalar FP32 fmaf
+ *   fp32_ffma2_tflops  paired FP32 (__ffma2_rn: two FMAs per instruction)
+ *   fp64_fma_tflops    FP64 fma
+ *   sm_count           multiprocessors of the device
+ * Synchronous on the legacy default stream; allocates and frees a small
+ * device buffer; about a quarter of a second.  SE_ERR_INVALID_ARG for a NULL
+ * out, SE_ERR_CUDA if a launch fails. */
+typedef struct {
+    double fp32_fma_tflops;
+    double fp32_ffma2_tflops;
+    double fp64_fma_tflops;
+    int sm_count;
+} se_peaks_t;
+se_status_t se_measure_peaks(se_peaks_t *out);
 
 #ifdef __cplusplus
 }

@@ -216,6 +216,218 @@ __device__ __forceinline__ void spread_col_body(const GP<float> &g, int tile, in
     }
 }
 
+// ---------------------------------------------------------------- paired spreading
+// FP32 spreading with the paired FP32 multiply-adds of sm_100 and later
+// (__ffma2_rn: two lanes of one 64-bit register pair per instruction, the
+// same rounding as two fmaf).  Thread (cx, cy) owns the column of the tile's
+// padded block as ZP float2 pairs per component, z values (2q, 2q + 1) in
+// pair q.  A point's P z weights are staged shifted by the parity of its z
+// offset oz in the column, so that they start on a pair boundary: P/2 pairs
+// when oz is even, P/2 + 1 (a zero at each end) when it is odd; the update of
+// one column is then P/2 (+1) paired FMAs per component.  Each point is staged
+// by three threads, one per dimension (its P weights), and the next batch of
+// points is staged while the current one is accumulated (two buffers, one
+// barrier per batch).  A warp skips, with a uniform test, the points whose
+// support misses its rows of columns.
+template <int P, int TE>
+struct C2Cfg {
+    static constexpr int PT = TE + P - 1;        // padded block edge
+    static constexpr int ZP = (PT + 1) / 2;      // z pairs per column and component
+    static constexpr int WP = P / 2 + 1;         // staged z-weight pairs (odd offsets need P/2 + 1)
+    static constexpr int WP4 = (WP + 1) / 2 * 2; // rounded up to whole 16-byte rows
+    static constexpr int NT = (PT * PT + 31) / 32 * 32;
+    static constexpr int NB = NT / 3;            // points per batch: three staging threads each
+};
+
+template <int P, int TE>
+struct C2Stage {
+    using C = C2Cfg<P, TE>;
+    float2 wz[C::NB][C::WP4];        // z weights, shifted by the parity of oz
+    float wx[C::NB][P];
+    float wy[C::NB][P];
+    float4 src[C::NB];               // the three source components
+    unsigned char off[C::NB][4];     // ox, oy, oz: window start in the padded block
+};
+
+template <int P, int TE>
+constexpr size_t c2_smem_bytes() {
+    return 2 * sizeof(C2Stage<P, TE>);
+}
+
+// Stage points b0 .. b0 + nb - 1 into S: thread t takes dimension d = t / NB
+// of point j = t mod NB.
+template <int P, int TE>
+__device__ __forceinline__ void c2_stage(C2Stage<P, TE> &S, const GP<float> &g, int b0, int nb, int gx0, int gy0,
+                                         int gz0, int c0, bool stress, const float4 *__restrict__ xs,
+                                         const float4 *__restrict__ fs, int fstride, int foff,
+                                         const float4 *__restrict__ qs) {
+    using C = C2Cfg<P, TE>;
+    const int t = threadIdx.x;
+    if (t >= 3 * C::NB) return;
+    const int d = t / C::NB, j = t - d * C::NB;
+    if (j >= nb) return;
+    const int n = b0 + j;
+    const float4 xv = xs[n];
+    int i0[3];
+    unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+    const float xd = d == 0 ? xv.x : (d == 1 ? xv.y : xv.z);
+    const int id = d == 0 ? i0[0] : (d == 1 ? i0[1] : i0[2]);
+    const float x0 = d == 0 ? g.x0[0] : (d == 1 ? g.x0[1] : g.x0[2]);
+    const int o0 = d == 0 ? gx0 : (d == 1 ? gy0 : gz0);
+    const float fr = ((xd - x0) * g.inv_h + g.half_ext) - (float)id;
+    const int o = min(max(id - o0, 0), TE - 1);
+    S.off[j][d] = (unsigned char)o;
+    if (d == 2) {
+        // the P weights at slots (oz & 1) .. (oz & 1) + P - 1, zeros elsewhere
+        float *w = reinterpret_cast<float *>(S.wz[j]);
+        const int sh = o & 1;
+#pragma unroll
+        for (int i = 0; i < 2 * C::WP4; i++) {
+            const int kk = i - sh;
+            const float tt = fr - (float)kk;
+            w[i] = (kk >= 0 && kk < P) ? __expf(-g.ah2 * tt * tt) : 0.0f;
+        }
+    } else {
+        float *w = d == 0 ? S.wx[j] : S.wy[j];
+#pragma unroll
+        for (int kk = 0; kk < P; kk++) {
+            const float tt = fr - (float)kk;
+            w[kk] = __expf(-g.ah2 * tt * tt);
+        }
+        if (d == 0) {
+            const float4 fv = fs[(size_t)n * fstride + foff];
+            float4 sv = fv;
+            if (stress) {
+                // components c0 .. c0+2 of the symmetric source (xx, yy, zz, xy, xz, yz)
+                const float4 qv = qs[n];
+                if (c0 == 0)
+                    sv = make_float4(fv.x * qv.x, fv.y * qv.y, fv.z * qv.z, 0.0f);
+                else
+                    sv = make_float4(0.5f * (fv.x * qv.y + fv.y * qv.x), 0.5f * (fv.x * qv.z + fv.z * qv.x),
+                                     0.5f * (fv.y * qv.z + fv.z * qv.y), 0.0f);
+            }
+            S.src[j] = sv;
+        }
+    }
+}
+
+// a_c[OZ/2 + k] += s_c wz[k] for the point's NP z pairs
+template <int P, int ZP, int OZ>
+__device__ __forceinline__ void col_add2(float2 (&a0)[ZP], float2 (&a1)[ZP], float2 (&a2)[ZP], float2 s0, float2 s1,
+                                         float2 s2, const float2 *wz) {
+    constexpr int Q0 = OZ / 2, NP = P / 2 + (OZ & 1);
+    static_assert(Q0 + NP <= ZP, "the point's z support stays inside the column");
+    const float4 *w4 = reinterpret_cast<const float4 *>(wz);
+#pragma unroll
+    for (int k2 = 0; k2 < (NP + 1) / 2; k2++) {
+        const float4 v = w4[k2];
+        const float2 lo = make_float2(v.x, v.y), hi = make_float2(v.z, v.w);
+        a0[Q0 + 2 * k2] = __ffma2_rn(lo, s0, a0[Q0 + 2 * k2]);
+        a1[Q0 + 2 * k2] = __ffma2_rn(lo, s1, a1[Q0 + 2 * k2]);
+        a2[Q0 + 2 * k2] = __ffma2_rn(lo, s2, a2[Q0 + 2 * k2]);
+        if (2 * k2 + 1 < NP) {
+            a0[Q0 + 2 * k2 + 1] = __ffma2_rn(hi, s0, a0[Q0 + 2 * k2 + 1]);
+            a1[Q0 + 2 * k2 + 1] = __ffma2_rn(hi, s1, a1[Q0 + 2 * k2 + 1]);
+            a2[Q0 + 2 * k2 + 1] = __ffma2_rn(hi, s2, a2[Q0 + 2 * k2 + 1]);
+        }
+    }
+}
+
+#define SE_COL2_CASES(...)                              \
+    switch (oz) {                                       \
+        case 0: col_add2<P, ZP, 0>(__VA_ARGS__); break; \
+        case 1: col_add2<P, ZP, 1>(__VA_ARGS__); break; \
+        case 2: col_add2<P, ZP, 2>(__VA_ARGS__); break; \
+        case 3: col_add2<P, ZP, 3>(__VA_ARGS__); break; \
+        case 4: col_add2<P, ZP, 4>(__VA_ARGS__); break; \
+        case 5: col_add2<P, ZP, 5>(__VA_ARGS__); break; \
+        case 6: col_add2<P, ZP, 6>(__VA_ARGS__); break; \
+        default: col_add2<P, ZP, 7>(__VA_ARGS__); break; \
+    }
+
+// Accumulate the nb staged points of S into the thread's column.
+template <int P, int TE>
+__device__ __forceinline__ void c2_accumulate(const C2Stage<P, TE> &S, int nb, bool own, int cx, int cy, int cyl,
+                                              int cyh, float2 (&a0)[C2Cfg<P, TE>::ZP],
+                                              float2 (&a1)[C2Cfg<P, TE>::ZP], float2 (&a2)[C2Cfg<P, TE>::ZP]) {
+    constexpr int ZP = C2Cfg<P, TE>::ZP;
+    for (int j = 0; j < nb; j++) {
+        const uchar4 o = *reinterpret_cast<const uchar4 *>(S.off[j]);
+        const int oy = o.y;
+        if (oy > cyh || oy + P - 1 < cyl) continue;  // uniform: the support misses the warp's rows
+        const int kx = cx - o.x, ky = cy - oy;
+        if (own && (unsigned)kx < (unsigned)P && (unsigned)ky < (unsigned)P) {
+            const float w = S.wx[j][kx] * S.wy[j][ky];
+            const float4 sv = S.src[j];
+            const float2 s0 = make_float2(sv.x * w, sv.x * w), s1 = make_float2(sv.y * w, sv.y * w),
+                         s2 = make_float2(sv.z * w, sv.z * w);
+            const int oz = o.z;
+            SE_COL2_CASES(a0, a1, a2, s0, s1, s2, S.wz[j])
+        }
+    }
+}
+
+// Add the thread's column (grid column (gx, gy), z planes gz0 ..) to the three
+// grids at grid, grid + gcs, grid + 2 gcs (z-plane stride gzs): global atomics,
+// since neighbouring tiles overlap in their halos.
+template <int P, int TE>
+__device__ __forceinline__ void c2_flush(const GP<float> &g, int gx, int gy, int gz0,
+                                         const float2 (&a0)[C2Cfg<P, TE>::ZP], const float2 (&a1)[C2Cfg<P, TE>::ZP],
+                                         const float2 (&a2)[C2Cfg<P, TE>::ZP], float *__restrict__ grid, size_t gzs,
+                                         size_t gcs) {
+    constexpr int PT = C2Cfg<P, TE>::PT, ZP = C2Cfg<P, TE>::ZP;
+    if (gx >= g.mt[0] || gy >= g.mt[1]) return;
+    float *base = grid + (size_t)gz0 * gzs + (size_t)gy * g.mf[0] + gx;
+#pragma unroll
+    for (int q = 0; q < ZP; q++) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int z = 2 * q + h;
+            if (z < PT && gz0 + z < g.mt[2]) {
+                float *pz = base + (size_t)z * gzs;
+                const float v0 = h ? a0[q].y : a0[q].x, v1 = h ? a1[q].y : a1[q].x, v2 = h ? a2[q].y : a2[q].x;
+                if (v0 != 0.0f) atomicAdd(pz, v0);
+                if (v1 != 0.0f) atomicAdd(pz + gcs, v1);
+                if (v2 != 0.0f) atomicAdd(pz + 2 * gcs, v2);
+            }
+        }
+    }
+}
+
+template <int P, int TE>
+__device__ __forceinline__ void spread_c2_body(const GP<float> &g, int tile, int beg, int end, int c0, bool stress,
+                                               const float4 *__restrict__ xs, const float4 *__restrict__ fs,
+                                               int fstride, int foff, const float4 *__restrict__ qs,
+                                               float *__restrict__ grid, size_t gzs, size_t gcs,
+                                               C2Stage<P, TE> *S) {
+    using C = C2Cfg<P, TE>;
+    constexpr int PT = C::PT, ZP = C::ZP, NB = C::NB;
+    static_assert(TE == 8, "the unrolled z offsets cover tiles of 8");
+    const int tid = threadIdx.x;
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
+    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
+    const bool own = tid < PT * PT;
+    const int cx = tid % PT, cy = tid / PT;
+    // the rows of columns this warp owns
+    const int w0 = tid & ~31;
+    const int cyl = w0 / PT, cyh = min(w0 + 31, PT * PT - 1) / PT;
+    float2 a0[ZP], a1[ZP], a2[ZP];
+#pragma unroll
+    for (int q = 0; q < ZP; q++) a0[q] = a1[q] = a2[q] = make_float2(0.0f, 0.0f);
+    c2_stage<P, TE>(S[0], g, beg, min(NB, end - beg), gx0, gy0, gz0, c0, stress, xs, fs, fstride, foff, qs);
+    __syncthreads();
+    int k = 0;
+    for (int b0 = beg; b0 < end; b0 += NB, k ^= 1) {
+        const int nb = min(NB, end - b0);
+        if (b0 + NB < end)
+            c2_stage<P, TE>(S[k ^ 1], g, b0 + NB, min(NB, end - b0 - NB), gx0, gy0, gz0, c0, stress, xs, fs, fstride,
+                            foff, qs);
+        c2_accumulate<P, TE>(S[k], nb, own, cx, cy, cyl, cyh, a0, a1, a2);
+        __syncthreads();
+    }
+    if (own) c2_flush<P, TE>(g, gx0 + cx, gy0 + cy, gz0, a0, a1, a2, grid + (size_t)c0 * gcs, gzs, gcs);
+}
+
 // w: three grids (the group of right-hand side r); u, f_orig: n_rhs three-vectors per point.
 template <int P, int TE>
 __device__ __forceinline__ void gather_col_body(const GP<float> &g, int tile, int beg, int end,
@@ -726,6 +938,22 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_spread_col(GP<float> g, i
 }
 
 template <int P, int TE>
+__global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? 2 : 1) k_spread_c2(GP<float> g, int c0, bool stress,
+                                                                                const int *__restrict__ tile_start,
+                                                                                const float4 *__restrict__ xs,
+                                                                                const float4 *__restrict__ fs,
+                                                                                const float4 *__restrict__ qs,
+                                                                                float *__restrict__ grid) {
+    extern __shared__ __align__(16) unsigned char c2_smem[];
+    const int tile = blockIdx.x;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    const size_t Mf = g.mf[0], Mf2 = Mf * g.mf[1];
+    spread_c2_body<P, TE>(g, tile, beg, end, c0, stress, xs, fs, 1, 0, qs, grid, Mf2, Mf2 * g.mf[2],
+                          reinterpret_cast<C2Stage<P, TE> *>(c2_smem));
+}
+
+template <int P, int TE>
 __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_gather_col(GP<float> g, const int *__restrict__ tile_start,
                                                                     const float4 *__restrict__ xs,
                                                                     const int *__restrict__ perm,
@@ -821,6 +1049,67 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT, 2) k_bspread_col_rhs(const 
     }
 }
 
+// Batched paired spreading: one CTA per (system, tile) with the right-hand
+// sides inside the item.  A tile of at most NB points is staged once (positions
+// and weights) and only its sources are staged again per right-hand side;
+// larger tiles are staged batch by batch for every right-hand side.  items:
+// the (system, tile, rhs) list with the right-hand side innermost; block b
+// takes item b * n_rhs.
+template <int P, int TE>
+__global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? 2 : 1) k_bspread_c2(const BSys<float> *__restrict__ sys,
+                                                                                 const int4 *__restrict__ items,
+                                                                                 const int *__restrict__ tile_start,
+                                                                                 int n_rhs,
+                                                                                 const float4 *__restrict__ xs,
+                                                                                 const float4 *__restrict__ fs) {
+    using C = C2Cfg<P, TE>;
+    constexpr int PT = C::PT, ZP = C::ZP, NB = C::NB;
+    extern __shared__ __align__(16) unsigned char c2_smem[];
+    C2Stage<P, TE> *S = reinterpret_cast<C2Stage<P, TE> *>(c2_smem);
+    const int4 it = items[(size_t)blockIdx.x * n_rhs];
+    const BSys<float> &B = sys[it.x];
+    const int key = B.tile_base + it.y;
+    const int beg = tile_start[key], end = tile_start[key + 1];
+    if (beg == end) return;
+    const GP<float> g = B.g;
+    const int tile = it.y, tid = threadIdx.x;
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
+    const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
+    const bool own = tid < PT * PT;
+    const int cx = tid % PT, cy = tid / PT;
+    const int w0 = tid & ~31;
+    const int cyl = w0 / PT, cyh = min(w0 + 31, PT * PT - 1) / PT;
+    const bool once = end - beg <= NB;
+    for (int r = 0; r < n_rhs; r++) {
+        float2 a0[ZP], a1[ZP], a2[ZP];
+#pragma unroll
+        for (int q = 0; q < ZP; q++) a0[q] = a1[q] = a2[q] = make_float2(0.0f, 0.0f);
+        if (once) {
+            if (r == 0) {
+                c2_stage<P, TE>(S[0], g, beg, end - beg, gx0, gy0, gz0, 0, false, xs, fs, n_rhs, 0, nullptr);
+            } else if (tid < end - beg) {
+                S[0].src[tid] = fs[(size_t)(beg + tid) * n_rhs + r];
+            }
+            __syncthreads();
+            c2_accumulate<P, TE>(S[0], end - beg, own, cx, cy, cyl, cyh, a0, a1, a2);
+            __syncthreads();
+        } else {
+            c2_stage<P, TE>(S[0], g, beg, NB, gx0, gy0, gz0, 0, false, xs, fs, n_rhs, r, nullptr);
+            __syncthreads();
+            int k = 0;
+            for (int b0 = beg; b0 < end; b0 += NB, k ^= 1) {
+                const int nb = min(NB, end - b0);
+                if (b0 + NB < end)
+                    c2_stage<P, TE>(S[k ^ 1], g, b0 + NB, min(NB, end - b0 - NB), gx0, gy0, gz0, 0, false, xs, fs,
+                                    n_rhs, r, nullptr);
+                c2_accumulate<P, TE>(S[k], nb, own, cx, cy, cyl, cyh, a0, a1, a2);
+                __syncthreads();
+            }
+        }
+        if (own) c2_flush<P, TE>(g, gx0 + cx, gy0 + cy, gz0, a0, a1, a2, B.grid + (size_t)r * 3 * B.gcs, B.gzs, B.gcs);
+    }
+}
+
 // Dispatch on the (even) support P, 4 <= P <= 16.
 template <template <int, int> class F, typename... A>
 cudaError_t with_p(int P, A... a) {
@@ -836,11 +1125,25 @@ cudaError_t with_p(int P, A... a) {
     }
 }
 
+// SE_SPREAD_PAIR: the paired-FMA spreading kernel (k_spread_c2); 0 keeps the
+// scalar register-column kernel (k_spread_col)
+#ifndef SE_SPREAD_PAIR
+#define SE_SPREAD_PAIR 1
+#endif
+
 template <int P, int TE>
 struct SpreadRun {
     static cudaError_t run(const GP<float> g, int ntiles, int c0, bool stress, const int *ts, const float4 *xs,
                            const float4 *fs, const float4 *qs, float *grid, cudaStream_t st) {
-        k_spread_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, c0, stress, ts, xs, fs, qs, grid);
+        if (SE_SPREAD_PAIR) {
+            constexpr size_t smem = c2_smem_bytes<P, TE>();
+            cudaError_t e =
+                cudaFuncSetAttribute(k_spread_c2<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e) return e;
+            k_spread_c2<P, TE><<<ntiles, C2Cfg<P, TE>::NT, smem, st>>>(g, c0, stress, ts, xs, fs, qs, grid);
+        } else {
+            k_spread_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, c0, stress, ts, xs, fs, qs, grid);
+        }
         return cudaGetLastError();
     }
 };
@@ -935,7 +1238,15 @@ template <int P, int TE>
 struct BSpreadRun {
     static cudaError_t run(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
                            const float4 *xs, const float4 *fs, cudaStream_t st) {
-        k_bspread_col_rhs<P, TE><<<nitems / n_rhs, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
+        if (SE_SPREAD_PAIR) {
+            constexpr size_t smem = c2_smem_bytes<P, TE>();
+            cudaError_t e =
+                cudaFuncSetAttribute(k_bspread_c2<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e) return e;
+            k_bspread_c2<P, TE><<<nitems / n_rhs, C2Cfg<P, TE>::NT, smem, st>>>(sys, items, ts, n_rhs, xs, fs);
+        } else {
+            k_bspread_col_rhs<P, TE><<<nitems / n_rhs, ColCfg<P, TE>::NT, 0, st>>>(sys, items, ts, n_rhs, xs, fs);
+        }
         return cudaGetLastError();
     }
 };

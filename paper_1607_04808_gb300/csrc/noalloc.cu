@@ -11,7 +11,11 @@
 //
 // The first call on a device looks up the array's device address
 // (cudaGetSymbolAddress) with that device current; make that first call before
-// any stream capture.  All calls share the one array: calls whose work
+// any stream capture.  Later calls on a stream that is not capturing look the
+// address up again (a cheap lookup once the module is loaded), so that a
+// context torn down and created again (cudaDeviceReset), which may place the
+// array elsewhere, is followed; calls on a capturing stream use the address
+// found last.  All calls share the one array: calls whose work
 // overlaps on the GPU (different streams, or several host threads) race and
 // corrupt each other's results; serialise them.
 //
@@ -73,12 +77,18 @@ extern "C" se_status_t se_real_space_noalloc(se_kernel_t kernel, se_prec_t prec,
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(SE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= 128) return fail(SE_ERR_INVALID_ARG, "device ordinal out of range");
+    cudaStream_t st = (cudaStream_t)stream;
     unsigned char *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            // first call on this device (the device is current): look up the
-            // array's device address once
+        // look the address up on the first call on this device (the device is
+        // current) and again on every call outside a stream capture
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cs = cudaStreamCaptureStatusActive;  // unknown: keep the address found last
+        }
+        if (!g_addr[dev] || cs == cudaStreamCaptureStatusNone) {
             void *ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
             if (e != cudaSuccess)
@@ -171,7 +181,6 @@ extern "C" se_status_t se_real_space_noalloc(se_kernel_t kernel, se_prec_t prec,
     p.b.ncl = (int *)(base + OFF_NCL);
     p.b.clusters = (int2 *)(base + OFF_CL);
     p.b.status = (int *)(base + OFF_STATUS);
-    cudaStream_t st = (cudaStream_t)stream;
     // the array keeps the previous call's contents: reset what must start at
     // zero (the counters are cleared inside the binning, the flags here)
     const size_t bytes = (size_t)N * 3 * (prec == SE_FP32 ? 4 : 8);

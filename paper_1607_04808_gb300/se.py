@@ -43,6 +43,11 @@ class SEParams(ctypes.Structure):
     ]
 
 
+class SEPeaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_tflops", ctypes.c_double), ("fp32_ffma2_tflops", ctypes.c_double),
+                ("fp64_fma_tflops", ctypes.c_double), ("sm_count", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -126,6 +131,8 @@ def lib():
             L.se_last_error.argtypes = []
             L.se_version.restype = ctypes.c_char_p
             L.se_version.argtypes = []
+            L.se_measure_peaks.restype = i32
+            L.se_measure_peaks.argtypes = [ctypes.POINTER(SEPeaks)]
             _lib = L
     return _lib
 
@@ -450,3 +457,12 @@ def choose_params_points(kernel: str, x, box=(0.0, 0.0, 0.0, 1.0), tol: float = 
 
 def version() -> str:
     return lib().se_version().decode()
+
+
+def measure_peaks() -> dict:
+    """Measured FP32 (scalar and paired) and FP64 FMA rates of the current device
+    in TFLOP/s, and its SM count (se_measure_peaks)."""
+    out = SEPeaks()
+    _check(lib().se_measure_peaks(ctypes.byref(out)))
+    return {"fp32_fma_tflops": out.fp32_fma_tflops, "fp32_ffma2_tflops": out.fp32_ffma2_tflops,
+            "fp64_fma_tflops": out.fp64_fma_tflops, "sm_count": out.sm_count}

@@ -162,8 +162,10 @@ def test_batch_out_of_box_flag():
 
 def test_batch_full_size_64_systems_8_rhs():
     """The 64-system workload: sizes lognormal(ln 1e4, 1) clipped to [1e3, 1e5],
-    8 right-hand sides each, every system in its own unit cube, FP32 at 2e-6;
-    16 sampled targets per system against the FP64 direct sum."""
+    8 right-hand sides each, every system in its own unit cube, FP32 at 2e-6.
+    Every system is held to the bar on its own (relative L2 and relative max
+    over its 8 right-hand sides) against the FP64 direct sum: at every target
+    for systems up to 2e4 points, at 256 sampled targets for larger ones."""
     pkg = P()
     R = 8
     systems = W.batched_systems(64, R, 5)
@@ -175,19 +177,22 @@ def test_batch_full_size_64_systems_8_rhs():
     u = u.double().cpu().numpy()
     rng = np.random.default_rng(5)
     num = den = 0.0
-    worst = 0.0
+    bad = []
     for s in range(64):
         o0 = B.offsets[s]
-        idx = rng.choice(sizes[s], 16, replace=False)
-        d_s = n_s = 0.0
+        idx = np.arange(sizes[s]) if sizes[s] <= 20000 else np.sort(rng.choice(sizes[s], 256, replace=False))
+        d_s = n_s = dmax = rmax = 0.0
         for r in range(R):
             ref = direct.direct("stokeslet", xs[s], fs[s][:, r, :], targets=idx)
-            got = u[o0 + idx, r, :]
-            d_s += float(np.sum((got - ref) ** 2))
+            d = u[o0 + idx, r, :] - ref
+            d_s += float(np.sum(d ** 2))
             n_s += float(np.sum(ref ** 2))
+            dmax, rmax = max(dmax, float(np.abs(d).max())), max(rmax, float(np.abs(ref).max()))
         num += d_s
         den += n_s
-        worst = max(worst, np.sqrt(d_s / n_s))
+        e2, em = np.sqrt(d_s / n_s), dmax / rmax
+        if e2 > 2e-6 or em > 2e-6:
+            bad.append((s, sizes[s], B.params(s)["P"], float(e2), float(em)))
     assert np.sqrt(num / den) <= 2e-6, np.sqrt(num / den)
-    assert worst <= 5e-6, worst
+    assert not bad, bad
     B.close()

@@ -72,6 +72,28 @@ def test_noalloc_matches_plan_entry_point(kernel, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_noalloc_narrow_cutoff_wide_cells(prec):
+    """A cutoff near L/24 with few points: the fixed cell list then caps the
+    cells along x, which become wider than rc (a geometry no plan uses).  The
+    sum must still equal the regular entry point's, on two calls in a row."""
+    import paper_1607_04808_gb300 as pkg
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    tol = 1e-6 if prec == "fp32" else 1e-12
+    N, xi, rc = 3000, 60.0, 1.0 / 24.5
+    plan = pkg.Plan("stokeslet", N, BOX, prec=prec, xi=xi, rc=rc, M=40, P=8)
+    for seed in (23, 24):
+        x, f = W.stokeslet_uniform(N, seed)
+        tx = torch.tensor(x, dtype=dt, device="cuda")
+        tf = torch.tensor(f, dtype=dt, device="cuda")
+        ref = plan.eval_real_space(tx, tf).double().cpu().numpy()
+        plan.check()
+        got = _noalloc("stokeslet", prec, tx, tf, None, xi, rc).double().cpu().numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= tol, (seed, err)
+    plan.close()
+
+
 def test_noalloc_rejects_oversized_requests():
     from paper_1607_04808_gb300 import se as sem
     x = torch.zeros((40000, 3), dtype=torch.float32, device="cuda")
