@@ -235,14 +235,14 @@ se_status_t create(se_batch_s *B, const int64_t *N_s, const double *box_s, doubl
     const bool fixed = params && (params->M > 0 || params->max_fft > 0 || params->xi > 0);
     for (int s = 0; s < S && SE_BATCH_FAST_FFT && !fixed; s++) {
         const int Mf0 = 2 * (pr[s].M + pr[s].P);
-        if (fast_fft_len(Mf0)) continue;
+        if (fast_fft_len(Mf0, prec)) continue;
         int lo = Mf0, hi = Mf0;
-        while (lo > 2 * (pr[s].P + 2) && !fast_fft_len(lo)) lo -= 2;
-        while (!fast_fft_len(hi)) hi += 2;
+        while (lo > 2 * (pr[s].P + 2) && !fast_fft_len(lo, prec)) lo -= 2;
+        while (!fast_fft_len(hi, prec)) hi += 2;
         double best = 1e300;
         se_params_t pick = pr[s];
         for (int Mf : {lo, hi}) {
-            if (!fast_fft_len(Mf) || Mf / 2 - pr[s].P < 2) continue;
+            if (!fast_fft_len(Mf, prec) || Mf / 2 - pr[s].P < 2) continue;
             se_params_t in;
             memset(&in, 0, sizeof(in));
             if (params) in = *params;

@@ -224,29 +224,52 @@ __device__ __forceinline__ void spread_col_body(const GP<float> &g, int tile, in
 // pair q.  A point's P z weights are staged shifted by the parity of its z
 // offset oz in the column, so that they start on a pair boundary: P/2 pairs
 // when oz is even, P/2 + 1 (a zero at each end) when it is odd; the update of
-// one column is then P/2 (+1) paired FMAs per component.  Each point is staged
-// by three threads, one per dimension (its P weights), and the next batch of
-// points is staged while the current one is accumulated (two buffers, one
-// barrier per batch).  A warp skips, with a uniform test, the points whose
-// support misses its rows of columns.
+// one column is then P/2 (+1) paired FMAs per component; register indices
+// must be compile-time constants, so a switch on oz selects one of TE unrolled
+// updates.  The staged points are put in order of oy (per chunk of 32 points,
+// by warp ballots), so that each warp runs only through the contiguous run of
+// points whose support meets its rows of columns.  The x and y weights are
+// staged over the whole padded block (zero outside the point's support), so
+// every lane of such a warp takes the update without a per-lane branch.  Each
+// point is staged by three threads, one per dimension, into one record, and
+// the next batch is staged while the current one is accumulated (two buffers,
+// one barrier per batch).
+// SE_C2_MINB: blocks per SM the paired spreading kernels are compiled for
+// (2: at most 80 registers per thread; 1: up to 168)
+#ifndef SE_C2_MINB
+#define SE_C2_MINB 2
+#endif
+
 template <int P, int TE>
 struct C2Cfg {
     static constexpr int PT = TE + P - 1;        // padded block edge
+    static constexpr int PTP = (PT + 3) / 4 * 4; // x, y weight rows padded to 16 bytes
     static constexpr int ZP = (PT + 1) / 2;      // z pairs per column and component
     static constexpr int WP = P / 2 + 1;         // staged z-weight pairs (odd offsets need P/2 + 1)
     static constexpr int WP4 = (WP + 1) / 2 * 2; // rounded up to whole 16-byte rows
     static constexpr int NT = (PT * PT + 31) / 32 * 32;
-    static constexpr int NB = NT / 3;            // points per batch: three staging threads each
+    static constexpr int NB = NT / 3 / 32 * 32;  // points per batch: three staging threads each, whole warps
+    static constexpr int NCH = NB / 32;          // chunks of 32 points ordered by oy
+};
+
+// One staged point: everything the column threads read, in one record so that
+// a single base address serves all its loads.
+template <int P, int TE>
+struct __align__(16) C2Rec {
+    using C = C2Cfg<P, TE>;
+    float4 wz[C::WP4 / 2];           // z weights as pairs, shifted by the parity of oz
+    float4 src;                      // the three source components
+    float wx[C::PTP];                // x weight of every column of the block (0 off the support)
+    float wy[C::PTP];
+    uchar4 off;                      // ox, oy, oz: window start in the padded block
 };
 
 template <int P, int TE>
 struct C2Stage {
     using C = C2Cfg<P, TE>;
-    float2 wz[C::NB][C::WP4];        // z weights, shifted by the parity of oz
-    float wx[C::NB][P];
-    float wy[C::NB][P];
-    float4 src[C::NB];               // the three source components
-    unsigned char off[C::NB][4];     // ox, oy, oz: window start in the padded block
+    C2Rec<P, TE> rec[C::NB];
+    unsigned char ord[C::NB];        // chunk c's points in order of oy: 32 c + ord[32 c + i]
+    unsigned char start[C::NCH][12]; // chunk c's points with oy = b: ord[32 c + start[b] .. 32 c + start[b + 1])
 };
 
 template <int P, int TE>
@@ -255,7 +278,8 @@ constexpr size_t c2_smem_bytes() {
 }
 
 // Stage points b0 .. b0 + nb - 1 into S: thread t takes dimension d = t / NB
-// of point j = t mod NB.
+// of point j = t mod NB.  The y threads (whole warps) also order their 32
+// points by oy.
 template <int P, int TE>
 __device__ __forceinline__ void c2_stage(C2Stage<P, TE> &S, const GP<float> &g, int b0, int nb, int gx0, int gy0,
                                          int gz0, int c0, bool stress, const float4 *__restrict__ xs,
@@ -265,35 +289,21 @@ __device__ __forceinline__ void c2_stage(C2Stage<P, TE> &S, const GP<float> &g, 
     const int t = threadIdx.x;
     if (t >= 3 * C::NB) return;
     const int d = t / C::NB, j = t - d * C::NB;
-    if (j >= nb) return;
-    const int n = b0 + j;
-    const float4 xv = xs[n];
-    int i0[3];
-    unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
-    const float xd = d == 0 ? xv.x : (d == 1 ? xv.y : xv.z);
-    const int id = d == 0 ? i0[0] : (d == 1 ? i0[1] : i0[2]);
-    const float x0 = d == 0 ? g.x0[0] : (d == 1 ? g.x0[1] : g.x0[2]);
-    const int o0 = d == 0 ? gx0 : (d == 1 ? gy0 : gz0);
-    const float fr = ((xd - x0) * g.inv_h + g.half_ext) - (float)id;
-    const int o = min(max(id - o0, 0), TE - 1);
-    S.off[j][d] = (unsigned char)o;
-    if (d == 2) {
-        // the P weights at slots (oz & 1) .. (oz & 1) + P - 1, zeros elsewhere
-        float *w = reinterpret_cast<float *>(S.wz[j]);
-        const int sh = o & 1;
-#pragma unroll
-        for (int i = 0; i < 2 * C::WP4; i++) {
-            const int kk = i - sh;
-            const float tt = fr - (float)kk;
-            w[i] = (kk >= 0 && kk < P) ? __expf(-g.ah2 * tt * tt) : 0.0f;
-        }
-    } else {
-        float *w = d == 0 ? S.wx[j] : S.wy[j];
-#pragma unroll
-        for (int kk = 0; kk < P; kk++) {
-            const float tt = fr - (float)kk;
-            w[kk] = __expf(-g.ah2 * tt * tt);
-        }
+    const bool valid = j < nb;
+    int o = TE;  // no valid point: an oz no bucket takes
+    float fr = 0.0f;
+    if (valid) {
+        const int n = b0 + j;
+        const float4 xv = xs[n];
+        int i0[3];
+        unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+        const float xd = d == 0 ? xv.x : (d == 1 ? xv.y : xv.z);
+        const int id = d == 0 ? i0[0] : (d == 1 ? i0[1] : i0[2]);
+        const float x0 = d == 0 ? g.x0[0] : (d == 1 ? g.x0[1] : g.x0[2]);
+        const int o0 = d == 0 ? gx0 : (d == 1 ? gy0 : gz0);
+        fr = ((xd - x0) * g.inv_h + g.half_ext) - (float)id;
+        o = min(max(id - o0, 0), TE - 1);
+        reinterpret_cast<unsigned char *>(&S.rec[j].off)[d] = (unsigned char)o;
         if (d == 0) {
             const float4 fv = fs[(size_t)n * fstride + foff];
             float4 sv = fv;
@@ -306,7 +316,44 @@ __device__ __forceinline__ void c2_stage(C2Stage<P, TE> &S, const GP<float> &g, 
                     sv = make_float4(0.5f * (fv.x * qv.y + fv.y * qv.x), 0.5f * (fv.x * qv.z + fv.z * qv.x),
                                      0.5f * (fv.y * qv.z + fv.z * qv.y), 0.0f);
             }
-            S.src[j] = sv;
+            S.rec[j].src = sv;
+        }
+    }
+    if (d == 1) {
+        // order the warp's 32 points by oy: rank within the bucket by ballots
+        const int lane = j & 31, ch = j >> 5;
+        const unsigned lt = (1u << lane) - 1u;
+        int base = 0, pos = 0;
+#pragma unroll
+        for (int bkt = 0; bkt < TE; bkt++) {
+            const unsigned m = __ballot_sync(0xffffffffu, o == bkt);
+            if (lane == 0) S.start[ch][bkt] = (unsigned char)base;
+            if (o == bkt) pos = base + __popc(m & lt);
+            base += __popc(m);
+        }
+        if (lane == 0) S.start[ch][TE] = (unsigned char)base;
+        if (valid) S.ord[32 * ch + pos] = (unsigned char)lane;
+    }
+    if (d == 2) {
+        if (valid) {
+            // the P weights at slots (oz & 1) .. (oz & 1) + P - 1, zeros elsewhere
+            float *w = reinterpret_cast<float *>(S.rec[j].wz);
+            const int sh = o & 1;
+#pragma unroll
+            for (int i = 0; i < 2 * C::WP4; i++) {
+                const int kk = i - sh;
+                const float tt = fr - (float)kk;
+                w[i] = (kk >= 0 && kk < P) ? __expf(-g.ah2 * tt * tt) : 0.0f;
+            }
+        }
+    } else if (valid) {
+        // weights of every column of the block: zero off the point's support
+        float *w = d == 0 ? S.rec[j].wx : S.rec[j].wy;
+#pragma unroll
+        for (int c = 0; c < C::PTP; c++) {
+            const int kk = c - o;
+            const float tt = fr - (float)kk;
+            w[c] = (kk >= 0 && kk < P) ? __expf(-g.ah2 * tt * tt) : 0.0f;
         }
     }
 }
@@ -314,10 +361,9 @@ __device__ __forceinline__ void c2_stage(C2Stage<P, TE> &S, const GP<float> &g, 
 // a_c[OZ/2 + k] += s_c wz[k] for the point's NP z pairs
 template <int P, int ZP, int OZ>
 __device__ __forceinline__ void col_add2(float2 (&a0)[ZP], float2 (&a1)[ZP], float2 (&a2)[ZP], float2 s0, float2 s1,
-                                         float2 s2, const float2 *wz) {
+                                         float2 s2, const float4 *w4) {
     constexpr int Q0 = OZ / 2, NP = P / 2 + (OZ & 1);
     static_assert(Q0 + NP <= ZP, "the point's z support stays inside the column");
-    const float4 *w4 = reinterpret_cast<const float4 *>(wz);
 #pragma unroll
     for (int k2 = 0; k2 < (NP + 1) / 2; k2++) {
         const float4 v = w4[k2];
@@ -333,36 +379,48 @@ __device__ __forceinline__ void col_add2(float2 (&a0)[ZP], float2 (&a1)[ZP], flo
     }
 }
 
-#define SE_COL2_CASES(...)                              \
-    switch (oz) {                                       \
-        case 0: col_add2<P, ZP, 0>(__VA_ARGS__); break; \
-        case 1: col_add2<P, ZP, 1>(__VA_ARGS__); break; \
-        case 2: col_add2<P, ZP, 2>(__VA_ARGS__); break; \
-        case 3: col_add2<P, ZP, 3>(__VA_ARGS__); break; \
-        case 4: col_add2<P, ZP, 4>(__VA_ARGS__); break; \
-        case 5: col_add2<P, ZP, 5>(__VA_ARGS__); break; \
-        case 6: col_add2<P, ZP, 6>(__VA_ARGS__); break; \
-        default: col_add2<P, ZP, 7>(__VA_ARGS__); break; \
+// One staged point into the thread's column (a column off the point's
+// support has zero x or y weight).
+template <int P, int TE, int OZ>
+__device__ __forceinline__ void c2_point(const C2Rec<P, TE> &R, int cx, int cy, float2 (&a0)[C2Cfg<P, TE>::ZP],
+                                         float2 (&a1)[C2Cfg<P, TE>::ZP], float2 (&a2)[C2Cfg<P, TE>::ZP]) {
+    constexpr int ZP = C2Cfg<P, TE>::ZP;
+    const float w = R.wx[cx] * R.wy[cy];
+    const float4 sv = R.src;
+    const float2 s0 = make_float2(sv.x * w, sv.x * w), s1 = make_float2(sv.y * w, sv.y * w),
+                 s2 = make_float2(sv.z * w, sv.z * w);
+    col_add2<P, ZP, OZ>(a0, a1, a2, s0, s1, s2, R.wz);
+}
+
+#define SE_COL2_CASES(...)                                \
+    switch (oz) {                                         \
+        case 0: c2_point<P, TE, 0>(__VA_ARGS__); break;   \
+        case 1: c2_point<P, TE, 1>(__VA_ARGS__); break;   \
+        case 2: c2_point<P, TE, 2>(__VA_ARGS__); break;   \
+        case 3: c2_point<P, TE, 3>(__VA_ARGS__); break;   \
+        case 4: c2_point<P, TE, 4>(__VA_ARGS__); break;   \
+        case 5: c2_point<P, TE, 5>(__VA_ARGS__); break;   \
+        case 6: c2_point<P, TE, 6>(__VA_ARGS__); break;   \
+        default: c2_point<P, TE, 7>(__VA_ARGS__); break;  \
     }
 
-// Accumulate the nb staged points of S into the thread's column.
+// Accumulate the nb staged points of S into the thread's column (threads
+// beyond the block's columns read column 0's weights and keep their sums to
+// themselves).
 template <int P, int TE>
-__device__ __forceinline__ void c2_accumulate(const C2Stage<P, TE> &S, int nb, bool own, int cx, int cy, int cyl,
-                                              int cyh, float2 (&a0)[C2Cfg<P, TE>::ZP],
-                                              float2 (&a1)[C2Cfg<P, TE>::ZP], float2 (&a2)[C2Cfg<P, TE>::ZP]) {
-    constexpr int ZP = C2Cfg<P, TE>::ZP;
-    for (int j = 0; j < nb; j++) {
-        const uchar4 o = *reinterpret_cast<const uchar4 *>(S.off[j]);
-        const int oy = o.y;
-        if (oy > cyh || oy + P - 1 < cyl) continue;  // uniform: the support misses the warp's rows
-        const int kx = cx - o.x, ky = cy - oy;
-        if (own && (unsigned)kx < (unsigned)P && (unsigned)ky < (unsigned)P) {
-            const float w = S.wx[j][kx] * S.wy[j][ky];
-            const float4 sv = S.src[j];
-            const float2 s0 = make_float2(sv.x * w, sv.x * w), s1 = make_float2(sv.y * w, sv.y * w),
-                         s2 = make_float2(sv.z * w, sv.z * w);
-            const int oz = o.z;
-            SE_COL2_CASES(a0, a1, a2, s0, s1, s2, S.wz[j])
+__device__ __forceinline__ void c2_accumulate(const C2Stage<P, TE> &S, int nb, int cx, int cy, int cyl, int cyh,
+                                              float2 (&a0)[C2Cfg<P, TE>::ZP], float2 (&a1)[C2Cfg<P, TE>::ZP],
+                                              float2 (&a2)[C2Cfg<P, TE>::ZP]) {
+    static_assert(TE == 8, "the unrolled z offsets cover tiles of 8");
+    // points in order of oy: the warp takes, per chunk, the contiguous run of
+    // those whose support meets its rows, with a switch on oz per point
+    const int ylo = max(0, cyl - (P - 1)), yhi = min(TE - 1, cyh);
+    for (int ch = 0; ch < (nb + 31) / 32; ch++) {
+        const int i1 = S.start[ch][yhi + 1];
+        for (int i = S.start[ch][ylo]; i < i1; i++) {
+            const C2Rec<P, TE> &R = S.rec[32 * ch + S.ord[32 * ch + i]];
+            const int oz = R.off.z;
+            SE_COL2_CASES(R, cx, cy, a0, a1, a2)
         }
     }
 }
@@ -394,6 +452,20 @@ __device__ __forceinline__ void c2_flush(const GP<float> &g, int gx, int gy, int
     }
 }
 
+// The column a thread owns: (cx, cy) of the block for tid < PT^2; the others
+// (the last warp's tail) take column 0 for their reads and never write.
+template <int P, int TE>
+__device__ __forceinline__ void c2_column(int tid, int &cx, int &cy, int &cyl, int &cyh) {
+    constexpr int PT = C2Cfg<P, TE>::PT;
+    const bool own = tid < PT * PT;
+    cx = own ? tid % PT : 0;
+    cy = own ? tid / PT : 0;
+    // the rows of columns this warp owns
+    const int w0 = tid & ~31;
+    cyl = w0 / PT;
+    cyh = min(w0 + 31, PT * PT - 1) / PT;
+}
+
 template <int P, int TE>
 __device__ __forceinline__ void spread_c2_body(const GP<float> &g, int tile, int beg, int end, int c0, bool stress,
                                                const float4 *__restrict__ xs, const float4 *__restrict__ fs,
@@ -402,15 +474,11 @@ __device__ __forceinline__ void spread_c2_body(const GP<float> &g, int tile, int
                                                C2Stage<P, TE> *S) {
     using C = C2Cfg<P, TE>;
     constexpr int PT = C::PT, ZP = C::ZP, NB = C::NB;
-    static_assert(TE == 8, "the unrolled z offsets cover tiles of 8");
     const int tid = threadIdx.x;
     const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
-    const bool own = tid < PT * PT;
-    const int cx = tid % PT, cy = tid / PT;
-    // the rows of columns this warp owns
-    const int w0 = tid & ~31;
-    const int cyl = w0 / PT, cyh = min(w0 + 31, PT * PT - 1) / PT;
+    int cx, cy, cyl, cyh;
+    c2_column<P, TE>(tid, cx, cy, cyl, cyh);
     float2 a0[ZP], a1[ZP], a2[ZP];
 #pragma unroll
     for (int q = 0; q < ZP; q++) a0[q] = a1[q] = a2[q] = make_float2(0.0f, 0.0f);
@@ -422,10 +490,10 @@ __device__ __forceinline__ void spread_c2_body(const GP<float> &g, int tile, int
         if (b0 + NB < end)
             c2_stage<P, TE>(S[k ^ 1], g, b0 + NB, min(NB, end - b0 - NB), gx0, gy0, gz0, c0, stress, xs, fs, fstride,
                             foff, qs);
-        c2_accumulate<P, TE>(S[k], nb, own, cx, cy, cyl, cyh, a0, a1, a2);
+        c2_accumulate<P, TE>(S[k], nb, cx, cy, cyl, cyh, a0, a1, a2);
         __syncthreads();
     }
-    if (own) c2_flush<P, TE>(g, gx0 + cx, gy0 + cy, gz0, a0, a1, a2, grid + (size_t)c0 * gcs, gzs, gcs);
+    if (tid < PT * PT) c2_flush<P, TE>(g, gx0 + cx, gy0 + cy, gz0, a0, a1, a2, grid + (size_t)c0 * gcs, gzs, gcs);
 }
 
 // w: three grids (the group of right-hand side r); u, f_orig: n_rhs three-vectors per point.
@@ -938,7 +1006,7 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT) k_spread_col(GP<float> g, i
 }
 
 template <int P, int TE>
-__global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? 2 : 1) k_spread_c2(GP<float> g, int c0, bool stress,
+__global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? SE_C2_MINB : 1) k_spread_c2(GP<float> g, int c0, bool stress,
                                                                                 const int *__restrict__ tile_start,
                                                                                 const float4 *__restrict__ xs,
                                                                                 const float4 *__restrict__ fs,
@@ -1056,7 +1124,7 @@ __global__ void __launch_bounds__(ColCfg<P, TE>::NT, 2) k_bspread_col_rhs(const 
 // the (system, tile, rhs) list with the right-hand side innermost; block b
 // takes item b * n_rhs.
 template <int P, int TE>
-__global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? 2 : 1) k_bspread_c2(const BSys<float> *__restrict__ sys,
+__global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? SE_C2_MINB : 1) k_bspread_c2(const BSys<float> *__restrict__ sys,
                                                                                  const int4 *__restrict__ items,
                                                                                  const int *__restrict__ tile_start,
                                                                                  int n_rhs,
@@ -1075,10 +1143,8 @@ __global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? 2 : 1) k_bspread_c
     const int tile = it.y, tid = threadIdx.x;
     const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int gx0 = tx * TE, gy0 = ty * TE, gz0 = tz * TE;
-    const bool own = tid < PT * PT;
-    const int cx = tid % PT, cy = tid / PT;
-    const int w0 = tid & ~31;
-    const int cyl = w0 / PT, cyh = min(w0 + 31, PT * PT - 1) / PT;
+    int cx, cy, cyl, cyh;
+    c2_column<P, TE>(tid, cx, cy, cyl, cyh);
     const bool once = end - beg <= NB;
     for (int r = 0; r < n_rhs; r++) {
         float2 a0[ZP], a1[ZP], a2[ZP];
@@ -1088,10 +1154,10 @@ __global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? 2 : 1) k_bspread_c
             if (r == 0) {
                 c2_stage<P, TE>(S[0], g, beg, end - beg, gx0, gy0, gz0, 0, false, xs, fs, n_rhs, 0, nullptr);
             } else if (tid < end - beg) {
-                S[0].src[tid] = fs[(size_t)(beg + tid) * n_rhs + r];
+                S[0].rec[tid].src = fs[(size_t)(beg + tid) * n_rhs + r];
             }
             __syncthreads();
-            c2_accumulate<P, TE>(S[0], end - beg, own, cx, cy, cyl, cyh, a0, a1, a2);
+            c2_accumulate<P, TE>(S[0], end - beg, cx, cy, cyl, cyh, a0, a1, a2);
             __syncthreads();
         } else {
             c2_stage<P, TE>(S[0], g, beg, NB, gx0, gy0, gz0, 0, false, xs, fs, n_rhs, r, nullptr);
@@ -1102,11 +1168,12 @@ __global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? 2 : 1) k_bspread_c
                 if (b0 + NB < end)
                     c2_stage<P, TE>(S[k ^ 1], g, b0 + NB, min(NB, end - b0 - NB), gx0, gy0, gz0, 0, false, xs, fs,
                                     n_rhs, r, nullptr);
-                c2_accumulate<P, TE>(S[k], nb, own, cx, cy, cyl, cyh, a0, a1, a2);
+                c2_accumulate<P, TE>(S[k], nb, cx, cy, cyl, cyh, a0, a1, a2);
                 __syncthreads();
             }
         }
-        if (own) c2_flush<P, TE>(g, gx0 + cx, gy0 + cy, gz0, a0, a1, a2, B.grid + (size_t)r * 3 * B.gcs, B.gzs, B.gcs);
+        if (tid < PT * PT)
+            c2_flush<P, TE>(g, gx0 + cx, gy0 + cy, gz0, a0, a1, a2, B.grid + (size_t)r * 3 * B.gcs, B.gzs, B.gcs);
     }
 }
 

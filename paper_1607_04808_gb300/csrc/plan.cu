@@ -63,12 +63,17 @@ double min_rc(int kernel, double Q, double xi, double L, double budget) {
 }
 
 // FFT lengths cuFFT handles fast and accurately: only prime factors 2, 3, 5, 7.
-// In FP32 the 256-point length is excluded: with 256^3 transforms the Fourier
-// part of the FP32 path measured an order of magnitude less accurate (5e-6
-// relative) than with the neighbouring lengths 248, 252, 264 (3e-7 to 9e-7).
+// In FP32 the powers of two from 32 on are excluded: cuFFT's single-precision
+// real-to-complex and complex-to-real transforms at 128^3 and 256^3 left the
+// Fourier part an order of magnitude less accurate (2.8e-6 and 5.2e-6
+// relative, N = 46030 and 1e6 uniform points at 2e-6) than the neighbouring
+// lengths 96 to 200 and 252 (3e-7 to 9e-7); the complex-to-complex transforms
+// of the same lengths were accurate, and so were 96 and 192.
+bool pow2_fp32_bad(int n, int prec) { return prec == SE_FP32 && n >= 32 && (n & (n - 1)) == 0; }
+
 bool good_fft(int n, int prec) {
     if (n < 2) return false;
-    if (prec == SE_FP32 && n == 256) return false;
+    if (pow2_fp32_bad(n, prec)) return false;
     int m = n;
     for (int f : {2, 3, 5, 7})
         while (m % f == 0) m /= f;
@@ -100,8 +105,9 @@ double model_cost(int prec, int64_t N, double L, int P, int M, double rc, const 
 // FFT lengths measured fast with cuFFT on GB300: 2^a 3^b, times at most one 5,
 // and a multiple of 4 (350, 400, 420 and 448 took 1.2 to 1.5 times the time
 // per point of 320, 360, 384 and 432).
-bool fast_fft_len(int n) {
+bool fast_fft_len(int n, int prec) {
     if (n < 8 || (n & 3)) return false;
+    if (pow2_fp32_bad(n, prec)) return false;
     int m = n, fives = 0;
     while (m % 2 == 0) m /= 2;
     while (m % 3 == 0) m /= 3;
@@ -545,7 +551,7 @@ extern "C" se_status_t se_choose_params_points(se_kernel_t kernel, se_prec_t pre
     if (s != SE_OK) return s;
     // FFT length: of the fast lengths (fast_fft_len) around 2 (M + P), the one
     // of least modelled work
-    auto fast = fast_fft_len;
+    auto fast = [prec](int n) { return fast_fft_len(n, prec); };
     const int Mf0 = 2 * (pm.M + pm.P);
     int lo = Mf0, hi = Mf0;
     while (lo > 2 * (pm.P + 2) && !fast(lo)) lo -= 2;

@@ -60,6 +60,33 @@ __device__ __forceinline__ float ex2_approx(float v) {
     return r;
 }
 
+// SE_RS_RAWMUFU: the reciprocal square root and reciprocal of the paired pair
+// sums as the plain PTX approximations (one special-function instruction
+// each, flush-to-zero).  Their arguments are normal numbers by construction
+// (r^2 of distinct FP32 points, 2 + xi r), so the special-value handling of
+// rsqrtf and __fdividef is never needed; 0 restores those.
+#ifndef SE_RS_RAWMUFU
+#define SE_RS_RAWMUFU 1
+#endif
+__device__ __forceinline__ float rsqrt_fast(float v) {
+#if SE_RS_RAWMUFU
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+#else
+    return rsqrtf(v);
+#endif
+}
+__device__ __forceinline__ float rcp_fast(float v) {
+#if SE_RS_RAWMUFU
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+#else
+    return __fdividef(1.0f, v);
+#endif
+}
+
 // erfcx(x) ~ Q(t), t = 1/(2 + x), from the fits of erfc_poly.cuh: PV = 1 for
 // x <= 5 (degree 8), PV = 0 for x <= 8 (degree 10).
 template <int PV>
@@ -101,12 +128,12 @@ __device__ __forceinline__ float2 erfcx_poly2(float2 t) {
 template <int PV>
 __device__ __forceinline__ void radial_ab2(const RC<float> &rk, float2 r2, bool ua, bool ub, float2 &a,
                                            float2 &b) {
-    const float2 rinv = make_float2(ua ? rsqrtf(r2.x) : 0.f, ub ? rsqrtf(r2.y) : 0.f);
+    const float2 rinv = make_float2(ua ? rsqrt_fast(r2.x) : 0.f, ub ? rsqrt_fast(r2.y) : 0.f);
     const float2 r = __fmul2_rn(r2, rinv);
     const float2 ce = __fmul2_rn(f2(rk.ce), r2);
     const float2 e = make_float2(ex2_approx(ce.x), ex2_approx(ce.y));
     const float2 y = __ffma2_rn(f2(rk.xi), r, f2(2.0f));
-    const float2 q = erfcx_poly2<PV>(make_float2(__fdividef(1.0f, y.x), __fdividef(1.0f, y.y)));
+    const float2 q = erfcx_poly2<PV>(make_float2(rcp_fast(y.x), rcp_fast(y.y)));
     const float2 er = __fmul2_rn(e, rinv);
     a = __fmul2_rn(er, __ffma2_rn(f2(-rk.c), r, q));
     b = __fmul2_rn(__fmul2_rn(er, __fmul2_rn(rinv, rinv)), __ffma2_rn(f2(rk.c), r, q));
@@ -119,12 +146,12 @@ __device__ __forceinline__ void radial_ab2(const RC<float> &rk, float2 r2, bool 
 template <int PV>
 __device__ __forceinline__ void radial_ab2_str(const RC<float> &rk, float2 r2, bool ua, bool ub, float2 &A,
                                                float2 &B) {
-    const float2 rinv = make_float2(ua ? rsqrtf(r2.x) : 0.f, ub ? rsqrtf(r2.y) : 0.f);
+    const float2 rinv = make_float2(ua ? rsqrt_fast(r2.x) : 0.f, ub ? rsqrt_fast(r2.y) : 0.f);
     const float2 r = __fmul2_rn(r2, rinv);
     const float2 ce = __fmul2_rn(f2(rk.ce), r2);
     const float2 e = make_float2(ex2_approx(ce.x), ex2_approx(ce.y));
     const float2 y = __ffma2_rn(f2(rk.xi), r, f2(2.0f));
-    const float2 q = erfcx_poly2<PV>(make_float2(__fdividef(1.0f, y.x), __fdividef(1.0f, y.y)));
+    const float2 q = erfcx_poly2<PV>(make_float2(rcp_fast(y.x), rcp_fast(y.y)));
     // A1 = -2 e [c r (2 x^2 + 3) + 3 Q] / r^2,  A2 = 2 xi^2 c r e,  x = xi r (from r,
     // not r2: a masked slot far away has r = 0, and 0 * (2 xi^2 r2) could be 0 * inf)
     const float2 cr = __fmul2_rn(f2(rk.c), r);
@@ -143,11 +170,11 @@ __device__ __forceinline__ void radial_ab2_str(const RC<float> &rk, float2 r2, b
 // terms, so a = (e / r)(Q - c r) and b = (e / r^3)(Q + c r), c = 2 xi/sqrt(pi).
 template <int KERNEL, int PV>
 __device__ __forceinline__ void radial_ab(const RC<float> &rk, float r2, float &rinv, float &a, float &b) {
-    rinv = rsqrtf(r2);
+    rinv = rsqrt_fast(r2);
     const float r = r2 * rinv;
     const float x = rk.xi * r;
     const float e = ex2_approx(rk.ce * r2);
-    const float q = erfcx_poly<PV>(__fdividef(1.0f, 2.0f + x));
+    const float q = erfcx_poly<PV>(rcp_fast(2.0f + x));
     const float cr = rk.c * r;  // (2/sqrt(pi)) x
     if (KERNEL == SE_STRESSLET) {
         a = -2.0f * e * fmaf(cr, fmaf(2.0f * x, x, 3.0f), 3.0f * q) * (rinv * rinv);
@@ -170,9 +197,9 @@ template <int KERNEL, int PV>
 __device__ __forceinline__ void grad_pair(const RC<float> &rk, float dx, float dy, float dz, float r2,
                                           const float4 &ft, const float4 &gt, const float4 &fj, const float4 &gj,
                                           float G[3]) {
-    const float rinv = rsqrtf(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+    const float rinv = rsqrt_fast(r2), r = r2 * rinv, rinv2 = rinv * rinv;
     const float e = ex2_approx(rk.ce * r2);
-    const float ec = e * erfcx_poly<PV>(__fdividef(1.0f, 2.0f + rk.xi * r));
+    const float ec = e * erfcx_poly<PV>(rcp_fast(2.0f + rk.xi * r));
     const float c1 = rk.c;
     const float b = fmaf(ec, rinv, c1 * e) * rinv2;
     const float bp = -3.0f * c1 * e * rinv2 * rinv - 3.0f * ec * rinv2 * rinv2 - 2.0f * c1 * rk.xi2 * e * rinv;
@@ -1181,8 +1208,10 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
         const int nq = min(fill, 32);
         {
             const bool valid = lane < nq;
-            // an idle lane's candidate: at infinity, or far but finite on the paired path
-            const float far = PAIR ? 1e18f : INF;
+            // an idle lane's candidate: at infinity, or far but finite on the paired
+            // path, on the other side from the empty target slots (+1e18), so that
+            // the two never meet at distance zero
+            const float far = PAIR ? -1e18f : INF;
             float4 xj = make_float4(far, far, far, 0.f);
             float4 fj = make_float4(0.f, 0.f, 0.f, 0.f), qj = fj;
             int vs = 0, mj = 0;

@@ -392,7 +392,7 @@ se_status_t choose_box_params(int kernel, int prec, int64_t N, const double box[
                               const PairFactor *pf = nullptr);
 // the work model of the parameter selection (relative to one real-space pair)
 double model_cost(int prec, int64_t N, double L, int P, int M, double rc, const PairFactor *pf, int n_rhs);
-// FFT lengths measured fast with cuFFT on GB300
-bool fast_fft_len(int n);
+// FFT lengths measured fast with cuFFT on GB300 (and, in FP32, accurate)
+bool fast_fft_len(int n, int prec);
 
 }  // namespace se

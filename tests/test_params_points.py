@@ -28,7 +28,12 @@ def same(a, b):
     return all(a[k] == b[k] for k in a)
 
 
-def fast_fft(n):
+def fast_fft(n, prec="fp32"):
+    """The fast FFT lengths of the selection: 2^a 3^b (at most one 5), a multiple of
+    4; FP32 leaves out the powers of two from 32 on (their single-precision
+    real-to-complex transforms were measured an order of magnitude less accurate)."""
+    if prec == "fp32" and n >= 32 and n & (n - 1) == 0:
+        return False
     m, fives = n, 0
     while m % 2 == 0:
         m //= 2
