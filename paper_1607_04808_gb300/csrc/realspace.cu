@@ -52,6 +52,11 @@ constexpr int QCAP = 64;
 #ifndef SE_RS_PAIR_STR
 #define SE_RS_PAIR_STR 1
 #endif
+// SE_RS_BRANCH: the paired sums skip the radial functions of a target pair
+// none of whose two pairs is within the cutoff (0: always evaluate, masked)
+#ifndef SE_RS_BRANCH
+#define SE_RS_BRANCH 1
+#endif
 constexpr int MAXROWS = 121;  // (2 reach_y + 1)(2 reach_z + 1) rows of cells at most
 
 __device__ __forceinline__ float ex2_approx(float v) {
@@ -991,33 +996,35 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
     static_assert(!(PER && STR), "periodic plans sum the stresslet with k_real_cmp");
     static_assert(!(GRAD && (PER || STR)), "the gradient mode is for free-space stokeslet and rotlet plans");
     constexpr bool HQ = STR || GRAD;  // a third vector per point: q, or g
-    __shared__ float4 tx_all[WPB][TC];
-    __shared__ float4 tf_all[WPB][TC];
-    __shared__ float4 tq_all[HQ ? WPB : 1][TC];
-    __shared__ float4 qx_all[WPB][QN];
-    __shared__ float4 qf_all[WPB][QN];
-    __shared__ float4 qq_all[HQ ? WPB : 1][QN];
-    __shared__ int qm_all[WPB][QN];
     constexpr int NSEG = PER ? 2 * MAXROWS : MAXROWS;  // entries of the segment list
-    __shared__ int2 seg_all[WPB][NSEG];
-    __shared__ int pre_all[WPB][NSEG + 1];
-    __shared__ float box_all[WPB][6];
     // PAIR: neighbouring targets 2p and 2p + 1 side by side (their cutoff
-    // tests mostly agree), [component][2 p + slot] = [component][t]; the
-    // components are x, f and, for the stresslet, q and f.q
+    // tests mostly agree); the components are x, f and, for the stresslet, q
+    // and f.q
     constexpr bool PAIR = SE_RS_PAIR && (!STR || SE_RS_PAIR_STR) && !GRAD;
     constexpr int NTP = STR ? 10 : 6;
-    __shared__ __align__(8) float tp_all[PAIR ? WPB : 1][NTP][TC];
+    // one warp's shared memory in one record, so that one base address serves
+    // every access
+    struct __align__(16) WarpSmem {
+        float4 tx[TC], tf[TC], tq[HQ ? TC : 1];
+        float4 qx[QN], qf[QN], qq[HQ ? QN : 1];  // the candidate queue
+        float tp[PAIR ? TC / 2 : 1][NTP][2];      // [pair p][component][slot]: 16-byte loads of two components
+        int qm[QN];
+        int2 seg[NSEG];
+        int pre[NSEG + 1];
+        float box[6];
+    };
+    __shared__ WarpSmem ws_all[WPB];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * WPB + wib;
     if (c >= *ncl_total) return;
-    float4 *tx = tx_all[wib], *tf = tf_all[wib], *tq = tq_all[HQ ? wib : 0];
-    float (*tp)[TC] = tp_all[PAIR ? wib : 0];
-    float *box = box_all[wib];
-    float4 *qx = qx_all[wib], *qf = qf_all[wib], *qq = qq_all[HQ ? wib : 0];
-    int *qm = qm_all[wib];
-    int2 *seg = seg_all[wib];
-    int *pre = pre_all[wib];
+    WarpSmem &W = ws_all[wib];
+    float4 *tx = W.tx, *tf = W.tf, *tq = W.tq;
+    float (*tp)[NTP][2] = W.tp;
+    float *box = W.box;
+    float4 *qx = W.qx, *qf = W.qf, *qq = W.qq;
+    int *qm = W.qm;
+    int2 *seg = W.seg;
+    int *pre = W.pre;
     const int2 cl = clusters[c];
     const float INF = __int_as_float(0x7f800000);
     // the cluster's targets (slots beyond its size at infinity: no pair) and
@@ -1038,19 +1045,19 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
         if (HQ) tq[lane] = qo;
         if (PAIR) {
             // empty slots far away but finite: a masked slot's products stay 0
-            const int o = lane;  // pair p = t / 2, slot t mod 2
+            const int pp = lane >> 1, o = lane & 1;  // pair p = t / 2, slot t mod 2
             const bool real = lane < cl.y;
-            tp[0][o] = real ? xo.x : 1e18f;
-            tp[1][o] = real ? xo.y : 1e18f;
-            tp[2][o] = real ? xo.z : 1e18f;
-            tp[3][o] = fo.x;
-            tp[4][o] = fo.y;
-            tp[5][o] = fo.z;
+            tp[pp][0][o] = real ? xo.x : 1e18f;
+            tp[pp][1][o] = real ? xo.y : 1e18f;
+            tp[pp][2][o] = real ? xo.z : 1e18f;
+            tp[pp][3][o] = fo.x;
+            tp[pp][4][o] = fo.y;
+            tp[pp][5][o] = fo.z;
             if (STR) {
-                tp[6][o] = qo.x;
-                tp[7][o] = qo.y;
-                tp[8][o] = qo.z;
-                tp[9][o] = fo.x * qo.x + fo.y * qo.y + fo.z * qo.z;
+                tp[pp][6][o] = qo.x;
+                tp[pp][7][o] = qo.y;
+                tp[pp][8][o] = qo.z;
+                tp[pp][9][o] = fo.x * qo.x + fo.y * qo.y + fo.z * qo.z;
             }
         }
     }
@@ -1231,9 +1238,11 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
                 float2 c2[3] = {f2(0.f), f2(0.f), f2(0.f)};
 #pragma unroll
                 for (int p2 = 0; p2 < TC / 2; p2++) {
-                    float2 dx = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[0][2 * p2]), nx);
-                    float2 dy = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[1][2 * p2]), ny);
-                    float2 dz = __fadd2_rn(*reinterpret_cast<const float2 *>(&tp[2][2 * p2]), nz);
+                    const float4 *t4 = reinterpret_cast<const float4 *>(tp[p2]);
+                    const float4 v0 = t4[0], v1 = t4[1], v2 = t4[2];
+                    float2 dx = __fadd2_rn(make_float2(v0.x, v0.y), nx);
+                    float2 dy = __fadd2_rn(make_float2(v0.z, v0.w), ny);
+                    float2 dz = __fadd2_rn(make_float2(v1.x, v1.y), nz);
                     if (PER && wide) {
                         // nearest images pair by pair
                         dx.x -= g.len[0] * rintf(dx.x * g.ilen[0]);
@@ -1250,15 +1259,14 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
                         ia = ia && 2 * p2 < cl.y;
                         ib = ib && 2 * p2 + 1 < cl.y;
                     }
-                    if (ia || ib) {
+                    if (!SE_RS_BRANCH || ia || ib) {
                         // zero distance: a distinct point at the same position, skipped
                         const bool ua = ia && r2.x > 0.f, ub = ib && r2.y > 0.f;
                         coinc |= (ia && !ua) || (ib && !ub);
                         float2 a, b;
                         if constexpr (!STR) radial_ab2<PV>(rk, r2, ua, ub, a, b);
-                        const float2 gx = *reinterpret_cast<const float2 *>(&tp[3][2 * p2]);
-                        const float2 gy = *reinterpret_cast<const float2 *>(&tp[4][2 * p2]);
-                        const float2 gz = *reinterpret_cast<const float2 *>(&tp[5][2 * p2]);
+                        const float2 gx = make_float2(v1.z, v1.w), gy = make_float2(v2.x, v2.y),
+                                     gz = make_float2(v2.z, v2.w);
                         if constexpr (STR) {
                             // u_t += T(d).(f_j, q_j),  u_j -= T(d).(f_t, q_t)
                             float2 A, B;
@@ -1272,10 +1280,9 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
                             accp[p2][0] = __ffma2_rn(s, dx, __ffma2_rn(B, w0, accp[p2][0]));
                             accp[p2][1] = __ffma2_rn(s, dy, __ffma2_rn(B, w1, accp[p2][1]));
                             accp[p2][2] = __ffma2_rn(s, dz, __ffma2_rn(B, w2, accp[p2][2]));
-                            const float2 hx = *reinterpret_cast<const float2 *>(&tp[6][2 * p2]);
-                            const float2 hy = *reinterpret_cast<const float2 *>(&tp[7][2 * p2]);
-                            const float2 hz = *reinterpret_cast<const float2 *>(&tp[8][2 * p2]);
-                            const float2 fqt = *reinterpret_cast<const float2 *>(&tp[9][2 * p2]);
+                            const float4 v3 = t4[3], v4 = t4[4];
+                            const float2 hx = make_float2(v3.x, v3.y), hy = make_float2(v3.z, v3.w);
+                            const float2 hz = make_float2(v4.x, v4.y), fqt = make_float2(v4.z, v4.w);
                             const float2 dg = __ffma2_rn(dz, gz, __ffma2_rn(dy, gy, __fmul2_rn(dx, gx)));
                             const float2 dh = __ffma2_rn(dz, hz, __ffma2_rn(dy, hy, __fmul2_rn(dx, hx)));
                             const float2 nB = __fmul2_rn(f2(-1.f), B);
