@@ -729,14 +729,22 @@ __device__ __forceinline__ void lane_columns(int lane, int (&kxs)[NIT], int (&ky
     }
 }
 
-template <int P, int TE, bool TMA, bool ZC = false>
+// MODE 0: u = the three gathered values (+ the self term).  MODE 1, 2: the
+// stresslet's adjoint strength gradients from the symmetric tensor field V
+// (xx, yy, zz, xy, xz, yz), three grids per pass: MODE 1 takes the diagonal
+// grids and writes grad_f_l = V_ll q_l, grad_q_l = V_ll f_l; MODE 2 takes
+// (xy, xz, yz) and adds the off-diagonal terms, grad_f_l += sum_{k != l} V_lk
+// q_k, grad_q_l += sum_{k != l} V_lk f_k (u is grad_f, gq grad_q; either may
+// be NULL).
+template <int P, int TE, bool TMA, bool ZC = false, int MODE = 0>
 __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, int beg, int end,
                                                  const float4 *__restrict__ xs, const int *__restrict__ perm,
                                                  const float *__restrict__ w, int n_rhs, int r,
                                                  const float *__restrict__ f_orig, double self_coef,
                                                  float *__restrict__ u, size_t gzs, size_t gcs,
                                                  const void *tmap = nullptr, int *status = nullptr,
-                                                 bool skip_copy = false) {
+                                                 bool skip_copy = false, const float *__restrict__ q_orig = nullptr,
+                                                 float *__restrict__ gq = nullptr) {
     // gzs, gcs: the grids' z-plane and component strides
     constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX, NIT = GsLayout<P, PT>::NIT;
     constexpr int PLANE = PT * PX;
@@ -814,11 +822,38 @@ __device__ __forceinline__ void gather_smem_body(const GP<float> &g, int tile, i
             acc1 += __shfl_xor_sync(FULL, acc1, o);
             acc2 += __shfl_xor_sync(FULL, acc2, o);
         }
-        if (lane < 3) {
+        if (MODE == 0 && lane < 3) {
             const size_t o3 = ((size_t)mcur * n_rhs + r) * 3 + lane;
             double o = (double)(lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2));
             if (self_coef != 0.0) o += self_coef * (double)fcur;
             u[o3] = (float)o;
+        }
+        if (MODE != 0 && lane < 3) {
+            const size_t b3 = 3 * (size_t)mcur;
+            const float q0 = q_orig[b3], q1 = q_orig[b3 + 1], q2 = q_orig[b3 + 2];
+            const float f0 = f_orig[b3], f1 = f_orig[b3 + 1], f2 = f_orig[b3 + 2];
+            if (MODE == 1) {
+                const float v = lane == 0 ? acc0 : (lane == 1 ? acc1 : acc2);
+                if (u) u[b3 + lane] = v * (lane == 0 ? q0 : (lane == 1 ? q1 : q2));
+                if (gq) gq[b3 + lane] = v * (lane == 0 ? f0 : (lane == 1 ? f1 : f2));
+            } else {
+                // (acc0, acc1, acc2) = (V_xy, V_xz, V_yz); row l of V without its
+                // diagonal: l = 0: (xy, xz) against (y, z); 1: (xy, yz) against
+                // (x, z); 2: (xz, yz) against (x, y)
+                float tq, tf;
+                if (lane == 0) {
+                    tq = acc0 * q1 + acc1 * q2;
+                    tf = acc0 * f1 + acc1 * f2;
+                } else if (lane == 1) {
+                    tq = acc0 * q0 + acc2 * q2;
+                    tf = acc0 * f0 + acc2 * f2;
+                } else {
+                    tq = acc1 * q0 + acc2 * q1;
+                    tf = acc1 * f0 + acc2 * f1;
+                }
+                if (u) u[b3 + lane] += tq;
+                if (gq) gq[b3 + lane] += tf;
+            }
         }
         __syncwarp();
     }
@@ -944,6 +979,24 @@ __device__ __forceinline__ void grad_smem_body(const GP<float> &g, int tile, int
         }
         __syncwarp();
     }
+}
+
+template <int P, int TE, bool TMA, int MODE>
+__global__ void __launch_bounds__(GS_WARPS * 32) k_gather_adj_smem(GP<float> g, const int *__restrict__ tile_start,
+                                                                   const float4 *__restrict__ xs,
+                                                                   const int *__restrict__ perm,
+                                                                   const float *__restrict__ w,
+                                                                   const float *__restrict__ f,
+                                                                   const float *__restrict__ q, float *__restrict__ gf,
+                                                                   float *__restrict__ gq,
+                                                                   const __grid_constant__ CUtensorMap tmap,
+                                                                   int *__restrict__ status) {
+    const int tile = blockIdx.x;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    const size_t Mf2 = (size_t)g.mf[0] * g.mf[1], Mf3 = Mf2 * g.mf[2];
+    gather_smem_body<P, TE, TMA, false, MODE>(g, tile, beg, end, xs, perm, w, 1, 0, f, 0.0, gf, Mf2, Mf3, &tmap,
+                                              status, false, q, gq);
 }
 
 template <int P, int TE, bool TMA>
@@ -1284,6 +1337,31 @@ struct GatherRun {
 };
 
 template <int P, int TE>
+struct GatherAdjRun {
+    // the two passes over V (diagonal, then off-diagonal grids)
+    static cudaError_t run(const GP<float> g, int ntiles, const int *ts, const float4 *xs, const int *perm,
+                           const float *V, const float *f, const float *q, float *gf, float *gq, int *status,
+                           cudaStream_t st) {
+        constexpr int PT = TE + P - 1, PX = GsLayout<P, PT>::PX;
+        const size_t smem = gather_smem_bytes<P, TE>();
+        const size_t Mf2 = (size_t)g.mf[0] * g.mf[1], Mf3 = vol(g);
+        for (int pass = 0; pass < 2; pass++) {
+            const float *w = V + (size_t)pass * 3 * Mf3;
+            alignas(64) CUtensorMap map;
+            memset(&map, 0, sizeof(map));
+            const bool tma = SE_GATHER_TMA && encode_gather_map(&map, g, w, Mf2, Mf3, PX, PT);
+            auto kern = pass == 0 ? (tma ? k_gather_adj_smem<P, TE, true, 1> : k_gather_adj_smem<P, TE, false, 1>)
+                                  : (tma ? k_gather_adj_smem<P, TE, true, 2> : k_gather_adj_smem<P, TE, false, 2>);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e) return e;
+            kern<<<ntiles, GS_WARPS * 32, smem, st>>>(g, ts, xs, perm, w, f, q, gf, gq, map, status);
+            if ((e = cudaGetLastError())) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
+template <int P, int TE>
 struct GradRun {
     static cudaError_t run(const GP<float> g, int ntiles, const int *ts, const float4 *xs, const int *perm,
                            const float *w, int mode, const float *ca, const float *cb, float c_grad, float *gx,
@@ -1362,6 +1440,14 @@ cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &
                                       (const int *)b.perm_t, (const float *)wgrid, f_orig, self_coef, u,
                                       p->b.status, p->test_flags & SE_TEST_SKIP_TILE_COPY, st);
     if (!e) p->launches++;
+    return e;
+}
+
+cudaError_t launch_gather_adj_col(se_plan_s *p, cudaStream_t st, const float *V, const float *f, const float *q,
+                                  float *gf, float *gq) {
+    cudaError_t e = with_p<GatherAdjRun>(p->P, p->gpf, p->ntiles, (const int *)p->b.cnt_t, (const float4 *)p->b.xs_t,
+                                         (const int *)p->b.perm_t, V, f, q, gf, gq, p->b.status, st);
+    if (!e) p->launches += 2;
     return e;
 }
 

@@ -200,12 +200,31 @@ se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *q, const T
     if (stress) {
         const size_t nk = (size_t)p->mf[2] * p->mf[1] * (p->mf[0] / 2 + 1);
         CK(launch_spread<T>(p, st, p->b.xs_t, p->b.fs_t, nullptr, p->grid, 3));
-        CF(cufftSetStream(p->fwd3, st));
-        CF(exec_fwd<T>(p->fwd3, p->grid, p->spec));
-        CK(launch_scale_adj_stresslet<T>(p, st, p->spec));
-        CF(cufftSetStream(p->inv, st));
-        CF(exec_inv<T>(p->inv, p->spec, p->wgrid2));
-        CF(exec_inv<T>(p->inv, (cplx<T> *)p->spec + 3 * nk, (T *)p->wgrid2 + 3 * Mf3));
+        if (p->pruned) {
+            // the zero-padding-aware transforms of the forward evaluation: three
+            // source grids in, the six components of V out (the gathers read
+            // only the z < Mtilde planes)
+            const size_t plane_c = (size_t)p->mf[1] * (p->mf[0] / 2 + 1), cs = sizeof(cplx<T>);
+            CF(cufftSetStream(p->f2d, st));
+            CF(cufftSetStream(p->zc, st));
+            CF(cufftSetStream(p->i2d, st));
+            for (int c = 0; c < 3; c++)
+                CF(exec_fwd<T>(p->f2d, (T *)p->grid + c * Mf3, (cplx<T> *)p->spec + c * nk));
+            CK(cudaMemset2DAsync((char *)p->spec + p->mt[2] * plane_c * cs, nk * cs, 0,
+                                 (p->mf[2] - p->mt[2]) * plane_c * cs, 3, st));
+            for (int c = 0; c < 3; c++) CF(exec_z<T>(p->zc, (cplx<T> *)p->spec + c * nk, CUFFT_FORWARD));
+            CK(launch_scale_adj_stresslet<T>(p, st, p->spec));
+            for (int c = 0; c < 6; c++) CF(exec_z<T>(p->zc, (cplx<T> *)p->spec + c * nk, CUFFT_INVERSE));
+            for (int c = 0; c < 6; c++)
+                CF(exec_inv<T>(p->i2d, (cplx<T> *)p->spec + c * nk, (T *)p->wgrid2 + c * Mf3));
+        } else {
+            CF(cufftSetStream(p->fwd3, st));
+            CF(exec_fwd<T>(p->fwd3, p->grid, p->spec));
+            CK(launch_scale_adj_stresslet<T>(p, st, p->spec));
+            CF(cufftSetStream(p->inv, st));
+            CF(exec_inv<T>(p->inv, p->spec, p->wgrid2));
+            CF(exec_inv<T>(p->inv, (cplx<T> *)p->spec + 3 * nk, (T *)p->wgrid2 + 3 * Mf3));
+        }
         tm.mark();
         if (gf || gq) CK(launch_gather_adjT<T>(p, st, p->wgrid2, f, q, gf, gq));
         tm.mark();

@@ -318,9 +318,16 @@ template cudaError_t launch_bgather<float>(const BSys<float> *, const int *, int
                                            const float *, float *, cudaStream_t);
 template cudaError_t launch_bgather<double>(const BSys<double> *, const int *, int, int, int, int, const Buffers &,
                                             const double *, double *, cudaStream_t);
+// SE_ADJ_COL: the FP32 stresslet adjoint gather on the shared-memory tiles
+#ifndef SE_ADJ_COL
+#define SE_ADJ_COL 1
+#endif
 template <typename T>
 cudaError_t launch_gather_adjT(se_plan_s *p, cudaStream_t st, const void *V, const T *f_orig, const T *q_orig,
                                T *gf, T *gq) {
+    if (sizeof(T) == 4 && p->colk && SE_ADJ_COL)
+        return launch_gather_adj_col(p, st, (const float *)V, (const float *)f_orig, (const float *)q_orig,
+                                     (float *)gf, (float *)gq);
     const int N = (int)p->N;
     k_gather_adjT<T><<<(N + WPB - 1) / WPB, WPB * 32, 0, st>>>(gp<T>(p), N, (const vec4<T> *)p->b.xs_t, p->b.perm_t,
                                                               (const T *)V, f_orig, q_orig, gf, gq);

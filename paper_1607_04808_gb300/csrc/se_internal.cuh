@@ -334,6 +334,10 @@ cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, con
 cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, const float *f_orig, float *u);
 cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &b, const void *wgrid,
                                   const float *f_orig, double self_coef, float *u);
+// the stresslet's adjoint strength gradients from the tensor field V on the
+// shared-memory tiles (FP32 column plans)
+cudaError_t launch_gather_adj_col(se_plan_s *p, cudaStream_t st, const float *V, const float *f, const float *q,
+                                  float *gf, float *gq);
 // du/dx of the Fourier part on the shared-memory tiles (FP32 column plans)
 cudaError_t launch_gather_grad_col(se_plan_s *p, cudaStream_t st, const float *w_fwd, const float *w_adj,
                                    const float *f_orig, const float *q_orig, const float *g_orig, float *gx);

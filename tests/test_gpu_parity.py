@@ -456,6 +456,31 @@ def test_full_size_fp32_rotlet_backward_sampled():
     assert checked == 3
 
 
+def test_full_size_fp32_stresslet_backward_sampled():
+    """N = 2e5 stresslet, FP32 forward and backward (du/df, du/dq and du/dx, grid
+    recomputed): u and the three gradients at 256 sampled points against the
+    exact direct sums."""
+    N = 200_000
+    x, f, g = W.rotlet_uniform(N, 3)
+    q = W.unit_vectors(N, 3)
+    x32, f32, g32, q32 = as32(x), as32(f), as32(g), as32(q)
+    x32 = np.minimum(x32, np.nextafter(np.float32(1.0), np.float32(0)))
+    pkg = P()
+    plan = pkg.Plan("stresslet", N, BOX, prec="fp32", tol=2e-6)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")  # noqa: E731
+    u = plan.eval(t(x32), t(f32), t(q32), check=True).double().cpu().numpy()
+    gf, gx, gq = plan.backward(t(x32), t(f32), t(g32), q=t(q32), want_q=True)
+    plan.check()
+    gf, gx, gq = gf.double().cpu().numpy(), gx.double().cpu().numpy(), gq.double().cpu().numpy()
+    plan.close()
+    idx = np.random.default_rng(4).choice(N, 256, replace=False)
+    ref_u = direct.direct("stresslet", x32, f32, q32, targets=idx)
+    ref_gf, ref_gq = direct.grad_fq(x32, f32, q32, g32, targets=idx)
+    ref_gx = direct.grad_x("stresslet", x32, f32, g32, q32, targets=idx)
+    for got, ref in ((u, ref_u), (gf, ref_gf), (gq, ref_gq), (gx, ref_gx)):
+        assert rel_l2(got[idx], ref) <= 2e-6 and rel_max(got[idx], ref) <= 2e-6
+
+
 # ------------------------------------------------------------------ separate targets
 
 @pytest.mark.parametrize("kernel", KN)
