@@ -92,8 +92,15 @@ bool good_fft(int n, int prec) {
 // extra side).
 }  // namespace
 
+#ifndef SE_MODEL_CGRID32
+#define SE_MODEL_CGRID32 0.12
+#endif
+#ifndef SE_MODEL_CFFT32
+#define SE_MODEL_CFFT32 0.6
+#endif
 double model_cost(int prec, int64_t N, double L, int P, int M, double rc, const PairFactor *pf, int n_rhs) {
-    const double cpair = 1.0, cgrid = (prec == SE_FP32) ? 0.12 : 0.036, cfft = (prec == SE_FP32) ? 0.6 : 0.11;
+    const double cpair = 1.0, cgrid = (prec == SE_FP32) ? SE_MODEL_CGRID32 : 0.036,
+                 cfft = (prec == SE_FP32) ? SE_MODEL_CFFT32 : 0.11;
     const double Mf = 2.0 * (M + P);
     double pairs = (double)N * (double)N * 4.18879 * rc * rc * rc / (L * L * L);
     if (pf) pairs *= pf->at(rc);

@@ -48,6 +48,10 @@ constexpr int QCAP = 64;
 #ifndef SE_GRAD_SYM
 #define SE_GRAD_SYM 1
 #endif
+// SE_GRAD_SYM_STR: the same for the stresslet's position gradient
+#ifndef SE_GRAD_SYM_STR
+#define SE_GRAD_SYM_STR 1
+#endif
 // SE_RS_PAIR_STR: the same for the stresslet's symmetric pair sum
 #ifndef SE_RS_PAIR_STR
 #define SE_RS_PAIR_STR 1
@@ -229,6 +233,50 @@ __device__ __forceinline__ void grad_pair(const RC<float> &rk, float dx, float d
         G[1] = b * cy + rcd * dy;
         G[2] = b * cz + rcd * dz;
     }
+}
+
+// The stresslet's pair term of L = sum g . u as a trilinear form of d = x_t -
+// x_j (Section 6, T^R rescaled for d itself: A = A1/r^3, B = A2/r):
+//   Phi(d; a, b, c) = A (d.a)(d.b)(d.c) + B [(a.b)(d.c) + (b.c)(d.a) + (c.a)(d.b)],
+//   A = -2 N / r^5, N = 3 erfc(x) + c r (3 + 2 x^2) e,  B = 2 xi^2 c e
+// (x = xi r, c = 2 xi/sqrt(pi), e = exp(-x^2)), with the radial derivatives
+//   A'/r = 8 c xi^4 e / r^2 + 10 N / r^7,  B'/r = -4 xi^4 c e.
+// The pair contributes Phi(d; g_t, f_j, q_j) - Phi(d; g_j, f_t, q_t) (T is odd),
+// so G = grad_d of that goes to x_t and -G to x_j:
+//   grad Phi = [(A'/r)(d.a)(d.b)(d.c) + (B'/r)((a.b)(d.c) + (b.c)(d.a) + (c.a)(d.b))] d
+//              + A [(d.b)(d.c) a + (d.a)(d.c) b + (d.a)(d.b) c] + B [(a.b) c + (b.c) a + (c.a) b].
+__device__ __forceinline__ void grad_phi_str(float dx, float dy, float dz, float Ar, float A, float Br, float B,
+                                             const float4 &a, const float4 &b, const float4 &c, float sgn,
+                                             float G[3]) {
+    const float da = dx * a.x + dy * a.y + dz * a.z, db = dx * b.x + dy * b.y + dz * b.z,
+                dc = dx * c.x + dy * c.y + dz * c.z;
+    const float ab = a.x * b.x + a.y * b.y + a.z * b.z, bc = b.x * c.x + b.y * c.y + b.z * c.z,
+                ca = c.x * a.x + c.y * a.y + c.z * a.z;
+    const float S = sgn * (Ar * da * db * dc + Br * (ab * dc + bc * da + ca * db));
+    const float pa = sgn * (A * db * dc + B * bc), pb = sgn * (A * da * dc + B * ca),
+                pc = sgn * (A * da * db + B * ab);
+    G[0] += S * dx + pa * a.x + pb * b.x + pc * c.x;
+    G[1] += S * dy + pa * a.y + pb * b.y + pc * c.y;
+    G[2] += S * dz + pa * a.z + pb * b.z + pc * c.z;
+}
+
+template <int PV>
+__device__ __forceinline__ void grad_pair_str(const RC<float> &rk, float dx, float dy, float dz, float r2,
+                                              const float4 &ft, const float4 &qt, const float4 &gt, const float4 &fj,
+                                              const float4 &qj, const float4 &gj, float G[3]) {
+    const float rinv = rsqrt_fast(r2), r = r2 * rinv, rinv2 = rinv * rinv;
+    const float x = rk.xi * r;
+    const float e = ex2_approx(rk.ce * r2);
+    const float Q = erfcx_poly<PV>(rcp_fast(2.0f + x));
+    const float N = e * fmaf(rk.c * r, fmaf(2.0f * x, x, 3.0f), 3.0f * Q);
+    const float rinv5 = rinv2 * rinv2 * rinv, x4c = rk.xi2 * rk.xi2 * rk.c;
+    const float A = -2.0f * N * rinv5;
+    const float Ar = 8.0f * x4c * e * rinv2 + 10.0f * N * rinv5 * rinv2;
+    const float B = 2.0f * rk.xi2 * rk.c * e;
+    const float Br = -4.0f * x4c * e;
+    G[0] = G[1] = G[2] = 0.0f;
+    grad_phi_str(dx, dy, dz, Ar, A, Br, B, gt, fj, qj, 1.0f, G);
+    grad_phi_str(dx, dy, dz, Ar, A, Br, B, gj, ft, qt, -1.0f, G);
 }
 
 // FP64 erfc(x) = e Q64(s), e = exp(-x^2), s = SA t + SB, t = 1/(2 + x): the
@@ -990,12 +1038,14 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
     k_real_symc(GP<float> g, RC<float> rk, const float4 *__restrict__ xs, const float4 *__restrict__ fs,
                 const float4 *__restrict__ qs, const int *__restrict__ cell_start, const int2 *__restrict__ clusters,
                 const int *__restrict__ ncl_total, const int *__restrict__ perm, float *__restrict__ u,
-                float *__restrict__ uj, int *__restrict__ status, float *__restrict__ rt) {
+                float *__restrict__ uj, int *__restrict__ status, float *__restrict__ rt,
+                const float4 *__restrict__ gs = nullptr) {
     constexpr int WPB = 8, TC = 8, QN = 64;
     constexpr bool STR = (KERNEL == SE_STRESSLET);
     static_assert(!(PER && STR), "periodic plans sum the stresslet with k_real_cmp");
-    static_assert(!(GRAD && (PER || STR)), "the gradient mode is for free-space stokeslet and rotlet plans");
-    constexpr bool HQ = STR || GRAD;  // a third vector per point: q, or g
+    static_assert(!(GRAD && PER), "the gradient mode is for free-space plans");
+    constexpr bool HQ = STR || GRAD;   // a third vector per point: q, or g
+    constexpr bool HG = STR && GRAD;   // and a fourth: the stresslet's gradient needs q and g
     constexpr int NSEG = PER ? 2 * MAXROWS : MAXROWS;  // entries of the segment list
     // PAIR: neighbouring targets 2p and 2p + 1 side by side (their cutoff
     // tests mostly agree); the components are x, f and, for the stresslet, q
@@ -1005,8 +1055,10 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
     // one warp's shared memory in one record, so that one base address serves
     // every access
     struct __align__(16) WarpSmem {
-        float4 tx[TC], tf[TC], tq[HQ ? TC : 1];
-        float4 qx[QN], qf[QN], qq[HQ ? QN : 1];  // the candidate queue
+        float4 tx[TC], tf[TC], tq[HQ ? TC : 1], tg[HG ? TC : 1];
+        // the candidate queue (the stresslet's gradient reads q and g of a
+        // candidate through its index instead, to stay within 48 KB per block)
+        float4 qx[QN], qf[QN], qq[HQ && !HG ? QN : 1];
         float tp[PAIR ? TC / 2 : 1][NTP][2];      // [pair p][component][slot]: 16-byte loads of two components
         int qm[QN];
         int2 seg[NSEG];
@@ -1031,11 +1083,12 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
     // their bounding box
     float blo[3] = {INF, INF, INF}, bhi[3] = {-INF, -INF, -INF};
     if (lane < TC) {
-        float4 xo = make_float4(INF, INF, INF, 0.f), fo = make_float4(0.f, 0.f, 0.f, 0.f), qo = fo;
+        float4 xo = make_float4(INF, INF, INF, 0.f), fo = make_float4(0.f, 0.f, 0.f, 0.f), qo = fo, go = fo;
         if (lane < cl.y) {
             xo = xs[cl.x + lane];
             fo = fs[cl.x + lane];
             if (HQ) qo = qs[cl.x + lane];
+            if (HG) go = gs[cl.x + lane];
             blo[0] = bhi[0] = xo.x;
             blo[1] = bhi[1] = xo.y;
             blo[2] = bhi[2] = xo.z;
@@ -1043,6 +1096,7 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
         tx[lane] = xo;
         tf[lane] = fo;
         if (HQ) tq[lane] = qo;
+        if (HG) W.tg[lane] = go;
         if (PAIR) {
             // empty slots far away but finite: a masked slot's products stay 0
             const int pp = lane >> 1, o = lane & 1;  // pair p = t / 2, slot t mod 2
@@ -1204,7 +1258,7 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
                 xm.w = __int_as_float(min(v, TC));  // the stream position, capped
                 qx[pos] = xm;
                 qf[pos] = fs[m];
-                if (HQ) qq[pos] = qs[m];
+                if (HQ && !HG) qq[pos] = qs[m];
                 qm[pos] = m;
             }
             fill += __popc(bal);
@@ -1220,12 +1274,16 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
             // the two never meet at distance zero
             const float far = PAIR ? -1e18f : INF;
             float4 xj = make_float4(far, far, far, 0.f);
-            float4 fj = make_float4(0.f, 0.f, 0.f, 0.f), qj = fj;
+            float4 fj = make_float4(0.f, 0.f, 0.f, 0.f), qj = fj, gj = fj;
             int vs = 0, mj = 0;
             if (valid) {
                 xj = qx[lane];
                 fj = qf[lane];
-                if (HQ) qj = qq[lane];
+                if (HQ && !HG) qj = qq[lane];
+                if (HG) {
+                    qj = qs[qm[lane]];
+                    gj = gs[qm[lane]];
+                }
                 vs = __float_as_int(xj.w);
                 mj = qm[lane];
             }
@@ -1325,7 +1383,10 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
                 if (r2 <= rk.rc2 && t < vs) {
                     if (GRAD && r2 > 0.f) {
                         float G[3];
-                        grad_pair<KERNEL, PV>(rk, dx, dy, dz, r2, tf[t], tq[t], fj, qj, G);
+                        if constexpr (HG)
+                            grad_pair_str<PV>(rk, dx, dy, dz, r2, tf[t], tq[t], W.tg[t], fj, qj, gj, G);
+                        else
+                            grad_pair<KERNEL, PV>(rk, dx, dy, dz, r2, tf[t], tq[t], fj, qj, G);
                         acc[t][0] += G[0];
                         acc[t][1] += G[1];
                         acc[t][2] += G[2];
@@ -1387,7 +1448,7 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
         if (lane < fill - nq) {
             qx[lane] = qx[nq + lane];
             qf[lane] = qf[nq + lane];
-            if (HQ) qq[lane] = qq[nq + lane];
+            if (HQ && !HG) qq[lane] = qq[nq + lane];
             qm[lane] = qm[nq + lane];
         }
         fill -= nq;
@@ -2055,7 +2116,8 @@ cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *
     k_sort_g<T><<<(N + 255) / 256, 256, 0, st>>>(N, p->b.perm_r, g_orig, gsort);
     p->launches++;
     if constexpr (sizeof(T) == 4) {
-        if (SE_RS_SYMC && SE_GRAD_SYM && p->kernel != SE_STRESSLET && !p->periodic && p->b.uj) {
+        if (SE_RS_SYMC && SE_GRAD_SYM && (p->kernel != SE_STRESSLET || SE_GRAD_SYM_STR) && !p->periodic &&
+            p->b.uj) {
             // each pair once over the clusters of 8 targets, the candidate's share through uj
             const int nrows = p->geom.ncel[1] * p->geom.ncel[2];
             k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], 8, p->b.cnt_r, p->b.ncl);
@@ -2070,7 +2132,18 @@ cudaError_t launch_real_grad(se_plan_s *p, cudaStream_t st, const T *g_orig, T *
                          *gf4 = (const float4 *)gsort;
             float *ujf = (float *)p->b.uj;
             const bool pv1 = real_pv(p->xi * p->rc) == 1;
-            if (p->kernel == SE_STOKESLET) {
+            if (p->kernel == SE_STRESSLET) {
+                // the targets and candidates carry f (fs), q (qs) and g (gs)
+                const float4 *qf4 = (const float4 *)p->b.qs_r;
+                if (pv1)
+                    k_real_symc<SE_STRESSLET, 1, false, true><<<nblk, 256, 0, st>>>(
+                        p->gpf, rk, xf, ff, qf4, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                        (float *)gx, ujf, p->b.status, nullptr, gf4);
+                else
+                    k_real_symc<SE_STRESSLET, 0, false, true><<<nblk, 256, 0, st>>>(
+                        p->gpf, rk, xf, ff, qf4, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
+                        (float *)gx, ujf, p->b.status, nullptr, gf4);
+            } else if (p->kernel == SE_STOKESLET) {
                 if (pv1)
                     k_real_symc<SE_STOKESLET, 1, false, true><<<nblk, 256, 0, st>>>(
                         p->gpf, rk, xf, ff, gf4, p->b.cnt_r, p->b.clusters, p->b.ncl + nrows, p->b.perm_r,
