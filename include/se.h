@@ -161,7 +161,9 @@ se_status_t se_eval_host(se_plan_t plan, const void *x_host, const void *f_host,
  *              kernel (the self term does not depend on x).
  * Same arrays as se_eval (q: the stresslet's q, else NULL); grad_u, grad_f,
  * grad_q, grad_x are N x 3 device arrays in the plan's precision, overwritten.
- * Any output may be NULL.  The forward grid is recomputed, not stored.
+ * Any output may be NULL.  The forward grid (needed by grad_x) is recomputed
+ * from x, f (, q), unless keep-grid is on (se_plan_set_keep_grid) and the
+ * plan's last se_eval or se_eval_targets was given the same x, f and q arrays.
  * se_eval_backward is se_eval_backward_q without grad_q.  grad_q must be NULL
  * for the stokeslet and the rotlet (SE_ERR_INVALID_ARG). */
 se_status_t se_eval_backward_q(se_plan_t plan, const void *x, const void *f, const void *q, const void *grad_u,
@@ -309,6 +311,20 @@ se_status_t se_plan_set_timing(se_plan_t plan, int on);
  * Returns SE_ERR_NOT_SUPPORTED when turning it on for a plan without it
  * (FP64 and periodic plans). */
 se_status_t se_plan_set_overlap(se_plan_t plan, int on);
+
+/* Keep-grid mode (off by default).  Every se_eval and se_eval_targets leaves
+ * the forward grid (the field on the grid after scaling and the inverse
+ * transforms, 3 or 9 components) in a plan buffer; with keep-grid on,
+ * se_eval_backward / se_eval_backward_q reuse it for grad_x instead of
+ * spreading and transforming again, when the x, f and q pointers equal those
+ * of the plan's last se_eval or se_eval_targets.  Only the pointers are
+ * compared: the caller promises that the arrays' contents did not change
+ * in between and that the backward is ordered after that evaluation (same
+ * stream, or an event); a failed evaluation, or a backward that recomputed the
+ * grid for other inputs, leaves the kept grid to those inputs.  The grid buffer
+ * exists in every plan, so the mode costs no memory.  Errors: SE_ERR_INVALID_ARG
+ * for a NULL plan. */
+se_status_t se_plan_set_keep_grid(se_plan_t plan, int on);
 
 /* Number of this library's kernels launched by the plan's last se_eval,
  * se_eval_host, se_eval_real_space or se_eval_backward call (cuFFT's kernels

@@ -117,10 +117,23 @@ se_status_t fourier_grid(se_plan_s *p, cudaStream_t st, void *wout, int nc, Stag
     return SE_OK;
 }
 
+// The forward grid in wgrid now belongs to the sources (x, f, q).
+void mark_grid(se_plan_s *p, const void *x, const void *f, const void *q) {
+    p->grid_valid = true;
+    p->grid_src[0] = x;
+    p->grid_src[1] = f;
+    p->grid_src[2] = q;
+}
+
+bool grid_kept_for(const se_plan_s *p, const void *x, const void *f, const void *q) {
+    return p->keep_grid && p->grid_valid && p->grid_src[0] == x && p->grid_src[1] == f && p->grid_src[2] == q;
+}
+
 template <typename T>
 se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaStream_t st) {
     p->last_stream = st;
     p->launches = 0;
+    p->grid_valid = false;
     if (p->overlap && !p->timing && p->s_four && real_can_defer(p)) {
         // the Fourier part (spread ... gather, which writes u) on the internal
         // high-priority stream, the real-space sum (into b.rt and b.uj) on st;
@@ -130,6 +143,7 @@ se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaS
         CK(cudaStreamWaitEvent(p->s_four, p->ev_fork, 0));
         se_status_t s = fourier_grid<T>(p, p->s_four, p->wgrid, p->nc, nullptr);
         if (s != SE_OK) return s;
+        mark_grid(p, x, f, q);
         CK(launch_gather<T>(p, p->s_four, p->wgrid, f, u));
         CK(cudaEventRecord(p->ev_join, p->s_four));
         CK(launch_real<T>(p, st, u, true));
@@ -143,6 +157,7 @@ se_status_t eval_t(se_plan_s *p, const T *x, const T *f, const T *q, T *u, cudaS
     tm.mark();
     se_status_t s = fourier_grid<T>(p, st, p->wgrid, p->nc, &tm);
     if (s != SE_OK) return s;
+    mark_grid(p, x, f, q);
     CK(launch_gather<T>(p, st, p->wgrid, f, u));
     tm.mark();
     CK(launch_real<T>(p, st, u));
@@ -242,9 +257,13 @@ se_status_t backward_t(se_plan_s *p, const T *x, const T *f, const T *q, const T
     }
     if (gx) CK(launch_bin<T>(p, x, f, q, st));
     tm.mark();
-    if (gx) {
+    if (gx && !grid_kept_for(p, x, f, q)) {
+        // the forward grid, recomputed (the grid of the plan's last evaluation
+        // is reused instead when keep-grid is on and the sources are the same)
+        p->grid_valid = false;
         s = fourier_grid<T>(p, st, p->wgrid, p->nc, nullptr);
         if (s != SE_OK) return s;
+        mark_grid(p, x, f, q);
     }
     tm.mark();
     if (gx) CK(launch_gather_grad<T>(p, st, p->wgrid, p->wgrid2, f, q, gu, gx));
@@ -321,8 +340,10 @@ se_status_t eval_targets_t(se_plan_s *p, const T *x, const T *f, const T *q, int
     p->launches = 0;
     CK(launch_bin<T>(p, x, f, q, st));
     CK(launch_bin_set<T>(p, p->bt, Nt, xt, nullptr, nullptr, st));
+    p->grid_valid = false;
     se_status_t s = fourier_grid<T>(p, st, p->wgrid, p->nc, nullptr);
     if (s != SE_OK) return s;
+    mark_grid(p, x, f, q);
     CK(launch_gather_targets<T>(p, st, p->bt, Nt, p->wgrid, ut));
     CK(launch_real_targets<T>(p, st, p->bt, Nt, ut));
     return SE_OK;

@@ -864,6 +864,12 @@ extern "C" se_status_t se_plan_set_overlap(se_plan_t p, int on) {
     return SE_OK;
 }
 
+extern "C" se_status_t se_plan_set_keep_grid(se_plan_t p, int on) {
+    if (!p) return fail(SE_ERR_INVALID_ARG, "NULL plan");
+    p->keep_grid = on != 0;
+    return SE_OK;
+}
+
 extern "C" int se_plan_stage_times(se_plan_t p, float *ms, int max_n) {
     if (!p || !ms) return 0;
     int n = std::min(max_n, p->n_stage);

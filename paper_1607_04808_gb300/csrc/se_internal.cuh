@@ -258,6 +258,11 @@ struct se_plan_s {
     float stage_ms[8] = {};
     int n_stage = 0;
     int64_t launches = 0;  // kernels of this library launched by the last evaluation call
+    // se_plan_set_keep_grid: the backward pass reuses the forward grid in wgrid
+    // when its sources are the arrays (device pointers) that produced it
+    bool keep_grid = false;
+    bool grid_valid = false;
+    const void *grid_src[3] = {nullptr, nullptr, nullptr};
     double precompute_ms = 0;
     bool precompute_cached = false;  // the precomputed kernel came from the cache
     // host staging for se_eval_host

@@ -71,3 +71,50 @@ def test_backward_stage_times():
     # timing changes nothing but the order of the FP32 atomics
     assert rel_l2(gf1.double().cpu().numpy(), gf0.double().cpu().numpy()) <= 1e-6
     assert rel_l2(gx1.double().cpu().numpy(), gx0.double().cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("kernel,prec", [("stokeslet", "fp32"), ("stresslet", "fp32"), ("rotlet", "fp32"),
+                                         ("stokeslet", "fp64"), ("stresslet", "fp64")])
+def test_keep_grid_reuses_forward_grid(kernel, prec):
+    """With keep-grid on, the backward after se_eval on the same arrays skips
+    the forward grid (fewer launches) and gives the gradients of a plan that
+    recomputes it; after an evaluation on other arrays it recomputes."""
+    import paper_1607_04808_gb300 as pkg
+    n = 20000
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    x, f = W.stokeslet_uniform(n, 83)
+    x = np.minimum(x.astype(np.float32), np.nextafter(np.float32(1), np.float32(0)))
+    g = W._rng(83, 5).standard_normal((n, 3))
+    q = W.unit_vectors(n, 83) if kernel == "stresslet" else None
+    t = lambda a: None if a is None else torch.tensor(a, dtype=dt, device="cuda")  # noqa: E731
+    tx, tf, tq, tg = t(x), t(f), t(q), t(g)
+    tf2 = t(-0.5 * f)
+    want_q = kernel == "stresslet"
+    ref = pkg.Plan(kernel, n, BOX, prec=prec, tol=2e-6 if prec == "fp32" else 1e-10)
+    prm = ref.params
+    plan = pkg.Plan(kernel, n, BOX, prec=prec, xi=prm["xi"], M=prm["M"], P=prm["P"], rc=prm["rc"])
+    plan.set_keep_grid(True)
+    ref.eval(tx, tf, tq)
+    out0 = ref.backward(tx, tf, tg, q=tq, want_q=want_q)
+    n_recompute = ref.launch_count()
+    plan.eval(tx, tf, tq)
+    out1 = plan.backward(tx, tf, tg, q=tq, want_q=want_q)
+    n_kept = plan.launch_count()
+    # a second backward on the same arrays still finds the grid
+    out2 = plan.backward(tx, tf, tg, q=tq, want_q=want_q)
+    assert plan.launch_count() == n_kept
+    # after an evaluation with other strengths the grid belongs to those
+    plan.eval(tx, tf2, tq)
+    out3 = plan.backward(tx, tf, tg, q=tq, want_q=want_q)
+    n_after = plan.launch_count()
+    plan.check()
+    ref.check()
+    plan.close()
+    ref.close()
+    assert n_kept < n_recompute and n_after == n_recompute, (n_kept, n_recompute, n_after)
+    tol = 1e-5 if prec == "fp32" else 1e-11  # FP32: the order of the spreading atomics
+    for o in (out1, out2, out3):
+        for a, b in zip(o, out0):
+            if b is None:
+                continue
+            assert rel_l2(a.double().cpu().numpy(), b.double().cpu().numpy()) <= tol
