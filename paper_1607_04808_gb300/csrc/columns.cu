@@ -1245,6 +1245,12 @@ cudaError_t with_p(int P, A... a) {
     }
 }
 
+// SE_SPREAD_SUB: single plans with P = 10 or 12 spread on sub-tiles of 4 x 4 x 8
+// window starts (k_spread_sub, subtile.cu); 0 keeps the 8^3-tile kernels
+#ifndef SE_SPREAD_SUB
+#define SE_SPREAD_SUB 1
+#endif
+
 // SE_SPREAD_PAIR: the paired-FMA spreading kernel (k_spread_c2); 0 keeps the
 // scalar register-column kernel (k_spread_col)
 #ifndef SE_SPREAD_PAIR
@@ -1420,9 +1426,13 @@ cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, con
                               void *grid, int nc) {
     // nc = 3: f; nc = 6: the symmetric stresslet source in two passes of three
     for (int c0 = 0; c0 < nc; c0 += 3) {
-        cudaError_t e = with_p<SpreadRun>(p->P, p->gpf, p->ntiles, c0, nc == 6, (const int *)p->b.cnt_t,
-                                          (const float4 *)xs, (const float4 *)fs, (const float4 *)qs,
-                                          (float *)grid, st);
+        cudaError_t e = (SE_SPREAD_SUB && sub_supported(p->P))
+                            ? launch_spread_sub(p->gpf, p->ntiles, c0, nc == 6, (const int *)p->b.cnt_t,
+                                                (const float4 *)xs, (const float4 *)fs, (const float4 *)qs,
+                                                (float *)grid, st)
+                            : with_p<SpreadRun>(p->P, p->gpf, p->ntiles, c0, nc == 6, (const int *)p->b.cnt_t,
+                                                (const float4 *)xs, (const float4 *)fs, (const float4 *)qs,
+                                                (float *)grid, st);
         if (e) return e;
         p->launches++;
     }

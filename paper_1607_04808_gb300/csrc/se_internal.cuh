@@ -346,6 +346,11 @@ cudaError_t launch_gather_adj_col(se_plan_s *p, cudaStream_t st, const float *V,
 // du/dx of the Fourier part on the shared-memory tiles (FP32 column plans)
 cudaError_t launch_gather_grad_col(se_plan_s *p, cudaStream_t st, const float *w_fwd, const float *w_adj,
                                    const float *f_orig, const float *q_orig, const float *g_orig, float *gx);
+// FP32 spreading on sub-tiles of 4 x 4 x 8 window starts (subtile.cu), P = 10 or 12;
+// the plan's tiles and binning are those of the column kernels
+bool sub_supported(int P);
+cudaError_t launch_spread_sub(const GP<float> &g, int ntiles, int c0, bool stress, const int *tile_start,
+                              const float4 *xs, const float4 *fs, const float4 *qs, float *grid, cudaStream_t st);
 cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const Buffers &b, cudaStream_t st);
 cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
