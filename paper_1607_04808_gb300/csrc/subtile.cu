@@ -5,21 +5,21 @@
 // sub-tiles of 4 x 4 window starts in (x, y), all 8 in z; one CTA takes one
 // sub-tile and filters the tile's points down to its own.  The supports of its
 // points cover a padded block of PT x PT columns, PT = 4 + P - 1 (15 at P =
-// 12), each PZ = 8 + P - 1 grid points long in z.  Thread (cx, cy) keeps column
-// (cx, cy) of the three source components in registers as z pairs and adds
-// every point whose support covers it with paired FP32 FMAs (two z values per
-// instruction).  A warp owns two rows of columns (32 / PT rows), so a point's
-// P x P support meets 6 or 7 of the 8 warps and covers P of the PT columns of
-// each of their rows: about 70 % of the lanes of the warps it meets do useful
-// work, against about 55 % with whole 8^3 tiles per CTA.
+// 12), each PZ = 8 + P - 1 grid points long in z.  Thread (cx, cy) keeps the
+// columns (cx, cy) and (cx, cy + 1) of the three source components in
+// registers as z pairs and adds every point whose support covers them with
+// paired FP32 FMAs (two z values per instruction); the point's z weights and
+// source, read once from shared memory, serve both columns.  A warp owns four
+// rows of columns (two groups of PT lanes), so a point's P x P support meets 3
+// or 4 of the 4 warps and covers P of the PT columns of each of their rows.
 //
-// Each batch of staged points is ordered by the key (oz, oy) of its window
-// start in the block (ranks within warps, counts combined over the batch), so a
-// warp runs, for each z offset oz in turn (a compile-time constant: register
-// indices must be constants), the contiguous run of points whose support
-// meets its rows: no per-point branch on oz and no per-point test.  The
-// columns go to the FFT input once per CTA with global atomics (sub-tiles
-// overlap in their halos).
+// Each batch of staged points is stored in the order of the key (oz, oy) of
+// its window start in the block (ranks within warps, counts combined over the
+// batch), so a warp runs, for each z offset oz in turn (a compile-time
+// constant: register indices must be constants), the contiguous run of
+// records whose support meets its rows: no per-point branch on oz and no
+// per-point test.  The columns go to the FFT input once per CTA through shared
+// memory with 16-byte vector atomics (sub-tiles overlap in their halos).
 #include "se_internal.cuh"
 
 namespace se {
@@ -35,21 +35,23 @@ struct SubCfg {
     static constexpr int PT = SUB + P - 1;         // columns per row and rows of the padded block
     static constexpr int PZ = TE + P - 1;          // grid points per column
     static constexpr int ZP = (PZ + 1) / 2;        // z pairs per column and component
-    static constexpr int RW = 32 / PT;             // rows of columns per warp
+    static constexpr int TR = 2;                   // rows of columns per thread (cy, cy + 1)
+    static constexpr int LR = 32 / PT;             // groups of PT lanes per warp
+    static constexpr int RW = LR * TR;             // rows of columns per warp
     static constexpr int NW = (PT + RW - 1) / RW;  // warps
     static constexpr int NT = 32 * NW;
-    static constexpr int WXY = 16;                 // x and y weights per record, a zero slot for idle lanes
+    static constexpr int WXY = 16;                 // x and y weights per record, zero slots for idle lanes
     static constexpr int WP = P / 2 + 1;           // staged z-weight pairs (odd offsets need P/2 + 1)
     static constexpr int WP4 = (WP + 1) / 2 * 2;   // in whole 16-byte rows
-    static constexpr int NB = NT / 64 * 32;        // points per staged batch (two staging threads each)
-    static constexpr int NCH = NB / 32;            // chunks of 32 points (one ranking warp each)
+    static constexpr int NB = NT;                  // points per staged batch (one staging thread each)
+    static constexpr int NCH = NB / 32;            // chunks of 32 points (one warp each)
     static constexpr int NKEY = TE * SUB;          // keys oz * SUB + oy
     static constexpr int CAP = 2048;               // tile points examined per round
     static constexpr int FX = 16;                  // x extent of the flush buffer (whole float4 of grid points)
-    static_assert(PT + 1 <= WXY && RW * NW <= WXY, "a weight for every column and row, idle slot included");
-    static_assert(2 * NB <= NT, "two staging threads per point");
+    static_assert(PT + 1 <= WXY && RW * NW <= WXY, "a weight for every column and row, idle slots included");
     static_assert(NKEY == 32, "one key per lane in the start table");
     static_assert(PT <= FX, "a row of the block in the flush buffer");
+    static_assert(NB <= 255, "record indices in one byte");
 };
 
 // One staged point: everything a column thread reads, in one record.
@@ -86,74 +88,62 @@ struct SubSmem {
 };
 
 // Stage the points list[b0 .. b0 + nb) of the round starting at tbeg (indices
-// into the sorted arrays: tbeg + list[i]) in key order.  Thread NB + j (whole
-// warps, chunks of 32 points) finds the key of point j and its place in the
-// batch's key order; then thread j writes the x and y weights and the source of
-// point j to that record, thread NB + j its z weights.
+// into the sorted arrays: tbeg + list[i]) in key order: thread j finds the key
+// of point j and its place in the batch's key order, then writes the point's
+// record there (its x, y and z weights and its source).  Called by every
+// thread of the CTA (it holds a CTA barrier).
 template <int P>
 __device__ __forceinline__ void sub_stage(SubStage<P> &S, const GP<float> &g, const float4 *__restrict__ xs,
                                           const float4 *__restrict__ fs, const float4 *__restrict__ qs, int fstride,
                                           int foff, int c0, bool stress, const unsigned short *list, int tbeg,
                                           int b0, int nb, int gx0, int gy0, int gz0) {
     using C = SubCfg<P>;
-    const int t = threadIdx.x;
-    if (t >= 2 * C::NB) return;
-    const bool zt = t >= C::NB;
-    const int j = zt ? t - C::NB : t;
+    const int j = threadIdx.x, lane = j & 31, ch = j >> 5;
     const bool valid = j < nb;
     int n = 0, i0[3] = {0, 0, 0};
     float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+    int key = C::NKEY;  // past every key: an empty slot of the last batch
+    int oz = 0;
     if (valid) {
         n = tbeg + list[b0 + j];
         xv = xs[n];
         unpack3(get_tag(xv), i0[0], i0[1], i0[2]);
+        oz = min(max(i0[2] - gz0, 0), C::TE - 1);
+        key = oz * SUB + min(max(i0[1] - gy0, 0), SUB - 1);
     }
-    int oz = 0;
-    if (zt) {
-        const int lane = j & 31, ch = j >> 5;
-        int key = C::NKEY;  // past every key: an empty slot of the last batch
-        if (valid) {
-            oz = min(max(i0[2] - gz0, 0), C::TE - 1);
-            key = oz * SUB + min(max(i0[1] - gy0, 0), SUB - 1);
-        }
-        // the chunk's points with the same key, and this point's rank among them
-        const unsigned same = __match_any_sync(FULLM, key);
-        const int within = __popc(same & ((1u << lane) - 1u));
-        // the chunk's count of every key (lane k: key k), for the batch-wide order
-        const int kcount = (valid && within == 0) ? __popc(same) : 0;
-        S.cnt[ch][lane] = 0;
-        __syncwarp();
-        if (kcount) S.cnt[ch][key] = (unsigned char)kcount;
-        // the ranking warps only: every chunk's counts are in place
-        asm volatile("bar.sync 1, %0;" ::"r"(C::NB) : "memory");
-        int tot = 0, pre = 0;
+    // the chunk's points with the same key, this point's rank among them, and
+    // the chunk's count of every key
+    const unsigned same = __match_any_sync(FULLM, key);
+    const int within = __popc(same & ((1u << lane) - 1u));
+    const int kcount = (valid && within == 0) ? __popc(same) : 0;
+    S.cnt[ch][lane] = 0;
+    __syncwarp();
+    if (kcount) S.cnt[ch][key] = (unsigned char)kcount;
+    __syncthreads();
+    int tot = 0, pre = 0;
 #pragma unroll
-        for (int c = 0; c < C::NCH; c++) {
-            const int v = S.cnt[c][lane];
-            tot += v;
-            pre += (c < ch) ? v : 0;
-        }
-        // exclusive scan of the totals over the keys: start of key `lane`
-        int incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(FULLM, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int kstart = incl - tot;
-        if (ch == 0) {
-            S.kst[lane] = (unsigned char)kstart;
-            if (lane == 31) S.kst[C::NKEY] = (unsigned char)incl;
-        }
-        const int base = __shfl_sync(FULLM, kstart + pre, key & 31);
-        if (valid) S.slot[j] = (unsigned char)(base + within);
+    for (int c = 0; c < C::NCH; c++) {
+        const int v = S.cnt[c][lane];
+        tot += v;
+        pre += (c < ch) ? v : 0;
     }
-    // all staging threads: every point's record is known
-    asm volatile("bar.sync 2, %0;" ::"r"(2 * C::NB) : "memory");
+    // exclusive scan of the totals over the keys: start of key `lane`
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULLM, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int kstart = incl - tot;
+    if (ch == 0) {
+        S.kst[lane] = (unsigned char)kstart;
+        if (lane == 31) S.kst[C::NKEY] = (unsigned char)incl;
+    }
+    const int slot = __shfl_sync(FULLM, kstart + pre, key & 31) + within;
     if (!valid) return;
-    SubRec<P> &R = S.rec[S.slot[j]];
-    if (zt) {
-        // the P weights at slots (oz & 1) .. (oz & 1) + P - 1, zeros elsewhere
+    SubRec<P> &R = S.rec[slot];
+    {
+        // the P z weights at slots (oz & 1) .. (oz & 1) + P - 1, zeros elsewhere
         const float fr = ((xv.z - g.x0[2]) * g.inv_h + g.half_ext) - (float)i0[2];
         float *w = reinterpret_cast<float *>(R.wz);
         const int sh = oz & 1;
@@ -163,84 +153,83 @@ __device__ __forceinline__ void sub_stage(SubStage<P> &S, const GP<float> &g, co
             const float tt = fr - (float)kk;
             w[i] = (kk >= 0 && kk < P) ? __expf(-g.ah2 * tt * tt) : 0.0f;
         }
-    } else {
-        // weights of every column and row of the block: zero off the point's support
-#pragma unroll
-        for (int d = 0; d < 2; d++) {
-            const float xd = d == 0 ? xv.x : xv.y;
-            const float x0 = d == 0 ? g.x0[0] : g.x0[1];
-            const int id = d == 0 ? i0[0] : i0[1];
-            const int o = min(max(id - (d == 0 ? gx0 : gy0), 0), SUB - 1);
-            const float fr = ((xd - x0) * g.inv_h + g.half_ext) - (float)id;
-            float *w = d == 0 ? R.wx : R.wy;
-#pragma unroll
-            for (int c = 0; c < C::WXY; c++) {
-                const int kk = c - o;
-                const float tt = fr - (float)kk;
-                w[c] = (kk >= 0 && kk < P) ? __expf(-g.ah2 * tt * tt) : 0.0f;
-            }
-        }
-        const float4 fv = fs[(size_t)n * fstride + foff];
-        float4 sv = fv;
-        if (stress) {
-            // components c0 .. c0 + 2 of the symmetric source (xx, yy, zz, xy, xz, yz)
-            const float4 qv = qs[n];
-            if (c0 == 0)
-                sv = make_float4(fv.x * qv.x, fv.y * qv.y, fv.z * qv.z, 0.0f);
-            else
-                sv = make_float4(0.5f * (fv.x * qv.y + fv.y * qv.x), 0.5f * (fv.x * qv.z + fv.z * qv.x),
-                                 0.5f * (fv.y * qv.z + fv.z * qv.y), 0.0f);
-        }
-        R.sxy = make_float4(sv.x, sv.x, sv.y, sv.y);
-        R.sz = make_float2(sv.z, sv.z);
     }
+    // weights of every column and row of the block: zero off the point's support
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        const float xd = d == 0 ? xv.x : xv.y;
+        const float x0 = d == 0 ? g.x0[0] : g.x0[1];
+        const int id = d == 0 ? i0[0] : i0[1];
+        const int o = min(max(id - (d == 0 ? gx0 : gy0), 0), SUB - 1);
+        const float fr = ((xd - x0) * g.inv_h + g.half_ext) - (float)id;
+        float *w = d == 0 ? R.wx : R.wy;
+#pragma unroll
+        for (int c = 0; c < C::WXY; c++) {
+            const int kk = c - o;
+            const float tt = fr - (float)kk;
+            w[c] = (kk >= 0 && kk < P) ? __expf(-g.ah2 * tt * tt) : 0.0f;
+        }
+    }
+    const float4 fv = fs[(size_t)n * fstride + foff];
+    float4 sv = fv;
+    if (stress) {
+        // components c0 .. c0 + 2 of the symmetric source (xx, yy, zz, xy, xz, yz)
+        const float4 qv = qs[n];
+        if (c0 == 0)
+            sv = make_float4(fv.x * qv.x, fv.y * qv.y, fv.z * qv.z, 0.0f);
+        else
+            sv = make_float4(0.5f * (fv.x * qv.y + fv.y * qv.x), 0.5f * (fv.x * qv.z + fv.z * qv.x),
+                             0.5f * (fv.y * qv.z + fv.z * qv.y), 0.0f);
+    }
+    R.sxy = make_float4(sv.x, sv.x, sv.y, sv.y);
+    R.sz = make_float2(sv.z, sv.z);
 }
 
-// SE_SUB_UNROLL: unroll factor of the loop over a run of points (0: the compiler's choice)
-#ifndef SE_SUB_UNROLL
-#define SE_SUB_UNROLL 0
-#endif
-constexpr int kSubUnroll = SE_SUB_UNROLL > 0 ? SE_SUB_UNROLL : 1;
+// Accumulators of a thread: rows r = 0, 1 (columns (cx, cy + r)), components
+// c, z pairs q
+template <int P>
+using SubAcc = float2[SubCfg<P>::TR][3][SubCfg<P>::ZP];
 
-// a_c[OZ/2 + k] += s_c wz[k] for the point's z pairs (P/2, or P/2 + 1 for odd OZ)
+// a[r][c][OZ/2 + k] += w_r s_c wz[k] for the point's z pairs (P/2, or P/2 + 1
+// for odd OZ), w_r = wx[cx] wy[cy + r]
 template <int P, int OZ>
-__device__ __forceinline__ void sub_point(const SubRec<P> &R, int cx, int cy, float2 (&a0)[SubCfg<P>::ZP],
-                                          float2 (&a1)[SubCfg<P>::ZP], float2 (&a2)[SubCfg<P>::ZP]) {
+__device__ __forceinline__ void sub_point(const SubRec<P> &R, int cx, int cy, SubAcc<P> &a) {
     constexpr int Q0 = OZ / 2, NP = P / 2 + (OZ & 1);
     static_assert(Q0 + NP <= SubCfg<P>::ZP, "the point's z support stays inside the column");
-    const float w = R.wx[cx] * R.wy[cy];
-    const float2 ww = make_float2(w, w);
+    const float wxv = R.wx[cx];
+    const float2 wyv = *reinterpret_cast<const float2 *>(&R.wy[cy]);
     const float4 sv = R.sxy;
-    const float2 s0 = __fmul2_rn(ww, make_float2(sv.x, sv.y));
-    const float2 s1 = __fmul2_rn(ww, make_float2(sv.z, sv.w));
-    const float2 s2 = __fmul2_rn(ww, R.sz);
+    const float2 sz = R.sz;
+    float2 s[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const float w = wxv * (r ? wyv.y : wyv.x);
+        const float2 ww = make_float2(w, w);
+        s[r][0] = __fmul2_rn(ww, make_float2(sv.x, sv.y));
+        s[r][1] = __fmul2_rn(ww, make_float2(sv.z, sv.w));
+        s[r][2] = __fmul2_rn(ww, sz);
+    }
 #pragma unroll
     for (int k2 = 0; k2 < (NP + 1) / 2; k2++) {
         const float4 v = R.wz[k2];
         const float2 lo = make_float2(v.x, v.y), hi = make_float2(v.z, v.w);
-        a0[Q0 + 2 * k2] = __ffma2_rn(lo, s0, a0[Q0 + 2 * k2]);
-        a1[Q0 + 2 * k2] = __ffma2_rn(lo, s1, a1[Q0 + 2 * k2]);
-        a2[Q0 + 2 * k2] = __ffma2_rn(lo, s2, a2[Q0 + 2 * k2]);
-        if (2 * k2 + 1 < NP) {
-            a0[Q0 + 2 * k2 + 1] = __ffma2_rn(hi, s0, a0[Q0 + 2 * k2 + 1]);
-            a1[Q0 + 2 * k2 + 1] = __ffma2_rn(hi, s1, a1[Q0 + 2 * k2 + 1]);
-            a2[Q0 + 2 * k2 + 1] = __ffma2_rn(hi, s2, a2[Q0 + 2 * k2 + 1]);
-        }
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                a[r][c][Q0 + 2 * k2] = __ffma2_rn(lo, s[r][c], a[r][c][Q0 + 2 * k2]);
+                if (2 * k2 + 1 < NP) a[r][c][Q0 + 2 * k2 + 1] = __ffma2_rn(hi, s[r][c], a[r][c][Q0 + 2 * k2 + 1]);
+            }
     }
 }
 
-// The batch's points with z offset OZ, OZ + 1, ... whose oy lies in [ylo, yhi].
+// The batch's records with z offset OZ, OZ + 1, ... whose oy lies in [ylo, yhi].
 template <int P, int OZ>
-__device__ __forceinline__ void sub_runs(const SubStage<P> &S, int ylo, int yhi, int cx, int cy,
-                                         float2 (&a0)[SubCfg<P>::ZP], float2 (&a1)[SubCfg<P>::ZP],
-                                         float2 (&a2)[SubCfg<P>::ZP]) {
+__device__ __forceinline__ void sub_runs(const SubStage<P> &S, int ylo, int yhi, int cx, int cy, SubAcc<P> &a) {
     if constexpr (OZ < SubCfg<P>::TE) {
         const int i0 = S.kst[OZ * SUB + ylo], i1 = S.kst[OZ * SUB + yhi + 1];
-#if SE_SUB_UNROLL
-#pragma unroll kSubUnroll
-#endif
-        for (int i = i0; i < i1; i++) sub_point<P, OZ>(S.rec[i], cx, cy, a0, a1, a2);
-        sub_runs<P, OZ + 1>(S, ylo, yhi, cx, cy, a0, a1, a2);
+        for (int i = i0; i < i1; i++) sub_point<P, OZ>(S.rec[i], cx, cy, a);
+        sub_runs<P, OZ + 1>(S, ylo, yhi, cx, cy, a);
     }
 }
 
@@ -271,17 +260,22 @@ __global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
     const int sx = sub & 1, sy = sub >> 1;
     const int gx0 = tx * TE + SUB * sx, gy0 = ty * TE + SUB * sy, gz0 = tz * TE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // the thread's column; idle lanes read the zero x weight of slot PT
-    const int rw = lane / C::PT;
-    const int cyw = warp * C::RW + rw;
-    const bool own = rw < C::RW && cyw < C::PT;
-    const int cx = own ? lane - rw * C::PT : C::PT, cy = own ? cyw : 0;
+    // the thread's columns (cx, cy) and (cx, cy + 1); idle lanes read the zero
+    // x weight of slot PT (a row cy + 1 = PT reads the zero y weight there)
+    const int lr = lane / C::PT;
+    const int cyw = warp * C::RW + lr * C::TR;
+    const bool own = lr < C::LR && cyw < C::PT;
+    const int cx = own ? lane - lr * C::PT : C::PT, cy = own ? cyw : 0;
     // the window-start rows oy whose support meets the warp's rows
     const int r0 = warp * C::RW, r1 = min(r0 + C::RW, C::PT) - 1;
     const int ylo = max(0, r0 - (P - 1)), yhi = min(SUB - 1, r1);
-    float2 a0[ZP], a1[ZP], a2[ZP];
+    SubAcc<P> a;
 #pragma unroll
-    for (int q = 0; q < ZP; q++) a0[q] = a1[q] = a2[q] = make_float2(0.0f, 0.0f);
+    for (int r = 0; r < C::TR; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int q = 0; q < ZP; q++) a[r][c][q] = make_float2(0.0f, 0.0f);
     const int *tags = reinterpret_cast<const int *>(xs);
     for (int rb = beg; rb < end; rb += C::CAP) {
         // the round's points of this sub-tile (tile points rb .. rb + rn)
@@ -305,7 +299,7 @@ __global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
                 if (b0 + C::NB < cnt)
                     sub_stage<P>(S[k ^ 1], g, xs, fs, qs, fstride, foff, c0, stress, list, rb, b0 + C::NB,
                                  min(C::NB, cnt - b0 - C::NB), gx0, gy0, gz0);
-                sub_runs<P, 0>(S[k], ylo, yhi, cx, cy, a0, a1, a2);
+                sub_runs<P, 0>(S[k], ylo, yhi, cx, cy, a);
                 __syncthreads();
             }
         } else {
@@ -317,15 +311,15 @@ __global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
     // allow it; grid points beyond the grid's Mtilde are zero and skipped
     if (own) {
 #pragma unroll
-        for (int q = 0; q < ZP; q++) {
+        for (int r = 0; r < C::TR; r++) {
+            if (cy + r < C::PT) {
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int z = 2 * q + h;
-                if (z < C::PZ) {
-                    sm.F[0][z][cy][cx] = h ? a0[q].y : a0[q].x;
-                    sm.F[1][z][cy][cx] = h ? a1[q].y : a1[q].x;
-                    sm.F[2][z][cy][cx] = h ? a2[q].y : a2[q].x;
-                }
+                for (int c = 0; c < 3; c++)
+#pragma unroll
+                    for (int q = 0; q < ZP; q++) {
+                        sm.F[c][2 * q][cy + r][cx] = a[r][c][q].x;
+                        if (2 * q + 1 < C::PZ) sm.F[c][2 * q + 1][cy + r][cx] = a[r][c][q].y;
+                    }
             }
         }
     }
@@ -338,22 +332,31 @@ __global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
     __syncthreads();
     float *gbase = grid + (size_t)c0 * gcs;
     const bool vec = ((g.mf[0] | gzs | gcs) & 3) == 0 && (reinterpret_cast<size_t>(gbase) & 15) == 0;
-    constexpr int NQ = C::FX / 4, NCHUNK = 3 * C::PZ * C::PT * NQ;
-    for (int i = tid; i < NCHUNK; i += C::NT) {
-        const int xq = i % NQ, r = i / NQ;
-        const int y = r % C::PT, zc = r / C::PT, z = zc % C::PZ, c = zc / C::PZ;
-        const int gx = gx0 + 4 * xq, gy = gy0 + y, gz = gz0 + z;
-        if (gx >= g.mt[0] || gy >= g.mt[1] || gz >= g.mt[2]) continue;
-        const float4 v = *reinterpret_cast<const float4 *>(&sm.F[c][z][y][4 * xq]);
-        if (v.x == 0.0f && v.y == 0.0f && v.z == 0.0f && v.w == 0.0f) continue;
-        float *dst = gbase + (size_t)c * gcs + (size_t)gz * gzs + (size_t)gy * g.mf[0] + gx;
-        if (vec && gx + 3 < g.mt[0]) {
-            atomicAdd(reinterpret_cast<float4 *>(dst), v);
-        } else {
-            if (v.x != 0.0f) atomicAdd(dst, v.x);
-            if (v.y != 0.0f && gx + 1 < g.mt[0]) atomicAdd(dst + 1, v.y);
-            if (v.z != 0.0f && gx + 2 < g.mt[0]) atomicAdd(dst + 2, v.z);
-            if (v.w != 0.0f && gx + 3 < g.mt[0]) atomicAdd(dst + 3, v.w);
+    // thread -> (plane parity, row y, float4 xq) of the (component, z) planes,
+    // two planes per pass
+    constexpr int NQ = C::FX / 4, PER = C::PT * NQ, NPL = 3 * C::PZ;
+    static_assert(2 * PER <= C::NT, "two planes of float4 per pass");
+    if (tid < 2 * PER) {
+        const int par = tid / PER, yq = tid - par * PER, y = yq / NQ, xq = yq - y * NQ;
+        const int gx = gx0 + 4 * xq, gy = gy0 + y;
+        if (gx < g.mt[0] && gy < g.mt[1]) {
+            const bool v4 = vec && gx + 3 < g.mt[0];
+            const float *src = &sm.F[0][0][y][4 * xq];
+            for (int pl = par; pl < NPL; pl += 2) {
+                const int c = pl / C::PZ, z = pl - c * C::PZ;
+                if (gz0 + z >= g.mt[2]) continue;
+                const float4 v = *reinterpret_cast<const float4 *>(src + (size_t)pl * C::PT * C::FX);
+                if (v.x == 0.0f && v.y == 0.0f && v.z == 0.0f && v.w == 0.0f) continue;
+                float *dst = gbase + (size_t)c * gcs + (size_t)(gz0 + z) * gzs + (size_t)gy * g.mf[0] + gx;
+                if (v4) {
+                    atomicAdd(reinterpret_cast<float4 *>(dst), v);
+                } else {
+                    if (v.x != 0.0f) atomicAdd(dst, v.x);
+                    if (v.y != 0.0f && gx + 1 < g.mt[0]) atomicAdd(dst + 1, v.y);
+                    if (v.z != 0.0f && gx + 2 < g.mt[0]) atomicAdd(dst + 2, v.z);
+                    if (v.w != 0.0f && gx + 3 < g.mt[0]) atomicAdd(dst + 3, v.w);
+                }
+            }
         }
     }
 }
