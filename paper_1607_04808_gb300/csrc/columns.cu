@@ -1245,8 +1245,9 @@ cudaError_t with_p(int P, A... a) {
     }
 }
 
-// SE_SPREAD_SUB: single plans with P = 10 or 12 spread on sub-tiles of 4 x 4 x 8
-// window starts (k_spread_sub, subtile.cu); 0 keeps the 8^3-tile kernels
+// SE_SPREAD_SUB: plans and batches with P = 10 or 12 spread on sub-tiles of 4 x 4
+// x 8 window starts (k_spread_sub, k_bspread_sub in subtile.cu); 0 keeps the
+// 8^3-tile kernels
 #ifndef SE_SPREAD_SUB
 #define SE_SPREAD_SUB 1
 #endif
@@ -1492,6 +1493,9 @@ cudaError_t launch_gather_grad_col(se_plan_s *p, cudaStream_t st, const float *w
 
 cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const Buffers &b, cudaStream_t st) {
+    if (SE_SPREAD_SUB && sub_supported(P))
+        return launch_bspread_sub(sys, items, nitems, P, n_rhs, (const int *)b.cnt_t, (const float4 *)b.xs_t,
+                                  (const float4 *)b.fs_t, st);
     return with_p<BSpreadRun>(P, sys, items, nitems, (const int *)b.cnt_t, n_rhs, (const float4 *)b.xs_t,
                               (const float4 *)b.fs_t, st);
 }

@@ -351,6 +351,8 @@ cudaError_t launch_gather_grad_col(se_plan_s *p, cudaStream_t st, const float *w
 bool sub_supported(int P);
 cudaError_t launch_spread_sub(const GP<float> &g, int ntiles, int c0, bool stress, const int *tile_start,
                               const float4 *xs, const float4 *fs, const float4 *qs, float *grid, cudaStream_t st);
+cudaError_t launch_bspread_sub(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
+                               const int *tile_start, const float4 *xs, const float4 *fs, cudaStream_t st);
 cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const Buffers &b, cudaStream_t st);
 cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,

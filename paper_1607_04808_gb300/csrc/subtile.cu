@@ -233,29 +233,21 @@ __device__ __forceinline__ void sub_runs(const SubStage<P> &S, int ylo, int yhi,
     }
 }
 
-// SE_SUB_MINB: CTAs per SM the sub-tile spreading kernel is compiled for
-#ifndef SE_SUB_MINB
-#define SE_SUB_MINB 3
-#endif
-
-// One CTA per (tile, sub-tile): block b takes sub-tile b mod 4 (x half, y
-// half) of tile b / 4.  grid: the first of the three component grids (z-plane
+// Spread the points [beg, end) of tile `tile` that lie in sub-tile `sub` (x
+// half sub & 1, y half sub >> 1) onto the three grids at grid + c0 gcs (z-plane
 // stride gzs, component stride gcs); the sources are fs[n * fstride + foff].
+// Called by every thread of the CTA.
 template <int P>
-__global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
-    k_spread_sub(GP<float> g, int c0, bool stress, const int *__restrict__ tile_start,
-                 const float4 *__restrict__ xs, const float4 *__restrict__ fs, const float4 *__restrict__ qs,
-                 int fstride, int foff, float *__restrict__ grid, size_t gzs, size_t gcs) {
+__device__ __forceinline__ void spread_sub_body(const GP<float> &g, int tile, int sub, int beg, int end, int c0,
+                                                bool stress, const float4 *__restrict__ xs,
+                                                const float4 *__restrict__ fs, const float4 *__restrict__ qs,
+                                                int fstride, int foff, float *__restrict__ grid, size_t gzs,
+                                                size_t gcs, SubSmem<P> &sm) {
     using C = SubCfg<P>;
     constexpr int ZP = C::ZP, TE = C::TE;
-    extern __shared__ __align__(16) unsigned char sub_smem_raw[];
-    SubSmem<P> &sm = *reinterpret_cast<SubSmem<P> *>(sub_smem_raw);
     SubStage<P> *S = sm.S;
     unsigned short *list = sm.list;
     int &s_cnt = sm.cnt;
-    const int tile = blockIdx.x >> 2, sub = blockIdx.x & 3;
-    const int beg = tile_start[tile], end = tile_start[tile + 1];
-    if (beg == end) return;
     const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int sx = sub & 1, sy = sub >> 1;
     const int gx0 = tx * TE + SUB * sx, gy0 = ty * TE + SUB * sy, gz0 = tz * TE;
@@ -361,15 +353,65 @@ __global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
     }
 }
 
+// SE_SUB_MINB: CTAs per SM the sub-tile spreading kernels are compiled for
+#ifndef SE_SUB_MINB
+#define SE_SUB_MINB 3
+#endif
+
+// One CTA per (tile, sub-tile): block b takes sub-tile b mod 4 of tile b / 4.
+template <int P>
+__global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
+    k_spread_sub(GP<float> g, int c0, bool stress, const int *__restrict__ tile_start,
+                 const float4 *__restrict__ xs, const float4 *__restrict__ fs, const float4 *__restrict__ qs,
+                 float *__restrict__ grid, size_t gzs, size_t gcs) {
+    extern __shared__ __align__(16) unsigned char sub_smem_raw[];
+    const int tile = blockIdx.x >> 2;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    spread_sub_body<P>(g, tile, blockIdx.x & 3, beg, end, c0, stress, xs, fs, qs, 1, 0, grid, gzs, gcs,
+                       *reinterpret_cast<SubSmem<P> *>(sub_smem_raw));
+}
+
+// Batches: one CTA per (system, tile, sub-tile) with the right-hand sides
+// inside: block b takes sub-tile b mod 4 of item (b / 4) n_rhs of the (system,
+// tile, rhs) list (right-hand side innermost) and spreads each right-hand side
+// r onto its three grids (the system's grid + 3 r gcs).
+template <int P>
+__global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
+    k_bspread_sub(const BSys<float> *__restrict__ sys, const int4 *__restrict__ items,
+                  const int *__restrict__ tile_start, int n_rhs, const float4 *__restrict__ xs,
+                  const float4 *__restrict__ fs) {
+    extern __shared__ __align__(16) unsigned char sub_smem_raw[];
+    const int4 it = items[(size_t)(blockIdx.x >> 2) * n_rhs];
+    const BSys<float> &B = sys[it.x];
+    const int key = B.tile_base + it.y;
+    const int beg = tile_start[key], end = tile_start[key + 1];
+    if (beg == end) return;
+    const GP<float> g = B.g;
+    for (int r = 0; r < n_rhs; r++)
+        spread_sub_body<P>(g, it.y, blockIdx.x & 3, beg, end, 0, false, xs, fs, nullptr, n_rhs, r,
+                           B.grid + (size_t)r * 3 * B.gcs, B.gzs, B.gcs,
+                           *reinterpret_cast<SubSmem<P> *>(sub_smem_raw));
+}
+
 template <int P>
 cudaError_t run_spread_sub(const GP<float> &g, int ntiles, int c0, bool stress, const int *ts, const float4 *xs,
-                           const float4 *fs, const float4 *qs, int fstride, int foff, float *grid, size_t gzs,
-                           size_t gcs, cudaStream_t st) {
+                           const float4 *fs, const float4 *qs, float *grid, cudaStream_t st) {
     constexpr size_t smem = sizeof(SubSmem<P>);
     cudaError_t e = cudaFuncSetAttribute(k_spread_sub<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
-    k_spread_sub<P><<<4 * ntiles, SubCfg<P>::NT, smem, st>>>(g, c0, stress, ts, xs, fs, qs, fstride, foff, grid,
-                                                             gzs, gcs);
+    const size_t gzs = (size_t)g.mf[0] * g.mf[1], gcs = gzs * g.mf[2];
+    k_spread_sub<P><<<4 * ntiles, SubCfg<P>::NT, smem, st>>>(g, c0, stress, ts, xs, fs, qs, grid, gzs, gcs);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t run_bspread_sub(const BSys<float> *sys, const int4 *items, int nitems, const int *ts, int n_rhs,
+                            const float4 *xs, const float4 *fs, cudaStream_t st) {
+    constexpr size_t smem = sizeof(SubSmem<P>);
+    cudaError_t e = cudaFuncSetAttribute(k_bspread_sub<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    k_bspread_sub<P><<<4 * (nitems / n_rhs), SubCfg<P>::NT, smem, st>>>(sys, items, ts, n_rhs, xs, fs);
     return cudaGetLastError();
 }
 
@@ -379,9 +421,15 @@ bool sub_supported(int P) { return P == 10 || P == 12; }
 
 cudaError_t launch_spread_sub(const GP<float> &g, int ntiles, int c0, bool stress, const int *tile_start,
                               const float4 *xs, const float4 *fs, const float4 *qs, float *grid, cudaStream_t st) {
-    const size_t gzs = (size_t)g.mf[0] * g.mf[1], gcs = gzs * g.mf[2];
-    if (g.P == 12) return run_spread_sub<12>(g, ntiles, c0, stress, tile_start, xs, fs, qs, 1, 0, grid, gzs, gcs, st);
-    if (g.P == 10) return run_spread_sub<10>(g, ntiles, c0, stress, tile_start, xs, fs, qs, 1, 0, grid, gzs, gcs, st);
+    if (g.P == 12) return run_spread_sub<12>(g, ntiles, c0, stress, tile_start, xs, fs, qs, grid, st);
+    if (g.P == 10) return run_spread_sub<10>(g, ntiles, c0, stress, tile_start, xs, fs, qs, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bspread_sub(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
+                               const int *tile_start, const float4 *xs, const float4 *fs, cudaStream_t st) {
+    if (P == 12) return run_bspread_sub<12>(sys, items, nitems, tile_start, n_rhs, xs, fs, st);
+    if (P == 10) return run_bspread_sub<10>(sys, items, nitems, tile_start, n_rhs, xs, fs, st);
     return cudaErrorInvalidValue;
 }
 
