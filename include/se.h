@@ -277,8 +277,9 @@ se_status_t se_plan_get_params(se_plan_t plan, se_params_t *out);
 se_status_t se_plan_get_grid(se_plan_t plan, int M[3], int Mtilde[3], int Mf[3], int Mg[3]);
 
 /* Synchronise the stream of the plan's last call and return (and clear) the
- * device-side status: SE_OK, SE_ERR_TIMEOUT (a bounded device wait ran out),
- * SE_ERR_OUT_OF_BOX or SE_ERR_COINCIDENT. */
+ * device-side status: SE_OK, SE_ERR_TIMEOUT (a bounded device wait ran out;
+ * the outputs of that call are undefined and must be discarded, the plan stays
+ * usable), SE_ERR_OUT_OF_BOX or SE_ERR_COINCIDENT. */
 se_status_t se_plan_check(se_plan_t plan);
 
 /* Test flags of a plan (0 restores normal operation).  SE_TEST_SKIP_TILE_COPY:

@@ -682,7 +682,10 @@ __device__ __forceinline__ bool stage_block(float *sg, uint64_t *bar_mem, const 
         }
         if (!mbar_wait(bar, 0, GS_WAIT_NS)) {
             // the copy did not land: report, give a copy in flight one more
-            // bounded wait, leave
+            // bounded wait, leave.  A copy still in flight after that may land
+            // in shared memory another CTA has taken over, so the results of
+            // an evaluation that reports the timeout are undefined (the host
+            // sees SE_ERR_TIMEOUT and discards them)
             if (threadIdx.x == 0) atomicOr(status, FLAG_TIMEOUT);
             if (!skip_copy) mbar_wait(bar, 0, GS_WAIT_NS);
             return false;
