@@ -1282,6 +1282,12 @@ struct SpreadRun {
 #define SE_GATHER_SMEM 1
 #endif
 
+// SE_GATHER_SUB: plans with P = 10 or 12 gather on sub-tiles with register
+// columns (k_gather_sub, subtile.cu); 0 keeps the tensor-copy tile gather
+#ifndef SE_GATHER_SUB
+#define SE_GATHER_SUB 1
+#endif
+
 #ifndef SE_GATHER_TMA
 #define SE_GATHER_TMA 1
 #endif
@@ -1450,6 +1456,14 @@ cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, 
 
 cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &b, const void *wgrid,
                                   const float *f_orig, double self_coef, float *u) {
+    // the sub-tile gather (P = 10, 12); the tiles of the failure-path test
+    // flag are those of the tensor-copy gather
+    if (SE_GATHER_SUB && sub_supported(p->P) && !(p->test_flags & SE_TEST_SKIP_TILE_COPY)) {
+        cudaError_t e = launch_gather_sub(p->gpf, p->ntiles, (const int *)b.cnt_t, (const float4 *)b.xs_t,
+                                          (const int *)b.perm_t, (const float *)wgrid, f_orig, self_coef, u, st);
+        if (!e) p->launches++;
+        return e;
+    }
     cudaError_t e = with_p<GatherRun>(p->P, p->gpf, p->ntiles, (const int *)b.cnt_t, (const float4 *)b.xs_t,
                                       (const int *)b.perm_t, (const float *)wgrid, f_orig, self_coef, u,
                                       p->b.status, p->test_flags & SE_TEST_SKIP_TILE_COPY, st);

@@ -353,6 +353,9 @@ cudaError_t launch_spread_sub(const GP<float> &g, int ntiles, int c0, bool stres
                               const float4 *xs, const float4 *fs, const float4 *qs, float *grid, cudaStream_t st);
 cudaError_t launch_bspread_sub(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const int *tile_start, const float4 *xs, const float4 *fs, cudaStream_t st);
+cudaError_t launch_gather_sub(const GP<float> &g, int ntiles, const int *tile_start, const float4 *xs,
+                              const int *perm, const float *w, const float *f_orig, double self_coef, float *u,
+                              cudaStream_t st);
 cudaError_t launch_bspread_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const Buffers &b, cudaStream_t st);
 cudaError_t launch_bgather_col(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,

@@ -60,7 +60,8 @@ struct __align__(16) SubRec {
     float4 wz[SubCfg<P>::WP4 / 2];  // z weights as pairs, from slot (oz & 1) on, zeros elsewhere
     float4 sxy;                     // (s0, s0, s1, s1): source components duplicated for the pairs
     float2 sz;                      // (s2, s2)
-    float2 pad_;
+    int n;                          // the point's index in the sorted arrays (gather)
+    int pad_;
     float wx[SubCfg<P>::WXY];       // x weight of every column of the block (0 off the support)
     float wy[SubCfg<P>::WXY];
 };
@@ -92,7 +93,7 @@ struct SubSmem {
 // of point j and its place in the batch's key order, then writes the point's
 // record there (its x, y and z weights and its source).  Called by every
 // thread of the CTA (it holds a CTA barrier).
-template <int P>
+template <int P, bool GATHER = false>
 __device__ __forceinline__ void sub_stage(SubStage<P> &S, const GP<float> &g, const float4 *__restrict__ xs,
                                           const float4 *__restrict__ fs, const float4 *__restrict__ qs, int fstride,
                                           int foff, int c0, bool stress, const unsigned short *list, int tbeg,
@@ -170,6 +171,8 @@ __device__ __forceinline__ void sub_stage(SubStage<P> &S, const GP<float> &g, co
             w[c] = (kk >= 0 && kk < P) ? __expf(-g.ah2 * tt * tt) : 0.0f;
         }
     }
+    R.n = n;
+    if (GATHER) return;
     const float4 fv = fs[(size_t)n * fstride + foff];
     float4 sv = fv;
     if (stress) {
@@ -233,6 +236,28 @@ __device__ __forceinline__ void sub_runs(const SubStage<P> &S, int ylo, int yhi,
     }
 }
 
+// The points of tile points rb .. rb + rn (window starts from the tags) that
+// lie in sub-tile (sx, sy) of the tile starting at (tx0, ty0): their offsets
+// from rb go to list, their count is returned.  Called by every thread of the
+// CTA (it holds two CTA barriers; the first also orders the previous round's
+// reads of the count before its reset).
+template <int NT>
+__device__ __forceinline__ int sub_filter(const int *__restrict__ tags, int rb, int rn, int tx0, int ty0, int sx,
+                                          int sy, unsigned short *list, int &s_cnt) {
+    const int tid = threadIdx.x;
+    __syncthreads();
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    for (int k = tid; k < rn; k += NT) {
+        int a, b, c;
+        unpack3(__ldg(tags + 4 * (size_t)(rb + k) + 3), a, b, c);
+        const int lx = min(max(a - tx0, 0), COL_TE - 1), ly = min(max(b - ty0, 0), COL_TE - 1);
+        if ((lx >> 2) == sx && (ly >> 2) == sy) list[atomicAdd(&s_cnt, 1)] = (unsigned short)k;
+    }
+    __syncthreads();
+    return s_cnt;
+}
+
 // Spread the points [beg, end) of tile `tile` that lie in sub-tile `sub` (x
 // half sub & 1, y half sub >> 1) onto the three grids at grid + c0 gcs (z-plane
 // stride gzs, component stride gcs); the sources are fs[n * fstride + foff].
@@ -271,17 +296,7 @@ __device__ __forceinline__ void spread_sub_body(const GP<float> &g, int tile, in
     const int *tags = reinterpret_cast<const int *>(xs);
     for (int rb = beg; rb < end; rb += C::CAP) {
         // the round's points of this sub-tile (tile points rb .. rb + rn)
-        const int rn = min(C::CAP, end - rb);
-        if (tid == 0) s_cnt = 0;
-        __syncthreads();
-        for (int k = tid; k < rn; k += C::NT) {
-            int a, b, c;
-            unpack3(__ldg(tags + 4 * (size_t)(rb + k) + 3), a, b, c);
-            const int lx = min(max(a - tx * TE, 0), TE - 1), ly = min(max(b - ty * TE, 0), TE - 1);
-            if ((lx >> 2) == sx && (ly >> 2) == sy) list[atomicAdd(&s_cnt, 1)] = (unsigned short)k;
-        }
-        __syncthreads();
-        const int cnt = s_cnt;
+        const int cnt = sub_filter<C::NT>(tags, rb, min(C::CAP, end - rb), tx * TE, ty * TE, sx, sy, list, s_cnt);
         if (cnt > 0) {
             sub_stage<P>(S[0], g, xs, fs, qs, fstride, foff, c0, stress, list, rb, 0, min(C::NB, cnt), gx0, gy0,
                          gz0);
@@ -294,8 +309,6 @@ __device__ __forceinline__ void spread_sub_body(const GP<float> &g, int tile, in
                 sub_runs<P, 0>(S[k], ylo, yhi, cx, cy, a);
                 __syncthreads();
             }
-        } else {
-            __syncthreads();  // every thread has read s_cnt before the next round resets it
         }
     }
     // flush: the columns through shared memory (x fastest), then added to the
@@ -394,6 +407,177 @@ __global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
                            *reinterpret_cast<SubSmem<P> *>(sub_smem_raw));
 }
 
+// ---------------------------------------------------------------- gather
+// Gather (step 5, eq. u_integr) on the same sub-tiles: thread (cx, cy) loads
+// columns (cx, cy) and (cx, cy + 1) of the three inverse-transformed grids into
+// registers once per CTA (as z pairs), and for each staged point in key order
+// forms the z sums of its two columns with paired FMAs, weights them by wx wy
+// and sums over its three components; a warp then reduces two points at a
+// time over its lanes (butterfly shuffles) and stores its part of each point
+// in a slot of its own, and the parts of the warps are added in a fixed order
+// when the batch is written out (no atomics: the result does not depend on
+// the order in which warps finish).
+
+template <int P>
+struct SubGSmem {
+    SubStage<P> S;
+    float part[SubCfg<P>::NW][SubCfg<P>::NB][3];  // each warp's part of each point of the batch
+    unsigned short list[SubCfg<P>::CAP];
+    int cnt;
+};
+
+// The point's sums over the thread's two columns: v[c] = sum_r wx wy_r sum_k wz_k G[r][c][z_k]
+template <int P, int OZ>
+__device__ __forceinline__ void subg_point(const SubRec<P> &R, int cx, int cy, const SubAcc<P> &G, float (&v)[3]) {
+    constexpr int Q0 = OZ / 2, NP = P / 2 + (OZ & 1);
+    static_assert(Q0 + NP <= SubCfg<P>::ZP, "the point's z support stays inside the column");
+    float2 d[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) d[r][c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k2 = 0; k2 < (NP + 1) / 2; k2++) {
+        const float4 wv = R.wz[k2];
+        const float2 lo = make_float2(wv.x, wv.y), hi = make_float2(wv.z, wv.w);
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                d[r][c] = __ffma2_rn(lo, G[r][c][Q0 + 2 * k2], d[r][c]);
+                if (2 * k2 + 1 < NP) d[r][c] = __ffma2_rn(hi, G[r][c][Q0 + 2 * k2 + 1], d[r][c]);
+            }
+    }
+    const float wxv = R.wx[cx];
+    const float2 wyv = *reinterpret_cast<const float2 *>(&R.wy[cy]);
+    const float w0 = wxv * wyv.x, w1 = wxv * wyv.y;
+#pragma unroll
+    for (int c = 0; c < 3; c++) v[c] = fmaf(w1, d[1][c].x + d[1][c].y, w0 * (d[0][c].x + d[0][c].y));
+}
+
+// Sum two points' values over the warp's lanes (lanes 0-15 end with point a's,
+// 16-31 with point b's) and store them in the warp's slots ia, ib.
+__device__ __forceinline__ void subg_reduce2(float (&va)[3], float (&vb)[3], float *pa, float *pb, int lane) {
+    const bool up = lane >= 16;
+    float t[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float send = up ? va[c] : vb[c], keep = up ? vb[c] : va[c];
+        t[c] = keep + __shfl_xor_sync(FULLM, send, 16);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; c++) t[c] += __shfl_xor_sync(FULLM, t[c], o);
+    const int c = lane & 15;
+    if (c < 3) (up ? pb : pa)[c] = c == 0 ? t[0] : (c == 1 ? t[1] : t[2]);
+}
+
+__device__ __forceinline__ void subg_reduce1(float (&va)[3], float *pa, int lane) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; c++) va[c] += __shfl_xor_sync(FULLM, va[c], o);
+    if (lane < 3) pa[lane] = lane == 0 ? va[0] : (lane == 1 ? va[1] : va[2]);
+}
+
+// The batch's records with z offset OZ, OZ + 1, ... whose oy lies in [ylo,
+// yhi], two at a time; part: this warp's slots.
+template <int P, int OZ>
+__device__ __forceinline__ void subg_runs(const SubStage<P> &S, float (*part)[3], int ylo, int yhi, int cx, int cy,
+                                          const SubAcc<P> &G, int lane) {
+    if constexpr (OZ < SubCfg<P>::TE) {
+        const int i0 = S.kst[OZ * SUB + ylo], i1 = S.kst[OZ * SUB + yhi + 1];
+        int i = i0;
+        for (; i + 1 < i1; i += 2) {
+            float va[3], vb[3];
+            subg_point<P, OZ>(S.rec[i], cx, cy, G, va);
+            subg_point<P, OZ>(S.rec[i + 1], cx, cy, G, vb);
+            subg_reduce2(va, vb, part[i], part[i + 1], lane);
+        }
+        if (i < i1) {
+            float va[3];
+            subg_point<P, OZ>(S.rec[i], cx, cy, G, va);
+            subg_reduce1(va, part[i], lane);
+        }
+        subg_runs<P, OZ + 1>(S, part, ylo, yhi, cx, cy, G, lane);
+    }
+}
+
+// One CTA per (tile, sub-tile), block b taking sub-tile b mod 4 of tile b / 4.
+// w: the three grids (z-plane stride gzs, component stride gcs); u[perm[n]] =
+// the gathered values + self_coef f_orig[perm[n]] (in FP64).
+template <int P>
+__global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
+    k_gather_sub(GP<float> g, const int *__restrict__ tile_start, const float4 *__restrict__ xs,
+                 const int *__restrict__ perm, const float *__restrict__ w, size_t gzs, size_t gcs,
+                 const float *__restrict__ f_orig, double self_coef, float *__restrict__ u) {
+    using C = SubCfg<P>;
+    constexpr int ZP = C::ZP, TE = C::TE;
+    extern __shared__ __align__(16) unsigned char subg_smem_raw[];
+    SubGSmem<P> &sm = *reinterpret_cast<SubGSmem<P> *>(subg_smem_raw);
+    const int tile = blockIdx.x >> 2, sub = blockIdx.x & 3;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;
+    const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
+    const int sx = sub & 1, sy = sub >> 1;
+    const int gx0 = tx * TE + SUB * sx, gy0 = ty * TE + SUB * sy, gz0 = tz * TE;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lr = lane / C::PT;
+    const int cyw = warp * C::RW + lr * C::TR;
+    const bool own = lr < C::LR && cyw < C::PT;
+    const int cx = own ? lane - lr * C::PT : C::PT, cy = own ? cyw : 0;
+    const int r0 = warp * C::RW, r1 = min(r0 + C::RW, C::PT) - 1;
+    const int ylo = max(0, r0 - (P - 1)), yhi = min(SUB - 1, r1);
+    // the thread's two columns of the three grids (zero outside the grids)
+    SubAcc<P> G;
+    const int gx = gx0 + cx;
+#pragma unroll
+    for (int r = 0; r < C::TR; r++) {
+        const int gy = gy0 + cy + r;
+        const bool col = own && cy + r < C::PT && gx < g.mt[0] && gy < g.mt[1];
+        const float *b = w + (size_t)gz0 * gzs + (size_t)gy * g.mf[0] + gx;
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int q = 0; q < ZP; q++) {
+                const int z0 = 2 * q, z1 = 2 * q + 1;
+                const float v0 = (col && gz0 + z0 < g.mt[2]) ? __ldg(b + (size_t)c * gcs + (size_t)z0 * gzs) : 0.0f;
+                const float v1 = (col && z1 < C::PZ && gz0 + z1 < g.mt[2])
+                                     ? __ldg(b + (size_t)c * gcs + (size_t)z1 * gzs)
+                                     : 0.0f;
+                G[r][c][q] = make_float2(v0, v1);
+            }
+    }
+    const int *tags = reinterpret_cast<const int *>(xs);
+    for (int rb = beg; rb < end; rb += C::CAP) {
+        const int cnt = sub_filter<C::NT>(tags, rb, min(C::CAP, end - rb), tx * TE, ty * TE, sx, sy, sm.list,
+                                          sm.cnt);
+        for (int b0 = 0; b0 < cnt; b0 += C::NB) {
+            const int nb = min(C::NB, cnt - b0);
+            sub_stage<P, true>(sm.S, g, xs, nullptr, nullptr, 1, 0, 0, false, sm.list, rb, b0, nb, gx0, gy0, gz0);
+            // every warp's slots start at zero (a warp whose rows no support of a
+            // point meets leaves them so)
+            for (int i = tid; i < C::NW * C::NB * 3; i += C::NT) (&sm.part[0][0][0])[i] = 0.0f;
+            __syncthreads();
+            subg_runs<P, 0>(sm.S, sm.part[warp], ylo, yhi, cx, cy, G, lane);
+            __syncthreads();
+            if (tid < nb) {
+                const int n = sm.S.rec[tid].n, m = perm[n];
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    float v = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < C::NW; k++) v += sm.part[k][tid][c];
+                    double o = (double)v;
+                    if (self_coef != 0.0) o += self_coef * (double)f_orig[3 * (size_t)m + c];
+                    u[3 * (size_t)m + c] = (float)o;
+                }
+            }
+        }
+    }
+}
+
 template <int P>
 cudaError_t run_spread_sub(const GP<float> &g, int ntiles, int c0, bool stress, const int *ts, const float4 *xs,
                            const float4 *fs, const float4 *qs, float *grid, cudaStream_t st) {
@@ -415,9 +599,28 @@ cudaError_t run_bspread_sub(const BSys<float> *sys, const int4 *items, int nitem
     return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t run_gather_sub(const GP<float> &g, int ntiles, const int *ts, const float4 *xs, const int *perm,
+                           const float *w, const float *f_orig, double self_coef, float *u, cudaStream_t st) {
+    constexpr size_t smem = sizeof(SubGSmem<P>);
+    cudaError_t e = cudaFuncSetAttribute(k_gather_sub<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    const size_t gzs = (size_t)g.mf[0] * g.mf[1], gcs = gzs * g.mf[2];
+    k_gather_sub<P><<<4 * ntiles, SubCfg<P>::NT, smem, st>>>(g, ts, xs, perm, w, gzs, gcs, f_orig, self_coef, u);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 bool sub_supported(int P) { return P == 10 || P == 12; }
+
+cudaError_t launch_gather_sub(const GP<float> &g, int ntiles, const int *tile_start, const float4 *xs,
+                              const int *perm, const float *w, const float *f_orig, double self_coef, float *u,
+                              cudaStream_t st) {
+    if (g.P == 12) return run_gather_sub<12>(g, ntiles, tile_start, xs, perm, w, f_orig, self_coef, u, st);
+    if (g.P == 10) return run_gather_sub<10>(g, ntiles, tile_start, xs, perm, w, f_orig, self_coef, u, st);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_spread_sub(const GP<float> &g, int ntiles, int c0, bool stress, const int *tile_start,
                               const float4 *xs, const float4 *fs, const float4 *qs, float *grid, cudaStream_t st) {
