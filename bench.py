@@ -605,23 +605,24 @@ def run_ours(args, rank, world, dist):
         "real": N_POINTS * (32 + 24),
     }
     stage_gbs = {k: stage_bytes[k] / (stages[k] * 1e-3) / 1e9 for k in stage_bytes if stages.get(k)}
-    # each hand-written stage against the roofline that binds it: spreading is
-    # FP32 FMA work in registers (3 P^3 FMA per point), the gather reads each
-    # point's 3 P^3 grid values from shared memory (one 128-byte wavefront per
-    # SM clock), the scaling streams the spectrum through HBM, the real-space
-    # sum is FP32 ALU work (58 flop per pair)
+    # each hand-written stage against the roofline that binds it: spreading and
+    # the gather are FP32 FMA work on register columns (3 P^3 FMA per point),
+    # the scaling streams the spectrum through HBM, the real-space sum is FP32
+    # ALU work (58 flop per pair); the FMA-bound stages also against the FMA
+    # rate measured on this GPU
     P = prm["P"]
     grid_flop = N_POINTS * 3 * P**3 * 2
-    smem_peak = n_sm * 128 * sm_max * 1e6 / 1e12  # TB/s: one 128-byte wavefront per SM clock
     stage_roofline = {}
     for k, bound, work, unit, peak in (
             ("spread", "fma", grid_flop, "TFLOP/s", alu_peak),
-            ("gather", "smem", N_POINTS * 3 * P**3 * 4, "TB/s", smem_peak),
+            ("gather", "fma", grid_flop, "TFLOP/s", alu_peak),
             ("scale", "hbm", stage_bytes["scale"], "GB/s", hbm),
             ("real", "alu", pairs * FLOP_PER_PAIR, "TFLOP/s", alu_peak)):
         if stages.get(k):
             a = work / (stages[k] * 1e-3) / (1e9 if unit == "GB/s" else 1e12)
             stage_roofline[k] = {"bound": bound, "achieved": a, "peak": peak, "unit": unit, "frac": a / peak}
+            if unit == "TFLOP/s" and probe.get("fp32_fma_tflops"):
+                stage_roofline[k]["frac_of_measured"] = a / probe["fp32_fma_tflops"]
     cpu = None
     if not args.no_cpu:
         cpu, cidx, cref = cpu_baseline(x64, f64)

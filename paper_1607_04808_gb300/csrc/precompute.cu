@@ -15,7 +15,7 @@
 // its real part kept and, in the first transform, only the Mt_d + 1 outputs
 // the truncation keeps.  Against the full 3-D transforms this evaluates B^R on
 // an eighth of the points and transforms a quarter of the lines, with the same
-// sums (SE_PRECOMPUTE_OCTANT = 0 restores the full transforms).
+// sums; large oversampled grids take it (SE_PRECOMPUTE_OCTANT = 0: never).
 #include <stdio.h>
 #include <string.h>
 
@@ -226,8 +226,17 @@ se_status_t precompute_octant(se_plan_s *p) {
     return st;
 }
 
+// The octant passes from this many points of the oversampled grid on (512^3):
+// below it the full 3-D transforms are as fast once warm, and the first
+// transform of a new line length in a process costs cuFFT 25 to 75 ms of
+// set-up (measured on GB300: FP64 1-D transforms of lengths 252, 350 and 800),
+// which the full transforms' kernels do not.  FP64 at 1e-10, N = 1e6 (Mg =
+// 800): 158 -> 54 ms (80 ms in a process's first plan); the FP32 plan of the
+// same points (Mg = 350) keeps the full transforms (16 ms).
+constexpr double OCTANT_MIN_POINTS = 134217728.0;
+
 se_status_t precompute_compute(se_plan_s *p) {
-    if (SE_PRECOMPUTE_OCTANT) {
+    if (SE_PRECOMPUTE_OCTANT && (double)p->mg[0] * p->mg[1] * p->mg[2] >= OCTANT_MIN_POINTS) {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
