@@ -1435,8 +1435,11 @@ bool col_supported(int prec, int P) { return prec == SE_FP32 && P >= 4 && P <= 1
 cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
                               void *grid, int nc) {
     // nc = 3: f; nc = 6: the symmetric stresslet source in two passes of three
+    // sub-tiles pay off from about 100 points per 8^3 tile on (N = 1e6: 296
+    // per tile at M = 114, 0.95 -> 0.59 ms; 94 at M = 168, 1.06 ms both ways)
+    const bool sub = SE_SPREAD_SUB && sub_supported(p->P) && p->N >= 128 * (int64_t)p->ntiles;
     for (int c0 = 0; c0 < nc; c0 += 3) {
-        cudaError_t e = (SE_SPREAD_SUB && sub_supported(p->P))
+        cudaError_t e = sub
                             ? launch_spread_sub(p->gpf, p->ntiles, c0, nc == 6, (const int *)p->b.cnt_t,
                                                 (const float4 *)xs, (const float4 *)fs, (const float4 *)qs,
                                                 (float *)grid, st)
@@ -1451,14 +1454,18 @@ cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, con
 
 cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, const float *f_orig, float *u) {
     const double self_coef = (p->kernel == SE_STOKESLET) ? -4.0 * p->xi / sqrt(M_PI) : 0.0;
-    return launch_gather_col_set(p, st, p->b, wgrid, f_orig, self_coef, u);
+    return launch_gather_col_set(p, st, p->b, wgrid, f_orig, self_coef, u, p->N);
 }
 
 cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &b, const void *wgrid,
-                                  const float *f_orig, double self_coef, float *u) {
-    // the sub-tile gather (P = 10, 12); the tiles of the failure-path test
-    // flag are those of the tensor-copy gather
-    if (SE_GATHER_SUB && sub_supported(p->P) && !(p->test_flags & SE_TEST_SKIP_TILE_COPY)) {
+                                  const float *f_orig, double self_coef, float *u, int64_t n_pts) {
+    // the sub-tile gather (P = 10, 12) from 256 points per 8^3 tile on (N =
+    // 1e6: 296 per tile at M = 114, 0.835 -> 0.79 ms; 94 per tile at M = 168,
+    // 1.37 ms against 0.90 ms; a cost per tile linear in its points puts the
+    // crossing near 250); the tiles of the failure-path test flag are those of
+    // the tensor-copy gather
+    if (SE_GATHER_SUB && sub_supported(p->P) && n_pts >= 256 * (int64_t)p->ntiles &&
+        !(p->test_flags & SE_TEST_SKIP_TILE_COPY)) {
         cudaError_t e = launch_gather_sub(p->gpf, p->ntiles, (const int *)b.cnt_t, (const float4 *)b.xs_t,
                                           (const int *)b.perm_t, (const float *)wgrid, f_orig, self_coef, u, st);
         if (!e) p->launches++;

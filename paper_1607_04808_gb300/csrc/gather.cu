@@ -343,7 +343,7 @@ template cudaError_t launch_gather_adjT<double>(se_plan_s *, cudaStream_t, const
 template <typename T>
 cudaError_t launch_gather_targets(se_plan_s *p, cudaStream_t st, const Buffers &bt, int Nt, const void *wgrid,
                                   T *ut) {
-    if (sizeof(T) == 4 && p->colk) return launch_gather_col_set(p, st, bt, wgrid, nullptr, 0.0, (float *)ut);
+    if (sizeof(T) == 4 && p->colk) return launch_gather_col_set(p, st, bt, wgrid, nullptr, 0.0, (float *)ut, Nt);
     dim3 gs((Nt + WPB - 1) / WPB), bs(WPB * 32);
     const vec4<T> *xs = (const vec4<T> *)bt.xs_t;
     const T *w = (const T *)wgrid;

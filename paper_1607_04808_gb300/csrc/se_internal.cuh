@@ -338,7 +338,7 @@ cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, con
                               void *grid, int nc);
 cudaError_t launch_gather_col(se_plan_s *p, cudaStream_t st, const void *wgrid, const float *f_orig, float *u);
 cudaError_t launch_gather_col_set(se_plan_s *p, cudaStream_t st, const Buffers &b, const void *wgrid,
-                                  const float *f_orig, double self_coef, float *u);
+                                  const float *f_orig, double self_coef, float *u, int64_t n_pts);
 // the stresslet's adjoint strength gradients from the tensor field V on the
 // shared-memory tiles (FP32 column plans)
 cudaError_t launch_gather_adj_col(se_plan_s *p, cudaStream_t st, const float *V, const float *f, const float *q,

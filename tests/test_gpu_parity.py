@@ -93,6 +93,42 @@ def test_fp32_small_vs_direct_and_o2(kernel):
     assert rel_l2(u, o2) <= 1e-6
 
 
+@pytest.mark.parametrize("kernel,Pw,M,xi,rc,bound", [
+    ("stokeslet", 12, 24, 8.0, 0.3, (2e-6, 2e-5)),
+    ("rotlet", 10, 24, 8.0, 0.3, (2e-6, 2e-5)),
+    ("stresslet", 12, 24, 8.0, 0.3, (2e-6, 2e-5)),
+    ("stokeslet", 12, 12, 4.0, 0.45, (1e-5, 2e-4)),
+])
+def test_fp32_dense_tiles_vs_o2(kernel, Pw, M, xi, rc, bound):
+    """Dense tiles of window starts (N = 30000): at M = 24 about 470 points
+    per 8^3 tile, at M = 12 about 3750, enough for the FP32 spreading and gather
+    on sub-tiles, and at M = 12 for several rounds of 2048 tile points and
+    several batches of 128 per sub-tile.  Against O2 with the same parameters,
+    at the sources and at 30000 separate targets (the gather at targets on
+    sub-tiles too).  The bounds (relative L2, relative max) are the FP32
+    path's: at M = 12 every grid value sums about 23000 terms, and the 8^3-tile
+    kernels leave the same 3.6e-6 and 5.7e-5 there; a batch of 128 points lost
+    would leave about 4e-3."""
+    N = 30000
+    x, f = W.stokeslet_uniform(N, 31)
+    q = W.unit_vectors(N, 31) if kernel == "stresslet" else None
+    x32, f32, q32 = as32(x), as32(f), as32(q)
+    kw = dict(M=M, P=Pw, xi=xi, rc=rc)
+    u, prm = gpu_eval(kernel, x32, f32, q32, "fp32", **kw)
+    assert prm["Mtilde"] == M + Pw
+    o2 = ose.se_eval(kernel, x32, f32, q32, **kw)
+    assert rel_l2(u, o2) <= bound[0] and rel_max(u, o2) <= bound[1], (rel_l2(u, o2), rel_max(u, o2))
+    pkg = P()
+    y = as32(W.uniform_points(N, 32))
+    plan = pkg.Plan(kernel, N, BOX, prec="fp32", **kw)
+    dev = lambda a: None if a is None else torch.tensor(a, dtype=torch.float32, device="cuda")  # noqa: E731
+    ut = plan.eval_targets(dev(x32), dev(f32), dev(y), q=dev(q32)).double().cpu().numpy()
+    plan.check()
+    plan.close()
+    o2t = ose.se_eval(kernel, x32, f32, q32, xt=y, **kw)
+    assert rel_l2(ut, o2t) <= bound[0] and rel_max(ut, o2t) <= bound[1], (rel_l2(ut, o2t), rel_max(ut, o2t))
+
+
 @pytest.mark.parametrize("N", [1, 2, 33, 517])
 def test_ragged_and_tiny(N):
     """Sizes that leave tiles, cells and warps partly empty; N = 1 has no pairs."""
