@@ -34,6 +34,9 @@ WORKLOAD = "stokeslet sum, N=1e6 uniform iid in [0,1)^3, f iid N(0,1)^3; FP32 pa
 # |r|^2 5, rsqrt 1, r 1, xi r 1, -xi^2 r^2 1, exp 2, erfc 20, c e 1, A 2, B 3,
 # r.f 5, B (r.f) 1, u += A f + B (r.f) r 12.
 FLOP_PER_PAIR = 58
+# the same split into the part shared by all right-hand sides (geometry and
+# radial functions, 40) and the update per right-hand side (18)
+FLOP_RADIAL, FLOP_UPDATE = 40, 18
 # DRAM bytes (read + write) of one launch of the FP32 stokeslet real-space kernel on
 # this workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 # Set to None whenever that kernel changes, until it is captured again.
@@ -286,6 +289,21 @@ def run_batched(args, rank, world, dist, dev, flush):
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    # per-stage times from 3 further evaluations with stage timing on (no graph)
+    B.set_timing(True)
+    st_acc = {}
+    for _ in range(3):
+        flush.zero_()
+        B.eval(xs, fs, out=u)
+        for k, v in B.stage_times().items():
+            st_acc.setdefault(k, []).append(v)
+    B.set_timing(False)
+    stages = {k: float(np.mean(v)) for k, v in st_acc.items()}
+    # the dominant kernel (real space: every ordered pair within each system's
+    # rc, the radial functions once per pair, the update per right-hand side)
+    pairs = sum(sizes[s] * (sizes[s] - 1) * pair_fraction_unit_cube(B.params(k)["rc"])
+                for k, s in enumerate(mine))
+    flop = pairs * (FLOP_RADIAL + FLOP_UPDATE * R)
     # this rank's systems at sampled targets (all targets of systems up to 2e3
     # points, 64 otherwise), for the error check after the timed regions
     uh = u.double().cpu().numpy()
@@ -306,7 +324,18 @@ def run_batched(args, rank, world, dist, dev, flush):
            "tol": 2e-6, "P": B.params(0)["P"], "launches_per_step": B.launch_count(),
            "graph": True, "workload": "64 stokeslet systems, N_s lognormal(ln 1e4, 1) clipped to [1e3, 1e5], "
                                       "each in [0,1)^3, 8 RHS ~ N(0,1)^3, FP32 rel. err 2e-6",
-           "sharding": f"{len(mine)} of 64 systems on rank {rank} (cost-balanced), max over {world} ranks"}
+           "sharding": f"{len(mine)} of 64 systems on rank {rank} (cost-balanced), max over {world} ranks",
+           "stages_ms": stages,
+           "stages_note": "3 further evaluations with stage timing on (kernels launched without the graph); "
+                          "spread includes the octant zeroing, real the cluster lists",
+           "roofline": {"bound": "alu", "kernel": "k_real_cl (batched real-space sum, full candidate lists, "
+                        f"{R} right-hand sides per pass)",
+                        "achieved": flop / (stages["real"] * 1e-3) / 1e12 if stages.get("real") else None,
+                        "unit": "TFLOP/s",
+                        "work": f"algorithmic: ordered pairs within each system's rc (expected count for uniform "
+                                f"points in its unit cube) x ({FLOP_RADIAL} + {FLOP_UPDATE} x {R}) flop (the "
+                                "radial functions once per pair, the update per right-hand side)",
+                        "pairs_per_launch": pairs}}
     B.close()
     return out, check
 
@@ -623,6 +652,10 @@ def run_ours(args, rank, world, dist):
             stage_roofline[k] = {"bound": bound, "achieved": a, "peak": peak, "unit": unit, "frac": a / peak}
             if unit == "TFLOP/s" and probe.get("fp32_fma_tflops"):
                 stage_roofline[k]["frac_of_measured"] = a / probe["fp32_fma_tflops"]
+    if batched is not None and batched.get("roofline", {}).get("achieved"):
+        br = batched["roofline"]
+        br.update(peak=alu_peak, frac=br["achieved"] / alu_peak, peak_measured=probe["fp32_fma_tflops"],
+                  frac_of_measured=br["achieved"] / probe["fp32_fma_tflops"])
     cpu = None
     if not args.no_cpu:
         cpu, cidx, cref = cpu_baseline(x64, f64)

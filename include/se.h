@@ -233,6 +233,16 @@ se_status_t se_batch_eval(se_batch_t batch, const void *x, const void *f, void *
 /* Graph mode on (1, default) or off (0: every call launches the kernels). */
 se_status_t se_batch_set_graph(se_batch_t batch, int on);
 
+/* Stage timing on (1) or off (0, default).  While on, se_batch_eval launches
+ * the kernels without the graph and records events between the stages;
+ * se_batch_stage_times then gives the device times (milliseconds) of the last
+ * timed call in the order bin, spread (octant zeroing included), fft, scale,
+ * ifft, gather, real (the cluster lists and the pair sums): returns the
+ * number written (7, or 0 before the first timed call or for NULL arguments).
+ * No counterpart in the paper (measurement only). */
+se_status_t se_batch_set_timing(se_batch_t batch, int on);
+int se_batch_stage_times(se_batch_t batch, float *ms, int max_n);
+
 /* Parameters chosen for system s (as se_plan_get_params). */
 se_status_t se_batch_get_params(se_batch_t batch, int s, se_params_t *out);
 

@@ -63,12 +63,18 @@ struct se_batch_s {
     void *gu = nullptr;
     int64_t launches = 0;
     cudaStream_t last_stream = nullptr;
+    // stage timing (se_batch_set_timing): events around the stages of an
+    // evaluation run without the graph
+    bool timing = false, timed = false;
+    cudaEvent_t ev[8] = {};
 };
 
 namespace {
 
 void free_batch(se_batch_s *B) {
     if (!B) return;
+    for (auto &e : B->ev)
+        if (e) cudaEventDestroy(e);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     if (B->cap) cudaStreamDestroy(B->cap);
@@ -142,13 +148,20 @@ se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t 
     const BSys<T> *sys = (const BSys<T> *)B->sys_d;
     const int S = B->S, R = B->R, Ntot = (int)B->Ntot;
     B->launches = 0;
+    // stage boundary k (timing only): bin | zero + spread | fft | scale | ifft | gather | real
+    auto mark = [&](int k) {
+        if (B->timing) cudaEventRecord(B->ev[k], st);
+    };
+    mark(0);
     BCK(launch_bbin<T>(sys, B->off_d, S, Ntot, R, B->ntiles_tot, B->ncells_tot, x, f, B->b, st, &B->launches));
+    mark(1);
     BCK(launch_bzero<T>(sys, B->zblk_base_d, S, B->nblk_zero, R, st));
     if (sizeof(T) == 4 && B->colk)
         BCK(launch_bspread_col((const BSys<float> *)sys, B->items_d, B->nitems, B->P, R, B->b, st));
     else
         BCK(launch_bspread<T>(sys, B->items_d, B->nitems, B->P, B->T_, R, B->b, st));
     B->launches += 2;
+    mark(2);
     for (auto &c : B->classes) {
         if (B->ilv) {
             // 2D (y, x) transforms of the nonzero planes of all the class's grids,
@@ -168,8 +181,10 @@ se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t 
         else
             BCF(cufftExecD2Z(c.fwd, (cufftDoubleReal *)c.grid, (cufftDoubleComplex *)c.spec));
     }
+    mark(3);
     BCK(launch_bscale<T>(B->kernel, sys, B->blk_base_d, S, B->nblk_scale, R, st));
     B->launches += 1;
+    mark(4);
     for (auto &c : B->classes) {
         if (B->ilv) {
             // back along z, then 2D on only the planes the gather reads
@@ -185,14 +200,18 @@ se_status_t enqueue_t(se_batch_s *B, const T *x, const T *f, T *u, cudaStream_t 
         else
             BCF(cufftExecZ2D(c.inv, (cufftDoubleComplex *)c.spec, (cufftDoubleReal *)c.wgrid));
     }
+    mark(5);
     if (sizeof(T) == 4 && B->colk)
         BCK(launch_bgather_col((const BSys<float> *)sys, B->items_d, B->nitems, B->P, R, B->b, (const float *)f,
                                (float *)u, B->maps_d, st));
     else
         BCK(launch_bgather<T>(sys, B->off_d, S, Ntot, B->P, R, B->b, f, u, st));
     B->launches += 1;
+    mark(6);
     BCK(launch_breal<T>(B->kernel, sys, B->row_base_d, S, B->nrows_tot, Ntot, R, B->b, B->cl_sys, u, st,
                         &B->launches));
+    mark(7);
+    if (B->timing) B->timed = true;
     return SE_OK;
 }
 
@@ -509,7 +528,7 @@ extern "C" se_status_t se_batch_eval(se_batch_t B, const void *x, const void *f,
     if (!B || !x || !f || !u) return fail(SE_ERR_INVALID_ARG, "se_batch_eval: NULL pointer");
     cudaStream_t st = (cudaStream_t)stream;
     B->last_stream = st;
-    if (!B->use_graph) return enqueue(B, x, f, u, st);
+    if (!B->use_graph || B->timing) return enqueue(B, x, f, u, st);
     if (!B->exec || B->gx != x || B->gf != f || B->gu != u) {
         if (B->exec) cudaGraphExecDestroy(B->exec);
         if (B->graph) cudaGraphDestroy(B->graph);
@@ -532,6 +551,29 @@ extern "C" se_status_t se_batch_eval(se_batch_t B, const void *x, const void *f,
     }
     BCK(cudaGraphLaunch(B->exec, st));
     return SE_OK;
+}
+
+extern "C" se_status_t se_batch_set_timing(se_batch_t B, int on) {
+    if (!B) return fail(SE_ERR_INVALID_ARG, "NULL batch");
+    if (on && !B->ev[0]) {
+        for (auto &e : B->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(SE_ERR_CUDA, "se_batch_set_timing: event");
+    }
+    B->timing = on != 0;
+    B->timed = false;
+    return SE_OK;
+}
+
+extern "C" int se_batch_stage_times(se_batch_t B, float *ms, int max_n) {
+    if (!B || !ms || !B->timed) return 0;
+    if (cudaEventSynchronize(B->ev[7]) != cudaSuccess) return 0;
+    int n = 0;
+    for (int k = 0; k < 7 && n < max_n; k++, n++) {
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, B->ev[k], B->ev[k + 1]);
+        ms[n] = t;
+    }
+    return n;
 }
 
 extern "C" se_status_t se_batch_set_graph(se_batch_t B, int on) {

@@ -26,6 +26,7 @@ STATUS = {
 STAGES = ["bin", "spread", "fft", "scale", "ifft", "gather", "real_setup", "real"]
 TEST_SKIP_TILE_COPY = 1  # se.h SE_TEST_SKIP_TILE_COPY
 BACK_STAGES = ["adj_bin", "adj_fourier", "adj_gather", "adj_real", "bin", "fourier", "grad_gather", "grad_real"]
+BATCH_STAGES = ["bin", "spread", "fft", "scale", "ifft", "gather", "real"]
 
 
 class SEError(RuntimeError):
@@ -120,6 +121,10 @@ def lib():
             L.se_batch_eval.argtypes = [vp, vp, vp, vp, vp]
             L.se_batch_set_graph.restype = i32
             L.se_batch_set_graph.argtypes = [vp, i32]
+            L.se_batch_set_timing.restype = i32
+            L.se_batch_set_timing.argtypes = [vp, i32]
+            L.se_batch_stage_times.restype = i32
+            L.se_batch_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
             L.se_batch_get_params.restype = i32
             L.se_batch_get_params.argtypes = [vp, i32, ctypes.POINTER(SEParams)]
             L.se_batch_check.restype = i32
@@ -383,6 +388,16 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(lib().se_batch_launch_count(self._h))
+
+    def set_timing(self, on: bool) -> None:
+        """se_batch_set_timing: stage timing of the following evaluations (no graph while on)."""
+        _check(lib().se_batch_set_timing(self._h, 1 if on else 0))
+
+    def stage_times(self) -> dict:
+        """se_batch_stage_times of the last timed evaluation."""
+        buf = (ctypes.c_float * 7)()
+        n = lib().se_batch_stage_times(self._h, buf, 7)
+        return {BATCH_STAGES[i]: buf[i] for i in range(n)}
 
     def close(self):
         if getattr(self, "_h", None):

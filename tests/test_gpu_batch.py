@@ -139,6 +139,29 @@ def test_batch_graph_replay_and_recapture():
     E.close()
 
 
+def test_batch_stage_timing():
+    """Stage timing: seven positive stage times after a timed evaluation, none
+    before or after turning it off, and the same result as the graph
+    evaluation."""
+    pkg = P()
+    R = 2
+    xs, fs = small_batch(14, [3000, 5000], [(0.0, 0.0, 0.0, 1.0)] * 2, R)
+    x = to_dev(np.concatenate(xs), "fp32")
+    f = to_dev(np.concatenate(fs), "fp32")
+    B = pkg.Batch("stokeslet", [3000, 5000], None, R, tol=2e-6, prec="fp32")
+    assert B.stage_times() == {}
+    ref = B.eval(x, f, check=True).double().cpu().numpy()
+    B.set_timing(True)
+    got = B.eval(x, f, check=True).double().cpu().numpy()
+    st = B.stage_times()
+    assert list(st) == ["bin", "spread", "fft", "scale", "ifft", "gather", "real"]
+    assert all(v > 0.0 for v in st.values()), st
+    assert rel_l2(got, ref) <= 1e-6
+    B.set_timing(False)
+    assert B.stage_times() == {}
+    B.close()
+
+
 def test_batch_rejects_unsupported():
     pkg = P()
     with pytest.raises(pkg.SEError):
