@@ -92,6 +92,19 @@ se_status_t fourier_grid(se_plan_s *p, cudaStream_t st, void *wout, int nc, Stag
         CF(cufftSetStream(p->i2d, st));
         for (int c = 0; c < nc; c++)
             CF(exec_fwd<T>(p->f2d, (T *)p->grid + c * vol_r, (cplx<T> *)p->spec + c * nk));
+        if (sizeof(T) == 4 && p->zw && nc == p->nc) {
+            // the z-transforms, the upper planes' zeros and the scaling in one
+            // kernel (zfft.cu); the stage times: fft = the 2D transforms, scale =
+            // the fused kernel, ifft = the inverse 2D transforms
+            if (tm) tm->mark();
+            CK(launch_zscale(p, st, p->spec, nc));
+            p->launches++;
+            if (tm) tm->mark();
+            for (int c = 0; c < 3; c++)
+                CF(exec_inv<T>(p->i2d, (cplx<T> *)p->spec + c * nk, (T *)wout + c * vol_r));
+            if (tm) tm->mark();
+            return SE_OK;
+        }
         CK(cudaMemset2DAsync((char *)p->spec + p->mt[2] * plane_c * cs, nk * cs, 0,
                              (p->mf[2] - p->mt[2]) * plane_c * cs, nc, st));
         for (int c = 0; c < nc; c++) CF(exec_z<T>(p->zc, (cplx<T> *)p->spec + c * nk, CUFFT_FORWARD));

@@ -236,7 +236,7 @@ void free_plan(se_plan_s *p) {
                     p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
                     p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
                     p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du, p->pgrid, p->b.rt,
-                    p->gsort};
+                    p->gsort, p->zw};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     void *tptrs[] = {p->bt.xs_t, p->bt.perm_t, p->bt.slot_t, p->bt.key_t, p->bt.tag_t, p->bt.cnt_t, p->bt.xs_r,
@@ -743,6 +743,9 @@ static se_status_t create_plan(se_kernel_t kernel, int64_t N, double xi, const d
 #ifndef SE_PRUNED_FFT
 #define SE_PRUNED_FFT 1
 #endif
+#ifndef SE_ZFUSE
+#define SE_ZFUSE 1
+#endif
         if (SE_PRUNED_FFT && !periodic) {
             // the spread grid is zero outside z, y, x < Mtilde and the gather reads
             // only that corner: the 2D (y, x) transforms run on the Mtilde planes
@@ -759,6 +762,12 @@ static se_status_t create_plan(se_kernel_t kernel, int64_t N, double xi, const d
                 return fail(SE_ERR_CUFFT, "cufftPlanMany (zero-padding-aware transforms) failed");
             }
             p->pruned = true;
+            // FP32: the z-transforms and the scaling fused into one kernel
+            if (SE_ZFUSE && prec == SE_FP32 && zfuse_supported(p->mf[2], p->nc) &&
+                zfuse_twiddles(p->mf[2], &p->zw) != cudaSuccess) {
+                free_plan(p);
+                return fail(SE_ERR_OOM, "twiddle table of the fused z-transforms");
+            }
         }
     }
     for (int i = 0; i < 9; i++) cudaEventCreate(&p->ev[i]);

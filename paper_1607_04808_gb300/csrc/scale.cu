@@ -1,25 +1,11 @@
-// Step 3 of Section 5.2 (scaling, eq. gridfcnsc): in Fourier space
-//   w^_j(k) = e^{-(1-eta) k^2 / 4 xi^2} A_j..(k) g^_..(k)
-// with the multipliers of eqs. AS, AT, AR where the truncated harmonic /
-// biharmonic transform is replaced by the precomputed mollified kernel G~^(k)
-// (Section 4.3, stored as the (Mt+1)^3 octant of a real, even array).
-//   stokeslet  A_jl  = -(k^2 d_jl - k_j k_l)(1 + k^2/4xi^2) G~^
-//   stresslet  A_jlm = -i[(k_m d_jl + k_j d_lm + k_l d_mj) k^2 - 2 k_j k_l k_m](1 + k^2/4xi^2) G~^
-//   rotlet     A_jl  = -i eps_jlm k_m G~^
-// The odd symbols are the transform of the kernel under f^(k) = int f e^{-ik.x}
-// (d/dx_m -> +i k_m), and the rotlet is the definition eps_jlm r_m / r^3.
-// The constant `norm` folds in the inverse-FFT normalisation 1/Mf^3, the
-// quadrature weight h^3 (Section 5.2 step 5) and the two Gaussian prefactors
-// (2 xi^2/(pi eta))^{3/2} of eqs. Hx and u_integr.
-// Memory-bound: reads nc complex values and writes 3 per k-point, in place.
-#include "se_internal.cuh"
+// Step 3 of Section 5.2 (scaling, eq. gridfcnsc) as a pass over the spectrum
+// (the multipliers are in multiplier.cuh).  Memory-bound: reads nc complex
+// values and writes 3 per k-point, in place.
+#include "multiplier.cuh"
 
 namespace se {
 
 namespace {
-
-__device__ __forceinline__ float sexp(float v) { return expf(v); }
-__device__ __forceinline__ double sexp(double v) { return exp(v); }
 
 // Half-spectrum point idx of the [kz][ky][kx] R2C layout: its wave vector and
 // the index of |k| in the stored octant of the precomputed kernel.
@@ -28,13 +14,7 @@ __device__ __forceinline__ size_t kpoint(const ScaleConst &sc, size_t idx, T kv[
     const int kx = idx % sc.nxh;
     const int ky = (idx / sc.nxh) % sc.mf[1];
     const int kz = idx / ((size_t)sc.nxh * sc.mf[1]);
-    const int bx = (kx == sc.mt[0]) ? -sc.mt[0] : kx;
-    const int by = (ky < sc.mt[1]) ? ky : ky - sc.mf[1];
-    const int bz = (kz < sc.mt[2]) ? kz : kz - sc.mf[2];
-    kv[0] = (T)sc.dk[0] * bx;
-    kv[1] = (T)sc.dk[1] * by;
-    kv[2] = (T)sc.dk[2] * bz;
-    return ((size_t)abs(bz) * (sc.mt[1] + 1) + abs(by)) * (sc.mt[0] + 1) + abs(bx);
+    return kpoint3<T>(sc, kx, ky, kz, kv);
 }
 
 __host__ __device__ inline size_t half_spectrum(const ScaleConst &sc) {
@@ -59,66 +39,13 @@ __device__ __forceinline__ void scale_point(const ScaleConst &sc, const T *__res
     }
     T kv[3];
     const T G = ghat[kpoint<T>(sc, idx, kv)];
-    T k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
-    T F = (T)sc.norm * G * sexp((T)sc.ecoef * k2);
-    if (KERNEL != SE_ROTLET) F *= (T(1) + k2 * (T)sc.inv4xi2);
     constexpr int NCG = (KERNEL == SE_STRESSLET) ? 6 : 3;
     for (int grp = 0; grp < ngroups; grp++) {
         C *w0 = spec + (size_t)grp * NCG * nk + off;
-        if (KERNEL == SE_STOKESLET) {
-            C g[3];
-            for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
-            C kg;
-            kg.x = kv[0] * g[0].x + kv[1] * g[1].x + kv[2] * g[2].x;
-            kg.y = kv[0] * g[0].y + kv[1] * g[1].y + kv[2] * g[2].y;
-            for (int j = 0; j < 3; j++) {
-                C o;
-                o.x = -F * (k2 * g[j].x - kv[j] * kg.x);
-                o.y = -F * (k2 * g[j].y - kv[j] * kg.y);
-                w0[j * nk] = o;
-            }
-        } else if (KERNEL == SE_ROTLET) {
-            C g[3];
-            for (int c = 0; c < 3; c++) g[c] = w0[c * nk];
-            // (g x k)_j = eps_jlm g_l k_m ; multiply by -i F: (a + ib)(-i) = b - ia
-            C cr[3];
-            cr[0].x = g[1].x * kv[2] - g[2].x * kv[1];
-            cr[0].y = g[1].y * kv[2] - g[2].y * kv[1];
-            cr[1].x = g[2].x * kv[0] - g[0].x * kv[2];
-            cr[1].y = g[2].y * kv[0] - g[0].y * kv[2];
-            cr[2].x = g[0].x * kv[1] - g[1].x * kv[0];
-            cr[2].y = g[0].y * kv[1] - g[1].y * kv[0];
-            for (int j = 0; j < 3; j++) {
-                C o;
-                o.x = F * cr[j].y;
-                o.y = -F * cr[j].x;
-                w0[j * nk] = o;
-            }
-        } else {
-            // symmetric source s: xx, yy, zz, xy, xz, yz
-            C s[6];
-            for (int c = 0; c < 6; c++) s[c] = w0[c * nk];
-            C sk[3], tr, ksk;
-            sk[0].x = s[0].x * kv[0] + s[3].x * kv[1] + s[4].x * kv[2];
-            sk[0].y = s[0].y * kv[0] + s[3].y * kv[1] + s[4].y * kv[2];
-            sk[1].x = s[3].x * kv[0] + s[1].x * kv[1] + s[5].x * kv[2];
-            sk[1].y = s[3].y * kv[0] + s[1].y * kv[1] + s[5].y * kv[2];
-            sk[2].x = s[4].x * kv[0] + s[5].x * kv[1] + s[2].x * kv[2];
-            sk[2].y = s[4].y * kv[0] + s[5].y * kv[1] + s[2].y * kv[2];
-            tr.x = s[0].x + s[1].x + s[2].x;
-            tr.y = s[0].y + s[1].y + s[2].y;
-            ksk.x = kv[0] * sk[0].x + kv[1] * sk[1].x + kv[2] * sk[2].x;
-            ksk.y = kv[0] * sk[0].y + kv[1] * sk[1].y + kv[2] * sk[2].y;
-            for (int j = 0; j < 3; j++) {
-                // b = k^2 (2 (s k)_j + k_j tr s) - 2 k_j (k.s.k); out = -i F b
-                T bx_ = k2 * (T(2) * sk[j].x + kv[j] * tr.x) - T(2) * kv[j] * ksk.x;
-                T by_ = k2 * (T(2) * sk[j].y + kv[j] * tr.y) - T(2) * kv[j] * ksk.y;
-                C o;
-                o.x = F * by_;
-                o.y = -F * bx_;
-                w0[j * nk] = o;
-            }
-        }
+        C g[NCG], o[3];
+        for (int c = 0; c < NCG; c++) g[c] = w0[c * nk];
+        apply_multiplier<T, KERNEL>(sc, kv, G, g, o);
+        for (int j = 0; j < 3; j++) w0[j * nk] = o[j];
     }
 }
 
@@ -145,7 +72,7 @@ __global__ void k_scale_adj_stresslet(ScaleConst sc, const T *__restrict__ ghat,
     T kv[3];
     const T G = ghat[kpoint<T>(sc, idx, kv)];
     const T k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
-    const T F = (T)sc.norm * G * sexp((T)sc.ecoef * k2) * (T(1) + k2 * (T)sc.inv4xi2);
+    const T F = (T)sc.norm * G * mexp((T)sc.ecoef * k2) * (T(1) + k2 * (T)sc.inv4xi2);
     C *w0 = spec + idx;
     C g[3];
     for (int c = 0; c < 3; c++) g[c] = w0[c * nk];

@@ -245,6 +245,7 @@ struct se_plan_s {
     // Mtilde planes that hold data or are read, and a 1D transform along z
     bool pruned = false;
     cufftHandle f2d = 0, i2d = 0, zc = 0;
+    void *zw = nullptr;  // FP32 pruned plans: twiddles of the fused z-transforms and scaling (zfft.cu)
     bool have_fwd = false, have_inv = false, have_fwd3 = false;
     cudaStream_t last_stream = nullptr;
     // overlapped evaluation (FP32): the Fourier part on a high-priority internal
@@ -346,6 +347,14 @@ cudaError_t launch_gather_adj_col(se_plan_s *p, cudaStream_t st, const float *V,
 // du/dx of the Fourier part on the shared-memory tiles (FP32 column plans)
 cudaError_t launch_gather_grad_col(se_plan_s *p, cudaStream_t st, const float *w_fwd, const float *w_adj,
                                    const float *f_orig, const float *q_orig, const float *g_orig, float *gx);
+// FP32 z-direction transforms fused with the scaling (zfft.cu): the fused
+// kernel handles FFT lengths n whose factors are 2, 3, 5, 7 with nc source
+// components; zfuse_twiddles allocates the table e^{-2 pi i t / n}
+constexpr int ZF_MAXPASS = 16;
+bool zfuse_supported(int n, int nc);
+cudaError_t zfuse_twiddles(int n, void **out);
+cudaError_t launch_zscale(const se_plan_s *p, cudaStream_t st, void *spec, int nc);
+
 // FP32 spreading on sub-tiles of 4 x 4 x 8 window starts (subtile.cu), P = 10 or 12;
 // the plan's tiles and binning are those of the column kernels
 bool sub_supported(int P);
