@@ -629,7 +629,9 @@ def run_ours(args, rank, world, dist):
     nk = Mf * Mf * (Mf // 2 + 1)
     stage_bytes = {
         "spread": N_POINTS * 32 + 2 * 3 * Mt**3 * 4,
-        "scale": nk * 48 + (Mt + 1) ** 3 * 4,
+        # the fused z-transforms and scaling: the Mtilde nonzero z-planes of the
+        # three spectra read and written once, and the kernel's octant
+        "scale": 2 * 3 * Mt * Mf * (Mf // 2 + 1) * 8 + (Mt + 1) ** 3 * 4,
         "gather": 3 * Mt**3 * 4 + N_POINTS * (16 + 12 + 12),
         "real": N_POINTS * (32 + 24),
     }
