@@ -157,17 +157,19 @@ __device__ float2 *zfft(float2 *A, float2 *B, int nsig, const ZRadices &zr, cons
     return A;
 }
 
-// Block (bx, ky) takes the columns kx = bx cb .. bx cb + cb - 1 of row ky.
-// spec: nc spectra of nk points ([kz][ky][kx], kx < nxh) whose z-planes below
-// nz hold the 2-D transforms; afterwards the three output spectra's planes
-// below nz hold the inverse z-transforms of the scaled values.
+__host__ __device__ bool factor(int n, ZRadices &zr);
+
+// The columns kx = kx0 .. kx0 + cb - 1 of row ky: element (c, kz, ky, kx) of
+// the spectra at base + c scs + kz szs + ky nxh + kx (kx < nxh), whose
+// z-planes below nz hold the 2-D transforms of the nc source components;
+// afterwards the planes below nz of the three output components hold the
+// inverse z-transforms of the scaled values.  zsm: n + 2 nc cb n float2 of
+// shared memory.
 template <int KERNEL>
-__global__ void __launch_bounds__(ZF_NT) k_zscale(ScaleConst sc, const float *__restrict__ ghat, float2 *spec,
-                                                  size_t nk, int nz, int nc, int cb, ZRadices zr,
-                                                  const float2 *__restrict__ Wg) {
-    extern __shared__ __align__(16) float2 zsm[];
-    const int n = zr.n, ky = blockIdx.y, kx0 = blockIdx.x * cb, tid = threadIdx.x;
-    const int nxh = sc.nxh, mf1 = sc.mf[1];
+__device__ __forceinline__ void zscale_body(const ScaleConst &sc, const float *__restrict__ ghat, float2 *base,
+                                            size_t scs, size_t szs, int nz, int nc, int cb, const ZRadices &zr,
+                                            const float2 *__restrict__ Wg, int ky, int kx0, float2 *zsm) {
+    const int n = zr.n, tid = threadIdx.x, nxh = sc.nxh;
     float2 *W = zsm, *A = zsm + n, *B = A + (size_t)nc * cb * n;
     for (int t = tid; t < n; t += ZF_NT) W[t] = Wg[t];
     // the columns' nonzero planes, zeros above (x fastest in global memory):
@@ -175,14 +177,14 @@ __global__ void __launch_bounds__(ZF_NT) k_zscale(ScaleConst sc, const float *__
     const int zstep = ZF_NT / cb, col = tid % cb, z0 = tid / cb, kx = kx0 + col;
     const bool colok = z0 < zstep && kx < nxh;
     for (int c = 0; c < nc; c++) {
-        const float2 *src = spec + (size_t)c * nk + (size_t)ky * nxh + kx;
+        const float2 *src = base + (size_t)c * scs + (size_t)ky * nxh + kx;
         float2 *dst = A + ((size_t)c * cb + col) * n;
         for (int zb = z0; zb < n && z0 < zstep; zb += ZF_LB * zstep) {
             float2 v[ZF_LB];
 #pragma unroll
             for (int u = 0; u < ZF_LB; u++) {
                 const int z = zb + u * zstep;
-                v[u] = (colok && z < nz) ? src[(size_t)z * mf1 * nxh] : make_float2(0.0f, 0.0f);
+                v[u] = (colok && z < nz) ? src[(size_t)z * szs] : make_float2(0.0f, 0.0f);
             }
 #pragma unroll
             for (int u = 0; u < ZF_LB; u++) {
@@ -200,40 +202,52 @@ __global__ void __launch_bounds__(ZF_NT) k_zscale(ScaleConst sc, const float *__
         float G[ZF_LB];
 #pragma unroll
         for (int u = 0; u < ZF_LB; u++) {
-            const int i = i0 + u * ZF_NT, col = i / n, kz = i - col * n, kx = kx0 + col;
+            const int i = i0 + u * ZF_NT, cl = i / n, kz = i - cl * n, kxx = kx0 + cl;
             float kv[3];
-            G[u] = (i < cb * n && kx < nxh) ? ghat[kpoint3<float>(sc, kx, ky, kz, kv)] : 0.0f;
+            G[u] = (i < cb * n && kxx < nxh) ? ghat[kpoint3<float>(sc, kxx, ky, kz, kv)] : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < ZF_LB; u++) {
-            const int i = i0 + u * ZF_NT, col = i / n, kz = i - col * n, kx = kx0 + col;
-            if (i >= cb * n || kx >= nxh) continue;
+            const int i = i0 + u * ZF_NT, cl = i / n, kz = i - cl * n, kxx = kx0 + cl;
+            if (i >= cb * n || kxx >= nxh) continue;
             float kv[3];
-            kpoint3<float>(sc, kx, ky, kz, kv);
+            kpoint3<float>(sc, kxx, ky, kz, kv);
             float2 g[6], o[3];
-            for (int c = 0; c < nc; c++) g[c] = F[((size_t)c * cb + col) * n + kz];
+            for (int c = 0; c < nc; c++) g[c] = F[((size_t)c * cb + cl) * n + kz];
             apply_multiplier<float, KERNEL>(sc, kv, G[u], g, o);
 #pragma unroll
-            for (int j = 0; j < 3; j++) F[((size_t)j * cb + col) * n + kz] = conj2(o[j]);
+            for (int j = 0; j < 3; j++) F[((size_t)j * cb + cl) * n + kz] = conj2(o[j]);
         }
     }
     __syncthreads();
     float2 *R = zfft(F, S, 3 * cb, zr, W);
     if (colok) {
         for (int j = 0; j < 3; j++) {
-            float2 *dst = spec + (size_t)j * nk + (size_t)ky * nxh + kx;
+            float2 *dst = base + (size_t)j * scs + (size_t)ky * nxh + kx;
             const float2 *src = R + ((size_t)j * cb + col) * n;
-            for (int z = z0; z < nz; z += zstep) dst[(size_t)z * mf1 * nxh] = conj2(src[z]);
+            for (int z = z0; z < nz; z += zstep) dst[(size_t)z * szs] = conj2(src[z]);
         }
     }
 }
 
-bool factor(int n, ZRadices &zr) {
+// One plan: block (bx, ky) takes the columns bx cb .. of row ky of the nc
+// spectra of nk points at spec ([kz][ky][kx]).
+template <int KERNEL>
+__global__ void __launch_bounds__(ZF_NT) k_zscale(ScaleConst sc, const float *__restrict__ ghat, float2 *spec,
+                                                  size_t nk, int nz, int nc, int cb, ZRadices zr,
+                                                  const float2 *__restrict__ Wg) {
+    extern __shared__ __align__(16) float2 zsm[];
+    zscale_body<KERNEL>(sc, ghat, spec, nk, (size_t)sc.mf[1] * sc.nxh, nz, nc, cb, zr, Wg, blockIdx.y,
+                        blockIdx.x * cb, zsm);
+}
+
+__host__ __device__ bool factor(int n, ZRadices &zr) {
     zr.n = n;
     zr.np = 0;
     int m = n;
-    for (int f : {4, 2, 3, 5, 7})
-        while (m % f == 0) {
+    const int fs[5] = {4, 2, 3, 5, 7};
+    for (int i = 0; i < 5; i++)
+        for (const int f = fs[i]; m % f == 0;) {
             if (zr.np == ZF_MAXPASS) return false;
             zr.r[zr.np++] = f;
             m /= f;
@@ -255,12 +269,16 @@ bool zfuse_supported(int n, int nc) {
     return n >= 2 && n <= 2 * ZF_NT && factor(n, zr) && (size_t)n * sizeof(float2) * (1 + 2 * (size_t)nc) <= ZF_SMEM;
 }
 
-cudaError_t zfuse_twiddles(int n, void **out) {
-    std::vector<float2> w(n);
+static void zfuse_table(int n, float2 *w) {
     for (int t = 0; t < n; t++) {
         const double a = -2.0 * M_PI * (double)t / (double)n;
         w[t] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
+}
+
+cudaError_t zfuse_twiddles(int n, void **out) {
+    std::vector<float2> w(n);
+    zfuse_table(n, w.data());
     cudaError_t e = cudaMalloc(out, n * sizeof(float2));
     if (e) return e;
     return cudaMemcpy(*out, w.data(), n * sizeof(float2), cudaMemcpyHostToDevice);
