@@ -168,6 +168,9 @@ def oracle_checks(chk):
         c = chk["fp32"]
         ref = direct.direct("stokeslet", c["x"], c["f"], targets=c["idx"])
         out["fp32"] = dict(rel_errors(c["u"], ref, 2e-6), targets=len(c["idx"]))
+        if "deterministic" in chk:  # the same points and targets, deterministic mode
+            out["stokeslet_deterministic"] = dict(rel_errors(chk["deterministic"]["u"], ref, 2e-6),
+                                                  targets=len(c["idx"]))
     if "fp64" in chk:
         c = chk["fp64"]
         out["fp64"] = dict(rel_errors(c["u"], c["ref"], 1e-10), targets=len(c["idx"]))
@@ -383,6 +386,30 @@ def run_other_configs(dev, flush, checks, x32=None, f32=None):
             "value": x32.shape[0] / (ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms,
             "params": {k: plan.params[k] for k in ("M", "P", "xi", "rc")}, "fft": plan.grid["Mf"][0],
             "stages_ms": st}
+        plan.close()
+        # the headline plan (FFT <= 256^3) in deterministic mode: stable bin
+        # order, atomic-free spreading, full-list real-space sum, in sequence
+        plan = se.Plan("stokeslet", x32.shape[0], BOX, prec="fp32", tol=2e-6, max_fft=256)
+        plan.set_deterministic(True)
+        u = torch.empty_like(x32)
+        ms = timed(lambda: plan.eval(x32, f32, out=u))
+        u1 = u.clone()
+        plan.eval(x32, f32, out=u)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(u, u1))
+        plan.set_timing(True)
+        plan.eval(x32, f32, out=u)
+        torch.cuda.synchronize()
+        st = plan.stage_times()
+        plan.check()
+        if "fp32" in checks:
+            checks["deterministic"] = {"u": u1[torch.as_tensor(checks["fp32"]["idx"], device=u1.device)]
+                                       .double().cpu().numpy()}
+        out["stokeslet_deterministic"] = {
+            "workload": "the headline workload (N = 1e6 uniform, FP32 at 2e-6, FFT <= 256^3) with "
+                        "se_plan_set_deterministic on",
+            "value": x32.shape[0] / (ms * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms,
+            "bit_identical_repeat": same, "stages_ms": st}
         plan.close()
     x, f, q = W.stresslet_blobs(500_000, 2)
     t = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)  # noqa: E731
@@ -682,7 +709,7 @@ def run_ours(args, rank, world, dist):
             if obj is not None and key in errors:
                 obj["error"] = errors[key]
         if others:
-            for key in ("stresslet_clustered", "rotlet_backward"):
+            for key in ("stresslet_clustered", "rotlet_backward", "stokeslet_deterministic"):
                 if key in others and key in errors:
                     others[key]["error"] = errors[key]
     line = {

@@ -202,6 +202,16 @@ cudaError_t launch_bin_set(se_plan_s *p, Buffers &b, int N, const T *x, const T 
     if ((e = launch_scan(b.cnt_t, (int)p->ntiles, st))) return e;
     if ((e = launch_scan(b.cnt_r, (int)p->ncells, st))) return e;
     p->launches += 2 + scan_launch_count((int)p->ntiles) + scan_launch_count((int)p->ncells);
+    if (p->deterministic) {
+        // slots by index within each bin instead of the atomic counters' order
+        if (N > p->rs_cap || !p->rs_scratch) return cudaErrorInvalidValue;
+        if ((e = launch_stable_slots(N, b.key_t, (int)p->ntiles, b.cnt_t, b.slot_t, p->rs_scratch, st,
+                                     &p->launches)))
+            return e;
+        if ((e = launch_stable_slots(N, b.key_r, (int)p->ncells, b.cnt_r, b.slot_r, p->rs_scratch, st,
+                                     &p->launches)))
+            return e;
+    }
     k_bin_scatter<T><<<gs, bs, 0, st>>>(N, x, f, q, b.cnt_t, b.slot_t, b.key_t, b.cnt_r, b.slot_r, b.key_r, b.tag_t,
                                         b.tag_r, (vec4<T> *)b.xs_t, (vec4<T> *)b.fs_t, (vec4<T> *)b.qs_t, b.perm_t,
                                         (vec4<T> *)b.xs_r, (vec4<T> *)b.fs_r, (vec4<T> *)b.qs_r, b.perm_r);

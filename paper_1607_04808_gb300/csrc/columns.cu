@@ -452,6 +452,37 @@ __device__ __forceinline__ void c2_flush(const GP<float> &g, int gx, int gy, int
     }
 }
 
+// Deterministic plans: store the thread's column (cx, cy) of the tile's padded
+// block, all PT z planes, in the tile's slot tbt of the tile buffer (no
+// atomics; k_merge_tiles adds the tiles later in a fixed order); the threads
+// tid < PT (XB - PT) zero the row padding.
+template <int P, int TE>
+__device__ __forceinline__ void c2_flush_tb(int tid, int cx, int cy, const float2 (&a0)[C2Cfg<P, TE>::ZP],
+                                            const float2 (&a1)[C2Cfg<P, TE>::ZP],
+                                            const float2 (&a2)[C2Cfg<P, TE>::ZP], float *__restrict__ tbt) {
+    using B = TileBufCfg<P>;
+    constexpr int PT = C2Cfg<P, TE>::PT, ZP = C2Cfg<P, TE>::ZP, NPAD = B::XB - PT;
+    static_assert(TE == COL_TE && B::PE == PT, "the tile buffer holds the kernel's padded block");
+    if (tid < PT * PT) {
+#pragma unroll
+        for (int q = 0; q < ZP; q++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int z = 2 * q + h;
+                if (z < PT) {
+                    float *pz = tbt + ((size_t)z * PT + cy) * B::XB + cx;
+                    pz[0] = h ? a0[q].y : a0[q].x;
+                    pz[(size_t)PT * PT * B::XB] = h ? a1[q].y : a1[q].x;
+                    pz[(size_t)2 * PT * PT * B::XB] = h ? a2[q].y : a2[q].x;
+                }
+            }
+    }
+    if (NPAD > 0 && tid < PT * NPAD) {
+        const int y = tid / NPAD, x = PT + tid % NPAD;
+        for (int cz = 0; cz < 3 * PT; cz++) tbt[((size_t)cz * PT + y) * B::XB + x] = 0.0f;
+    }
+}
+
 // The column a thread owns: (cx, cy) of the block for tid < PT^2; the others
 // (the last warp's tail) take column 0 for their reads and never write.
 template <int P, int TE>
@@ -471,7 +502,7 @@ __device__ __forceinline__ void spread_c2_body(const GP<float> &g, int tile, int
                                                const float4 *__restrict__ xs, const float4 *__restrict__ fs,
                                                int fstride, int foff, const float4 *__restrict__ qs,
                                                float *__restrict__ grid, size_t gzs, size_t gcs,
-                                               C2Stage<P, TE> *S) {
+                                               C2Stage<P, TE> *S, float *__restrict__ tbt = nullptr) {
     using C = C2Cfg<P, TE>;
     constexpr int PT = C::PT, ZP = C::ZP, NB = C::NB;
     const int tid = threadIdx.x;
@@ -493,7 +524,10 @@ __device__ __forceinline__ void spread_c2_body(const GP<float> &g, int tile, int
         c2_accumulate<P, TE>(S[k], nb, cx, cy, cyl, cyh, a0, a1, a2);
         __syncthreads();
     }
-    if (tid < PT * PT) c2_flush<P, TE>(g, gx0 + cx, gy0 + cy, gz0, a0, a1, a2, grid + (size_t)c0 * gcs, gzs, gcs);
+    if (tbt)
+        c2_flush_tb<P, TE>(tid, cx, cy, a0, a1, a2, tbt);
+    else if (tid < PT * PT)
+        c2_flush<P, TE>(g, gx0 + cx, gy0 + cy, gz0, a0, a1, a2, grid + (size_t)c0 * gcs, gzs, gcs);
 }
 
 // w: three grids (the group of right-hand side r); u, f_orig: n_rhs three-vectors per point.
@@ -1067,14 +1101,18 @@ __global__ void __launch_bounds__(C2Cfg<P, TE>::NT, P <= 12 ? SE_C2_MINB : 1) k_
                                                                                 const float4 *__restrict__ xs,
                                                                                 const float4 *__restrict__ fs,
                                                                                 const float4 *__restrict__ qs,
-                                                                                float *__restrict__ grid) {
+                                                                                float *__restrict__ grid,
+                                                                                float *__restrict__ tb) {
     extern __shared__ __align__(16) unsigned char c2_smem[];
     const int tile = blockIdx.x;
     const int beg = tile_start[tile], end = tile_start[tile + 1];
     if (beg == end) return;
     const size_t Mf = g.mf[0], Mf2 = Mf * g.mf[1];
+    float *tbt = nullptr;
+    if constexpr (TE == COL_TE)
+        if (tb) tbt = tb + (size_t)tile * TileBufCfg<P>::FLOATS;
     spread_c2_body<P, TE>(g, tile, beg, end, c0, stress, xs, fs, 1, 0, qs, grid, Mf2, Mf2 * g.mf[2],
-                          reinterpret_cast<C2Stage<P, TE> *>(c2_smem));
+                          reinterpret_cast<C2Stage<P, TE> *>(c2_smem), tbt);
 }
 
 template <int P, int TE>
@@ -1263,14 +1301,15 @@ cudaError_t with_p(int P, A... a) {
 
 template <int P, int TE>
 struct SpreadRun {
+    // tb: the tile buffer of a deterministic plan (the paired kernel only), else NULL
     static cudaError_t run(const GP<float> g, int ntiles, int c0, bool stress, const int *ts, const float4 *xs,
-                           const float4 *fs, const float4 *qs, float *grid, cudaStream_t st) {
-        if (SE_SPREAD_PAIR) {
+                           const float4 *fs, const float4 *qs, float *grid, float *tb, cudaStream_t st) {
+        if (SE_SPREAD_PAIR || tb) {
             constexpr size_t smem = c2_smem_bytes<P, TE>();
             cudaError_t e =
                 cudaFuncSetAttribute(k_spread_c2<P, TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e) return e;
-            k_spread_c2<P, TE><<<ntiles, C2Cfg<P, TE>::NT, smem, st>>>(g, c0, stress, ts, xs, fs, qs, grid);
+            k_spread_c2<P, TE><<<ntiles, C2Cfg<P, TE>::NT, smem, st>>>(g, c0, stress, ts, xs, fs, qs, grid, tb);
         } else {
             k_spread_col<P, TE><<<ntiles, ColCfg<P, TE>::NT, 0, st>>>(g, c0, stress, ts, xs, fs, qs, grid);
         }
@@ -1432,22 +1471,39 @@ struct BGatherRun {
 
 bool col_supported(int prec, int P) { return prec == SE_FP32 && P >= 4 && P <= 16 && (P % 2) == 0; }
 
-cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
-                              void *grid, int nc) {
-    // nc = 3: f; nc = 6: the symmetric stresslet source in two passes of three
+bool spread_uses_sub(const se_plan_s *p) {
     // sub-tiles pay off from about 100 points per 8^3 tile on (N = 1e6: 296
     // per tile at M = 114, 0.95 -> 0.59 ms; 94 at M = 168, 1.06 ms both ways)
-    const bool sub = SE_SPREAD_SUB && sub_supported(p->P) && p->N >= 128 * (int64_t)p->ntiles;
+    return SE_SPREAD_SUB && p->colk && sub_supported(p->P) && p->N >= 128 * (int64_t)p->ntiles;
+}
+
+cudaError_t launch_spread_col(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
+                              void *grid, int nc) {
+    // nc = 3: f; nc = 6: the symmetric stresslet source in two passes of three.
+    // Deterministic plans: each tile's padded block goes to the tile buffer and
+    // a second kernel adds the tiles into the grid in a fixed order, no
+    // atomics (the caller skips the zeroing)
+    const bool sub = spread_uses_sub(p);
+    const bool det = p->deterministic && p->tilebuf;
     for (int c0 = 0; c0 < nc; c0 += 3) {
-        cudaError_t e = sub
-                            ? launch_spread_sub(p->gpf, p->ntiles, c0, nc == 6, (const int *)p->b.cnt_t,
-                                                (const float4 *)xs, (const float4 *)fs, (const float4 *)qs,
-                                                (float *)grid, st)
-                            : with_p<SpreadRun>(p->P, p->gpf, p->ntiles, c0, nc == 6, (const int *)p->b.cnt_t,
-                                                (const float4 *)xs, (const float4 *)fs, (const float4 *)qs,
-                                                (float *)grid, st);
+        cudaError_t e;
+        const int *ts = (const int *)p->b.cnt_t;
+        if (sub && det) {
+            e = launch_spread_sub_tb(p->gpf, p->ntiles, c0, nc == 6, ts, (const float4 *)xs, (const float4 *)fs,
+                                     (const float4 *)qs, p->tilebuf, st);
+        } else if (sub) {
+            e = launch_spread_sub(p->gpf, p->ntiles, c0, nc == 6, ts, (const float4 *)xs, (const float4 *)fs,
+                                  (const float4 *)qs, (float *)grid, st);
+        } else {
+            e = with_p<SpreadRun>(p->P, p->gpf, p->ntiles, c0, nc == 6, ts, (const float4 *)xs, (const float4 *)fs,
+                                  (const float4 *)qs, (float *)grid, det ? p->tilebuf : nullptr, st);
+        }
         if (e) return e;
         p->launches++;
+        if (det) {
+            if ((e = launch_merge_tiles(p->gpf, ts, p->tilebuf, (float *)grid, c0, st))) return e;
+            p->launches++;
+        }
     }
     return cudaSuccess;
 }

@@ -2,6 +2,7 @@
 // L = sum g . u for the backward pass.
 //   bin -> spread (step 1) -> R2C FFT (step 2) -> scale (step 3) -> C2R FFT
 //   (step 4) -> gather + self (step 5, eq. Slimit) -> real-space sum (Section 6)
+#include <algorithm>
 #include <string>
 
 #include "se_internal.cuh"
@@ -343,6 +344,46 @@ static se_status_t ensure_targets(se_plan_s *p, int64_t Nt) {
     }
     b.status = p->b.status;
     p->nt_cap = Nt;
+    if (p->deterministic && Nt > p->rs_cap) {
+        int *rs = nullptr;
+        if (cudaMalloc(&rs, stable_scratch_ints(Nt) * sizeof(int))) {
+            cudaGetLastError();
+            return fail(SE_ERR_OOM, "se_eval_targets: scratch of the stable bin order");
+        }
+        cudaFree(p->rs_scratch);
+        p->rs_scratch = rs;
+        p->rs_cap = Nt;
+    }
+    return SE_OK;
+}
+
+extern "C" se_status_t se_plan_set_deterministic(se_plan_t p, int on) {
+    if (!p) return fail(SE_ERR_INVALID_ARG, "se_plan_set_deterministic: NULL plan");
+    if (!on) {
+        p->deterministic = false;
+        return SE_OK;
+    }
+    if (p->prec != SE_FP32 || p->periodic || !p->colk)
+        return fail(SE_ERR_NOT_SUPPORTED,
+                    "se_plan_set_deterministic: FP32 free-space plans with the register-column kernels only");
+    const int64_t cap = std::max<int64_t>(p->N, p->nt_cap);
+    cudaDeviceSynchronize();
+    if (cap > p->rs_cap) {
+        int *rs = nullptr;
+        if (cudaMalloc(&rs, stable_scratch_ints(cap) * sizeof(int))) {
+            cudaGetLastError();
+            return fail(SE_ERR_OOM, "se_plan_set_deterministic: scratch of the stable bin order");
+        }
+        cudaFree(p->rs_scratch);
+        p->rs_scratch = rs;
+        p->rs_cap = cap;
+    }
+    if (!p->tilebuf && cudaMalloc(&p->tilebuf, tilebuf_floats(p->P, p->ntiles) * sizeof(float))) {
+        cudaGetLastError();
+        p->tilebuf = nullptr;
+        return fail(SE_ERR_OOM, "se_plan_set_deterministic: tile buffer of the atomic-free spreading");
+    }
+    p->deterministic = true;
     return SE_OK;
 }
 

@@ -236,7 +236,7 @@ void free_plan(se_plan_s *p) {
                     p->spec2, p->tmp3, p->b.xs_t, p->b.fs_t, p->b.qs_t, p->b.perm_t, p->b.cnt_t, p->b.slot_t,
                     p->b.key_t, p->b.xs_r, p->b.fs_r, p->b.qs_r, p->b.perm_r, p->b.cnt_r, p->b.slot_r,
                     p->b.key_r, p->b.tag_t, p->b.tag_r, p->b.status, p->dx, p->df, p->dq, p->du, p->pgrid, p->b.rt,
-                    p->gsort, p->zw};
+                    p->gsort, p->zw, p->tilebuf, p->rs_scratch};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     void *tptrs[] = {p->bt.xs_t, p->bt.perm_t, p->bt.slot_t, p->bt.key_t, p->bt.tag_t, p->bt.cnt_t, p->bt.xs_r,

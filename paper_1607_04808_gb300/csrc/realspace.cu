@@ -1900,7 +1900,8 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u, 
         p->launches++;
         return cudaGetLastError();
     }
-    const bool sym = p->b.uj && SE_RS_SYM;
+    // (deterministic plans: the full lists, whose sums need no atomics)
+    const bool sym = p->b.uj && SE_RS_SYM && !p->deterministic;
     // targets per cluster: the symmetric kernel's or the full-list kernel's
     // (FP32 runs the transposed symmetric kernel, clusters of 8 targets)
     constexpr bool symc = sizeof(T) == 4 && SE_RS_SYMC;
@@ -2053,7 +2054,8 @@ cudaError_t launch_real(se_plan_s *p, cudaStream_t st, T *u, bool defer) {
 
 // The FP32 symmetric kernel can leave u alone (its sums in b.rt and b.uj).
 bool real_can_defer(const se_plan_s *p) {
-    return p->prec == SE_FP32 && !p->periodic && SE_RS_SYM && SE_RS_SYMC && p->b.uj && p->b.rt;
+    return p->prec == SE_FP32 && !p->periodic && SE_RS_SYM && SE_RS_SYMC && p->b.uj && p->b.rt &&
+           !p->deterministic;
 }
 
 template <typename T>

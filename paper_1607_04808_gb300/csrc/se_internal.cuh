@@ -246,6 +246,12 @@ struct se_plan_s {
     bool pruned = false;
     cufftHandle f2d = 0, i2d = 0, zc = 0;
     void *zw = nullptr;  // FP32 pruned plans: twiddles of the fused z-transforms and scaling (zfft.cu)
+    float *tilebuf = nullptr;  // deterministic plans: the tiles' padded blocks (atomic-free spreading)
+    // se_plan_set_deterministic: stable bin order, the atomic-free spreading,
+    // the full-list real-space kernel, no overlap
+    bool deterministic = false;
+    int *rs_scratch = nullptr;  // stable_scratch_ints(rs_cap) ints
+    int64_t rs_cap = 0;
     bool have_fwd = false, have_inv = false, have_fwd3 = false;
     cudaStream_t last_stream = nullptr;
     // overlapped evaluation (FP32): the Fourier part on a high-priority internal
@@ -362,6 +368,36 @@ cudaError_t launch_spread_sub(const GP<float> &g, int ntiles, int c0, bool stres
                               const float4 *xs, const float4 *fs, const float4 *qs, float *grid, cudaStream_t st);
 cudaError_t launch_bspread_sub(const BSys<float> *sys, const int4 *items, int nitems, int P, int n_rhs,
                                const int *tile_start, const float4 *xs, const float4 *fs, cudaStream_t st);
+// Tile buffer of the atomic-free spreading (deterministic plans): the three
+// components of a tile's padded block, (8 + P - 1)^3 grid points, z-major
+// planes of x rows padded to whole float4; tiles of COL_TE window starts.
+template <int P>
+struct TileBufCfg {
+    static constexpr int PE = COL_TE + P - 1;    // grid points per edge
+    static constexpr int XB = (PE + 3) / 4 * 4;  // row length
+    static constexpr int NQ = XB / 4;            // float4 per row
+    static constexpr size_t FLOATS = (size_t)3 * PE * PE * XB;
+};
+
+size_t tilebuf_floats(int P, int ntiles);
+// Atomic-free spreading: the tile kernels store each tile's padded block in
+// the tile buffer tb (k_spread_c2 with a tile buffer; on sub-tiles, P = 10 or
+// 12, the four sub-tiles of a tile as one cluster of CTAs add their blocks in a
+// fixed order), then launch_merge_tiles writes the corner [0, Mt)^3 of
+// components c0 .. c0 + 2 of `grid` from it, adding the tiles in a fixed order
+// (no zeroing needed before)
+cudaError_t launch_spread_sub_tb(const GP<float> &g, int ntiles, int c0, bool stress, const int *tile_start,
+                                 const float4 *xs, const float4 *fs, const float4 *qs, float *tb, cudaStream_t st);
+cudaError_t launch_merge_tiles(const GP<float> &g, const int *tile_start, const float *tb, float *grid, int c0,
+                               cudaStream_t st);
+// Stable slots (stable.cu): slot[i] = the rank of point i among the points
+// with its key and smaller indices, from the keys (< nkeys) and the bins'
+// starts; scratch holds stable_scratch_ints(N) ints
+size_t stable_scratch_ints(int64_t n);
+cudaError_t launch_stable_slots(int N, const int *keys, int nkeys, const int *start, int *slot, int *scratch,
+                                cudaStream_t st, int64_t *launches);
+// true when a plan's FP32 spreading runs on the sub-tiles (columns.cu)
+bool spread_uses_sub(const se_plan_s *p);
 cudaError_t launch_gather_sub(const GP<float> &g, int ntiles, const int *tile_start, const float4 *xs,
                               const int *perm, const float *w, const float *f_orig, double self_coef, float *u,
                               cudaStream_t st);

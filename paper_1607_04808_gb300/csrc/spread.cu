@@ -282,6 +282,8 @@ template <typename T>
 cudaError_t launch_spread(se_plan_s *p, cudaStream_t st, const void *xs, const void *fs, const void *qs,
                           void *grid, int nc) {
     cudaError_t e;
+    if (sizeof(T) == 4 && p->colk && p->deterministic && p->tilebuf)  // writes the whole corner
+        return launch_spread_col(p, st, xs, fs, qs, grid, nc);
     if ((e = launch_zero_octant<T>(p, st, grid, nc))) return e;
     if (sizeof(T) == 4 && p->colk) return launch_spread_col(p, st, xs, fs, qs, grid, nc);
     size_t smem = spread_smem_bytes(p, nc, sizeof(T));

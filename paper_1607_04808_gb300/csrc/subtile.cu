@@ -20,6 +20,8 @@
 // records whose support meets its rows: no per-point branch on oz and no
 // per-point test.  The columns go to the FFT input once per CTA through shared
 // memory with 16-byte vector atomics (sub-tiles overlap in their halos).
+#include <cooperative_groups.h>
+
 #include "se_internal.cuh"
 
 namespace se {
@@ -85,7 +87,7 @@ struct SubSmem {
         float F[3][SubCfg<P>::PZ][SubCfg<P>::PT][SubCfg<P>::FX];
     };
     unsigned short list[SubCfg<P>::CAP];
-    int cnt;
+    int wc[SubCfg<P>::NW];
 };
 
 // Stage the points list[b0 .. b0 + nb) of the round starting at tbeg (indices
@@ -238,31 +240,95 @@ __device__ __forceinline__ void sub_runs(const SubStage<P> &S, int ylo, int yhi,
 
 // The points of tile points rb .. rb + rn (window starts from the tags) that
 // lie in sub-tile (sx, sy) of the tile starting at (tx0, ty0): their offsets
-// from rb go to list, their count is returned.  Called by every thread of the
-// CTA (it holds two CTA barriers; the first also orders the previous round's
-// reads of the count before its reset).
+// from rb go to list in increasing order, their count is returned.  Each
+// chunk of NT points is compacted by warp ballots and a prefix over the
+// warps' counts, so the list does not depend on the order in which threads
+// run.  Called by every thread of the CTA (it holds CTA barriers; the first
+// also orders the previous round's reads of the list before it is rewritten).
 template <int NT>
 __device__ __forceinline__ int sub_filter(const int *__restrict__ tags, int rb, int rn, int tx0, int ty0, int sx,
-                                          int sy, unsigned short *list, int &s_cnt) {
-    const int tid = threadIdx.x;
-    __syncthreads();
-    if (tid == 0) s_cnt = 0;
-    __syncthreads();
-    for (int k = tid; k < rn; k += NT) {
-        int a, b, c;
-        unpack3(__ldg(tags + 4 * (size_t)(rb + k) + 3), a, b, c);
-        const int lx = min(max(a - tx0, 0), COL_TE - 1), ly = min(max(b - ty0, 0), COL_TE - 1);
-        if ((lx >> 2) == sx && (ly >> 2) == sy) list[atomicAdd(&s_cnt, 1)] = (unsigned short)k;
+                                          int sy, unsigned short *list, int *wc) {
+    constexpr int NWF = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int base = 0;
+    for (int k0 = 0; k0 < rn; k0 += NT) {
+        const int k = k0 + tid;
+        bool in = false;
+        if (k < rn) {
+            int a, b, c;
+            unpack3(__ldg(tags + 4 * (size_t)(rb + k) + 3), a, b, c);
+            const int lx = min(max(a - tx0, 0), COL_TE - 1), ly = min(max(b - ty0, 0), COL_TE - 1);
+            in = (lx >> 2) == sx && (ly >> 2) == sy;
+        }
+        const unsigned m = __ballot_sync(FULLM, in);
+        __syncthreads();
+        if (lane == 0) wc[w] = __popc(m);
+        __syncthreads();
+        int off = base, tot = 0;
+#pragma unroll
+        for (int i = 0; i < NWF; i++) {
+            const int c = wc[i];
+            off += (i < w) ? c : 0;
+            tot += c;
+        }
+        if (in) list[off + __popc(m & ((1u << lane) - 1u))] = (unsigned short)k;
+        base += tot;
     }
     __syncthreads();
-    return s_cnt;
+    return base;
+}
+
+
+// The four sub-tiles of a tile run as one cluster of CTAs (rank = sub-tile).
+// Once all four hold their columns in shared memory (F, rows of FX with zero
+// padding), CTA `sub` forms the planes pl = sub, sub + 4, ... of the tile's
+// padded block by adding the four sub-tiles' values from distributed shared
+// memory in a fixed order (sub-tile 0 to 3), and stores them to the tile
+// buffer tb.  The second cluster barrier keeps every CTA's shared memory alive
+// until the other three have read it.
+template <int P>
+__device__ __forceinline__ void tile_combine(SubSmem<P> &sm, float *__restrict__ tb, int sub) {
+    using C = SubCfg<P>;
+    using B = TileBufCfg<P>;
+    static_assert(C::PZ == B::PE, "a sub-tile's columns span the tile's z extent");
+    static_assert(C::FX % 4 == 0 && C::FX >= C::PT, "whole float4 rows in the flush buffer");
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    const float *Fs[4];
+#pragma unroll
+    for (int s = 0; s < 4; s++) Fs[s] = cl.map_shared_rank(&sm.F[0][0][0][0], (unsigned)s);
+    constexpr int PER = B::PE * B::NQ;  // float4 of one plane
+    const int npl = (3 * B::PE - sub + 3) / 4;
+    for (int i = threadIdx.x; i < npl * PER; i += C::NT) {
+        const int k = i / PER, r = i - k * PER;
+        const int pl = sub + 4 * k, y = r / B::NQ, x = 4 * (r - (r / B::NQ) * B::NQ);
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            const int yl = y - SUB * (s >> 1), xl = x - SUB * (s & 1);
+            if (yl >= 0 && yl < C::PT && xl >= 0 && xl + 4 <= C::FX) {
+                const float4 v =
+                    *reinterpret_cast<const float4 *>(Fs[s] + ((size_t)pl * C::PT + yl) * C::FX + xl);
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+            }
+        }
+        *reinterpret_cast<float4 *>(tb + ((size_t)pl * B::PE + y) * B::XB + x) = acc;
+    }
+    __threadfence();  // the block is visible to every CTA before the tile is signalled done
+    cl.sync();
 }
 
 // Spread the points [beg, end) of tile `tile` that lie in sub-tile `sub` (x
 // half sub & 1, y half sub >> 1) onto the three grids at grid + c0 gcs (z-plane
 // stride gzs, component stride gcs); the sources are fs[n * fstride + foff].
-// Called by every thread of the CTA.
-template <int P>
+// TB: the CTA is one of the tile's cluster of four, and the tile's padded block
+// goes to its tile buffer at `grid` instead (tile_combine).  Called by every
+// thread of the CTA.
+template <int P, bool TB = false>
 __device__ __forceinline__ void spread_sub_body(const GP<float> &g, int tile, int sub, int beg, int end, int c0,
                                                 bool stress, const float4 *__restrict__ xs,
                                                 const float4 *__restrict__ fs, const float4 *__restrict__ qs,
@@ -272,7 +338,6 @@ __device__ __forceinline__ void spread_sub_body(const GP<float> &g, int tile, in
     constexpr int ZP = C::ZP, TE = C::TE;
     SubStage<P> *S = sm.S;
     unsigned short *list = sm.list;
-    int &s_cnt = sm.cnt;
     const int tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / (g.nt[0] * g.nt[1]);
     const int sx = sub & 1, sy = sub >> 1;
     const int gx0 = tx * TE + SUB * sx, gy0 = ty * TE + SUB * sy, gz0 = tz * TE;
@@ -296,7 +361,7 @@ __device__ __forceinline__ void spread_sub_body(const GP<float> &g, int tile, in
     const int *tags = reinterpret_cast<const int *>(xs);
     for (int rb = beg; rb < end; rb += C::CAP) {
         // the round's points of this sub-tile (tile points rb .. rb + rn)
-        const int cnt = sub_filter<C::NT>(tags, rb, min(C::CAP, end - rb), tx * TE, ty * TE, sx, sy, list, s_cnt);
+        const int cnt = sub_filter<C::NT>(tags, rb, min(C::CAP, end - rb), tx * TE, ty * TE, sx, sy, list, sm.wc);
         if (cnt > 0) {
             sub_stage<P>(S[0], g, xs, fs, qs, fstride, foff, c0, stress, list, rb, 0, min(C::NB, cnt), gx0, gy0,
                          gz0);
@@ -335,6 +400,10 @@ __device__ __forceinline__ void spread_sub_body(const GP<float> &g, int tile, in
         (&sm.F[0][0][0][0])[r * C::FX + C::PT + (i - r * NPAD)] = 0.0f;
     }
     __syncthreads();
+    if constexpr (TB) {
+        tile_combine<P>(sm, grid, sub);
+        return;
+    }
     float *gbase = grid + (size_t)c0 * gcs;
     const bool vec = ((g.mf[0] | gzs | gcs) & 3) == 0 && (reinterpret_cast<size_t>(gbase) & 15) == 0;
     // thread -> (plane parity, row y, float4 xq) of the (component, z) planes,
@@ -385,6 +454,83 @@ __global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
                        *reinterpret_cast<SubSmem<P> *>(sub_smem_raw));
 }
 
+// The float4 at grid (x4, y, z) of component c, x4 a multiple of 4: the sum,
+// in a fixed order (tiles by z, then y, then x), of the tile-buffer values of
+// the tiles whose padded blocks hold it; a tile without points adds nothing.
+template <int P>
+__device__ __forceinline__ float4 merge_point4(const GP<float> &g, const int *__restrict__ tile_start,
+                                               const float *__restrict__ tb, int c, int z, int y, int x4) {
+    using B = TileBufCfg<P>;
+    constexpr int TE = COL_TE;
+    // tiles t with t TE <= z < t TE + PE (truncating division: a negative
+    // numerator gives at most 0, clamped to 0); in x the float4 lies inside
+    // the tile's row: t TE <= x4 <= t TE + XB - 4
+    const int tz0 = max(0, (z - B::PE + TE) / TE), tz1 = min(g.nt[2] - 1, z / TE);
+    const int ty0 = max(0, (y - B::PE + TE) / TE), ty1 = min(g.nt[1] - 1, y / TE);
+    const int tx0 = max(0, (x4 - B::XB + 4 + TE - 1) / TE), tx1 = min(g.nt[0] - 1, x4 / TE);
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int tz = tz0; tz <= tz1; tz++)
+        for (int ty = ty0; ty <= ty1; ty++) {
+            const int trow = (tz * g.nt[1] + ty) * g.nt[0];
+            for (int tx = tx0; tx <= tx1; tx++) {
+                const int t = trow + tx;
+                if (__ldg(tile_start + t) == __ldg(tile_start + t + 1)) continue;
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(
+                    tb + (size_t)t * B::FLOATS +
+                    (((size_t)c * B::PE + (z - TE * tz)) * B::PE + (y - TE * ty)) * B::XB + (x4 - TE * tx)));
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+            }
+        }
+    return acc;
+}
+
+// Atomic-free variant: the four sub-tiles of a tile form a cluster, and the
+// tile's padded block goes to its slot of the tile buffer tb (three
+// components); k_merge_tiles then writes the grids.
+template <int P>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
+    k_spread_sub_tb(GP<float> g, int c0, bool stress, const int *__restrict__ tile_start,
+                    const float4 *__restrict__ xs, const float4 *__restrict__ fs, const float4 *__restrict__ qs,
+                    float *__restrict__ tb) {
+    extern __shared__ __align__(16) unsigned char sub_smem_raw[];
+    const int tile = blockIdx.x >> 2;
+    const int beg = tile_start[tile], end = tile_start[tile + 1];
+    if (beg == end) return;  // the whole cluster (one tile) returns
+    spread_sub_body<P, true>(g, tile, blockIdx.x & 3, beg, end, c0, stress, xs, fs, qs, 1, 0,
+                             tb + (size_t)tile * TileBufCfg<P>::FLOATS, 0, 0,
+                             *reinterpret_cast<SubSmem<P> *>(sub_smem_raw));
+}
+
+// Second pass of the atomic-free flush: every grid point of the corner [0,
+// Mt)^3 of the three grids at `grid` is written once from the tile buffer
+// (merge_point4), without atomics and without zeroing the grid first, so its
+// values do not depend on the order in which CTAs ran.  Thread (threadIdx.x,
+// row): the float4 at x = 4 threadIdx.x (+ 4 blockDim.x ...) of x row `row` =
+// (c Mt_z + z) Mt_y + y.
+template <int P>
+__global__ void k_merge_tiles(GP<float> g, const int *__restrict__ tile_start, const float *__restrict__ tb,
+                              float *__restrict__ grid, size_t gzs, size_t gcs, bool vec) {
+    const size_t row = (size_t)blockIdx.x * blockDim.y + threadIdx.y;
+    if (row >= (size_t)3 * g.mt[1] * g.mt[2]) return;
+    const int y = (int)(row % g.mt[1]), z = (int)((row / g.mt[1]) % g.mt[2]);
+    const int c = (int)(row / ((size_t)g.mt[1] * g.mt[2]));
+    float *out = grid + (size_t)c * gcs + (size_t)z * gzs + (size_t)y * g.mf[0];
+    for (int x4 = 4 * threadIdx.x; x4 < g.mt[0]; x4 += 4 * blockDim.x) {
+        const float4 acc = merge_point4<P>(g, tile_start, tb, c, z, y, x4);
+        if (vec && x4 + 3 < g.mt[0]) {
+            *reinterpret_cast<float4 *>(out + x4) = acc;
+        } else {
+            out[x4] = acc.x;
+            if (x4 + 1 < g.mt[0]) out[x4 + 1] = acc.y;
+            if (x4 + 2 < g.mt[0]) out[x4 + 2] = acc.z;
+            if (x4 + 3 < g.mt[0]) out[x4 + 3] = acc.w;
+        }
+    }
+}
+
 // Batches: one CTA per (system, tile, sub-tile) with the right-hand sides
 // inside: block b takes sub-tile b mod 4 of item (b / 4) n_rhs of the (system,
 // tile, rhs) list (right-hand side innermost) and spreads each right-hand side
@@ -423,7 +569,7 @@ struct SubGSmem {
     SubStage<P> S;
     float part[SubCfg<P>::NW][SubCfg<P>::NB][3];  // each warp's part of each point of the batch
     unsigned short list[SubCfg<P>::CAP];
-    int cnt;
+    int wc[SubCfg<P>::NW];
 };
 
 // The point's sums over the thread's two columns: v[c] = sum_r wx wy_r sum_k wz_k G[r][c][z_k]
@@ -552,7 +698,7 @@ __global__ void __launch_bounds__(SubCfg<P>::NT, SE_SUB_MINB)
     const int *tags = reinterpret_cast<const int *>(xs);
     for (int rb = beg; rb < end; rb += C::CAP) {
         const int cnt = sub_filter<C::NT>(tags, rb, min(C::CAP, end - rb), tx * TE, ty * TE, sx, sy, sm.list,
-                                          sm.cnt);
+                                          sm.wc);
         for (int b0 = 0; b0 < cnt; b0 += C::NB) {
             const int nb = min(C::NB, cnt - b0);
             sub_stage<P, true>(sm.S, g, xs, nullptr, nullptr, 1, 0, 0, false, sm.list, rb, b0, nb, gx0, gy0, gz0);
@@ -586,6 +732,29 @@ cudaError_t run_spread_sub(const GP<float> &g, int ntiles, int c0, bool stress, 
     if (e) return e;
     const size_t gzs = (size_t)g.mf[0] * g.mf[1], gcs = gzs * g.mf[2];
     k_spread_sub<P><<<4 * ntiles, SubCfg<P>::NT, smem, st>>>(g, c0, stress, ts, xs, fs, qs, grid, gzs, gcs);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t run_spread_sub_tb(const GP<float> &g, int ntiles, int c0, bool stress, const int *ts, const float4 *xs,
+                              const float4 *fs, const float4 *qs, float *tb, cudaStream_t st) {
+    constexpr size_t smem = sizeof(SubSmem<P>);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_spread_sub_tb<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    k_spread_sub_tb<P><<<4 * ntiles, SubCfg<P>::NT, smem, st>>>(g, c0, stress, ts, xs, fs, qs, tb);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t run_merge_tiles(const GP<float> &g, const int *ts, const float *tb, float *grid, int c0,
+                            cudaStream_t st) {
+    const size_t gzs = (size_t)g.mf[0] * g.mf[1], gcs = gzs * g.mf[2];
+    float *gbase = grid + (size_t)c0 * gcs;
+    const bool vec = ((g.mf[0] | gzs | gcs) & 3) == 0 && (reinterpret_cast<size_t>(gbase) & 15) == 0;
+    const size_t rows = (size_t)3 * g.mt[1] * g.mt[2];
+    const dim3 bs(32, 8);
+    k_merge_tiles<P><<<(unsigned)((rows + bs.y - 1) / bs.y), bs, 0, st>>>(g, ts, tb, gbase, gzs, gcs, vec);
     return cudaGetLastError();
 }
 
@@ -626,6 +795,40 @@ cudaError_t launch_spread_sub(const GP<float> &g, int ntiles, int c0, bool stres
                               const float4 *xs, const float4 *fs, const float4 *qs, float *grid, cudaStream_t st) {
     if (g.P == 12) return run_spread_sub<12>(g, ntiles, c0, stress, tile_start, xs, fs, qs, grid, st);
     if (g.P == 10) return run_spread_sub<10>(g, ntiles, c0, stress, tile_start, xs, fs, qs, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+size_t tilebuf_floats(int P, int ntiles) {
+    switch (P) {
+        case 4: return TileBufCfg<4>::FLOATS * (size_t)ntiles;
+        case 6: return TileBufCfg<6>::FLOATS * (size_t)ntiles;
+        case 8: return TileBufCfg<8>::FLOATS * (size_t)ntiles;
+        case 10: return TileBufCfg<10>::FLOATS * (size_t)ntiles;
+        case 12: return TileBufCfg<12>::FLOATS * (size_t)ntiles;
+        case 14: return TileBufCfg<14>::FLOATS * (size_t)ntiles;
+        case 16: return TileBufCfg<16>::FLOATS * (size_t)ntiles;
+        default: return 0;
+    }
+}
+
+cudaError_t launch_merge_tiles(const GP<float> &g, const int *tile_start, const float *tb, float *grid, int c0,
+                               cudaStream_t st) {
+    switch (g.P) {
+        case 4: return run_merge_tiles<4>(g, tile_start, tb, grid, c0, st);
+        case 6: return run_merge_tiles<6>(g, tile_start, tb, grid, c0, st);
+        case 8: return run_merge_tiles<8>(g, tile_start, tb, grid, c0, st);
+        case 10: return run_merge_tiles<10>(g, tile_start, tb, grid, c0, st);
+        case 12: return run_merge_tiles<12>(g, tile_start, tb, grid, c0, st);
+        case 14: return run_merge_tiles<14>(g, tile_start, tb, grid, c0, st);
+        case 16: return run_merge_tiles<16>(g, tile_start, tb, grid, c0, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_spread_sub_tb(const GP<float> &g, int ntiles, int c0, bool stress, const int *tile_start,
+                                 const float4 *xs, const float4 *fs, const float4 *qs, float *tb, cudaStream_t st) {
+    if (g.P == 12) return run_spread_sub_tb<12>(g, ntiles, c0, stress, tile_start, xs, fs, qs, tb, st);
+    if (g.P == 10) return run_spread_sub_tb<10>(g, ntiles, c0, stress, tile_start, xs, fs, qs, tb, st);
     return cudaErrorInvalidValue;
 }
 

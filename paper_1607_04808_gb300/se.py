@@ -103,6 +103,8 @@ def lib():
             L.se_plan_set_overlap.argtypes = [vp, i32]
             L.se_plan_set_keep_grid.restype = i32
             L.se_plan_set_keep_grid.argtypes = [vp, i32]
+            L.se_plan_set_deterministic.restype = i32
+            L.se_plan_set_deterministic.argtypes = [vp, i32]
             L.se_plan_set_test_flags.restype = i32
             L.se_plan_set_test_flags.argtypes = [vp, i32]
             L.se_plan_stage_times.restype = i32
@@ -297,6 +299,11 @@ class Plan:
         """se_plan_set_keep_grid: the backward reuses the last evaluation's grid
         when given the same x, f (, q) tensors (their contents unchanged)."""
         _check(lib().se_plan_set_keep_grid(self._h, 1 if on else 0))
+
+    def set_deterministic(self, on: bool = True):
+        """se_plan_set_deterministic: bit-identical results call after call
+        (stable bin order, atomic-free spreading, full-list real-space sum)."""
+        _check(lib().se_plan_set_deterministic(self._h, 1 if on else 0))
 
     def set_test_flags(self, flags: int):
         """se_plan_set_test_flags (tests of the failure path; 0 restores normal operation)."""
