@@ -681,6 +681,10 @@ def run_ours(args, rank, world, dist):
             stage_roofline[k] = {"bound": bound, "achieved": a, "peak": peak, "unit": unit, "frac": a / peak}
             if unit == "TFLOP/s" and probe.get("fp32_fma_tflops"):
                 stage_roofline[k]["frac_of_measured"] = a / probe["fp32_fma_tflops"]
+    if "scale" in stage_roofline:
+        stage_roofline["scale"]["note"] = ("the scaling fused with the transforms along z: its algorithmic bytes "
+                                           "against the copy rate; the kernel is bound by its shared-memory passes "
+                                           "(profiles/k_zscale_stokeslet_N1e6_fp32.md)")
     if batched is not None and batched.get("roofline", {}).get("achieved"):
         br = batched["roofline"]
         br.update(peak=alu_peak, frac=br["achieved"] / alu_peak, peak_measured=probe["fp32_fma_tflops"],
