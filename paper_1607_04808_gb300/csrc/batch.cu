@@ -503,6 +503,8 @@ extern "C" se_status_t se_batch_create(se_kernel_t kernel, int S, const int64_t 
     if (prec != SE_FP32 && prec != SE_FP64) return fail(SE_ERR_INVALID_ARG, "unknown precision");
     if (S < 1 || !N_s || !box_s) return fail(SE_ERR_INVALID_ARG, "se_batch_create: need S >= 1 systems");
     if (n_rhs < 1 || n_rhs > 64) return fail(SE_ERR_INVALID_ARG, "se_batch_create: n_rhs must be in [1, 64]");
+    if (prec == SE_FP64 && erfc_table_init() != cudaSuccess)
+        return fail(SE_ERR_CUDA, "the FP64 erfc table could not be copied to the device");
     int64_t tot = 0;
     for (int s = 0; s < S; s++) {
         if (N_s[s] < 1) return fail(SE_ERR_INVALID_ARG, "se_batch_create: every system needs N >= 1");

@@ -770,6 +770,10 @@ static se_status_t create_plan(se_kernel_t kernel, int64_t N, double xi, const d
             }
         }
     }
+    if (prec == SE_FP64 && erfc_table_init() != cudaSuccess) {
+        free_plan(p);
+        return fail(SE_ERR_CUDA, "the FP64 erfc table could not be copied to the device");
+    }
     for (int i = 0; i < 9; i++) cudaEventCreate(&p->ev[i]);
     cudaEventCreate(&p->ev_real);
     s = periodic ? periodic_octant(p) : precompute(p);

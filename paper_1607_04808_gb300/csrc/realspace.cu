@@ -296,15 +296,50 @@ __device__ __forceinline__ double erfc_fit64(double x, double e) {
     return erfc(x);
 }
 
-// FP64: the same multipliers from exp and erfc
+// FP64 table of erfc(x) and g(x) = (2/sqrt(pi)) x exp(-x^2) on [0, ERFT_XMAX]:
+// ERFT_N intervals of width h, on each the degree-ERFT_D polynomials in t =
+// 2 (x - x0) / h - 1 that interpolate both functions at the Chebyshev points
+// (coefficients from the discrete Chebyshev transform of the values there,
+// turned into powers of t), stored as (erfc, g) pairs, constant term first.
+// Both functions are analytic in x; the interpolation error is below 2e-15
+// absolute on the whole range and 5e-14 relative on [0, 5] (x = xi r <= xi
+// rc, about 4.7 on FP64 plans at 1e-10).  One 16-byte load and two FMAs per
+// degree replace exp, a division and the degree-18 erfcx fit.
+constexpr int ERFT_N = 256, ERFT_D = 7;
+constexpr double ERFT_XMAX = 8.0;
+__device__ double2 g_erft[ERFT_N * (ERFT_D + 1)];
+
+__device__ __forceinline__ void erfc_g_tab(double x, double &ec, double &g) {
+    const double s = x * (ERFT_N / ERFT_XMAX);
+    const int i = min((int)s, ERFT_N - 1);
+    const double t = 2.0 * (s - (double)i) - 1.0;
+    const double2 *c = g_erft + i * (ERFT_D + 1);
+    double2 v = __ldg(c + ERFT_D);
+#pragma unroll
+    for (int k = ERFT_D - 1; k >= 0; k--) {
+        const double2 ck = __ldg(c + k);
+        v.x = fma(v.x, t, ck.x);
+        v.y = fma(v.y, t, ck.y);
+    }
+    ec = v.x;
+    g = v.y;
+}
+
+// FP64: the same multipliers from erfc and the Gaussian term (the table, or
+// exp and the erfcx fit)
 template <int KERNEL, int PV>
 __device__ __forceinline__ void radial_ab(const RC<double> &rk, double r2, double &rinv, double &a, double &b) {
     rinv = rsqrt(r2);
     const double r = r2 * rinv;
     const double x = rk.xi * r;
-    const double e = exp(-x * x);
-    const double ec = erfc_fit64(x, e);
-    const double g = 1.1283791670955126 * x * e;  // (2/sqrt(pi)) x e
+    double ec, g;
+    if (rk.tab && x < ERFT_XMAX) {
+        erfc_g_tab(x, ec, g);
+    } else {
+        const double e = exp(-x * x);
+        ec = erfc_fit64(x, e);
+        g = 1.1283791670955126 * x * e;  // (2/sqrt(pi)) x e
+    }
     if (KERNEL == SE_STRESSLET) {
         a = -2.0 * (3.0 * ec + g * (3.0 + 2.0 * x * x)) * (rinv * rinv);
         b = 2.0 * rk.xi2 * g;
@@ -2014,6 +2049,62 @@ cudaError_t launch_breal_k(const BSys<T> *sys, const int *row_base, int S, int n
 
 }  // namespace
 
+// The table's coefficients, computed once on the host in FP64 from the C
+// library's erfc and exp, and whether each device holds them.
+static int g_erft_ready[64];
+
+static void erfc_table_host(std::vector<double> &tab) {
+    tab.assign(2 * ERFT_N * (ERFT_D + 1), 0.0);
+    constexpr int K = ERFT_D + 1;
+    // powers of t in T_0 .. T_D (T_{k+1} = 2 t T_k - T_{k-1})
+    double tp[K][K] = {};
+    tp[0][0] = 1.0;
+    if (K > 1) tp[1][1] = 1.0;
+    for (int k = 1; k + 1 < K; k++)
+        for (int m = 0; m < K; m++) tp[k + 1][m] = (m > 0 ? 2.0 * tp[k][m - 1] : 0.0) - tp[k - 1][m];
+    const double h = ERFT_XMAX / ERFT_N;
+    for (int i = 0; i < ERFT_N; i++) {
+        double fv[2][K], tj[K];
+        for (int j = 0; j < K; j++) {
+            tj[j] = cos(M_PI * (j + 0.5) / K);
+            const double x = i * h + 0.5 * (tj[j] + 1.0) * h;
+            fv[0][j] = erfc(x);
+            fv[1][j] = 2.0 / sqrt(M_PI) * x * exp(-x * x);
+        }
+        for (int f = 0; f < 2; f++) {
+            double cheb[K];
+            for (int k = 0; k < K; k++) {
+                double sum = 0.0;
+                for (int j = 0; j < K; j++) sum += fv[f][j] * cos(M_PI * k * (j + 0.5) / K);
+                cheb[k] = (k == 0 ? 1.0 : 2.0) * sum / K;
+            }
+            for (int m = 0; m < K; m++) {
+                double a = 0.0;
+                for (int k = 0; k < K; k++) a += cheb[k] * tp[k][m];
+                tab[2 * (i * K + m) + f] = a;
+            }
+        }
+    }
+}
+
+static int erfc_table_ready() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    return g_erft_ready[dev];
+}
+
+cudaError_t erfc_table_init() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    if (dev < 0 || dev >= 64 || g_erft_ready[dev]) return cudaSuccess;
+    static std::vector<double> tab;
+    if (tab.empty()) erfc_table_host(tab);
+    if ((e = cudaMemcpyToSymbol(g_erft, tab.data(), tab.size() * sizeof(double)))) return e;
+    g_erft_ready[dev] = 1;
+    return cudaSuccess;
+}
+
 template <typename T>
 RC<T> make_rc(const se_plan_s *p) {
     RC<T> rk;
@@ -2026,6 +2117,7 @@ RC<T> make_rc(const se_plan_s *p) {
     // rows farther than the last cell of a side hold nothing: cap the reach
     rk.reach[0] = std::min((int)ceil(p->rc * p->geom.icw[1] - 1e-9), p->geom.ncel[1] - 1);
     rk.reach[1] = std::min((int)ceil(p->rc * p->geom.icw[2] - 1e-9), p->geom.ncel[2] - 1);
+    rk.tab = (sizeof(T) == 8) ? erfc_table_ready() : 0;
     return rk;
 }
 

@@ -85,6 +85,7 @@ struct RC {
     T xi, xi2, c, c3, rc2;  // xi, xi^2, 2 xi/sqrt(pi), 4 xi^3/sqrt(pi), rc^2
     T ce;                   // -xi^2 / ln 2: exp(-xi^2 r^2) = 2^(ce r^2)
     int reach[2];           // rows of cells within reach on each side in y and in z
+    int tab;                // FP64: erfc and the Gaussian term from the device table (erfc_table_init)
 };
 
 // Constants of the k-space scaling of one system.
@@ -390,6 +391,11 @@ cudaError_t launch_spread_sub_tb(const GP<float> &g, int ntiles, int c0, bool st
                                  const float4 *xs, const float4 *fs, const float4 *qs, float *tb, cudaStream_t st);
 cudaError_t launch_merge_tiles(const GP<float> &g, const int *tile_start, const float *tb, float *grid, int c0,
                                cudaStream_t st);
+// FP64 real-space sums: the piecewise-polynomial table of erfc(x) and
+// (2/sqrt(pi)) x exp(-x^2) on the current device (realspace.cu); call before
+// the first evaluation of an FP64 plan (not during stream capture), then
+// make_rc<double> selects it
+cudaError_t erfc_table_init();
 // Stable slots (stable.cu): slot[i] = the rank of point i among the points
 // with its key and smaller indices, from the keys (< nkeys) and the bins'
 // starts; scratch holds stable_scratch_ints(N) ints
