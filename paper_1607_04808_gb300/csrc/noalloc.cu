@@ -99,6 +99,7 @@ extern "C" se_status_t se_real_space_noalloc(se_kernel_t kernel, se_prec_t prec,
     }
     // a plan on the stack: geometry of the cell list only, buffers in the scratch
     se_plan_s p;
+    p.erfc_table_off = true;
     p.kernel = kernel;
     p.prec = prec;
     p.N = N;

@@ -2093,11 +2093,13 @@ static int erfc_table_ready() {
     return g_erft_ready[dev];
 }
 
+// Copied at every FP64 plan or batch creation (32 KB), so that a context
+// reset (cudaDeviceReset) followed by new plans finds the table again.
 cudaError_t erfc_table_init() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e) return e;
-    if (dev < 0 || dev >= 64 || g_erft_ready[dev]) return cudaSuccess;
+    if (dev < 0 || dev >= 64) return cudaSuccess;
     static std::vector<double> tab;
     if (tab.empty()) erfc_table_host(tab);
     if ((e = cudaMemcpyToSymbol(g_erft, tab.data(), tab.size() * sizeof(double)))) return e;
@@ -2117,7 +2119,7 @@ RC<T> make_rc(const se_plan_s *p) {
     // rows farther than the last cell of a side hold nothing: cap the reach
     rk.reach[0] = std::min((int)ceil(p->rc * p->geom.icw[1] - 1e-9), p->geom.ncel[1] - 1);
     rk.reach[1] = std::min((int)ceil(p->rc * p->geom.icw[2] - 1e-9), p->geom.ncel[2] - 1);
-    rk.tab = (sizeof(T) == 8) ? erfc_table_ready() : 0;
+    rk.tab = (sizeof(T) == 8 && !p->erfc_table_off) ? erfc_table_ready() : 0;
     return rk;
 }
 

@@ -253,6 +253,10 @@ struct se_plan_s {
     bool deterministic = false;
     int *rs_scratch = nullptr;  // stable_scratch_ints(rs_cap) ints
     int64_t rs_cap = 0;
+    // FP64 radial functions from exp and the erfcx fit instead of the device
+    // table (the allocation-free entry point, which keeps nothing that a
+    // context reset would lose)
+    bool erfc_table_off = false;
     bool have_fwd = false, have_inv = false, have_fwd3 = false;
     cudaStream_t last_stream = nullptr;
     // overlapped evaluation (FP32): the Fourier part on a high-priority internal
