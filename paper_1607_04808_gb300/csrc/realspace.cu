@@ -1053,11 +1053,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SE_RS_SYM_MINB : 2)
 #ifndef SE_RS_SYMC_MINB
 #define SE_RS_SYMC_MINB 4
 #endif
-// SE_RS_SYMC_TC: targets per cluster of the forward stokeslet and rotlet
-// kernels (the stresslet and the gradient modes keep 8)
-#ifndef SE_RS_SYMC_TC
-#define SE_RS_SYMC_TC 8
-#endif
 // the stresslet's paired pair sum needs more registers: 2 blocks of 256 (128 each)
 #ifndef SE_RS_SYMC_MINB_STR
 #define SE_RS_SYMC_MINB_STR 2
@@ -1080,8 +1075,8 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
                 const int *__restrict__ ncl_total, const int *__restrict__ perm, float *__restrict__ u,
                 float *__restrict__ uj, int *__restrict__ status, float *__restrict__ rt,
                 const float4 *__restrict__ gs = nullptr) {
+    constexpr int WPB = 8, TC = 8, QN = 64;
     constexpr bool STR = (KERNEL == SE_STRESSLET);
-    constexpr int WPB = 8, TC = (STR || GRAD) ? 8 : SE_RS_SYMC_TC, QN = 64;
     static_assert(!(PER && STR), "periodic plans sum the stresslet with k_real_cmp");
     static_assert(!(GRAD && PER), "the gradient mode is for free-space plans");
     constexpr bool HQ = STR || GRAD;   // a third vector per point: q, or g
@@ -1504,14 +1499,11 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
             }
     }
     // sum the accumulators over the lanes: a reduce-scatter over lane bits 4,
-    // 3, 2 (and 1 for clusters of 16) leaves lane l with the 3 components of
-    // target (l >> 2) & 7 (or (l >> 1) & 15) summed over 32 / TC lanes, then
-    // butterflies over the lower bits finish the sums
-    static_assert(TC == 8 || TC == 16, "clusters of 8 or 16 targets");
-    constexpr int LT = TC == 16 ? 4 : 3, LW = 32 >> LT;  // log2 TC; lanes per target
+    // 3, 2 leaves lane l with the 3 components of target ((l >> 2) & 7) summed
+    // over 8 lanes, then butterflies over bits 1, 0 finish the sums
     float* a = &acc[0][0];
 #pragma unroll
-    for (int h = 16, len = 3 * TC; h >= LW; h >>= 1, len >>= 1) {
+    for (int h = 16, len = 3 * TC; h >= 4; h >>= 1, len >>= 1) {
         const bool up = (lane & h) != 0;
 #pragma unroll
         for (int i = 0; i < len / 2; i++) {
@@ -1521,14 +1513,13 @@ __global__ void __launch_bounds__(256, (KERNEL == SE_STRESSLET || GRAD) ? SE_RS_
         }
     }
 #pragma unroll
-    for (int d = 0; d < 3; d++)
-#pragma unroll
-        for (int o = LW / 2; o >= 1; o >>= 1) a[d] += __shfl_xor_sync(FULL, a[d], o);
+    for (int d = 0; d < 3; d++) {
+        a[d] += __shfl_xor_sync(FULL, a[d], 2);
+        a[d] += __shfl_xor_sync(FULL, a[d], 1);
+    }
     if (__any_sync(FULL, coinc) && lane == 0) atomicOr(status, FLAG_COINCIDENT);
-    int tt = 0;
-#pragma unroll
-    for (int k = 0; k < LT; k++) tt |= ((lane >> (4 - k)) & 1) << (LT - 1 - k);
-    if ((lane & (LW - 1)) == 0 && tt < cl.y) {
+    const int tt = (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && tt < cl.y) {
         if (rt) {
             // overlapped evaluation: u is being written by the gather meanwhile
             *reinterpret_cast<float4 *>(rt + 4 * (size_t)(cl.x + tt)) = make_float4(a[0], a[1], a[2], 0.f);
@@ -1949,9 +1940,7 @@ cudaError_t launch_real_k(se_plan_s *p, cudaStream_t st, const RC<T> &rk, T *u, 
     // targets per cluster: the symmetric kernel's or the full-list kernel's
     // (FP32 runs the transposed symmetric kernel, clusters of 8 targets)
     constexpr bool symc = sizeof(T) == 4 && SE_RS_SYMC;
-    constexpr int TPW = SE_RS_TPW,
-                  TPWS = symc ? (KERNEL == SE_STRESSLET ? 8 : SE_RS_SYMC_TC)
-                              : sizeof(T) == 4 ? SE_RS_SYM_TPW : SE_RS_SYM_TPW64;
+    constexpr int TPW = SE_RS_TPW, TPWS = symc ? 8 : sizeof(T) == 4 ? SE_RS_SYM_TPW : SE_RS_SYM_TPW64;
     const int tpw = sym ? TPWS : TPW;
     const int nrows = p->geom.ncel[1] * p->geom.ncel[2];
     k_cluster_count<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p->geom.ncel[0], tpw, p->b.cnt_r, p->b.ncl);
